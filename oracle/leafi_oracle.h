@@ -1,0 +1,122 @@
+/*
+ * LeaFi oracle — TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct CPU restatement of the LeaFi search path
+ * (Wang, Ileana, Palpanas, "LeaFi: Data Series Indexes on Steroids with
+ * Learned Filters", SIGMOD 2025).  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library; the product path never
+ * does, and this file shares no code with the CUDA implementation.
+ *
+ * Floating point: distances are the canonical float32 definition below (the
+ * decision precision of the product); everything else is float64.
+ */
+#ifndef LEAFI_ORACLE_H
+#define LEAFI_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct or_tree or_tree;
+
+enum { OR_DSTREE = 0, OR_ISAX = 1 };
+
+/* Canonical squared Euclidean distance (Sec. 3, "Similarity search"):
+ * acc = 0; for i in 0..m-1 { t = q_i - x_i; acc = fmaf(t, t, acc); }  (float32). */
+float or_sqdist(const float* q, const float* x, int m);
+
+/* Brute-force k-NN (Sec. 3 problem statement): the k series with the smallest
+ * (canonical d^2, id), lexicographic.  Outputs nq x k; pads with -1 / +inf. */
+void or_knn(const float* X, int64_t n, int m, const float* Q, int64_t nq, int k,
+            int64_t* ids, float* d2);
+
+/* Segment statistics of one series from float64 prefix sums. */
+void or_segment_stats(const float* x, int m, int s, int e, double* mu, double* sd);
+
+/* DSTree (EAPCA) build; X must stay alive while the tree is used. */
+or_tree* or_dstree_build(const float* X, int64_t n, int m, int leaf_cap, int init_segments);
+/* iSAX build: w PAA segments, 2^card_bits symbols. */
+or_tree* or_isax_build(const float* X, int64_t n, int m, int leaf_cap, int w, int card_bits);
+void or_tree_free(or_tree* t);
+
+int32_t or_tree_n_leaves(const or_tree* t);
+int32_t or_tree_n_nodes(const or_tree* t);
+/* leaf id of every series (original id order) */
+void or_tree_leaf_of(const or_tree* t, int32_t* leaf_of);
+void or_tree_leaf_sizes(const or_tree* t, int64_t* sizes);
+/* series ids of one leaf (ascending); returns the count */
+int64_t or_tree_leaf_members(const or_tree* t, int32_t leaf, int64_t* ids, int64_t cap);
+/* iSAX breakpoints beta_1..beta_{2^b - 1} (float64) */
+void or_isax_breakpoints(int card_bits, double* beta);
+
+/* Leaf lower bounds LB^2 (float64, max over the root-to-leaf path), nq x L. */
+void or_leaf_lb2(const or_tree* t, const float* Q, int64_t nq, double* lb2);
+/* Route leaf of each query (descend by the split rules). */
+void or_route(const or_tree* t, const float* Q, int64_t nq, int32_t* leaf);
+
+/* Per-(query, leaf) top-k inside one leaf: for each query i, leaf leaves[i*nl + j]
+ * (j < nl); outputs [nq][nl][k] (d2, id), padded with +inf / -1. */
+void or_leaf_topk(const or_tree* t, const float* Q, int64_t nq, const int32_t* leaves, int nl,
+                  int k, float* d2, int64_t* ids);
+
+/* MLP filters m -> h -> 1, ReLU hidden, linear output (Sec. 5.1): float64. */
+void or_mlp_forward(const float* W1, const float* b1, const float* w2, const float* b2,
+                    int F, int h, int m, const float* Q, int64_t nq, double* out);
+
+/* Training targets d^L (Alg. 1, Sec. 4.3): global queries x filtered leaves and
+ * local queries x their own leaf, Euclidean float32 (sqrtf of canonical d^2). */
+void or_train_targets(const or_tree* t, const int32_t* filter_leaf, int F,
+                      const float* Qg, int64_t ng, const float* Ql, int64_t nl,
+                      float* Tg /* ng x F */, float* Tl /* F x nl */);
+
+typedef struct {
+  int32_t n_gtrain, n_gval;   /* global queries: first n_gtrain train, next n_gval val */
+  int32_t n_ltrain, n_lval;   /* local queries per filter */
+  int32_t batch;              /* minibatch size */
+  int32_t max_epochs;
+  int32_t patience;           /* epochs without improvement before lr /= 10 */
+  double lr0, lr_min;
+} or_train_params;
+
+/* SGD training of all F filters (Sec. 5.1).  Weights in/out (float32, updated in
+ * place with the best-validation weights).  perms: [max_epochs][n_gtrain+n_ltrain].
+ * epochs_run/best_val (nullable) receive per-filter statistics. */
+void or_train(const or_train_params* p, int F, int h, int m,
+              const float* Qg, const float* Tg, const float* Ql, const float* Tl,
+              const int32_t* perms, float* W1, float* b1, float* w2, float* b2,
+              int32_t* epochs_run, double* best_val);
+
+/* Auto-tuner learning (Alg. 4) for one k: calibration queries Qc (nc).
+ * Outputs alpha_sorted [F][nc] (descending) and qprime [nc] (running-min
+ * of the calibration recall at each sorted position). */
+void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const float* w2,
+                      const float* b2, const int32_t* filter_leaf, int F, int h,
+                      const float* Qc, int64_t nc, int k, int wave,
+                      double* alpha_sorted, double* qprime);
+
+/* Sorted position j* for a target (STEP reading): the largest j with
+ * qprime[j] >= target; -1 means "no position meets it -> filters off". */
+int32_t or_offset_position(const double* qprime, int64_t nc, double target);
+
+/* Steffen (1990) monotone interpolation through (x_i, y_i), x strictly increasing,
+ * evaluated at xs (clamped to the end points). */
+double or_steffen_eval(const double* x, const double* y, int n, double xs);
+
+/* LeaFi search (Alg. 2) in wave semantics: route leaf first, then waves of up to
+ * `wave` leaves in (LB^2, leaf id) order.  Per query: k[i], kclass index kc[i]
+ * (-1 = filters off) and sorted position jpos[i] (-1 = filters off).  Offsets
+ * o_f = alpha_sorted[f][jpos].  Outputs nq x kmax ids/d2 and per-query stats
+ * [leaves_scanned, series_scanned, lb_pruned, filter_pruned] plus min_margin
+ * = min over filter decisions of |d^F - bsf| (for near-tie accounting). */
+void or_leafi_search(const or_tree* t, const float* W1, const float* b1, const float* w2,
+                     const float* b2, const int32_t* filter_leaf, int F, int h,
+                     const double* alpha_sorted, int64_t nc,
+                     const float* Q, int64_t nq, const int32_t* k, const int32_t* jpos,
+                     int kmax, int wave, int64_t* ids, float* d2, int64_t* stats,
+                     double* min_margin);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,385 @@
+"""Pins of the oracle against facts fixed outside it (no GPU).
+
+Each test checks one oracle function against something other than itself:
+hand-worked golden cases (tests/golden/, cited), closed forms, textbook
+library values, exhaustive enumeration on tiny inputs, or invariants that the
+mathematics guarantees.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+import fixtures as fx
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- distances
+
+def test_sqdist_within_float32_bound_of_exact():
+    """Canonical float32 d^2 is within gamma_{m+1} of the exact value (Higham)."""
+    rng = np.random.default_rng(1)
+    m = 256
+    u = 2.0 ** -24
+    gamma = (m + 1) * u / (1 - (m + 1) * u)
+    for _ in range(200):
+        q = rng.standard_normal(m).astype(np.float32)
+        x = rng.standard_normal(m).astype(np.float32)
+        exact = float(np.sum((q.astype(np.float64) - x.astype(np.float64)) ** 2))
+        assert abs(float(O.sqdist(q, x)) - exact) <= gamma * exact
+
+
+def test_sqdist_integer_data_exact():
+    q = np.array([3, -1, 2, 0, 5], np.float32)
+    x = np.array([1, 1, -2, 0, 5], np.float32)
+    assert O.sqdist(q, x) == np.float32(4 + 4 + 16)
+
+
+def test_knn_matches_exhaustive_enumeration_with_ties():
+    """Integer-valued data makes every distance exact and ties frequent: the
+    oracle must return the k smallest (d^2, id) pairs of the definition."""
+    rng = np.random.default_rng(7)
+    for m in (4, 8, 16):
+        X = rng.integers(-2, 3, size=(64, m)).astype(np.float32)
+        Q = rng.integers(-2, 3, size=(20, m)).astype(np.float32)
+        for k in (1, 3, 10, 64):
+            ids, d2 = O.knn(X, Q, k)
+            for i in range(Q.shape[0]):
+                d = ((X.astype(np.int64) - Q[i].astype(np.int64)) ** 2).sum(1)
+                order = sorted(range(X.shape[0]), key=lambda s: (d[s], s))[:k]
+                assert ids[i].tolist() == order
+                assert d2[i].tolist() == [float(d[s]) for s in order]
+
+
+def test_knn_pads_when_k_exceeds_n():
+    X = np.eye(3, dtype=np.float32)
+    ids, d2 = O.knn(X, X[:1], 5)
+    assert ids[0].tolist() == [0, 1, 2, -1, -1]
+    assert np.isinf(d2[0, 3:]).all()
+
+
+# ---------------------------------------------------------------- statistics
+
+def test_segment_stats_closed_form():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(96).astype(np.float32)
+    for s, e in [(0, 96), (0, 1), (10, 37), (95, 96)]:
+        mu, sd = O.segment_stats(x, s, e)
+        seg = x[s:e].astype(np.float64)
+        assert mu == pytest.approx(seg.mean(), abs=1e-13)
+        assert sd == pytest.approx(seg.std(), abs=1e-7)
+
+
+# ---------------------------------------------------------------- DSTree
+
+def test_dstree_lb_hand_example():
+    g = _golden("dstree_lb_hand.json")
+    X = np.array(g["series"], np.float32)
+    t = O.Tree(X, "dstree", leaf_cap=g["leaf_cap"], init_segments=g["init_segments"])
+    assert t.L == 1
+    lb = t.lb2(np.array([g["query"]], np.float32))
+    assert lb[0, 0] == g["lb2"]
+    _, d2 = O.knn(X, np.array([g["query"]], np.float32), 2)
+    assert d2[0].tolist() == g["d2"]
+
+
+def test_dstree_split_hand_example():
+    g = _golden("dstree_split_hand.json")
+    X = np.array(g["series"], np.float32)
+    t = O.Tree(X, "dstree", leaf_cap=g["leaf_cap"], init_segments=g["init_segments"])
+    assert t.L == g["n_leaves"]
+    assert t.n_nodes == g["n_nodes"]
+    assert t.leaf_of().tolist() == g["leaf_of"]
+    # routing sends every series to its own leaf
+    assert t.route(X).tolist() == g["leaf_of"]
+
+
+@pytest.fixture(scope="module")
+def rw():
+    X = fx.random_walk(6000, 64, seed=11)
+    Q = fx.test_queries(X, 40, seed=12)
+    return X, Q
+
+
+def test_dstree_structure_and_lb_invariant(rw):
+    X, Q = rw
+    t = O.Tree(X, "dstree", leaf_cap=300, init_segments=4)
+    sizes = t.leaf_sizes()
+    assert sizes.sum() == X.shape[0] and sizes.max() <= 300 and sizes.min() >= 1
+    lo = t.leaf_of()
+    for leaf in range(t.L):
+        mem = t.leaf_members(leaf)
+        assert (lo[mem] == leaf).all() and (np.diff(mem) > 0).all()
+    # every series routes to the leaf that holds it
+    assert (t.route(X[::7]) == lo[::7]).all()
+    lb = t.lb2(Q)
+    leaves = np.tile(np.arange(t.L, dtype=np.int32), (Q.shape[0], 1))
+    d2, _ = t.leaf_topk(Q, leaves, 1)
+    # LB^2 <= leaf min d^2 (exact arithmetic); the deflated test never prunes a true minimum
+    assert (lb * (1 - 1e-4) <= d2[:, :, 0]).all()
+    assert (lb <= d2[:, :, 0] * (1 + 1e-5)).all()
+    # a series' own leaf has LB 0 to itself (its statistics lie inside the ranges)
+    own = t.lb2(X[:50])
+    assert (own[np.arange(50), lo[:50]] == 0.0).all()
+
+
+# ---------------------------------------------------------------- iSAX
+
+def test_isax_breakpoints_are_normal_quantiles():
+    for bits in (1, 2, 3, 8):
+        beta = O.isax_breakpoints(bits)
+        C = 1 << bits
+        ref = scipy.stats.norm.ppf(np.arange(1, C) / C)
+        assert np.allclose(beta, ref, rtol=0, atol=1e-12)
+    assert O.isax_breakpoints(8)[127] == 0.0
+    b2 = O.isax_breakpoints(2)
+    assert b2[1] == 0.0 and abs(b2[2] - 0.6744897501960817) < 1e-12
+
+
+def test_isax_mindist_hand_example():
+    g = _golden("isax_mindist_hand.json")
+    X = np.array(g["series"], np.float32)
+    t = O.Tree(X, "isax", leaf_cap=g["leaf_cap"], isax_w=g["w"], isax_bits=g["bits"])
+    assert t.L == 1
+    q = np.array([g["query"]], np.float32)
+    assert t.lb2(q)[0, 0] == g["lb2"]
+    assert O.knn(X, q, 1)[1][0, 0] == g["d2"]
+
+
+def test_isax_structure_and_lb_invariant(rw):
+    X, Q = rw
+    t = O.Tree(X, "isax", leaf_cap=200, isax_w=16, isax_bits=8)
+    sizes = t.leaf_sizes()
+    assert sizes.sum() == X.shape[0] and sizes.min() >= 1
+    lo = t.leaf_of()
+    assert (t.route(X[::5]) == lo[::5]).all()
+    lb = t.lb2(Q)
+    leaves = np.tile(np.arange(t.L, dtype=np.int32), (Q.shape[0], 1))
+    d2, _ = t.leaf_topk(Q, leaves, 1)
+    assert (lb * (1 - 1e-4) <= d2[:, :, 0]).all()
+
+
+# ---------------------------------------------------------------- MLP filter
+
+def test_mlp_forward_hand_weights():
+    """W1 = I, b1 = 0, w2 = 1, b2 = 0.5  =>  y = 0.5 + sum_i relu(q_i)."""
+    m = 8
+    W1 = np.eye(m, dtype=np.float32)[None]
+    b1 = np.zeros((1, m), np.float32)
+    w2 = np.ones((1, m), np.float32)
+    b2 = np.array([0.5], np.float32)
+    Q = np.array([[1, -2, 3, -4, 0.25, 0, -1, 2]], np.float32)
+    y = O.mlp_forward(W1, b1, w2, b2, Q)
+    assert y[0, 0] == 0.5 + 1 + 3 + 0.25 + 2
+    # one-hot hidden unit with a negative bias is cut by the ReLU
+    b1n = np.full((1, m), -10.0, np.float32)
+    assert O.mlp_forward(W1, b1n, w2, b2, Q)[0, 0] == 0.5
+
+
+def _loss(W1, b1, w2, b2, X, T):
+    Z = X @ W1.T + b1
+    Y = np.maximum(Z, 0) @ w2 + b2
+    return np.mean((Y - T) ** 2)
+
+
+def test_sgd_step_matches_finite_difference_gradient():
+    """One full-batch SGD step moves every weight by -lr * dLoss/dw."""
+    rng = np.random.default_rng(5)
+    m = h = 6
+    ng, nl = 10, 5
+    Qg = rng.standard_normal((ng, m)).astype(np.float32)
+    Ql = rng.standard_normal((1, nl, m)).astype(np.float32)
+    Tg = rng.uniform(1, 3, (ng, 1)).astype(np.float32)
+    Tl = rng.uniform(1, 3, (1, nl)).astype(np.float32)
+    W1 = rng.uniform(-.5, .5, (1, h, m)).astype(np.float32)
+    b1 = rng.uniform(-.5, .5, (1, h)).astype(np.float32)
+    w2 = rng.uniform(-.5, .5, (1, h)).astype(np.float32)
+    b2 = np.array([0.1], np.float32)
+    p = O.TrainParams(n_gtrain=8, n_gval=2, n_ltrain=4, n_lval=1, batch=12, max_epochs=1,
+                      patience=10, lr0=1e-3, lr_min=1e-5)
+    perms = np.arange(12, dtype=np.int32)[None]
+    (W1n, b1n, w2n, b2n), ep, _ = O.train(p, Qg, Tg, Ql, Tl, perms, W1, b1, w2, b2)
+    X = np.concatenate([Qg[:8], Ql[0, :4]]).astype(np.float64)
+    T = np.concatenate([Tg[:8, 0], Tl[0, :4]]).astype(np.float64)
+    P0 = [a.astype(np.float64)[0] for a in (W1, b1, w2)] + [np.float64(b2[0])]
+
+    def L(params):
+        return _loss(params[0], params[1], params[2], params[3], X, T)
+
+    eps = 1e-6
+    newp = [W1n[0], b1n[0], w2n[0], b2n[0]]
+    for pi in range(4):
+        base = np.array(P0[pi], dtype=np.float64)
+        flat = base.reshape(-1)
+        for idx in range(flat.size):
+            plus = [np.array(a, copy=True) for a in P0]
+            minus = [np.array(a, copy=True) for a in P0]
+            plus[pi].reshape(-1)[idx] += eps
+            minus[pi].reshape(-1)[idx] -= eps
+            g = (L(plus) - L(minus)) / (2 * eps)
+            moved = float(np.asarray(newp[pi], np.float64).reshape(-1)[idx]) - flat[idx]
+            assert moved == pytest.approx(-1e-3 * g, abs=2e-7)
+
+
+def test_training_reduces_validation_loss_and_plateau_stops():
+    rng = np.random.default_rng(9)
+    m = h = 16
+    Qg = rng.standard_normal((50, m)).astype(np.float32)
+    Ql = rng.standard_normal((2, 20, m)).astype(np.float32)
+    wtrue = rng.standard_normal(m)
+    Tg = np.abs(Qg @ wtrue)[:, None].repeat(2, 1).astype(np.float32)
+    Tl = np.abs(Ql @ wtrue).astype(np.float32)
+    W = fx.filter_init(2, m, h, seed=3)
+    p = O.TrainParams(n_gtrain=40, n_gval=10, n_ltrain=16, n_lval=4, batch=8, max_epochs=400,
+                      patience=3, lr0=0.01, lr_min=1e-5)
+    perms = fx.epoch_permutations(400, 56, seed=4)
+    Wt, ep, bv = O.train(p, Qg, Tg, Ql, Tl, perms, *W)
+    Xv = np.concatenate([Qg[40:], Ql[0, 16:]])
+    Tv = np.concatenate([Tg[40:, 0], Tl[0, 16:]])
+    before = _loss(*(a[0].astype(np.float64) for a in W[:3]), np.float64(W[3][0]), Xv, Tv)
+    after = _loss(*(a[0].astype(np.float64) for a in Wt[:3]), np.float64(Wt[3][0]), Xv, Tv)
+    assert after < 0.8 * before
+    assert after == pytest.approx(bv[0], rel=1e-4)
+    # lr goes 1e-2 -> 1e-3 -> 1e-4 -> 1e-5 and stops at the next plateau
+    assert (ep < 400).all()
+
+
+# ---------------------------------------------------------------- Steffen
+
+def test_steffen_properties():
+    x = np.array([0.0, 1.0, 2.5, 3.0, 5.0])
+    y = np.array([0.0, 0.5, 0.6, 2.0, 2.1])
+    for xi, yi in zip(x, y):
+        assert O.steffen_eval(x, y, xi) == pytest.approx(yi, abs=1e-15)
+    xs = np.linspace(-1, 6, 701)
+    ys = np.array([O.steffen_eval(x, y, v) for v in xs])
+    assert (np.diff(ys) >= -1e-15).all()          # monotone on monotone data
+    assert ys.min() >= y.min() - 1e-15 and ys.max() <= y.max() + 1e-15  # no overshoot
+    lin = 3.0 * x - 1.0
+    for v in np.linspace(0, 5, 51):
+        assert O.steffen_eval(x, lin, v) == pytest.approx(3.0 * v - 1.0, abs=1e-12)
+
+
+# ---------------------------------------------------------------- search
+
+def _alg2_sequential(lb_row, route, lists, df_row, k):
+    """Literal Alg. 2 loop: route leaf first, then ascending (LB, id)."""
+    L = lb_row.shape[0]
+    order = [route] + sorted((l for l in range(L) if l != route), key=lambda l: (lb_row[l], l))
+    res = []
+    bsf = np.float32(np.inf)
+    for leaf in order:
+        if lb_row[leaf] * (1 - 1e-4) > float(bsf):
+            continue
+        if df_row is not None and not np.isnan(df_row[leaf]) and \
+                df_row[leaf] > float(np.sqrt(np.float32(bsf))):
+            continue
+        d2, ids = lists[leaf]
+        res = sorted(res + [(float(a), int(b)) for a, b in zip(d2, ids) if b >= 0])[:k]
+        bsf = np.float32(res[k - 1][0]) if len(res) == k else np.float32(np.inf)
+    return [b for _, b in res]
+
+
+@pytest.fixture(scope="module")
+def small_index():
+    X = fx.random_walk(3000, 32, seed=21)
+    t = O.Tree(X, "dstree", leaf_cap=150, init_segments=4)
+    Q = fx.test_queries(X, 30, seed=22)
+    return X, t, Q
+
+
+def test_exact_search_equals_brute_force_for_any_wave(small_index):
+    X, t, Q = small_index
+    for k in (1, 5, 40):
+        bf_ids, bf_d2 = O.knn(X, Q, k)
+        for wave in (1, 3, 1000):
+            ids, d2, st, _ = O.leafi_search(t, None, None, None, Q, k, -1, wave)
+            assert np.array_equal(ids, bf_ids) and np.array_equal(d2, bf_d2)
+            assert (st[:, 0] <= t.L).all()
+
+
+def test_wave_one_is_the_sequential_algorithm(small_index):
+    X, t, Q = small_index
+    rng = np.random.default_rng(4)
+    F = min(6, t.L)
+    W = fx.filter_init(F, 32, 32, seed=5)
+    fl = np.arange(F, dtype=np.int32)
+    alpha = np.sort(rng.uniform(0, 3, (F, 7)), axis=1)[:, ::-1].copy()
+    P = O.mlp_forward(*W, Q)
+    lb = t.lb2(Q)
+    route = t.route(Q)
+    leaves = np.tile(np.arange(t.L, dtype=np.int32), (Q.shape[0], 1))
+    for k in (1, 4):
+        d2l, idl = t.leaf_topk(Q, leaves, k)
+        for j in (0, 3, 6):
+            ids, _, _, _ = O.leafi_search(t, W, fl, alpha, Q, k, j, 1)
+            for i in range(Q.shape[0]):
+                df = np.full(t.L, np.nan)
+                df[fl] = P[i] - alpha[:, j]
+                lists = [(d2l[i, l], idl[i, l]) for l in range(t.L)]
+                ref = _alg2_sequential(lb[i], route[i], lists, df, k)
+                assert ids[i, :len(ref)].tolist() == ref
+
+
+def test_autotuner_table_matches_search_recall(small_index):
+    """Alg. 4's simulated quality at each position equals the recall that the
+    search itself reaches with those offsets (measured against brute force)."""
+    X, t, Q = small_index
+    F = t.L
+    W = fx.filter_init(F, 32, 32, seed=8)
+    fl = np.arange(F, dtype=np.int32)
+    Qc = Q[:12]
+    for k in (1, 3):
+        alpha, qp = O.fit_autotuner(t, W, fl, Qc, k, 2)
+        assert (np.diff(alpha, axis=1) <= 0).all()          # descending per filter
+        assert (np.diff(qp) <= 0).all() and qp[0] == 1.0     # largest offsets are safe
+        bf, _ = O.knn(X, Qc, k)
+        run = np.inf
+        for j in range(Qc.shape[0]):
+            ids, _, _, _ = O.leafi_search(t, W, fl, alpha, Qc, k, j, 2)
+            r = O.recall_at_k(ids, bf, k).mean()
+            run = min(run, r)
+            assert qp[j] == pytest.approx(run, abs=1e-12)
+
+
+def test_offset_position_step_rule():
+    qp = np.array([1.0, 1.0, 0.99, 0.97, 0.97, 0.9])
+    assert O.offset_position(qp, 0.99) == 2
+    assert O.offset_position(qp, 0.95) == 4
+    assert O.offset_position(qp, 1.0) == 1
+    assert O.offset_position(np.array([0.9, 0.8]), 0.95) == -1
+
+
+def test_huge_offsets_give_the_exact_answer(small_index):
+    X, t, Q = small_index
+    F = t.L
+    W = fx.filter_init(F, 32, 32, seed=8)
+    alpha = np.full((F, 1), 1e30)
+    ids, d2, _, _ = O.leafi_search(t, W, np.arange(F, dtype=np.int32), alpha, Q, 3, 0, 4)
+    bf_ids, bf_d2 = O.knn(X, Q, 3)
+    assert np.array_equal(ids, bf_ids)
+
+
+def test_train_targets_are_leaf_minima(small_index):
+    X, t, Q = small_index
+    fl = np.array([0, t.L - 1], np.int32)
+    Ql = np.stack([Q[:5], Q[5:10]])
+    Tg, Tl = O.train_targets(t, fl, Q, Ql)
+    for f, leaf in enumerate(fl):
+        mem = t.leaf_members(int(leaf))
+        for i in range(Q.shape[0]):
+            d = min(O.sqdist(Q[i], X[s]) for s in mem)
+            assert Tg[i, f] == np.sqrt(np.float32(d))
+        for i in range(5):
+            d = min(O.sqdist(Ql[f, i], X[s]) for s in mem)
+            assert Tl[f, i] == np.sqrt(np.float32(d))
