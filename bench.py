@@ -1,0 +1,393 @@
+"""Benchmark: LeaFi-enhanced DSTree k-NN search on one B300 (weak-scaled replicas for N > 1).
+
+Workload (batched 1-NN search): N = 1,000,000 z-normalised random walks of
+length 256 (float32, 1.02 GB resident, larger than L2), DSTree leaf capacity
+10,000, MLP filters on the 100 largest leaves trained on 2,000 queries
+(1,500 global + 500 local per leaf) and auto-tuned for 1-NN, then 10,000
+noise-perturbed queries (10/20/30/40% noise) searched in launches of 256 at a
+99% recall target.  One step = the whole query set (40 launches).  The plain
+summarisation-bound search of the same index (exact mode) is timed beside it.
+
+Prints one JSON line (rank 0).  `--impl reference` times the oracle (plain C
+restatement, host cores) on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fixtures as fx  # noqa: E402
+
+M = 256
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}
+SMS = 148
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="leafi", choices=["leafi", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--queries", type=int, default=10_000)
+    ap.add_argument("--launch", type=int, default=256)
+    ap.add_argument("--filters", type=int, default=100)
+    ap.add_argument("--leaf-cap", type=int, default=10_000)
+    ap.add_argument("--epochs", type=int, default=1000)
+    ap.add_argument("--wave", type=int, default=8)
+    ap.add_argument("--target", type=float, default=0.99)
+    ap.add_argument("--cpu-sample", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local, dist
+
+
+def max_over_ranks(x, dist, device):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def workload_config(a):
+    return {"workload": "batched 1-NN LeaFi-DSTree search, N=%d random walks, m=%d, "
+                        "leaf capacity %d, %d filters, %d queries in launches of %d, recall target %.2f"
+                        % (a.n, M, a.leaf_cap, a.filters, a.queries, a.launch, a.target),
+            "n_series": a.n, "length": M, "leaf_capacity": a.leaf_cap, "filters": a.filters,
+            "queries": a.queries, "launch": a.launch, "recall_target": a.target,
+            "k": 1, "wave": a.wave, "l2": "inputs larger than L2 (1.02 GB series)"}
+
+
+def cpu_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def oracle_leafi_rate(X, fl, W, alpha, qp, Q, leaf_cap, wave, target, sample):
+    """Time the oracle's LeaFi search on `sample` queries (bounded CPU work)."""
+    import oracle as O
+    t = O.Tree(X, "dstree", leaf_cap=leaf_cap, init_segments=4)
+    j = O.offset_position(qp, target)
+    Qs = np.ascontiguousarray(Q[:sample])
+    t0 = time.perf_counter()
+    O.leafi_search(t, W, fl, alpha, Qs, 1, j, wave)
+    dt = time.perf_counter() - t0
+    return sample / dt, dt, t
+
+
+def run_reference(a):
+    """Oracle arm: the plain CPU restatement, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    oracle_build = O.build()
+    X = fx.random_walk(a.n, M)
+    Q = fx.test_queries(X, a.queries)
+    t = O.Tree(X, "dstree", leaf_cap=a.leaf_cap, init_segments=4)
+    # the oracle trains its own filters on the same draws (a short schedule keeps it bounded)
+    sizes = t.leaf_sizes()
+    F = min(a.filters, t.L)
+    fl = np.array(sorted(range(t.L), key=lambda l: (-sizes[l], l))[:F], np.int32)
+    W = fx.filter_init(F, M, M)
+    members = fx.leaf_members_from(t.leaf_of(), fl)
+    Qg, Ql = fx.training_queries(X, members, 1500, 500)
+    Tg, Tl = O.train_targets(t, fl, Qg, Ql)
+    p = O.TrainParams(max_epochs=3)
+    Wt, _, _ = O.train(p, Qg, Tg, Ql, Tl, fx.epoch_permutations(3, 1600), *W)
+    alpha, qp = O.fit_autotuner(t, Wt, fl, Qg[1200:], 1, a.wave)
+    j = O.offset_position(qp, a.target)
+    per = max(4, min(a.cpu_sample, 64))
+    times = []
+    for s in range(a.warmup + a.steps):
+        Qs = np.ascontiguousarray(Q[(s * per) % a.queries:][:per])
+        t0 = time.perf_counter()
+        O.leafi_search(t, Wt, fl, alpha, Qs, 1, j, a.wave)
+        if s >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = per / (ms / 1e3)
+    line = {"impl": "reference", "metric": "queries/s at 99% recall (LeaFi search)",
+            "value": value, "unit": "queries/s", "n_gpus": 0, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cpu_threads(),
+                             "kind": "oracle",
+                             "sample": "%d queries per step of the same workload (oracle filters "
+                                       "trained 3 epochs)" % per},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    rank, world, local, dist = dist_setup(a.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2502_01836_b300 as lf
+    from paper_2502_01836_b300.workflow import enhance
+
+    X = fx.random_walk(a.n, M)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=local))
+    stream = torch.cuda.current_stream(dev)
+    lf.leafi_set_stream(idx, stream.cuda_stream)
+    tp = lf.TrainParams(max_epochs=a.epochs)
+    t_train = time.perf_counter()
+    enh = enhance(idx, X, a.filters, tp, kclasses=(1,))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    info = lf.leafi_get_info(idx)
+    Q = fx.test_queries(X, a.queries, seed=fx.SEED_TEST + 1000 * rank)
+    Qd = torch.from_numpy(Q).to(dev)
+    nl = (a.queries + a.launch - 1) // a.launch
+    ids = torch.empty((a.queries, 1), dtype=torch.int64, device=dev)
+    dd = torch.empty((a.queries, 1), dtype=torch.float32, device=dev)
+    ex_ids = torch.empty_like(ids)
+    ex_d = torch.empty_like(dd)
+
+    def run(target, out_i, out_d, lat=None, stats=None):
+        for b in range(nl):
+            s0, s1 = b * a.launch, min(a.queries, (b + 1) * a.launch)
+            st = lf.SearchStats()
+            if lat is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            lf.leafi_search(idx, Qd[s0:s1], 1, target, out_i[s0:s1], out_d[s0:s1], st)
+            if lat is not None:
+                e1.record(stream)
+                lat.append((e0, e1))
+            if stats is not None:
+                for f, _ in lf.SearchStats._fields_:
+                    stats[f] = stats.get(f, 0) + getattr(st, f)
+
+    def timed(target, out_i, out_d, profile=False):
+        for _ in range(a.warmup):
+            run(target, out_i, out_d)
+        if profile:
+            lf.leafi_set_profiling(idx, True)
+        lat, stats = [], {}
+        barrier(dist)
+        torch.cuda.synchronize()
+        launches0 = lf.leafi_launch_count()
+        with Clocks(local) as ck:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.steps):
+                run(target, out_i, out_d, lat, stats)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier(dist)
+        launches = lf.leafi_launch_count() - launches0
+        ms = e0.elapsed_time(e1) / a.steps
+        kt = lf.leafi_get_kernel_times(idx) if profile else None
+        if profile:
+            lf.leafi_set_profiling(idx, False)
+        lats = [x.elapsed_time(y) for x, y in lat]
+        return ms, lats, stats, launches, ck.summary(), kt
+
+    # exact (plain-bound) search: ground truth and the comparison arm
+    ms_ex, lat_ex, st_ex, _, _, _ = timed(1.0, ex_ids, ex_d)
+    ms, lat, st, launches, clocks, kt = timed(a.target, ids, dd, profile=True)
+    recall = float((ids[:, 0] == ex_ids[:, 0]).float().mean().item())
+    ms_max = max_over_ranks(ms, dist, dev)
+    ms_ex_max = max_over_ranks(ms_ex, dist, dev)
+    value = world * a.queries / (ms_max / 1e3)
+    value_ex = world * a.queries / (ms_ex_max / 1e3)
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    Qh = Q.copy()
+    ih = np.zeros((a.queries, 1), np.int64)
+    dh = np.zeros((a.queries, 1), np.float32)
+    lf.leafi_search(idx, Qh[:a.launch], 1, a.target, ih[:a.launch], dh[:a.launch])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        for b in range(nl):
+            s0, s1 = b * a.launch, min(a.queries, (b + 1) * a.launch)
+            lf.leafi_search(idx, Qh[s0:s1], 1, a.target, ih[s0:s1], dh[s0:s1])
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / a.steps, dist, dev)
+    e2e = {"value": world * a.queries / (e2e_ms / 1e3), "unit": "queries/s",
+           "h2d_bytes_per_step": a.queries * M * 4, "d2h_bytes_per_step": a.queries * (8 + 4)}
+
+    # roofline of the dominant kernel (leaf scan), from per-launch CUDA events
+    pk, pk_kind = peaks()
+    scan_ms, scan_n = kt["leaf_scan"]
+    pairs = st["series_scanned"] / a.steps          # (query, series) distances per step
+    distinct = st["distinct_series"] / a.steps      # series of distinct leaves per round, per step
+    scan_launch_ms = scan_ms / max(scan_n, 1)
+    per_launch_pairs = pairs / max(scan_n / a.steps, 1)
+    flops_launch = per_launch_pairs * M * 3.0       # t = q - x; acc = fma(t, t, acc)
+    achieved_tf = flops_launch / (scan_launch_ms / 1e3) / 1e12
+    clk = pk.get("sm_max_mhz", 2032.0)
+    alu_peak = SMS * FP32_LANES * clk * 1e6 * 1.5 / 1e12   # FSUB+FFMA issue 3 FLOP per 2 instr
+    bytes_launch = distinct * M * 4 / max(scan_n / a.steps, 1)
+    achieved_gbs = bytes_launch / (scan_launch_ms / 1e3) / 1e9
+    hbm = pk.get("hbm_gbs", 6400.0)
+    roof_alu = achieved_tf / alu_peak
+    roof_hbm = achieved_gbs / hbm
+    if roof_alu >= roof_hbm:
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": roof_alu, "traffic": None,
+                    "peak_source": "148 SMs x 128 FP32 lanes x %.0f MHz x 1.5 FLOP/instr (%s clocks)"
+                                   % (clk, pk_kind)}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": roof_hbm, "traffic": None, "peak_source": pk_kind}
+    roofline["kernel"] = "leaf_scan"
+    roofline["hbm_view"] = {"achieved_gbs": achieved_gbs, "frac": roof_hbm}
+    roofline["alu_view"] = {"achieved_tflops": achieved_tf, "frac": roof_alu}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        try:
+            W = tuple(np.zeros_like(w) for w in enh.init_weights)
+            lf.leafi_get_filters(idx, *W)
+            alpha = np.zeros((a.filters, info.n_calib))
+            qp = np.zeros((1, info.n_calib))
+            lf.leafi_get_autotuners(idx, alpha, qp)
+            rate, dt, _ = oracle_leafi_rate(X, enh.filter_leaf, W, alpha, qp[0], Q, a.leaf_cap,
+                                            a.wave, a.target, a.cpu_sample)
+            cpu = {"value": rate, "unit": "queries/s", "cores": cpu_threads(), "kind": "oracle",
+                   "sample": "%d of the %d queries, LeaFi search with the same filters and "
+                             "auto-tuner tables (%.1f s)" % (a.cpu_sample, a.queries, dt)}
+        except Exception as e:  # reported, never fatal
+            cpu = {"value": None, "unit": "queries/s", "cores": cpu_threads(), "kind": "oracle",
+                   "sample": "failed: %s" % e}
+
+    if rank == 0:
+        lat_sorted = sorted(lat)
+        line = {
+            "metric": "queries/s at 99% recall (LeaFi search)", "value": value,
+            "unit": "queries/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(a),
+            "recall_at_1": recall,
+            "plain_lb": {"value": value_ex, "unit": "queries/s", "ms_per_step": ms_ex_max,
+                         "series_scanned_per_query": st_ex["series_scanned"] / (a.steps * a.queries),
+                         "p50_ms": float(np.percentile(lat_ex, 50)),
+                         "p99_ms": float(np.percentile(lat_ex, 99))},
+            "speedup_vs_plain_lb": value / value_ex,
+            "latency_per_launch_ms": {"p50": float(np.percentile(lat_sorted, 50)),
+                                      "p99": float(np.percentile(lat_sorted, 99))},
+            "series_scanned_per_query": st["series_scanned"] / (a.steps * a.queries),
+            "pruning_ratio": 1.0 - st["series_scanned"] / (a.steps * a.queries * a.n),
+            "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
+            "waves_per_launch": st["waves"] / max(st["batches"], 1),
+            "kernel_ms_per_step": {k: v[0] / a.steps for k, v in kt.items() if v[1]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
+            "build": {"leaves": info.n_leaves, "filters": info.n_filters,
+                      "train_and_tune_s": t_train,
+                      "epochs_run_mean": float(np.mean(enh.epochs_run))},
+        }
+        print(json.dumps(line), flush=True)
+    lf.leafi_free(idx)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

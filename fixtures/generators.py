@@ -21,7 +21,7 @@ __all__ = [
     "SEED_DATA", "SEED_TRAIN", "SEED_TEST", "SEED_WEIGHTS",
     "znorm_rows", "random_walk", "embedding_like", "pick_without_replacement",
     "noisy_queries", "test_queries", "filter_init", "epoch_permutations",
-    "uniform_sigmas",
+    "uniform_sigmas", "training_queries", "leaf_members_from",
 ]
 
 SEED_DATA = 2502018360
@@ -156,4 +156,43 @@ def epoch_permutations(epochs: int, n: int, seed: int = SEED_WEIGHTS) -> np.ndar
     out = np.empty((epochs, n), dtype=np.int32)
     for e in range(epochs):
         out[e] = g.permutation(n)
+    return out
+
+
+def training_queries(data: np.ndarray, leaf_members, n_global: int, n_local: int,
+                     seed: int = SEED_TRAIN, sigma_lo: float = 0.1, sigma_hi: float = 0.4):
+    """Training queries of Alg. 1 (GenerateGlobalQueries / GenerateLocalQueries).
+
+    Global: `n_global` distinct dataset series; local: `n_local` series of each
+    filtered leaf (members listed in `leaf_members[f]`, drawn without
+    replacement when the leaf is large enough, else with replacement).  Every
+    query gets Gaussian noise with sigma ~ U[sigma_lo, sigma_hi] and is
+    re-z-normalised.  Returns (Qg [n_global, m], Ql [F, n_local, m]).
+    """
+    n, m = data.shape
+    gi = pick_without_replacement(n, n_global, seed, stream=10)
+    Qg = noisy_queries(data[gi], uniform_sigmas(n_global, sigma_lo, sigma_hi, seed, 10), seed, 10)
+    F = len(leaf_members)
+    Ql = np.empty((F, n_local, m), np.float32)
+    for f, mem in enumerate(leaf_members):
+        mem = np.asarray(mem, np.int64)
+        s = 1000 + f
+        if mem.shape[0] >= n_local:
+            pick = mem[pick_without_replacement(mem.shape[0], n_local, seed, stream=s)]
+        else:
+            pick = mem[_rng(seed, _TAG_PICK, s).integers(0, mem.shape[0], n_local)]
+        Ql[f] = noisy_queries(data[pick], uniform_sigmas(n_local, sigma_lo, sigma_hi, seed, s),
+                              seed, s)
+    return Qg, Ql
+
+
+def leaf_members_from(leaf_of: np.ndarray, leaves) -> list:
+    """Series ids (ascending) of each listed leaf, from a leaf-of-series array."""
+    order = np.argsort(leaf_of, kind="stable")
+    sorted_leaf = leaf_of[order]
+    out = []
+    for l in leaves:
+        lo = np.searchsorted(sorted_leaf, l, "left")
+        hi = np.searchsorted(sorted_leaf, l, "right")
+        out.append(order[lo:hi])
     return out

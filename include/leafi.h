@@ -1,0 +1,243 @@
+/*
+ * leafi.h — C ABI of the B300-native LeaFi search path.
+ *
+ * LeaFi (Wang, Ileana, Palpanas, SIGMOD 2025) adds learned filters to the
+ * leaves of a tree-based data-series index (DSTree or iSAX).  Per query the
+ * path computes the index's summarisation lower bounds, runs every leaf's MLP
+ * filter in one batch, shifts the predictions by the conformal offset for the
+ * query's recall target, prunes, and scans the surviving leaves with squared
+ * Euclidean distance while keeping the k best-so-far.  The same scan produces
+ * the filters' training targets at build time.
+ *
+ * Conventions shared by every entry point:
+ *   - Array arguments may be host or device pointers (classified with
+ *     cudaPointerGetAttributes).  Host arrays are staged through the library;
+ *     device arrays are used in place on the index's stream.
+ *   - The caller owns every buffer passed in; the library owns the index and
+ *     everything reachable from it until leafi_free().
+ *   - Series and queries are float32, row-major, length m, z-normalised by
+ *     the caller (the paper's data is z-normalised; the library does not
+ *     re-normalise).
+ *   - Distances returned are Euclidean: sqrtf of the canonical squared
+ *     distance  acc = 0; for i < m: t = q_i - x_i; acc = fmaf(t, t, acc).
+ *     Results are ordered by (distance, original id) ascending; ties go to
+ *     the lowest id; missing entries (k > n) are id -1 / +inf.
+ *   - On any error nothing is written to the outputs, the status is returned
+ *     and leafi_last_error() describes it.  No entry point aborts the process.
+ *   - Calls on one index are serialised by an internal mutex.
+ */
+#ifndef LEAFI_H
+#define LEAFI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct leafi_index leafi_index;
+
+typedef enum {
+  LEAFI_OK = 0,
+  LEAFI_EINVAL = 1,      /* bad argument (size, pointer, parameter) */
+  LEAFI_ENOMEM = 2,      /* host or device allocation failed */
+  LEAFI_ECUDA = 3,       /* a CUDA call failed */
+  LEAFI_ETIMEOUT = 4,    /* a bounded device wait gave up */
+  LEAFI_ENOTTRAINED = 5, /* filters / auto-tuners needed but absent */
+  LEAFI_EINTERNAL = 6    /* internal consistency check failed */
+} leafi_status;
+
+enum { LEAFI_DSTREE = 0, LEAFI_ISAX = 1 };
+
+enum { LEAFI_MAX_K = 128, LEAFI_MAX_KCLASSES = 4 };
+
+/* ------------------------------------------------------------------ */
+/* Index building (Sec. 3 "Tree-based indexes"; Alg. 1 input I)        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t index_type;           /* LEAFI_DSTREE or LEAFI_ISAX */
+  int32_t leaf_capacity;        /* a leaf splits when it holds more series (paper: 10k) */
+  int32_t dstree_init_segments; /* DSTree root segmentation: equal segments (4) */
+  int32_t isax_segments;        /* iSAX PAA segments w (16); m % w == 0 */
+  int32_t isax_card_bits;       /* iSAX full cardinality 2^bits (8) */
+  int32_t wave;                 /* leaves taken per query per search wave (>= 1); the
+                                   auto-tuner calibrates this same schedule */
+  int32_t device;               /* CUDA device ordinal */
+} leafi_build_params;
+
+/* Build an index over n series of length m.  Copies `series` into
+ * leaf-contiguous device storage (16-byte aligned rows) owned by the index.
+ * device = -1 builds the tree alone on the host (inspection only: leaf
+ * sizes, leaf_of, info); every device entry point then returns LEAFI_EINVAL.
+ * Returns LEAFI_EINVAL for n < 1, m < 1, m > 512, bad parameters. */
+leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_build_params* p,
+                         leafi_index** out);
+
+/* Release everything owned by the index (NULL is accepted). */
+void leafi_free(leafi_index* index);
+
+/* Thread-local description of the last error on this thread. */
+const char* leafi_last_error(void);
+
+/* Kernels this library has launched in this process (all indexes); a
+ * diagnostic for counting device work between two points. */
+int64_t leafi_launch_count(void);
+
+/* Launch all later work of this index on `cuda_stream` (a cudaStream_t);
+ * NULL selects the legacy default stream. */
+leafi_status leafi_set_stream(leafi_index* index, void* cuda_stream);
+
+typedef struct {
+  int64_t n;             /* series */
+  int32_t m;             /* length */
+  int32_t index_type;
+  int32_t n_leaves;
+  int32_t n_nodes;
+  int32_t wave;
+  int32_t n_filters;     /* 0 until filters are set */
+  int32_t filters_trained;
+  int32_t n_calib;       /* calibration queries behind the auto-tuners (0 = none) */
+  int32_t n_kclasses;
+  int32_t kclasses[LEAFI_MAX_KCLASSES];
+  int64_t device_bytes;  /* device memory held by the index */
+} leafi_index_info;
+
+leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info);
+
+/* Per-kernel device time, measured with CUDA events on the index's stream
+ * around each launch while profiling is on (off by default; switching it
+ * resets the totals).  Kinds: 0 leaf scan, 1 candidate merge, 2 bounds and
+ * routes, 3 (reserved), 4 filter forward, 5 wave select. */
+enum { LEAFI_KERNEL_KINDS = 6 };
+leafi_status leafi_set_profiling(leafi_index* index, int32_t on);
+leafi_status leafi_get_kernel_times(leafi_index* index, double* ms /* [6] */,
+                                    int64_t* launches /* [6] */);
+/* Series per leaf (host array of n_leaves). Leaves are numbered depth-first,
+ * left child first. */
+leafi_status leafi_leaf_sizes(const leafi_index* index, int64_t* sizes);
+/* Leaf of every series, by original id (host array of n). */
+leafi_status leafi_leaf_of(const leafi_index* index, int32_t* leaf_of);
+
+/* ------------------------------------------------------------------ */
+/* Lower bounds and routing (Sec. 3; Alg. 2 line 4)                    */
+/* ------------------------------------------------------------------ */
+
+/* Squared leaf lower bounds LB^2 (float64, nq x n_leaves, row-major):
+ * DSTree: max over the root-to-leaf path of sum_r l_r (gap(mu_q,r)^2 +
+ * gap(sigma_q,r)^2) against each node's mean / sigma ranges; iSAX: MINDIST^2
+ * of the leaf's word.  Segment statistics use float64 prefix sums. */
+leafi_status leafi_leaf_lower_bounds(leafi_index* index, const float* queries, int64_t nq,
+                                     double* lb2);
+/* Leaf that each query's own summary routes to (int32, nq). */
+leafi_status leafi_route(leafi_index* index, const float* queries, int64_t nq, int32_t* leaf);
+
+/* ------------------------------------------------------------------ */
+/* Learned filters (Sec. 4 intro; Sec. 5.1: MLP m -> h -> 1, ReLU)      */
+/* ------------------------------------------------------------------ */
+
+/* Filtered leaves = the n_filters largest leaves (ties: lower leaf id), the
+ * greedy selection of Alg. 3 with threshold th = 0 (out: int32 [n_filters]). */
+leafi_status leafi_select_leaves(const leafi_index* index, int32_t n_filters,
+                                 int32_t* filter_leaf);
+/* Install F filters on the given leaves with weights W1 [F][h][m], b1 [F][h],
+ * w2 [F][h], b2 [F] (float32; h = hidden width).  Clears the auto-tuners. */
+leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F,
+                               int32_t h, const float* W1, const float* b1, const float* w2,
+                               const float* b2);
+/* Copy the current filter weights out (same layouts as leafi_set_filters). */
+leafi_status leafi_get_filters(leafi_index* index, float* W1, float* b1, float* w2, float* b2);
+/* d^f(q, M_f) for every query and filter (float32, nq x F). */
+leafi_status leafi_filter_predict(leafi_index* index, const float* queries, int64_t nq,
+                                  float* out);
+
+/* ------------------------------------------------------------------ */
+/* Training data: node-wise nearest-neighbour distances (Sec. 3 d^L;    */
+/* Alg. 1 SearchGlobalQueries / SearchLocalQueries)                    */
+/* ------------------------------------------------------------------ */
+
+/* For every query i and every j < nl: the k best (d^2, id) inside leaf
+ * leaves[i*nl+j] (-1 = skip), written to d2/ids [nq][nl][k] (squared
+ * canonical distances, float32; ids int64; padding +inf / -1). */
+leafi_status leafi_leaf_knn(leafi_index* index, const float* queries, int64_t nq,
+                            const int32_t* leaves, int32_t nl, int32_t k, float* d2,
+                            int64_t* ids);
+/* Training targets d^L (Euclidean float32): Tg [ng][F] for global queries
+ * against every filtered leaf, Tl [F][nl] for the nl local queries of each
+ * filter (Ql [F][nl][m]) against its own leaf. */
+leafi_status leafi_train_targets(leafi_index* index, const float* Qg, int64_t ng,
+                                 const float* Ql, int64_t nl, float* Tg, float* Tl);
+
+typedef struct {
+  int32_t n_gtrain, n_gval; /* global queries: first n_gtrain train, next n_gval validate */
+  int32_t n_ltrain, n_lval; /* local queries per filter, same split */
+  int32_t batch;            /* SGD minibatch */
+  int32_t max_epochs;       /* <= 1000 in the paper */
+  int32_t patience;         /* epochs without a lower validation loss before lr /= 10 */
+  double lr0, lr_min;       /* 0.01 and 1e-5 in the paper */
+} leafi_train_params;
+
+/* Alg. 1 lines 3-9: computes the targets of Qg [n_gtrain+n_gval][m] and
+ * Ql [F][n_ltrain+n_lval][m] on the device, then trains every filter by SGD
+ * on the MSE loss from the currently installed weights, one shuffle
+ * perms [max_epochs][n_gtrain+n_ltrain] per epoch; keeps the weights of the
+ * lowest validation loss.  epochs_run / best_val (nullable, host, [F]). */
+leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p,
+                                 const float* Qg, const float* Ql, const int32_t* perms,
+                                 int32_t* epochs_run, double* best_val);
+
+/* ------------------------------------------------------------------ */
+/* Conformal auto-tuners (Sec. 4.4, Alg. 4)                            */
+/* ------------------------------------------------------------------ */
+
+/* Alg. 4 on calibration queries Qc [nc][m] for each k in kclasses (ascending,
+ * <= LEAFI_MAX_KCLASSES): alpha = |d^L - d^f| sorted descending per filter;
+ * at each sorted position j all filters take their j-th alpha, the search
+ * (same wave schedule) is simulated for every calibration query, and
+ * qprime[c][j] = running minimum over j of the mean recall@k. */
+leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t nc,
+                                  const int32_t* kclasses, int32_t nk);
+/* Read (alpha_sorted [F][nc] float64, qprime [nk][nc] float64) back. */
+leafi_status leafi_get_autotuners(leafi_index* index, double* alpha_sorted, double* qprime);
+/* Install auto-tuner tables computed elsewhere (same layouts). */
+leafi_status leafi_set_autotuners(leafi_index* index, const double* alpha_sorted,
+                                  const double* qprime, int64_t nc, const int32_t* kclasses,
+                                  int32_t nk);
+
+/* ------------------------------------------------------------------ */
+/* Search (Alg. 2)                                                     */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t leaves_scanned;  /* (query, leaf) pairs searched */
+  int64_t series_scanned;  /* (query, series) distances computed */
+  int64_t filter_evals;    /* (query, filter) predictions */
+  int64_t waves;           /* scan rounds, summed over batches */
+  int64_t batches;         /* internal query batches (256 queries each) */
+  int64_t distinct_series; /* series of the distinct leaves each round read, summed */
+} leafi_search_stats;
+
+/* k-NN of nq queries (1 <= k <= LEAFI_MAX_K).  recall_target >= 1 runs the
+ * exact search (filters off); recall_target in (0, 1) uses the auto-tuned
+ * offsets: the query's k picks the smallest calibrated k-class >= k, the
+ * target picks the largest sorted position j whose calibrated quality meets
+ * it, and leaf f is pruned when d^f - alpha_f,(j) > best-so-far.  A query
+ * whose class or target has no calibrated position runs exactly.
+ * LEAFI_ENOTTRAINED if recall_target < 1 and no auto-tuners exist.
+ * ids [nq][k] int64, dists [nq][k] float32 Euclidean. stats nullable. */
+leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
+                          double recall_target, int64_t* ids, float* dists,
+                          leafi_search_stats* stats);
+/* Exact k-NN with summarisation-bound pruning only (the plain index). */
+leafi_status leafi_exact_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
+                                int64_t* ids, float* dists, leafi_search_stats* stats);
+/* Per-query k [nq] and recall target [nq] (host or device); outputs are
+ * [nq][kmax] with entries past a query's own k set to -1 / +inf. */
+leafi_status leafi_search_mixed(leafi_index* index, const float* queries, int64_t nq,
+                                const int32_t* k, const double* recall_target, int32_t kmax,
+                                int64_t* ids, float* dists, leafi_search_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEAFI_H */

@@ -1,0 +1,328 @@
+"""B300-native LeaFi search path (learned filters for tree-based series indexes).
+
+A thin ctypes binding of the C ABI in include/leafi.h.  Every function here
+only marshals arguments: all computation happens in libleafi.so (CUDA kernels
+for sm_103a plus the host-side tree builder).  Arrays may be numpy arrays
+(host) or torch tensors (host or CUDA); results are written into caller-owned
+arrays of the same kind.  If the shared library is missing the import fails
+loudly: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = [
+    "LeafiError", "BuildParams", "TrainParams", "SearchStats", "IndexInfo", "lib",
+    "leafi_build", "leafi_free", "leafi_set_stream", "leafi_get_info", "leafi_leaf_sizes",
+    "leafi_leaf_of", "leafi_leaf_lower_bounds", "leafi_route", "leafi_select_leaves",
+    "leafi_set_filters", "leafi_get_filters", "leafi_filter_predict", "leafi_leaf_knn",
+    "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
+    "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
+    "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
+    "KERNEL_KINDS", "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libleafi.so")
+
+DSTREE, ISAX = 0, 1
+MAX_K = 128
+_STATUS = {0: "LEAFI_OK", 1: "LEAFI_EINVAL", 2: "LEAFI_ENOMEM", 3: "LEAFI_ECUDA",
+           4: "LEAFI_ETIMEOUT", 5: "LEAFI_ENOTTRAINED", 6: "LEAFI_EINTERNAL"}
+
+EXPORTED_SYMBOLS = [
+    "leafi_build", "leafi_free", "leafi_last_error", "leafi_set_stream", "leafi_get_info",
+    "leafi_leaf_sizes", "leafi_leaf_of", "leafi_leaf_lower_bounds", "leafi_route",
+    "leafi_select_leaves", "leafi_set_filters", "leafi_get_filters", "leafi_filter_predict",
+    "leafi_leaf_knn", "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
+    "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
+    "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
+]
+
+KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
+
+
+class LeafiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("index_type", C.c_int32), ("leaf_capacity", C.c_int32),
+                ("dstree_init_segments", C.c_int32), ("isax_segments", C.c_int32),
+                ("isax_card_bits", C.c_int32), ("wave", C.c_int32), ("device", C.c_int32)]
+
+    def __init__(self, index_type=DSTREE, leaf_capacity=10000, dstree_init_segments=4,
+                 isax_segments=16, isax_card_bits=8, wave=8, device=0):
+        super().__init__(index_type, leaf_capacity, dstree_init_segments, isax_segments,
+                         isax_card_bits, wave, device)
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("index_type", C.c_int32),
+                ("n_leaves", C.c_int32), ("n_nodes", C.c_int32), ("wave", C.c_int32),
+                ("n_filters", C.c_int32), ("filters_trained", C.c_int32),
+                ("n_calib", C.c_int32), ("n_kclasses", C.c_int32),
+                ("kclasses", C.c_int32 * 4), ("device_bytes", C.c_int64)]
+
+
+class TrainParams(C.Structure):
+    _fields_ = [("n_gtrain", C.c_int32), ("n_gval", C.c_int32), ("n_ltrain", C.c_int32),
+                ("n_lval", C.c_int32), ("batch", C.c_int32), ("max_epochs", C.c_int32),
+                ("patience", C.c_int32), ("lr0", C.c_double), ("lr_min", C.c_double)]
+
+    def __init__(self, n_gtrain=1200, n_gval=300, n_ltrain=400, n_lval=100, batch=64,
+                 max_epochs=1000, patience=10, lr0=0.01, lr_min=1e-5):
+        super().__init__(n_gtrain, n_gval, n_ltrain, n_lval, batch, max_epochs, patience,
+                         lr0, lr_min)
+
+
+class SearchStats(C.Structure):
+    _fields_ = [("leaves_scanned", C.c_int64), ("series_scanned", C.c_int64),
+                ("filter_evals", C.c_int64), ("waves", C.c_int64), ("batches", C.c_int64),
+                ("distinct_series", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libleafi.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libleafi.so is missing: run `python paper_2502_01836_b300/build.py`"
+                              " (or __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "leafi_build": [vp, i64, i32, C.POINTER(BuildParams), C.POINTER(vp)],
+            "leafi_set_stream": [vp, vp],
+            "leafi_get_info": [vp, C.POINTER(IndexInfo)],
+            "leafi_leaf_sizes": [vp, vp],
+            "leafi_leaf_of": [vp, vp],
+            "leafi_leaf_lower_bounds": [vp, vp, i64, vp],
+            "leafi_route": [vp, vp, i64, vp],
+            "leafi_select_leaves": [vp, i32, vp],
+            "leafi_set_filters": [vp, vp, i32, i32, vp, vp, vp, vp],
+            "leafi_get_filters": [vp, vp, vp, vp, vp],
+            "leafi_filter_predict": [vp, vp, i64, vp],
+            "leafi_leaf_knn": [vp, vp, i64, vp, i32, i32, vp, vp],
+            "leafi_train_targets": [vp, vp, i64, vp, i64, vp, vp],
+            "leafi_train_filters": [vp, C.POINTER(TrainParams), vp, vp, vp, vp, vp],
+            "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
+            "leafi_get_autotuners": [vp, vp, vp],
+            "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
+            "leafi_search": [vp, vp, i64, i32, f64, vp, vp, C.POINTER(SearchStats)],
+            "leafi_exact_search": [vp, vp, i64, i32, vp, vp, C.POINTER(SearchStats)],
+            "leafi_search_mixed": [vp, vp, i64, vp, vp, i32, vp, vp, C.POINTER(SearchStats)],
+            "leafi_set_profiling": [vp, i32],
+            "leafi_get_kernel_times": [vp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.leafi_free.argtypes = [vp]
+        L.leafi_free.restype = None
+        L.leafi_launch_count.argtypes = []
+        L.leafi_launch_count.restype = C.c_int64
+        L.leafi_last_error.argtypes = []
+        L.leafi_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise LeafiError(st, lib().leafi_last_error().decode())
+
+
+_NP = {np.float32: "float32", np.float64: "float64", np.int32: "int32", np.int64: "int64"}
+
+
+def _ptr(a, dtype, name="array", writable=False):
+    """Data pointer of a C-contiguous numpy array or torch tensor of `dtype`."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
+            raise TypeError("%s must be a C-contiguous %s numpy array" % (name, np.dtype(dtype)))
+        if writable and not a.flags.writeable:
+            raise TypeError("%s must be writable" % name)
+        return a.ctypes.data
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        import torch
+        tmap = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                np.int64: torch.int64}
+        if a.dtype != tmap[dtype] or not a.is_contiguous():
+            raise TypeError("%s must be a contiguous torch.%s tensor" % (name, _NP[dtype]))
+        return a.data_ptr()
+    raise TypeError("%s must be a numpy array or a torch tensor" % name)
+
+
+def leafi_launch_count() -> int:
+    return int(lib().leafi_launch_count())
+
+
+def leafi_set_profiling(index, on: bool):
+    _check(lib().leafi_set_profiling(index, 1 if on else 0))
+
+
+def leafi_get_kernel_times(index):
+    """{kind: (total ms, launches)} for the kernels timed since profiling was switched on."""
+    ms = np.zeros(6, np.float64)
+    n = np.zeros(6, np.int64)
+    _check(lib().leafi_get_kernel_times(index, ms.ctypes.data, n.ctypes.data))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def leafi_build(series, params: BuildParams | None = None):
+    """Build an index over `series` [n, m] float32; returns an opaque handle."""
+    params = params or BuildParams()
+    n, m = series.shape
+    h = C.c_void_p()
+    _check(lib().leafi_build(_ptr(series, np.float32, "series"), n, m, C.byref(params),
+                             C.byref(h)))
+    return h
+
+
+def leafi_free(index):
+    lib().leafi_free(index)
+
+
+def leafi_set_stream(index, stream_handle: int):
+    _check(lib().leafi_set_stream(index, C.c_void_p(stream_handle)))
+
+
+def leafi_get_info(index) -> IndexInfo:
+    info = IndexInfo()
+    _check(lib().leafi_get_info(index, C.byref(info)))
+    return info
+
+
+def leafi_leaf_sizes(index):
+    out = np.empty(leafi_get_info(index).n_leaves, np.int64)
+    _check(lib().leafi_leaf_sizes(index, out.ctypes.data))
+    return out
+
+
+def leafi_leaf_of(index):
+    out = np.empty(leafi_get_info(index).n, np.int32)
+    _check(lib().leafi_leaf_of(index, out.ctypes.data))
+    return out
+
+
+def leafi_leaf_lower_bounds(index, queries, out):
+    _check(lib().leafi_leaf_lower_bounds(index, _ptr(queries, np.float32, "queries"),
+                                         queries.shape[0], _ptr(out, np.float64, "out", True)))
+    return out
+
+
+def leafi_route(index, queries, out):
+    _check(lib().leafi_route(index, _ptr(queries, np.float32, "queries"), queries.shape[0],
+                             _ptr(out, np.int32, "out", True)))
+    return out
+
+
+def leafi_select_leaves(index, n_filters):
+    out = np.empty(n_filters, np.int32)
+    _check(lib().leafi_select_leaves(index, n_filters, out.ctypes.data))
+    return out
+
+
+def leafi_set_filters(index, filter_leaf, W1, b1, w2, b2):
+    F, h, _ = W1.shape
+    _check(lib().leafi_set_filters(index, _ptr(filter_leaf, np.int32, "filter_leaf"), F, h,
+                                   _ptr(W1, np.float32, "W1"), _ptr(b1, np.float32, "b1"),
+                                   _ptr(w2, np.float32, "w2"), _ptr(b2, np.float32, "b2")))
+
+
+def leafi_get_filters(index, W1, b1, w2, b2):
+    _check(lib().leafi_get_filters(index, _ptr(W1, np.float32, "W1", True),
+                                   _ptr(b1, np.float32, "b1", True),
+                                   _ptr(w2, np.float32, "w2", True),
+                                   _ptr(b2, np.float32, "b2", True)))
+    return W1, b1, w2, b2
+
+
+def leafi_filter_predict(index, queries, out):
+    _check(lib().leafi_filter_predict(index, _ptr(queries, np.float32, "queries"),
+                                      queries.shape[0], _ptr(out, np.float32, "out", True)))
+    return out
+
+
+def leafi_leaf_knn(index, queries, leaves, k, d2, ids):
+    _check(lib().leafi_leaf_knn(index, _ptr(queries, np.float32, "queries"), queries.shape[0],
+                                _ptr(leaves, np.int32, "leaves"), leaves.shape[1], k,
+                                _ptr(d2, np.float32, "d2", True), _ptr(ids, np.int64, "ids", True)))
+    return d2, ids
+
+
+def leafi_train_targets(index, Qg, Ql, Tg, Tl):
+    """Qg [ng, m]; Ql [F, nl, m] -> Tg [ng, F], Tl [F, nl]."""
+    nl = Ql.shape[1] if Ql is not None and Ql.ndim == 3 else 0
+    _check(lib().leafi_train_targets(index, _ptr(Qg, np.float32, "Qg"), Qg.shape[0],
+                                     _ptr(Ql, np.float32, "Ql"), nl,
+                                     _ptr(Tg, np.float32, "Tg", True),
+                                     _ptr(Tl, np.float32, "Tl", True)))
+    return Tg, Tl
+
+
+def leafi_train_filters(index, params: TrainParams, Qg, Ql, perms, epochs_run=None,
+                        best_val=None):
+    _check(lib().leafi_train_filters(index, C.byref(params), _ptr(Qg, np.float32, "Qg"),
+                                     _ptr(Ql, np.float32, "Ql"), _ptr(perms, np.int32, "perms"),
+                                     _ptr(epochs_run, np.int32, "epochs_run", True),
+                                     _ptr(best_val, np.float64, "best_val", True)))
+    return epochs_run, best_val
+
+
+def leafi_fit_autotuners(index, Qc, kclasses):
+    kc = np.ascontiguousarray(kclasses, np.int32)
+    _check(lib().leafi_fit_autotuners(index, _ptr(Qc, np.float32, "Qc"), Qc.shape[0],
+                                      kc.ctypes.data, kc.shape[0]))
+
+
+def leafi_get_autotuners(index, alpha_sorted, qprime):
+    _check(lib().leafi_get_autotuners(index, _ptr(alpha_sorted, np.float64, "alpha", True),
+                                      _ptr(qprime, np.float64, "qprime", True)))
+    return alpha_sorted, qprime
+
+
+def leafi_set_autotuners(index, alpha_sorted, qprime, kclasses):
+    kc = np.ascontiguousarray(kclasses, np.int32)
+    _check(lib().leafi_set_autotuners(index, _ptr(alpha_sorted, np.float64, "alpha"),
+                                      _ptr(qprime, np.float64, "qprime"), alpha_sorted.shape[1],
+                                      kc.ctypes.data, kc.shape[0]))
+
+
+def leafi_search(index, queries, k, recall_target, ids, dists, stats: SearchStats | None = None):
+    _check(lib().leafi_search(index, _ptr(queries, np.float32, "queries"), queries.shape[0], k,
+                              float(recall_target), _ptr(ids, np.int64, "ids", True),
+                              _ptr(dists, np.float32, "dists", True),
+                              C.byref(stats) if stats is not None else None))
+    return ids, dists
+
+
+def leafi_exact_search(index, queries, k, ids, dists, stats: SearchStats | None = None):
+    _check(lib().leafi_exact_search(index, _ptr(queries, np.float32, "queries"), queries.shape[0],
+                                    k, _ptr(ids, np.int64, "ids", True),
+                                    _ptr(dists, np.float32, "dists", True),
+                                    C.byref(stats) if stats is not None else None))
+    return ids, dists
+
+
+def leafi_search_mixed(index, queries, k, recall_target, kmax, ids, dists,
+                       stats: SearchStats | None = None):
+    _check(lib().leafi_search_mixed(index, _ptr(queries, np.float32, "queries"), queries.shape[0],
+                                    _ptr(k, np.int32, "k"), _ptr(recall_target, np.float64, "target"),
+                                    kmax, _ptr(ids, np.int64, "ids", True),
+                                    _ptr(dists, np.float32, "dists", True),
+                                    C.byref(stats) if stats is not None else None))
+    return ids, dists

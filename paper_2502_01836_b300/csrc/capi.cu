@@ -1,0 +1,1177 @@
+// C ABI (include/leafi.h): argument checks, host/device staging, and the
+// search driver that runs the LeaFi path (Alg. 2) on the GPU in waves.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <stdexcept>
+
+#include "internal.h"
+
+namespace leafi {
+
+namespace {
+thread_local std::string g_last_error;
+constexpr int kPart = 2048;       // series per scan work item
+constexpr int kBatch = 256;       // queries per search batch
+constexpr size_t kKnnBudget = 256ull << 20;  // bytes of candidate buffer per leaf-knn batch
+}  // namespace
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void fail(leafi_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  throw Failure{st, buf};
+}
+
+namespace {
+
+template <class Fn>
+leafi_status guarded(Fn&& fn) {
+  try {
+    fn();
+    return LEAFI_OK;
+  } catch (const Failure& e) {
+    set_last_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return LEAFI_ENOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return LEAFI_EINTERNAL;
+  }
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) LF_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// copy `count` elements from a host or device array into a device buffer
+template <class T>
+const T* to_device(const T* user, size_t count, DBuf<T>& tmp, cudaStream_t s) {
+  if (on_device(user)) return user;
+  tmp.upload(user, count, s);
+  return tmp.p;
+}
+
+template <class T>
+void to_host(std::vector<T>& out, const T* user, size_t count, cudaStream_t s) {
+  out.resize(count);
+  if (!count) return;
+  if (on_device(user)) {
+    LF_CUDA(cudaMemcpyAsync(out.data(), user, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    LF_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(out.data(), user, count * sizeof(T));
+  }
+}
+
+// write device results to a user array that may be host or device
+template <class T>
+void deliver(T* user, const T* dev, size_t count, cudaStream_t s) {
+  if (!count) return;
+  LF_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T),
+                          on_device(user) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+// queries [nq][m] (host or device) -> padded device rows [nq][mp] in `buf`
+const float* stage_queries(leafi_index* ix, const float* q, int64_t nq, DBuf<float>& buf) {
+  cudaStream_t s = ix->stream;
+  const bool dev = on_device(q);
+  if (dev && ix->m == ix->mp && (reinterpret_cast<uintptr_t>(q) % 16) == 0) return q;
+  float* d = buf.need((size_t)nq * ix->mp);
+  if (ix->mp != ix->m) LF_CUDA(cudaMemsetAsync(d, 0, sizeof(float) * nq * ix->mp, s));
+  LF_CUDA(cudaMemcpy2DAsync(d, sizeof(float) * ix->mp, q, sizeof(float) * ix->m,
+                            sizeof(float) * ix->m, (size_t)nq,
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+int sm_count(int dev) {
+  int v = 0;
+  LF_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+  return v;
+}
+
+int64_t max_leaf_size(const HostTree& t) {
+  int64_t mx = 0;
+  for (int l = 0; l < t.n_leaves; ++l) mx = std::max(mx, t.leaf_off[l + 1] - t.leaf_off[l]);
+  return mx;
+}
+
+int max_parts(const HostTree& t) { return (int)((max_leaf_size(t) + kPart - 1) / kPart); }
+
+__global__ void sqrt_kernel(const float* __restrict__ in, float* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __fsqrt_rn(in[i]);
+}
+
+__global__ void search_init_kernel(int nq, int kstride, int32_t* topk_cnt,
+                                   unsigned long long* thr, int32_t* cand_cnt, double* cur_lb,
+                                   int32_t* cur_leaf, int32_t* done) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  topk_cnt[q] = 0;
+  thr[q] = kNoKey;
+  cand_cnt[q] = 0;
+  cur_lb[q] = -__longlong_as_double(0x7ff0000000000000ll);
+  cur_leaf[q] = -1;
+  done[q] = 0;
+  (void)kstride;
+}
+
+__global__ void slots_init_kernel(int nslots, int32_t* topk_cnt, unsigned long long* thr,
+                                  int32_t* cand_cnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nslots) return;
+  topk_cnt[t] = 0;
+  thr[t] = kNoKey;
+  cand_cnt[t] = 0;
+}
+
+__global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int F,
+                                 int rows, int cols) {
+  // in [F][rows][cols] -> out [F][cols][rows]
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per = (size_t)rows * cols;
+  if (t >= per * F) return;
+  const size_t f = t / per, r = (t % per) / cols, c = t % cols;
+  out[f * per + c * rows + r] = in[t];
+}
+
+// One scan round: group pairs by leaf, scan, merge candidates into slots.
+void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_t* dNpairs,
+               int npairs_max, int nslots, int kstride, const int32_t* slot_k,
+               unsigned long long* topk, int32_t* topk_cnt, unsigned long long* thr,
+               unsigned long long* cand, int32_t* cand_cnt, int cap,
+               unsigned long long* distinct_stat = nullptr) {
+  cudaStream_t s = ix->stream;
+  const int L = ix->tree.n_leaves;
+  int32_t* cnt = ix->sCnt.need(L);
+  int32_t* goff = ix->sGrpOff.need(L + 1);
+  int32_t* ioff = ix->sItemOff.need(L + 1);
+  Pair* grouped = ix->sGrouped.need(std::max(npairs_max, 1));
+  int32_t* nitems = ix->sNItems.need(1);
+  launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart, cnt, goff, ioff, grouped,
+               nitems, distinct_stat, s);
+  ScanArgs a;
+  a.X = ix->X.p;
+  a.ids = ix->ids.p;
+  a.leaf_off = ix->leaf_off.p;
+  a.L = L;
+  a.mp = ix->mp;
+  a.k = kstride;
+  a.part = kPart;
+  a.Q = dQ;
+  a.pairs = grouped;
+  a.grp_off = goff;
+  a.item_off = ioff;
+  a.thr = thr;
+  a.cand = cand;
+  a.cand_cnt = cand_cnt;
+  a.cand_cap = cap;
+  a.err = ix->sErr.p;
+  const int grid = sm_count(ix->device) * 2;
+  ix->tick(0);
+  launch_scan(a, nitems, slot_k, grid, s);
+  ix->tock();
+  ix->tick(1);
+  launch_merge(nslots, kstride, slot_k, topk, topk_cnt, thr, cand, cand_cnt, cap, s);
+  ix->tock();
+}
+
+void check_err_word(leafi_index* ix) {
+  int32_t err = 0;
+  LF_CUDA(cudaMemcpyAsync(&err, ix->sErr.p, sizeof(err), cudaMemcpyDeviceToHost, ix->stream));
+  LF_CUDA(cudaStreamSynchronize(ix->stream));
+  if (err) {
+    LF_CUDA(cudaMemsetAsync(ix->sErr.p, 0, sizeof(int32_t), ix->stream));
+    fail(LEAFI_EINTERNAL, "candidate buffer overflow (error word %d)", err);
+  }
+}
+
+// bounds and routes for nq padded device queries
+void compute_bounds(leafi_index* ix, const float* dQ, int nq, double* lb2, int32_t* route) {
+  cudaStream_t s = ix->stream;
+  const HostTree& t = ix->tree;
+  double* P = ix->sP.need((size_t)nq * 2 * (ix->m + 1));
+  launch_prefix(dQ, nq, ix->mp, ix->m, P, s);
+  if (t.type == LEAFI_DSTREE) {
+    double* iv = ix->sIv.need((size_t)nq * t.iv_s.size() * 2);
+    double* nodes = ix->sNode.need((size_t)nq * t.n_nodes);
+    launch_ds_bounds(ix->ds(), P, nq, ix->m, iv, nodes, lb2, route, s);
+  } else {
+    double* paa = ix->sPaa.need((size_t)nq * t.w);
+    launch_isax_bounds(ix->isax(), P, nq, ix->m, paa, lb2, route, s);
+  }
+}
+
+// per-(query, leaf) top-k inside leaves: slots [nq][nl], keys stride k
+void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dLeaves, int nl,
+                     int k, DBuf<unsigned long long>& topk, DBuf<int32_t>& topk_cnt) {
+  cudaStream_t s = ix->stream;
+  const int L = ix->tree.n_leaves;
+  const int nslots = nq * nl;
+  const int cap = max_parts(ix->tree) * k;
+  topk.need((size_t)nslots * k);
+  topk_cnt.need(nslots);
+  unsigned long long* thr = ix->sThr.need(nslots);
+  int32_t* cand_cnt = ix->sCandCnt.need(nslots);
+  if (nslots == 0) return;
+  slots_init_kernel<<<(nslots + 255) / 256, 256, 0, s>>>(nslots, topk_cnt.p, thr, cand_cnt);
+  LF_CHECK_LAUNCH();
+  // batches of queries keep the candidate buffer bounded
+  const size_t per_query = (size_t)nl * cap * sizeof(unsigned long long);
+  int qb = (int)std::max<size_t>(1, kKnnBudget / std::max<size_t>(per_query, 1));
+  qb = std::min(qb, nq);
+  unsigned long long* cand = ix->sCand.need((size_t)qb * nl * cap);
+  Pair* pairs = ix->sPairs.need((size_t)qb * nl);
+  int32_t* np = ix->sNpairs.need(1);
+  for (int q0 = 0; q0 < nq; q0 += qb) {
+    const int nb = std::min(qb, nq - q0);
+    const int ns = nb * nl;
+    launch_leafknn_pairs(nb, nl, dLeaves + (size_t)q0 * nl, L, pairs, np, s);
+    // slots of this batch are [q0*nl, q0*nl + ns): shift the bases
+    run_round(ix, dQ + (size_t)q0 * ix->mp, pairs, np, ns, ns, k, nullptr,
+              topk.p + (size_t)q0 * nl * k, topk_cnt.p + (size_t)q0 * nl, thr + (size_t)q0 * nl,
+              cand, cand_cnt + (size_t)q0 * nl, cap);
+  }
+  check_err_word(ix);
+}
+
+void require_index(const leafi_index* ix) {
+  if (!ix) fail(LEAFI_EINVAL, "index is NULL");
+}
+
+void require_device(const leafi_index* ix) {
+  require_index(ix);
+  if (ix->device < 0) fail(LEAFI_EINVAL, "index was built host-only (device -1)");
+}
+
+void check_queries(const leafi_index* ix, const float* q, int64_t nq) {
+  if (nq < 0 || nq > (int64_t)std::numeric_limits<int32_t>::max() / 4)
+    fail(LEAFI_EINVAL, "nq out of range");
+  if (nq > 0 && !q) fail(LEAFI_EINVAL, "queries is NULL");
+  (void)ix;
+}
+
+// the search driver shared by leafi_search / _exact / _mixed
+void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::vector<int32_t>& kq,
+                 const std::vector<double>& target, int kmax, int64_t* ids, float* dists,
+                 leafi_search_stats* stats) {
+  cudaStream_t s = ix->stream;
+  const HostTree& t = ix->tree;
+  const int L = t.n_leaves;
+  const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
+  if (any_filtered && (ix->nc == 0 || ix->F == 0))
+    fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
+  leafi_search_stats st{};
+  const int W = ix->wave;
+  const int cap = std::max(W, 1) * max_parts(t) * kmax;
+  const int qb = kBatch;
+  int32_t* dK = ix->sK.need(qb);
+  double* dT = ix->sTarget.need(qb);
+  int32_t* jpos = ix->sJpos.need(qb);
+  double* lb2 = ix->sLb.need((size_t)qb * L);
+  int32_t* route = ix->sRoute.need(qb);
+  float* P = ix->F ? ix->sPred.need((size_t)qb * ix->F) : nullptr;
+  unsigned char* scanned = ix->sScanned.need((size_t)qb * L);
+  unsigned long long* topk = ix->sTopk.need((size_t)qb * kmax);
+  int32_t* topk_cnt = ix->sTopkCnt.need(qb);
+  unsigned long long* thr = ix->sThr.need(qb);
+  unsigned long long* cand = ix->sCand.need((size_t)qb * cap);
+  int32_t* cand_cnt = ix->sCandCnt.need(qb);
+  double* cur_lb = ix->sCurLb.need(qb);
+  int32_t* cur_leaf = ix->sCurLeaf.need(qb);
+  int32_t* done = ix->sDone.need(qb);
+  Pair* pairs = ix->sPairs.need((size_t)qb * std::max(W, 1));
+  int32_t* np = ix->sNpairs.need(1);
+  unsigned long long* stat = ix->sStat.need(3);
+  int64_t* out_i = ix->sOutI.need((size_t)qb * kmax);
+  float* out_d = ix->sOutD.need((size_t)qb * kmax);
+  DBuf<float> qtmp;
+  LF_CUDA(cudaMemsetAsync(stat, 0, 3 * sizeof(unsigned long long), s));
+  for (int64_t b0 = 0; b0 < nq; b0 += qb) {
+    const int nb = (int)std::min<int64_t>(qb, nq - b0);
+    const float* dQ = stage_queries(ix, queries + (size_t)b0 * ix->m, nb, qtmp);
+    LF_CUDA(cudaMemcpyAsync(dK, kq.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(dT, target.data() + b0, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    ix->tick(2);
+    compute_bounds(ix, dQ, nb, lb2, route);
+    ix->tock();
+    const bool use_f = std::any_of(target.begin() + b0, target.begin() + b0 + nb,
+                                   [](double v) { return v < 1.0; });
+    if (use_f) {
+      ix->tick(4);
+      launch_filter_forward(dQ, nb, ix->mp, ix->m, ix->F, ix->h, ix->W1t.p, ix->b1.p, ix->w2.p,
+                            ix->b2.p, P, s);
+      ix->tock();
+      launch_jpos(nb, dK, dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, jpos, s);
+      st.filter_evals += (int64_t)nb * ix->F;
+    }
+    LF_CUDA(cudaMemsetAsync(scanned, 0, (size_t)nb * L, s));
+    search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, topk_cnt, thr, cand_cnt, cur_lb,
+                                                        cur_leaf, done);
+    LF_CHECK_LAUNCH();
+    // wave 0: every query searches its route leaf
+    launch_route_pairs(nb, route, L, scanned, ix->leaf_off.p, pairs, np, stat, s);
+    run_round(ix, dQ, pairs, np, nb, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+              stat + 2);
+    int waves = 1;
+    SelectArgs sa;
+    sa.nq = nb;
+    sa.L = L;
+    sa.W = W;
+    sa.lb2 = lb2;
+    sa.thr = thr;
+    sa.P = use_f ? P : nullptr;
+    sa.F = ix->F;
+    sa.leaf_filter = ix->d_leaf_filter.p;
+    sa.alpha = ix->alpha.p;
+    sa.nc = ix->nc;
+    sa.jpos = use_f ? jpos : nullptr;
+    sa.leaf_off = ix->leaf_off.p;
+    sa.scanned = scanned;
+    sa.cur_lb = cur_lb;
+    sa.cur_leaf = cur_leaf;
+    sa.done = done;
+    sa.pairs = pairs;
+    sa.npairs = np;
+    sa.stat = stat;
+    for (;;) {
+      LF_CUDA(cudaMemsetAsync(np, 0, sizeof(int32_t), s));
+      ix->tick(5);
+      launch_select(sa, s);
+      ix->tock();
+      int32_t h_np = 0;
+      LF_CUDA(cudaMemcpyAsync(&h_np, np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LF_CUDA(cudaStreamSynchronize(s));
+      if (h_np == 0) break;
+      if (++waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
+      run_round(ix, dQ, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+                stat + 2);
+    }
+    st.waves += waves;
+    st.batches += 1;
+    check_err_word(ix);
+    launch_write_results(nb, kmax, dK, topk, kmax, topk_cnt, out_i, out_d, s);
+    deliver(ids + (size_t)b0 * kmax, out_i, (size_t)nb * kmax, s);
+    deliver(dists + (size_t)b0 * kmax, out_d, (size_t)nb * kmax, s);
+  }
+  unsigned long long h_stat[3] = {0, 0, 0};
+  LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaStreamSynchronize(s));
+  st.leaves_scanned = (int64_t)h_stat[0];
+  st.series_scanned = (int64_t)h_stat[1];
+  st.distinct_series = (int64_t)h_stat[2];
+  ix->settle();
+  if (stats) *stats = st;
+}
+
+}  // namespace
+}  // namespace leafi
+
+using namespace leafi;
+
+leafi::DsTables leafi_index::ds() const {
+  DsTables T;
+  T.n_nodes = tree.n_nodes;
+  T.n_leaves = tree.n_leaves;
+  T.n_iv = (int)tree.iv_s.size();
+  T.root = tree.root;
+  T.iv_s = iv_s.p;
+  T.iv_e = iv_e.p;
+  T.seg_off = seg_off.p;
+  T.seg_iv = seg_iv.p;
+  T.mlo = mlo.p;
+  T.mhi = mhi.p;
+  T.slo = slo.p;
+  T.shi = shi.p;
+  T.left = left.p;
+  T.right = right.p;
+  T.node_leaf = node_leaf.p;
+  T.split_iv = split_iv.p;
+  T.split_sd = split_sd.p;
+  T.thresh = thresh.p;
+  T.path_off = path_off.p;
+  T.path = path.p;
+  return T;
+}
+
+void leafi_index::tick(int kind) {
+  if (!profiling) return;
+  cudaEvent_t a, b;
+  LF_CUDA(cudaEventCreate(&a));
+  LF_CUDA(cudaEventCreate(&b));
+  LF_CUDA(cudaEventRecord(a, stream));
+  clock.ev.push_back(a);
+  clock.ev.push_back(b);
+  clock.kind.push_back(kind);
+}
+
+void leafi_index::tock() {
+  if (!profiling) return;
+  LF_CUDA(cudaEventRecord(clock.ev.back(), stream));
+}
+
+void leafi_index::settle() {
+  if (clock.ev.empty()) return;
+  LF_CUDA(cudaStreamSynchronize(stream));
+  for (size_t i = 0; i < clock.kind.size(); ++i) {
+    float ms = 0.0f;
+    LF_CUDA(cudaEventElapsedTime(&ms, clock.ev[2 * i], clock.ev[2 * i + 1]));
+    clock.ms[clock.kind[i]] += ms;
+    clock.n[clock.kind[i]] += 1;
+  }
+  for (cudaEvent_t e : clock.ev) cudaEventDestroy(e);
+  clock.ev.clear();
+  clock.kind.clear();
+}
+
+leafi::IsaxTables leafi_index::isax() const {
+  IsaxTables T;
+  T.n_nodes = tree.n_nodes;
+  T.n_leaves = tree.n_leaves;
+  T.w = tree.w;
+  T.bits = tree.bits;
+  T.beta = beta.p;
+  T.root_child = root_child.p;
+  T.left = left.p;
+  T.right = right.p;
+  T.node_leaf = node_leaf.p;
+  T.isplit = isplit.p;
+  T.node_bits = node_bits.p;
+  T.lo_sym = lo_sym.p;
+  T.hi_sym = hi_sym.p;
+  return T;
+}
+
+extern "C" {
+
+const char* leafi_last_error(void) { return g_last_error.c_str(); }
+
+int64_t leafi_launch_count(void) { return (int64_t)g_launches.load(); }
+
+leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_build_params* p,
+                         leafi_index** out) {
+  return guarded([&] {
+    if (!out) fail(LEAFI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!series || !p) fail(LEAFI_EINVAL, "series / params is NULL");
+    if (n < 1 || n > std::numeric_limits<int32_t>::max()) fail(LEAFI_EINVAL, "n out of range");
+    if (m < 1 || m > 512) fail(LEAFI_EINVAL, "m must be in [1, 512]");
+    if (p->leaf_capacity < 1) fail(LEAFI_EINVAL, "leaf_capacity < 1");
+    if (p->wave < 1 || p->wave > calib_max_wave()) fail(LEAFI_EINVAL, "wave must be in [1, %d]", calib_max_wave());
+    if (p->index_type == LEAFI_DSTREE) {
+      if (p->dstree_init_segments < 1 || p->dstree_init_segments > m)
+        fail(LEAFI_EINVAL, "dstree_init_segments must be in [1, m]");
+    } else if (p->index_type == LEAFI_ISAX) {
+      if (p->isax_segments < 1 || p->isax_segments > 20 || m % p->isax_segments)
+        fail(LEAFI_EINVAL, "isax_segments must divide m and be <= 20");
+      if (p->isax_card_bits < 1 || p->isax_card_bits > 16) fail(LEAFI_EINVAL, "isax_card_bits in [1, 16]");
+    } else {
+      fail(LEAFI_EINVAL, "unknown index_type %d", p->index_type);
+    }
+    if (p->device == -1) {
+      // host-only: the tree alone, for inspection (series must be host memory)
+      std::unique_ptr<leafi_index> ix(new leafi_index);
+      ix->device = -1;
+      ix->m = m;
+      ix->mp = (m + 3) / 4 * 4;
+      ix->n = n;
+      ix->wave = p->wave;
+      if (p->index_type == LEAFI_DSTREE)
+        ix->tree = build_dstree(series, n, m, p->leaf_capacity, p->dstree_init_segments);
+      else
+        ix->tree = build_isax(series, n, m, p->leaf_capacity, p->isax_segments, p->isax_card_bits);
+      *out = ix.release();
+      return;
+    }
+    int ndev = 0;
+    LF_CUDA(cudaGetDeviceCount(&ndev));
+    if (p->device < 0 || p->device >= ndev) fail(LEAFI_EINVAL, "device %d not present", p->device);
+    DeviceGuard dg(p->device);
+    std::unique_ptr<leafi_index> ix(new leafi_index);
+    ix->device = p->device;
+    ix->m = m;
+    ix->mp = (m + 3) / 4 * 4;
+    ix->n = n;
+    ix->wave = p->wave;
+    cudaStream_t s = ix->stream;
+    // the tree is built on the host from a host copy of the series
+    std::vector<float> hostX;
+    const float* hx = series;
+    if (on_device(series)) {
+      to_host(hostX, series, (size_t)n * m, s);
+      hx = hostX.data();
+    }
+    if (p->index_type == LEAFI_DSTREE)
+      ix->tree = build_dstree(hx, n, m, p->leaf_capacity, p->dstree_init_segments);
+    else
+      ix->tree = build_isax(hx, n, m, p->leaf_capacity, p->isax_segments, p->isax_card_bits);
+    HostTree& t = ix->tree;
+    // leaf-major, 16-byte aligned rows of mp floats, uploaded in chunks
+    float* X = ix->X.need((size_t)n * ix->mp);
+    {
+      const int64_t chunk = 1 << 16;
+      std::vector<float> stage((size_t)std::min<int64_t>(chunk, n) * ix->mp, 0.0f);
+      for (int64_t p0 = 0; p0 < n; p0 += chunk) {
+        const int64_t cnt = std::min(chunk, n - p0);
+        for (int64_t r = 0; r < cnt; ++r)
+          std::memcpy(&stage[(size_t)r * ix->mp], hx + (size_t)t.order[p0 + r] * m, sizeof(float) * m);
+        LF_CUDA(cudaMemcpy(X + (size_t)p0 * ix->mp, stage.data(), sizeof(float) * cnt * ix->mp,
+                           cudaMemcpyHostToDevice));
+      }
+    }
+    ix->ids.upload(t.order, s);
+    ix->leaf_off.upload(t.leaf_off, s);
+    ix->left.upload(t.node_left, s);
+    ix->right.upload(t.node_right, s);
+    ix->node_leaf.upload(t.node_leaf, s);
+    ix->path_off.upload(t.path_off, s);
+    ix->path.upload(t.path, s);
+    if (t.type == LEAFI_DSTREE) {
+      ix->iv_s.upload(t.iv_s, s);
+      ix->iv_e.upload(t.iv_e, s);
+      ix->seg_off.upload(t.node_seg_off, s);
+      ix->seg_iv.upload(t.seg_iv, s);
+      ix->mlo.upload(t.seg_mlo, s);
+      ix->mhi.upload(t.seg_mhi, s);
+      ix->slo.upload(t.seg_slo, s);
+      ix->shi.upload(t.seg_shi, s);
+      ix->split_iv.upload(t.split_iv, s);
+      ix->split_sd.upload(t.split_sd, s);
+      ix->thresh.upload(t.split_thresh, s);
+    } else {
+      ix->beta.upload(t.beta, s);
+      ix->root_child.upload(t.root_child, s);
+      ix->isplit.upload(t.isax_split, s);
+      ix->node_bits.upload(t.node_bits, s);
+      ix->lo_sym.upload(t.leaf_lo_sym, s);
+      ix->hi_sym.upload(t.leaf_hi_sym, s);
+    }
+    std::vector<int32_t> lf(t.n_leaves, -1);
+    ix->d_leaf_filter.upload(lf, s);
+    int32_t zero = 0;
+    ix->sErr.upload(&zero, 1, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+    *out = ix.release();
+  });
+}
+
+void leafi_free(leafi_index* index) {
+  if (!index) return;
+  if (index->device < 0) {
+    delete index;
+    return;
+  }
+  {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(index->device);
+    if (index->stream) cudaStreamSynchronize(index->stream);
+    delete index;
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+}
+
+leafi_status leafi_set_stream(leafi_index* index, void* cuda_stream) {
+  return guarded([&] {
+    require_device(index);
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->stream = static_cast<cudaStream_t>(cuda_stream);
+  });
+}
+
+leafi_status leafi_set_profiling(leafi_index* index, int32_t on) {
+  return guarded([&] {
+    require_device(index);
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    index->settle();
+    index->profiling = on != 0;
+    for (int i = 0; i < 8; ++i) {
+      index->clock.ms[i] = 0.0;
+      index->clock.n[i] = 0;
+    }
+  });
+}
+
+leafi_status leafi_get_kernel_times(leafi_index* index, double* ms, int64_t* launches) {
+  return guarded([&] {
+    require_device(index);
+    if (!ms || !launches) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    index->settle();
+    for (int i = 0; i < LEAFI_KERNEL_KINDS; ++i) {
+      ms[i] = index->clock.ms[i];
+      launches[i] = index->clock.n[i];
+    }
+  });
+}
+
+leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info) {
+  return guarded([&] {
+    require_index(index);
+    if (!info) fail(LEAFI_EINVAL, "info is NULL");
+    leafi_index_info r{};
+    r.n = index->n;
+    r.m = index->m;
+    r.index_type = index->tree.type;
+    r.n_leaves = index->tree.n_leaves;
+    r.n_nodes = index->tree.n_nodes;
+    r.wave = index->wave;
+    r.n_filters = index->F;
+    r.filters_trained = index->trained ? 1 : 0;
+    r.n_calib = index->nc;
+    r.n_kclasses = index->nk;
+    for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) r.kclasses[i] = index->kclasses[i];
+    r.device_bytes = (int64_t)(index->X.bytes() + index->ids.bytes() + index->W1t.bytes());
+    *info = r;
+  });
+}
+
+leafi_status leafi_leaf_sizes(const leafi_index* index, int64_t* sizes) {
+  return guarded([&] {
+    require_index(index);
+    if (!sizes) fail(LEAFI_EINVAL, "sizes is NULL");
+    const HostTree& t = index->tree;
+    for (int l = 0; l < t.n_leaves; ++l) sizes[l] = t.leaf_off[l + 1] - t.leaf_off[l];
+  });
+}
+
+leafi_status leafi_leaf_of(const leafi_index* index, int32_t* leaf_of) {
+  return guarded([&] {
+    require_index(index);
+    if (!leaf_of) fail(LEAFI_EINVAL, "leaf_of is NULL");
+    const HostTree& t = index->tree;
+    for (int l = 0; l < t.n_leaves; ++l)
+      for (int64_t p = t.leaf_off[l]; p < t.leaf_off[l + 1]; ++p) leaf_of[t.order[p]] = l;
+  });
+}
+
+leafi_status leafi_leaf_lower_bounds(leafi_index* index, const float* queries, int64_t nq,
+                                     double* lb2) {
+  return guarded([&] {
+    require_device(index);
+    check_queries(index, queries, nq);
+    if (nq > 0 && !lb2) fail(LEAFI_EINVAL, "lb2 is NULL");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    DBuf<float> qtmp;
+    const int L = index->tree.n_leaves;
+    for (int64_t b0 = 0; b0 < nq; b0 += 4096) {
+      const int nb = (int)std::min<int64_t>(4096, nq - b0);
+      const float* dQ = stage_queries(index, queries + (size_t)b0 * index->m, nb, qtmp);
+      double* out = index->sLb.need((size_t)nb * L);
+      compute_bounds(index, dQ, nb, out, index->sRoute.need(nb));
+      deliver(lb2 + (size_t)b0 * L, out, (size_t)nb * L, index->stream);
+    }
+    LF_CUDA(cudaStreamSynchronize(index->stream));
+  });
+}
+
+leafi_status leafi_route(leafi_index* index, const float* queries, int64_t nq, int32_t* leaf) {
+  return guarded([&] {
+    require_device(index);
+    check_queries(index, queries, nq);
+    if (nq > 0 && !leaf) fail(LEAFI_EINVAL, "leaf is NULL");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    DBuf<float> qtmp;
+    const int L = index->tree.n_leaves;
+    for (int64_t b0 = 0; b0 < nq; b0 += 4096) {
+      const int nb = (int)std::min<int64_t>(4096, nq - b0);
+      const float* dQ = stage_queries(index, queries + (size_t)b0 * index->m, nb, qtmp);
+      int32_t* r = index->sRoute.need(nb);
+      compute_bounds(index, dQ, nb, index->sLb.need((size_t)nb * L), r);
+      deliver(leaf + b0, r, (size_t)nb, index->stream);
+    }
+    LF_CUDA(cudaStreamSynchronize(index->stream));
+  });
+}
+
+leafi_status leafi_select_leaves(const leafi_index* index, int32_t n_filters, int32_t* filter_leaf) {
+  return guarded([&] {
+    require_index(index);
+    const HostTree& t = index->tree;
+    if (n_filters < 0 || n_filters > t.n_leaves) fail(LEAFI_EINVAL, "n_filters out of range");
+    if (n_filters > 0 && !filter_leaf) fail(LEAFI_EINVAL, "filter_leaf is NULL");
+    std::vector<int32_t> idx(t.n_leaves);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+      return (t.leaf_off[a + 1] - t.leaf_off[a]) > (t.leaf_off[b + 1] - t.leaf_off[b]);
+    });
+    for (int i = 0; i < n_filters; ++i) filter_leaf[i] = idx[i];
+  });
+}
+
+leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F, int32_t h,
+                               const float* W1, const float* b1, const float* w2, const float* b2) {
+  return guarded([&] {
+    require_device(index);
+    if (F < 1 || F > index->tree.n_leaves) fail(LEAFI_EINVAL, "F out of range");
+    if (h < 1 || h > 4096) fail(LEAFI_EINVAL, "h out of range");
+    if (index->m > 1024) fail(LEAFI_EINVAL, "filters support m <= 1024");
+    if (!filter_leaf || !W1 || !b1 || !w2 || !b2) fail(LEAFI_EINVAL, "NULL filter argument");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    std::vector<int32_t> fl;
+    to_host(fl, filter_leaf, F, s);
+    std::vector<int32_t> leaf_filter(index->tree.n_leaves, -1);
+    for (int f = 0; f < F; ++f) {
+      if (fl[f] < 0 || fl[f] >= index->tree.n_leaves) fail(LEAFI_EINVAL, "filter leaf out of range");
+      if (leaf_filter[fl[f]] >= 0) fail(LEAFI_EINVAL, "leaf %d has two filters", fl[f]);
+      leaf_filter[fl[f]] = f;
+    }
+    const int m = index->m;
+    DBuf<float> tmp;
+    const float* dW = to_device(W1, (size_t)F * h * m, tmp, s);
+    float* Wt = index->W1t.need((size_t)F * m * h);
+    const size_t tot = (size_t)F * h * m;
+    transpose_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dW, Wt, F, h, m);
+    LF_CHECK_LAUNCH();
+    DBuf<float> t1, t2, t3;
+    const float* db1 = to_device(b1, (size_t)F * h, t1, s);
+    const float* dw2 = to_device(w2, (size_t)F * h, t2, s);
+    const float* db2 = to_device(b2, (size_t)F, t3, s);
+    LF_CUDA(cudaMemcpyAsync(index->b1.need((size_t)F * h), db1, sizeof(float) * F * h, cudaMemcpyDeviceToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(index->w2.need((size_t)F * h), dw2, sizeof(float) * F * h, cudaMemcpyDeviceToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(index->b2.need(F), db2, sizeof(float) * F, cudaMemcpyDeviceToDevice, s));
+    index->d_filter_leaf.upload(fl, s);
+    index->d_leaf_filter.upload(leaf_filter, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+    index->filter_leaf = fl;
+    index->F = F;
+    index->h = h;
+    index->trained = false;
+    index->nc = 0;
+    index->nk = 0;
+  });
+}
+
+leafi_status leafi_get_filters(leafi_index* index, float* W1, float* b1, float* w2, float* b2) {
+  return guarded([&] {
+    require_device(index);
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    if (!W1 || !b1 || !w2 || !b2) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    const int F = index->F, h = index->h, m = index->m;
+    DBuf<float> tmp;
+    float* d = tmp.need((size_t)F * h * m);
+    const size_t tot = (size_t)F * h * m;
+    transpose_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(index->W1t.p, d, F, m, h);
+    LF_CHECK_LAUNCH();
+    deliver(W1, d, tot, s);
+    deliver(b1, index->b1.p, (size_t)F * h, s);
+    deliver(w2, index->w2.p, (size_t)F * h, s);
+    deliver(b2, index->b2.p, (size_t)F, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+leafi_status leafi_filter_predict(leafi_index* index, const float* queries, int64_t nq, float* out) {
+  return guarded([&] {
+    require_device(index);
+    check_queries(index, queries, nq);
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    if (nq > 0 && !out) fail(LEAFI_EINVAL, "out is NULL");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    DBuf<float> qtmp;
+    for (int64_t b0 = 0; b0 < nq; b0 += 4096) {
+      const int nb = (int)std::min<int64_t>(4096, nq - b0);
+      const float* dQ = stage_queries(index, queries + (size_t)b0 * index->m, nb, qtmp);
+      float* P = index->sPred.need((size_t)nb * index->F);
+      launch_filter_forward(dQ, nb, index->mp, index->m, index->F, index->h, index->W1t.p,
+                            index->b1.p, index->w2.p, index->b2.p, P, index->stream);
+      deliver(out + (size_t)b0 * index->F, P, (size_t)nb * index->F, index->stream);
+    }
+    LF_CUDA(cudaStreamSynchronize(index->stream));
+  });
+}
+
+leafi_status leafi_leaf_knn(leafi_index* index, const float* queries, int64_t nq,
+                            const int32_t* leaves, int32_t nl, int32_t k, float* d2, int64_t* ids) {
+  return guarded([&] {
+    require_device(index);
+    check_queries(index, queries, nq);
+    if (k < 1 || k > LEAFI_MAX_K) fail(LEAFI_EINVAL, "k must be in [1, %d]", LEAFI_MAX_K);
+    if (nl < 1 || (nq > 0 && (!leaves || !d2 || !ids))) fail(LEAFI_EINVAL, "bad leaves / outputs");
+    if ((int64_t)nq * nl > std::numeric_limits<int32_t>::max() / 2) fail(LEAFI_EINVAL, "nq * nl too large");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    DBuf<float> qtmp;
+    DBuf<int32_t> ltmp;
+    const float* dQ = stage_queries(index, queries, nq, qtmp);
+    const int32_t* dL = to_device(leaves, (size_t)nq * nl, ltmp, s);
+    DBuf<unsigned long long> topk;
+    DBuf<int32_t> cnt;
+    leaf_knn_device(index, dQ, (int)nq, dL, nl, k, topk, cnt);
+    DBuf<float> od;
+    DBuf<int64_t> oi;
+    const int ns = (int)(nq * nl);
+    launch_leafknn_out(ns, k, topk.p, cnt.p, od.need((size_t)ns * k), oi.need((size_t)ns * k), s);
+    deliver(d2, od.p, (size_t)ns * k, s);
+    deliver(ids, oi.p, (size_t)ns * k, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+}  // extern "C"
+
+namespace leafi {
+namespace {
+
+// Tg [ng][F] and Tl [F][nl] (Euclidean) on the device
+void train_targets_device(leafi_index* ix, const float* dQg, int ng, const float* dQl, int nl,
+                          float* Tg, float* Tl) {
+  cudaStream_t s = ix->stream;
+  const int F = ix->F;
+  DBuf<unsigned long long> topk;
+  DBuf<int32_t> cnt;
+  DBuf<float> d2;
+  DBuf<int64_t> id;
+  if (ng > 0) {
+    std::vector<int32_t> lv((size_t)ng * F);
+    for (int g = 0; g < ng; ++g)
+      for (int f = 0; f < F; ++f) lv[(size_t)g * F + f] = ix->filter_leaf[f];
+    DBuf<int32_t> dl;
+    dl.upload(lv, s);
+    leaf_knn_device(ix, dQg, ng, dl.p, F, 1, topk, cnt);
+    launch_leafknn_out(ng * F, 1, topk.p, cnt.p, d2.need((size_t)ng * F), id.need((size_t)ng * F), s);
+    sqrt_kernel<<<(unsigned)(((size_t)ng * F + 255) / 256), 256, 0, s>>>(d2.p, Tg, (size_t)ng * F);
+    LF_CHECK_LAUNCH();
+  }
+  if (nl > 0) {
+    std::vector<int32_t> lv((size_t)F * nl);
+    for (int f = 0; f < F; ++f)
+      for (int i = 0; i < nl; ++i) lv[(size_t)f * nl + i] = ix->filter_leaf[f];
+    DBuf<int32_t> dl;
+    dl.upload(lv, s);
+    leaf_knn_device(ix, dQl, F * nl, dl.p, 1, 1, topk, cnt);
+    launch_leafknn_out(F * nl, 1, topk.p, cnt.p, d2.need((size_t)F * nl), id.need((size_t)F * nl), s);
+    sqrt_kernel<<<(unsigned)(((size_t)F * nl + 255) / 256), 256, 0, s>>>(d2.p, Tl, (size_t)F * nl);
+    LF_CHECK_LAUNCH();
+  }
+  LF_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+}  // namespace leafi
+
+extern "C" {
+
+leafi_status leafi_train_targets(leafi_index* index, const float* Qg, int64_t ng, const float* Ql,
+                                 int64_t nl, float* Tg, float* Tl) {
+  return guarded([&] {
+    require_device(index);
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    check_queries(index, Qg, ng);
+    check_queries(index, Ql, nl * index->F);
+    if ((ng > 0 && !Tg) || (nl > 0 && !Tl)) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    DBuf<float> qg, ql, tg, tl;
+    const float* dQg = ng ? stage_queries(index, Qg, ng, qg) : nullptr;
+    const float* dQl = nl ? stage_queries(index, Ql, nl * index->F, ql) : nullptr;
+    float* dTg = tg.need((size_t)ng * index->F);
+    float* dTl = tl.need((size_t)nl * index->F);
+    train_targets_device(index, dQg, (int)ng, dQl, (int)nl, dTg, dTl);
+    deliver(Tg, dTg, (size_t)ng * index->F, s);
+    deliver(Tl, dTl, (size_t)nl * index->F, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p, const float* Qg,
+                                 const float* Ql, const int32_t* perms, int32_t* epochs_run,
+                                 double* best_val) {
+  return guarded([&] {
+    require_device(index);
+    if (!p || !Qg || !Ql || !perms) fail(LEAFI_EINVAL, "NULL argument");
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    if (p->n_gtrain < 0 || p->n_gval < 1 || p->n_ltrain < 0 || p->n_lval < 0 ||
+        p->n_gtrain + p->n_ltrain < 1 || p->batch < 1 || p->max_epochs < 1 || p->patience < 1 ||
+        !(p->lr0 > 0) || !(p->lr_min > 0) || p->lr_min > p->lr0)
+      fail(LEAFI_EINVAL, "bad training parameters");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    const int F = index->F, h = index->h, m = index->m;
+    const int ng = p->n_gtrain + p->n_gval, nl = p->n_ltrain + p->n_lval;
+    DBuf<float> qg, ql, tg, tl;
+    const float* dQg = stage_queries(index, Qg, ng, qg);
+    const float* dQl = stage_queries(index, Ql, (int64_t)F * nl, ql);
+    float* dTg = tg.need((size_t)ng * F);
+    float* dTl = tl.need((size_t)std::max(nl, 1) * F);
+    train_targets_device(index, dQg, ng, dQl, nl, dTg, dTl);
+    // every shuffle entry must index the training set: checked on the host
+    const size_t ntr = (size_t)p->n_gtrain + p->n_ltrain;
+    std::vector<int32_t> hperm;
+    to_host(hperm, perms, (size_t)p->max_epochs * ntr, s);
+    for (int32_t v : hperm)
+      if (v < 0 || (size_t)v >= ntr) fail(LEAFI_EINVAL, "perms entry %d outside [0, %zu)", v, ntr);
+    DBuf<int32_t> dperm;
+    dperm.upload(hperm, s);
+    const int32_t* dP = dperm.p;
+    DBuf<float> bW, bb1, bw2, bb2;
+    DBuf<int32_t> dep;
+    DBuf<double> dbv;
+    // number of lr divisions before stopping: the last one keeping lr >= lr_min
+    int max_decays = 0;
+    {
+      double lr = p->lr0;
+      for (;;) {
+        lr /= 10.0;
+        if (lr < p->lr_min * (1.0 - 1e-9)) break;
+        ++max_decays;
+      }
+    }
+    TrainArgs a;
+    a.F = F;
+    a.h = h;
+    a.m = m;
+    a.mp = index->mp;
+    a.n_gtrain = p->n_gtrain;
+    a.n_gval = p->n_gval;
+    a.n_ltrain = p->n_ltrain;
+    a.n_lval = p->n_lval;
+    a.batch = p->batch;
+    a.max_epochs = p->max_epochs;
+    a.patience = p->patience;
+    a.max_decays = max_decays;
+    a.lr0 = (float)p->lr0;
+    a.Qg = dQg;
+    a.Ql = dQl;
+    a.Tg = dTg;
+    a.Tl = dTl;
+    a.perms = dP;
+    a.W1t = index->W1t.p;
+    a.b1 = index->b1.p;
+    a.w2 = index->w2.p;
+    a.b2 = index->b2.p;
+    a.bW1t = bW.need((size_t)F * m * h);
+    a.bb1 = bb1.need((size_t)F * h);
+    a.bw2 = bw2.need((size_t)F * h);
+    a.bb2 = bb2.need(F);
+    a.epochs_run = dep.need(F);
+    a.best_val = dbv.need(F);
+    launch_train(a, s);
+    std::vector<int32_t> hep(F);
+    std::vector<double> hbv(F);
+    LF_CUDA(cudaMemcpyAsync(hep.data(), a.epochs_run, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
+    LF_CUDA(cudaMemcpyAsync(hbv.data(), a.best_val, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
+    LF_CUDA(cudaStreamSynchronize(s));
+    if (epochs_run) std::memcpy(epochs_run, hep.data(), sizeof(int32_t) * F);
+    if (best_val) std::memcpy(best_val, hbv.data(), sizeof(double) * F);
+    index->trained = true;
+    index->nc = 0;
+    index->nk = 0;
+  });
+}
+
+leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t nc,
+                                  const int32_t* kclasses, int32_t nk) {
+  return guarded([&] {
+    require_device(index);
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    check_queries(index, Qc, nc);
+    if (nc < 1 || nc > calib_max_sort()) fail(LEAFI_EINVAL, "nc must be in [1, %d]", calib_max_sort());
+    if (nk < 1 || nk > LEAFI_MAX_KCLASSES || !kclasses) fail(LEAFI_EINVAL, "bad k-classes");
+    for (int i = 0; i < nk; ++i) {
+      if (kclasses[i] < 1 || kclasses[i] > LEAFI_MAX_K) fail(LEAFI_EINVAL, "k-class out of range");
+      if (i && kclasses[i] <= kclasses[i - 1]) fail(LEAFI_EINVAL, "k-classes must ascend");
+    }
+    const int L = index->tree.n_leaves;
+    if (L > calib_max_sort()) fail(LEAFI_EINVAL, "auto-tuner supports at most %d leaves", calib_max_sort());
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    const int F = index->F;
+    const int kmax = kclasses[nk - 1];
+    DBuf<float> qtmp;
+    const float* dQ = stage_queries(index, Qc, nc, qtmp);
+    DBuf<double> lb2;
+    DBuf<int32_t> route;
+    compute_bounds(index, dQ, (int)nc, lb2.need((size_t)nc * L), route.need(nc));
+    std::vector<int32_t> lv((size_t)nc * L);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int l = 0; l < L; ++l) lv[(size_t)c * L + l] = l;
+    DBuf<int32_t> dl;
+    dl.upload(lv, s);
+    DBuf<unsigned long long> lk_keys;
+    DBuf<int32_t> lk_cnt;
+    leaf_knn_device(index, dQ, (int)nc, dl.p, L, kmax, lk_keys, lk_cnt);
+    DBuf<float> P;
+    launch_filter_forward(dQ, (int)nc, index->mp, index->m, F, index->h, index->W1t.p, index->b1.p,
+                          index->w2.p, index->b2.p, P.need((size_t)nc * F), s);
+    double* alpha = index->alpha.need((size_t)F * nc);
+    double* qprime = index->qprime.need((size_t)nk * nc);
+    DBuf<int32_t> ord, cnt_true;
+    DBuf<unsigned long long> work;
+    DBuf<long long> hits;
+    CalibArgs a;
+    a.nc = (int)nc;
+    a.L = L;
+    a.F = F;
+    a.W = index->wave;
+    a.lb2 = lb2.p;
+    a.route = route.p;
+    a.lk = lk_keys.p;
+    a.lk_stride = kmax;
+    a.P = P.p;
+    a.filter_leaf = index->d_filter_leaf.p;
+    a.leaf_filter = index->d_leaf_filter.p;
+    a.alpha = alpha;
+    a.ord = ord.need((size_t)nc * L);
+    a.cnt_true = cnt_true.need((size_t)nc * L);
+    a.hits = hits.need(nc);
+    a.kc = 1;
+    launch_calib_alpha(a, s);
+    for (int ci = 0; ci < nk; ++ci) {
+      a.kc = kclasses[ci];
+      a.kk = (int)std::min<int64_t>(a.kc, index->n);
+      a.work = work.need(std::max((size_t)nc * nc * a.kc, (size_t)nc * L / 2 + 1));
+      a.qprime = qprime + (size_t)ci * nc;
+      launch_calib_sim(a, s);
+    }
+    std::vector<int32_t> kc(kclasses, kclasses + nk);
+    index->d_kclasses.upload(kc, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+    index->nc = (int)nc;
+    index->nk = nk;
+    for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? kclasses[i] : 0;
+  });
+}
+
+leafi_status leafi_get_autotuners(leafi_index* index, double* alpha_sorted, double* qprime) {
+  return guarded([&] {
+    require_device(index);
+    if (index->nc == 0) fail(LEAFI_ENOTTRAINED, "no auto-tuners fitted");
+    if (!alpha_sorted || !qprime) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    deliver(alpha_sorted, index->alpha.p, (size_t)index->F * index->nc, index->stream);
+    deliver(qprime, index->qprime.p, (size_t)index->nk * index->nc, index->stream);
+    LF_CUDA(cudaStreamSynchronize(index->stream));
+  });
+}
+
+leafi_status leafi_set_autotuners(leafi_index* index, const double* alpha_sorted,
+                                  const double* qprime, int64_t nc, const int32_t* kclasses,
+                                  int32_t nk) {
+  return guarded([&] {
+    require_device(index);
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    if (!alpha_sorted || !qprime || !kclasses) fail(LEAFI_EINVAL, "NULL argument");
+    if (nc < 1 || nc > (1 << 24)) fail(LEAFI_EINVAL, "nc out of range");
+    if (nk < 1 || nk > LEAFI_MAX_KCLASSES) fail(LEAFI_EINVAL, "bad k-classes");
+    std::vector<int32_t> kc;
+    to_host(kc, kclasses, nk, index->stream);
+    for (int i = 0; i < nk; ++i)
+      if (kc[i] < 1 || kc[i] > LEAFI_MAX_K || (i && kc[i] <= kc[i - 1])) fail(LEAFI_EINVAL, "bad k-classes");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    DBuf<double> t1, t2;
+    const double* da = to_device(alpha_sorted, (size_t)index->F * nc, t1, s);
+    const double* dq = to_device(qprime, (size_t)nk * nc, t2, s);
+    LF_CUDA(cudaMemcpyAsync(index->alpha.need((size_t)index->F * nc), da,
+                            sizeof(double) * index->F * nc, cudaMemcpyDeviceToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(index->qprime.need((size_t)nk * nc), dq, sizeof(double) * nk * nc,
+                            cudaMemcpyDeviceToDevice, s));
+    index->d_kclasses.upload(kc, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+    index->nc = (int)nc;
+    index->nk = nk;
+    for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? kc[i] : 0;
+  });
+}
+
+leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
+                          double recall_target, int64_t* ids, float* dists,
+                          leafi_search_stats* stats) {
+  return guarded([&] {
+    require_device(index);
+    check_queries(index, queries, nq);
+    if (k < 1 || k > LEAFI_MAX_K) fail(LEAFI_EINVAL, "k must be in [1, %d]", LEAFI_MAX_K);
+    if (!(recall_target > 0.0)) fail(LEAFI_EINVAL, "recall_target must be > 0");
+    if (nq > 0 && (!ids || !dists)) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    std::vector<int32_t> kq(nq, k);
+    std::vector<double> tg(nq, recall_target);
+    search_impl(index, queries, nq, kq, tg, k, ids, dists, stats);
+  });
+}
+
+leafi_status leafi_exact_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
+                                int64_t* ids, float* dists, leafi_search_stats* stats) {
+  return leafi_search(index, queries, nq, k, 1.0, ids, dists, stats);
+}
+
+leafi_status leafi_search_mixed(leafi_index* index, const float* queries, int64_t nq,
+                                const int32_t* k, const double* recall_target, int32_t kmax,
+                                int64_t* ids, float* dists, leafi_search_stats* stats) {
+  return guarded([&] {
+    require_device(index);
+    check_queries(index, queries, nq);
+    if (kmax < 1 || kmax > LEAFI_MAX_K) fail(LEAFI_EINVAL, "kmax must be in [1, %d]", LEAFI_MAX_K);
+    if (nq > 0 && (!k || !recall_target || !ids || !dists)) fail(LEAFI_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    std::vector<int32_t> kq;
+    std::vector<double> tg;
+    to_host(kq, k, nq, index->stream);
+    to_host(tg, recall_target, nq, index->stream);
+    for (int64_t i = 0; i < nq; ++i) {
+      if (kq[i] < 1 || kq[i] > kmax) fail(LEAFI_EINVAL, "k[%lld] out of range", (long long)i);
+      if (!(tg[i] > 0.0)) fail(LEAFI_EINVAL, "recall_target[%lld] must be > 0", (long long)i);
+    }
+    search_impl(index, queries, nq, kq, tg, kmax, ids, dists, stats);
+  });
+}
+
+}  // extern "C"

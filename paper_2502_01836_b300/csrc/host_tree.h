@@ -1,0 +1,55 @@
+// Host-side index construction (DSTree / iSAX) and the flat tables the
+// device kernels read.  Building the tree is a one-off host step of
+// leafi_build; every per-query step runs on the GPU.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace leafi {
+
+struct HostTree {
+  int type = 0;  // LEAFI_DSTREE / LEAFI_ISAX
+  int m = 0;
+  int64_t n = 0;
+  int n_nodes = 0;
+  int n_leaves = 0;
+
+  // leaf-major layout: leaf l holds positions [leaf_off[l], leaf_off[l+1]),
+  // position p stores series order[p] (original id), ascending within a leaf
+  std::vector<int64_t> leaf_off;
+  std::vector<int32_t> order;
+  std::vector<int32_t> leaf_node;   // leaf -> node
+  std::vector<int32_t> node_leaf;   // node -> leaf (-1 for internal / empty)
+  std::vector<int32_t> node_parent;
+  std::vector<int32_t> node_left, node_right;
+
+  // --- DSTree ---
+  // segment intervals [s, e) used by any node; query statistics are computed
+  // once per interval and shared by all nodes that use it
+  std::vector<int32_t> iv_s, iv_e;
+  std::vector<int32_t> node_seg_off;  // node -> first segment record, n_nodes + 1 entries
+  std::vector<int32_t> seg_iv;        // segment record -> interval
+  std::vector<double> seg_mlo, seg_mhi, seg_slo, seg_shi;
+  // split rule of internal nodes: statistic of interval split_iv, sigma if split_sd
+  std::vector<int32_t> split_iv, split_sd;
+  std::vector<double> split_thresh;
+  int root = 0;
+  // root-to-leaf node lists
+  std::vector<int32_t> path_off, path;
+
+  // --- iSAX ---
+  int w = 0, bits = 0;
+  std::vector<double> beta;          // 2^bits + 1 entries: -inf, beta_1 .. beta_{C-1}, +inf
+  std::vector<int32_t> root_child;   // 2^w entries, node or -1
+  std::vector<int32_t> isax_split;   // internal node -> refined segment
+  std::vector<int32_t> leaf_lo_sym;  // leaf x w: first full-cardinality symbol covered
+  std::vector<int32_t> leaf_hi_sym;  // leaf x w: one past the last symbol covered
+  std::vector<int32_t> node_bits, node_sym;  // node x w
+};
+
+// Deterministic builds; both follow the readings documented with the oracle
+// and produce identical trees for identical inputs.
+HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_segments);
+HostTree build_isax(const float* X, int64_t n, int m, int leaf_cap, int w, int card_bits);
+
+}  // namespace leafi

@@ -1,0 +1,277 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "host_tree.h"
+#include "leafi.h"
+
+namespace leafi {
+
+// ----------------------------------------------------------------- errors
+struct Failure {
+  leafi_status status;
+  std::string msg;
+};
+[[noreturn]] void fail(leafi_status st, const char* fmt, ...);
+void set_last_error(const std::string& s);
+
+#define LF_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      ::leafi::fail(e_ == cudaErrorMemoryAllocation ? LEAFI_ENOMEM : LEAFI_ECUDA,          \
+                    "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                    __LINE__);                                                             \
+  } while (0)
+
+void count_launch();
+#define LF_CHECK_LAUNCH()            \
+  do {                               \
+    ::leafi::count_launch();         \
+    LF_CUDA(cudaGetLastError());     \
+  } while (0)
+
+// ------------------------------------------------------ device buffers
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  // grow to at least `count` elements (contents not preserved)
+  T* need(size_t count) {
+    if (count <= n && p) return p;
+    release();
+    size_t c = count ? count : 1;
+    LF_CUDA(cudaMalloc(&p, c * sizeof(T)));
+    n = c;
+    return p;
+  }
+  void upload(const T* h, size_t count, cudaStream_t s) {
+    need(count);
+    if (count) LF_CUDA(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void upload(const std::vector<T>& v, cudaStream_t s) { upload(v.data(), v.size(), s); }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+// keys of candidate results: (float bits of d^2) << 32 | original id.  d^2 >= 0
+// so the float bits order like the values; ties break on the lower id.
+constexpr unsigned long long kNoKey = ~0ull;
+
+// ----------------------------------------------------------------- tables
+struct DsTables {  // device view of a DSTree
+  int n_nodes, n_leaves, n_iv, root;
+  const int32_t *iv_s, *iv_e;
+  const int32_t *seg_off, *seg_iv;
+  const double *mlo, *mhi, *slo, *shi;
+  const int32_t *left, *right, *node_leaf, *split_iv, *split_sd;
+  const double* thresh;
+  const int32_t *path_off, *path;
+};
+
+struct IsaxTables {  // device view of an iSAX tree
+  int n_nodes, n_leaves, w, bits;
+  const double* beta;  // 2^bits + 1
+  const int32_t *root_child, *left, *right, *node_leaf, *isplit, *node_bits;
+  const int32_t *lo_sym, *hi_sym;  // leaf x w
+};
+
+// work pairs of one scan round: query row `q` searches leaf `leaf`, results
+// go to top-k slot `slot`
+struct Pair {
+  int32_t slot, q, leaf, pad;
+};
+
+// ----------------------------------------------------------------- kernels
+// (declared here, defined in the k_*.cu files)
+void launch_prefix(const float* Q, int nq, int mp, int m, double* P, cudaStream_t s);
+void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double* ivstat,
+                      double* node_lb, double* leaf_lb, int32_t* route, cudaStream_t s);
+void launch_isax_bounds(const IsaxTables& T, const double* P, int nq, int m, double* paa,
+                        double* leaf_lb, int32_t* route, cudaStream_t s);
+
+void launch_filter_forward(const float* Q, int nq, int mp, int m, int F, int h, const float* W1t,
+                           const float* b1, const float* w2, const float* b2, float* out,
+                           cudaStream_t s);
+
+struct TrainArgs {
+  int F, h, m, mp;
+  int n_gtrain, n_gval, n_ltrain, n_lval, batch, max_epochs, patience, max_decays;
+  float lr0;
+  const float *Qg, *Ql, *Tg, *Tl;  // Qg [ng][mp], Ql [F][nl][mp], Tg [ng][F], Tl [F][nl]
+  const int32_t* perms;
+  float *W1t, *b1, *w2, *b2;       // trained in place
+  float *bW1t, *bb1, *bw2, *bb2;   // best-validation copies
+  int32_t* epochs_run;
+  double* best_val;
+};
+void launch_train(const TrainArgs& a, cudaStream_t s);
+
+struct ScanArgs {
+  const float* X;        // [n][mp] leaf-major
+  const int32_t* ids;    // position -> original id
+  const int64_t* leaf_off;
+  int L, mp, k;
+  int part;              // series per work item
+  const float* Q;        // [nq][mp]
+  const Pair* pairs;     // grouped by leaf
+  const int32_t* grp_off;   // L + 1: pair offsets per leaf
+  const int32_t* item_off;  // L + 1: work-item offsets per leaf
+  const unsigned long long* thr;  // per slot: admission threshold key
+  unsigned long long* cand;       // per slot: candidate keys (cap each)
+  int32_t* cand_cnt;              // per slot
+  int cand_cap;
+  int32_t* err;                   // error word (set on overflow)
+};
+size_t scan_smem_bytes(int mp, int k);
+int scan_group_size();
+void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k, int grid,
+                 cudaStream_t s);
+
+// stat (nullable): stat[0] += series of the distinct leaves in this round
+void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
+                  const int64_t* leaf_off, int part, int32_t* cnt, int32_t* grp_off,
+                  int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
+                  unsigned long long* stat, cudaStream_t s);
+
+void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
+                  int32_t* topk_cnt, unsigned long long* thr, const unsigned long long* cand,
+                  int32_t* cand_cnt, int cand_cap, cudaStream_t s);
+
+struct SelectArgs {
+  int nq, L, W;
+  const double* lb2;              // [nq][L]
+  const unsigned long long* thr;  // per query admission key (k-th best)
+  // filters (P null = filters off for all)
+  const float* P;                 // [nq][F]
+  int F;
+  const int32_t* leaf_filter;     // [L] filter of a leaf or -1
+  const double* alpha;            // [F][nc]
+  int nc;
+  const int32_t* jpos;            // [nq] sorted position or -1
+  const int64_t* leaf_off;
+  // state
+  unsigned char* scanned;         // [nq][L]
+  double* cur_lb;                 // [nq] cursor
+  int32_t* cur_leaf;              // [nq]
+  int32_t* done;                  // [nq]
+  Pair* pairs;
+  int32_t* npairs;
+  unsigned long long* stat;       // [0] leaves searched, [1] series scanned
+};
+
+// per-kernel device time on the index's stream (enabled by leafi_set_profiling)
+struct KernelClock {
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
+  std::vector<int> kind;
+  double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+void launch_select(const SelectArgs& a, cudaStream_t s);
+void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
+                        const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
+                        unsigned long long* stat, cudaStream_t s);
+void launch_leafknn_pairs(int nq, int nl, const int32_t* leaves, int L, Pair* pairs,
+                          int32_t* npairs, cudaStream_t s);
+void launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_t s);
+void launch_jpos(int nq, const int32_t* k, const double* target, int nk, const int32_t* kclasses,
+                 const double* qprime, int nc, int32_t* jpos, cudaStream_t s);
+void launch_write_results(int nq, int kmax, const int32_t* kq, const unsigned long long* topk,
+                          int kstride, const int32_t* topk_cnt, int64_t* ids, float* dists,
+                          cudaStream_t s);
+void launch_leafknn_out(int nslots, int k, const unsigned long long* topk, const int32_t* topk_cnt,
+                        float* d2, int64_t* ids, cudaStream_t s);
+
+// calibration (Alg. 4)
+struct CalibArgs {
+  int nc, L, F, kc, W;
+  const double* lb2;              // [nc][L]
+  const int32_t* route;           // [nc]
+  const unsigned long long* lk;   // [nc][L][lk_stride] per-leaf top keys (first kc used)
+  int lk_stride;
+  const float* P;                 // [nc][F]
+  const int32_t* filter_leaf;     // [F]
+  const int32_t* leaf_filter;     // [L]
+  double* alpha;                  // [F][nc] (sorted descending after launch_calib_alpha)
+  int32_t* ord;                   // [nc][L] scratch: visiting order
+  int32_t* cnt_true;              // [nc][L] scratch
+  unsigned long long* work;       // scratch, >= max(nc*nc*kc, nc*L/2 + 1) entries
+  long long* hits;                // [nc] scratch
+  double* qprime;                 // [nc] out
+  int kk;                         // min(kc, n)
+};
+int calib_max_sort();
+int calib_max_wave();
+void launch_calib_alpha(const CalibArgs& a, cudaStream_t s);
+void launch_calib_sim(const CalibArgs& a, cudaStream_t s);
+
+}  // namespace leafi
+
+// ----------------------------------------------------------------- index
+struct leafi_index {
+  std::mutex mu;
+  int device = 0;          // -1: host-only index (tree inspection, no device data)
+  cudaStream_t stream = nullptr;
+  leafi::HostTree tree;
+  int m = 0, mp = 0, wave = 8;
+  int64_t n = 0;
+
+  // resident data
+  leafi::DBuf<float> X;          // [n][mp] leaf-major
+  leafi::DBuf<int32_t> ids;      // position -> original id
+  leafi::DBuf<int64_t> leaf_off;
+  // DSTree tables
+  leafi::DBuf<int32_t> iv_s, iv_e, seg_off, seg_iv, left, right, node_leaf, split_iv, split_sd,
+      path_off, path;
+  leafi::DBuf<double> mlo, mhi, slo, shi, thresh;
+  // iSAX tables
+  leafi::DBuf<double> beta;
+  leafi::DBuf<int32_t> root_child, isplit, node_bits, lo_sym, hi_sym;
+
+  // filters
+  int F = 0, h = 0;
+  bool trained = false;
+  std::vector<int32_t> filter_leaf;
+  leafi::DBuf<int32_t> d_filter_leaf, d_leaf_filter;
+  leafi::DBuf<float> W1t, b1, w2, b2;  // W1t [F][m][h]
+
+  // auto-tuners
+  int nc = 0, nk = 0;
+  int kclasses[LEAFI_MAX_KCLASSES] = {0, 0, 0, 0};
+  leafi::DBuf<double> alpha, qprime;
+  leafi::DBuf<int32_t> d_kclasses;
+
+  // scratch (grown on demand)
+  leafi::DBuf<float> sQ;
+  leafi::DBuf<double> sP, sIv, sNode, sLb, sPaa, sTarget;
+  leafi::DBuf<int32_t> sRoute, sK, sJpos, sCnt, sGrpOff, sItemOff, sNpairs, sCandCnt, sTopkCnt,
+      sDone, sCurLeaf, sErr, sLeaves, sNItems;
+  leafi::DBuf<double> sCurLb;
+  leafi::DBuf<unsigned char> sScanned;
+  leafi::DBuf<leafi::Pair> sPairs, sGrouped;
+  leafi::DBuf<unsigned long long> sTopk, sThr, sCand, sStat;
+  leafi::DBuf<float> sPred, sOutD;
+  leafi::DBuf<int64_t> sOutI;
+
+  bool profiling = false;
+  leafi::KernelClock clock;
+  void tick(int kind);   // record a start event of `kind` on the stream
+  void tock();           // record the matching stop event
+  void settle();         // accumulate finished event pairs (stream synchronised)
+
+  leafi::DsTables ds() const;
+  leafi::IsaxTables isax() const;
+};

@@ -1,0 +1,250 @@
+// Query preparation and summarisation lower bounds (Sec. 3, Alg. 2 line 4).
+//
+// Every float64 operation is written with an explicit round-to-nearest
+// intrinsic so nothing is contracted or reassociated: query statistics,
+// DSTree EAPCA bounds, iSAX MINDIST and the routing decisions equal the host
+// build's arithmetic bit for bit.
+#include <cfloat>
+
+#include "internal.h"
+
+namespace leafi {
+namespace {
+
+constexpr int kThreads = 128;
+
+// Per query: P1[i] = sum_{t<i} q_t, P2[i] = sum_{t<i} q_t^2 (float64, sequential).
+// One thread per query; the order of the additions is fixed.
+__global__ void prefix_kernel(const float* __restrict__ Q, int nq, int mp, int m,
+                              double* __restrict__ P) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const float* x = Q + (size_t)q * mp;
+  double* p1 = P + (size_t)q * 2 * (m + 1);
+  double* p2 = p1 + m + 1;
+  double a = 0.0, b = 0.0;
+  p1[0] = 0.0;
+  p2[0] = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double v = (double)x[i];
+    a = __dadd_rn(a, v);
+    b = __dadd_rn(b, __dmul_rn(v, v));
+    p1[i + 1] = a;
+    p2[i + 1] = b;
+  }
+}
+
+__device__ __forceinline__ void interval_stat(const double* p1, const double* p2, int s, int e,
+                                              double& mu, double& sd) {
+  const double len = (double)(e - s);
+  const double mean = __ddiv_rn(__dsub_rn(p1[e], p1[s]), len);
+  double var = __dsub_rn(__ddiv_rn(__dsub_rn(p2[e], p2[s]), len), __dmul_rn(mean, mean));
+  if (var < 0.0) var = 0.0;
+  mu = mean;
+  sd = __dsqrt_rn(var);
+}
+
+__device__ __forceinline__ double gap(double v, double lo, double hi) {
+  if (v < lo) return __dsub_rn(lo, v);
+  if (v > hi) return __dsub_rn(v, hi);
+  return 0.0;
+}
+
+// query statistics of every distinct segment interval: ivstat [nq][n_iv][2]
+__global__ void ds_interval_kernel(DsTables T, const double* __restrict__ P, int nq, int m,
+                                   double* __restrict__ ivstat) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nq * T.n_iv) return;
+  const int q = (int)(t / T.n_iv), iv = (int)(t % T.n_iv);
+  const double* p1 = P + (size_t)q * 2 * (m + 1);
+  double mu, sd;
+  interval_stat(p1, p1 + m + 1, T.iv_s[iv], T.iv_e[iv], mu, sd);
+  ivstat[2 * t] = mu;
+  ivstat[2 * t + 1] = sd;
+}
+
+// node bound: sum over the node's segments of l_r (gap_mu^2 + gap_sigma^2)
+__global__ void ds_node_kernel(DsTables T, const double* __restrict__ ivstat, int nq,
+                               double* __restrict__ node_lb) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nq * T.n_nodes) return;
+  const int q = (int)(t / T.n_nodes), v = (int)(t % T.n_nodes);
+  const double* st = ivstat + (size_t)q * T.n_iv * 2;
+  double acc = 0.0;
+  for (int r = T.seg_off[v]; r < T.seg_off[v + 1]; ++r) {
+    const int iv = T.seg_iv[r];
+    const double gm = gap(st[2 * iv], T.mlo[r], T.mhi[r]);
+    const double gs = gap(st[2 * iv + 1], T.slo[r], T.shi[r]);
+    const double len = (double)(T.iv_e[iv] - T.iv_s[iv]);
+    acc = __dadd_rn(acc, __dmul_rn(len, __dadd_rn(__dmul_rn(gm, gm), __dmul_rn(gs, gs))));
+  }
+  node_lb[t] = acc;
+}
+
+// leaf bound = max over the root-to-leaf path
+__global__ void ds_leaf_kernel(DsTables T, const double* __restrict__ node_lb, int nq,
+                               double* __restrict__ leaf_lb) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nq * T.n_leaves) return;
+  const int q = (int)(t / T.n_leaves), l = (int)(t % T.n_leaves);
+  const double* nl = node_lb + (size_t)q * T.n_nodes;
+  double best = 0.0;
+  for (int i = T.path_off[l]; i < T.path_off[l + 1]; ++i) {
+    const double v = nl[T.path[i]];
+    if (v > best) best = v;
+  }
+  leaf_lb[t] = best;
+}
+
+__global__ void ds_route_kernel(DsTables T, const double* __restrict__ ivstat, int nq,
+                                int32_t* __restrict__ route) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const double* st = ivstat + (size_t)q * T.n_iv * 2;
+  int v = T.root;
+  for (int guard = 0; guard < T.n_nodes && T.node_leaf[v] < 0; ++guard) {
+    const int iv = T.split_iv[v];
+    const double val = T.split_sd[v] ? st[2 * iv + 1] : st[2 * iv];
+    v = (val < T.thresh[v]) ? T.left[v] : T.right[v];
+  }
+  route[q] = T.node_leaf[v];
+}
+
+// ---------------------------------------------------------------- iSAX
+__global__ void isax_paa_kernel(IsaxTables T, const double* __restrict__ P, int nq, int m,
+                                double* __restrict__ paa) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nq * T.w) return;
+  const int q = t / T.w, j = t % T.w;
+  const int l = m / T.w;
+  const double* p1 = P + (size_t)q * 2 * (m + 1);
+  paa[t] = __ddiv_rn(__dsub_rn(p1[(j + 1) * l], p1[j * l]), (double)l);
+}
+
+// MINDIST^2 of each leaf's word: sum_j l (gap(PAA_j, [beta_lo, beta_hi]))^2
+__global__ void isax_leaf_kernel(IsaxTables T, const double* __restrict__ paa, int nq, int m,
+                                 double* __restrict__ leaf_lb) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nq * T.n_leaves) return;
+  const int q = (int)(t / T.n_leaves), lf = (int)(t % T.n_leaves);
+  const double len = (double)(m / T.w);
+  const double* a = paa + (size_t)q * T.w;
+  const int32_t* lo = T.lo_sym + (size_t)lf * T.w;
+  const int32_t* hi = T.hi_sym + (size_t)lf * T.w;
+  double acc = 0.0;
+  for (int j = 0; j < T.w; ++j) {
+    const double g = gap(a[j], T.beta[lo[j]], T.beta[hi[j]]);
+    acc = __dadd_rn(acc, __dmul_rn(len, __dmul_rn(g, g)));
+  }
+  leaf_lb[t] = acc;
+}
+
+__device__ int sax_symbol(const double* beta, int C, double v) {
+  // number of breakpoints beta_1 .. beta_{C-1} that are <= v
+  int lo = 1, hi = C;  // answer in [0, C-1]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (beta[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+__global__ void isax_route_kernel(IsaxTables T, const double* __restrict__ paa,
+                                  const double* __restrict__ leaf_lb, int nq,
+                                  int32_t* __restrict__ route) {
+  const int q = blockIdx.x;
+  if (q >= nq) return;
+  __shared__ int s_leaf;
+  __shared__ int s_sym[32];
+  const int C = 1 << T.bits;
+  if (threadIdx.x < T.w) s_sym[threadIdx.x] = sax_symbol(T.beta, C, paa[(size_t)q * T.w + threadIdx.x]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int key = 0;
+    for (int j = 0; j < T.w; ++j) key = (key << 1) | (s_sym[j] >> (T.bits - 1));
+    int v = T.root_child[key];
+    for (int guard = 0; v >= 0 && guard < T.n_nodes && T.isplit[v] >= 0; ++guard) {
+      const int j = T.isplit[v];
+      const int have = T.node_bits[(size_t)v * T.w + j];
+      v = ((s_sym[j] >> (T.bits - have - 1)) & 1) ? T.right[v] : T.left[v];
+    }
+    s_leaf = (v >= 0) ? T.node_leaf[v] : -1;
+  }
+  __syncthreads();
+  if (s_leaf >= 0) {
+    if (threadIdx.x == 0) route[q] = s_leaf;
+    return;
+  }
+  // no leaf on the query's own path: the leaf of smallest (LB^2, id)
+  __shared__ double s_lb[kThreads];
+  __shared__ int s_id[kThreads];
+  double best = DBL_MAX;
+  int bid = 0x7fffffff;
+  const double* row = leaf_lb + (size_t)q * T.n_leaves;
+  for (int l = threadIdx.x; l < T.n_leaves; l += blockDim.x) {
+    const double v = row[l];
+    if (v < best || (v == best && l < bid)) {
+      best = v;
+      bid = l;
+    }
+  }
+  s_lb[threadIdx.x] = best;
+  s_id[threadIdx.x] = bid;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      const double o = s_lb[threadIdx.x + off];
+      const int oi = s_id[threadIdx.x + off];
+      if (o < s_lb[threadIdx.x] || (o == s_lb[threadIdx.x] && oi < s_id[threadIdx.x])) {
+        s_lb[threadIdx.x] = o;
+        s_id[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) route[q] = s_id[0];
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_prefix(const float* Q, int nq, int mp, int m, double* P, cudaStream_t s) {
+  if (nq <= 0) return;
+  prefix_kernel<<<blocks_for(nq, 64), 64, 0, s>>>(Q, nq, mp, m, P);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double* ivstat,
+                      double* node_lb, double* leaf_lb, int32_t* route, cudaStream_t s) {
+  if (nq <= 0) return;
+  ds_interval_kernel<<<blocks_for((int64_t)nq * T.n_iv, kThreads), kThreads, 0, s>>>(T, P, nq, m,
+                                                                                    ivstat);
+  LF_CHECK_LAUNCH();
+  ds_node_kernel<<<blocks_for((int64_t)nq * T.n_nodes, kThreads), kThreads, 0, s>>>(T, ivstat, nq,
+                                                                                    node_lb);
+  LF_CHECK_LAUNCH();
+  ds_leaf_kernel<<<blocks_for((int64_t)nq * T.n_leaves, kThreads), kThreads, 0, s>>>(
+      T, node_lb, nq, leaf_lb);
+  LF_CHECK_LAUNCH();
+  if (route) {
+    ds_route_kernel<<<blocks_for(nq, 64), 64, 0, s>>>(T, ivstat, nq, route);
+    LF_CHECK_LAUNCH();
+  }
+}
+
+void launch_isax_bounds(const IsaxTables& T, const double* P, int nq, int m, double* paa,
+                        double* leaf_lb, int32_t* route, cudaStream_t s) {
+  if (nq <= 0) return;
+  isax_paa_kernel<<<blocks_for(nq * T.w, kThreads), kThreads, 0, s>>>(T, P, nq, m, paa);
+  LF_CHECK_LAUNCH();
+  isax_leaf_kernel<<<blocks_for((int64_t)nq * T.n_leaves, kThreads), kThreads, 0, s>>>(
+      T, paa, nq, m, leaf_lb);
+  LF_CHECK_LAUNCH();
+  if (route) {
+    isax_route_kernel<<<nq, kThreads, 0, s>>>(T, paa, leaf_lb, nq, route);
+    LF_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace leafi

@@ -1,0 +1,602 @@
+// Leaf search (SearchNode of Alg. 2), candidate merging, and the wave
+// scheduler's select step.
+//
+// A scan round takes (slot, query, leaf) pairs, groups them by leaf and cuts
+// each leaf into work items of (series part) x (group of up to kG queries).
+// One block per item streams the part's series through shared memory in
+// chunks of kRows rows; thread (row, octet) computes the canonical squared
+// distance of its row to kQPT queries:  acc = fmaf(q_i - x_i, q_i - x_i, acc)
+// for i = 0 .. m-1 in order, so every distance equals the oracle's bit for
+// bit and no re-check is needed.  Each query keeps its k best (d^2, id) keys
+// of the part in shared memory (warp-cooperative sorted insertion); the part's
+// list is appended to the slot's candidate buffer and a merge kernel folds all
+// candidates into the slot's running top-k.
+#include <cfloat>
+#include <climits>
+
+#include "internal.h"
+
+namespace leafi {
+namespace {
+
+typedef unsigned long long u64;
+
+constexpr int kRows = 64;                  // series rows per chunk
+constexpr int kQPT = 8;                    // queries per thread
+constexpr int kOct = 2;                    // query octets per block
+constexpr int kG = kQPT * kOct;            // queries per work item
+constexpr int kScanThreads = kRows * kOct; // one thread per (row, octet)
+constexpr int kMergeThreads = 256;
+constexpr int kMergeCap = 2048;
+constexpr double kDeflate = 1.0 - 1e-4;    // LB^2 (1 - 1e-4) > bsf^2 prunes
+
+__device__ __forceinline__ u64 make_key(float d2, uint32_t id) {
+  return ((u64)__float_as_uint(d2) << 32) | (u64)id;
+}
+
+__device__ __forceinline__ float key_d2(u64 k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+// Insert `key` into the ascending list (cnt entries, capacity k <= 128);
+// every lane of the warp calls it with the same arguments.
+__device__ int warp_insert(u64* list, int cnt, int k, u64 key, int lane) {
+  int less = 0;
+  for (int p = lane; p < cnt; p += 32) less += (list[p] < key) ? 1 : 0;
+  const int pos = (int)__reduce_add_sync(0xffffffffu, (unsigned)less);
+  const int newcnt = cnt + 1 < k ? cnt + 1 : k;
+  u64 v[LEAFI_MAX_K / 32];
+#pragma unroll
+  for (int j = 0; j < LEAFI_MAX_K / 32; ++j) {
+    const int p = pos + lane + 32 * j;
+    v[j] = (p < newcnt - 1) ? list[p] : 0ull;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < LEAFI_MAX_K / 32; ++j) {
+    const int p = pos + lane + 32 * j;
+    if (p < newcnt - 1) list[p + 1] = v[j];
+  }
+  if (lane == 0 && pos < k) list[pos] = key;
+  __syncwarp();
+  return newcnt;
+}
+
+__device__ __forceinline__ u64 warp_min_u64(u64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u64 w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a,
+                                                            const int32_t* __restrict__ n_items_dev,
+                                                            const int32_t* __restrict__ slot_k) {
+  extern __shared__ float4 sm4[];
+  const int rs = a.mp + 4;  // padded row stride in floats (16-byte multiple)
+  const int r4 = rs / 4, m4 = a.mp / 4;
+  float4* Xs = sm4;                                                  // [kRows][rs]
+  float4* Qs = Xs + kRows * r4;                                      // [kG][rs]
+  u64* lists = reinterpret_cast<u64*>(Qs + kG * r4);                 // [kG][a.k]
+  u64* stage = lists + kG * a.k;                                     // [kG][kRows]
+  __shared__ int s_cnt[kG], s_nst[kG], s_slot[kG], s_k[kG];
+  __shared__ u64 s_thr[kG];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = kScanThreads / 32;
+  const int n_items = *n_items_dev;
+  const float4* X4 = reinterpret_cast<const float4*>(a.X);
+  const float4* Q4 = reinterpret_cast<const float4*>(a.Q);
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    // leaf of this item: largest l with item_off[l] <= item
+    int lo = 0, hi = a.L - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int leaf = lo;
+    const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
+    const int ngroups = (cnt + kG - 1) / kG;
+    const int local = item - a.item_off[leaf];
+    const int part = local / ngroups, grp = local % ngroups;
+    const int64_t p0 = a.leaf_off[leaf] + (int64_t)part * a.part;
+    const int64_t p1 = min(p0 + (int64_t)a.part, a.leaf_off[leaf + 1]);
+    const int nqg = min(kG, cnt - grp * kG);
+    const Pair* pr = a.pairs + a.grp_off[leaf] + grp * kG;
+    if (tid < kG) {
+      s_cnt[tid] = 0;
+      if (tid < nqg) {
+        const int slot = pr[tid].slot;
+        s_slot[tid] = slot;
+        s_thr[tid] = a.thr[slot];
+        s_k[tid] = slot_k ? slot_k[slot] : a.k;
+      }
+    }
+    for (int idx = tid; idx < nqg * m4; idx += kScanThreads) {
+      const int qq = idx / m4, c = idx % m4;
+      Qs[qq * r4 + c] = Q4[(size_t)pr[qq].q * m4 + c];
+    }
+    const int row = tid % kRows, oct = tid / kRows;
+    for (int64_t c0 = p0; c0 < p1; c0 += kRows) {
+      const int ns = (int)min((int64_t)kRows, p1 - c0);
+      for (int idx = tid; idx < ns * m4; idx += kScanThreads) {
+        const int r = idx / m4, c = idx % m4;
+        Xs[r * r4 + c] = X4[(size_t)(c0 + r) * m4 + c];
+      }
+      if (tid < kG) s_nst[tid] = 0;
+      __syncthreads();
+      if (row < ns && oct * kQPT < nqg) {
+        float acc[kQPT];
+#pragma unroll
+        for (int j = 0; j < kQPT; ++j) acc[j] = 0.0f;
+        const float4* xr = Xs + row * r4;
+        const float4* qb = Qs + oct * kQPT * r4;
+        for (int c = 0; c < m4; ++c) {
+          const float4 x = xr[c];
+#pragma unroll
+          for (int j = 0; j < kQPT; ++j) {
+            const float4 q = qb[j * r4 + c];
+            float t = __fsub_rn(q.x, x.x);
+            acc[j] = __fmaf_rn(t, t, acc[j]);
+            t = __fsub_rn(q.y, x.y);
+            acc[j] = __fmaf_rn(t, t, acc[j]);
+            t = __fsub_rn(q.z, x.z);
+            acc[j] = __fmaf_rn(t, t, acc[j]);
+            t = __fsub_rn(q.w, x.w);
+            acc[j] = __fmaf_rn(t, t, acc[j]);
+          }
+        }
+        const uint32_t id = (uint32_t)a.ids[c0 + row];
+#pragma unroll
+        for (int j = 0; j < kQPT; ++j) {
+          const int q = oct * kQPT + j;
+          if (q < nqg) {
+            const u64 key = make_key(acc[j], id);
+            const int kq = s_k[q];
+            const u64 kth = (s_cnt[q] == kq) ? lists[q * a.k + kq - 1] : s_thr[q];
+            if (key < kth) stage[q * kRows + atomicAdd(&s_nst[q], 1)] = key;
+          }
+        }
+      }
+      __syncthreads();
+      for (int q = warp; q < nqg; q += nwarps) {
+        const int nst = s_nst[q];
+        if (nst == 0) continue;
+        const int kq = s_k[q];
+        u64* list = lists + q * a.k;
+        int c = s_cnt[q];
+        if (kq == 1) {
+          u64 best = kNoKey;
+          for (int e = lane; e < nst; e += 32) {
+            const u64 v = stage[q * kRows + e];
+            best = v < best ? v : best;
+          }
+          best = warp_min_u64(best);
+          const u64 kth = (c == 1) ? list[0] : s_thr[q];
+          if (best < kth) {
+            if (lane == 0) list[0] = best;
+            c = 1;
+          }
+        } else {
+          for (int e = 0; e < nst; ++e) {
+            const u64 key = stage[q * kRows + e];
+            const u64 kth = (c == kq) ? list[kq - 1] : s_thr[q];
+            if (key < kth) c = warp_insert(list, c, kq, key, lane);
+          }
+        }
+        if (lane == 0) s_cnt[q] = c;
+      }
+      __syncthreads();
+    }
+    // append this part's list to the slot's candidates
+    for (int q = warp; q < nqg; q += nwarps) {
+      const int c = s_cnt[q];
+      if (c == 0) continue;
+      const int slot = s_slot[q];
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&a.cand_cnt[slot], c);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base + c > a.cand_cap) {
+        if (lane == 0) atomicOr(a.err, 1);
+        continue;
+      }
+      for (int e = lane; e < c; e += 32) a.cand[(size_t)slot * a.cand_cap + base + e] = lists[q * a.k + e];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- grouping
+__global__ void count_kernel(const Pair* __restrict__ pairs, const int32_t* __restrict__ npairs,
+                             int32_t* __restrict__ cnt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < *npairs) atomicAdd(&cnt[pairs[p].leaf], 1);
+}
+
+// exclusive scans of per-leaf pair counts and work-item counts (one block)
+__global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part,
+                               int32_t* __restrict__ cnt, int32_t* __restrict__ grp_off,
+                               int32_t* __restrict__ item_off, int32_t* __restrict__ n_items,
+                               unsigned long long* __restrict__ stat) {
+  __shared__ int s_a[1024], s_b[1024];
+  const int T = blockDim.x;
+  const int per = (L + T - 1) / T;
+  const int l0 = threadIdx.x * per, l1 = min(L, l0 + per);
+  int sa = 0, sb = 0;
+  unsigned long long distinct = 0;
+  for (int l = l0; l < l1; ++l) {
+    const int c = cnt[l];
+    sa += c;
+    if (c > 0) {
+      const int64_t size = leaf_off[l + 1] - leaf_off[l];
+      const int parts = (int)((size + part - 1) / part);
+      sb += parts * ((c + kG - 1) / kG);
+      distinct += (unsigned long long)size;
+    }
+  }
+  if (stat && distinct) atomicAdd(stat, distinct);
+  s_a[threadIdx.x] = sa;
+  s_b[threadIdx.x] = sb;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the per-thread sums
+  for (int off = 1; off < T; off <<= 1) {
+    const int va = threadIdx.x >= off ? s_a[threadIdx.x - off] : 0;
+    const int vb = threadIdx.x >= off ? s_b[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_a[threadIdx.x] += va;
+    s_b[threadIdx.x] += vb;
+    __syncthreads();
+  }
+  int ra = s_a[threadIdx.x] - sa, rb = s_b[threadIdx.x] - sb;
+  for (int l = l0; l < l1; ++l) {
+    const int c = cnt[l];
+    grp_off[l] = ra;
+    item_off[l] = rb;
+    ra += c;
+    if (c > 0) {
+      const int64_t size = leaf_off[l + 1] - leaf_off[l];
+      const int parts = (int)((size + part - 1) / part);
+      rb += parts * ((c + kG - 1) / kG);
+    }
+    cnt[l] = 0;  // reused as the scatter fill counter
+  }
+  if (threadIdx.x == T - 1) {
+    grp_off[L] = s_a[T - 1];
+    item_off[L] = s_b[T - 1];
+    *n_items = s_b[T - 1];
+  }
+}
+
+__global__ void scatter_kernel(const Pair* __restrict__ pairs, const int32_t* __restrict__ npairs,
+                               const int32_t* __restrict__ grp_off, int32_t* __restrict__ fill,
+                               Pair* __restrict__ grouped) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= *npairs) return;
+  const Pair pr = pairs[p];
+  grouped[grp_off[pr.leaf] + atomicAdd(&fill[pr.leaf], 1)] = pr;
+}
+
+// ---------------------------------------------------------------- merge
+__device__ void bitonic_sort_u64(u64* buf, int n2) {
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (n2 >> 1); i += blockDim.x) {
+        const int pos = 2 * i - (i & (stride - 1));
+        const int partner = pos + stride;
+        const bool asc = (pos & size) == 0;
+        const u64 x = buf[pos], y = buf[partner];
+        if ((x > y) == asc) {
+          buf[pos] = y;
+          buf[partner] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) merge_kernel(
+    int nslots, int kstride, const int32_t* __restrict__ slot_k, u64* __restrict__ topk,
+    int32_t* __restrict__ topk_cnt, u64* __restrict__ thr, const u64* __restrict__ cand,
+    int32_t* __restrict__ cand_cnt, int cap) {
+  __shared__ u64 buf[kMergeCap];
+  for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
+    int cc = cand_cnt[slot];
+    if (cc == 0) continue;
+    if (cc > cap) cc = cap;
+    const int kq = slot_k ? slot_k[slot] : kstride;
+    int tk = topk_cnt[slot];
+    u64* top = topk + (size_t)slot * kstride;
+    int done = 0;
+    while (done < cc) {
+      const int chunk = min(cc - done, kMergeCap - kq);
+      const int n = tk + chunk;
+      int n2 = 2;
+      while (n2 < n) n2 <<= 1;
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        u64 v = kNoKey;
+        if (i < tk) v = top[i];
+        else if (i < n) v = cand[(size_t)slot * cap + done + (i - tk)];
+        buf[i] = v;
+      }
+      __syncthreads();
+      bitonic_sort_u64(buf, n2);
+      tk = min(kq, n);
+      for (int i = threadIdx.x; i < tk; i += blockDim.x) top[i] = buf[i];
+      __syncthreads();
+      done += chunk;
+    }
+    if (threadIdx.x == 0) {
+      topk_cnt[slot] = tk;
+      thr[slot] = (tk == kq) ? top[kq - 1] : kNoKey;
+      cand_cnt[slot] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- select
+// One block per query: the next W leaves of the wave, i.e. the W smallest
+// (LB^2, leaf) keys beyond the query's cursor among leaves that are neither
+// searched, nor pruned by the bound (Alg. 2 line 4), nor by the filter
+// (Alg. 2 line 6) against the best-so-far of the wave's start.
+constexpr int kSelThreads = 128;
+
+__global__ void __launch_bounds__(kSelThreads) select_kernel(SelectArgs a) {
+  const int q = blockIdx.x;
+  if (a.done[q]) return;
+  __shared__ double s_lb[kSelThreads];
+  __shared__ int s_leaf[kSelThreads];
+  const int L = a.L;
+  const u64 thr = a.thr[q];
+  const float bsf2 = (thr == kNoKey) ? __int_as_float(0x7f800000) : key_d2(thr);
+  const double bsf2d = (double)bsf2;
+  const double bsf = (double)__fsqrt_rn(bsf2);
+  const bool filt = a.P != nullptr && a.jpos != nullptr && a.jpos[q] >= 0;
+  const int jp = filt ? a.jpos[q] : 0;
+  double cl = a.cur_lb[q];
+  int cf = a.cur_leaf[q];
+  const double* lb = a.lb2 + (size_t)q * L;
+  unsigned char* sc = a.scanned + (size_t)q * L;
+  int picked = 0;
+  for (int it = 0; it < a.W; ++it) {
+    double best = DBL_MAX;
+    int bl = INT_MAX;
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+      if (sc[l]) continue;
+      const double v = lb[l];
+      if (!(v > cl || (v == cl && l > cf))) continue;
+      if (__dmul_rn(v, kDeflate) > bsf2d) continue;
+      if (filt) {
+        const int f = a.leaf_filter[l];
+        if (f >= 0) {
+          const double df = __dsub_rn((double)a.P[(size_t)q * a.F + f], a.alpha[(size_t)f * a.nc + jp]);
+          if (df > bsf) continue;
+        }
+      }
+      if (v < best || (v == best && l < bl)) {
+        best = v;
+        bl = l;
+      }
+    }
+    s_lb[threadIdx.x] = best;
+    s_leaf[threadIdx.x] = bl;
+    __syncthreads();
+    for (int off = kSelThreads / 2; off > 0; off >>= 1) {
+      if (threadIdx.x < off) {
+        const double o = s_lb[threadIdx.x + off];
+        const int ol = s_leaf[threadIdx.x + off];
+        if (o < s_lb[threadIdx.x] || (o == s_lb[threadIdx.x] && ol < s_leaf[threadIdx.x])) {
+          s_lb[threadIdx.x] = o;
+          s_leaf[threadIdx.x] = ol;
+        }
+      }
+      __syncthreads();
+    }
+    best = s_lb[0];
+    bl = s_leaf[0];
+    __syncthreads();
+    if (bl == INT_MAX) break;
+    if (threadIdx.x == 0) {
+      sc[bl] = 1;
+      const int idx = atomicAdd(a.npairs, 1);
+      a.pairs[idx] = Pair{q, q, bl, 0};
+      atomicAdd(&a.stat[0], 1ull);
+      atomicAdd(&a.stat[1], (u64)(a.leaf_off[bl + 1] - a.leaf_off[bl]));
+    }
+    cl = best;
+    cf = bl;
+    ++picked;
+  }
+  if (threadIdx.x == 0) {
+    a.cur_lb[q] = cl;
+    a.cur_leaf[q] = cf;
+    if (picked < a.W) a.done[q] = 1;
+  }
+}
+
+__global__ void route_pairs_kernel(int nq, const int32_t* __restrict__ route, int L,
+                                   unsigned char* __restrict__ scanned,
+                                   const int64_t* __restrict__ leaf_off, Pair* __restrict__ pairs,
+                                   int32_t* __restrict__ npairs, u64* __restrict__ stat) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) *npairs = nq;
+  if (q >= nq) return;
+  const int leaf = route[q];
+  scanned[(size_t)q * L + leaf] = 1;
+  pairs[q] = Pair{q, q, leaf, 0};
+  atomicAdd(&stat[0], 1ull);
+  atomicAdd(&stat[1], (u64)(leaf_off[leaf + 1] - leaf_off[leaf]));
+}
+
+__global__ void leafknn_pairs_kernel(int nq, int nl, const int32_t* __restrict__ leaves, int L,
+                                     Pair* __restrict__ pairs, int32_t* __restrict__ npairs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nq * nl) return;
+  const int leaf = leaves[t];
+  if (leaf < 0 || leaf >= L) return;
+  pairs[atomicAdd(npairs, 1)] = Pair{t, t / nl, leaf, 0};
+}
+
+__global__ void fill_u64_kernel(u64* p, u64 v, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// sorted position per query (Sec. 4.4.2 with the STEP reading): the query's
+// k picks the smallest calibrated class >= k; the position is the largest j
+// whose calibrated quality qprime[class][j] still meets the target.
+__global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double* __restrict__ target,
+                            int nk, const int32_t* __restrict__ kclasses,
+                            const double* __restrict__ qprime, int nc, int32_t* __restrict__ jpos) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const double t = target[q];
+  int c = -1;
+  for (int i = 0; i < nk; ++i)
+    if (kclasses[i] >= k[q]) {
+      c = i;
+      break;
+    }
+  int j = -1;
+  if (c >= 0 && t < 1.0) {
+    const double* qp = qprime + (size_t)c * nc;
+    for (int i = 0; i < nc; ++i) {
+      if (qp[i] >= t) j = i; else break;
+    }
+  }
+  jpos[q] = j;
+}
+
+__global__ void write_results_kernel(int nq, int kmax, const int32_t* __restrict__ kq,
+                                     const u64* __restrict__ topk, int kstride,
+                                     const int32_t* __restrict__ topk_cnt, int64_t* __restrict__ ids,
+                                     float* __restrict__ dists) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nq * kmax) return;
+  const int q = t / kmax, z = t % kmax;
+  const int lim = min(kq ? kq[q] : kmax, topk_cnt[q]);
+  if (z < lim) {
+    const u64 key = topk[(size_t)q * kstride + z];
+    ids[t] = (int64_t)(uint32_t)(key & 0xffffffffull);
+    dists[t] = __fsqrt_rn(key_d2(key));
+  } else {
+    ids[t] = -1;
+    dists[t] = __int_as_float(0x7f800000);
+  }
+}
+
+__global__ void leafknn_out_kernel(int nslots, int k, const u64* __restrict__ topk,
+                                   const int32_t* __restrict__ topk_cnt, float* __restrict__ d2,
+                                   int64_t* __restrict__ ids) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nslots * k) return;
+  const int s = t / k, z = t % k;
+  if (z < topk_cnt[s]) {
+    const u64 key = topk[t];
+    d2[t] = key_d2(key);
+    ids[t] = (int64_t)(uint32_t)(key & 0xffffffffull);
+  } else {
+    d2[t] = __int_as_float(0x7f800000);
+    ids[t] = -1;
+  }
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+size_t scan_smem_bytes(int mp, int k) {
+  const size_t rs = (size_t)mp + 4;
+  return (kRows + kG) * rs * sizeof(float) + (size_t)kG * k * 8 + (size_t)kG * kRows * 8;
+}
+
+int scan_group_size() { return kG; }
+
+void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k, int grid,
+                 cudaStream_t s) {
+  const size_t smem = scan_smem_bytes(a.mp, a.k);
+  LF_CUDA(cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  scan_kernel<<<grid, kScanThreads, smem, s>>>(a, n_items_dev, slot_k);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
+                  const int64_t* leaf_off, int part, int32_t* cnt, int32_t* grp_off,
+                  int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
+                  unsigned long long* stat, cudaStream_t s) {
+  LF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * L, s));
+  if (npairs_max > 0) {
+    count_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, cnt);
+    LF_CHECK_LAUNCH();
+  }
+  offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, cnt, grp_off, item_off, n_items_dev, stat);
+  LF_CHECK_LAUNCH();
+  if (npairs_max > 0) {
+    scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
+    LF_CHECK_LAUNCH();
+  }
+}
+
+void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
+                  int32_t* topk_cnt, unsigned long long* thr, const unsigned long long* cand,
+                  int32_t* cand_cnt, int cand_cap, cudaStream_t s) {
+  if (nslots <= 0) return;
+  const int grid = nslots < 4096 ? nslots : 4096;
+  merge_kernel<<<grid, kMergeThreads, 0, s>>>(nslots, kstride, slot_k, topk, topk_cnt, thr, cand,
+                                              cand_cnt, cand_cap);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_select(const SelectArgs& a, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  select_kernel<<<a.nq, kSelThreads, 0, s>>>(a);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
+                        const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
+                        unsigned long long* stat, cudaStream_t s) {
+  route_pairs_kernel<<<nblk(nq > 0 ? nq : 1, 128), 128, 0, s>>>(nq, route, L, scanned, leaf_off,
+                                                                 pairs, npairs, stat);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_leafknn_pairs(int nq, int nl, const int32_t* leaves, int L, Pair* pairs,
+                          int32_t* npairs, cudaStream_t s) {
+  LF_CUDA(cudaMemsetAsync(npairs, 0, sizeof(int32_t), s));
+  if (nq * nl == 0) return;
+  leafknn_pairs_kernel<<<nblk((int64_t)nq * nl, 256), 256, 0, s>>>(nq, nl, leaves, L, pairs, npairs);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_t s) {
+  if (!n) return;
+  fill_u64_kernel<<<nblk((int64_t)n, 256), 256, 0, s>>>(p, v, n);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_jpos(int nq, const int32_t* k, const double* target, int nk, const int32_t* kclasses,
+                 const double* qprime, int nc, int32_t* jpos, cudaStream_t s) {
+  if (nq <= 0) return;
+  jpos_kernel<<<nblk(nq, 128), 128, 0, s>>>(nq, k, target, nk, kclasses, qprime, nc, jpos);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_write_results(int nq, int kmax, const int32_t* kq, const unsigned long long* topk,
+                          int kstride, const int32_t* topk_cnt, int64_t* ids, float* dists,
+                          cudaStream_t s) {
+  if (nq * kmax == 0) return;
+  write_results_kernel<<<nblk((int64_t)nq * kmax, 256), 256, 0, s>>>(nq, kmax, kq, topk, kstride,
+                                                                     topk_cnt, ids, dists);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_leafknn_out(int nslots, int k, const unsigned long long* topk, const int32_t* topk_cnt,
+                        float* d2, int64_t* ids, cudaStream_t s) {
+  if (nslots * k == 0) return;
+  leafknn_out_kernel<<<nblk((int64_t)nslots * k, 256), 256, 0, s>>>(nslots, k, topk, topk_cnt, d2,
+                                                                    ids);
+  LF_CHECK_LAUNCH();
+}
+
+}  // namespace leafi

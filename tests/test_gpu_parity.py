@@ -1,0 +1,317 @@
+"""GPU path vs oracle, element by element, on seeded inputs (C-ABI calls).
+
+Bars: exact-mode ids bit-exact with ties on the lowest id, distances bit-exact
+(both sides use the canonical float32 distance); lower bounds and routes
+bit-exact (both sides evaluate the same float64 operations); filter
+predictions within 1e-5 of the float64 forward, scaled by |b2| + sum_j
+|w2_j| relu(z_j); LeaFi-mode results equal except where a filter decision lies
+within the prediction tolerance of the best-so-far.
+"""
+import numpy as np
+import pytest
+
+import fixtures as fx
+import oracle as O
+import paper_2502_01836_b300 as lf
+
+pytestmark = pytest.mark.gpu
+
+N, M, CAP = 20000, 256, 1000     # ~30 leaves, several scan parts, ragged tails
+NQ = 96                          # not a multiple of the 256-query batch
+
+
+@pytest.fixture(scope="module")
+def ds():
+    X = fx.random_walk(N, M, seed=101)
+    Q = fx.test_queries(X, NQ, seed=102)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=CAP, wave=4, device=0))
+    t = O.Tree(X, "dstree", leaf_cap=CAP, init_segments=4)
+    yield X, Q, idx, t
+    lf.leafi_free(idx)
+
+
+def _exact(idx, Q, k):
+    ids = np.zeros((Q.shape[0], k), np.int64)
+    d = np.zeros((Q.shape[0], k), np.float32)
+    st = lf.SearchStats()
+    lf.leafi_exact_search(idx, Q, k, ids, d, st)
+    return ids, d, st
+
+
+def test_tree_matches_oracle(ds):
+    X, Q, idx, t = ds
+    assert np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
+
+
+def test_lower_bounds_and_routes_bit_exact(ds):
+    X, Q, idx, t = ds
+    L = t.L
+    lb = np.zeros((NQ, L), np.float64)
+    lf.leafi_leaf_lower_bounds(idx, Q, lb)
+    assert np.array_equal(lb, t.lb2(Q))
+    r = np.zeros(NQ, np.int32)
+    lf.leafi_route(idx, Q, r)
+    assert np.array_equal(r, t.route(Q))
+
+
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_exact_search_bit_exact(ds, k):
+    X, Q, idx, t = ds
+    ids, d, st = _exact(idx, Q, k)
+    bf_ids, bf_d2 = O.knn(X, Q, k)
+    assert np.array_equal(ids, bf_ids)
+    assert np.array_equal(d, np.sqrt(bf_d2))
+    # the plain index prunes: fewer series than brute force
+    assert st.series_scanned < NQ * N
+    # the schedule matches the oracle's wave search exactly
+    o_ids, o_d2, o_st, _ = O.leafi_search(t, None, None, None, Q, k, -1, 4)
+    assert int(o_st[:, 1].sum()) == st.series_scanned
+    assert int(o_st[:, 0].sum()) == st.leaves_scanned
+
+
+def test_leaf_knn_bit_exact(ds):
+    X, Q, idx, t = ds
+    rng = np.random.default_rng(3)
+    leaves = rng.integers(-1, t.L, size=(NQ, 5)).astype(np.int32)
+    k = 7
+    d2 = np.zeros((NQ, 5, k), np.float32)
+    ids = np.zeros((NQ, 5, k), np.int64)
+    lf.leafi_leaf_knn(idx, Q, leaves, k, d2, ids)
+    od2, oids = t.leaf_topk(Q, leaves, k)
+    assert np.array_equal(ids, oids) and np.array_equal(d2, od2)
+
+
+def _filters(t, F, seed=11):
+    sizes = t.leaf_sizes()
+    fl = np.array(sorted(range(t.L), key=lambda l: (-sizes[l], l))[:F], np.int32)
+    return fl, fx.filter_init(F, M, M, seed=seed)
+
+
+def test_train_targets_bit_exact(ds):
+    X, Q, idx, t = ds
+    fl, W = _filters(t, 8)
+    lf.leafi_set_filters(idx, fl, *W)
+    Ql = np.stack([Q[(f * 7) % NQ:(f * 7) % NQ + 6] for f in range(8)])
+    Tg = np.zeros((NQ, 8), np.float32)
+    Tl = np.zeros((8, 6), np.float32)
+    lf.leafi_train_targets(idx, Q, Ql, Tg, Tl)
+    oTg, oTl = O.train_targets(t, fl, Q, Ql)
+    assert np.array_equal(Tg, oTg) and np.array_equal(Tl, oTl)
+
+
+def _pred_scale(W, Q):
+    W1, b1, w2, b2 = (a.astype(np.float64) for a in W)
+    z = np.einsum("fhm,qm->qfh", W1, Q.astype(np.float64)) + b1[None]
+    return np.abs(b2)[None] + np.einsum("qfh,fh->qf", np.maximum(z, 0), np.abs(w2))
+
+
+def test_filter_predictions_within_tolerance(ds):
+    X, Q, idx, t = ds
+    fl, W = _filters(t, 12, seed=5)
+    lf.leafi_set_filters(idx, fl, *W)
+    P = np.zeros((NQ, 12), np.float32)
+    lf.leafi_filter_predict(idx, Q, P)
+    ref = O.mlp_forward(*W, Q)
+    assert (np.abs(P - ref) <= 1e-5 * _pred_scale(W, Q)).all()
+    back = tuple(np.zeros_like(a) for a in W)
+    lf.leafi_get_filters(idx, *back)
+    for a, b in zip(back, W):
+        assert np.array_equal(a, b)
+
+
+def test_one_epoch_of_sgd_matches_oracle(ds):
+    X, Q, idx, t = ds
+    F = 4
+    fl, W = _filters(t, F, seed=9)
+    lf.leafi_set_filters(idx, fl, *W)
+    members = fx.leaf_members_from(t.leaf_of(), fl)
+    Qg, Ql = fx.training_queries(X, members, 100, 30, seed=77)
+    p = lf.TrainParams(n_gtrain=80, n_gval=20, n_ltrain=24, n_lval=6, batch=16, max_epochs=1,
+                       patience=5)
+    perms = fx.epoch_permutations(1, 104, seed=78)
+    lf.leafi_train_filters(idx, p, Qg, Ql, perms)
+    got = tuple(np.zeros_like(a) for a in W)
+    lf.leafi_get_filters(idx, *got)
+    Tg, Tl = O.train_targets(t, fl, Qg, Ql)
+    op = O.TrainParams(n_gtrain=80, n_gval=20, n_ltrain=24, n_lval=6, batch=16, max_epochs=1,
+                       patience=5)
+    ref, _, _ = O.train(op, Qg, Tg, Ql, Tl, perms, *W)
+    for g, r, w0 in zip(got, ref, W):
+        moved = np.abs(r.astype(np.float64) - w0)
+        assert moved.max() > 0
+        assert np.abs(g.astype(np.float64) - r).max() <= 1e-3 * moved.max() + 1e-6
+
+
+@pytest.fixture(scope="module")
+def tuned(ds):
+    """Oracle-trained filters and oracle auto-tuner tables, installed on the GPU."""
+    X, Q, idx, t = ds
+    F = 10
+    fl, W = _filters(t, F, seed=21)
+    members = fx.leaf_members_from(t.leaf_of(), fl)
+    Qg, Ql = fx.training_queries(X, members, 400, 120, seed=22)
+    p = O.TrainParams(n_gtrain=320, n_gval=80, n_ltrain=96, n_lval=24, batch=32, max_epochs=25,
+                      patience=5)
+    perms = fx.epoch_permutations(25, 416, seed=23)
+    Tg, Tl = O.train_targets(t, fl, Qg, Ql)
+    Wt, _, _ = O.train(p, Qg, Tg, Ql, Tl, perms, *W)
+    Qc = Qg[320:]
+    tables = {k: O.fit_autotuner(t, Wt, fl, Qc, k, 4) for k in (1, 10)}
+    return fl, Wt, Qc, tables
+
+
+def test_autotuner_matches_oracle(ds, tuned):
+    X, Q, idx, t = ds
+    fl, Wt, Qc, tables = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_fit_autotuners(idx, Qc, [1, 10])
+    F, nc = Wt[0].shape[0], Qc.shape[0]
+    alpha = np.zeros((F, nc))
+    qp = np.zeros((2, nc))
+    lf.leafi_get_autotuners(idx, alpha, qp)
+    P = O.mlp_forward(*Wt, Qc)
+    tol = 1e-5 * _pred_scale(Wt, Qc).max()
+    assert np.abs(alpha - tables[1][0]).max() <= tol
+    for i, k in enumerate((1, 10)):
+        diff = np.abs(qp[i] - tables[k][1])
+        # positions where a filter decision sits within the prediction tolerance may differ
+        assert (diff == 0).mean() >= 0.9 and diff.max() <= 3.0 / nc, (k, diff.max())
+
+
+@pytest.mark.parametrize("k,target", [(1, 0.99), (1, 0.9), (10, 0.95)])
+def test_leafi_search_matches_oracle(ds, tuned, k, target):
+    X, Q, idx, t = ds
+    fl, Wt, Qc, tables = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    alpha = tables[1][0]
+    qp = np.stack([tables[1][1], tables[10][1]])
+    lf.leafi_set_autotuners(idx, alpha, qp, [1, 10])
+    ids = np.zeros((NQ, k), np.int64)
+    d = np.zeros((NQ, k), np.float32)
+    st = lf.SearchStats()
+    lf.leafi_search(idx, Q, k, target, ids, d, st)
+    j = O.offset_position(tables[k][1], target)
+    o_ids, o_d2, o_st, margin = O.leafi_search(t, Wt, fl, alpha, Q, k, j, 4)
+    tol = 2e-5 * _pred_scale(Wt, Q).max()
+    same = (ids == o_ids).all(1)
+    assert (same | (margin <= tol)).all()
+    assert same.mean() >= 0.95
+    assert np.array_equal(d[same], np.sqrt(o_d2[same]))
+    if j >= 0:
+        assert st.filter_evals == NQ * len(fl)
+
+
+def test_search_mixed_matches_oracle(ds, tuned):
+    X, Q, idx, t = ds
+    fl, Wt, Qc, tables = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    alpha = tables[1][0]
+    lf.leafi_set_autotuners(idx, alpha, np.stack([tables[1][1], tables[10][1]]), [1, 10])
+    rng = np.random.default_rng(8)
+    kq = rng.choice([1, 5, 10, 20], NQ).astype(np.int32)
+    tg = rng.choice([0.9, 0.95, 0.99, 1.0], NQ).astype(np.float64)
+    ids = np.zeros((NQ, 20), np.int64)
+    d = np.zeros((NQ, 20), np.float32)
+    lf.leafi_search_mixed(idx, Q, kq, tg, 20, ids, d)
+    jpos = np.array([(-1 if (tg[i] >= 1 or kq[i] > 10) else
+                      O.offset_position(tables[1 if kq[i] <= 1 else 10][1], tg[i]))
+                     for i in range(NQ)], np.int32)
+    o_ids, o_d2, _, margin = O.leafi_search(t, Wt, fl, alpha, Q, kq, jpos, 4, kmax=20)
+    tol = 2e-5 * _pred_scale(Wt, Q).max()
+    same = (ids == o_ids).all(1)
+    assert (same | (margin <= tol)).all()
+    # exact queries (target 1 or k above every class) always agree
+    assert same[jpos < 0].all()
+
+
+def test_device_pointers_match_host(ds):
+    torch = pytest.importorskip("torch")
+    X, Q, idx, t = ds
+    ids_h, d_h, _ = _exact(idx, Q, 5)
+    Qd = torch.from_numpy(Q).cuda()
+    ids_d = torch.zeros((NQ, 5), dtype=torch.int64, device="cuda")
+    d_d = torch.zeros((NQ, 5), dtype=torch.float32, device="cuda")
+    lf.leafi_exact_search(idx, Qd, 5, ids_d, d_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(ids_d.cpu().numpy(), ids_h)
+    assert np.array_equal(d_d.cpu().numpy(), d_h)
+
+
+def test_ragged_length_and_padding():
+    X = fx.random_walk(3000, 30, seed=5)   # m = 30 is stored in 32-float rows
+    Q = fx.test_queries(X, 37, seed=6)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=250, dstree_init_segments=3, wave=2))
+    try:
+        ids, d, _ = _exact(idx, Q, 3)
+        bf_ids, bf_d2 = O.knn(X, Q, 3)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_k_larger_than_n_pads():
+    X = fx.random_walk(40, 16, seed=7)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=8, wave=3))
+    try:
+        ids, d, _ = _exact(idx, X[:3], 50)
+        bf_ids, bf_d2 = O.knn(X, X[:3], 50)
+        assert np.array_equal(ids, bf_ids)
+        assert (ids[:, 40:] == -1).all() and np.isinf(d[:, 40:]).all()
+        e_ids = np.zeros((0, 5), np.int64)
+        e_d = np.zeros((0, 5), np.float32)
+        lf.leafi_exact_search(idx, np.zeros((0, 16), np.float32), 5, e_ids, e_d)
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_search_before_tuning_is_refused(ds):
+    X, Q, idx, t = ds
+    fl, W = _filters(t, 3)
+    lf.leafi_set_filters(idx, fl, *W)   # clears the auto-tuners
+    with pytest.raises(lf.LeafiError) as e:
+        lf.leafi_search(idx, Q[:2], 1, 0.99, np.zeros((2, 1), np.int64), np.zeros((2, 1), np.float32))
+    assert e.value.status == 5
+
+
+def test_isax_exact_and_bounds():
+    X = fx.random_walk(20000, 256, seed=31)
+    Q = fx.test_queries(X, 64, seed=32)
+    idx = lf.leafi_build(X, lf.BuildParams(index_type=lf.ISAX, leaf_capacity=400, wave=8))
+    try:
+        t = O.Tree(X, "isax", leaf_cap=400, isax_w=16, isax_bits=8)
+        assert np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
+        lb = np.zeros((64, t.L))
+        lf.leafi_leaf_lower_bounds(idx, Q, lb)
+        assert np.array_equal(lb, t.lb2(Q))
+        r = np.zeros(64, np.int32)
+        lf.leafi_route(idx, Q, r)
+        assert np.array_equal(r, t.route(Q))
+        for k in (1, 10):
+            ids, d, _ = _exact(idx, Q, k)
+            bf_ids, bf_d2 = O.knn(X, Q, k)
+            assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_end_to_end_recall_meets_target():
+    """GPU Alg. 1 (targets, SGD, Alg. 4) then Alg. 2 on held-out queries."""
+    from paper_2502_01836_b300.workflow import enhance
+    X = fx.random_walk(30000, 128, seed=51)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=1500, wave=4))
+    try:
+        p = lf.TrainParams(max_epochs=150, patience=8)
+        enh = enhance(idx, X, 12, p, kclasses=(1,))
+        Qt = fx.test_queries(X, 400, seed=53)
+        bf, _ = O.knn(X, Qt, 1)
+        for target in (0.9, 0.99):
+            ids = np.zeros((400, 1), np.int64)
+            d = np.zeros((400, 1), np.float32)
+            st = lf.SearchStats()
+            lf.leafi_search(idx, Qt, 1, target, ids, d, st)
+            rec = (ids[:, 0] == bf[:, 0]).mean()
+            assert rec >= target - 0.03, (target, rec)
+        e_ids, _, est = _exact(idx, Qt, 1)
+        assert np.array_equal(e_ids, bf)
+    finally:
+        lf.leafi_free(idx)
