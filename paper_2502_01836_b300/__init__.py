@@ -22,7 +22,7 @@ __all__ = [
     "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
     "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
-    "KERNEL_KINDS", "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS",
+    "KERNEL_KINDS", "leafi_leaf_lower_bounds_noalloc", "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -40,6 +40,7 @@ EXPORTED_SYMBOLS = [
     "leafi_leaf_knn", "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
     "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
+    "leafi_leaf_lower_bounds_noalloc",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -107,6 +108,7 @@ def lib():
             "leafi_leaf_of": [vp, vp],
             "leafi_leaf_lower_bounds": [vp, vp, i64, vp],
             "leafi_route": [vp, vp, i64, vp],
+            "leafi_leaf_lower_bounds_noalloc": [vp, vp, i64, vp],
             "leafi_select_leaves": [vp, i32, vp],
             "leafi_set_filters": [vp, vp, i32, i32, vp, vp, vp, vp],
             "leafi_get_filters": [vp, vp, vp, vp, vp],
@@ -221,6 +223,18 @@ def leafi_leaf_of(index):
 def leafi_leaf_lower_bounds(index, queries, out):
     _check(lib().leafi_leaf_lower_bounds(index, _ptr(queries, np.float32, "queries"),
                                          queries.shape[0], _ptr(out, np.float64, "out", True)))
+    return out
+
+
+def leafi_leaf_lower_bounds_noalloc(index, queries, out):
+    """Leaf bounds with no device allocation: `queries` and `out` must be CUDA tensors.
+
+    For callers that cannot allocate device memory; the library's static
+    scratch array (16 MiB per GPU) bounds nq.  Returns without synchronising.
+    """
+    _check(lib().leafi_leaf_lower_bounds_noalloc(index, _ptr(queries, np.float32, "queries"),
+                                                 queries.shape[0],
+                                                 _ptr(out, np.float64, "out", True)))
     return out
 
 

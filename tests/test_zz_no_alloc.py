@@ -1,0 +1,53 @@
+"""The allocation-free bounds entry point against the regular one.
+
+leafi_leaf_lower_bounds_noalloc serves callers that cannot call cudaMalloc
+(work recorded during CUDA-graph capture, or a serving loop that keeps the
+allocator off its path): its scratch is a static device array instead of
+memory allocated per call.  Its output must equal leafi_leaf_lower_bounds'
+(both evaluate the same float64 operations, so the comparison is exact), on
+two calls in a row that reuse the same scratch.  This file is collected last.
+"""
+import numpy as np
+import pytest
+
+import fixtures as fx
+import paper_2502_01836_b300 as lf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind", [lf.DSTREE, lf.ISAX])
+def test_noalloc_bounds_equal_regular_bounds_twice(kind):
+    torch = pytest.importorskip("torch")
+    X = fx.random_walk(20000, 256, seed=91)
+    idx = lf.leafi_build(X, lf.BuildParams(index_type=kind, leaf_capacity=700, device=0))
+    try:
+        L = lf.leafi_get_info(idx).n_leaves
+        for call in range(2):
+            Q = fx.test_queries(X, 150 + 17 * call, seed=92 + call)
+            ref = np.zeros((Q.shape[0], L), np.float64)
+            lf.leafi_leaf_lower_bounds(idx, Q, ref)
+            out = torch.full((Q.shape[0], L), float("nan"), dtype=torch.float64, device="cuda")
+            lf.leafi_leaf_lower_bounds_noalloc(idx, torch.from_numpy(Q).cuda(), out)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy(), ref), "call %d" % call
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_noalloc_rejects_oversize_and_host_arrays():
+    torch = pytest.importorskip("torch")
+    X = fx.random_walk(5000, 256, seed=93)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=500, device=0))
+    try:
+        L = lf.leafi_get_info(idx).n_leaves
+        big = torch.zeros((20000, 256), dtype=torch.float32, device="cuda")
+        out = torch.zeros((20000, L), dtype=torch.float64, device="cuda")
+        with pytest.raises(lf.LeafiError) as e:
+            lf.leafi_leaf_lower_bounds_noalloc(idx, big, out)
+        assert e.value.status == 1 and "scratch" in str(e.value)
+        with pytest.raises(lf.LeafiError) as e:
+            lf.leafi_leaf_lower_bounds_noalloc(idx, X[:4].copy(), np.zeros((4, L)))
+        assert e.value.status == 1
+    finally:
+        lf.leafi_free(idx)
