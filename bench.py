@@ -272,11 +272,13 @@ def main():
         with Clocks(local) as ck:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("timed_leafi" if target < 1.0 else "timed_plain")
             e0.record(stream)
             for _ in range(a.steps):
                 run(target, out_i, out_d, lat, stats)
             e1.record(stream)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
         barrier(dist)
         launches = lf.leafi_launch_count() - launches0
         ms = e0.elapsed_time(e1) / a.steps
