@@ -63,7 +63,11 @@ typedef struct {
   int32_t isax_card_bits;       /* iSAX full cardinality 2^bits (8) */
   int32_t wave;                 /* leaves taken per query per search wave (>= 1); the
                                    auto-tuner calibrates this same schedule */
-  int32_t device;               /* CUDA device ordinal */
+  int32_t device;               /* CUDA device ordinal (-1: host-only tree) */
+  int32_t scan_path;            /* 0: tensor-core scan (float16 dot products on tcgen05
+                                   with a proven error band and a canonical float32
+                                   re-check); 1: CUDA-core scan (canonical float32 for
+                                   every pair).  Both give identical results. */
 } leafi_build_params;
 
 /* Build an index over n series of length m.  Copies `series` into

@@ -164,6 +164,31 @@ __global__ void slots_init_kernel(int nslots, int32_t* topk_cnt, unsigned long l
   cand_cnt[t] = 0;
 }
 
+// float16 copy (rows of kp, zero padded) and squared norms of the series;
+// maxabs receives max |x| (as float bits) to decide whether float16 is safe
+__global__ void half_copy_kernel(const float* __restrict__ X, int64_t n, int mp, int m, int kp,
+                                 __half* __restrict__ Xh, float* __restrict__ xn,
+                                 unsigned int* __restrict__ maxabs) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x / 32);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float ss = 0.0f, mx = 0.0f;
+  for (int i = lane; i < kp; i += 32) {
+    const float v = i < m ? X[row * mp + i] : 0.0f;
+    ss = fmaf(v, v, ss);
+    mx = fmaxf(mx, fabsf(v));
+    Xh[row * kp + i] = __float2half_rn(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    xn[row] = ss;
+    atomicMax(maxabs, __float_as_uint(mx));
+  }
+}
+
 __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int F,
                                  int rows, int cols) {
   // in [F][rows][cols] -> out [F][cols][rows]
@@ -187,8 +212,42 @@ void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_
   int32_t* ioff = ix->sItemOff.need(L + 1);
   Pair* grouped = ix->sGrouped.need(std::max(npairs_max, 1));
   int32_t* nitems = ix->sNItems.need(1);
-  launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart, cnt, goff, ioff, grouped,
-               nitems, distinct_stat, s);
+  const int kstride_smem = kstride;
+  const bool use_tc = ix->tc_ok && ix->scan_path == 0 &&
+                      tc_scan_smem_bytes(ix->kp, kstride_smem) + 4096 <= (size_t)ix->smem_optin;
+  launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
+               use_tc ? tc_group_size() : scan_group_size(), cnt, goff, ioff, grouped, nitems,
+               distinct_stat, s);
+  const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
+  if (use_tc) {
+    TcScanArgs t;
+    t.X = ix->X.p;
+    t.Xh = ix->Xh.p;
+    t.xn = ix->xn.p;
+    t.ids = ix->ids.p;
+    t.leaf_off = ix->leaf_off.p;
+    t.L = L;
+    t.mp = ix->mp;
+    t.kp = ix->kp;
+    t.k = kstride;
+    t.part = kPart;
+    t.Q = dQ;
+    t.pairs = grouped;
+    t.grp_off = goff;
+    t.item_off = ioff;
+    t.thr = thr;
+    t.cand = cand;
+    t.cand_cnt = cand_cnt;
+    t.cand_cap = cap;
+    t.err = ix->sErr.p;
+    ix->tick(0);
+    launch_tc_scan(t, nitems, slot_k, grid, s);
+    ix->tock();
+    ix->tick(1);
+    launch_merge(nslots, kstride, slot_k, topk, topk_cnt, thr, cand, cand_cnt, cap, s);
+    ix->tock();
+    return;
+  }
   ScanArgs a;
   a.X = ix->X.p;
   a.ids = ix->ids.p;
@@ -206,7 +265,6 @@ void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_
   a.cand_cnt = cand_cnt;
   a.cand_cap = cap;
   a.err = ix->sErr.p;
-  const int grid = sm_count(ix->device) * 2;
   ix->tick(0);
   launch_scan(a, nitems, slot_k, grid, s);
   ix->tock();
@@ -221,6 +279,7 @@ void check_err_word(leafi_index* ix) {
   LF_CUDA(cudaStreamSynchronize(ix->stream));
   if (err) {
     LF_CUDA(cudaMemsetAsync(ix->sErr.p, 0, sizeof(int32_t), ix->stream));
+    if (err & 2) fail(LEAFI_ETIMEOUT, "a tensor-core scan wait timed out (error word %d)", err);
     fail(LEAFI_EINTERNAL, "candidate buffer overflow (error word %d)", err);
   }
 }
@@ -497,6 +556,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     if (m < 1 || m > 512) fail(LEAFI_EINVAL, "m must be in [1, 512]");
     if (p->leaf_capacity < 1) fail(LEAFI_EINVAL, "leaf_capacity < 1");
     if (p->wave < 1 || p->wave > calib_max_wave()) fail(LEAFI_EINVAL, "wave must be in [1, %d]", calib_max_wave());
+    if (p->scan_path < 0 || p->scan_path > 1) fail(LEAFI_EINVAL, "scan_path must be 0 or 1");
     if (p->index_type == LEAFI_DSTREE) {
       if (p->dstree_init_segments < 1 || p->dstree_init_segments > m)
         fail(LEAFI_EINVAL, "dstree_init_segments must be in [1, m]");
@@ -584,6 +644,29 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
       ix->node_bits.upload(t.node_bits, s);
       ix->lo_sym.upload(t.leaf_lo_sym, s);
       ix->hi_sym.upload(t.leaf_hi_sym, s);
+    }
+    // float16 copy for the tensor-core scan (rows of kp = m rounded up to 32)
+    ix->scan_path = p->scan_path;
+    ix->kp = (m + 31) / 32 * 32;
+    LF_CUDA(cudaDeviceGetAttribute(&ix->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    if (ix->kp <= 256 && p->scan_path == 0) {
+      __half* Xh = ix->Xh.need((size_t)n * ix->kp);
+      float* xn = ix->xn.need((size_t)n);
+      DBuf<unsigned int> mx;
+      unsigned int zero_u = 0;
+      mx.upload(&zero_u, 1, s);
+      half_copy_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(X, n, ix->mp, m, ix->kp, Xh, xn, mx.p);
+      LF_CHECK_LAUNCH();
+      unsigned int h_mx = 0;
+      LF_CUDA(cudaMemcpyAsync(&h_mx, mx.p, sizeof(h_mx), cudaMemcpyDeviceToHost, s));
+      LF_CUDA(cudaStreamSynchronize(s));
+      float fmx;
+      std::memcpy(&fmx, &h_mx, sizeof(fmx));
+      ix->tc_ok = fmx < 30000.0f;  // float16 represents the data without overflow
+      if (!ix->tc_ok) {
+        ix->Xh.release();
+        ix->xn.release();
+      }
     }
     std::vector<int32_t> lf(t.n_leaves, -1);
     ix->d_leaf_filter.upload(lf, s);

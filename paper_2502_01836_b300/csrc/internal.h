@@ -1,5 +1,6 @@
 // Internal declarations shared by the C-ABI layer and the kernels.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -138,12 +139,36 @@ struct ScanArgs {
 };
 size_t scan_smem_bytes(int mp, int k);
 int scan_group_size();
+
+struct TcScanArgs {
+  const float* X;                  // [n][mp] float32 leaf-major (canonical re-check)
+  const __half* Xh;                // [n][kp] float16 copy (tensor-core operand)
+  const float* xn;                 // [n] |x|^2
+  const int32_t* ids;
+  const int64_t* leaf_off;
+  int L, mp, kp, k;
+  int part;
+  const float* Q;                  // [nq][mp]
+  const Pair* pairs;
+  const int32_t* grp_off;
+  const int32_t* item_off;
+  const unsigned long long* thr;
+  unsigned long long* cand;
+  int32_t* cand_cnt;
+  int cand_cap;
+  int32_t* err;
+};
+int tc_group_size();
+size_t tc_scan_smem_bytes(int kp, int k);
+void launch_tc_scan(const TcScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k,
+                    int grid, cudaStream_t s);
 void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k, int grid,
                  cudaStream_t s);
 
-// stat (nullable): stat[0] += series of the distinct leaves in this round
+// stat (nullable): stat[0] += series of the distinct leaves in this round;
+// g = queries per work item of the scan kernel that follows
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
-                  const int64_t* leaf_off, int part, int32_t* cnt, int32_t* grp_off,
+                  const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s);
 
@@ -226,11 +251,16 @@ struct leafi_index {
   int device = 0;          // -1: host-only index (tree inspection, no device data)
   cudaStream_t stream = nullptr;
   leafi::HostTree tree;
-  int m = 0, mp = 0, wave = 8;
+  int m = 0, mp = 0, wave = 8, scan_path = 0;
   int64_t n = 0;
 
   // resident data
   leafi::DBuf<float> X;          // [n][mp] leaf-major
+  leafi::DBuf<__half> Xh;        // [n][kp] float16 copy for the tensor-core scan
+  leafi::DBuf<float> xn;         // [n] squared norms
+  int kp = 0;                    // float16 row length (multiple of 32)
+  bool tc_ok = false;            // tensor-core scan usable for this index
+  int smem_optin = 0;            // opt-in shared memory per block of the device
   leafi::DBuf<int32_t> ids;      // position -> original id
   leafi::DBuf<int64_t> leaf_off;
   // DSTree tables

@@ -213,7 +213,7 @@ __global__ void count_kernel(const Pair* __restrict__ pairs, const int32_t* __re
 }
 
 // exclusive scans of per-leaf pair counts and work-item counts (one block)
-__global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part,
+__global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part, int g,
                                int32_t* __restrict__ cnt, int32_t* __restrict__ grp_off,
                                int32_t* __restrict__ item_off, int32_t* __restrict__ n_items,
                                unsigned long long* __restrict__ stat) {
@@ -229,7 +229,7 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
     if (c > 0) {
       const int64_t size = leaf_off[l + 1] - leaf_off[l];
       const int parts = (int)((size + part - 1) / part);
-      sb += parts * ((c + kG - 1) / kG);
+      sb += parts * ((c + g - 1) / g);
       distinct += (unsigned long long)size;
     }
   }
@@ -255,7 +255,7 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
     if (c > 0) {
       const int64_t size = leaf_off[l + 1] - leaf_off[l];
       const int parts = (int)((size + part - 1) / part);
-      rb += parts * ((c + kG - 1) / kG);
+      rb += parts * ((c + g - 1) / g);
     }
     cnt[l] = 0;  // reused as the scatter fill counter
   }
@@ -521,7 +521,7 @@ void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* s
 }
 
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
-                  const int64_t* leaf_off, int part, int32_t* cnt, int32_t* grp_off,
+                  const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s) {
   LF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * L, s));
@@ -529,7 +529,8 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
     count_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, cnt);
     LF_CHECK_LAUNCH();
   }
-  offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, cnt, grp_off, item_off, n_items_dev, stat);
+  offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, g, cnt, grp_off, item_off, n_items_dev,
+                                    stat);
   LF_CHECK_LAUNCH();
   if (npairs_max > 0) {
     scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
