@@ -375,6 +375,7 @@ def main():
             "latency_per_launch_ms": {"p50": float(np.percentile(lat_sorted, 50)),
                                       "p99": float(np.percentile(lat_sorted, 99))},
             "series_scanned_per_query": st["series_scanned"] / (a.steps * a.queries),
+            "rechecks_per_query": st["rechecks"] / (a.steps * a.queries),
             "pruning_ratio": 1.0 - st["series_scanned"] / (a.steps * a.queries * a.n),
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
             "waves_per_launch": st["waves"] / max(st["batches"], 1),

@@ -234,6 +234,7 @@ typedef struct {
   int64_t waves;           /* scan rounds, summed over batches */
   int64_t batches;         /* internal query batches (256 queries each) */
   int64_t distinct_series; /* series of the distinct leaves each round read, summed */
+  int64_t rechecks;        /* canonical float32 re-checks by the tensor-core scan */
 } leafi_search_stats;
 
 /* k-NN of nq queries (1 <= k <= LEAFI_MAX_K).  recall_target >= 1 runs the

@@ -199,12 +199,40 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
   out[f * per + c * rows + r] = in[t];
 }
 
+// 2-D TMA descriptor of the float16 copy: dims {kp, n}, row stride kp*2 bytes,
+// box {8 columns, 128 rows} (one 16-byte column slab of a 128-row chunk)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_xh_map(leafi_index* ix) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)ix->kp, (cuuint64_t)ix->n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ix->kp * 2};
+  const cuuint32_t box[2] = {8, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = reinterpret_cast<EncodeTiledFn>(fn)(
+      &ix->xh_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ix->Xh.p, dims, strides, box, estr,
+      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // One scan round: group pairs by leaf, scan, merge candidates into slots.
 void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_t* dNpairs,
                int npairs_max, int nslots, int kstride, const int32_t* slot_k,
                unsigned long long* topk, int32_t* topk_cnt, unsigned long long* thr,
                unsigned long long* cand, int32_t* cand_cnt, int cap,
-               unsigned long long* distinct_stat = nullptr) {
+               unsigned long long* distinct_stat = nullptr,
+               unsigned long long* recheck_stat = nullptr) {
   cudaStream_t s = ix->stream;
   const int L = ix->tree.n_leaves;
   int32_t* cnt = ix->sCnt.need(L);
@@ -240,8 +268,9 @@ void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_
     t.cand_cnt = cand_cnt;
     t.cand_cap = cap;
     t.err = ix->sErr.p;
+    t.stat = recheck_stat;
     ix->tick(0);
-    launch_tc_scan(t, nitems, slot_k, grid, s);
+    launch_tc_scan(ix->xh_map, t, nitems, slot_k, grid, s);
     ix->tock();
     ix->tick(1);
     launch_merge(nslots, kstride, slot_k, topk, topk_cnt, thr, cand, cand_cnt, cap, s);
@@ -380,11 +409,11 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   int32_t* done = ix->sDone.need(qb);
   Pair* pairs = ix->sPairs.need((size_t)qb * std::max(W, 1));
   int32_t* np = ix->sNpairs.need(1);
-  unsigned long long* stat = ix->sStat.need(3);
+  unsigned long long* stat = ix->sStat.need(4);
   int64_t* out_i = ix->sOutI.need((size_t)qb * kmax);
   float* out_d = ix->sOutD.need((size_t)qb * kmax);
   DBuf<float> qtmp;
-  LF_CUDA(cudaMemsetAsync(stat, 0, 3 * sizeof(unsigned long long), s));
+  LF_CUDA(cudaMemsetAsync(stat, 0, 4 * sizeof(unsigned long long), s));
   for (int64_t b0 = 0; b0 < nq; b0 += qb) {
     const int nb = (int)std::min<int64_t>(qb, nq - b0);
     const float* dQ = stage_queries(ix, queries + (size_t)b0 * ix->m, nb, qtmp);
@@ -410,7 +439,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     // wave 0: every query searches its route leaf
     launch_route_pairs(nb, route, L, scanned, ix->leaf_off.p, pairs, np, stat, s);
     run_round(ix, dQ, pairs, np, nb, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
-              stat + 2);
+              stat + 2, stat + 3);
     int waves = 1;
     SelectArgs sa;
     sa.nq = nb;
@@ -443,7 +472,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       if (h_np == 0) break;
       if (++waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
       run_round(ix, dQ, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
-                stat + 2);
+                stat + 2, stat + 3);
     }
     st.waves += waves;
     st.batches += 1;
@@ -452,12 +481,13 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     deliver(ids + (size_t)b0 * kmax, out_i, (size_t)nb * kmax, s);
     deliver(dists + (size_t)b0 * kmax, out_d, (size_t)nb * kmax, s);
   }
-  unsigned long long h_stat[3] = {0, 0, 0};
+  unsigned long long h_stat[4] = {0, 0, 0, 0};
   LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, s));
   LF_CUDA(cudaStreamSynchronize(s));
   st.leaves_scanned = (int64_t)h_stat[0];
   st.series_scanned = (int64_t)h_stat[1];
   st.distinct_series = (int64_t)h_stat[2];
+  st.rechecks = (int64_t)h_stat[3];
   ix->settle();
   if (stats) *stats = st;
 }
@@ -662,7 +692,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
       LF_CUDA(cudaStreamSynchronize(s));
       float fmx;
       std::memcpy(&fmx, &h_mx, sizeof(fmx));
-      ix->tc_ok = fmx < 30000.0f;  // float16 represents the data without overflow
+      ix->tc_ok = fmx < 30000.0f && encode_xh_map(ix.get());  // float16 is safe and TMA is available
       if (!ix->tc_ok) {
         ix->Xh.release();
         ix->xn.release();

@@ -2,6 +2,8 @@
 // insertion, and thin wrappers over the sm_100-family PTX used by the
 // tensor-core scan (shared-memory descriptors, mbarriers, tcgen05).
 #pragma once
+#include <cuda.h>
+
 #include <cstdint>
 
 #include "internal.h"
@@ -162,6 +164,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// arrive on the mbarrier and add `bytes` to its expected transaction count
+__device__ __forceinline__ void mbar_expect_tx(u64* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 2-D tiled TMA load of one box into shared memory, completing on `mbar`
+__device__ __forceinline__ void tma_load_2d(void* dst_smem, const CUtensorMap* tmap, int x, int y,
+                                            u64* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst_smem)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+      : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {

@@ -1,5 +1,6 @@
 // Internal declarations shared by the C-ABI layer and the kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -157,11 +158,12 @@ struct TcScanArgs {
   int32_t* cand_cnt;
   int cand_cap;
   int32_t* err;
+  unsigned long long* stat;        // nullable: [0] += canonical re-checks
 };
 int tc_group_size();
 size_t tc_scan_smem_bytes(int kp, int k);
-void launch_tc_scan(const TcScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k,
-                    int grid, cudaStream_t s);
+void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
+                    const int32_t* slot_k, int grid, cudaStream_t s);
 void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k, int grid,
                  cudaStream_t s);
 
@@ -260,6 +262,7 @@ struct leafi_index {
   leafi::DBuf<float> xn;         // [n] squared norms
   int kp = 0;                    // float16 row length (multiple of 32)
   bool tc_ok = false;            // tensor-core scan usable for this index
+  CUtensorMap xh_map;            // 2-D TMA map of Xh: {kp columns, n rows}, box {8, 128}
   int smem_optin = 0;            // opt-in shared memory per block of the device
   leafi::DBuf<int32_t> ids;      // position -> original id
   leafi::DBuf<int64_t> leaf_off;

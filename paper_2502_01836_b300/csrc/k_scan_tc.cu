@@ -2,11 +2,13 @@
 //
 // A work item is (leaf, part of the leaf, group of up to kTcG queries).  The
 // part's series stream through shared memory in chunks of 128 rows of an
-// fp16 copy of the data (cp.async, double buffered) laid out as K-major core
-// matrices; one thread issues tcgen05.mma (M = 128 series, N = the query group
-// rounded to 16, K = the padded length) into a TMEM accumulator, and the four
-// warps read their 32 TMEM lanes back (one series row per thread) with
-// tcgen05.ld.  The dot products give approximate squared distances
+// fp16 copy of the data: one 2-D TMA per 8-column slab lands each chunk
+// directly in the K-major core-matrix layout the MMA reads (two stages, loads
+// run two chunks ahead); one thread issues tcgen05.mma (M = 128 series, N =
+// the query group rounded to 16, K = the padded length) into one of two TMEM
+// accumulators, so the MMA of chunk c+1 overlaps the epilogue of chunk c, in
+// which the four warps read their 32 TMEM lanes back (one series row per
+// thread) with tcgen05.ld.  The dot products give approximate squared distances
 //     a = |q|^2 + |x|^2 - 2 <q~, x~>
 // whose error against the canonical float32 distance is bounded per pair by
 //     band = 2 (c |q| |x| + 2^-24 sqrt(m) (|q| + |x|)) + 1e-4 (|q|^2 + |x|^2),
@@ -33,9 +35,11 @@ constexpr int kTcG = 64;         // queries per work item (MMA N <= 64)
 constexpr int kTcThreads = 128;  // 4 warps, one TMEM lane quarter each
 constexpr int kTmemCols = 2 * kTcG;
 constexpr long long kWaitLimit = 1ll << 26;
+constexpr int kCandCap = 2048;   // deferred re-check buffer (k = 1 rounds)
 
 struct TcShared {
-  u64 mbar[2];
+  u64 mbar[2];         // MMA of stage s finished
+  u64 full[2];         // TMA of stage s landed
   uint32_t tmem_base;
   int abort;
   u64 thr[kTcG];       // slot's k-th best key at the start of the round
@@ -44,6 +48,8 @@ struct TcShared {
   float qn[kTcG];      // |q|^2 (float32)
   float qnorm[kTcG];   // |q|
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
+  int ncb;             // buffered candidates of the current item
+  unsigned long long rechecks;
 };
 
 __device__ __forceinline__ void atomic_min_float_nonneg(float* p, float v) {
@@ -51,9 +57,9 @@ __device__ __forceinline__ void atomic_min_float_nonneg(float* p, float v) {
   atomicMin(reinterpret_cast<unsigned int*>(p), __float_as_uint(v));
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
-                                                               const int32_t* __restrict__ n_items_dev,
-                                                               const int32_t* __restrict__ slot_k) {
+__global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
+    const __grid_constant__ CUtensorMap tmap, TcScanArgs a, const int32_t* __restrict__ n_items_dev,
+    const int32_t* __restrict__ slot_k) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ TcShared S;
   const int Kp = a.kp;                       // fp16 row length (multiple of 32)
@@ -62,6 +68,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
   unsigned char* A1 = smem + tileA;
   unsigned char* B = smem + 2 * tileA;       // kTcG x Kp fp16
   u64* lists = reinterpret_cast<u64*>(B + kTcG * Kp * 2);  // [kTcG][a.k]
+  // k = 1 rounds defer re-checks: (query, position, lower bound) of each candidate
+  int* cb_pos = reinterpret_cast<int*>(lists + kTcG * a.k);
+  int* cb_j = cb_pos + kCandCap;
+  float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
+  const bool defer = (a.k == 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = Kp / 8;                      // 16-byte pieces per row
   const uint32_t sbo = 16u * Kp;             // bytes between 8-row groups
@@ -70,14 +81,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
   if (tid == 0) {
     dev::mbar_init(&S.mbar[0], 1);
     dev::mbar_init(&S.mbar[1], 1);
+    dev::mbar_init(&S.full[0], 1);
+    dev::mbar_init(&S.full[1], 1);
     S.abort = 0;
+    S.ncb = 0;
+    S.rechecks = 0;
   }
   if (warp == 0) dev::tmem_alloc(&S.tmem_base, kTmemCols);
   dev::tc_fence_before();
   __syncthreads();
   dev::tc_fence_after();
   const uint32_t tmem = S.tmem_base;
-  uint32_t phase0 = 0, phase1 = 0;
+  uint32_t mma_ph[2] = {0u, 0u};   // parity of the next completion to wait for
+  uint32_t full_ph[2] = {0u, 0u};  // (only thread 0 uses full_ph)
   const int n_items = *n_items_dev;
   const float4* Q4 = reinterpret_cast<const float4*>(a.Q);
   const float4* X4 = reinterpret_cast<const float4*>(a.X);
@@ -132,48 +148,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
         if (S.kq[qq] == 1) lists[qq * a.k] = S.thr[qq];
       }
     }
-    // first chunk of the part
-    auto load_chunk = [&](int c, unsigned char* dst) {
-      const int64_t r0 = p0 + (int64_t)c * kTcRows;
-      const int ns = (int)min((int64_t)kTcRows, p1 - r0);
-      const int total = kTcRows * P;
-      for (int idx = tid; idx < total; idx += kTcThreads) {
-        const int ln = idx & 31, w = idx >> 5;
-        const int r = (w / (P / 4)) * 8 + (ln & 7);
-        const int piece = (w % (P / 4)) * 4 + (ln >> 3);
-        if (r < ns)
-          dev::cp_async16(dst + (r / 8) * sbo + piece * 128 + (r % 8) * 16,
-                          a.Xh + (size_t)(r0 + r) * Kp + piece * 8);
-      }
-      dev::cp_async_commit();
+    // A tile of chunk c: slab p (8 columns) of rows r0..r0+127 is one TMA box
+    // landing at p * 2048 bytes, i.e. K-adjacent core matrices 2048 bytes apart
+    // and 8-row groups 128 bytes apart.
+    auto issue_tma = [&](int c, int st) {
+      unsigned char* dst = st ? A1 : A0;
+      const int r0 = (int)(p0 + (int64_t)c * kTcRows);
+      dev::mbar_expect_tx(&S.full[st], (uint32_t)tileA);
+      for (int piece = 0; piece < P; ++piece)
+        dev::tma_load_2d(dst + piece * 2048, &tmap, piece * 8, r0, &S.full[st]);
     };
-    load_chunk(0, A0);
-    dev::cp_async_wait_all();
+    auto issue_mma = [&](int c) {
+      const int st = c & 1;
+      if (!dev::mbar_wait(&S.full[st], full_ph[st], kWaitLimit)) {
+        atomicOr(a.err, 2);
+        S.abort = 1;
+      }
+      full_ph[st] ^= 1u;
+      dev::tc_fence_after();
+      const uint32_t idesc = dev::idesc_f16(kTcRows, N);
+      const uint32_t a_base = dev::smem_addr(st ? A1 : A0), b_base = dev::smem_addr(B);
+      for (int kk = 0; kk < Kp / 16; ++kk)
+        dev::mma_f16(tmem + (uint32_t)(st * kTcG), dev::smem_desc(a_base + kk * 4096, 2048, 128),
+                     dev::smem_desc(b_base + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
+      dev::mma_commit(&S.mbar[st]);
+    };
     dev::fence_async_smem();
     __syncthreads();
+    if (tid == 0) {
+      issue_tma(0, 0);
+      if (nchunks > 1) issue_tma(1, 1);
+      issue_mma(0);
+    }
 
     for (int c = 0; c < nchunks; ++c) {
       const int s = c & 1;
-      unsigned char* As = s ? A1 : A0;
-      if (tid == 0) {
-        dev::tc_fence_after();
-        const uint32_t idesc = dev::idesc_f16(kTcRows, N);
-        const uint32_t a_base = dev::smem_addr(As), b_base = dev::smem_addr(B);
-        for (int kk = 0; kk < Kp / 16; ++kk)
-          dev::mma_f16(tmem + (uint32_t)(s * kTcG), dev::smem_desc(a_base + kk * 256, 128, sbo),
-                       dev::smem_desc(b_base + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
-        dev::mma_commit(&S.mbar[s]);
-      }
-      if (c + 1 < nchunks) load_chunk(c + 1, s ? A0 : A1);
-      const bool ok = dev::mbar_wait(&S.mbar[s], s ? phase1 : phase0, kWaitLimit);
-      if (s) phase1 ^= 1u; else phase0 ^= 1u;
-      if (!ok) {
-        if (tid == 0) atomicOr(a.err, 2);
+      const bool ok = dev::mbar_wait(&S.mbar[s], mma_ph[s], kWaitLimit);
+      mma_ph[s] ^= 1u;
+      if (!ok && tid == 0) {
+        atomicOr(a.err, 2);
         S.abort = 1;
       }
       dev::tc_fence_after();
-      __syncthreads();
-      if (S.abort) break;
+      if (tid == 0 && ok) {
+        if (c + 2 < nchunks) issue_tma(c + 2, s);  // stage s is free: MMA(c) is done
+        if (c + 1 < nchunks) issue_mma(c + 1);     // overlaps this chunk's epilogue
+      }
 
       // ---- epilogue: one series row per thread
       const int64_t r0 = p0 + (int64_t)c * kTcRows;
@@ -233,13 +253,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
               cand = S.wide[j] || !(ap - band > T);
             }
             u64 key = kNoKey;
-            if (cand) {
-              const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
-              key = dev::make_key(e, (uint32_t)a.ids[pos]);
-            }
             if (kq == 1) {
-              if (cand) atomicMin(&lists[j * a.k], key);
+              if (cand) {
+                // defer: the part's final bound usually rejects it without a re-check
+                const int slotc = defer ? atomicAdd(&S.ncb, 1) : kCandCap;
+                if (slotc < kCandCap) {
+                  const float ap = S.qn[j] + xn - 2.0f * d[jj];
+                  const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
+                                     1e-4f * (S.qn[j] + xn);
+                  cb_pos[slotc] = (int)pos;
+                  cb_j[slotc] = j;
+                  cb_lo[slotc] = S.wide[j] ? -1.0f : ap - band;
+                } else {
+                  const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+                  atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
+                  atomicAdd(&S.rechecks, 1ull);
+                }
+              }
             } else {
+              if (cand) {
+                const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+                key = dev::make_key(e, (uint32_t)a.ids[pos]);
+                atomicAdd(&S.rechecks, 1ull);
+              }
               unsigned mask = __ballot_sync(0xffffffffu, cand);
               int cc = S.cnt[j];
               while (mask) {
@@ -257,11 +293,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
         __syncthreads();
       }
       dev::tc_fence_before();
-      dev::cp_async_wait_all();
-      dev::fence_async_smem();
       __syncthreads();
+      if (S.abort) break;
     }
     if (S.abort) break;
+    // deferred re-checks: only candidates whose lower bound still reaches the
+    // part's final bound (round threshold, smallest upper bound, best exact)
+    if (defer) {
+      const int ncb = min(S.ncb, kCandCap);
+      for (int e = tid; e < ncb; e += kTcThreads) {
+        const int j = cb_j[e];
+        const float T = fminf(fminf(S.thrd[j], S.H[j]),
+                              dev::key_d2(*(volatile u64*)&lists[j * a.k]));
+        if (!(cb_lo[e] > T)) {
+          const int64_t pos = cb_pos[e];
+          const float d2 = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+          atomicMin(&lists[j * a.k], dev::make_key(d2, (uint32_t)a.ids[pos]));
+          atomicAdd(&S.rechecks, 1ull);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) S.ncb = 0;
+    }
     // k = 1 lists hold the part's best key if it beat the round's threshold
     if (tid < nqg && S.kq[tid] == 1) S.cnt[tid] = (lists[tid * a.k] < S.thr[tid]) ? 1 : 0;
     __syncthreads();
@@ -281,10 +334,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
     }
     __syncthreads();
   }
-  dev::cp_async_wait_all();
   dev::tc_fence_before();
   __syncthreads();
   dev::tc_fence_after();
+  if (tid == 0 && a.stat && S.rechecks) atomicAdd(a.stat, S.rechecks);
   if (warp == 0) dev::tmem_dealloc(tmem, kTmemCols);
 }
 
@@ -293,14 +346,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(TcScanArgs a,
 int tc_group_size() { return kTcG; }
 
 size_t tc_scan_smem_bytes(int kp, int k) {
-  return (size_t)2 * kTcRows * kp * 2 + (size_t)kTcG * kp * 2 + (size_t)kTcG * k * 8;
+  return (size_t)2 * kTcRows * kp * 2 + (size_t)kTcG * kp * 2 + (size_t)kTcG * k * 8 +
+         (k == 1 ? (size_t)kCandCap * 12 : 0);
 }
 
-void launch_tc_scan(const TcScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k,
-                    int grid, cudaStream_t s) {
+void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
+                    const int32_t* slot_k, int grid, cudaStream_t s) {
   const size_t smem = tc_scan_smem_bytes(a.kp, a.k);
   LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tc_scan_kernel<<<grid, kTcThreads, smem, s>>>(a, n_items_dev, slot_k);
+  tc_scan_kernel<<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
   LF_CHECK_LAUNCH();
 }
 

@@ -69,6 +69,22 @@ def test_exact_search_bit_exact(ds, k):
     assert int(o_st[:, 0].sum()) == st.leaves_scanned
 
 
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("k", [1, 7, 100])
+def test_scan_paths_bit_exact(k, path):
+    """Tensor-core scan (float16 MMA + band + canonical re-check) and CUDA-core scan
+    both return the brute-force answer."""
+    X = fx.random_walk(12000, 96, seed=201)
+    Q = fx.test_queries(X, 70, seed=202)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=700, wave=3, device=0, scan_path=path))
+    try:
+        ids, d, _ = _exact(idx, Q, k)
+        bf_ids, bf_d2 = O.knn(X, Q, k)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+    finally:
+        lf.leafi_free(idx)
+
+
 def test_leaf_knn_bit_exact(ds):
     X, Q, idx, t = ds
     rng = np.random.default_rng(3)
