@@ -200,7 +200,7 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 }
 
 // 2-D TMA descriptor of the float16 copy: dims {kp, n}, row stride kp*2 bytes,
-// box {8 columns, 128 rows} (one 16-byte column slab of a 128-row chunk)
+// box {64 columns, 128 rows} with 128-byte swizzle (one 16 KB block of a chunk)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -217,11 +217,11 @@ bool encode_xh_map(leafi_index* ix) {
   }
   const cuuint64_t dims[2] = {(cuuint64_t)ix->kp, (cuuint64_t)ix->n};
   const cuuint64_t strides[1] = {(cuuint64_t)ix->kp * 2};
-  const cuuint32_t box[2] = {8, 128};
+  const cuuint32_t box[2] = {64, 128};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = reinterpret_cast<EncodeTiledFn>(fn)(
       &ix->xh_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ix->Xh.p, dims, strides, box, estr,
-      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -677,7 +677,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     }
     // float16 copy for the tensor-core scan (rows of kp = m rounded up to 32)
     ix->scan_path = p->scan_path;
-    ix->kp = (m + 31) / 32 * 32;
+    ix->kp = (m + 63) / 64 * 64;
     LF_CUDA(cudaDeviceGetAttribute(&ix->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     if (ix->kp <= 256 && p->scan_path == 0) {
       __half* Xh = ix->Xh.need((size_t)n * ix->kp);

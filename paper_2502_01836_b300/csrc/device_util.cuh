@@ -76,15 +76,19 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// tcgen05 shared-memory matrix descriptor, no swizzle, K-major canonical
-// layout: core matrices of 8 rows x 16 bytes; `lbo` = byte step between
-// K-adjacent core matrices, `sbo` = byte step between 8-row groups.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// tcgen05 shared-memory matrix descriptor of a K-major operand.  No swizzle:
+// core matrices of 8 rows x 16 bytes, `lbo` = byte step between K-adjacent
+// core matrices, `sbo` = byte step between 8-row groups.  128-byte swizzle:
+// rows of 128 bytes (64 fp16) in 8-row atoms of 1024 bytes, `sbo` = 1024.
+// `layout` 0 = no swizzle, 2 = 128-byte swizzle (tile base 1024-byte aligned).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t layout = 0) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version for the tcgen05 family
+  d |= (uint64_t)(layout & 7u) << 61;
   return d;
 }
 

@@ -260,9 +260,9 @@ struct leafi_index {
   leafi::DBuf<float> X;          // [n][mp] leaf-major
   leafi::DBuf<__half> Xh;        // [n][kp] float16 copy for the tensor-core scan
   leafi::DBuf<float> xn;         // [n] squared norms
-  int kp = 0;                    // float16 row length (multiple of 32)
+  int kp = 0;                    // float16 row length (multiple of 64)
   bool tc_ok = false;            // tensor-core scan usable for this index
-  CUtensorMap xh_map;            // 2-D TMA map of Xh: {kp columns, n rows}, box {8, 128}
+  CUtensorMap xh_map;            // 2-D TMA map of Xh: {kp columns, n rows}, box {64, 128}
   int smem_optin = 0;            // opt-in shared memory per block of the device
   leafi::DBuf<int32_t> ids;      // position -> original id
   leafi::DBuf<int64_t> leaf_off;

@@ -2,9 +2,9 @@
 //
 // A work item is (leaf, part of the leaf, group of up to kTcG queries).  The
 // part's series stream through shared memory in chunks of 128 rows of an
-// fp16 copy of the data: one 2-D TMA per 8-column slab lands each chunk
-// directly in the K-major core-matrix layout the MMA reads (two stages, loads
-// run two chunks ahead); one thread issues tcgen05.mma (M = 128 series, N =
+// fp16 copy of the data: one 2-D TMA per 64-column block (128-byte rows,
+// 128-byte swizzle) lands each chunk directly in the K-major layout the MMA
+// reads (two stages, loads run two chunks ahead); one thread issues tcgen05.mma (M = 128 series, N =
 // the query group rounded to 16, K = the padded length) into one of two TMEM
 // accumulators, so the MMA of chunk c+1 overlaps the epilogue of chunk c, in
 // which the four warps read their 32 TMEM lanes back (one series row per
@@ -60,9 +60,12 @@ __device__ __forceinline__ void atomic_min_float_nonneg(float* p, float v) {
 __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     const __grid_constant__ CUtensorMap tmap, TcScanArgs a, const int32_t* __restrict__ n_items_dev,
     const int32_t* __restrict__ slot_k) {
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ TcShared S;
-  const int Kp = a.kp;                       // fp16 row length (multiple of 32)
+  // 128-byte swizzled tiles need 1024-byte aligned bases
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int Kp = a.kp;                       // fp16 row length (multiple of 64)
   const int tileA = kTcRows * Kp * 2;        // bytes per A stage
   unsigned char* A0 = smem;
   unsigned char* A1 = smem + tileA;
@@ -74,7 +77,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
   const bool defer = (a.k == 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int P = Kp / 8;                      // 16-byte pieces per row
   const uint32_t sbo = 16u * Kp;             // bytes between 8-row groups
   const int m4 = a.mp / 4;
 
@@ -148,15 +150,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         if (S.kq[qq] == 1) lists[qq * a.k] = S.thr[qq];
       }
     }
-    // A tile of chunk c: slab p (8 columns) of rows r0..r0+127 is one TMA box
-    // landing at p * 2048 bytes, i.e. K-adjacent core matrices 2048 bytes apart
-    // and 8-row groups 128 bytes apart.
+    // A tile of chunk c: columns [64 kb, 64 kb + 64) of rows r0..r0+127 are one
+    // TMA box (128-byte rows, 128-byte swizzle) landing at kb * 16 KB.
     auto issue_tma = [&](int c, int st) {
       unsigned char* dst = st ? A1 : A0;
       const int r0 = (int)(p0 + (int64_t)c * kTcRows);
       dev::mbar_expect_tx(&S.full[st], (uint32_t)tileA);
-      for (int piece = 0; piece < P; ++piece)
-        dev::tma_load_2d(dst + piece * 2048, &tmap, piece * 8, r0, &S.full[st]);
+      for (int kb = 0; kb < Kp / 64; ++kb)
+        dev::tma_load_2d(dst + kb * 16384, &tmap, kb * 64, r0, &S.full[st]);
     };
     auto issue_mma = [&](int c) {
       const int st = c & 1;
@@ -169,7 +170,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       const uint32_t idesc = dev::idesc_f16(kTcRows, N);
       const uint32_t a_base = dev::smem_addr(st ? A1 : A0), b_base = dev::smem_addr(B);
       for (int kk = 0; kk < Kp / 16; ++kk)
-        dev::mma_f16(tmem + (uint32_t)(st * kTcG), dev::smem_desc(a_base + kk * 4096, 2048, 128),
+        dev::mma_f16(tmem + (uint32_t)(st * kTcG),
+                     dev::smem_desc(a_base + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024, 2),
                      dev::smem_desc(b_base + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
       dev::mma_commit(&S.mbar[st]);
     };
@@ -205,92 +207,133 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       const float cK = 9.7656250e-4f + 2.3841858e-7f + (float)Kp * 1.1920929e-7f;
       const float sm = sqrtf((float)a.mp) * 5.9604645e-8f;
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kTcG);
-      // pass 1 (k = 1 queries): H_j = min over rows of a + band
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float d[16];
-        dev::tmem_ld16(tl + (uint32_t)c0, d);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int j = c0 + jj;
-          if (j < nqg && S.kq[j] == 1) {
-            float hiv = __int_as_float(0x7f800000);
-            if (valid) {
-              const float ap = S.qn[j] + xn - 2.0f * d[jj];
-              const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
-                                 1e-4f * (S.qn[j] + xn);
-              hiv = fmaxf(ap + band, 0.0f);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) hiv = fminf(hiv, __shfl_xor_sync(0xffffffffu, hiv, o));
-            if (lane == 0) atomic_min_float_nonneg(&S.H[j], hiv);
-          }
-        }
-      }
-      __syncthreads();
-      // pass 2: admission, canonical re-check, top-k update
-      for (int turn = 0; turn < 4; ++turn) {
+      if (defer) {
+        // 1-NN round, one pass: the part's smallest upper bound so far (block
+        // running value and this warp's rows) caps the admission bound
         for (int c0 = 0; c0 < N; c0 += 16) {
           float d[16];
           dev::tmem_ld16(tl + (uint32_t)c0, d);
-#pragma unroll 1
+#pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int j = c0 + jj;
-            if (j >= nqg) break;
-            const int kq = S.kq[j];
-            // k = 1 is handled by every warp in turn 0 (atomic min); k > 1 one warp per turn
-            if (kq == 1 ? (turn != 0) : (turn != warp)) continue;
-            bool cand = false;
-            if (valid) {
-              const float ap = S.qn[j] + xn - 2.0f * d[jj];
-              const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
-                                 1e-4f * (S.qn[j] + xn);
-              float T = S.thrd[j];
-              if (kq == 1) {
-                T = fminf(fminf(T, S.H[j]), dev::key_d2(*(volatile u64*)&lists[j * a.k]));
-              } else if (S.cnt[j] == kq) {
-                T = fminf(T, dev::key_d2(lists[j * a.k + kq - 1]));
+            if (j < nqg) {
+              float lov = __int_as_float(0x7f800000), hiv = __int_as_float(0x7f800000);
+              if (valid) {
+                const float ap = S.qn[j] + xn - 2.0f * d[jj];
+                const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
+                                   1e-4f * (S.qn[j] + xn);
+                lov = ap - band;
+                hiv = fmaxf(ap + band, 0.0f);
               }
-              cand = S.wide[j] || !(ap - band > T);
-            }
-            u64 key = kNoKey;
-            if (kq == 1) {
-              if (cand) {
-                // defer: the part's final bound usually rejects it without a re-check
-                const int slotc = defer ? atomicAdd(&S.ncb, 1) : kCandCap;
+              float hw = hiv;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) hw = fminf(hw, __shfl_xor_sync(0xffffffffu, hw, o));
+              const float T = fminf(fminf(S.thrd[j], fminf(S.H[j], hw)),
+                                    dev::key_d2(*(volatile u64*)&lists[j * a.k]));
+              if (valid && (S.wide[j] || !(lov > T))) {
+                const int slotc = atomicAdd(&S.ncb, 1);
                 if (slotc < kCandCap) {
-                  const float ap = S.qn[j] + xn - 2.0f * d[jj];
-                  const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
-                                     1e-4f * (S.qn[j] + xn);
                   cb_pos[slotc] = (int)pos;
                   cb_j[slotc] = j;
-                  cb_lo[slotc] = S.wide[j] ? -1.0f : ap - band;
+                  cb_lo[slotc] = S.wide[j] ? -1.0f : lov;
                 } else {
                   const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
                   atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
                   atomicAdd(&S.rechecks, 1ull);
                 }
               }
-            } else {
-              if (cand) {
-                const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
-                key = dev::make_key(e, (uint32_t)a.ids[pos]);
-                atomicAdd(&S.rechecks, 1ull);
+              if (lane == 0) atomic_min_float_nonneg(&S.H[j], hw);
+            }
+          }
+        }
+      } else {
+        // pass 1 (k = 1 queries): H_j = min over rows of a + band
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float d[16];
+          dev::tmem_ld16(tl + (uint32_t)c0, d);
+  #pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = c0 + jj;
+            if (j < nqg && S.kq[j] == 1) {
+              float hiv = __int_as_float(0x7f800000);
+              if (valid) {
+                const float ap = S.qn[j] + xn - 2.0f * d[jj];
+                const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
+                                   1e-4f * (S.qn[j] + xn);
+                hiv = fmaxf(ap + band, 0.0f);
               }
-              unsigned mask = __ballot_sync(0xffffffffu, cand);
-              int cc = S.cnt[j];
-              while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const u64 kk = __shfl_sync(0xffffffffu, key, src);
-                const u64 kth = (cc == kq) ? lists[j * a.k + kq - 1] : S.thr[j];
-                if (kk < kth) cc = dev::warp_insert(lists + j * a.k, cc, kq, kk, lane);
-              }
-              if (lane == 0) S.cnt[j] = cc;
-              __syncwarp();
+  #pragma unroll
+              for (int o = 16; o > 0; o >>= 1) hiv = fminf(hiv, __shfl_xor_sync(0xffffffffu, hiv, o));
+              if (lane == 0) atomic_min_float_nonneg(&S.H[j], hiv);
             }
           }
         }
         __syncthreads();
+        // pass 2: admission, canonical re-check, top-k update
+        for (int turn = 0; turn < 4; ++turn) {
+          for (int c0 = 0; c0 < N; c0 += 16) {
+            float d[16];
+            dev::tmem_ld16(tl + (uint32_t)c0, d);
+  #pragma unroll 1
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = c0 + jj;
+              if (j >= nqg) break;
+              const int kq = S.kq[j];
+              // k = 1 is handled by every warp in turn 0 (atomic min); k > 1 one warp per turn
+              if (kq == 1 ? (turn != 0) : (turn != warp)) continue;
+              bool cand = false;
+              if (valid) {
+                const float ap = S.qn[j] + xn - 2.0f * d[jj];
+                const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
+                                   1e-4f * (S.qn[j] + xn);
+                float T = S.thrd[j];
+                if (kq == 1) {
+                  T = fminf(fminf(T, S.H[j]), dev::key_d2(*(volatile u64*)&lists[j * a.k]));
+                } else if (S.cnt[j] == kq) {
+                  T = fminf(T, dev::key_d2(lists[j * a.k + kq - 1]));
+                }
+                cand = S.wide[j] || !(ap - band > T);
+              }
+              u64 key = kNoKey;
+              if (kq == 1) {
+                if (cand) {
+                  // defer: the part's final bound usually rejects it without a re-check
+                  const int slotc = defer ? atomicAdd(&S.ncb, 1) : kCandCap;
+                  if (slotc < kCandCap) {
+                    const float ap = S.qn[j] + xn - 2.0f * d[jj];
+                    const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
+                                       1e-4f * (S.qn[j] + xn);
+                    cb_pos[slotc] = (int)pos;
+                    cb_j[slotc] = j;
+                    cb_lo[slotc] = S.wide[j] ? -1.0f : ap - band;
+                  } else {
+                    const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+                    atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
+                    atomicAdd(&S.rechecks, 1ull);
+                  }
+                }
+              } else {
+                if (cand) {
+                  const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+                  key = dev::make_key(e, (uint32_t)a.ids[pos]);
+                  atomicAdd(&S.rechecks, 1ull);
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, cand);
+                int cc = S.cnt[j];
+                while (mask) {
+                  const int src = __ffs(mask) - 1;
+                  mask &= mask - 1;
+                  const u64 kk = __shfl_sync(0xffffffffu, key, src);
+                  const u64 kth = (cc == kq) ? lists[j * a.k + kq - 1] : S.thr[j];
+                  if (kk < kth) cc = dev::warp_insert(lists + j * a.k, cc, kq, kk, lane);
+                }
+                if (lane == 0) S.cnt[j] = cc;
+                __syncwarp();
+              }
+            }
+          }
+          __syncthreads();
+        }
       }
       dev::tc_fence_before();
       __syncthreads();
@@ -346,7 +389,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
 int tc_group_size() { return kTcG; }
 
 size_t tc_scan_smem_bytes(int kp, int k) {
-  return (size_t)2 * kTcRows * kp * 2 + (size_t)kTcG * kp * 2 + (size_t)kTcG * k * 8 +
+  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)kTcG * kp * 2 + (size_t)kTcG * k * 8 +
          (k == 1 ? (size_t)kCandCap * 12 : 0);
 }
 
