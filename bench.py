@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--filters", type=int, default=100)
     ap.add_argument("--leaf-cap", type=int, default=10_000)
     ap.add_argument("--epochs", type=int, default=1000)
-    ap.add_argument("--wave", type=int, default=8)
+    ap.add_argument("--wave", type=int, default=64)
     ap.add_argument("--target", type=float, default=0.99)
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -284,6 +284,8 @@ def main():
         ms = e0.elapsed_time(e1) / a.steps
         kt = lf.leafi_get_kernel_times(idx) if profile else None
         if profile:
+            kt["_phases"] = lf.leafi_get_scan_phases(idx)
+        if profile:
             lf.leafi_set_profiling(idx, False)
         lats = [x.elapsed_time(y) for x, y in lat]
         return ms, lats, stats, launches, ck.summary(), kt
@@ -316,6 +318,7 @@ def main():
     # roofline of the dominant kernel (leaf scan), from per-launch CUDA events
     pk, pk_kind = peaks()
     scan_ms, scan_n = kt["leaf_scan"]
+    phases = kt.get("_phases", {})
     pairs = st["series_scanned"] / a.steps          # (query, series) distances per step
     distinct = st["distinct_series"] / a.steps      # series of distinct leaves per round, per step
     scan_launch_ms = scan_ms / max(scan_n, 1)
@@ -324,7 +327,7 @@ def main():
     achieved_tf = flops_launch / (scan_launch_ms / 1e3) / 1e12
     clk = pk.get("sm_max_mhz", 2032.0)
     alu_peak = SMS * FP32_LANES * clk * 1e6 * 1.5 / 1e12   # FSUB+FFMA issue 3 FLOP per 2 instr
-    bytes_launch = distinct * M * 4 / max(scan_n / a.steps, 1)
+    bytes_launch = distinct * info.scan_row_bytes / max(scan_n / a.steps, 1)
     achieved_gbs = bytes_launch / (scan_launch_ms / 1e3) / 1e9
     hbm = pk.get("hbm_gbs", 6400.0)
     roof_alu = achieved_tf / alu_peak
@@ -337,7 +340,8 @@ def main():
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": roof_hbm, "traffic": None, "peak_source": pk_kind}
-    roofline["kernel"] = "leaf_scan"
+    roofline["kernel"] = "leaf_scan (tensor cores)" if info.tensor_scan else "leaf_scan (CUDA cores)"
+    roofline["bytes_per_series"] = info.scan_row_bytes
     roofline["hbm_view"] = {"achieved_gbs": achieved_gbs, "frac": roof_hbm}
     roofline["alu_view"] = {"achieved_tflops": achieved_tf, "frac": roof_alu}
 
@@ -379,7 +383,9 @@ def main():
             "pruning_ratio": 1.0 - st["series_scanned"] / (a.steps * a.queries * a.n),
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
             "waves_per_launch": st["waves"] / max(st["batches"], 1),
-            "kernel_ms_per_step": {k: v[0] / a.steps for k, v in kt.items() if v[1]},
+            "kernel_ms_per_step": {k: v[0] / a.steps for k, v in kt.items()
+                                   if not k.startswith("_") and v[1]},
+            "scan_phase_cycles_per_block": {k: v / SMS for k, v in kt["_phases"].items()},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
             "build": {"leaves": info.n_leaves, "filters": info.n_filters,

@@ -105,6 +105,8 @@ typedef struct {
   int32_t n_kclasses;
   int32_t kclasses[LEAFI_MAX_KCLASSES];
   int64_t device_bytes;  /* device memory held by the index */
+  int32_t tensor_scan;   /* 1 if leaf scans run on the tensor cores */
+  int32_t scan_row_bytes;/* bytes the leaf scan streams per series (fp16 row or fp32 row) */
 } leafi_index_info;
 
 leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info);
@@ -117,6 +119,12 @@ enum { LEAFI_KERNEL_KINDS = 6 };
 leafi_status leafi_set_profiling(leafi_index* index, int32_t on);
 leafi_status leafi_get_kernel_times(leafi_index* index, double* ms /* [6] */,
                                     int64_t* launches /* [6] */);
+/* Tensor-core scan phase cycles summed over blocks while profiling is on
+ * (16 doubles): 0 query tile, 1 wait for an accumulator, 2 epilogue, 3 flush
+ * and emit (one epilogue thread per block); 4 wait for a free stage, 5 wait
+ * for the query tile, 6 wait for a TMA load, 7 wait for a free accumulator,
+ * 8 issue (the control thread); 9 work items, 10 chunks. */
+leafi_status leafi_get_scan_phases(leafi_index* index, double* cycles);
 /* Series per leaf (host array of n_leaves). Leaves are numbered depth-first,
  * left child first. */
 leafi_status leafi_leaf_sizes(const leafi_index* index, int64_t* sizes);

@@ -22,7 +22,8 @@ __all__ = [
     "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
     "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
-    "KERNEL_KINDS", "leafi_leaf_lower_bounds_noalloc", "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS",
+    "KERNEL_KINDS", "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases", "SCAN_PHASES",
+    "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -40,7 +41,7 @@ EXPORTED_SYMBOLS = [
     "leafi_leaf_knn", "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
     "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
-    "leafi_leaf_lower_bounds_noalloc",
+    "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -59,7 +60,7 @@ class BuildParams(C.Structure):
                 ("scan_path", C.c_int32)]
 
     def __init__(self, index_type=DSTREE, leaf_capacity=10000, dstree_init_segments=4,
-                 isax_segments=16, isax_card_bits=8, wave=8, device=0, scan_path=0):
+                 isax_segments=16, isax_card_bits=8, wave=64, device=0, scan_path=0):
         super().__init__(index_type, leaf_capacity, dstree_init_segments, isax_segments,
                          isax_card_bits, wave, device, scan_path)
 
@@ -69,7 +70,8 @@ class IndexInfo(C.Structure):
                 ("n_leaves", C.c_int32), ("n_nodes", C.c_int32), ("wave", C.c_int32),
                 ("n_filters", C.c_int32), ("filters_trained", C.c_int32),
                 ("n_calib", C.c_int32), ("n_kclasses", C.c_int32),
-                ("kclasses", C.c_int32 * 4), ("device_bytes", C.c_int64)]
+                ("kclasses", C.c_int32 * 4), ("device_bytes", C.c_int64),
+                ("tensor_scan", C.c_int32), ("scan_row_bytes", C.c_int32)]
 
 
 class TrainParams(C.Structure):
@@ -125,6 +127,7 @@ def lib():
             "leafi_search_mixed": [vp, vp, i64, vp, vp, i32, vp, vp, C.POINTER(SearchStats)],
             "leafi_set_profiling": [vp, i32],
             "leafi_get_kernel_times": [vp, vp, vp],
+            "leafi_get_scan_phases": [vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -183,6 +186,17 @@ def leafi_get_kernel_times(index):
     n = np.zeros(6, np.int64)
     _check(lib().leafi_get_kernel_times(index, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+SCAN_PHASES = ["query_tile", "wait_accumulator", "epilogue", "flush_emit", "wait_stage_free",
+               "wait_query_tile", "wait_tma", "wait_accumulator_free", "issue", "items", "chunks"]
+
+
+def leafi_get_scan_phases(index):
+    """Tensor-core scan phase cycle totals recorded while profiling was on."""
+    c = np.zeros(16, np.float64)
+    _check(lib().leafi_get_scan_phases(index, c.ctypes.data))
+    return {k: float(c[i]) for i, k in enumerate(SCAN_PHASES)}
 
 
 def leafi_build(series, params: BuildParams | None = None):

@@ -269,6 +269,7 @@ void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_
     t.cand_cap = cap;
     t.err = ix->sErr.p;
     t.stat = recheck_stat;
+    t.prof = ix->profiling ? ix->scan_prof.p : nullptr;
     ix->tick(0);
     launch_tc_scan(ix->xh_map, t, nitems, slot_k, grid, s);
     ix->tock();
@@ -433,6 +434,14 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       st.filter_evals += (int64_t)nb * ix->F;
     }
     LF_CUDA(cudaMemsetAsync(scanned, 0, (size_t)nb * L, s));
+    // visiting order per query, walked by the wave select (small trees)
+    const bool walk = L <= calib_max_sort();
+    int32_t* ord = walk ? ix->sOrd.need((size_t)nb * L) : nullptr;
+    int32_t* cursor = walk ? ix->sCursor.need(nb) : nullptr;
+    if (walk) {
+      launch_leaf_order(nb, L, lb2, ord, s);
+      LF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nb, s));
+    }
     search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, topk_cnt, thr, cand_cnt, cur_lb,
                                                         cur_leaf, done);
     LF_CHECK_LAUNCH();
@@ -464,7 +473,10 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     for (;;) {
       LF_CUDA(cudaMemsetAsync(np, 0, sizeof(int32_t), s));
       ix->tick(5);
-      launch_select(sa, s);
+      if (walk)
+        launch_select_walk(sa, ord, cursor, s);
+      else
+        launch_select(sa, s);
       ix->tock();
       int32_t h_np = 0;
       LF_CUDA(cudaMemcpyAsync(&h_np, np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -738,6 +750,8 @@ leafi_status leafi_set_profiling(leafi_index* index, int32_t on) {
     DeviceGuard dg(index->device);
     index->settle();
     index->profiling = on != 0;
+    index->scan_prof.need(16);
+    LF_CUDA(cudaMemset(index->scan_prof.p, 0, 16 * sizeof(unsigned long long)));
     for (int i = 0; i < 8; ++i) {
       index->clock.ms[i] = 0.0;
       index->clock.n[i] = 0;
@@ -759,6 +773,19 @@ leafi_status leafi_get_kernel_times(leafi_index* index, double* ms, int64_t* lau
   });
 }
 
+leafi_status leafi_get_scan_phases(leafi_index* index, double* cycles) {
+  return guarded([&] {
+    require_device(index);
+    if (!cycles) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    unsigned long long h[16] = {0};
+    if (index->scan_prof.p)
+      LF_CUDA(cudaMemcpy(h, index->scan_prof.p, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 16; ++i) cycles[i] = (double)h[i];
+  });
+}
+
 leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info) {
   return guarded([&] {
     require_index(index);
@@ -775,7 +802,10 @@ leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info) {
     r.n_calib = index->nc;
     r.n_kclasses = index->nk;
     for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) r.kclasses[i] = index->kclasses[i];
-    r.device_bytes = (int64_t)(index->X.bytes() + index->ids.bytes() + index->W1t.bytes());
+    r.device_bytes = (int64_t)(index->X.bytes() + index->Xh.bytes() + index->xn.bytes() +
+                               index->ids.bytes() + index->W1t.bytes());
+    r.tensor_scan = (index->tc_ok && index->scan_path == 0) ? 1 : 0;
+    r.scan_row_bytes = r.tensor_scan ? index->kp * 2 : index->mp * 4;
     *info = r;
   });
 }

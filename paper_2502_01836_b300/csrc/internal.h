@@ -159,6 +159,7 @@ struct TcScanArgs {
   int cand_cap;
   int32_t* err;
   unsigned long long* stat;        // nullable: [0] += canonical re-checks
+  unsigned long long* prof;        // nullable: per-phase cycle counters (16)
 };
 int tc_group_size();
 size_t tc_scan_smem_bytes(int kp, int k);
@@ -208,6 +209,8 @@ struct KernelClock {
   long long n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 void launch_select(const SelectArgs& a, cudaStream_t s);
+// the same selection walking a precomputed visiting order (`ord`, cursor = position)
+void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s);
 void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
                         const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
                         unsigned long long* stat, cudaStream_t s);
@@ -241,6 +244,8 @@ struct CalibArgs {
   int kk;                         // min(kc, n)
 };
 int calib_max_sort();
+// per query: leaves sorted by ascending (LB^2, leaf id), ord [nq][L] (L <= calib_max_sort())
+void launch_leaf_order(int nq, int L, const double* lb2, int32_t* ord, cudaStream_t s);
 int calib_max_wave();
 void launch_calib_alpha(const CalibArgs& a, cudaStream_t s);
 void launch_calib_sim(const CalibArgs& a, cudaStream_t s);
@@ -291,7 +296,7 @@ struct leafi_index {
   leafi::DBuf<float> sQ;
   leafi::DBuf<double> sP, sIv, sNode, sLb, sPaa, sTarget;
   leafi::DBuf<int32_t> sRoute, sK, sJpos, sCnt, sGrpOff, sItemOff, sNpairs, sCandCnt, sTopkCnt,
-      sDone, sCurLeaf, sErr, sLeaves, sNItems;
+      sDone, sCurLeaf, sErr, sLeaves, sNItems, sOrd, sCursor;
   leafi::DBuf<double> sCurLb;
   leafi::DBuf<unsigned char> sScanned;
   leafi::DBuf<leafi::Pair> sPairs, sGrouped;
@@ -300,6 +305,7 @@ struct leafi_index {
   leafi::DBuf<int64_t> sOutI;
 
   bool profiling = false;
+  leafi::DBuf<unsigned long long> scan_prof;  // tensor-core scan phase cycles (profiling)
   leafi::KernelClock clock;
   void tick(int kind);   // record a start event of `kind` on the stream
   void tock();           // record the matching stop event

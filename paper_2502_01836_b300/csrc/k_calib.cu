@@ -213,6 +213,15 @@ __global__ void qprime_kernel(int nc, int kk, const long long* __restrict__ hits
 }  // namespace
 
 int calib_max_sort() { return kMaxSortN; }
+
+void launch_leaf_order(int nq, int L, const double* lb2, int32_t* ord, cudaStream_t s) {
+  if (nq <= 0) return;
+  if (L > kMaxSortN) fail(LEAFI_EINVAL, "visiting order supports at most %d leaves", kMaxSortN);
+  const size_t smem = kMaxSortN * (sizeof(double) + sizeof(int));
+  LF_CUDA(cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  order_kernel<<<nq, 256, smem, s>>>(L, lb2, ord);
+  LF_CHECK_LAUNCH();
+}
 int calib_max_wave() { return kMaxWave; }
 
 void launch_calib_alpha(const CalibArgs& a, cudaStream_t s) {

@@ -414,6 +414,99 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(SelectArgs a) {
   }
 }
 
+// Walk of the precomputed visiting order from the query's cursor: the next W
+// positions that are neither searched nor filter-pruned, stopping at the first
+// bound-pruned leaf (the order ascends in LB^2, so every later leaf is pruned
+// too).  Equivalent to select_kernel; one block of 128 threads per query
+// examines 128 positions per step with a block-wide prefix count.
+__global__ void __launch_bounds__(kSelThreads) select_walk_kernel(SelectArgs a,
+                                                                 const int32_t* __restrict__ ord,
+                                                                 int32_t* __restrict__ cursor) {
+  const int q = blockIdx.x;
+  if (a.done[q]) return;
+  __shared__ int s_warp[kSelThreads / 32];
+  __shared__ int s_stop, s_newcur;
+  const int L = a.L;
+  const u64 thr = a.thr[q];
+  const float bsf2 = (thr == kNoKey) ? __int_as_float(0x7f800000) : key_d2(thr);
+  const double bsf2d = (double)bsf2;
+  const double bsf = (double)__fsqrt_rn(bsf2);
+  const bool filt = a.P != nullptr && a.jpos != nullptr && a.jpos[q] >= 0;
+  const int jp = filt ? a.jpos[q] : 0;
+  const double* lb = a.lb2 + (size_t)q * L;
+  const int32_t* od = ord + (size_t)q * L;
+  unsigned char* sc = a.scanned + (size_t)q * L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int pos0 = cursor[q];
+  int picked = 0;
+  bool finished = false;  // reached the end or a bound-pruned leaf
+  while (pos0 < L && picked < a.W) {
+    const int p = pos0 + (int)threadIdx.x;
+    int leaf = -1, elig = 0, stop = 0;
+    if (p < L) {
+      leaf = od[p];
+      if (__dmul_rn(lb[leaf], kDeflate) > bsf2d) {
+        stop = 1;
+      } else if (!sc[leaf]) {
+        elig = 1;
+        if (filt) {
+          const int f = a.leaf_filter[leaf];
+          if (f >= 0) {
+            const double df =
+                __dsub_rn((double)a.P[(size_t)q * a.F + f], a.alpha[(size_t)f * a.nc + jp]);
+            if (df > bsf) elig = 0;
+          }
+        }
+      }
+    }
+    if (threadIdx.x == 0) s_stop = INT_MAX;
+    __syncthreads();
+    if (stop) atomicMin(&s_stop, p);
+    __syncthreads();
+    const int first_stop = s_stop;
+    if (p >= first_stop) elig = 0;
+    // block exclusive prefix count of eligible positions
+    const unsigned bal = __ballot_sync(0xffffffffu, elig);
+    const int in_warp = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+      if (w < warp) before += s_warp[w];
+      total += s_warp[w];
+    }
+    const int rank = picked + before + in_warp;
+    if (threadIdx.x == 0) s_newcur = -1;
+    __syncthreads();
+    if (elig && rank < a.W) {
+      sc[leaf] = 1;
+      const int idx = atomicAdd(a.npairs, 1);
+      a.pairs[idx] = Pair{q, q, leaf, 0};
+      atomicAdd(&a.stat[0], 1ull);
+      atomicAdd(&a.stat[1], (u64)(a.leaf_off[leaf + 1] - a.leaf_off[leaf]));
+      if (rank == a.W - 1) s_newcur = p + 1;
+    }
+    __syncthreads();
+    if (picked + total >= a.W) {
+      pos0 = s_newcur;
+      picked = a.W;
+      break;
+    }
+    picked += total;
+    if (first_stop != INT_MAX || pos0 + kSelThreads >= L) {
+      finished = true;
+      pos0 = L;
+      break;
+    }
+    pos0 += kSelThreads;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    cursor[q] = (finished || pos0 >= L) ? L : pos0;
+    if (picked < a.W) a.done[q] = 1;
+  }
+}
+
 __global__ void route_pairs_kernel(int nq, const int32_t* __restrict__ route, int L,
                                    unsigned char* __restrict__ scanned,
                                    const int64_t* __restrict__ leaf_off, Pair* __restrict__ pairs,
@@ -551,6 +644,12 @@ void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long 
 void launch_select(const SelectArgs& a, cudaStream_t s) {
   if (a.nq <= 0) return;
   select_kernel<<<a.nq, kSelThreads, 0, s>>>(a);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s) {
+  if (a.nq <= 0) return;
+  select_walk_kernel<<<a.nq, kSelThreads, 0, s>>>(a, ord, cursor);
   LF_CHECK_LAUNCH();
 }
 

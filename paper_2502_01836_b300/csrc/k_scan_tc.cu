@@ -30,31 +30,93 @@ namespace {
 
 using dev::u64;
 
-constexpr int kTcRows = 128;     // MMA M: series per chunk
-constexpr int kTcG = 64;         // queries per work item (MMA N <= 64)
-constexpr int kTcThreads = 128;  // 4 warps, one TMEM lane quarter each
+constexpr int kTcRows = 128;      // MMA M: series per chunk
+constexpr int kTcG = 64;          // queries per work item (MMA N <= 64)
+constexpr int kEpi = 256;         // epilogue threads: warps 0-7, two per TMEM lane quarter
+constexpr int kEpiWarps = kEpi / 32;
+constexpr int kLoadWarp = kEpiWarps;      // lane 0 issues the TMA loads
+constexpr int kMmaWarp = kEpiWarps + 1;   // lane 0 issues the MMAs
+constexpr int kTcThreads = kEpi + 64;
 constexpr int kTmemCols = 2 * kTcG;
 constexpr long long kWaitLimit = 1ll << 26;
-constexpr int kCandCap = 2048;   // deferred re-check buffer (k = 1 rounds)
+constexpr int kCandCap = 2048;    // deferred re-check buffer (k = 1 rounds)
 
 struct TcShared {
-  u64 mbar[2];         // MMA of stage s finished
-  u64 full[2];         // TMA of stage s landed
+  u64 full[2];    // TMA of stage s landed (1 arrival + bytes)
+  u64 empty[2];   // MMAs reading stage s finished (tcgen05.commit)
+  u64 tfull[2];   // accumulator t written (tcgen05.commit)
+  u64 tempty[2];  // accumulator t read back by the epilogue threads
+  u64 bready;     // the item's query tile is in shared memory (kEpi arrivals)
   uint32_t tmem_base;
   int abort;
+  int stop;            // epilogue warps' uniform snapshot of `abort`
   u64 thr[kTcG];       // slot's k-th best key at the start of the round
   float thrd[kTcG];    // its squared distance (inf if fewer than k)
   float H[kTcG];       // k = 1: smallest upper bound a + band in the part
-  float qn[kTcG];      // |q|^2 (float32)
-  float qnorm[kTcG];   // |q|
+  float4 qc[kTcG];     // per query: |q|^2, |q|, k-th best d^2 (inf if none), wide flag
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
   int ncb;             // buffered candidates of the current item
   unsigned long long rechecks;
 };
 
+// optional per-phase cycle counters (TcScanArgs::prof, 16 entries):
+// epilogue warp 0 lane 0: 0 query tile, 1 wait accumulator, 2 epilogue, 3 flush+emit;
+// MMA thread: 5 wait query tile, 6 wait TMA, 7 wait accumulator free, 8 MMA issue;
+// load thread: 4 wait stage free, 11 TMA issue; 9 items, 10 chunks
+#define PROF_T0() long long _pt = clock64()
+#define PROF_ADD(i)                                              \
+  do {                                                           \
+    const long long _nw = clock64();                             \
+    if (prof_on) pr[i] += (unsigned long long)(_nw - _pt);       \
+    _pt = _nw;                                                   \
+  } while (0)
+
+struct Item {
+  int64_t p0, p1;
+  int nqg, N, nchunks;
+  const Pair* pr;
+};
+
+__device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
+  int lo = 0, hi = a.L - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  const int leaf = lo;
+  const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
+  const int ngroups = (cnt + kTcG - 1) / kTcG;
+  const int local = item - a.item_off[leaf];
+  const int part = local / ngroups, grp = local % ngroups;
+  Item it;
+  it.p0 = a.leaf_off[leaf] + (int64_t)part * a.part;
+  it.p1 = min(it.p0 + (int64_t)a.part, a.leaf_off[leaf + 1]);
+  it.nqg = min(kTcG, cnt - grp * kTcG);
+  it.N = ((it.nqg + 15) / 16) * 16;
+  it.pr = a.pairs + a.grp_off[leaf] + grp * kTcG;
+  it.nchunks = (int)((it.p1 - it.p0 + kTcRows - 1) / kTcRows);
+  return it;
+}
+
 __device__ __forceinline__ void atomic_min_float_nonneg(float* p, float v) {
   // non-negative floats order like their bit patterns
   atomicMin(reinterpret_cast<unsigned int*>(p), __float_as_uint(v));
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(u64* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(dev::smem_addr(mbar)) : "memory");
+}
+
+// bounded wait that also gives up once another role has aborted
+__device__ __forceinline__ bool wait_phase(u64* mbar, uint32_t parity, volatile int* abort) {
+  if (*abort) return false;
+  for (int round = 0; round < 64; ++round) {
+    if (dev::mbar_wait(mbar, parity, kWaitLimit >> 6)) return true;
+    if (*abort) return false;
+  }
+  return false;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
@@ -69,23 +131,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   const int tileA = kTcRows * Kp * 2;        // bytes per A stage
   unsigned char* A0 = smem;
   unsigned char* A1 = smem + tileA;
-  unsigned char* B = smem + 2 * tileA;       // kTcG x Kp fp16
+  unsigned char* B = smem + 2 * tileA;       // kTcG x Kp fp16, no swizzle
   u64* lists = reinterpret_cast<u64*>(B + kTcG * Kp * 2);  // [kTcG][a.k]
-  // k = 1 rounds defer re-checks: (query, position, lower bound) of each candidate
   int* cb_pos = reinterpret_cast<int*>(lists + kTcG * a.k);
   int* cb_j = cb_pos + kCandCap;
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
   const bool defer = (a.k == 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t sbo = 16u * Kp;             // bytes between 8-row groups
+  const uint32_t sbo = 16u * Kp;             // B: bytes between 8-row groups
   const int m4 = a.mp / 4;
+  volatile int* abort = &S.abort;
 
   if (tid == 0) {
-    dev::mbar_init(&S.mbar[0], 1);
-    dev::mbar_init(&S.mbar[1], 1);
-    dev::mbar_init(&S.full[0], 1);
-    dev::mbar_init(&S.full[1], 1);
+    for (int i = 0; i < 2; ++i) {
+      dev::mbar_init(&S.full[i], 1);
+      dev::mbar_init(&S.empty[i], 1);
+      dev::mbar_init(&S.tfull[i], 1);
+      dev::mbar_init(&S.tempty[i], kEpi);
+    }
+    dev::mbar_init(&S.bready, kEpi);
     S.abort = 0;
+    S.stop = 0;
     S.ncb = 0;
     S.rechecks = 0;
   }
@@ -94,289 +160,315 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   __syncthreads();
   dev::tc_fence_after();
   const uint32_t tmem = S.tmem_base;
-  uint32_t mma_ph[2] = {0u, 0u};   // parity of the next completion to wait for
-  uint32_t full_ph[2] = {0u, 0u};  // (only thread 0 uses full_ph)
   const int n_items = *n_items_dev;
-  const float4* Q4 = reinterpret_cast<const float4*>(a.Q);
-  const float4* X4 = reinterpret_cast<const float4*>(a.X);
+  unsigned long long pr[16];
+  for (int i = 0; i < 16; ++i) pr[i] = 0;
+  const bool prof_on = a.prof != nullptr && (tid == 0 || tid == kLoadWarp * 32 || tid == kMmaWarp * 32);
 
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    int lo = 0, hi = a.L - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    const int leaf = lo;
-    const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
-    const int ngroups = (cnt + kTcG - 1) / kTcG;
-    const int local = item - a.item_off[leaf];
-    const int part = local / ngroups, grp = local % ngroups;
-    const int64_t p0 = a.leaf_off[leaf] + (int64_t)part * a.part;
-    const int64_t p1 = min(p0 + (int64_t)a.part, a.leaf_off[leaf + 1]);
-    const int nqg = min(kTcG, cnt - grp * kTcG);
-    const int N = ((nqg + 15) / 16) * 16;
-    const Pair* pr = a.pairs + a.grp_off[leaf] + grp * kTcG;
-    const int nchunks = (int)((p1 - p0 + kTcRows - 1) / kTcRows);
-
-    // queries of the group: fp16 into the B tile (K-major core matrices), norms
-    for (int qq = warp; qq < N; qq += kTcThreads / 32) {
-      const int qrow = qq < nqg ? pr[qq].q : -1;
-      float ss = 0.0f, mx = 0.0f;
-      for (int i = lane; i < Kp; i += 32) {
-        float v = 0.0f;
-        if (qrow >= 0 && i < a.mp) v = a.Q[(size_t)qrow * a.mp + i];
-        ss = fmaf(v, v, ss);
-        mx = fmaxf(mx, fabsf(v));
-        *reinterpret_cast<__half*>(B + (qq / 8) * sbo + (i / 8) * 128 + (qq % 8) * 16 + (i % 8) * 2) =
-            __float2half_rn(v);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      }
-      if (lane == 0 && qq < nqg) {
-        const int slot = pr[qq].slot;
-        S.slot[qq] = slot;
-        S.qrow[qq] = qrow;
-        S.kq[qq] = slot_k ? slot_k[slot] : a.k;
-        S.thr[qq] = a.thr[slot];
-        S.thrd[qq] = (a.thr[slot] == kNoKey) ? __int_as_float(0x7f800000) : dev::key_d2(a.thr[slot]);
-        S.H[qq] = __int_as_float(0x7f800000);
-        S.qn[qq] = ss;
-        S.qnorm[qq] = sqrtf(ss);
-        S.cnt[qq] = 0;
-        S.wide[qq] = (mx >= 30000.0f) ? 1 : 0;  // outside the safe fp16 range: re-check all
-        if (S.kq[qq] == 1) lists[qq * a.k] = S.thr[qq];
-      }
-    }
-    // A tile of chunk c: columns [64 kb, 64 kb + 64) of rows r0..r0+127 are one
-    // TMA box (128-byte rows, 128-byte swizzle) landing at kb * 16 KB.
-    auto issue_tma = [&](int c, int st) {
-      unsigned char* dst = st ? A1 : A0;
-      const int r0 = (int)(p0 + (int64_t)c * kTcRows);
-      dev::mbar_expect_tx(&S.full[st], (uint32_t)tileA);
-      for (int kb = 0; kb < Kp / 64; ++kb)
-        dev::tma_load_2d(dst + kb * 16384, &tmap, kb * 64, r0, &S.full[st]);
-    };
-    auto issue_mma = [&](int c) {
-      const int st = c & 1;
-      if (!dev::mbar_wait(&S.full[st], full_ph[st], kWaitLimit)) {
-        atomicOr(a.err, 2);
-        S.abort = 1;
-      }
-      full_ph[st] ^= 1u;
-      dev::tc_fence_after();
-      const uint32_t idesc = dev::idesc_f16(kTcRows, N);
-      const uint32_t a_base = dev::smem_addr(st ? A1 : A0), b_base = dev::smem_addr(B);
-      for (int kk = 0; kk < Kp / 16; ++kk)
-        dev::mma_f16(tmem + (uint32_t)(st * kTcG),
-                     dev::smem_desc(a_base + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024, 2),
-                     dev::smem_desc(b_base + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
-      dev::mma_commit(&S.mbar[st]);
-    };
-    dev::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      issue_tma(0, 0);
-      if (nchunks > 1) issue_tma(1, 1);
-      issue_mma(0);
-    }
-
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c & 1;
-      const bool ok = dev::mbar_wait(&S.mbar[s], mma_ph[s], kWaitLimit);
-      mma_ph[s] ^= 1u;
-      if (!ok && tid == 0) {
-        atomicOr(a.err, 2);
-        S.abort = 1;
-      }
-      dev::tc_fence_after();
-      if (tid == 0 && ok) {
-        if (c + 2 < nchunks) issue_tma(c + 2, s);  // stage s is free: MMA(c) is done
-        if (c + 1 < nchunks) issue_mma(c + 1);     // overlaps this chunk's epilogue
-      }
-
-      // ---- epilogue: one series row per thread
-      const int64_t r0 = p0 + (int64_t)c * kTcRows;
-      const int r = warp * 32 + lane;
-      const bool valid = r0 + r < p1;
-      const int64_t pos = r0 + r;
-      const float xn = valid ? a.xn[pos] : 0.0f;
-      const float xnorm = sqrtf(xn);
-      const float cK = 9.7656250e-4f + 2.3841858e-7f + (float)Kp * 1.1920929e-7f;
-      const float sm = sqrtf((float)a.mp) * 5.9604645e-8f;
-      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kTcG);
-      if (defer) {
-        // 1-NN round, one pass: the part's smallest upper bound so far (block
-        // running value and this warp's rows) caps the admission bound
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          float d[16];
-          dev::tmem_ld16(tl + (uint32_t)c0, d);
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = c0 + jj;
-            if (j < nqg) {
-              float lov = __int_as_float(0x7f800000), hiv = __int_as_float(0x7f800000);
-              if (valid) {
-                const float ap = S.qn[j] + xn - 2.0f * d[jj];
-                const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
-                                   1e-4f * (S.qn[j] + xn);
-                lov = ap - band;
-                hiv = fmaxf(ap + band, 0.0f);
-              }
-              float hw = hiv;
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) hw = fminf(hw, __shfl_xor_sync(0xffffffffu, hw, o));
-              const float T = fminf(fminf(S.thrd[j], fminf(S.H[j], hw)),
-                                    dev::key_d2(*(volatile u64*)&lists[j * a.k]));
-              if (valid && (S.wide[j] || !(lov > T))) {
-                const int slotc = atomicAdd(&S.ncb, 1);
-                if (slotc < kCandCap) {
-                  cb_pos[slotc] = (int)pos;
-                  cb_j[slotc] = j;
-                  cb_lo[slotc] = S.wide[j] ? -1.0f : lov;
-                } else {
-                  const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
-                  atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
-                  atomicAdd(&S.rechecks, 1ull);
-                }
-              }
-              if (lane == 0) atomic_min_float_nonneg(&S.H[j], hw);
-            }
+  if (warp == kLoadWarp) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      PROF_T0();
+      long long g_ld = 0;
+      uint32_t empty_ph[2] = {0u, 0u};
+      for (int item = blockIdx.x; item < n_items && !*abort; item += gridDim.x) {
+        const Item I = decode_item(a, item);
+        for (int c = 0; c < I.nchunks; ++c) {
+          const int st = (int)(g_ld & 1);
+          if (g_ld >= 2) {
+            PROF_ADD(11);
+            const bool ok = wait_phase(&S.empty[st], empty_ph[st], abort);
+            empty_ph[st] ^= 1u;
+            PROF_ADD(4);
+            if (!ok) break;
           }
+          unsigned char* dst = st ? A1 : A0;
+          const int r0 = (int)(I.p0 + (int64_t)c * kTcRows);
+          dev::mbar_expect_tx(&S.full[st], (uint32_t)tileA);
+          for (int kb = 0; kb < Kp / 64; ++kb)
+            dev::tma_load_2d(dst + kb * 16384, &tmap, kb * 64, r0, &S.full[st]);
+          ++g_ld;
         }
-      } else {
-        // pass 1 (k = 1 queries): H_j = min over rows of a + band
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          float d[16];
-          dev::tmem_ld16(tl + (uint32_t)c0, d);
-  #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = c0 + jj;
-            if (j < nqg && S.kq[j] == 1) {
-              float hiv = __int_as_float(0x7f800000);
-              if (valid) {
-                const float ap = S.qn[j] + xn - 2.0f * d[jj];
-                const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
-                                   1e-4f * (S.qn[j] + xn);
-                hiv = fmaxf(ap + band, 0.0f);
-              }
-  #pragma unroll
-              for (int o = 16; o > 0; o >>= 1) hiv = fminf(hiv, __shfl_xor_sync(0xffffffffu, hiv, o));
-              if (lane == 0) atomic_min_float_nonneg(&S.H[j], hiv);
-            }
+      }
+      PROF_ADD(11);
+    }
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------ MMA issue
+    if (lane == 0) {
+      PROF_T0();
+      long long g_mm = 0;
+      uint32_t full_ph[2] = {0u, 0u}, tempty_ph[2] = {0u, 0u};
+      uint32_t bready_ph = 0;
+      for (int item = blockIdx.x; item < n_items && !*abort; item += gridDim.x) {
+        const Item I = decode_item(a, item);
+        bool ok = wait_phase(&S.bready, bready_ph, abort);
+        bready_ph ^= 1u;
+        PROF_ADD(5);
+        const uint32_t idesc = dev::idesc_f16(kTcRows, I.N);
+        for (int c = 0; ok && c < I.nchunks; ++c) {
+          const int st = (int)(g_mm & 1);
+          ok = wait_phase(&S.full[st], full_ph[st], abort);
+          full_ph[st] ^= 1u;
+          PROF_ADD(6);
+          if (ok && g_mm >= 2) {
+            ok = wait_phase(&S.tempty[st], tempty_ph[st], abort);
+            tempty_ph[st] ^= 1u;
+            PROF_ADD(7);
           }
+          if (!ok) break;
+          dev::tc_fence_after();
+          const uint32_t a_base = dev::smem_addr(st ? A1 : A0), b_base = dev::smem_addr(B);
+          for (int kk = 0; kk < Kp / 16; ++kk)
+            dev::mma_f16(tmem + (uint32_t)(st * kTcG),
+                         dev::smem_desc(a_base + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024, 2),
+                         dev::smem_desc(b_base + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
+          dev::mma_commit(&S.empty[st]);
+          dev::mma_commit(&S.tfull[st]);
+          ++g_mm;
+          PROF_ADD(8);
         }
-        __syncthreads();
-        // pass 2: admission, canonical re-check, top-k update
-        for (int turn = 0; turn < 4; ++turn) {
-          for (int c0 = 0; c0 < N; c0 += 16) {
+        if (!ok) {
+          atomicOr(a.err, 2);
+          S.abort = 1;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue warps 0-7
+    const float4* Q4 = reinterpret_cast<const float4*>(a.Q);
+    const float4* X4 = reinterpret_cast<const float4*>(a.X);
+    const float cK = 9.7656250e-4f + 2.3841858e-7f + (float)Kp * 1.1920929e-7f;
+    const float sm = sqrtf((float)a.mp) * 5.9604645e-8f;
+    uint32_t tfull_ph[2] = {0u, 0u};
+    long long g = 0;
+    PROF_T0();
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+      const Item I = decode_item(a, item);
+      const int nqg = I.nqg, N = I.N;
+      if (prof_on) pr[9] += 1;
+      // the previous item's MMAs are complete (its last accumulator was read),
+      // so the query tile can be replaced
+      // one warp per query row: each lane converts 8 consecutive values (16 bytes)
+      for (int qq = warp; qq < N; qq += kEpiWarps) {
+        const int qrow = qq < nqg ? I.pr[qq].q : -1;
+        float ss = 0.0f, mx = 0.0f;
+        for (int piece = lane; piece < Kp / 8; piece += 32) {
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int i = piece * 8 + e;
+            v[e] = (qrow >= 0 && i < a.mp) ? a.Q[(size_t)qrow * a.mp + i] : 0.0f;
+            ss = fmaf(v[e], v[e], ss);
+            mx = fmaxf(mx, fabsf(v[e]));
+          }
+          __align__(16) __half hv[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) hv[e] = __float2half_rn(v[e]);
+          *reinterpret_cast<uint4*>(B + (qq / 8) * sbo + piece * 128 + (qq % 8) * 16) =
+              *reinterpret_cast<const uint4*>(hv);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0 && qq < nqg) {
+          const int slot = I.pr[qq].slot;
+          S.slot[qq] = slot;
+          S.qrow[qq] = qrow;
+          S.kq[qq] = slot_k ? slot_k[slot] : a.k;
+          S.thr[qq] = a.thr[slot];
+          S.thrd[qq] = (a.thr[slot] == kNoKey) ? __int_as_float(0x7f800000) : dev::key_d2(a.thr[slot]);
+          S.H[qq] = __int_as_float(0x7f800000);
+          S.cnt[qq] = 0;
+          S.wide[qq] = (mx >= 30000.0f) ? 1 : 0;  // outside the safe fp16 range: re-check all
+          S.qc[qq] = make_float4(ss, sqrtf(ss), S.thrd[qq], S.wide[qq] ? 1.0f : 0.0f);
+          if (S.kq[qq] == 1) lists[qq * a.k] = S.thr[qq];
+        }
+      }
+      dev::fence_async_smem();
+      mbar_arrive(&S.bready);
+      epi_sync();
+      PROF_ADD(0);
+
+      const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+      const int r = quarter * 32 + lane;
+      // squared norm of this thread's row in the next chunk, loaded ahead
+      float xn_next = (I.p0 + r < I.p1) ? a.xn[I.p0 + r] : 0.0f;
+      for (int c = 0; c < I.nchunks; ++c) {
+        const int t = (int)(g & 1);
+        if (prof_on) pr[10] += 1;
+        const int64_t r0 = I.p0 + (int64_t)c * kTcRows;
+        const bool valid = r0 + r < I.p1;
+        const int64_t pos = r0 + r;
+        const float xn = valid ? xn_next : 0.0f;
+        xn_next = (pos + kTcRows < I.p1) ? a.xn[pos + kTcRows] : 0.0f;
+        const float xnorm = sqrtf(xn);
+        // on a timeout every later wait returns at once; the loop still reaches
+        // all arrivals and barriers, and the error word reports the failure
+        const bool ok = wait_phase(&S.tfull[t], tfull_ph[t], abort);
+        tfull_ph[t] ^= 1u;
+        if (!ok) {
+          atomicOr(a.err, 2);
+          S.abort = 1;
+        }
+        PROF_ADD(1);
+        const bool okw = __all_sync(0xffffffffu, ok);  // warp-uniform for tcgen05.ld
+        dev::tc_fence_after();
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kTcG);
+        if (defer) {
+          // 1-NN round, one pass over this warp's column groups (warps w and w+4
+          // share the rows and split the 16-column groups); 16 columns at a
+          // time so the loads and warp reductions overlap
+          for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
             float d[16];
             dev::tmem_ld16(tl + (uint32_t)c0, d);
-  #pragma unroll 1
+            float lov[16], hw[16];
+#pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
               const int j = c0 + jj;
-              if (j >= nqg) break;
-              const int kq = S.kq[j];
-              // k = 1 is handled by every warp in turn 0 (atomic min); k > 1 one warp per turn
-              if (kq == 1 ? (turn != 0) : (turn != warp)) continue;
-              bool cand = false;
-              if (valid) {
-                const float ap = S.qn[j] + xn - 2.0f * d[jj];
-                const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
-                                   1e-4f * (S.qn[j] + xn);
-                float T = S.thrd[j];
-                if (kq == 1) {
-                  T = fminf(fminf(T, S.H[j]), dev::key_d2(*(volatile u64*)&lists[j * a.k]));
-                } else if (S.cnt[j] == kq) {
-                  T = fminf(T, dev::key_d2(lists[j * a.k + kq - 1]));
-                }
-                cand = S.wide[j] || !(ap - band > T);
+              lov[jj] = __int_as_float(0x7f800000);
+              hw[jj] = __int_as_float(0x7f800000);
+              if (valid && j < nqg) {
+                const float4 qc = S.qc[j];
+                const float ap = qc.x + xn - 2.0f * d[jj];
+                const float band = 2.0f * (cK * qc.y * xnorm + sm * (qc.y + xnorm)) + 1e-4f * (qc.x + xn);
+                lov[jj] = (qc.w != 0.0f) ? -1.0f : ap - band;
+                hw[jj] = fmaxf(ap + band, 0.0f);
               }
-              u64 key = kNoKey;
-              if (kq == 1) {
-                if (cand) {
-                  // defer: the part's final bound usually rejects it without a re-check
-                  const int slotc = defer ? atomicAdd(&S.ncb, 1) : kCandCap;
+            }
+            // warp minimum of the (non-negative) upper bounds: one REDUX per column
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+              hw[jj] = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(hw[jj])));
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = c0 + jj;
+              if (j < nqg) {
+                const float T = fminf(fminf(S.thrd[j], fminf(S.H[j], hw[jj])),
+                                      dev::key_d2(*(volatile u64*)&lists[j * a.k]));
+                if (valid && !(lov[jj] > T)) {
+                  const int slotc = atomicAdd(&S.ncb, 1);
                   if (slotc < kCandCap) {
-                    const float ap = S.qn[j] + xn - 2.0f * d[jj];
-                    const float band = 2.0f * (cK * S.qnorm[j] * xnorm + sm * (S.qnorm[j] + xnorm)) +
-                                       1e-4f * (S.qn[j] + xn);
                     cb_pos[slotc] = (int)pos;
                     cb_j[slotc] = j;
-                    cb_lo[slotc] = S.wide[j] ? -1.0f : ap - band;
+                    cb_lo[slotc] = lov[jj];
                   } else {
                     const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
                     atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
                     atomicAdd(&S.rechecks, 1ull);
                   }
                 }
-              } else {
+              }
+            }
+            if (lane == 0) {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj)
+                if (c0 + jj < nqg) atomic_min_float_nonneg(&S.H[c0 + jj], hw[jj]);
+            }
+          }
+        } else {
+          // general k: immediate re-checks; warps 0-3 take turns inserting into
+          // the lists (warps 4-7 only join the barriers)
+          for (int turn = 0; turn < 4; ++turn) {
+            for (int c0 = 0; okw && warp < 4 && c0 < N; c0 += 16) {
+              float d[16];
+              dev::tmem_ld16(tl + (uint32_t)c0, d);
+#pragma unroll 1
+              for (int jj = 0; jj < 16; ++jj) {
+                const int j = c0 + jj;
+                if (j >= nqg) break;
+                const int kq = S.kq[j];
+                if (kq == 1 ? (turn != 0) : (turn != warp)) continue;
+                bool cand = false;
+                if (valid) {
+                  const float4 qc = S.qc[j];
+                  const float ap = qc.x + xn - 2.0f * d[jj];
+                  const float band = 2.0f * (cK * qc.y * xnorm + sm * (qc.y + xnorm)) + 1e-4f * (qc.x + xn);
+                  float T = qc.z;
+                  if (kq == 1)
+                    T = fminf(T, dev::key_d2(*(volatile u64*)&lists[j * a.k]));
+                  else if (S.cnt[j] == kq)
+                    T = fminf(T, dev::key_d2(lists[j * a.k + kq - 1]));
+                  cand = S.wide[j] || !(ap - band > T);
+                }
+                u64 key = kNoKey;
                 if (cand) {
                   const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
                   key = dev::make_key(e, (uint32_t)a.ids[pos]);
                   atomicAdd(&S.rechecks, 1ull);
                 }
-                unsigned mask = __ballot_sync(0xffffffffu, cand);
-                int cc = S.cnt[j];
-                while (mask) {
-                  const int src = __ffs(mask) - 1;
-                  mask &= mask - 1;
-                  const u64 kk = __shfl_sync(0xffffffffu, key, src);
-                  const u64 kth = (cc == kq) ? lists[j * a.k + kq - 1] : S.thr[j];
-                  if (kk < kth) cc = dev::warp_insert(lists + j * a.k, cc, kq, kk, lane);
+                if (kq == 1) {
+                  if (cand) atomicMin(&lists[j * a.k], key);
+                } else {
+                  unsigned mask = __ballot_sync(0xffffffffu, cand);
+                  int cc = S.cnt[j];
+                  while (mask) {
+                    const int src = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const u64 kk = __shfl_sync(0xffffffffu, key, src);
+                    const u64 kth = (cc == kq) ? lists[j * a.k + kq - 1] : S.thr[j];
+                    if (kk < kth) cc = dev::warp_insert(lists + j * a.k, cc, kq, kk, lane);
+                  }
+                  if (lane == 0) S.cnt[j] = cc;
+                  __syncwarp();
                 }
-                if (lane == 0) S.cnt[j] = cc;
-                __syncwarp();
               }
             }
+            epi_sync();
           }
-          __syncthreads();
         }
+        dev::tc_fence_before();
+        mbar_arrive(&S.tempty[t]);
+        ++g;
+        PROF_ADD(2);
       }
-      dev::tc_fence_before();
-      __syncthreads();
-      if (S.abort) break;
-    }
-    if (S.abort) break;
-    // deferred re-checks: only candidates whose lower bound still reaches the
-    // part's final bound (round threshold, smallest upper bound, best exact)
-    if (defer) {
-      const int ncb = min(S.ncb, kCandCap);
-      for (int e = tid; e < ncb; e += kTcThreads) {
-        const int j = cb_j[e];
-        const float T = fminf(fminf(S.thrd[j], S.H[j]),
-                              dev::key_d2(*(volatile u64*)&lists[j * a.k]));
-        if (!(cb_lo[e] > T)) {
-          const int64_t pos = cb_pos[e];
-          const float d2 = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
-          atomicMin(&lists[j * a.k], dev::make_key(d2, (uint32_t)a.ids[pos]));
-          atomicAdd(&S.rechecks, 1ull);
+      epi_sync();
+      if (defer) {
+        // deferred re-checks: only candidates whose lower bound still reaches the
+        // part's final bound (round threshold, smallest upper bound, best exact)
+        const int ncb = min(S.ncb, kCandCap);
+        for (int e = tid; e < ncb; e += kEpi) {
+          const int j = cb_j[e];
+          const float T = fminf(fminf(S.thrd[j], S.H[j]), dev::key_d2(*(volatile u64*)&lists[j * a.k]));
+          if (!(cb_lo[e] > T)) {
+            const int64_t pos = cb_pos[e];
+            const float d2 = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+            atomicMin(&lists[j * a.k], dev::make_key(d2, (uint32_t)a.ids[pos]));
+            atomicAdd(&S.rechecks, 1ull);
+          }
         }
+        epi_sync();
+        if (tid == 0) S.ncb = 0;
       }
-      __syncthreads();
-      if (tid == 0) S.ncb = 0;
-    }
-    // k = 1 lists hold the part's best key if it beat the round's threshold
-    if (tid < nqg && S.kq[tid] == 1) S.cnt[tid] = (lists[tid * a.k] < S.thr[tid]) ? 1 : 0;
-    __syncthreads();
-    for (int q = warp; q < nqg; q += kTcThreads / 32) {
-      const int c = S.cnt[q];
-      if (c == 0) continue;
-      const int slot = S.slot[q];
-      int base = 0;
-      if (lane == 0) base = atomicAdd(&a.cand_cnt[slot], c);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (base + c > a.cand_cap) {
-        if (lane == 0) atomicOr(a.err, 1);
-        continue;
+      // k = 1 lists hold the part's best key if it beat the round's threshold
+      if (tid < nqg && S.kq[tid] == 1) S.cnt[tid] = (lists[tid * a.k] < S.thr[tid]) ? 1 : 0;
+      epi_sync();
+      for (int q = warp; q < nqg; q += kEpiWarps) {
+        const int cc = S.cnt[q];
+        if (cc == 0) continue;
+        const int slot = S.slot[q];
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&a.cand_cnt[slot], cc);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base + cc > a.cand_cap) {
+          if (lane == 0) atomicOr(a.err, 1);
+          continue;
+        }
+        for (int e = lane; e < cc; e += 32)
+          a.cand[(size_t)slot * a.cand_cap + base + e] = lists[q * a.k + e];
       }
-      for (int e = lane; e < c; e += 32)
-        a.cand[(size_t)slot * a.cand_cap + base + e] = lists[q * a.k + e];
+      // one thread snapshots the abort flag before the barrier so that every
+      // epilogue thread leaves the item loop at the same item
+      if (tid == 0) S.stop = *abort;
+      epi_sync();
+      PROF_ADD(3);
+      if (S.stop) break;
     }
-    __syncthreads();
   }
+  if (prof_on)
+    for (int i = 0; i < 16; ++i)
+      if (pr[i]) atomicAdd(&a.prof[i], pr[i]);
   dev::tc_fence_before();
   __syncthreads();
   dev::tc_fence_after();
