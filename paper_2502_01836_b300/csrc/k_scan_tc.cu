@@ -54,6 +54,7 @@ struct TcShared {
   float thrd[kTcG];    // its squared distance (inf if fewer than k)
   float H[kTcG];       // k = 1: smallest upper bound a + band in the part
   float4 qc[kTcG];     // per query: |q|^2, |q|, k-th best d^2 (inf if none), wide flag
+  float4 qb[kTcG];     // per query band terms: U_lo, U_hi, alpha (see the epilogue)
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
   int ncb;             // buffered candidates of the current item
   unsigned long long rechecks;
@@ -283,6 +284,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           S.cnt[qq] = 0;
           S.wide[qq] = (mx >= 30000.0f) ? 1 : 0;  // outside the safe fp16 range: re-check all
           S.qc[qq] = make_float4(ss, sqrtf(ss), S.thrd[qq], S.wide[qq] ? 1.0f : 0.0f);
+          {
+            // band(q, x) = alpha |x| + beta + 1e-4 |x|^2 with alpha = 2 (c |q| + s),
+            // beta = 2 s |q| + 1e-4 |q|^2; the bounds are then
+            //   lo = (|q|^2 - beta) + |x|^2 (1 - 1e-4) - alpha |x| - 2 <q~, x~>
+            //   hi = (|q|^2 + beta) + |x|^2 (1 + 1e-4) + alpha |x| - 2 <q~, x~>
+            const float qm = sqrtf(ss);
+            const float alpha = 2.0f * (cK * qm + sm);
+            const float beta = 2.0f * sm * qm + 1e-4f * ss;
+            S.qb[qq] = make_float4(S.wide[qq] ? -__int_as_float(0x7f800000) : ss - beta, ss + beta,
+                                   alpha, 0.0f);
+          }
           if (S.kq[qq] == 1) lists[qq * a.k] = S.thr[qq];
         }
       }
@@ -304,6 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         const float xn = valid ? xn_next : 0.0f;
         xn_next = (pos + kTcRows < I.p1) ? a.xn[pos + kTcRows] : 0.0f;
         const float xnorm = sqrtf(xn);
+        const float vlo = xn * (1.0f - 1e-4f), vhi = xn * (1.0f + 1e-4f);
         // on a timeout every later wait returns at once; the loop still reaches
         // all arrivals and barriers, and the error word reports the failure
         const bool ok = wait_phase(&S.tfull[t], tfull_ph[t], abort);
@@ -330,11 +343,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               lov[jj] = __int_as_float(0x7f800000);
               hw[jj] = __int_as_float(0x7f800000);
               if (valid && j < nqg) {
-                const float4 qc = S.qc[j];
-                const float ap = qc.x + xn - 2.0f * d[jj];
-                const float band = 2.0f * (cK * qc.y * xnorm + sm * (qc.y + xnorm)) + 1e-4f * (qc.x + xn);
-                lov[jj] = (qc.w != 0.0f) ? -1.0f : ap - band;
-                hw[jj] = fmaxf(ap + band, 0.0f);
+                const float4 qb = S.qb[j];
+                lov[jj] = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
+                hw[jj] = fmaxf(fmaf(-2.0f, d[jj], fmaf(qb.z, xnorm, qb.y + vhi)), 0.0f);
               }
             }
             // warp minimum of the (non-negative) upper bounds: one REDUX per column
