@@ -383,6 +383,7 @@ def main():
             "pruning_ratio": 1.0 - st["series_scanned"] / (a.steps * a.queries * a.n),
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
             "waves_per_launch": st["waves"] / max(st["batches"], 1),
+            "graph_batch_fraction": st["graph_batches"] / max(st["batches"], 1),
             "kernel_ms_per_step": {k: v[0] / a.steps for k, v in kt.items()
                                    if not k.startswith("_") and v[1]},
             "scan_phase_cycles_per_block": {k: v / SMS for k, v in kt["_phases"].items()},

@@ -239,10 +239,12 @@ typedef struct {
   int64_t leaves_scanned;  /* (query, leaf) pairs searched */
   int64_t series_scanned;  /* (query, series) distances computed */
   int64_t filter_evals;    /* (query, filter) predictions */
-  int64_t waves;           /* scan rounds, summed over batches */
+  int64_t waves;           /* scan rounds launched, summed over batches (a full batch
+                              always launches its first two, the second maybe empty) */
   int64_t batches;         /* internal query batches (256 queries each) */
   int64_t distinct_series; /* series of the distinct leaves each round read, summed */
   int64_t rechecks;        /* canonical float32 re-checks by the tensor-core scan */
+  int64_t graph_batches;   /* batches replayed from a captured CUDA graph */
 } leafi_search_stats;
 
 /* k-NN of nq queries (1 <= k <= LEAFI_MAX_K).  recall_target >= 1 runs the

@@ -88,7 +88,8 @@ class TrainParams(C.Structure):
 class SearchStats(C.Structure):
     _fields_ = [("leaves_scanned", C.c_int64), ("series_scanned", C.c_int64),
                 ("filter_evals", C.c_int64), ("waves", C.c_int64), ("batches", C.c_int64),
-                ("distinct_series", C.c_int64), ("rechecks", C.c_int64)]
+                ("distinct_series", C.c_int64), ("rechecks", C.c_int64),
+                ("graph_batches", C.c_int64)]
 
 
 _lib = None

@@ -16,6 +16,8 @@
 
 namespace leafi {
 
+unsigned long long g_realloc_epoch = 0;
+
 namespace {
 thread_local std::string g_last_error;
 constexpr int kPart = 2048;       // series per scan work item
@@ -29,6 +31,8 @@ namespace {
 std::atomic<long long> g_launches{0};
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(); }
 
 void fail(leafi_status st, const char* fmt, ...) {
   char buf[512];
@@ -380,10 +384,19 @@ void check_queries(const leafi_index* ix, const float* q, int64_t nq) {
 }
 
 // the search driver shared by leafi_search / _exact / _mixed
+__global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, double tval) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nb) {
+    k[i] = kval;
+    target[i] = tval;
+  }
+}
+
+// the search driver shared by leafi_search / _exact / _mixed
 void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::vector<int32_t>& kq,
                  const std::vector<double>& target, int kmax, int64_t* ids, float* dists,
                  leafi_search_stats* stats) {
-  cudaStream_t s = ix->stream;
+  cudaStream_t s = ix->stream;  // swapped for the capture stream while capturing
   const HostTree& t = ix->tree;
   const int L = t.n_leaves;
   const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
@@ -393,6 +406,10 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   const int W = ix->wave;
   const int cap = std::max(W, 1) * max_parts(t) * kmax;
   const int qb = kBatch;
+  const bool walk = L <= calib_max_sort();
+  // every buffer a batch touches is sized for a full batch up front, so a
+  // captured batch never sees a reallocation while it is replayed
+  float* gQ = ix->sQ.need((size_t)qb * ix->mp);
   int32_t* dK = ix->sK.need(qb);
   double* dT = ix->sTarget.need(qb);
   int32_t* jpos = ix->sJpos.need(qb);
@@ -413,31 +430,69 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   unsigned long long* stat = ix->sStat.need(4);
   int64_t* out_i = ix->sOutI.need((size_t)qb * kmax);
   float* out_d = ix->sOutD.need((size_t)qb * kmax);
-  DBuf<float> qtmp;
+  int32_t* ord = walk ? ix->sOrd.need((size_t)qb * L) : nullptr;
+  int32_t* cursor = walk ? ix->sCursor.need(qb) : nullptr;
+  ix->sCnt.need(L);
+  ix->sGrpOff.need(L + 1);
+  ix->sItemOff.need(L + 1);
+  ix->sGrouped.need((size_t)qb * std::max(W, 1));
+  ix->sNItems.need(1);
+  ix->sP.need((size_t)qb * 2 * (ix->m + 1));
+  if (t.type == LEAFI_DSTREE) {
+    ix->sIv.need((size_t)qb * t.iv_s.size() * 2);
+    ix->sNode.need((size_t)qb * t.n_nodes);
+  } else {
+    ix->sPaa.need((size_t)qb * t.w);
+  }
+  const bool uniform =
+      std::all_of(kq.begin(), kq.end(), [&](int32_t v) { return v == kq[0]; }) &&
+      std::all_of(target.begin(), target.end(), [&](double v) { return v == target[0]; });
   LF_CUDA(cudaMemsetAsync(stat, 0, 4 * sizeof(unsigned long long), s));
-  for (int64_t b0 = 0; b0 < nq; b0 += qb) {
-    const int nb = (int)std::min<int64_t>(qb, nq - b0);
-    const float* dQ = stage_queries(ix, queries + (size_t)b0 * ix->m, nb, qtmp);
-    LF_CUDA(cudaMemcpyAsync(dK, kq.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-    LF_CUDA(cudaMemcpyAsync(dT, target.data() + b0, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
-    ix->tick(2);
-    compute_bounds(ix, dQ, nb, lb2, route);
+
+  SelectArgs sa;
+  sa.L = L;
+  sa.W = W;
+  sa.lb2 = lb2;
+  sa.thr = thr;
+  sa.F = ix->F;
+  sa.leaf_filter = ix->d_leaf_filter.p;
+  sa.alpha = ix->alpha.p;
+  sa.nc = ix->nc;
+  sa.leaf_off = ix->leaf_off.p;
+  sa.scanned = scanned;
+  sa.cur_lb = cur_lb;
+  sa.cur_leaf = cur_leaf;
+  sa.done = done;
+  sa.pairs = pairs;
+  sa.npairs = np;
+  sa.stat = stat;
+
+  auto select = [&](int nb) {
+    LF_CUDA(cudaMemsetAsync(np, 0, sizeof(int32_t), s));
+    ix->tick(5);
+    if (walk)
+      launch_select_walk(sa, ord, cursor, s);
+    else
+      launch_select(sa, s);
     ix->tock();
-    const bool use_f = std::any_of(target.begin() + b0, target.begin() + b0 + nb,
-                                   [](double v) { return v < 1.0; });
+    (void)nb;
+  };
+  // everything of one batch up to (and including) the select of its first wave
+  auto enqueue_head = [&](int nb, bool use_f) {
+    sa.nq = nb;
+    sa.P = use_f ? P : nullptr;
+    sa.jpos = use_f ? jpos : nullptr;
+    ix->tick(2);
+    compute_bounds(ix, gQ, nb, lb2, route);
+    ix->tock();
     if (use_f) {
       ix->tick(4);
-      launch_filter_forward(dQ, nb, ix->mp, ix->m, ix->F, ix->h, ix->W1t.p, ix->b1.p, ix->w2.p,
+      launch_filter_forward(gQ, nb, ix->mp, ix->m, ix->F, ix->h, ix->W1t.p, ix->b1.p, ix->w2.p,
                             ix->b2.p, P, s);
       ix->tock();
       launch_jpos(nb, dK, dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, jpos, s);
-      st.filter_evals += (int64_t)nb * ix->F;
     }
     LF_CUDA(cudaMemsetAsync(scanned, 0, (size_t)nb * L, s));
-    // visiting order per query, walked by the wave select (small trees)
-    const bool walk = L <= calib_max_sort();
-    int32_t* ord = walk ? ix->sOrd.need((size_t)nb * L) : nullptr;
-    int32_t* cursor = walk ? ix->sCursor.need(nb) : nullptr;
     if (walk) {
       launch_leaf_order(nb, L, lb2, ord, s);
       LF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nb, s));
@@ -447,44 +502,135 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     LF_CHECK_LAUNCH();
     // wave 0: every query searches its route leaf
     launch_route_pairs(nb, route, L, scanned, ix->leaf_off.p, pairs, np, stat, s);
-    run_round(ix, dQ, pairs, np, nb, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+    run_round(ix, gQ, pairs, np, nb, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
               stat + 2, stat + 3);
+    select(nb);
+  };
+  // a full batch of the same shape replays a captured graph of enqueue_head
+  // followed by its first wave and the next select
+  auto graph_for = [&](int nb, bool use_f) -> leafi::BatchGraph* {
+    if (!ix->graphs_ok || nb != qb) return nullptr;
+    const unsigned long long epoch0 = g_realloc_epoch;
+    for (auto& g : ix->graphs)
+      if (g.nb == nb && g.kmax == kmax && g.use_f == (int)use_f && g.walk == (int)walk &&
+          g.profiling == (int)ix->profiling && g.epoch == epoch0)
+        return &g;
+    // graphs of an older epoch point at freed scratch: drop them
+    for (size_t i = 0; i < ix->graphs.size();) {
+      leafi::BatchGraph& o = ix->graphs[i];
+      if (o.epoch == epoch0) {
+        ++i;
+        continue;
+      }
+      if (o.exec) cudaGraphExecDestroy(o.exec);
+      for (cudaEvent_t e : o.ev) cudaEventDestroy(e);
+      ix->graphs.erase(ix->graphs.begin() + i);
+    }
+    if (!ix->cap_stream &&
+        cudaStreamCreateWithFlags(&ix->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      ix->cap_stream = nullptr;
+      ix->graphs_ok = false;
+      return nullptr;
+    }
+    ix->graphs.emplace_back();
+    leafi::BatchGraph& g = ix->graphs.back();
+    g.nb = nb;
+    g.kmax = kmax;
+    g.use_f = use_f;
+    g.walk = walk;
+    g.profiling = ix->profiling;
+    g.epoch = epoch0;
+    // capture on the index's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured); nothing runs while capturing
+    cudaGraph_t graph = nullptr;
+    cudaStream_t user = s;
+    s = ix->cap_stream;
+    ix->stream = ix->cap_stream;
+    ix->capturing = &g;
+    const long long l0 = launches_so_far();
+    bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        enqueue_head(nb, use_f);
+        run_round(ix, gQ, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+                  stat + 2, stat + 3);
+        select(nb);
+      } catch (...) {
+        ok = false;
+      }
+      const cudaError_t e = cudaStreamEndCapture(s, &graph);
+      ok = ok && e == cudaSuccess && graph;
+    }
+    g.launches = launches_so_far() - l0;
+    count_launches(-g.launches);
+    ix->capturing = nullptr;
+    s = user;
+    ix->stream = user;
+    if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    // a scratch buffer that grew while capturing invalidates the capture
+    const bool stale = g_realloc_epoch != epoch0;
+    if (!ok || stale) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (cudaEvent_t e2 : g.ev) cudaEventDestroy(e2);
+      ix->graphs.pop_back();
+      if (!ok) ix->graphs_ok = false;  // capture is not available here: stay eager
+      return nullptr;
+    }
+    return &g;
+  };
+
+  for (int64_t b0 = 0; b0 < nq; b0 += qb) {
+    const int nb = (int)std::min<int64_t>(qb, nq - b0);
+    // stage this batch's queries, k and targets into the fixed buffers
+    {
+      const float* src = queries + (size_t)b0 * ix->m;
+      const bool dev = on_device(src);
+      if (ix->mp != ix->m) LF_CUDA(cudaMemsetAsync(gQ, 0, sizeof(float) * nb * ix->mp, s));
+      LF_CUDA(cudaMemcpy2DAsync(gQ, sizeof(float) * ix->mp, src, sizeof(float) * ix->m,
+                                sizeof(float) * ix->m, (size_t)nb,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    if (uniform) {
+      fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, dK, dT, kq[0], target[0]);
+      LF_CHECK_LAUNCH();
+    } else {
+      LF_CUDA(cudaMemcpyAsync(dK, kq.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+      LF_CUDA(cudaMemcpyAsync(dT, target.data() + b0, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    }
+    const bool use_f = std::any_of(target.begin() + b0, target.begin() + b0 + nb,
+                                   [](double v) { return v < 1.0; });
+    if (use_f) st.filter_evals += (int64_t)nb * ix->F;
     int waves = 1;
-    SelectArgs sa;
-    sa.nq = nb;
-    sa.L = L;
-    sa.W = W;
-    sa.lb2 = lb2;
-    sa.thr = thr;
-    sa.P = use_f ? P : nullptr;
-    sa.F = ix->F;
-    sa.leaf_filter = ix->d_leaf_filter.p;
-    sa.alpha = ix->alpha.p;
-    sa.nc = ix->nc;
-    sa.jpos = use_f ? jpos : nullptr;
-    sa.leaf_off = ix->leaf_off.p;
-    sa.scanned = scanned;
-    sa.cur_lb = cur_lb;
-    sa.cur_leaf = cur_leaf;
-    sa.done = done;
-    sa.pairs = pairs;
-    sa.npairs = np;
-    sa.stat = stat;
+    leafi::BatchGraph* g = graph_for(nb, use_f);
+    if (g) {
+      LF_CUDA(cudaGraphLaunch(g->exec, s));
+      count_launches(g->launches);
+      st.graph_batches += 1;
+      waves = 2;
+    } else {
+      enqueue_head(nb, use_f);
+    }
     for (;;) {
-      LF_CUDA(cudaMemsetAsync(np, 0, sizeof(int32_t), s));
-      ix->tick(5);
-      if (walk)
-        launch_select_walk(sa, ord, cursor, s);
-      else
-        launch_select(sa, s);
-      ix->tock();
       int32_t h_np = 0;
       LF_CUDA(cudaMemcpyAsync(&h_np, np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       LF_CUDA(cudaStreamSynchronize(s));
+      if (g && ix->profiling) {
+        for (size_t i = 0; i < g->kind.size(); ++i) {
+          float ms = 0.0f;
+          LF_CUDA(cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]));
+          ix->clock.ms[g->kind[i]] += ms;
+          ix->clock.n[g->kind[i]] += 1;
+        }
+        g = nullptr;
+      }
       if (h_np == 0) break;
       if (++waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
-      run_round(ix, dQ, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+      run_round(ix, gQ, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
                 stat + 2, stat + 3);
+      select(nb);
     }
     st.waves += waves;
     st.batches += 1;
@@ -534,8 +680,27 @@ leafi::DsTables leafi_index::ds() const {
   return T;
 }
 
+void leafi_index::drop_graphs() {
+  for (auto& g : graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+  }
+  graphs.clear();
+}
+
 void leafi_index::tick(int kind) {
   if (!profiling) return;
+  if (capturing) {
+    cudaEvent_t a, b;
+    LF_CUDA(cudaEventCreate(&a));
+    LF_CUDA(cudaEventCreate(&b));
+    // an external record becomes an event-record node of the graph
+    LF_CUDA(cudaEventRecordWithFlags(a, stream, cudaEventRecordExternal));
+    capturing->ev.push_back(a);
+    capturing->ev.push_back(b);
+    capturing->kind.push_back(kind);
+    return;
+  }
   cudaEvent_t a, b;
   LF_CUDA(cudaEventCreate(&a));
   LF_CUDA(cudaEventCreate(&b));
@@ -547,6 +712,10 @@ void leafi_index::tick(int kind) {
 
 void leafi_index::tock() {
   if (!profiling) return;
+  if (capturing) {
+    LF_CUDA(cudaEventRecordWithFlags(capturing->ev.back(), stream, cudaEventRecordExternal));
+    return;
+  }
   LF_CUDA(cudaEventRecord(clock.ev.back(), stream));
 }
 
@@ -730,6 +899,8 @@ void leafi_free(leafi_index* index) {
     cudaGetDevice(&prev);
     cudaSetDevice(index->device);
     if (index->stream) cudaStreamSynchronize(index->stream);
+    index->drop_graphs();
+    if (index->cap_stream) cudaStreamDestroy(index->cap_stream);
     delete index;
     if (prev >= 0) cudaSetDevice(prev);
   }
@@ -748,6 +919,7 @@ leafi_status leafi_set_profiling(leafi_index* index, int32_t on) {
     require_device(index);
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
+    index->drop_graphs();
     index->settle();
     index->profiling = on != 0;
     index->scan_prof.need(16);
@@ -895,6 +1067,7 @@ leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, i
     if (!filter_leaf || !W1 || !b1 || !w2 || !b2) fail(LEAFI_EINVAL, "NULL filter argument");
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
+    index->drop_graphs();
     cudaStream_t s = index->stream;
     std::vector<int32_t> fl;
     to_host(fl, filter_leaf, F, s);
@@ -1081,6 +1254,7 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
       fail(LEAFI_EINVAL, "bad training parameters");
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
+    index->drop_graphs();
     cudaStream_t s = index->stream;
     const int F = index->F, h = index->h, m = index->m;
     const int ng = p->n_gtrain + p->n_gval, nl = p->n_ltrain + p->n_lval;
@@ -1171,6 +1345,7 @@ leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t n
     if (L > calib_max_sort()) fail(LEAFI_EINVAL, "auto-tuner supports at most %d leaves", calib_max_sort());
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
+    index->drop_graphs();
     cudaStream_t s = index->stream;
     const int F = index->F;
     const int kmax = kclasses[nk - 1];
@@ -1257,6 +1432,7 @@ leafi_status leafi_set_autotuners(leafi_index* index, const double* alpha_sorted
       if (kc[i] < 1 || kc[i] > LEAFI_MAX_K || (i && kc[i] <= kc[i - 1])) fail(LEAFI_EINVAL, "bad k-classes");
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
+    index->drop_graphs();
     cudaStream_t s = index->stream;
     DBuf<double> t1, t2;
     const double* da = to_device(alpha_sorted, (size_t)index->F * nc, t1, s);

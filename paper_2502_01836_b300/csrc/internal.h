@@ -32,6 +32,8 @@ void set_last_error(const std::string& s);
   } while (0)
 
 void count_launch();
+void count_launches(long long delta);
+long long launches_so_far();
 #define LF_CHECK_LAUNCH()            \
   do {                               \
     ::leafi::count_launch();         \
@@ -39,6 +41,10 @@ void count_launch();
   } while (0)
 
 // ------------------------------------------------------ device buffers
+// bumped whenever any DBuf reallocates: captured CUDA graphs that hold buffer
+// addresses compare it to know whether they are still valid
+extern unsigned long long g_realloc_epoch;
+
 template <class T>
 struct DBuf {
   T* p = nullptr;
@@ -59,6 +65,7 @@ struct DBuf {
     size_t c = count ? count : 1;
     LF_CUDA(cudaMalloc(&p, c * sizeof(T)));
     n = c;
+    ++g_realloc_epoch;
     return p;
   }
   void upload(const T* h, size_t count, cudaStream_t s) {
@@ -201,6 +208,16 @@ struct SelectArgs {
   unsigned long long* stat;       // [0] leaves searched, [1] series scanned
 };
 
+// one captured search batch (full 256-query batch, route round + one wave)
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  int nb = 0, kmax = 0, use_f = 0, walk = 0, profiling = 0;
+  unsigned long long epoch = 0;
+  long long launches = 0;       // kernels in the graph (added to the launch counter per replay)
+  std::vector<cudaEvent_t> ev;  // start/stop pairs recorded inside the graph
+  std::vector<int> kind;
+};
+
 // per-kernel device time on the index's stream (enabled by leafi_set_profiling)
 struct KernelClock {
   std::vector<cudaEvent_t> ev;  // start/stop pairs
@@ -305,6 +322,11 @@ struct leafi_index {
   leafi::DBuf<int64_t> sOutI;
 
   bool profiling = false;
+  std::vector<leafi::BatchGraph> graphs;   // captured search batches
+  cudaStream_t cap_stream = nullptr;       // private stream used only to capture them
+  leafi::BatchGraph* capturing = nullptr;  // entry being captured (tick/tock record into it)
+  bool graphs_ok = true;                   // cleared if capture is not possible
+  void drop_graphs();
   leafi::DBuf<unsigned long long> scan_prof;  // tensor-core scan phase cycles (profiling)
   leafi::KernelClock clock;
   void tick(int kind);   // record a start event of `kind` on the stream

@@ -242,6 +242,48 @@ def test_search_mixed_matches_oracle(ds, tuned):
     assert same[jpos < 0].all()
 
 
+@pytest.mark.parametrize("k,target", [(1, 0.95), (10, 1.0)])
+def test_captured_batches_match_eager(ds, tuned, k, target):
+    """Full 256-query batches replay a captured CUDA graph; their results and
+    counters equal those of the same queries searched in small (eager) batches,
+    with and without per-kernel timing, and exact mode equals brute force."""
+    X, Q, idx, t = ds
+    fl, Wt, Qc, tables = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_set_autotuners(idx, tables[1][0], np.stack([tables[1][1], tables[10][1]]), [1, 10])
+    Q2 = fx.test_queries(X, 600, seed=303)      # two full batches and a ragged one
+
+    def run(Qs):
+        ids = np.zeros((Qs.shape[0], k), np.int64)
+        d = np.zeros((Qs.shape[0], k), np.float32)
+        st = lf.SearchStats()
+        lf.leafi_search(idx, Qs, k, target, ids, d, st)
+        return ids, d, st
+
+    e_ids, e_d = [], []
+    e_leaves = e_series = 0
+    for i in range(0, 600, 100):
+        a, b, st = run(Q2[i:i + 100])
+        assert st.graph_batches == 0
+        e_ids.append(a)
+        e_d.append(b)
+        e_leaves += st.leaves_scanned
+        e_series += st.series_scanned
+    e_ids, e_d = np.concatenate(e_ids), np.concatenate(e_d)
+    for profiling in (False, False, True):      # capture, replay, capture with timing
+        lf.leafi_set_profiling(idx, profiling)
+        ids, d, st = run(Q2)
+        assert st.graph_batches == 2
+        assert np.array_equal(ids, e_ids) and np.array_equal(d, e_d)
+        assert st.leaves_scanned == e_leaves and st.series_scanned == e_series
+    times = lf.leafi_get_kernel_times(idx)
+    lf.leafi_set_profiling(idx, False)
+    assert times["leaf_scan"][1] >= 2 and times["leaf_scan"][0] > 0
+    if target >= 1.0:
+        bf_ids, bf_d2 = O.knn(X, Q2, k)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+
+
 def test_device_pointers_match_host(ds):
     torch = pytest.importorskip("torch")
     X, Q, idx, t = ds
