@@ -332,7 +332,17 @@ def main():
     hbm = pk.get("hbm_gbs", 6400.0)
     roof_alu = achieved_tf / alu_peak
     roof_hbm = achieved_gbs / hbm
-    if roof_alu >= roof_hbm:
+    if info.tensor_scan:
+        # float16 dot products on tcgen05: the contraction is far below the tensor
+        # peak (2 m FLOP per pair), so the stream of distinct float16 rows is the bound
+        tc_tf = per_launch_pairs * 2.0 * M / (scan_launch_ms / 1e3) / 1e12
+        tc_peak = pk.get("bf16_tflops", 1800.0)
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": roof_hbm, "traffic": None, "peak_source": pk_kind,
+                    "tensor_view": {"achieved_tflops": tc_tf, "peak": tc_peak,
+                                    "frac": tc_tf / tc_peak,
+                                    "peak_source": "fp16 dense = measured bf16 burst rate"}}
+    elif roof_alu >= roof_hbm:
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": roof_alu, "traffic": None,
                     "peak_source": "148 SMs x 128 FP32 lanes x %.0f MHz x 1.5 FLOP/instr (%s clocks)"
@@ -343,7 +353,8 @@ def main():
     roofline["kernel"] = "leaf_scan (tensor cores)" if info.tensor_scan else "leaf_scan (CUDA cores)"
     roofline["bytes_per_series"] = info.scan_row_bytes
     roofline["hbm_view"] = {"achieved_gbs": achieved_gbs, "frac": roof_hbm}
-    roofline["alu_view"] = {"achieved_tflops": achieved_tf, "frac": roof_alu}
+    if not info.tensor_scan:
+        roofline["alu_view"] = {"achieved_tflops": achieved_tf, "frac": roof_alu}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:

@@ -120,10 +120,12 @@ leafi_status leafi_set_profiling(leafi_index* index, int32_t on);
 leafi_status leafi_get_kernel_times(leafi_index* index, double* ms /* [6] */,
                                     int64_t* launches /* [6] */);
 /* Tensor-core scan phase cycles summed over blocks while profiling is on
- * (16 doubles): 0 query tile, 1 wait for an accumulator, 2 epilogue, 3 flush
- * and emit (one epilogue thread per block); 4 wait for a free stage, 5 wait
- * for the query tile, 6 wait for a TMA load, 7 wait for a free accumulator,
- * 8 issue (the control thread); 9 work items, 10 chunks. */
+ * (16 doubles): 0 item set-up, 1 wait for an accumulator, 2 epilogue, 3 flush
+ * and emit (epilogue warp 0, lane 0); 4 wait for a free stage, 11 TMA issue
+ * (the TMA thread); 5 wait for the query tile, 6 wait for a TMA load, 7 wait
+ * for a free accumulator, 8 MMA issue (the MMA thread); 12 wait for a free
+ * query tile, 13 gather (the query loader); 9 work items, 10 chunks read by
+ * epilogue warp 0. */
 leafi_status leafi_get_scan_phases(leafi_index* index, double* cycles);
 /* Series per leaf (host array of n_leaves). Leaves are numbered depth-first,
  * left child first. */

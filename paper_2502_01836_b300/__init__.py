@@ -189,8 +189,9 @@ def leafi_get_kernel_times(index):
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
-SCAN_PHASES = ["query_tile", "wait_accumulator", "epilogue", "flush_emit", "wait_stage_free",
-               "wait_query_tile", "wait_tma", "wait_accumulator_free", "issue", "items", "chunks"]
+SCAN_PHASES = ["item_setup", "wait_accumulator", "epilogue", "flush_emit", "wait_stage_free",
+               "wait_query_tile", "wait_tma", "wait_accumulator_free", "issue", "items", "chunks",
+               "tma_issue", "wait_tile_free", "gather"]
 
 
 def leafi_get_scan_phases(index):

@@ -231,10 +231,37 @@ bool encode_xh_map(leafi_index* ix) {
 }
 
 // One scan round: group pairs by leaf, scan, merge candidates into slots.
-void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_t* dNpairs,
-               int npairs_max, int nslots, int kstride, const int32_t* slot_k,
-               unsigned long long* topk, int32_t* topk_cnt, unsigned long long* thr,
-               unsigned long long* cand, int32_t* cand_cnt, int cap,
+// query tiles of the tensor-core scan for top-k lists of k keys (0: CUDA-core scan)
+int tc_nbuf(leafi_index* ix, int k) {
+  if (!ix->tc_ok || ix->scan_path != 0) return 0;
+  auto it = ix->tc_plan.find(k);
+  if (it != ix->tc_plan.end()) return it->second;
+  const int nb = tc_scan_plan(ix->kp, k, ix->smem_optin, nullptr);
+  ix->tc_plan[k] = nb;
+  return nb;
+}
+
+// float16 rows and band constants of nq queries for the tensor-core scan
+// (null pointers when the index scans on CUDA cores)
+struct TcQueries {
+  __half* Qh = nullptr;
+  float4* Qk = nullptr;
+};
+TcQueries prep_tc_queries(leafi_index* ix, const float* dQ, int nq, int cap_rows) {
+  TcQueries r;
+  if (!ix->tc_ok || ix->scan_path != 0) return r;
+  __half* Qh = ix->sQh.need((size_t)std::max(nq, cap_rows) * ix->kp);
+  float4* Qk = ix->sQk.need((size_t)2 * std::max(nq, cap_rows));
+  launch_tc_query_prep(dQ, nq, ix->mp, ix->kp, Qh, Qk, ix->stream);
+  r.Qh = Qh;
+  r.Qk = Qk;
+  return r;
+}
+
+void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair* pairs,
+               const int32_t* dNpairs, int npairs_max, int nslots, int kstride,
+               const int32_t* slot_k, unsigned long long* topk, int32_t* topk_cnt,
+               unsigned long long* thr, unsigned long long* cand, int32_t* cand_cnt, int cap,
                unsigned long long* distinct_stat = nullptr,
                unsigned long long* recheck_stat = nullptr) {
   cudaStream_t s = ix->stream;
@@ -244,9 +271,8 @@ void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_
   int32_t* ioff = ix->sItemOff.need(L + 1);
   Pair* grouped = ix->sGrouped.need(std::max(npairs_max, 1));
   int32_t* nitems = ix->sNItems.need(1);
-  const int kstride_smem = kstride;
-  const bool use_tc = ix->tc_ok && ix->scan_path == 0 &&
-                      tc_scan_smem_bytes(ix->kp, kstride_smem) + 4096 <= (size_t)ix->smem_optin;
+  const int nbuf = tq.Qh ? tc_nbuf(ix, kstride) : 0;
+  const bool use_tc = nbuf > 0;
   launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
                use_tc ? tc_group_size() : scan_group_size(), cnt, goff, ioff, grouped, nitems,
                distinct_stat, s);
@@ -264,6 +290,9 @@ void run_round(leafi_index* ix, const float* dQ, const Pair* pairs, const int32_
     t.k = kstride;
     t.part = kPart;
     t.Q = dQ;
+    t.Qh = tq.Qh;
+    t.Qk = tq.Qk;
+    t.nbuf = nbuf;
     t.pairs = grouped;
     t.grp_off = goff;
     t.item_off = ioff;
@@ -355,12 +384,18 @@ void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dL
   unsigned long long* cand = ix->sCand.need((size_t)qb * nl * cap);
   Pair* pairs = ix->sPairs.need((size_t)qb * nl);
   int32_t* np = ix->sNpairs.need(1);
+  const TcQueries tq = prep_tc_queries(ix, dQ, nq, 0);
   for (int q0 = 0; q0 < nq; q0 += qb) {
     const int nb = std::min(qb, nq - q0);
     const int ns = nb * nl;
     launch_leafknn_pairs(nb, nl, dLeaves + (size_t)q0 * nl, L, pairs, np, s);
+    TcQueries tb;
+    if (tq.Qh) {
+      tb.Qh = tq.Qh + (size_t)q0 * ix->kp;
+      tb.Qk = tq.Qk + (size_t)2 * q0;
+    }
     // slots of this batch are [q0*nl, q0*nl + ns): shift the bases
-    run_round(ix, dQ + (size_t)q0 * ix->mp, pairs, np, ns, ns, k, nullptr,
+    run_round(ix, dQ + (size_t)q0 * ix->mp, tb, pairs, np, ns, ns, k, nullptr,
               topk.p + (size_t)q0 * nl * k, topk_cnt.p + (size_t)q0 * nl, thr + (size_t)q0 * nl,
               cand, cand_cnt + (size_t)q0 * nl, cap);
   }
@@ -432,6 +467,11 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   float* out_d = ix->sOutD.need((size_t)qb * kmax);
   int32_t* ord = walk ? ix->sOrd.need((size_t)qb * L) : nullptr;
   int32_t* cursor = walk ? ix->sCursor.need(qb) : nullptr;
+  TcQueries tq;
+  if (ix->tc_ok && ix->scan_path == 0) {
+    tq.Qh = ix->sQh.need((size_t)qb * ix->kp);
+    tq.Qk = ix->sQk.need((size_t)2 * qb);
+  }
   ix->sCnt.need(L);
   ix->sGrpOff.need(L + 1);
   ix->sItemOff.need(L + 1);
@@ -485,6 +525,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     ix->tick(2);
     compute_bounds(ix, gQ, nb, lb2, route);
     ix->tock();
+    if (tq.Qh) launch_tc_query_prep(gQ, nb, ix->mp, ix->kp, tq.Qh, tq.Qk, s);
     if (use_f) {
       ix->tick(4);
       launch_filter_forward(gQ, nb, ix->mp, ix->m, ix->F, ix->h, ix->W1t.p, ix->b1.p, ix->w2.p,
@@ -502,7 +543,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     LF_CHECK_LAUNCH();
     // wave 0: every query searches its route leaf
     launch_route_pairs(nb, route, L, scanned, ix->leaf_off.p, pairs, np, stat, s);
-    run_round(ix, gQ, pairs, np, nb, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+    run_round(ix, gQ, tq, pairs, np, nb, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
               stat + 2, stat + 3);
     select(nb);
   };
@@ -553,7 +594,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     if (ok) {
       try {
         enqueue_head(nb, use_f);
-        run_round(ix, gQ, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+        run_round(ix, gQ, tq, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
                   stat + 2, stat + 3);
         select(nb);
       } catch (...) {
@@ -628,7 +669,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       }
       if (h_np == 0) break;
       if (++waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
-      run_round(ix, gQ, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
+      run_round(ix, gQ, tq, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
                 stat + 2, stat + 3);
       select(nb);
     }

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "host_tree.h"
@@ -157,6 +158,9 @@ struct TcScanArgs {
   int L, mp, kp, k;
   int part;
   const float* Q;                  // [nq][mp]
+  const __half* Qh;                // [nq][kp] float16 queries (launch_tc_query_prep)
+  const float4* Qk;                // [nq][2] band constants (launch_tc_query_prep)
+  int nbuf;                        // query tiles in shared memory (tc_scan_plan)
   const Pair* pairs;
   const int32_t* grp_off;
   const int32_t* item_off;
@@ -169,7 +173,11 @@ struct TcScanArgs {
   unsigned long long* prof;        // nullable: per-phase cycle counters (16)
 };
 int tc_group_size();
-size_t tc_scan_smem_bytes(int kp, int k);
+// query tiles (2 or 1) the tensor-core scan can keep for rows of kp halves and
+// top-k lists of k keys within `smem_optin` bytes; 0 if it does not fit
+int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem);
+void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, float4* Qk,
+                          cudaStream_t s);
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s);
 void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k, int grid,
@@ -311,6 +319,9 @@ struct leafi_index {
 
   // scratch (grown on demand)
   leafi::DBuf<float> sQ;
+  leafi::DBuf<__half> sQh;       // float16 queries of the tensor-core scan
+  leafi::DBuf<float4> sQk;       // their band constants
+  std::map<int, int> tc_plan;    // k -> query tiles of the tensor-core scan (0: does not fit)
   leafi::DBuf<double> sP, sIv, sNode, sLb, sPaa, sTarget;
   leafi::DBuf<int32_t> sRoute, sK, sJpos, sCnt, sGrpOff, sItemOff, sNpairs, sCandCnt, sTopkCnt,
       sDone, sCurLeaf, sErr, sLeaves, sNItems, sOrd, sCursor;

@@ -4,11 +4,12 @@
 // part's series stream through shared memory in chunks of 128 rows of an
 // fp16 copy of the data: one 2-D TMA per 64-column block (128-byte rows,
 // 128-byte swizzle) lands each chunk directly in the K-major layout the MMA
-// reads (two stages, loads run two chunks ahead); one thread issues tcgen05.mma (M = 128 series, N =
-// the query group rounded to 16, K = the padded length) into one of two TMEM
-// accumulators, so the MMA of chunk c+1 overlaps the epilogue of chunk c, in
-// which the four warps read their 32 TMEM lanes back (one series row per
-// thread) with tcgen05.ld.  The dot products give approximate squared distances
+// reads (two stages).  A loader warp gathers the item's query rows (fp16,
+// prepared once per batch) into one of two query tiles while the previous item
+// is still being scanned.  One thread issues tcgen05.mma (M = 128 series,
+// N = the query group rounded to 16, K = the padded length) into one of four
+// TMEM accumulators; the epilogue warps read them back with tcgen05.ld (one
+// series row per thread).  The dot products give approximate squared distances
 //     a = |q|^2 + |x|^2 - 2 <q~, x~>
 // whose error against the canonical float32 distance is bounded per pair by
 //     band = 2 (c |q| |x| + 2^-24 sqrt(m) (|q| + |x|)) + 1e-4 (|q|^2 + |x|^2),
@@ -21,6 +22,13 @@
 // minimum).  No series whose canonical distance could enter the top-k is
 // skipped, so results are bit-exact while almost all arithmetic runs on the
 // tensor cores.
+//
+// Roles (352 threads): warps 0-7 epilogue, warp 8 lane 0 TMA producer, warp 9
+// lane 0 MMA issuer, warp 10 query-tile loader.  For k = 1 the epilogue warps
+// split into two halves that take alternate accumulators (warps 0-3 even
+// chunks, 4-7 odd chunks), so all eight warps work even for small query
+// groups; the re-checks are deferred to the end of the item.  For k > 1 all
+// eight warps walk every chunk and warps 0-3 insert into the lists in turns.
 #include <cfloat>
 
 #include "device_util.cuh"
@@ -36,34 +44,38 @@ constexpr int kEpi = 256;         // epilogue threads: warps 0-7, two per TMEM l
 constexpr int kEpiWarps = kEpi / 32;
 constexpr int kLoadWarp = kEpiWarps;      // lane 0 issues the TMA loads
 constexpr int kMmaWarp = kEpiWarps + 1;   // lane 0 issues the MMAs
-constexpr int kTcThreads = kEpi + 64;
-constexpr int kTmemCols = 2 * kTcG;
+constexpr int kQueryWarp = kEpiWarps + 2; // gathers the query tiles
+constexpr int kTcThreads = kEpi + 96;
+constexpr int kAcc = 4;                   // TMEM accumulators of kTcG columns
+constexpr int kTmemCols = kAcc * kTcG;
 constexpr long long kWaitLimit = 1ll << 26;
 constexpr int kCandCap = 2048;    // deferred re-check buffer (k = 1 rounds)
 
 struct TcShared {
-  u64 full[2];    // TMA of stage s landed (1 arrival + bytes)
-  u64 empty[2];   // MMAs reading stage s finished (tcgen05.commit)
-  u64 tfull[2];   // accumulator t written (tcgen05.commit)
-  u64 tempty[2];  // accumulator t read back by the epilogue threads
-  u64 bready;     // the item's query tile is in shared memory (kEpi arrivals)
+  u64 full[2];      // TMA of stage s landed (1 arrival + bytes)
+  u64 empty[2];     // MMAs reading stage s finished (tcgen05.commit)
+  u64 tfull[kAcc];  // accumulator t written (tcgen05.commit)
+  u64 tempty[kAcc]; // accumulator t read back by the epilogue threads
+  u64 bready[2];    // query tile b gathered (32 arrivals of the loader warp)
+  u64 bempty[2];    // MMAs reading query tile b finished (tcgen05.commit)
   uint32_t tmem_base;
   int abort;
   int stop;            // epilogue warps' uniform snapshot of `abort`
   u64 thr[kTcG];       // slot's k-th best key at the start of the round
   float thrd[kTcG];    // its squared distance (inf if fewer than k)
-  float H[kTcG];       // k = 1: smallest upper bound a + band in the part
-  float4 qc[kTcG];     // per query: |q|^2, |q|, k-th best d^2 (inf if none), wide flag
-  float4 qb[kTcG];     // per query band terms: U_lo, U_hi, alpha (see the epilogue)
+  float H[kTcG];       // k = 1: running admission bound (thrd, smallest a + band so far)
+  float4 qb[kTcG];     // per query: U_lo, U_hi, alpha, |q|^2 (see the epilogue)
+  float qm[kTcG];      // |q|
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
   int ncb;             // buffered candidates of the current item
   unsigned long long rechecks;
 };
 
 // optional per-phase cycle counters (TcScanArgs::prof, 16 entries):
-// epilogue warp 0 lane 0: 0 query tile, 1 wait accumulator, 2 epilogue, 3 flush+emit;
+// epilogue warp 0 lane 0: 0 item set-up, 1 wait accumulator, 2 epilogue, 3 flush+emit;
 // MMA thread: 5 wait query tile, 6 wait TMA, 7 wait accumulator free, 8 MMA issue;
-// load thread: 4 wait stage free, 11 TMA issue; 9 items, 10 chunks
+// load thread: 4 wait stage free, 11 TMA issue; 9 items, 10 chunks (of warp 0);
+// query loader lane 0: 12 wait tile free, 13 gather
 #define PROF_T0() long long _pt = clock64()
 #define PROF_ADD(i)                                              \
   do {                                                           \
@@ -120,6 +132,55 @@ __device__ __forceinline__ bool wait_phase(u64* mbar, uint32_t parity, volatile 
   return false;
 }
 
+// Band constants of one query (fp16 operands over Kp columns, mp-float rows):
+// alpha = 2 (c |q| + s), beta = 2 s |q| + 1e-4 |q|^2 with c = 2^-10 + 2^-22 +
+// Kp 2^-23 and s = sqrt(mp) 2^-24, so that for any series x
+//   lo = (|q|^2 - beta) + |x|^2 (1 - 1e-4) - alpha |x| - 2 <q~, x~>
+//   hi = (|q|^2 + beta) + |x|^2 (1 + 1e-4) + alpha |x| - 2 <q~, x~>
+// bracket the canonical squared distance.
+__device__ __forceinline__ float band_c(int Kp) {
+  return 9.7656250e-4f + 2.3841858e-7f + (float)Kp * 1.1920929e-7f;
+}
+__device__ __forceinline__ float band_s(int mp) { return sqrtf((float)mp) * 5.9604645e-8f; }
+
+// fp16 query rows and band constants, one warp per query:
+// Qk[2q] = (U_lo, U_hi, alpha, |q|^2), Qk[2q+1] = (|q|, wide, 0, 0), where
+// U_lo = |q|^2 - beta (-inf for a query outside the safe fp16 range, whose
+// series are then all re-checked) and U_hi = |q|^2 + beta
+__global__ void tc_query_prep_kernel(const float* __restrict__ Q, int nq, int mp, int Kp,
+                                     __half* __restrict__ Qh, float4* __restrict__ Qk) {
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  float ss = 0.0f, mx = 0.0f;
+  for (int piece = lane; piece < Kp / 8; piece += 32) {
+    __align__(16) __half hv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = piece * 8 + e;
+      const float v = i < mp ? Q[(size_t)q * mp + i] : 0.0f;
+      ss = fmaf(v, v, ss);
+      mx = fmaxf(mx, fabsf(v));
+      hv[e] = __float2half_rn(v);
+    }
+    *reinterpret_cast<uint4*>(Qh + (size_t)q * Kp + piece * 8) = *reinterpret_cast<const uint4*>(hv);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    const float qm = sqrtf(ss);
+    const float sm = band_s(mp);
+    const float alpha = 2.0f * (band_c(Kp) * qm + sm);
+    const float beta = 2.0f * sm * qm + 1e-4f * ss;
+    const bool wide = mx >= 30000.0f;
+    Qk[2 * (size_t)q] = make_float4(wide ? -__int_as_float(0x7f800000) : ss - beta, ss + beta, alpha, ss);
+    Qk[2 * (size_t)q + 1] = make_float4(qm, wide ? 1.0f : 0.0f, 0.0f, 0.0f);
+  }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     const __grid_constant__ CUtensorMap tmap, TcScanArgs a, const int32_t* __restrict__ n_items_dev,
     const int32_t* __restrict__ slot_k) {
@@ -130,14 +191,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int Kp = a.kp;                       // fp16 row length (multiple of 64)
   const int tileA = kTcRows * Kp * 2;        // bytes per A stage
+  const int tileB = kTcG * Kp * 2;           // bytes per query tile
+  const int nbuf = a.nbuf;                   // query tiles (1 or 2)
   unsigned char* A0 = smem;
   unsigned char* A1 = smem + tileA;
-  unsigned char* B = smem + 2 * tileA;       // kTcG x Kp fp16, no swizzle
-  u64* lists = reinterpret_cast<u64*>(B + kTcG * Kp * 2);  // [kTcG][a.k]
+  unsigned char* B0 = smem + 2 * tileA;      // kTcG x Kp fp16, no swizzle
+  unsigned char* B1 = B0 + (nbuf - 1) * tileB;
+  u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);  // [kTcG][a.k]
   int* cb_pos = reinterpret_cast<int*>(lists + kTcG * a.k);
   int* cb_j = cb_pos + kCandCap;
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
-  const bool defer = (a.k == 1);
+  const bool split = (a.k == 1);             // k = 1: halves on alternate accumulators, deferred re-checks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sbo = 16u * Kp;             // B: bytes between 8-row groups
   const int m4 = a.mp / 4;
@@ -147,10 +211,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     for (int i = 0; i < 2; ++i) {
       dev::mbar_init(&S.full[i], 1);
       dev::mbar_init(&S.empty[i], 1);
-      dev::mbar_init(&S.tfull[i], 1);
-      dev::mbar_init(&S.tempty[i], kEpi);
+      dev::mbar_init(&S.bready[i], 32);
+      dev::mbar_init(&S.bempty[i], 1);
     }
-    dev::mbar_init(&S.bready, kEpi);
+    for (int i = 0; i < kAcc; ++i) {
+      dev::mbar_init(&S.tfull[i], 1);
+      dev::mbar_init(&S.tempty[i], split ? kEpi / 2 : kEpi);
+    }
     S.abort = 0;
     S.stop = 0;
     S.ncb = 0;
@@ -164,7 +231,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   const int n_items = *n_items_dev;
   unsigned long long pr[16];
   for (int i = 0; i < 16; ++i) pr[i] = 0;
-  const bool prof_on = a.prof != nullptr && (tid == 0 || tid == kLoadWarp * 32 || tid == kMmaWarp * 32);
+  const bool prof_on = a.prof != nullptr &&
+                       (tid == 0 || tid == kLoadWarp * 32 || tid == kMmaWarp * 32 || tid == kQueryWarp * 32);
 
   if (warp == kLoadWarp) {
     // ------------------------------------------------ TMA producer
@@ -193,41 +261,108 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       }
       PROF_ADD(11);
     }
+  } else if (warp == kQueryWarp) {
+    // ------------------------------------------------ query-tile loader
+    // (lane 0 takes every decision and broadcasts it, so the warp stays converged)
+    PROF_T0();
+    uint32_t bempty_ph[2] = {0u, 0u};
+    int li = 0;
+    const int pieces = Kp / 8;                 // 16-byte pieces per query row
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++li) {
+      if (__shfl_sync(0xffffffffu, *abort, 0)) break;
+      const Item I = decode_item(a, item);
+      const int b = li % nbuf;
+      if (li >= nbuf) {
+        bool ok = true;
+        if (lane == 0) ok = wait_phase(&S.bempty[b], bempty_ph[b], abort);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        bempty_ph[b] ^= 1u;
+        if (!ok) {
+          if (lane == 0) {
+            atomicOr(a.err, 2);
+            S.abort = 1;
+          }
+          break;
+        }
+      }
+      PROF_ADD(12);
+      unsigned char* Bt = b ? B1 : B0;
+      // rows beyond the group are zero; four rows in flight per lane
+      for (int q0 = 0; q0 < I.N; q0 += 4) {
+        uint4 v[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int qq = q0 + u;
+          const int row = qq < I.nqg ? I.pr[qq].q : -1;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int piece = lane + 32 * h;
+            v[u][h] = make_uint4(0u, 0u, 0u, 0u);
+            if (row >= 0 && piece < pieces)
+              v[u][h] = *reinterpret_cast<const uint4*>(a.Qh + (size_t)row * Kp + piece * 8);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int qq = q0 + u;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int piece = lane + 32 * h;
+            if (piece < pieces)
+              *reinterpret_cast<uint4*>(Bt + (qq / 8) * sbo + piece * 128 + (qq % 8) * 16) = v[u][h];
+          }
+        }
+      }
+      dev::fence_async_smem();
+      __syncwarp();
+      mbar_arrive(&S.bready[b]);
+      PROF_ADD(13);
+    }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------ MMA issue
     if (lane == 0) {
       PROF_T0();
       long long g_mm = 0;
-      uint32_t full_ph[2] = {0u, 0u}, tempty_ph[2] = {0u, 0u};
-      uint32_t bready_ph = 0;
-      for (int item = blockIdx.x; item < n_items && !*abort; item += gridDim.x) {
+      int li = 0;
+      uint32_t full_ph[2] = {0u, 0u}, bready_ph[2] = {0u, 0u}, tempty_ph[kAcc] = {0u, 0u, 0u, 0u};
+      const uint64_t adesc[2] = {dev::smem_desc(dev::smem_addr(A0), 16, 1024, 2),
+                                 dev::smem_desc(dev::smem_addr(A1), 16, 1024, 2)};
+      const uint64_t bdesc[2] = {dev::smem_desc(dev::smem_addr(B0), 128, sbo),
+                                 dev::smem_desc(dev::smem_addr(B1), 128, sbo)};
+      for (int item = blockIdx.x; item < n_items && !*abort; item += gridDim.x, ++li) {
         const Item I = decode_item(a, item);
-        bool ok = wait_phase(&S.bready, bready_ph, abort);
-        bready_ph ^= 1u;
+        const int b = li % nbuf;
+        bool ok = wait_phase(&S.bready[b], bready_ph[b], abort);
+        bready_ph[b] ^= 1u;
         PROF_ADD(5);
         const uint32_t idesc = dev::idesc_f16(kTcRows, I.N);
         for (int c = 0; ok && c < I.nchunks; ++c) {
-          const int st = (int)(g_mm & 1);
+          const int st = (int)(g_mm & 1), t = (int)(g_mm & (kAcc - 1));
           ok = wait_phase(&S.full[st], full_ph[st], abort);
           full_ph[st] ^= 1u;
           PROF_ADD(6);
-          if (ok && g_mm >= 2) {
-            ok = wait_phase(&S.tempty[st], tempty_ph[st], abort);
-            tempty_ph[st] ^= 1u;
+          if (ok && g_mm >= kAcc) {
+            ok = wait_phase(&S.tempty[t], tempty_ph[t], abort);
+            tempty_ph[t] ^= 1u;
             PROF_ADD(7);
           }
           if (!ok) break;
           dev::tc_fence_after();
-          const uint32_t a_base = dev::smem_addr(st ? A1 : A0), b_base = dev::smem_addr(B);
+          // descriptor start addresses advance in 16-byte units: +32 bytes per
+          // K step inside a 128-byte swizzle row, +16 KB per 64-column block (A);
+          // +256 bytes per K step (B, two core matrices)
+          const uint64_t ad = adesc[st], bd = bdesc[b];
+          const uint32_t dt = tmem + (uint32_t)(t * kTcG);
           for (int kk = 0; kk < Kp / 16; ++kk)
-            dev::mma_f16(tmem + (uint32_t)(st * kTcG),
-                         dev::smem_desc(a_base + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024, 2),
-                         dev::smem_desc(b_base + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
+            dev::mma_f16(dt, ad + (uint64_t)((kk >> 2) * 1024 + (kk & 3) * 2), bd + (uint64_t)(kk * 16),
+                         idesc, kk > 0 ? 1u : 0u);
           dev::mma_commit(&S.empty[st]);
-          dev::mma_commit(&S.tfull[st]);
+          dev::mma_commit(&S.tfull[t]);
           ++g_mm;
           PROF_ADD(8);
         }
+        // the query tile is free once this item's MMAs have completed
+        dev::mma_commit(&S.bempty[b]);
         if (!ok) {
           atomicOr(a.err, 2);
           S.abort = 1;
@@ -238,85 +373,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     // ------------------------------------------------ epilogue warps 0-7
     const float4* Q4 = reinterpret_cast<const float4*>(a.Q);
     const float4* X4 = reinterpret_cast<const float4*>(a.X);
-    const float cK = 9.7656250e-4f + 2.3841858e-7f + (float)Kp * 1.1920929e-7f;
-    const float sm = sqrtf((float)a.mp) * 5.9604645e-8f;
-    uint32_t tfull_ph[2] = {0u, 0u};
+    const float cK = band_c(Kp);
+    const float sm = band_s(a.mp);
+    const float kInf = __int_as_float(0x7f800000);
+    const int half = warp >> 2;
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int r = quarter * 32 + lane;
+    uint32_t tfull_ph[kAcc] = {0u, 0u, 0u, 0u};
     long long g = 0;
     PROF_T0();
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       const Item I = decode_item(a, item);
       const int nqg = I.nqg, N = I.N;
       if (prof_on) pr[9] += 1;
-      // the previous item's MMAs are complete (its last accumulator was read),
-      // so the query tile can be replaced
-      // one warp per query row: each lane converts 8 consecutive values (16 bytes)
-      for (int qq = warp; qq < N; qq += kEpiWarps) {
-        const int qrow = qq < nqg ? I.pr[qq].q : -1;
-        float ss = 0.0f, mx = 0.0f;
-        for (int piece = lane; piece < Kp / 8; piece += 32) {
-          float v[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int i = piece * 8 + e;
-            v[e] = (qrow >= 0 && i < a.mp) ? a.Q[(size_t)qrow * a.mp + i] : 0.0f;
-            ss = fmaf(v[e], v[e], ss);
-            mx = fmaxf(mx, fabsf(v[e]));
-          }
-          __align__(16) __half hv[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) hv[e] = __float2half_rn(v[e]);
-          *reinterpret_cast<uint4*>(B + (qq / 8) * sbo + piece * 128 + (qq % 8) * 16) =
-              *reinterpret_cast<const uint4*>(hv);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          ss += __shfl_xor_sync(0xffffffffu, ss, o);
-          mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if (lane == 0 && qq < nqg) {
-          const int slot = I.pr[qq].slot;
+      // per-query state of the item (padding columns never admit a series)
+      if (tid < N) {
+        const int qq = tid;
+        if (qq < nqg) {
+          const int slot = I.pr[qq].slot, qrow = I.pr[qq].q;
+          const float4 k0 = a.Qk[2 * (size_t)qrow], k1 = a.Qk[2 * (size_t)qrow + 1];
+          const u64 th = a.thr[slot];
+          const float thd = (th == kNoKey) ? kInf : dev::key_d2(th);
           S.slot[qq] = slot;
           S.qrow[qq] = qrow;
           S.kq[qq] = slot_k ? slot_k[slot] : a.k;
-          S.thr[qq] = a.thr[slot];
-          S.thrd[qq] = (a.thr[slot] == kNoKey) ? __int_as_float(0x7f800000) : dev::key_d2(a.thr[slot]);
-          S.H[qq] = __int_as_float(0x7f800000);
+          S.thr[qq] = th;
+          S.thrd[qq] = thd;
+          S.H[qq] = thd;
           S.cnt[qq] = 0;
-          S.wide[qq] = (mx >= 30000.0f) ? 1 : 0;  // outside the safe fp16 range: re-check all
-          S.qc[qq] = make_float4(ss, sqrtf(ss), S.thrd[qq], S.wide[qq] ? 1.0f : 0.0f);
-          {
-            // band(q, x) = alpha |x| + beta + 1e-4 |x|^2 with alpha = 2 (c |q| + s),
-            // beta = 2 s |q| + 1e-4 |q|^2; the bounds are then
-            //   lo = (|q|^2 - beta) + |x|^2 (1 - 1e-4) - alpha |x| - 2 <q~, x~>
-            //   hi = (|q|^2 + beta) + |x|^2 (1 + 1e-4) + alpha |x| - 2 <q~, x~>
-            const float qm = sqrtf(ss);
-            const float alpha = 2.0f * (cK * qm + sm);
-            const float beta = 2.0f * sm * qm + 1e-4f * ss;
-            S.qb[qq] = make_float4(S.wide[qq] ? -__int_as_float(0x7f800000) : ss - beta, ss + beta,
-                                   alpha, 0.0f);
-          }
-          if (S.kq[qq] == 1) lists[qq * a.k] = S.thr[qq];
+          S.wide[qq] = k1.y != 0.0f ? 1 : 0;
+          S.qb[qq] = k0;
+          S.qm[qq] = k1.x;
+          if (S.kq[qq] == 1) lists[qq * a.k] = th;
+        } else {
+          S.qb[qq] = make_float4(kInf, kInf, 0.0f, 0.0f);
+          S.H[qq] = 0.0f;  // lo = inf > 0: never a candidate
         }
       }
-      dev::fence_async_smem();
-      mbar_arrive(&S.bready);
       epi_sync();
       PROF_ADD(0);
 
-      const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
-      const int r = quarter * 32 + lane;
-      // squared norm of this thread's row in the next chunk, loaded ahead
-      float xn_next = (I.p0 + r < I.p1) ? a.xn[I.p0 + r] : 0.0f;
-      for (int c = 0; c < I.nchunks; ++c) {
-        const int t = (int)(g & 1);
+      for (int c = 0; c < I.nchunks; ++c, ++g) {
+        const int t = (int)(g & (kAcc - 1));
+        if (split && (t & 1) != half) continue;
         if (prof_on) pr[10] += 1;
-        const int64_t r0 = I.p0 + (int64_t)c * kTcRows;
-        const bool valid = r0 + r < I.p1;
-        const int64_t pos = r0 + r;
-        const float xn = valid ? xn_next : 0.0f;
-        xn_next = (pos + kTcRows < I.p1) ? a.xn[pos + kTcRows] : 0.0f;
-        const float xnorm = sqrtf(xn);
-        const float vlo = xn * (1.0f - 1e-4f), vhi = xn * (1.0f + 1e-4f);
+        const int64_t pos = I.p0 + (int64_t)c * kTcRows + r;
+        const bool valid = pos < I.p1;
+        const float xn = valid ? a.xn[pos] : 0.0f;
         // on a timeout every later wait returns at once; the loop still reaches
         // all arrivals and barriers, and the error word reports the failure
         const bool ok = wait_phase(&S.tfull[t], tfull_ph[t], abort);
@@ -329,58 +432,75 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         const bool okw = __all_sync(0xffffffffu, ok);  // warp-uniform for tcgen05.ld
         dev::tc_fence_after();
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kTcG);
-        if (defer) {
-          // 1-NN round, one pass over this warp's column groups (warps w and w+4
-          // share the rows and split the 16-column groups); 16 columns at a
-          // time so the loads and warp reductions overlap
-          for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
+        if (split) {
+          // rows past the part end never admit a series
+          const float xnorm = sqrtf(xn);
+          const float vlo = valid ? xn * (1.0f - 1e-4f) : kInf;
+          const float vhi = valid ? xn * (1.0f + 1e-4f) : kInf;
+          for (int c0 = 0; okw && c0 < N; c0 += 16) {
             float d[16];
             dev::tmem_ld16(tl + (uint32_t)c0, d);
             float lov[16], hw[16];
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
-              const int j = c0 + jj;
-              lov[jj] = __int_as_float(0x7f800000);
-              hw[jj] = __int_as_float(0x7f800000);
-              if (valid && j < nqg) {
-                const float4 qb = S.qb[j];
-                lov[jj] = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
-                hw[jj] = fmaxf(fmaf(-2.0f, d[jj], fmaf(qb.z, xnorm, qb.y + vhi)), 0.0f);
-              }
+              const float4 qb = S.qb[c0 + jj];
+              lov[jj] = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
+              hw[jj] = fmaxf(fmaf(-2.0f, d[jj], fmaf(qb.z, xnorm, qb.y + vhi)), 0.0f);
             }
             // warp minimum of the (non-negative) upper bounds: one REDUX per column
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj)
               hw[jj] = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(hw[jj])));
+            const float4* H4 = reinterpret_cast<const float4*>(&S.H[c0]);
+            float T[16];
+#pragma unroll
+            for (int v4 = 0; v4 < 4; ++v4) {
+              // re-read every 16 columns: the tcgen05.ld above carries a memory clobber
+              const float4 h = H4[v4];
+              T[4 * v4 + 0] = h.x;
+              T[4 * v4 + 1] = h.y;
+              T[4 * v4 + 2] = h.z;
+              T[4 * v4 + 3] = h.w;
+            }
+            unsigned lower = 0, cand = 0;
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
-              const int j = c0 + jj;
-              if (j < nqg) {
-                const float T = fminf(fminf(S.thrd[j], fminf(S.H[j], hw[jj])),
-                                      dev::key_d2(*(volatile u64*)&lists[j * a.k]));
-                if (valid && !(lov[jj] > T)) {
-                  const int slotc = atomicAdd(&S.ncb, 1);
-                  if (slotc < kCandCap) {
-                    cb_pos[slotc] = (int)pos;
-                    cb_j[slotc] = j;
-                    cb_lo[slotc] = lov[jj];
-                  } else {
-                    const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
-                    atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
-                    atomicAdd(&S.rechecks, 1ull);
-                  }
-                }
-              }
+              if (hw[jj] < T[jj]) lower |= 1u << jj;
+              T[jj] = fminf(T[jj], hw[jj]);
+              if (valid && !(lov[jj] > T[jj])) cand |= 1u << jj;
             }
-            if (lane == 0) {
+            // a tighter upper bound is rare once the part is under way
+            if (lane == 0 && lower) {
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj)
-                if (c0 + jj < nqg) atomic_min_float_nonneg(&S.H[c0 + jj], hw[jj]);
+                if (lower & (1u << jj)) atomic_min_float_nonneg(&S.H[c0 + jj], hw[jj]);
+            }
+            if (__any_sync(0xffffffffu, cand != 0u)) {
+              while (cand) {
+                const int jj = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const int j = c0 + jj;
+                const int slotc = atomicAdd(&S.ncb, 1);
+                float lo_j = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                  if (u == jj) lo_j = lov[u];
+                if (slotc < kCandCap) {
+                  cb_pos[slotc] = (int)pos;
+                  cb_j[slotc] = j;
+                  cb_lo[slotc] = lo_j;
+                } else {
+                  const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+                  atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
+                  atomicAdd(&S.rechecks, 1ull);
+                }
+              }
             }
           }
         } else {
           // general k: immediate re-checks; warps 0-3 take turns inserting into
           // the lists (warps 4-7 only join the barriers)
+          const float xnorm = sqrtf(xn);
           for (int turn = 0; turn < 4; ++turn) {
             for (int c0 = 0; okw && warp < 4 && c0 < N; c0 += 16) {
               float d[16];
@@ -393,10 +513,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                 if (kq == 1 ? (turn != 0) : (turn != warp)) continue;
                 bool cand = false;
                 if (valid) {
-                  const float4 qc = S.qc[j];
-                  const float ap = qc.x + xn - 2.0f * d[jj];
-                  const float band = 2.0f * (cK * qc.y * xnorm + sm * (qc.y + xnorm)) + 1e-4f * (qc.x + xn);
-                  float T = qc.z;
+                  const float qss = S.qb[j].w, qm = S.qm[j];
+                  const float ap = qss + xn - 2.0f * d[jj];
+                  const float band = 2.0f * (cK * qm * xnorm + sm * (qm + xnorm)) + 1e-4f * (qss + xn);
+                  float T = S.thrd[j];
                   if (kq == 1)
                     T = fminf(T, dev::key_d2(*(volatile u64*)&lists[j * a.k]));
                   else if (S.cnt[j] == kq)
@@ -431,17 +551,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         }
         dev::tc_fence_before();
         mbar_arrive(&S.tempty[t]);
-        ++g;
         PROF_ADD(2);
       }
       epi_sync();
-      if (defer) {
+      if (split) {
         // deferred re-checks: only candidates whose lower bound still reaches the
         // part's final bound (round threshold, smallest upper bound, best exact)
         const int ncb = min(S.ncb, kCandCap);
         for (int e = tid; e < ncb; e += kEpi) {
           const int j = cb_j[e];
-          const float T = fminf(fminf(S.thrd[j], S.H[j]), dev::key_d2(*(volatile u64*)&lists[j * a.k]));
+          const float T = fminf(S.H[j], dev::key_d2(*(volatile u64*)&lists[j * a.k]));
           if (!(cb_lo[e] > T)) {
             const int64_t pos = cb_pos[e];
             const float d2 = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
@@ -491,14 +610,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
 
 int tc_group_size() { return kTcG; }
 
-size_t tc_scan_smem_bytes(int kp, int k) {
-  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)kTcG * kp * 2 + (size_t)kTcG * k * 8 +
+static size_t tc_dyn_smem(int kp, int k, int nbuf) {
+  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * kTcG * kp * 2 + (size_t)kTcG * k * 8 +
          (k == 1 ? (size_t)kCandCap * 12 : 0);
+}
+
+int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem) {
+  cudaFuncAttributes fa;
+  LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel));
+  for (int nbuf = 2; nbuf >= 1; --nbuf) {
+    const size_t dyn = tc_dyn_smem(kp, k, nbuf);
+    if (dyn + fa.sharedSizeBytes <= (size_t)smem_optin) {
+      if (smem) *smem = dyn;
+      return nbuf;
+    }
+  }
+  return 0;
+}
+
+void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, float4* Qk,
+                          cudaStream_t s) {
+  if (nq <= 0) return;
+  tc_query_prep_kernel<<<(nq + 7) / 8, 256, 0, s>>>(Q, nq, mp, kp, Qh, Qk);
+  LF_CHECK_LAUNCH();
 }
 
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s) {
-  const size_t smem = tc_scan_smem_bytes(a.kp, a.k);
+  const size_t smem = tc_dyn_smem(a.kp, a.k, a.nbuf);
   LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   tc_scan_kernel<<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
   LF_CHECK_LAUNCH();
