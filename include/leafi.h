@@ -114,16 +114,18 @@ leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info);
 /* Per-kernel device time, measured with CUDA events on the index's stream
  * around each launch while profiling is on (off by default; switching it
  * resets the totals).  Kinds: 0 leaf scan, 1 candidate merge, 2 bounds and
- * routes, 3 (reserved), 4 filter forward, 5 wave select. */
+ * routes, 3 (reserved), 4 filter forward, 5 wave select.  `level`: 0 off,
+ * 1 leaf-scan launches only (the cheapest, for timing a run), 2 every kind
+ * plus the tensor-core scan's phase counters. */
 enum { LEAFI_KERNEL_KINDS = 6 };
-leafi_status leafi_set_profiling(leafi_index* index, int32_t on);
+leafi_status leafi_set_profiling(leafi_index* index, int32_t level);
 leafi_status leafi_get_kernel_times(leafi_index* index, double* ms /* [6] */,
                                     int64_t* launches /* [6] */);
 /* Tensor-core scan phase cycles summed over blocks while profiling is on
  * (16 doubles): 0 item set-up, 1 wait for an accumulator, 2 epilogue, 3 flush
  * and emit (epilogue warp 0, lane 0); 4 wait for a free stage, 11 TMA issue
  * (the TMA thread); 5 wait for the query tile, 6 wait for a TMA load, 7 wait
- * for a free accumulator, 8 MMA issue (the MMA thread); 12 wait for a free
+ * for a free accumulator, 14 MMA issue, 8 commits (the MMA thread); 12 wait for a free
  * query tile, 13 gather (the query loader); 9 work items, 10 chunks read by
  * epilogue warp 0. */
 leafi_status leafi_get_scan_phases(leafi_index* index, double* cycles);

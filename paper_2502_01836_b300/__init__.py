@@ -177,8 +177,9 @@ def leafi_launch_count() -> int:
     return int(lib().leafi_launch_count())
 
 
-def leafi_set_profiling(index, on: bool):
-    _check(lib().leafi_set_profiling(index, 1 if on else 0))
+def leafi_set_profiling(index, level):
+    """0 off, 1 (or True) leaf-scan kernel times only, 2 every kernel kind and scan phases."""
+    _check(lib().leafi_set_profiling(index, int(level)))
 
 
 def leafi_get_kernel_times(index):
@@ -190,8 +191,8 @@ def leafi_get_kernel_times(index):
 
 
 SCAN_PHASES = ["item_setup", "wait_accumulator", "epilogue", "flush_emit", "wait_stage_free",
-               "wait_query_tile", "wait_tma", "wait_accumulator_free", "issue", "items", "chunks",
-               "tma_issue", "wait_tile_free", "gather"]
+               "wait_query_tile", "wait_tma", "wait_accumulator_free", "commit", "items", "chunks",
+               "tma_issue", "wait_tile_free", "gather", "mma_issue"]
 
 
 def leafi_get_scan_phases(index):

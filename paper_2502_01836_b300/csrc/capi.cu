@@ -210,24 +210,77 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-bool encode_xh_map(leafi_index* ix) {
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-          cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn) {
-    cudaGetLastError();
-    return false;
+// 2-D tiled TMA descriptor with 128-byte swizzle: `inner` elements per row
+// (row stride `row_bytes`), `outer` rows, boxes of box_inner x box_outer
+bool encode_2d(CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t inner, uint64_t outer,
+               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  static void* fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      fn = nullptr;
+      return false;
+    }
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)ix->kp, (cuuint64_t)ix->n};
-  const cuuint64_t strides[1] = {(cuuint64_t)ix->kp * 2};
-  const cuuint32_t box[2] = {64, 128};
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = reinterpret_cast<EncodeTiledFn>(fn)(
-      &ix->xh_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ix->Xh.p, dims, strides, box, estr,
-      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+// 2-D TMA descriptor of the float16 copy: dims {kp, n}, boxes of 64 x 128
+bool encode_xh_map(leafi_index* ix) {
+  return encode_2d(&ix->xh_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, ix->Xh.p, (uint64_t)ix->kp,
+                   (uint64_t)ix->n, (uint64_t)ix->kp * 2, 64, 128);
+}
+
+// ---------------------------------------------------------------- filters
+// The tensor-core forward (3xTF32) serves indexes on the tensor-core scan path
+// whose hidden width fits one MMA (h <= 256); the CUDA-core forward the rest.
+bool filter_tc(const leafi_index* ix) {
+  return ix->scan_path == 0 && ix->F > 0 && filter_tc_fits(ix->m, ix->h, ix->smem_optin);
+}
+
+// (re)build the tf32 weight planes after the weights changed
+void ensure_wsplit(leafi_index* ix) {
+  if (!filter_tc(ix) || !ix->ws_dirty) return;
+  const int hp = (ix->h + 15) / 16 * 16, Kq = (ix->m + 31) / 32 * 32;
+  float* Ws = ix->Ws.need((size_t)2 * ix->F * hp * Kq);
+  launch_wsplit(ix->W1t.p, ix->F, ix->m, ix->h, Ws, ix->stream);
+  if (!encode_2d(&ix->wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws, (uint64_t)Kq,
+                 (uint64_t)2 * ix->F * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp))
+    fail(LEAFI_ECUDA, "cannot encode the filter weight tensor map");
+  ix->ws_dirty = false;
+}
+
+// P[q][f] for nq queries (device rows of mp floats); `cap_rows` sizes the
+// scratch for later calls of up to that many queries
+void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_rows = 0) {
+  if (nq <= 0 || ix->F <= 0) return;
+  if (!filter_tc(ix)) {
+    launch_filter_forward(dQ, nq, ix->mp, ix->m, ix->F, ix->h, ix->W1t.p, ix->b1.p, ix->w2.p,
+                          ix->b2.p, P, ix->stream);
+    return;
+  }
+  if (ix->ws_dirty) fail(LEAFI_EINTERNAL, "filter weight planes are stale");
+  const int Kq = (ix->m + 31) / 32 * 32;
+  const int nqp = (nq + 127) / 128 * 128;
+  const int capp = (std::max(nq, cap_rows) + 127) / 128 * 128;
+  float* Qs = ix->sQs.need((size_t)2 * capp * Kq);
+  CUtensorMap qmap;
+  if (!encode_2d(&qmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Qs, (uint64_t)Kq, (uint64_t)2 * nqp,
+                 (uint64_t)Kq * 4, 32, 128))
+    fail(LEAFI_ECUDA, "cannot encode the query tensor map");
+  launch_filter_tc(qmap, ix->wmap, dQ, nq, ix->mp, ix->m, ix->F, ix->h, Qs, ix->b1.p, ix->w2.p,
+                   ix->b2.p, P, ix->sErr.p, ix->stream);
 }
 
 // One scan round: group pairs by leaf, scan, merge candidates into slots.
@@ -273,9 +326,11 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
   int32_t* nitems = ix->sNItems.need(1);
   const int nbuf = tq.Qh ? tc_nbuf(ix, kstride) : 0;
   const bool use_tc = nbuf > 0;
+  int32_t* item_leaf =
+      use_tc ? ix->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix->tree)) : nullptr;
   launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
                use_tc ? tc_group_size() : scan_group_size(), cnt, goff, ioff, grouped, nitems,
-               distinct_stat, s);
+               distinct_stat, s, item_leaf);
   const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
   if (use_tc) {
     TcScanArgs t;
@@ -296,13 +351,16 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.pairs = grouped;
     t.grp_off = goff;
     t.item_off = ioff;
+    t.item_leaf = item_leaf;
+    t.work = ix->sWork.need(1);
+    LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
     t.thr = thr;
     t.cand = cand;
     t.cand_cnt = cand_cnt;
     t.cand_cap = cap;
     t.err = ix->sErr.p;
     t.stat = recheck_stat;
-    t.prof = ix->profiling ? ix->scan_prof.p : nullptr;
+    t.prof = ix->profiling >= 2 ? ix->scan_prof.p : nullptr;
     ix->tick(0);
     launch_tc_scan(ix->xh_map, t, nitems, slot_k, grid, s);
     ix->tock();
@@ -437,6 +495,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
   if (any_filtered && (ix->nc == 0 || ix->F == 0))
     fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
+  if (any_filtered) ensure_wsplit(ix);
   leafi_search_stats st{};
   const int W = ix->wave;
   const int cap = std::max(W, 1) * max_parts(t) * kmax;
@@ -467,6 +526,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   float* out_d = ix->sOutD.need((size_t)qb * kmax);
   int32_t* ord = walk ? ix->sOrd.need((size_t)qb * L) : nullptr;
   int32_t* cursor = walk ? ix->sCursor.need(qb) : nullptr;
+  if (any_filtered && filter_tc(ix)) ix->sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
   TcQueries tq;
   if (ix->tc_ok && ix->scan_path == 0) {
     tq.Qh = ix->sQh.need((size_t)qb * ix->kp);
@@ -476,6 +536,10 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   ix->sGrpOff.need(L + 1);
   ix->sItemOff.need(L + 1);
   ix->sGrouped.need((size_t)qb * std::max(W, 1));
+  if (tq.Qh) {
+    ix->sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(t));
+    ix->sWork.need(1);
+  }
   ix->sNItems.need(1);
   ix->sP.need((size_t)qb * 2 * (ix->m + 1));
   if (t.type == LEAFI_DSTREE) {
@@ -528,8 +592,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     if (tq.Qh) launch_tc_query_prep(gQ, nb, ix->mp, ix->kp, tq.Qh, tq.Qk, s);
     if (use_f) {
       ix->tick(4);
-      launch_filter_forward(gQ, nb, ix->mp, ix->m, ix->F, ix->h, ix->W1t.p, ix->b1.p, ix->w2.p,
-                            ix->b2.p, P, s);
+      filter_forward(ix, gQ, nb, P, qb);
       ix->tock();
       launch_jpos(nb, dK, dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, jpos, s);
     }
@@ -617,7 +680,8 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       if (g.exec) cudaGraphExecDestroy(g.exec);
       for (cudaEvent_t e2 : g.ev) cudaEventDestroy(e2);
       ix->graphs.pop_back();
-      if (!ok) ix->graphs_ok = false;  // capture is not available here: stay eager
+      // a failure without a reallocation means capture is not available here
+      if (!ok && !stale) ix->graphs_ok = false;
       return nullptr;
     }
     return &g;
@@ -730,7 +794,11 @@ void leafi_index::drop_graphs() {
 }
 
 void leafi_index::tick(int kind) {
-  if (!profiling) return;
+  if (!profiling || (profiling == 1 && kind != 0)) {
+    ticked = false;
+    return;
+  }
+  ticked = true;
   if (capturing) {
     cudaEvent_t a, b;
     LF_CUDA(cudaEventCreate(&a));
@@ -752,7 +820,7 @@ void leafi_index::tick(int kind) {
 }
 
 void leafi_index::tock() {
-  if (!profiling) return;
+  if (!ticked) return;
   if (capturing) {
     LF_CUDA(cudaEventRecordWithFlags(capturing->ev.back(), stream, cudaEventRecordExternal));
     return;
@@ -962,7 +1030,7 @@ leafi_status leafi_set_profiling(leafi_index* index, int32_t on) {
     DeviceGuard dg(index->device);
     index->drop_graphs();
     index->settle();
-    index->profiling = on != 0;
+    index->profiling = on < 0 ? 0 : (on > 2 ? 2 : on);
     index->scan_prof.need(16);
     LF_CUDA(cudaMemset(index->scan_prof.p, 0, 16 * sizeof(unsigned long long)));
     for (int i = 0; i < 8; ++i) {
@@ -1138,6 +1206,7 @@ leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, i
     index->filter_leaf = fl;
     index->F = F;
     index->h = h;
+    index->ws_dirty = true;
     index->trained = false;
     index->nc = 0;
     index->nk = 0;
@@ -1179,8 +1248,8 @@ leafi_status leafi_filter_predict(leafi_index* index, const float* queries, int6
       const int nb = (int)std::min<int64_t>(4096, nq - b0);
       const float* dQ = stage_queries(index, queries + (size_t)b0 * index->m, nb, qtmp);
       float* P = index->sPred.need((size_t)nb * index->F);
-      launch_filter_forward(dQ, nb, index->mp, index->m, index->F, index->h, index->W1t.p,
-                            index->b1.p, index->w2.p, index->b2.p, P, index->stream);
+      ensure_wsplit(index);
+      filter_forward(index, dQ, nb, P);
       deliver(out + (size_t)b0 * index->F, P, (size_t)nb * index->F, index->stream);
     }
     LF_CUDA(cudaStreamSynchronize(index->stream));
@@ -1357,6 +1426,7 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     a.epochs_run = dep.need(F);
     a.best_val = dbv.need(F);
     launch_train(a, s);
+    index->ws_dirty = true;
     std::vector<int32_t> hep(F);
     std::vector<double> hbv(F);
     LF_CUDA(cudaMemcpyAsync(hep.data(), a.epochs_run, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
@@ -1404,8 +1474,8 @@ leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t n
     DBuf<int32_t> lk_cnt;
     leaf_knn_device(index, dQ, (int)nc, dl.p, L, kmax, lk_keys, lk_cnt);
     DBuf<float> P;
-    launch_filter_forward(dQ, (int)nc, index->mp, index->m, F, index->h, index->W1t.p, index->b1.p,
-                          index->w2.p, index->b2.p, P.need((size_t)nc * F), s);
+    ensure_wsplit(index);
+    filter_forward(index, dQ, (int)nc, P.need((size_t)nc * F));
     double* alpha = index->alpha.need((size_t)F * nc);
     double* qprime = index->qprime.need((size_t)nk * nc);
     DBuf<int32_t> ord, cnt_true;

@@ -113,6 +113,11 @@ void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double*
 void launch_isax_bounds(const IsaxTables& T, const double* P, int nq, int m, double* paa,
                         double* leaf_lb, int32_t* route, cudaStream_t s);
 
+bool filter_tc_fits(int m, int h, int smem_optin);
+void launch_wsplit(const float* W1t, int F, int m, int h, float* Ws, cudaStream_t s);
+void launch_filter_tc(const CUtensorMap& qmap, const CUtensorMap& wmap, const float* Q, int nq,
+                      int mp, int m, int F, int h, float* Qs, const float* b1, const float* w2,
+                      const float* b2, float* out, int32_t* err, cudaStream_t s);
 void launch_filter_forward(const float* Q, int nq, int mp, int m, int F, int h, const float* W1t,
                            const float* b1, const float* w2, const float* b2, float* out,
                            cudaStream_t s);
@@ -164,6 +169,8 @@ struct TcScanArgs {
   const Pair* pairs;
   const int32_t* grp_off;
   const int32_t* item_off;
+  const int32_t* item_leaf;        // leaf of every work item
+  int32_t* work;                   // work-item counter (zero at launch)
   const unsigned long long* thr;
   unsigned long long* cand;
   int32_t* cand_cnt;
@@ -188,7 +195,7 @@ void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* s
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
-                  unsigned long long* stat, cudaStream_t s);
+                  unsigned long long* stat, cudaStream_t s, int32_t* item_leaf = nullptr);
 
 void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
                   int32_t* topk_cnt, unsigned long long* thr, const unsigned long long* cand,
@@ -320,6 +327,12 @@ struct leafi_index {
   // scratch (grown on demand)
   leafi::DBuf<float> sQ;
   leafi::DBuf<__half> sQh;       // float16 queries of the tensor-core scan
+  leafi::DBuf<float> Ws;         // tf32 hi/lo weight planes of the tensor-core filter forward
+  CUtensorMap wmap;              // TMA descriptor of Ws
+  bool ws_dirty = true;          // weights changed since Ws was built
+  leafi::DBuf<float> sQs;        // tf32 hi/lo query planes
+  leafi::DBuf<int32_t> sItemLeaf; // leaf of every scan work item of a round
+  leafi::DBuf<int32_t> sWork;     // work-item counter of the tensor-core scan
   leafi::DBuf<float4> sQk;       // their band constants
   std::map<int, int> tc_plan;    // k -> query tiles of the tensor-core scan (0: does not fit)
   leafi::DBuf<double> sP, sIv, sNode, sLb, sPaa, sTarget;
@@ -332,7 +345,8 @@ struct leafi_index {
   leafi::DBuf<float> sPred, sOutD;
   leafi::DBuf<int64_t> sOutI;
 
-  bool profiling = false;
+  int profiling = 0;       // 0 off, 1 leaf-scan kernel times, 2 every kind + scan phases
+  bool ticked = false;     // the last tick() recorded a start event
   std::vector<leafi::BatchGraph> graphs;   // captured search batches
   cudaStream_t cap_stream = nullptr;       // private stream used only to capture them
   leafi::BatchGraph* capturing = nullptr;  // entry being captured (tick/tock record into it)

@@ -14,7 +14,9 @@ namespace {
 constexpr int kThreads = 128;
 
 // Per query: P1[i] = sum_{t<i} q_t, P2[i] = sum_{t<i} q_t^2 (float64, sequential).
-// One thread per query; the order of the additions is fixed.
+// One thread per query; the order of the additions is fixed.  The chains are
+// bound by float64 latency, so the kernel uses no shared memory and few
+// registers and can share SMs with a running leaf scan.
 __global__ void prefix_kernel(const float* __restrict__ Q, int nq, int mp, int m,
                               double* __restrict__ P) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,6 +107,34 @@ __global__ void ds_route_kernel(DsTables T, const double* __restrict__ ivstat, i
   for (int guard = 0; guard < T.n_nodes && T.node_leaf[v] < 0; ++guard) {
     const int iv = T.split_iv[v];
     const double val = T.split_sd[v] ? st[2 * iv + 1] : st[2 * iv];
+    v = (val < T.thresh[v]) ? T.left[v] : T.right[v];
+  }
+  route[q] = T.node_leaf[v];
+}
+
+// One block per query: the interval statistics go to global memory (for the
+// node bounds) and to shared memory, where one thread then walks the tree to
+// the query's route leaf without a global round trip per level.
+__global__ void ds_interval_route_kernel(DsTables T, const double* __restrict__ P, int nq, int m,
+                                         double* __restrict__ ivstat, int32_t* __restrict__ route) {
+  extern __shared__ double st_s[];  // [n_iv][2]
+  const int q = blockIdx.x;
+  const double* p1 = P + (size_t)q * 2 * (m + 1);
+  double* out = ivstat + (size_t)q * T.n_iv * 2;
+  for (int iv = threadIdx.x; iv < T.n_iv; iv += blockDim.x) {
+    double mu, sd;
+    interval_stat(p1, p1 + m + 1, T.iv_s[iv], T.iv_e[iv], mu, sd);
+    out[2 * iv] = mu;
+    out[2 * iv + 1] = sd;
+    st_s[2 * iv] = mu;
+    st_s[2 * iv + 1] = sd;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0 || !route) return;
+  int v = T.root;
+  for (int guard = 0; guard < T.n_nodes && T.node_leaf[v] < 0; ++guard) {
+    const int iv = T.split_iv[v];
+    const double val = T.split_sd[v] ? st_s[2 * iv + 1] : st_s[2 * iv];
     v = (val < T.thresh[v]) ? T.left[v] : T.right[v];
   }
   route[q] = T.node_leaf[v];
@@ -218,8 +248,14 @@ void launch_prefix(const float* Q, int nq, int mp, int m, double* P, cudaStream_
 void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double* ivstat,
                       double* node_lb, double* leaf_lb, int32_t* route, cudaStream_t s) {
   if (nq <= 0) return;
-  ds_interval_kernel<<<blocks_for((int64_t)nq * T.n_iv, kThreads), kThreads, 0, s>>>(T, P, nq, m,
-                                                                                    ivstat);
+  const size_t st_bytes = (size_t)T.n_iv * 2 * sizeof(double);
+  const bool fused = st_bytes <= 48 * 1024;
+  if (fused) {
+    ds_interval_route_kernel<<<nq, kThreads, st_bytes, s>>>(T, P, nq, m, ivstat, route);
+  } else {
+    ds_interval_kernel<<<blocks_for((int64_t)nq * T.n_iv, kThreads), kThreads, 0, s>>>(T, P, nq, m,
+                                                                                      ivstat);
+  }
   LF_CHECK_LAUNCH();
   ds_node_kernel<<<blocks_for((int64_t)nq * T.n_nodes, kThreads), kThreads, 0, s>>>(T, ivstat, nq,
                                                                                     node_lb);
@@ -227,7 +263,7 @@ void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double*
   ds_leaf_kernel<<<blocks_for((int64_t)nq * T.n_leaves, kThreads), kThreads, 0, s>>>(
       T, node_lb, nq, leaf_lb);
   LF_CHECK_LAUNCH();
-  if (route) {
+  if (route && !fused) {
     ds_route_kernel<<<blocks_for(nq, 64), 64, 0, s>>>(T, ivstat, nq, route);
     LF_CHECK_LAUNCH();
   }

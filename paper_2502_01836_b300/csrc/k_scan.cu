@@ -216,7 +216,8 @@ __global__ void count_kernel(const Pair* __restrict__ pairs, const int32_t* __re
 __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part, int g,
                                int32_t* __restrict__ cnt, int32_t* __restrict__ grp_off,
                                int32_t* __restrict__ item_off, int32_t* __restrict__ n_items,
-                               unsigned long long* __restrict__ stat) {
+                               unsigned long long* __restrict__ stat,
+                               int32_t* __restrict__ item_leaf) {
   __shared__ int s_a[1024], s_b[1024];
   const int T = blockDim.x;
   const int per = (L + T - 1) / T;
@@ -255,7 +256,10 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
     if (c > 0) {
       const int64_t size = leaf_off[l + 1] - leaf_off[l];
       const int parts = (int)((size + part - 1) / part);
-      rb += parts * ((c + g - 1) / g);
+      const int ni = parts * ((c + g - 1) / g);
+      if (item_leaf)
+        for (int i = 0; i < ni; ++i) item_leaf[rb + i] = l;
+      rb += ni;
     }
     cnt[l] = 0;  // reused as the scatter fill counter
   }
@@ -263,6 +267,75 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
     grp_off[L] = s_a[T - 1];
     item_off[L] = s_b[T - 1];
     *n_items = s_b[T - 1];
+  }
+}
+
+// count + offsets + scatter in one block for indexes of up to kFuseLeaves
+// leaves (the per-leaf counters live in shared memory)
+constexpr int kFuseLeaves = 8192;
+
+__global__ void __launch_bounds__(1024) group_fused_kernel(
+    const Pair* __restrict__ pairs, const int32_t* __restrict__ npairs, int L,
+    const int64_t* __restrict__ leaf_off, int part, int g, int32_t* __restrict__ grp_off,
+    int32_t* __restrict__ item_off, int32_t* __restrict__ n_items, Pair* __restrict__ grouped,
+    unsigned long long* __restrict__ stat, int32_t* __restrict__ item_leaf) {
+  __shared__ int cnt[kFuseLeaves];
+  __shared__ int s_a[1024], s_b[1024];
+  const int T = blockDim.x;
+  const int np = *npairs;
+  for (int l = threadIdx.x; l < L; l += T) cnt[l] = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += T) atomicAdd(&cnt[pairs[p].leaf], 1);
+  __syncthreads();
+  const int per = (L + T - 1) / T;
+  const int l0 = threadIdx.x * per, l1 = min(L, l0 + per);
+  int sa = 0, sb = 0;
+  unsigned long long distinct = 0;
+  for (int l = l0; l < l1; ++l) {
+    const int c = cnt[l];
+    sa += c;
+    if (c > 0) {
+      const int64_t size = leaf_off[l + 1] - leaf_off[l];
+      sb += (int)((size + part - 1) / part) * ((c + g - 1) / g);
+      distinct += (unsigned long long)size;
+    }
+  }
+  if (stat && distinct) atomicAdd(stat, distinct);
+  s_a[threadIdx.x] = sa;
+  s_b[threadIdx.x] = sb;
+  __syncthreads();
+  for (int off = 1; off < T; off <<= 1) {
+    const int va = threadIdx.x >= off ? s_a[threadIdx.x - off] : 0;
+    const int vb = threadIdx.x >= off ? s_b[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_a[threadIdx.x] += va;
+    s_b[threadIdx.x] += vb;
+    __syncthreads();
+  }
+  int ra = s_a[threadIdx.x] - sa, rb = s_b[threadIdx.x] - sb;
+  for (int l = l0; l < l1; ++l) {
+    const int c = cnt[l];
+    grp_off[l] = ra;
+    item_off[l] = rb;
+    cnt[l] = ra;  // becomes the leaf's fill cursor
+    ra += c;
+    if (c > 0) {
+      const int64_t size = leaf_off[l + 1] - leaf_off[l];
+      const int ni = (int)((size + part - 1) / part) * ((c + g - 1) / g);
+      if (item_leaf)
+        for (int i = 0; i < ni; ++i) item_leaf[rb + i] = l;
+      rb += ni;
+    }
+  }
+  if (threadIdx.x == T - 1) {
+    grp_off[L] = s_a[T - 1];
+    item_off[L] = s_b[T - 1];
+    *n_items = s_b[T - 1];
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += T) {
+    const Pair pr = pairs[p];
+    grouped[atomicAdd(&cnt[pr.leaf], 1)] = pr;
   }
 }
 
@@ -541,7 +614,10 @@ __global__ void fill_u64_kernel(u64* p, u64 v, size_t n) {
 __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double* __restrict__ target,
                             int nk, const int32_t* __restrict__ kclasses,
                             const double* __restrict__ qprime, int nc, int32_t* __restrict__ jpos) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per query; the table is read 32 entries at a time and the
+  // position is the entry before the first one below the target
+  const int q = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (q >= nq) return;
   const double t = target[q];
   int c = -1;
@@ -553,11 +629,17 @@ __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double*
   int j = -1;
   if (c >= 0 && t < 1.0) {
     const double* qp = qprime + (size_t)c * nc;
-    for (int i = 0; i < nc; ++i) {
-      if (qp[i] >= t) j = i; else break;
+    j = nc - 1;
+    for (int base = 0; base < nc; base += 32) {
+      const int i = base + lane;
+      const unsigned below = __ballot_sync(0xffffffffu, i < nc && !(qp[i] >= t));
+      if (below) {
+        j = base + __ffs(below) - 2;
+        break;
+      }
     }
   }
-  jpos[q] = j;
+  if (lane == 0) jpos[q] = j;
 }
 
 __global__ void write_results_kernel(int nq, int kmax, const int32_t* __restrict__ kq,
@@ -616,14 +698,20 @@ void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* s
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
-                  unsigned long long* stat, cudaStream_t s) {
+                  unsigned long long* stat, cudaStream_t s, int32_t* item_leaf) {
+  if (L <= kFuseLeaves) {
+    group_fused_kernel<<<1, 1024, 0, s>>>(pairs, npairs_dev, L, leaf_off, part, g, grp_off,
+                                          item_off, n_items_dev, grouped, stat, item_leaf);
+    LF_CHECK_LAUNCH();
+    return;
+  }
   LF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * L, s));
   if (npairs_max > 0) {
     count_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, cnt);
     LF_CHECK_LAUNCH();
   }
   offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, g, cnt, grp_off, item_off, n_items_dev,
-                                    stat);
+                                    stat, item_leaf);
   LF_CHECK_LAUNCH();
   if (npairs_max > 0) {
     scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
@@ -678,7 +766,7 @@ void launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cuda
 void launch_jpos(int nq, const int32_t* k, const double* target, int nk, const int32_t* kclasses,
                  const double* qprime, int nc, int32_t* jpos, cudaStream_t s) {
   if (nq <= 0) return;
-  jpos_kernel<<<nblk(nq, 128), 128, 0, s>>>(nq, k, target, nk, kclasses, qprime, nc, jpos);
+  jpos_kernel<<<nblk((int64_t)nq * 32, 256), 256, 0, s>>>(nq, k, target, nk, kclasses, qprime, nc, jpos);
   LF_CHECK_LAUNCH();
 }
 

@@ -50,6 +50,7 @@ constexpr int kAcc = 4;                   // TMEM accumulators of kTcG columns
 constexpr int kTmemCols = kAcc * kTcG;
 constexpr long long kWaitLimit = 1ll << 26;
 constexpr int kCandCap = 2048;    // deferred re-check buffer (k = 1 rounds)
+constexpr int kRing = 4;          // work items handed from the TMA thread to the other roles
 
 struct TcShared {
   u64 full[2];      // TMA of stage s landed (1 arrival + bytes)
@@ -58,6 +59,10 @@ struct TcShared {
   u64 tempty[kAcc]; // accumulator t read back by the epilogue threads
   u64 bready[2];    // query tile b gathered (32 arrivals of the loader warp)
   u64 bempty[2];    // MMAs reading query tile b finished (tcgen05.commit)
+  u64 iready[kRing];  // ring slot holds the next work item (TMA thread)
+  u64 ifree[kRing];   // ring slot read by the loader, the MMA thread and the epilogue
+  int ring[kRing];    // work item index, -1 = no more work
+  int eitem;          // epilogue's current item (broadcast through shared memory)
   uint32_t tmem_base;
   int abort;
   int stop;            // epilogue warps' uniform snapshot of `abort`
@@ -73,7 +78,7 @@ struct TcShared {
 
 // optional per-phase cycle counters (TcScanArgs::prof, 16 entries):
 // epilogue warp 0 lane 0: 0 item set-up, 1 wait accumulator, 2 epilogue, 3 flush+emit;
-// MMA thread: 5 wait query tile, 6 wait TMA, 7 wait accumulator free, 8 MMA issue;
+// MMA thread: 5 wait query tile, 6 wait TMA, 7 wait accumulator free, 14 MMA issue, 8 commits;
 // load thread: 4 wait stage free, 11 TMA issue; 9 items, 10 chunks (of warp 0);
 // query loader lane 0: 12 wait tile free, 13 gather
 #define PROF_T0() long long _pt = clock64()
@@ -91,12 +96,7 @@ struct Item {
 };
 
 __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
-  int lo = 0, hi = a.L - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
-  }
-  const int leaf = lo;
+  const int leaf = a.item_leaf[item];
   const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
   const int ngroups = (cnt + kTcG - 1) / kTcG;
   const int local = item - a.item_off[leaf];
@@ -109,6 +109,27 @@ __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
   it.pr = a.pairs + a.grp_off[leaf] + grp * kTcG;
   it.nchunks = (int)((it.p1 - it.p0 + kTcRows - 1) / kTcRows);
   return it;
+}
+
+// One chunk's MMAs (KS steps of K = 16), fully unrolled: the descriptors'
+// upper words are fixed, the lower words advance by constants (start address
+// in 16-byte units: +32 bytes per step inside a 128-byte swizzled row of A and
+// +16 KB per 64-column block; +256 bytes per step of the no-swizzle B), so the
+// issuing thread spends a few instructions per MMA.
+template <int KS>
+__device__ __forceinline__ void issue_chunk(uint32_t dt, uint32_t a_lo, uint32_t a_hi,
+                                            uint32_t b_lo, uint32_t b_hi, uint32_t idesc) {
+#pragma unroll
+  for (int kk = 0; kk < KS; ++kk) {
+    const uint32_t ao = a_lo + (uint32_t)((kk >> 2) * 1024 + (kk & 3) * 2);
+    const uint32_t bo = b_lo + (uint32_t)(kk * 16);
+    const uint32_t acc = kk > 0 ? 1u : 0u;
+    asm volatile(
+        "{\n.reg .b64 ad, bd;\n.reg .pred p;\nmov.b64 ad, {%1, %2};\nmov.b64 bd, {%3, %4};\n"
+        "setp.ne.b32 p, %6, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n}\n" ::"r"(dt),
+        "r"(ao), "r"(a_hi), "r"(bo), "r"(b_hi), "r"(idesc), "r"(acc)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void atomic_min_float_nonneg(float* p, float v) {
@@ -130,6 +151,53 @@ __device__ __forceinline__ bool wait_phase(u64* mbar, uint32_t parity, volatile 
     if (*abort) return false;
   }
   return false;
+}
+
+// Canonical squared distance (the same operations in the same order as
+// dev::canonical_d2) computed by a whole warp: lane l loads float4 words l and
+// l + 32 of both rows, the differences are broadcast in order by shuffles.
+// Rows of up to 64 float4 words (m <= 256, the tensor-core scan's limit).
+__device__ __forceinline__ float warp_canonical_d2(const float4* __restrict__ q,
+                                                   const float4* __restrict__ x, int m4, int lane) {
+  float4 t[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = lane + 32 * h;
+    t[h] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (c < m4) {
+      const float4 a = q[c], b = x[c];
+      t[h] = make_float4(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z),
+                         __fsub_rn(a.w, b.w));
+    }
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int cnt = min(32, m4 - 32 * h);
+    for (int u = 0; u < cnt; ++u) {
+      const float tx = __shfl_sync(0xffffffffu, t[h].x, u);
+      const float ty = __shfl_sync(0xffffffffu, t[h].y, u);
+      const float tz = __shfl_sync(0xffffffffu, t[h].z, u);
+      const float tw = __shfl_sync(0xffffffffu, t[h].w, u);
+      acc = __fmaf_rn(tx, tx, acc);
+      acc = __fmaf_rn(ty, ty, acc);
+      acc = __fmaf_rn(tz, tz, acc);
+      acc = __fmaf_rn(tw, tw, acc);
+    }
+  }
+  return acc;
+}
+
+// Work items are claimed dynamically: the TMA thread takes the next index
+// from a global counter (one item ahead of the one it is loading) and hands
+// it to the other roles through a ring of kRing slots, so every role of the
+// CTA walks the same sequence and CTAs that finish early take more work.
+__device__ __forceinline__ int ring_take(TcShared& S, int n, volatile int* abort) {
+  const int s = n % kRing;
+  const bool ok = wait_phase(&S.iready[s], (uint32_t)((n / kRing) & 1), abort);
+  const int item = ok ? *reinterpret_cast<volatile int*>(&S.ring[s]) : -1;
+  mbar_arrive(&S.ifree[s]);
+  return item;
 }
 
 // Band constants of one query (fp16 operands over Kp columns, mp-float rows):
@@ -214,6 +282,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       dev::mbar_init(&S.bready[i], 32);
       dev::mbar_init(&S.bempty[i], 1);
     }
+    for (int i = 0; i < kRing; ++i) {
+      dev::mbar_init(&S.iready[i], 1);
+      dev::mbar_init(&S.ifree[i], 3);
+    }
     for (int i = 0; i < kAcc; ++i) {
       dev::mbar_init(&S.tfull[i], 1);
       dev::mbar_init(&S.tempty[i], split ? kEpi / 2 : kEpi);
@@ -235,13 +307,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                        (tid == 0 || tid == kLoadWarp * 32 || tid == kMmaWarp * 32 || tid == kQueryWarp * 32);
 
   if (warp == kLoadWarp) {
-    // ------------------------------------------------ TMA producer
+    // ------------------------------------------------ TMA producer + item scheduler
     if (lane == 0) {
       PROF_T0();
       long long g_ld = 0;
       uint32_t empty_ph[2] = {0u, 0u};
-      for (int item = blockIdx.x; item < n_items && !*abort; item += gridDim.x) {
-        const Item I = decode_item(a, item);
+      bool alive = true;
+      auto publish = [&](int n) -> int {
+        const int sl = n % kRing;
+        if (n >= kRing && !wait_phase(&S.ifree[sl], (uint32_t)((n / kRing - 1) & 1), abort)) {
+          atomicOr(a.err, 2);
+          S.abort = 1;
+          alive = false;
+          return -1;
+        }
+        int item = atomicAdd(a.work, 1);
+        if (item >= n_items) item = -1;
+        S.ring[sl] = item;
+        mbar_arrive(&S.iready[sl]);
+        return item;
+      };
+      int cur = publish(0);
+      for (int n = 0; cur >= 0 && alive && !*abort; ++n) {
+        const int nxt = publish(n + 1);
+        const Item I = decode_item(a, cur);
         for (int c = 0; c < I.nchunks; ++c) {
           const int st = (int)(g_ld & 1);
           if (g_ld >= 2) {
@@ -249,7 +338,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
             const bool ok = wait_phase(&S.empty[st], empty_ph[st], abort);
             empty_ph[st] ^= 1u;
             PROF_ADD(4);
-            if (!ok) break;
+            if (!ok) {
+              atomicOr(a.err, 2);
+              S.abort = 1;
+              break;
+            }
           }
           unsigned char* dst = st ? A1 : A0;
           const int r0 = (int)(I.p0 + (int64_t)c * kTcRows);
@@ -258,6 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
             dev::tma_load_2d(dst + kb * 16384, &tmap, kb * 64, r0, &S.full[st]);
           ++g_ld;
         }
+        cur = nxt;
       }
       PROF_ADD(11);
     }
@@ -268,8 +362,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     uint32_t bempty_ph[2] = {0u, 0u};
     int li = 0;
     const int pieces = Kp / 8;                 // 16-byte pieces per query row
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++li) {
-      if (__shfl_sync(0xffffffffu, *abort, 0)) break;
+    for (;; ++li) {
+      int item = -1;
+      if (lane == 0) item = ring_take(S, li, abort);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item < 0) break;
       const Item I = decode_item(a, item);
       const int b = li % nbuf;
       if (li >= nbuf) {
@@ -329,7 +426,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                                  dev::smem_desc(dev::smem_addr(A1), 16, 1024, 2)};
       const uint64_t bdesc[2] = {dev::smem_desc(dev::smem_addr(B0), 128, sbo),
                                  dev::smem_desc(dev::smem_addr(B1), 128, sbo)};
-      for (int item = blockIdx.x; item < n_items && !*abort; item += gridDim.x, ++li) {
+      for (;; ++li) {
+        const int item = ring_take(S, li, abort);
+        if (item < 0) break;
         const Item I = decode_item(a, item);
         const int b = li % nbuf;
         bool ok = wait_phase(&S.bready[b], bready_ph[b], abort);
@@ -353,9 +452,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           // +256 bytes per K step (B, two core matrices)
           const uint64_t ad = adesc[st], bd = bdesc[b];
           const uint32_t dt = tmem + (uint32_t)(t * kTcG);
-          for (int kk = 0; kk < Kp / 16; ++kk)
-            dev::mma_f16(dt, ad + (uint64_t)((kk >> 2) * 1024 + (kk & 3) * 2), bd + (uint64_t)(kk * 16),
-                         idesc, kk > 0 ? 1u : 0u);
+          const uint32_t alo = (uint32_t)ad, ahi = (uint32_t)(ad >> 32);
+          const uint32_t blo = (uint32_t)bd, bhi = (uint32_t)(bd >> 32);
+          switch (Kp) {
+            case 64: issue_chunk<4>(dt, alo, ahi, blo, bhi, idesc); break;
+            case 128: issue_chunk<8>(dt, alo, ahi, blo, bhi, idesc); break;
+            case 192: issue_chunk<12>(dt, alo, ahi, blo, bhi, idesc); break;
+            default: issue_chunk<16>(dt, alo, ahi, blo, bhi, idesc); break;
+          }
+          PROF_ADD(14);
           dev::mma_commit(&S.empty[st]);
           dev::mma_commit(&S.tfull[t]);
           ++g_mm;
@@ -382,7 +487,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     uint32_t tfull_ph[kAcc] = {0u, 0u, 0u, 0u};
     long long g = 0;
     PROF_T0();
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    for (int n = 0;; ++n) {
+      if (tid == 0) S.eitem = ring_take(S, n, abort);
+      epi_sync();
+      const int item = S.eitem;
+      if (item < 0) break;
       const Item I = decode_item(a, item);
       const int nqg = I.nqg, N = I.N;
       if (prof_on) pr[9] += 1;
@@ -489,6 +598,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                   cb_pos[slotc] = (int)pos;
                   cb_j[slotc] = j;
                   cb_lo[slotc] = lo_j;
+                  // the float32 row is re-read at the end of the item: start it now
+                  const char* row = reinterpret_cast<const char*>(X4 + (size_t)pos * m4);
+                  for (int o = 0; o < m4 * 16; o += 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + o));
                 } else {
                   const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
                   atomicMin(&lists[j * a.k], dev::make_key(e, (uint32_t)a.ids[pos]));
@@ -557,15 +670,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       if (split) {
         // deferred re-checks: only candidates whose lower bound still reaches the
         // part's final bound (round threshold, smallest upper bound, best exact)
+        // one warp per candidate: the lanes load the two rows, the chain of
+        // fused multiply-adds runs in the canonical order on shuffled values
         const int ncb = min(S.ncb, kCandCap);
-        for (int e = tid; e < ncb; e += kEpi) {
+        for (int e = warp; e < ncb; e += kEpiWarps) {
           const int j = cb_j[e];
           const float T = fminf(S.H[j], dev::key_d2(*(volatile u64*)&lists[j * a.k]));
           if (!(cb_lo[e] > T)) {
             const int64_t pos = cb_pos[e];
-            const float d2 = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
-            atomicMin(&lists[j * a.k], dev::make_key(d2, (uint32_t)a.ids[pos]));
-            atomicAdd(&S.rechecks, 1ull);
+            const float d2 = warp_canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4, lane);
+            if (lane == 0) {
+              atomicMin(&lists[j * a.k], dev::make_key(d2, (uint32_t)a.ids[pos]));
+              atomicAdd(&S.rechecks, 1ull);
+            }
           }
         }
         epi_sync();

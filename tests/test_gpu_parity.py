@@ -135,6 +135,28 @@ def test_filter_predictions_within_tolerance(ds):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("path", [0, 1])
+def test_filter_forward_paths_ragged(path):
+    """Tensor-core (3xTF32) and CUDA-core forwards on a ragged shape: m = 100
+    (K padded to 128), h = 100 (N padded to 112), 300 queries (three 128-row
+    tiles, the last partial); re-installing weights rebuilds the tf32 planes."""
+    m, h, F, nq = 100, 100, 5, 300
+    X = fx.random_walk(3000, m, seed=61)
+    Q = fx.test_queries(X, nq, seed=62)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=300, wave=2, device=0, scan_path=path))
+    try:
+        fl = np.arange(F, dtype=np.int32)
+        for seed in (63, 64):
+            W = fx.filter_init(F, m, h, seed=seed)
+            lf.leafi_set_filters(idx, fl, *W)
+            P = np.zeros((nq, F), np.float32)
+            lf.leafi_filter_predict(idx, Q, P)
+            ref = O.mlp_forward(*W, Q)
+            assert (np.abs(P - ref) <= 1e-5 * _pred_scale(W, Q)).all(), seed
+    finally:
+        lf.leafi_free(idx)
+
+
 def test_one_epoch_of_sgd_matches_oracle(ds):
     X, Q, idx, t = ds
     F = 4
