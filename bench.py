@@ -38,7 +38,7 @@ FP32_LANES = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="leafi", choices=["leafi", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
@@ -74,12 +74,13 @@ class Clocks:
         self.device = device
         self.proc = None
         self.lines = []
+        self.nearest = False
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -89,7 +90,18 @@ class Clocks:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0, t1):
+        """Keep the samples that arrived in [t0, t1] (plus one sampling period);
+        if none did, the nearest sample on either side."""
+        inside = [x for x in self.lines if t0 <= x[0] <= t1 + 0.1]
+        if not inside and self.lines:
+            before = [x for x in self.lines if x[0] < t0][-1:]
+            after = [x for x in self.lines if x[0] > t1][:1]
+            inside = before + after
+            self.nearest = True
+        self.lines = inside
 
     def __exit__(self, *a):
         if self.proc:
@@ -102,7 +114,7 @@ class Clocks:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -114,8 +126,11 @@ class Clocks:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if self.nearest:
+            out["note"] = "timed region shorter than the sampling period: nearest samples"
+        return out
 
 
 def dist_setup(gpus):
@@ -244,9 +259,12 @@ def main():
     ex_ids = torch.empty_like(ids)
     ex_d = torch.empty_like(dd)
 
-    def run(target, out_i, out_d, lat=None, stats=None):
-        for b in range(nl):
-            s0, s1 = b * a.launch, min(a.queries, (b + 1) * a.launch)
+    def run(target, out_i, out_d, lat=None, stats=None, per_launch=False):
+        # one call over all queries (the library runs them in launches of
+        # a.launch, two in flight), or one call per launch for the latencies
+        spans = ([(b * a.launch, min(a.queries, (b + 1) * a.launch)) for b in range(nl)]
+                 if per_launch else [(0, a.queries)])
+        for s0, s1 in spans:
             st = lf.SearchStats()
             if lat is not None:
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -261,6 +279,7 @@ def main():
                     stats[f] = stats.get(f, 0) + getattr(st, f)
 
     def timed(target, out_i, out_d, profile=False):
+        ck = Clocks(local).__enter__()   # sampling starts before the warm-up
         for _ in range(a.warmup):
             run(target, out_i, out_d)
         if profile:
@@ -269,22 +288,29 @@ def main():
         barrier(dist)
         torch.cuda.synchronize()
         launches0 = lf.leafi_launch_count()
-        with Clocks(local) as ck:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.nvtx.range_push("timed_leafi" if target < 1.0 else "timed_plain")
-            e0.record(stream)
-            for _ in range(a.steps):
-                run(target, out_i, out_d, lat, stats)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            torch.cuda.nvtx.range_pop()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_leafi" if target < 1.0 else "timed_plain")
+        t_0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(a.steps):
+            run(target, out_i, out_d, None, stats)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_1 = time.perf_counter()
+        torch.cuda.nvtx.range_pop()
+        time.sleep(0.15)
+        ck.__exit__()
+        ck.mark(t_0, t_1)
         barrier(dist)
         launches = lf.leafi_launch_count() - launches0
         ms = e0.elapsed_time(e1) / a.steps
         kt = lf.leafi_get_kernel_times(idx) if profile else None
         if profile:
             lf.leafi_set_profiling(idx, 0)
+        # latency of one launch-sized call (a request of a.launch queries), untimed pass
+        run(target, out_i, out_d, lat, None, per_launch=True)
+        torch.cuda.synchronize()
         lats = [x.elapsed_time(y) for x, y in lat]
         return ms, lats, stats, launches, ck.summary(), kt
 
@@ -304,17 +330,16 @@ def main():
     value = world * a.queries / (ms_max / 1e3)
     value_ex = world * a.queries / (ms_ex_max / 1e3)
 
-    # end to end through the public API with host buffers (copies inside the timed region)
-    Qh = Q.copy()
-    ih = np.zeros((a.queries, 1), np.int64)
-    dh = np.zeros((a.queries, 1), np.float32)
-    lf.leafi_search(idx, Qh[:a.launch], 1, a.target, ih[:a.launch], dh[:a.launch])
+    # end to end through the public API with pinned host buffers (the copies run
+    # inside the timed region, overlapped with the other lane's work)
+    Qh = torch.from_numpy(Q).pin_memory()
+    ih = torch.zeros((a.queries, 1), dtype=torch.int64).pin_memory()
+    dh = torch.zeros((a.queries, 1), dtype=torch.float32).pin_memory()
+    lf.leafi_search(idx, Qh, 1, a.target, ih, dh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        for b in range(nl):
-            s0, s1 = b * a.launch, min(a.queries, (b + 1) * a.launch)
-            lf.leafi_search(idx, Qh[s0:s1], 1, a.target, ih[s0:s1], dh[s0:s1])
+        lf.leafi_search(idx, Qh, 1, a.target, ih, dh)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / a.steps, dist, dev)
     e2e = {"value": world * a.queries / (e2e_ms / 1e3), "unit": "queries/s",

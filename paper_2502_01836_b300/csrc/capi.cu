@@ -274,7 +274,7 @@ void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_
   const int Kq = (ix->m + 31) / 32 * 32;
   const int nqp = (nq + 127) / 128 * 128;
   const int capp = (std::max(nq, cap_rows) + 127) / 128 * 128;
-  float* Qs = ix->sQs.need((size_t)2 * capp * Kq);
+  float* Qs = ix->sc->sQs.need((size_t)2 * capp * Kq);
   CUtensorMap qmap;
   if (!encode_2d(&qmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Qs, (uint64_t)Kq, (uint64_t)2 * nqp,
                  (uint64_t)Kq * 4, 32, 128))
@@ -303,8 +303,8 @@ struct TcQueries {
 TcQueries prep_tc_queries(leafi_index* ix, const float* dQ, int nq, int cap_rows) {
   TcQueries r;
   if (!ix->tc_ok || ix->scan_path != 0) return r;
-  __half* Qh = ix->sQh.need((size_t)std::max(nq, cap_rows) * ix->kp);
-  float4* Qk = ix->sQk.need((size_t)2 * std::max(nq, cap_rows));
+  __half* Qh = ix->sc->sQh.need((size_t)std::max(nq, cap_rows) * ix->kp);
+  float4* Qk = ix->sc->sQk.need((size_t)2 * std::max(nq, cap_rows));
   launch_tc_query_prep(dQ, nq, ix->mp, ix->kp, Qh, Qk, ix->stream);
   r.Qh = Qh;
   r.Qk = Qk;
@@ -319,15 +319,15 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
                unsigned long long* recheck_stat = nullptr) {
   cudaStream_t s = ix->stream;
   const int L = ix->tree.n_leaves;
-  int32_t* cnt = ix->sCnt.need(L);
-  int32_t* goff = ix->sGrpOff.need(L + 1);
-  int32_t* ioff = ix->sItemOff.need(L + 1);
-  Pair* grouped = ix->sGrouped.need(std::max(npairs_max, 1));
-  int32_t* nitems = ix->sNItems.need(1);
+  int32_t* cnt = ix->sc->sCnt.need(L);
+  int32_t* goff = ix->sc->sGrpOff.need(L + 1);
+  int32_t* ioff = ix->sc->sItemOff.need(L + 1);
+  Pair* grouped = ix->sc->sGrouped.need(std::max(npairs_max, 1));
+  int32_t* nitems = ix->sc->sNItems.need(1);
   const int nbuf = tq.Qh ? tc_nbuf(ix, kstride) : 0;
   const bool use_tc = nbuf > 0;
   int32_t* item_leaf =
-      use_tc ? ix->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix->tree)) : nullptr;
+      use_tc ? ix->sc->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix->tree)) : nullptr;
   launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
                use_tc ? tc_group_size() : scan_group_size(), cnt, goff, ioff, grouped, nitems,
                distinct_stat, s, item_leaf);
@@ -352,7 +352,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.grp_off = goff;
     t.item_off = ioff;
     t.item_leaf = item_leaf;
-    t.work = ix->sWork.need(1);
+    t.work = ix->sc->sWork.need(1);
     LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
     t.thr = thr;
     t.cand = cand;
@@ -409,14 +409,14 @@ void check_err_word(leafi_index* ix) {
 void compute_bounds(leafi_index* ix, const float* dQ, int nq, double* lb2, int32_t* route) {
   cudaStream_t s = ix->stream;
   const HostTree& t = ix->tree;
-  double* P = ix->sP.need((size_t)nq * 2 * (ix->m + 1));
+  double* P = ix->sc->sP.need((size_t)nq * 2 * (ix->m + 1));
   launch_prefix(dQ, nq, ix->mp, ix->m, P, s);
   if (t.type == LEAFI_DSTREE) {
-    double* iv = ix->sIv.need((size_t)nq * t.iv_s.size() * 2);
-    double* nodes = ix->sNode.need((size_t)nq * t.n_nodes);
+    double* iv = ix->sc->sIv.need((size_t)nq * t.iv_s.size() * 2);
+    double* nodes = ix->sc->sNode.need((size_t)nq * t.n_nodes);
     launch_ds_bounds(ix->ds(), P, nq, ix->m, iv, nodes, lb2, route, s);
   } else {
-    double* paa = ix->sPaa.need((size_t)nq * t.w);
+    double* paa = ix->sc->sPaa.need((size_t)nq * t.w);
     launch_isax_bounds(ix->isax(), P, nq, ix->m, paa, lb2, route, s);
   }
 }
@@ -430,8 +430,8 @@ void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dL
   const int cap = max_parts(ix->tree) * k;
   topk.need((size_t)nslots * k);
   topk_cnt.need(nslots);
-  unsigned long long* thr = ix->sThr.need(nslots);
-  int32_t* cand_cnt = ix->sCandCnt.need(nslots);
+  unsigned long long* thr = ix->sc->sThr.need(nslots);
+  int32_t* cand_cnt = ix->sc->sCandCnt.need(nslots);
   if (nslots == 0) return;
   slots_init_kernel<<<(nslots + 255) / 256, 256, 0, s>>>(nslots, topk_cnt.p, thr, cand_cnt);
   LF_CHECK_LAUNCH();
@@ -439,9 +439,9 @@ void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dL
   const size_t per_query = (size_t)nl * cap * sizeof(unsigned long long);
   int qb = (int)std::max<size_t>(1, kKnnBudget / std::max<size_t>(per_query, 1));
   qb = std::min(qb, nq);
-  unsigned long long* cand = ix->sCand.need((size_t)qb * nl * cap);
-  Pair* pairs = ix->sPairs.need((size_t)qb * nl);
-  int32_t* np = ix->sNpairs.need(1);
+  unsigned long long* cand = ix->sc->sCand.need((size_t)qb * nl * cap);
+  Pair* pairs = ix->sc->sPairs.need((size_t)qb * nl);
+  int32_t* np = ix->sc->sNpairs.need(1);
   const TcQueries tq = prep_tc_queries(ix, dQ, nq, 0);
   for (int q0 = 0; q0 < nq; q0 += qb) {
     const int nb = std::min(qb, nq - q0);
@@ -476,7 +476,6 @@ void check_queries(const leafi_index* ix, const float* q, int64_t nq) {
   (void)ix;
 }
 
-// the search driver shared by leafi_search / _exact / _mixed
 __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, double tval) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nb) {
@@ -485,11 +484,38 @@ __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, 
   }
 }
 
-// the search driver shared by leafi_search / _exact / _mixed
+// Device pointers of one lane's batch scratch, sized for a full batch.
+struct LaneView {
+  float* gQ;
+  int32_t *dK, *jpos, *route, *topk_cnt, *cand_cnt, *cur_leaf, *done, *np, *ord, *cursor;
+  double *dT, *lb2, *cur_lb;
+  float *P, *out_d;
+  unsigned char* scanned;
+  unsigned long long *topk, *thr, *cand;
+  Pair* pairs;
+  int64_t* out_i;
+  TcQueries tq;
+};
+
+// one batch in flight on a lane
+struct InFlight {
+  bool active = false;
+  int64_t b0 = 0;
+  int nb = 0;
+  bool use_f = false;
+  BatchGraph* g = nullptr;
+  int waves = 0;
+};
+
+// The search driver shared by leafi_search / _exact / _mixed (Alg. 2 over
+// batches of kBatch queries).  Batches alternate between two lanes, each
+// with its own scratch and stream, so the preparation of one batch (bounds,
+// filters, leaf order) and the host's wait for its wave count overlap the
+// other batch's scan.  A full batch replays a captured graph of its first two
+// waves; later waves are enqueued as the host learns that pairs remain.
 void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::vector<int32_t>& kq,
                  const std::vector<double>& target, int kmax, int64_t* ids, float* dists,
                  leafi_search_stats* stats) {
-  cudaStream_t s = ix->stream;  // swapped for the capture stream while capturing
   const HostTree& t = ix->tree;
   const int L = t.n_leaves;
   const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
@@ -501,165 +527,199 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   const int cap = std::max(W, 1) * max_parts(t) * kmax;
   const int qb = kBatch;
   const bool walk = L <= calib_max_sort();
+  const int nlanes = nq > qb ? 2 : 1;
+  const cudaStream_t user = ix->stream;
+  // every entry point after this one runs on lanes[0] and the caller's stream
+  struct Restore {
+    leafi_index* ix;
+    cudaStream_t user;
+    ~Restore() {
+      ix->sc = &ix->lanes[0];
+      ix->stream = user;
+      ix->capturing = nullptr;
+    }
+  } restore{ix, user};
+
   // every buffer a batch touches is sized for a full batch up front, so a
   // captured batch never sees a reallocation while it is replayed
-  float* gQ = ix->sQ.need((size_t)qb * ix->mp);
-  int32_t* dK = ix->sK.need(qb);
-  double* dT = ix->sTarget.need(qb);
-  int32_t* jpos = ix->sJpos.need(qb);
-  double* lb2 = ix->sLb.need((size_t)qb * L);
-  int32_t* route = ix->sRoute.need(qb);
-  float* P = ix->F ? ix->sPred.need((size_t)qb * ix->F) : nullptr;
-  unsigned char* scanned = ix->sScanned.need((size_t)qb * L);
-  unsigned long long* topk = ix->sTopk.need((size_t)qb * kmax);
-  int32_t* topk_cnt = ix->sTopkCnt.need(qb);
-  unsigned long long* thr = ix->sThr.need(qb);
-  unsigned long long* cand = ix->sCand.need((size_t)qb * cap);
-  int32_t* cand_cnt = ix->sCandCnt.need(qb);
-  double* cur_lb = ix->sCurLb.need(qb);
-  int32_t* cur_leaf = ix->sCurLeaf.need(qb);
-  int32_t* done = ix->sDone.need(qb);
-  Pair* pairs = ix->sPairs.need((size_t)qb * std::max(W, 1));
-  int32_t* np = ix->sNpairs.need(1);
+  LaneView lv[2];
+  for (int li = 0; li < nlanes; ++li) {
+    Scratch& S = ix->lanes[li];
+    if (!S.st) {
+      LF_CUDA(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking));
+      LF_CUDA(cudaEventCreateWithFlags(&S.ev_np, cudaEventDisableTiming));
+      LF_CUDA(cudaMallocHost(&S.h_np, sizeof(int32_t)));
+    }
+    LaneView& v = lv[li];
+    v.gQ = S.sQ.need((size_t)qb * ix->mp);
+    v.dK = S.sK.need(qb);
+    v.dT = S.sTarget.need(qb);
+    v.jpos = S.sJpos.need(qb);
+    v.lb2 = S.sLb.need((size_t)qb * L);
+    v.route = S.sRoute.need(qb);
+    v.P = ix->F ? S.sPred.need((size_t)qb * ix->F) : nullptr;
+    v.scanned = S.sScanned.need((size_t)qb * L);
+    v.topk = S.sTopk.need((size_t)qb * kmax);
+    v.topk_cnt = S.sTopkCnt.need(qb);
+    v.thr = S.sThr.need(qb);
+    v.cand = S.sCand.need((size_t)qb * cap);
+    v.cand_cnt = S.sCandCnt.need(qb);
+    v.cur_lb = S.sCurLb.need(qb);
+    v.cur_leaf = S.sCurLeaf.need(qb);
+    v.done = S.sDone.need(qb);
+    v.pairs = S.sPairs.need((size_t)qb * std::max(W, 1));
+    v.np = S.sNpairs.need(1);
+    v.out_i = S.sOutI.need((size_t)qb * kmax);
+    v.out_d = S.sOutD.need((size_t)qb * kmax);
+    v.ord = walk ? S.sOrd.need((size_t)qb * L) : nullptr;
+    v.cursor = walk ? S.sCursor.need(qb) : nullptr;
+    if (any_filtered && filter_tc(ix)) S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
+    v.tq = TcQueries();
+    if (ix->tc_ok && ix->scan_path == 0) {
+      v.tq.Qh = S.sQh.need((size_t)qb * ix->kp);
+      v.tq.Qk = S.sQk.need((size_t)2 * qb);
+      S.sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(t));
+      S.sWork.need(1);
+    }
+    S.sCnt.need(L);
+    S.sGrpOff.need(L + 1);
+    S.sItemOff.need(L + 1);
+    S.sGrouped.need((size_t)qb * std::max(W, 1));
+    S.sNItems.need(1);
+    S.sP.need((size_t)qb * 2 * (ix->m + 1));
+    if (t.type == LEAFI_DSTREE) {
+      S.sIv.need((size_t)qb * t.iv_s.size() * 2);
+      S.sNode.need((size_t)qb * t.n_nodes);
+    } else {
+      S.sPaa.need((size_t)qb * t.w);
+    }
+  }
   unsigned long long* stat = ix->sStat.need(4);
-  int64_t* out_i = ix->sOutI.need((size_t)qb * kmax);
-  float* out_d = ix->sOutD.need((size_t)qb * kmax);
-  int32_t* ord = walk ? ix->sOrd.need((size_t)qb * L) : nullptr;
-  int32_t* cursor = walk ? ix->sCursor.need(qb) : nullptr;
-  if (any_filtered && filter_tc(ix)) ix->sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
-  TcQueries tq;
-  if (ix->tc_ok && ix->scan_path == 0) {
-    tq.Qh = ix->sQh.need((size_t)qb * ix->kp);
-    tq.Qk = ix->sQk.need((size_t)2 * qb);
-  }
-  ix->sCnt.need(L);
-  ix->sGrpOff.need(L + 1);
-  ix->sItemOff.need(L + 1);
-  ix->sGrouped.need((size_t)qb * std::max(W, 1));
-  if (tq.Qh) {
-    ix->sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(t));
-    ix->sWork.need(1);
-  }
-  ix->sNItems.need(1);
-  ix->sP.need((size_t)qb * 2 * (ix->m + 1));
-  if (t.type == LEAFI_DSTREE) {
-    ix->sIv.need((size_t)qb * t.iv_s.size() * 2);
-    ix->sNode.need((size_t)qb * t.n_nodes);
-  } else {
-    ix->sPaa.need((size_t)qb * t.w);
-  }
   const bool uniform =
       std::all_of(kq.begin(), kq.end(), [&](int32_t v) { return v == kq[0]; }) &&
       std::all_of(target.begin(), target.end(), [&](double v) { return v == target[0]; });
-  LF_CUDA(cudaMemsetAsync(stat, 0, 4 * sizeof(unsigned long long), s));
+  // the lanes start after the caller's stream (inputs written there are visible)
+  LF_CUDA(cudaMemsetAsync(stat, 0, 4 * sizeof(unsigned long long), user));
+  cudaEvent_t ev_start = nullptr;
+  LF_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t e;
+    ~EvGuard() { cudaEventDestroy(e); }
+  } evg{ev_start};
+  LF_CUDA(cudaEventRecord(ev_start, user));
+  for (int li = 0; li < nlanes; ++li) LF_CUDA(cudaStreamWaitEvent(ix->lanes[li].st, ev_start, 0));
 
+  int cur_lane = 0;
+  cudaStream_t s = user;
+  auto use_lane = [&](int li) {
+    cur_lane = li;
+    ix->sc = &ix->lanes[li];
+    s = ix->lanes[li].st;
+    ix->stream = s;
+  };
   SelectArgs sa;
-  sa.L = L;
-  sa.W = W;
-  sa.lb2 = lb2;
-  sa.thr = thr;
-  sa.F = ix->F;
-  sa.leaf_filter = ix->d_leaf_filter.p;
-  sa.alpha = ix->alpha.p;
-  sa.nc = ix->nc;
-  sa.leaf_off = ix->leaf_off.p;
-  sa.scanned = scanned;
-  sa.cur_lb = cur_lb;
-  sa.cur_leaf = cur_leaf;
-  sa.done = done;
-  sa.pairs = pairs;
-  sa.npairs = np;
-  sa.stat = stat;
-
-  auto select = [&](int nb) {
-    LF_CUDA(cudaMemsetAsync(np, 0, sizeof(int32_t), s));
+  auto make_sa = [&](const LaneView& v, int nb, bool use_f) {
+    sa = SelectArgs();
+    sa.L = L;
+    sa.W = W;
+    sa.nq = nb;
+    sa.lb2 = v.lb2;
+    sa.thr = v.thr;
+    sa.F = ix->F;
+    sa.leaf_filter = ix->d_leaf_filter.p;
+    sa.alpha = ix->alpha.p;
+    sa.nc = ix->nc;
+    sa.leaf_off = ix->leaf_off.p;
+    sa.scanned = v.scanned;
+    sa.cur_lb = v.cur_lb;
+    sa.cur_leaf = v.cur_leaf;
+    sa.done = v.done;
+    sa.pairs = v.pairs;
+    sa.npairs = v.np;
+    sa.stat = stat;
+    sa.P = use_f ? v.P : nullptr;
+    sa.jpos = use_f ? v.jpos : nullptr;
+  };
+  auto select = [&](const LaneView& v) {
+    LF_CUDA(cudaMemsetAsync(v.np, 0, sizeof(int32_t), s));
     ix->tick(5);
     if (walk)
-      launch_select_walk(sa, ord, cursor, s);
+      launch_select_walk(sa, v.ord, v.cursor, s);
     else
       launch_select(sa, s);
     ix->tock();
-    (void)nb;
+  };
+  auto round = [&](const LaneView& v, int nb) {
+    run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb * W, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr,
+              v.cand, v.cand_cnt, cap, stat + 2, stat + 3);
+    select(v);
   };
   // everything of one batch up to (and including) the select of its first wave
-  auto enqueue_head = [&](int nb, bool use_f) {
-    sa.nq = nb;
-    sa.P = use_f ? P : nullptr;
-    sa.jpos = use_f ? jpos : nullptr;
+  auto enqueue_head = [&](const LaneView& v, int nb, bool use_f) {
+    make_sa(v, nb, use_f);
     ix->tick(2);
-    compute_bounds(ix, gQ, nb, lb2, route);
+    compute_bounds(ix, v.gQ, nb, v.lb2, v.route);
     ix->tock();
-    if (tq.Qh) launch_tc_query_prep(gQ, nb, ix->mp, ix->kp, tq.Qh, tq.Qk, s);
+    if (v.tq.Qh) launch_tc_query_prep(v.gQ, nb, ix->mp, ix->kp, v.tq.Qh, v.tq.Qk, s);
     if (use_f) {
       ix->tick(4);
-      filter_forward(ix, gQ, nb, P, qb);
+      filter_forward(ix, v.gQ, nb, v.P, qb);
       ix->tock();
-      launch_jpos(nb, dK, dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, jpos, s);
+      launch_jpos(nb, v.dK, v.dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, v.jpos, s);
     }
-    LF_CUDA(cudaMemsetAsync(scanned, 0, (size_t)nb * L, s));
+    LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
     if (walk) {
-      launch_leaf_order(nb, L, lb2, ord, s);
-      LF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nb, s));
+      launch_leaf_order(nb, L, v.lb2, v.ord, s);
+      LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
     }
-    search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, topk_cnt, thr, cand_cnt, cur_lb,
-                                                        cur_leaf, done);
+    search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, v.topk_cnt, v.thr, v.cand_cnt,
+                                                        v.cur_lb, v.cur_leaf, v.done);
     LF_CHECK_LAUNCH();
     // wave 0: every query searches its route leaf
-    launch_route_pairs(nb, route, L, scanned, ix->leaf_off.p, pairs, np, stat, s);
-    run_round(ix, gQ, tq, pairs, np, nb, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
-              stat + 2, stat + 3);
-    select(nb);
+    launch_route_pairs(nb, v.route, L, v.scanned, ix->leaf_off.p, v.pairs, v.np, stat, s);
+    run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr, v.cand,
+              v.cand_cnt, cap, stat + 2, stat + 3);
+    select(v);
   };
   // a full batch of the same shape replays a captured graph of enqueue_head
-  // followed by its first wave and the next select
-  auto graph_for = [&](int nb, bool use_f) -> leafi::BatchGraph* {
+  // followed by its second wave and the next select (captured per lane)
+  auto graph_for = [&](const LaneView& v, int nb, bool use_f) -> BatchGraph* {
     if (!ix->graphs_ok || nb != qb) return nullptr;
+    std::vector<BatchGraph>& graphs = ix->lanes[cur_lane].graphs;
     const unsigned long long epoch0 = g_realloc_epoch;
-    for (auto& g : ix->graphs)
+    for (auto& g : graphs)
       if (g.nb == nb && g.kmax == kmax && g.use_f == (int)use_f && g.walk == (int)walk &&
           g.profiling == (int)ix->profiling && g.epoch == epoch0)
         return &g;
     // graphs of an older epoch point at freed scratch: drop them
-    for (size_t i = 0; i < ix->graphs.size();) {
-      leafi::BatchGraph& o = ix->graphs[i];
+    for (size_t i = 0; i < graphs.size();) {
+      BatchGraph& o = graphs[i];
       if (o.epoch == epoch0) {
         ++i;
         continue;
       }
       if (o.exec) cudaGraphExecDestroy(o.exec);
       for (cudaEvent_t e : o.ev) cudaEventDestroy(e);
-      ix->graphs.erase(ix->graphs.begin() + i);
+      graphs.erase(graphs.begin() + i);
     }
-    if (!ix->cap_stream &&
-        cudaStreamCreateWithFlags(&ix->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-      cudaGetLastError();
-      ix->cap_stream = nullptr;
-      ix->graphs_ok = false;
-      return nullptr;
-    }
-    ix->graphs.emplace_back();
-    leafi::BatchGraph& g = ix->graphs.back();
+    graphs.emplace_back();
+    BatchGraph& g = graphs.back();
     g.nb = nb;
     g.kmax = kmax;
     g.use_f = use_f;
     g.walk = walk;
     g.profiling = ix->profiling;
     g.epoch = epoch0;
-    // capture on the index's own stream (the caller's may be the legacy
-    // default stream, which cannot be captured); nothing runs while capturing
+    // the lane stream is the library's own (never the legacy default stream);
+    // nothing runs while capturing
     cudaGraph_t graph = nullptr;
-    cudaStream_t user = s;
-    s = ix->cap_stream;
-    ix->stream = ix->cap_stream;
     ix->capturing = &g;
     const long long l0 = launches_so_far();
     bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       try {
-        enqueue_head(nb, use_f);
-        run_round(ix, gQ, tq, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
-                  stat + 2, stat + 3);
-        select(nb);
+        enqueue_head(v, nb, use_f);
+        round(v, nb);
       } catch (...) {
         ok = false;
       }
@@ -669,8 +729,6 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     g.launches = launches_so_far() - l0;
     count_launches(-g.launches);
     ix->capturing = nullptr;
-    s = user;
-    ix->stream = user;
     if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
@@ -679,74 +737,110 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     if (!ok || stale) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
       for (cudaEvent_t e2 : g.ev) cudaEventDestroy(e2);
-      ix->graphs.pop_back();
+      graphs.pop_back();
       // a failure without a reallocation means capture is not available here
       if (!ok && !stale) ix->graphs_ok = false;
       return nullptr;
     }
     return &g;
   };
-
-  for (int64_t b0 = 0; b0 < nq; b0 += qb) {
+  // the lane's pair count goes to its pinned word; the host waits on the event
+  auto post_np = [&](const LaneView& v) {
+    Scratch& S = ix->lanes[cur_lane];
+    LF_CUDA(cudaMemcpyAsync(S.h_np, v.np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LF_CUDA(cudaEventRecord(S.ev_np, s));
+  };
+  InFlight fl[2];
+  auto start = [&](int li, int64_t b0) {
+    use_lane(li);
+    const LaneView& v = lv[li];
     const int nb = (int)std::min<int64_t>(qb, nq - b0);
-    // stage this batch's queries, k and targets into the fixed buffers
-    {
-      const float* src = queries + (size_t)b0 * ix->m;
-      const bool dev = on_device(src);
-      if (ix->mp != ix->m) LF_CUDA(cudaMemsetAsync(gQ, 0, sizeof(float) * nb * ix->mp, s));
-      LF_CUDA(cudaMemcpy2DAsync(gQ, sizeof(float) * ix->mp, src, sizeof(float) * ix->m,
-                                sizeof(float) * ix->m, (size_t)nb,
-                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    }
+    // stage this batch's queries, k and targets into the lane's buffers
+    const float* src = queries + (size_t)b0 * ix->m;
+    const bool dev = on_device(src);
+    if (ix->mp != ix->m) LF_CUDA(cudaMemsetAsync(v.gQ, 0, sizeof(float) * nb * ix->mp, s));
+    LF_CUDA(cudaMemcpy2DAsync(v.gQ, sizeof(float) * ix->mp, src, sizeof(float) * ix->m,
+                              sizeof(float) * ix->m, (size_t)nb,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     if (uniform) {
-      fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, dK, dT, kq[0], target[0]);
+      fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.dK, v.dT, kq[0], target[0]);
       LF_CHECK_LAUNCH();
     } else {
-      LF_CUDA(cudaMemcpyAsync(dK, kq.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-      LF_CUDA(cudaMemcpyAsync(dT, target.data() + b0, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+      LF_CUDA(cudaMemcpyAsync(v.dK, kq.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+      LF_CUDA(cudaMemcpyAsync(v.dT, target.data() + b0, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
     }
-    const bool use_f = std::any_of(target.begin() + b0, target.begin() + b0 + nb,
-                                   [](double v) { return v < 1.0; });
-    if (use_f) st.filter_evals += (int64_t)nb * ix->F;
-    int waves = 1;
-    leafi::BatchGraph* g = graph_for(nb, use_f);
-    if (g) {
-      LF_CUDA(cudaGraphLaunch(g->exec, s));
-      count_launches(g->launches);
+    InFlight& f = fl[li];
+    f = InFlight();
+    f.active = true;
+    f.b0 = b0;
+    f.nb = nb;
+    f.use_f = std::any_of(target.begin() + b0, target.begin() + b0 + nb,
+                          [](double x) { return x < 1.0; });
+    if (f.use_f) st.filter_evals += (int64_t)nb * ix->F;
+    f.g = graph_for(v, nb, f.use_f);
+    if (f.g) {
+      LF_CUDA(cudaGraphLaunch(f.g->exec, s));
+      count_launches(f.g->launches);
       st.graph_batches += 1;
-      waves = 2;
+      f.waves = 2;
+      make_sa(v, nb, f.use_f);
     } else {
-      enqueue_head(nb, use_f);
+      enqueue_head(v, nb, f.use_f);
+      f.waves = 1;
     }
+    post_np(v);
+  };
+  auto finish = [&](int li) {
+    InFlight& f = fl[li];
+    if (!f.active) return;
+    use_lane(li);
+    const LaneView& v = lv[li];
+    make_sa(v, f.nb, f.use_f);
+    Scratch& S = ix->lanes[li];
     for (;;) {
-      int32_t h_np = 0;
-      LF_CUDA(cudaMemcpyAsync(&h_np, np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      LF_CUDA(cudaStreamSynchronize(s));
-      if (g && ix->profiling) {
-        for (size_t i = 0; i < g->kind.size(); ++i) {
+      LF_CUDA(cudaEventSynchronize(S.ev_np));
+      if (f.g && ix->profiling) {
+        for (size_t i = 0; i < f.g->kind.size(); ++i) {
           float ms = 0.0f;
-          LF_CUDA(cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]));
-          ix->clock.ms[g->kind[i]] += ms;
-          ix->clock.n[g->kind[i]] += 1;
+          LF_CUDA(cudaEventElapsedTime(&ms, f.g->ev[2 * i], f.g->ev[2 * i + 1]));
+          ix->clock.ms[f.g->kind[i]] += ms;
+          ix->clock.n[f.g->kind[i]] += 1;
         }
-        g = nullptr;
       }
-      if (h_np == 0) break;
-      if (++waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
-      run_round(ix, gQ, tq, pairs, np, nb * W, nb, kmax, dK, topk, topk_cnt, thr, cand, cand_cnt, cap,
-                stat + 2, stat + 3);
-      select(nb);
+      f.g = nullptr;
+      if (*S.h_np == 0) break;
+      if (++f.waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
+      round(v, f.nb);
+      post_np(v);
     }
-    st.waves += waves;
+    st.waves += f.waves;
     st.batches += 1;
-    check_err_word(ix);
-    launch_write_results(nb, kmax, dK, topk, kmax, topk_cnt, out_i, out_d, s);
-    deliver(ids + (size_t)b0 * kmax, out_i, (size_t)nb * kmax, s);
-    deliver(dists + (size_t)b0 * kmax, out_d, (size_t)nb * kmax, s);
+    launch_write_results(f.nb, kmax, v.dK, v.topk, kmax, v.topk_cnt, v.out_i, v.out_d, s);
+    deliver(ids + (size_t)f.b0 * kmax, v.out_i, (size_t)f.nb * kmax, s);
+    deliver(dists + (size_t)f.b0 * kmax, v.out_d, (size_t)f.nb * kmax, s);
+    f.active = false;
+  };
+
+  int bi = 0;
+  for (int64_t b0 = 0; b0 < nq; b0 += qb, ++bi) {
+    const int li = bi % nlanes;
+    finish(li);  // the lane's previous batch (two batches back)
+    start(li, b0);
   }
+  // the remaining batches, oldest first
+  for (int i = 0; i < nlanes; ++i) finish((bi + i) % nlanes);
+
+  // the caller's stream continues after both lanes
+  for (int li = 0; li < nlanes; ++li) {
+    LF_CUDA(cudaEventRecord(ix->lanes[li].ev_np, ix->lanes[li].st));
+    LF_CUDA(cudaStreamWaitEvent(user, ix->lanes[li].ev_np, 0));
+  }
+  ix->sc = &ix->lanes[0];
+  ix->stream = user;
   unsigned long long h_stat[4] = {0, 0, 0, 0};
-  LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, s));
-  LF_CUDA(cudaStreamSynchronize(s));
+  LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, user));
+  LF_CUDA(cudaStreamSynchronize(user));
+  check_err_word(ix);
   st.leaves_scanned = (int64_t)h_stat[0];
   st.series_scanned = (int64_t)h_stat[1];
   st.distinct_series = (int64_t)h_stat[2];
@@ -786,11 +880,22 @@ leafi::DsTables leafi_index::ds() const {
 }
 
 void leafi_index::drop_graphs() {
-  for (auto& g : graphs) {
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+  for (auto& lane : lanes) {
+    for (auto& g : lane.graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+    }
+    lane.graphs.clear();
   }
-  graphs.clear();
+}
+
+void leafi::Scratch::release_lane() {
+  if (st) cudaStreamDestroy(st);
+  if (ev_np) cudaEventDestroy(ev_np);
+  if (h_np) cudaFreeHost(h_np);
+  st = nullptr;
+  ev_np = nullptr;
+  h_np = nullptr;
 }
 
 void leafi_index::tick(int kind) {
@@ -1009,7 +1114,7 @@ void leafi_free(leafi_index* index) {
     cudaSetDevice(index->device);
     if (index->stream) cudaStreamSynchronize(index->stream);
     index->drop_graphs();
-    if (index->cap_stream) cudaStreamDestroy(index->cap_stream);
+    for (auto& lane : index->lanes) lane.release_lane();
     delete index;
     if (prev >= 0) cudaSetDevice(prev);
   }
@@ -1123,8 +1228,8 @@ leafi_status leafi_leaf_lower_bounds(leafi_index* index, const float* queries, i
     for (int64_t b0 = 0; b0 < nq; b0 += 4096) {
       const int nb = (int)std::min<int64_t>(4096, nq - b0);
       const float* dQ = stage_queries(index, queries + (size_t)b0 * index->m, nb, qtmp);
-      double* out = index->sLb.need((size_t)nb * L);
-      compute_bounds(index, dQ, nb, out, index->sRoute.need(nb));
+      double* out = index->sc->sLb.need((size_t)nb * L);
+      compute_bounds(index, dQ, nb, out, index->sc->sRoute.need(nb));
       deliver(lb2 + (size_t)b0 * L, out, (size_t)nb * L, index->stream);
     }
     LF_CUDA(cudaStreamSynchronize(index->stream));
@@ -1143,8 +1248,8 @@ leafi_status leafi_route(leafi_index* index, const float* queries, int64_t nq, i
     for (int64_t b0 = 0; b0 < nq; b0 += 4096) {
       const int nb = (int)std::min<int64_t>(4096, nq - b0);
       const float* dQ = stage_queries(index, queries + (size_t)b0 * index->m, nb, qtmp);
-      int32_t* r = index->sRoute.need(nb);
-      compute_bounds(index, dQ, nb, index->sLb.need((size_t)nb * L), r);
+      int32_t* r = index->sc->sRoute.need(nb);
+      compute_bounds(index, dQ, nb, index->sc->sLb.need((size_t)nb * L), r);
       deliver(leaf + b0, r, (size_t)nb, index->stream);
     }
     LF_CUDA(cudaStreamSynchronize(index->stream));
@@ -1247,7 +1352,7 @@ leafi_status leafi_filter_predict(leafi_index* index, const float* queries, int6
     for (int64_t b0 = 0; b0 < nq; b0 += 4096) {
       const int nb = (int)std::min<int64_t>(4096, nq - b0);
       const float* dQ = stage_queries(index, queries + (size_t)b0 * index->m, nb, qtmp);
-      float* P = index->sPred.need((size_t)nb * index->F);
+      float* P = index->sc->sPred.need((size_t)nb * index->F);
       ensure_wsplit(index);
       filter_forward(index, dQ, nb, P);
       deliver(out + (size_t)b0 * index->F, P, (size_t)nb * index->F, index->stream);

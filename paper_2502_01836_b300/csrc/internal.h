@@ -284,6 +284,33 @@ void launch_calib_sim(const CalibArgs& a, cudaStream_t s);
 
 }  // namespace leafi
 
+namespace leafi {
+// Per-lane scratch of the search driver and the other entry points.
+struct Scratch {
+  DBuf<float> sQ;
+  DBuf<__half> sQh;        // float16 queries of the tensor-core scan
+  DBuf<float4> sQk;        // their band constants
+  DBuf<float> sQs;         // tf32 hi/lo query planes of the tensor-core filter forward
+  DBuf<int32_t> sItemLeaf; // leaf of every scan work item of a round
+  DBuf<int32_t> sWork;     // work-item counter of the tensor-core scan
+  DBuf<double> sP, sIv, sNode, sLb, sPaa, sTarget;
+  DBuf<int32_t> sRoute, sK, sJpos, sCnt, sGrpOff, sItemOff, sNpairs, sCandCnt, sTopkCnt, sDone,
+      sCurLeaf, sLeaves, sNItems, sOrd, sCursor;
+  DBuf<double> sCurLb;
+  DBuf<unsigned char> sScanned;
+  DBuf<Pair> sPairs, sGrouped;
+  DBuf<unsigned long long> sTopk, sThr, sCand;
+  DBuf<float> sPred, sOutD;
+  DBuf<int64_t> sOutI;
+  // search lane
+  cudaStream_t st = nullptr;       // created on first use (non-blocking)
+  cudaEvent_t ev_np = nullptr;     // the pair count of the lane's batch reached the host
+  int32_t* h_np = nullptr;         // pinned host word
+  std::vector<BatchGraph> graphs;  // captured batches of this lane
+  void release_lane();
+};
+}  // namespace leafi
+
 // ----------------------------------------------------------------- index
 struct leafi_index {
   std::mutex mu;
@@ -324,31 +351,19 @@ struct leafi_index {
   leafi::DBuf<double> alpha, qprime;
   leafi::DBuf<int32_t> d_kclasses;
 
-  // scratch (grown on demand)
-  leafi::DBuf<float> sQ;
-  leafi::DBuf<__half> sQh;       // float16 queries of the tensor-core scan
+  // scratch (grown on demand): lanes[0] serves every entry point; a search of
+  // more than one batch alternates batches between the two lanes
+  leafi::Scratch lanes[2];
+  leafi::Scratch* sc = &lanes[0];  // lane in use
+  leafi::DBuf<int32_t> sErr;       // error word shared by all launches
+  leafi::DBuf<unsigned long long> sStat;  // search counters of one call
   leafi::DBuf<float> Ws;         // tf32 hi/lo weight planes of the tensor-core filter forward
   CUtensorMap wmap;              // TMA descriptor of Ws
   bool ws_dirty = true;          // weights changed since Ws was built
-  leafi::DBuf<float> sQs;        // tf32 hi/lo query planes
-  leafi::DBuf<int32_t> sItemLeaf; // leaf of every scan work item of a round
-  leafi::DBuf<int32_t> sWork;     // work-item counter of the tensor-core scan
-  leafi::DBuf<float4> sQk;       // their band constants
   std::map<int, int> tc_plan;    // k -> query tiles of the tensor-core scan (0: does not fit)
-  leafi::DBuf<double> sP, sIv, sNode, sLb, sPaa, sTarget;
-  leafi::DBuf<int32_t> sRoute, sK, sJpos, sCnt, sGrpOff, sItemOff, sNpairs, sCandCnt, sTopkCnt,
-      sDone, sCurLeaf, sErr, sLeaves, sNItems, sOrd, sCursor;
-  leafi::DBuf<double> sCurLb;
-  leafi::DBuf<unsigned char> sScanned;
-  leafi::DBuf<leafi::Pair> sPairs, sGrouped;
-  leafi::DBuf<unsigned long long> sTopk, sThr, sCand, sStat;
-  leafi::DBuf<float> sPred, sOutD;
-  leafi::DBuf<int64_t> sOutI;
 
   int profiling = 0;       // 0 off, 1 leaf-scan kernel times, 2 every kind + scan phases
   bool ticked = false;     // the last tick() recorded a start event
-  std::vector<leafi::BatchGraph> graphs;   // captured search batches
-  cudaStream_t cap_stream = nullptr;       // private stream used only to capture them
   leafi::BatchGraph* capturing = nullptr;  // entry being captured (tick/tock record into it)
   bool graphs_ok = true;                   // cleared if capture is not possible
   void drop_graphs();
