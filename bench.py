@@ -164,7 +164,9 @@ def workload_config(a):
                         % (a.n, M, a.leaf_cap, a.filters, a.queries, a.launch, a.target),
             "n_series": a.n, "length": M, "leaf_capacity": a.leaf_cap, "filters": a.filters,
             "queries": a.queries, "launch": a.launch, "recall_target": a.target,
-            "k": 1, "wave": a.wave, "l2": "inputs larger than L2 (1.02 GB series)"}
+            "k": 1, "wave": a.wave,
+            "l2": "inputs larger than L2 (%.2f GB float32 series, %.2f GB float16 copy)"
+                  % (a.n * M * 4 / 1e9, a.n * M * 2 / 1e9)}
 
 
 def cpu_threads():
