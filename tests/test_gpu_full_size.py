@@ -1,0 +1,118 @@
+"""Parity at the full configuration sizes (GPU path vs oracle, C-ABI calls).
+
+Correctness configuration: 100,000 random walks x 256, DSTree capacity 2,000,
+one filter per leaf trained on 2,000 queries (1,500 global + 500 local per
+leaf, Alg. 1), 100 test queries, recall target 0.99, and exact mode.
+
+Batched configuration: 1,000,000 random walks x 256, capacity 10,000, filters
+on the 100 largest leaves, 10,000 test queries searched in one call (launches
+of 256 queries, two in flight) - the launch configuration bench.py times.
+Outputs the oracle cannot produce for all queries at this size are checked on
+a seeded sample (exact k-NN by brute force; LeaFi search with the GPU's trained
+weights and auto-tuner tables), the rest through properties that hold at any
+size (recall against exact mode at least the target).
+"""
+import numpy as np
+import pytest
+
+import fixtures as fx
+import oracle as O
+import paper_2502_01836_b300 as lf
+from paper_2502_01836_b300.workflow import enhance
+
+pytestmark = pytest.mark.gpu
+
+M = 256
+W_WAVE = 64
+
+
+def _search(idx, Q, k, target):
+    ids = np.zeros((len(Q), k), np.int64)
+    d = np.zeros((len(Q), k), np.float32)
+    st = lf.SearchStats()
+    lf.leafi_search(idx, Q, k, target, ids, d, st)
+    return ids, d, st
+
+
+def _gpu_model(idx, F, nc):
+    """The trained weights and fitted tables, read back through the ABI."""
+    W = (np.zeros((F, M, M), np.float32), np.zeros((F, M), np.float32),
+         np.zeros((F, M), np.float32), np.zeros(F, np.float32))
+    lf.leafi_get_filters(idx, *W)
+    alpha = np.zeros((F, nc))
+    qp = np.zeros((1, nc))
+    lf.leafi_get_autotuners(idx, alpha, qp)
+    return W, alpha, qp[0]
+
+
+def _pred_scale(W, Q):
+    W1, b1, w2, b2 = (a.astype(np.float64) for a in W)
+    z = np.einsum("fhm,qm->qfh", W1, Q.astype(np.float64)) + b1[None]
+    return np.abs(b2)[None] + np.einsum("qfh,fh->qf", np.maximum(z, 0), np.abs(w2))
+
+
+def _leafi_vs_oracle(idx, t, enh, Q, ids_gpu):
+    F = len(enh.filter_leaf)
+    nc = lf.leafi_get_info(idx).n_calib
+    W, alpha, qp = _gpu_model(idx, F, nc)
+    j = O.offset_position(qp, 0.99)
+    o_ids, o_d2, _, margin = O.leafi_search(t, W, enh.filter_leaf, alpha, Q, 1, j, W_WAVE)
+    tol = 2e-5 * _pred_scale(W, Q).max()
+    same = (ids_gpu == o_ids).all(1)
+    # a query may differ only where a filter decision sits within the prediction tolerance
+    assert (same | (margin <= tol)).all()
+    assert same.mean() >= 0.95
+
+
+def test_correctness_config_100k():
+    X = fx.random_walk(100_000, M)
+    Q = fx.test_queries(X, 100)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=2000, wave=W_WAVE, device=0))
+    try:
+        t = O.Tree(X, "dstree", leaf_cap=2000, init_segments=4)
+        assert np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
+        # exact mode: brute force, bit for bit, k = 1 and 10
+        for k in (1, 10):
+            ids, d, _ = _search(idx, Q, k, 1.0)
+            bf_ids, bf_d2 = O.knn(X, Q, k)
+            assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+        # LeaFi mode: one filter per leaf
+        L = lf.leafi_get_info(idx).n_leaves
+        enh = enhance(idx, X, L, lf.TrainParams())
+        ids, d, st = _search(idx, Q, 1, 0.99)
+        ex_ids, _ = O.knn(X, Q, 1)
+        assert (ids[:, 0] == ex_ids[:, 0]).mean() >= 0.99
+        assert st.series_scanned < len(Q) * len(X)
+        _leafi_vs_oracle(idx, t, enh, Q, ids)
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_batched_config_1m_sampled():
+    X = fx.random_walk(1_000_000, M)
+    Q = fx.test_queries(X, 10_000)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=10_000, wave=W_WAVE, device=0))
+    try:
+        # exact mode over all 10,000 queries in one call; brute force on a sample
+        ex_ids, ex_d, st = _search(idx, Q, 1, 1.0)
+        assert st.batches == 40 and st.graph_batches == 39
+        rng = np.random.default_rng(2502)
+        sample = np.sort(rng.choice(len(Q), 200, replace=False))
+        bf_ids, bf_d2 = O.knn(X, Q[sample], 1)
+        assert np.array_equal(ex_ids[sample], bf_ids)
+        assert np.array_equal(ex_d[sample], np.sqrt(bf_d2))
+        # k = 10 on a 256-query slice (one full batch, the captured graph)
+        ids10, d10, _ = _search(idx, np.ascontiguousarray(Q[:256]), 10, 1.0)
+        bf10, bf10_d2 = O.knn(X, Q[:32], 10)
+        assert np.array_equal(ids10[:32], bf10) and np.array_equal(d10[:32], np.sqrt(bf10_d2))
+        # LeaFi mode, filters on the 100 largest leaves
+        enh = enhance(idx, X, 100, lf.TrainParams())
+        ids, _, st = _search(idx, Q, 1, 0.99)
+        assert (ids[:, 0] == ex_ids[:, 0]).mean() >= 0.99
+        assert st.filter_evals == len(Q) * 100
+        t = O.Tree(X, "dstree", leaf_cap=10_000, init_segments=4)
+        assert np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
+        few = sample[:40]
+        _leafi_vs_oracle(idx, t, enh, np.ascontiguousarray(Q[few]), ids[few])
+    finally:
+        lf.leafi_free(idx)
