@@ -494,6 +494,7 @@ struct LaneView {
   unsigned long long *topk, *thr, *cand;
   Pair* pairs;
   int64_t* out_i;
+  unsigned char* order_tmp;  // sort scratch for more than 4096 leaves
   TcQueries tq;
 };
 
@@ -526,7 +527,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   const int W = ix->wave;
   const int cap = std::max(W, 1) * max_parts(t) * kmax;
   const int qb = kBatch;
-  const bool walk = L <= calib_max_sort();
+  const bool walk = true;  // visiting order by (LB^2, leaf id) for any number of leaves
   const int nlanes = nq > qb ? 2 : 1;
   const cudaStream_t user = ix->stream;
   // every entry point after this one runs on lanes[0] and the caller's stream
@@ -572,6 +573,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     v.out_i = S.sOutI.need((size_t)qb * kmax);
     v.out_d = S.sOutD.need((size_t)qb * kmax);
     v.ord = walk ? S.sOrd.need((size_t)qb * L) : nullptr;
+    v.order_tmp = L > calib_max_sort() ? S.sOrderTmp.need(leaf_order_scratch(qb, L)) : nullptr;
     v.cursor = walk ? S.sCursor.need(qb) : nullptr;
     if (any_filtered && filter_tc(ix)) S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
     v.tq = TcQueries();
@@ -669,7 +671,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     }
     LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
     if (walk) {
-      launch_leaf_order(nb, L, v.lb2, v.ord, s);
+      launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);
       LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
     }
     search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, v.topk_cnt, v.thr, v.cand_cnt,
@@ -1558,7 +1560,6 @@ leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t n
       if (i && kclasses[i] <= kclasses[i - 1]) fail(LEAFI_EINVAL, "k-classes must ascend");
     }
     const int L = index->tree.n_leaves;
-    if (L > calib_max_sort()) fail(LEAFI_EINVAL, "auto-tuner supports at most %d leaves", calib_max_sort());
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
     index->drop_graphs();
@@ -1586,7 +1587,9 @@ leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t n
     DBuf<int32_t> ord, cnt_true;
     DBuf<unsigned long long> work;
     DBuf<long long> hits;
+    DBuf<unsigned char> order_tmp;
     CalibArgs a;
+    a.order_scratch = L > calib_max_sort() ? order_tmp.need(leaf_order_scratch((int)nc, L)) : nullptr;
     a.nc = (int)nc;
     a.L = L;
     a.F = F;

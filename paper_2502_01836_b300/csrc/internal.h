@@ -274,10 +274,14 @@ struct CalibArgs {
   long long* hits;                // [nc] scratch
   double* qprime;                 // [nc] out
   int kk;                         // min(kc, n)
+  void* order_scratch;            // leaf_order_scratch(nc, L) bytes (more than 4096 leaves)
 };
 int calib_max_sort();
-// per query: leaves sorted by ascending (LB^2, leaf id), ord [nq][L] (L <= calib_max_sort())
-void launch_leaf_order(int nq, int L, const double* lb2, int32_t* ord, cudaStream_t s);
+// per query: leaves sorted by ascending (LB^2, leaf id), ord [nq][L]
+// bytes of scratch launch_leaf_order needs for nq queries over L leaves (0 up to 4096 leaves)
+size_t leaf_order_scratch(int nq, int L);
+void launch_leaf_order(int nq, int L, const double* lb2, int32_t* ord, cudaStream_t s,
+                       void* scratch = nullptr);
 int calib_max_wave();
 void launch_calib_alpha(const CalibArgs& a, cudaStream_t s);
 void launch_calib_sim(const CalibArgs& a, cudaStream_t s);
@@ -297,7 +301,7 @@ struct Scratch {
   DBuf<int32_t> sRoute, sK, sJpos, sCnt, sGrpOff, sItemOff, sNpairs, sCandCnt, sTopkCnt, sDone,
       sCurLeaf, sLeaves, sNItems, sOrd, sCursor;
   DBuf<double> sCurLb;
-  DBuf<unsigned char> sScanned;
+  DBuf<unsigned char> sScanned, sOrderTmp;
   DBuf<Pair> sPairs, sGrouped;
   DBuf<unsigned long long> sTopk, sThr, sCand;
   DBuf<float> sPred, sOutD;

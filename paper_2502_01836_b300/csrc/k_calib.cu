@@ -93,6 +93,76 @@ __global__ void order_kernel(int L, const double* __restrict__ lb2, int32_t* __r
   for (int i = threadIdx.x; i < L; i += blockDim.x) ord[(size_t)blockIdx.x * L + i] = id[i];
 }
 
+// Visiting order for more than kMaxSortN leaves: the same bitonic network on
+// n2 = next power of two >= L entries held in global scratch (one block per
+// query); compare-exchange stages with a stride of at least one tile run on
+// the global arrays, the rest of each stage group tile by tile in shared memory.
+constexpr int kOrderThreads = 1024;
+
+__device__ __forceinline__ void cx_pair(double* key, int* id, int pos, int partner, bool asc) {
+  const double x = key[pos], y = key[partner];
+  const int xi = id[pos], yi = id[partner];
+  const bool gt = x > y || (x == y && xi > yi);
+  if (gt == asc) {
+    key[pos] = y;
+    key[partner] = x;
+    id[pos] = yi;
+    id[partner] = xi;
+  }
+}
+
+// strides s_hi .. 1 of bitonic stage group `size` on one tile in shared memory
+__device__ void tile_stages(double* gkey, int* gid, double* tk, int* ti, int t0, int size, int s_hi) {
+  for (int i = threadIdx.x; i < kMaxSortN; i += blockDim.x) {
+    tk[i] = gkey[t0 + i];
+    ti[i] = gid[t0 + i];
+  }
+  __syncthreads();
+  for (int stride = s_hi; stride > 0; stride >>= 1) {
+    for (int t = threadIdx.x; t < kMaxSortN / 2; t += blockDim.x) {
+      const int pos = 2 * t - (t & (stride - 1));
+      cx_pair(tk, ti, pos, pos + stride, ((t0 + pos) & size) == 0);
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < kMaxSortN; i += blockDim.x) {
+    gkey[t0 + i] = tk[i];
+    gid[t0 + i] = ti[i];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kOrderThreads) order_global_kernel(
+    int L, int n2, const double* __restrict__ lb2, double* __restrict__ kbuf,
+    int* __restrict__ ibuf, int32_t* __restrict__ ord) {
+  extern __shared__ double tsm[];
+  double* tk = tsm;
+  int* ti = reinterpret_cast<int*>(tsm + kMaxSortN);
+  const int q = blockIdx.x;
+  double* key = kbuf + (size_t)q * n2;
+  int* id = ibuf + (size_t)q * n2;
+  const double* row = lb2 + (size_t)q * L;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    key[i] = i < L ? row[i] : DBL_MAX;
+    id[i] = i < L ? i : INT_MAX;
+  }
+  __syncthreads();
+  // stage groups up to one tile: every tile sorted in shared memory
+  for (int size = 2; size <= kMaxSortN; size <<= 1)
+    for (int t0 = 0; t0 < n2; t0 += kMaxSortN) tile_stages(key, id, tk, ti, t0, size, size >> 1);
+  for (int size = 2 * kMaxSortN; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride >= kMaxSortN; stride >>= 1) {
+      for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
+        const int pos = 2 * t - (t & (stride - 1));
+        cx_pair(key, id, pos, pos + stride, (pos & size) == 0);
+      }
+      __syncthreads();
+    }
+    for (int t0 = 0; t0 < n2; t0 += kMaxSortN) tile_stages(key, id, tk, ti, t0, size, kMaxSortN >> 1);
+  }
+  for (int i = threadIdx.x; i < L; i += blockDim.x) ord[(size_t)q * L + i] = id[i];
+}
+
 // where the true top-k of each calibration query lies: cnt_true [nc][L]
 __global__ void truth_kernel(int nc, int L, int kc, int stride, const u64* __restrict__ lk,
                              int32_t* __restrict__ heads, int32_t* __restrict__ cnt_true) {
@@ -214,12 +284,31 @@ __global__ void qprime_kernel(int nc, int kk, const long long* __restrict__ hits
 
 int calib_max_sort() { return kMaxSortN; }
 
-void launch_leaf_order(int nq, int L, const double* lb2, int32_t* ord, cudaStream_t s) {
+size_t leaf_order_scratch(int nq, int L) {
+  if (L <= kMaxSortN) return 0;
+  size_t n2 = kMaxSortN;
+  while (n2 < (size_t)L) n2 <<= 1;
+  return (size_t)nq * n2 * (sizeof(double) + sizeof(int));
+}
+
+void launch_leaf_order(int nq, int L, const double* lb2, int32_t* ord, cudaStream_t s,
+                       void* scratch) {
   if (nq <= 0) return;
-  if (L > kMaxSortN) fail(LEAFI_EINVAL, "visiting order supports at most %d leaves", kMaxSortN);
   const size_t smem = kMaxSortN * (sizeof(double) + sizeof(int));
-  LF_CUDA(cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  order_kernel<<<nq, 256, smem, s>>>(L, lb2, ord);
+  if (L <= kMaxSortN) {
+    LF_CUDA(cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    order_kernel<<<nq, 256, smem, s>>>(L, lb2, ord);
+    LF_CHECK_LAUNCH();
+    return;
+  }
+  if (!scratch) fail(LEAFI_EINTERNAL, "visiting order of %d leaves needs scratch", L);
+  int n2 = kMaxSortN;
+  while (n2 < L) n2 <<= 1;
+  double* kbuf = static_cast<double*>(scratch);
+  int* ibuf = reinterpret_cast<int*>(kbuf + (size_t)nq * n2);
+  LF_CUDA(cudaFuncSetAttribute(order_global_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  order_global_kernel<<<nq, kOrderThreads, smem, s>>>(L, n2, lb2, kbuf, ibuf, ord);
   LF_CHECK_LAUNCH();
 }
 int calib_max_wave() { return kMaxWave; }
@@ -235,12 +324,8 @@ void launch_calib_alpha(const CalibArgs& a, cudaStream_t s) {
 }
 
 void launch_calib_sim(const CalibArgs& a, cudaStream_t s) {
-  if (a.L > kMaxSortN) fail(LEAFI_EINVAL, "auto-tuner supports at most %d leaves", kMaxSortN);
   if (a.W > kMaxWave) fail(LEAFI_EINVAL, "wave > %d", kMaxWave);
-  const size_t smem = kMaxSortN * (sizeof(double) + sizeof(int));
-  LF_CUDA(cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  order_kernel<<<a.nc, 256, smem, s>>>(a.L, a.lb2, a.ord);
-  LF_CHECK_LAUNCH();
+  launch_leaf_order(a.nc, a.L, a.lb2, a.ord, s, a.order_scratch);
   // `work` doubles as the truth kernel's per-leaf head pointers (nc * L ints)
   truth_kernel<<<(a.nc + 63) / 64, 64, 0, s>>>(a.nc, a.L, a.kc, a.lk_stride, a.lk,
                                                reinterpret_cast<int32_t*>(a.work), a.cnt_true);
