@@ -7,6 +7,10 @@ leaf, Alg. 1), 100 test queries, recall target 0.99, and exact mode.
 Batched configuration: 1,000,000 random walks x 256, capacity 10,000, filters
 on the 100 largest leaves, 10,000 test queries searched in one call (launches
 of 256 queries, two in flight) - the launch configuration bench.py times.
+Mixed-k configuration (reduced from 25M series): iSAX, 16 PAA segments,
+cardinality 256, uneven leaves; k drawn from {1, 10, 100}, recall targets from
+{0.9, 0.95, 0.99}; training targets (the build phase) bit-exact.
+
 Outputs the oracle cannot produce for all queries at this size are checked on
 a seeded sample (exact k-NN by brute force; LeaFi search with the GPU's trained
 weights and auto-tuner tables), the rest through properties that hold at any
@@ -114,5 +118,57 @@ def test_batched_config_1m_sampled():
         assert np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
         few = sample[:40]
         _leafi_vs_oracle(idx, t, enh, np.ascontiguousarray(Q[few]), ids[few])
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_mixed_k_isax_config_reduced():
+    X = fx.random_walk(200_000, M, seed=fx.SEED_DATA + 7)
+    idx = lf.leafi_build(X, lf.BuildParams(index_type=lf.ISAX, leaf_capacity=2000, wave=16,
+                                           device=0))
+    try:
+        t = O.Tree(X, "isax", leaf_cap=2000, isax_w=16, isax_bits=8)
+        assert np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
+        sizes = lf.leafi_leaf_sizes(idx)
+        assert sizes.max() >= 3 * max(1.0, float(np.median(sizes)))   # uneven leaves
+        F = 24
+        p = lf.TrainParams(max_epochs=60, patience=5)
+        enh = enhance(idx, X, F, p, kclasses=(1, 10, 100))
+        # the build phase: node-wise nearest-neighbour targets, bit for bit
+        Ql = np.ascontiguousarray(enh.Ql[:, :40])
+        Qg = np.ascontiguousarray(enh.Qg[:300])
+        Tg = np.zeros((300, F), np.float32)
+        Tl = np.zeros((F, 40), np.float32)
+        lf.leafi_train_targets(idx, Qg, Ql, Tg, Tl)
+        oTg, oTl = O.train_targets(t, enh.filter_leaf, Qg, Ql)
+        assert np.array_equal(Tg, oTg) and np.array_equal(Tl, oTl)
+        # mixed requests: k in {1, 10, 100}, targets in {0.9, 0.95, 0.99}, some exact
+        Q = fx.test_queries(X, 400, seed=fx.SEED_TEST + 7)
+        rng = np.random.default_rng(25)
+        kq = rng.choice([1, 10, 100], len(Q)).astype(np.int32)
+        tg = rng.choice([0.9, 0.95, 0.99, 1.0], len(Q)).astype(np.float64)
+        ids = np.zeros((len(Q), 100), np.int64)
+        d = np.zeros((len(Q), 100), np.float32)
+        lf.leafi_search_mixed(idx, Q, kq, tg, 100, ids, d)
+        nc = lf.leafi_get_info(idx).n_calib
+        W = (np.zeros((F, M, M), np.float32), np.zeros((F, M), np.float32),
+             np.zeros((F, M), np.float32), np.zeros(F, np.float32))
+        lf.leafi_get_filters(idx, *W)
+        alpha = np.zeros((F, nc))
+        qp = np.zeros((3, nc))
+        lf.leafi_get_autotuners(idx, alpha, qp)
+        cls = {1: 0, 10: 1, 100: 2}
+        jpos = np.array([-1 if tg[i] >= 1 else O.offset_position(qp[cls[kq[i]]], tg[i])
+                         for i in range(len(Q))], np.int32)
+        o_ids, o_d2, _, margin = O.leafi_search(t, W, enh.filter_leaf, alpha, Q, kq, jpos, 16,
+                                                kmax=100)
+        tol = 2e-5 * _pred_scale(W, Q).max()
+        same = (ids == o_ids).all(1)
+        assert (same | (margin <= tol)).all()
+        assert same[jpos < 0].all()
+        assert same.mean() >= 0.95
+        # padding beyond each query's k
+        for i in range(len(Q)):
+            assert (ids[i, kq[i]:] == -1).all()
     finally:
         lf.leafi_free(idx)
