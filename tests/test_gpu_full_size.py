@@ -11,6 +11,12 @@ Mixed-k configuration (reduced from 25M series): iSAX, 16 PAA segments,
 cardinality 256, uneven leaves; k drawn from {1, 10, 100}, recall targets from
 {0.9, 0.95, 0.99}; training targets (the build phase) bit-exact.
 
+Precision configuration (reduced from 10M series): embedding-like vectors
+(1,000 Gaussian clusters, m = 96), k = 10, exact mode on the tensor-core path
+(float16 products, float32 re-check band) and on the CUDA-core path; both equal
+the canonical float32 brute force, and the error against float64 distances
+stays within the float32 bound.
+
 Outputs the oracle cannot produce for all queries at this size are checked on
 a seeded sample (exact k-NN by brute force; LeaFi search with the GPU's trained
 weights and auto-tuner tables), the rest through properties that hold at any
@@ -170,5 +176,39 @@ def test_mixed_k_isax_config_reduced():
         # padding beyond each query's k
         for i in range(len(Q)):
             assert (ids[i, kq[i]:] == -1).all()
+    finally:
+        lf.leafi_free(idx)
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_precision_config_reduced(path):
+    m, n, k = 96, 300_000, 10
+    X = fx.embedding_like(n, m)
+    Q = fx.test_queries(X, 300, seed=fx.SEED_TEST + 3)   # two batches: both lanes
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=10_000, wave=W_WAVE, device=0,
+                                           scan_path=path))
+    try:
+        info = lf.leafi_get_info(idx)
+        assert bool(info.tensor_scan) == (path == 0)
+        ids = np.zeros((len(Q), k), np.int64)
+        d = np.zeros((len(Q), k), np.float32)
+        st = lf.SearchStats()
+        lf.leafi_exact_search(idx, Q, k, ids, d, st)
+        bf_ids, bf_d2 = O.knn(X, Q, k)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+        # against float64 distances of the same series: the float32 canonical sum's bound
+        X64, Q64 = X.astype(np.float64), Q.astype(np.float64)
+        d64 = np.sqrt(np.einsum("qkm,qkm->qk", X64[ids] - Q64[:, None], X64[ids] - Q64[:, None]))
+        rel = np.abs(d.astype(np.float64) - d64) / np.maximum(d64, 1e-30)
+        assert rel.max() <= m * 2.0 ** -24
+        # recall@10 against the float64 ranking (near-ties may swap the last place)
+        sub = np.arange(0, len(Q), 10)
+        truth = np.stack([np.argsort(((X64 - Q64[i]) ** 2).sum(-1), kind="stable")[:k]
+                          for i in sub])
+        rec = np.mean([len(set(ids[i]) & set(truth[j])) / k for j, i in enumerate(sub)])
+        assert rec >= 0.99
+        if path == 0:
+            # the band admits few re-checks per query
+            assert st.rechecks < 0.01 * st.series_scanned
     finally:
         lf.leafi_free(idx)
