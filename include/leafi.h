@@ -44,7 +44,8 @@ typedef enum {
   LEAFI_ECUDA = 3,       /* a CUDA call failed */
   LEAFI_ETIMEOUT = 4,    /* a bounded device wait gave up */
   LEAFI_ENOTTRAINED = 5, /* filters / auto-tuners needed but absent */
-  LEAFI_EINTERNAL = 6    /* internal consistency check failed */
+  LEAFI_EINTERNAL = 6,   /* internal consistency check failed */
+  LEAFI_EAGAIN = 7       /* serving: admission refused for now (memory budget); retry later */
 } leafi_status;
 
 enum { LEAFI_DSTREE = 0, LEAFI_ISAX = 1 };
@@ -270,6 +271,69 @@ leafi_status leafi_exact_search(leafi_index* index, const float* queries, int64_
 leafi_status leafi_search_mixed(leafi_index* index, const float* queries, int64_t nq,
                                 const int32_t* k, const double* recall_target, int32_t kmax,
                                 int64_t* ids, float* dists, leafi_search_stats* stats);
+
+/* ------------------------------------------------------------------ */
+/* Serving: a request loop over a resident index (no counterpart in the  */
+/* paper, which answers one query at a time; the search it runs is       */
+/* Alg. 2 as above).                                                     */
+/* ------------------------------------------------------------------ */
+
+/* A server owns a worker thread and its own pair of search lanes (scratch
+ * and streams) on the index's device; the index, its filters and its
+ * auto-tuner tables stay resident and are shared with the index's other
+ * entry points (calls on the index are serialised with the server's batches
+ * by the index mutex).  Requests carry their own k and recall target per
+ * query.  Pending queries of all requests form batches of up to `max_batch`
+ * (continuous batching: a request that arrives while batches are on the GPU
+ * joins the next batch; two batches are in flight, so one's preparation
+ * overlaps the other's scan), and each batch groups its (query, leaf) pairs
+ * by leaf, so requests share leaf scans.  A partial batch launches when
+ * nothing is in flight or its oldest query has waited `max_wait_ms`.
+ * Results are those of leafi_search_mixed on the same queries: each is the
+ * same alone and in any mix. */
+typedef struct leafi_server leafi_server;
+
+typedef struct {
+  int32_t max_batch;    /* queries per batch, 1..256 (default 256) */
+  int32_t kmax;         /* largest k of any request, 1..LEAFI_MAX_K; results are [nq][kmax] */
+  double max_wait_ms;   /* a partial batch waits at most this long for company (default 0.2) */
+  int64_t max_bytes;    /* admission budget: host bytes of queries and results of the requests
+                           admitted and not yet collected (0 = 1 GiB) */
+} leafi_serve_params;
+
+/* Start serving `index` (device index, built and, for targets < 1, tuned).
+ * The server must be stopped before the index is freed. */
+leafi_status leafi_serve_start(leafi_index* index, const leafi_serve_params* params,
+                               leafi_server** out);
+
+/* Submit nq queries (host memory, [nq][m] float32; copied before returning)
+ * with per-query k [nq] (1..kmax) and recall targets [nq] (>= 1 exact).
+ * On success *ticket identifies the request.  LEAFI_EAGAIN: the admission
+ * budget is full (collect results, then retry); LEAFI_ENOTTRAINED: a target
+ * below 1 on an index without auto-tuners. */
+leafi_status leafi_serve_submit(leafi_server* server, const float* queries, int64_t nq,
+                                const int32_t* k, const double* recall_target, int64_t* ticket);
+
+/* Wait up to wait_ms (0 = just look) for request `ticket`.  When it is done,
+ * copies its results to ids / dists (host, [nq][kmax], entries past a
+ * query's k are -1 / +inf), sets *done = 1 and *latency_ms (submit to last
+ * result), and forgets the request (its budget is released); otherwise
+ * *done = 0.  An unknown ticket is LEAFI_EINVAL. */
+leafi_status leafi_serve_poll(leafi_server* server, int64_t ticket, int64_t* ids, float* dists,
+                              double wait_ms, int32_t* done, double* latency_ms);
+
+/* Counters since the start: requests and queries completed, batches run,
+ * batches that replayed a captured graph, and the search statistics summed
+ * over the batches. */
+typedef struct {
+  int64_t requests, queries, batches, graph_batches;
+  leafi_search_stats search;
+} leafi_serve_stats;
+leafi_status leafi_serve_get_stats(leafi_server* server, leafi_serve_stats* stats);
+
+/* Finish every admitted request, stop the worker and free the server.
+ * Results not yet collected are discarded. */
+leafi_status leafi_serve_stop(leafi_server* server);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,9 @@ __all__ = [
     "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
     "KERNEL_KINDS", "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases", "SCAN_PHASES",
-    "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS",
+    "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS", "EAGAIN", "ServeParams", "ServeStats",
+    "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
+    "leafi_serve_stop",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,7 +34,9 @@ LIB_PATH = os.path.join(_HERE, "libleafi.so")
 DSTREE, ISAX = 0, 1
 MAX_K = 128
 _STATUS = {0: "LEAFI_OK", 1: "LEAFI_EINVAL", 2: "LEAFI_ENOMEM", 3: "LEAFI_ECUDA",
-           4: "LEAFI_ETIMEOUT", 5: "LEAFI_ENOTTRAINED", 6: "LEAFI_EINTERNAL"}
+           4: "LEAFI_ETIMEOUT", 5: "LEAFI_ENOTTRAINED", 6: "LEAFI_EINTERNAL",
+           7: "LEAFI_EAGAIN"}
+EAGAIN = 7
 
 EXPORTED_SYMBOLS = [
     "leafi_build", "leafi_free", "leafi_last_error", "leafi_set_stream", "leafi_get_info",
@@ -42,6 +46,8 @@ EXPORTED_SYMBOLS = [
     "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
     "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases",
+    "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
+    "leafi_serve_stop",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -92,6 +98,16 @@ class SearchStats(C.Structure):
                 ("graph_batches", C.c_int64)]
 
 
+class ServeParams(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("kmax", C.c_int32), ("max_wait_ms", C.c_double),
+                ("max_bytes", C.c_int64)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("requests", C.c_int64), ("queries", C.c_int64), ("batches", C.c_int64),
+                ("graph_batches", C.c_int64), ("search", SearchStats)]
+
+
 _lib = None
 
 
@@ -129,6 +145,11 @@ def lib():
             "leafi_set_profiling": [vp, i32],
             "leafi_get_kernel_times": [vp, vp, vp],
             "leafi_get_scan_phases": [vp, vp],
+            "leafi_serve_start": [vp, C.POINTER(ServeParams), C.POINTER(vp)],
+            "leafi_serve_submit": [vp, vp, i64, vp, vp, C.POINTER(i64)],
+            "leafi_serve_poll": [vp, i64, vp, vp, f64, C.POINTER(i32), C.POINTER(f64)],
+            "leafi_serve_get_stats": [vp, C.POINTER(ServeStats)],
+            "leafi_serve_stop": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -358,3 +379,44 @@ def leafi_search_mixed(index, queries, k, recall_target, kmax, ids, dists,
                                     _ptr(dists, np.float32, "dists", True),
                                     C.byref(stats) if stats is not None else None))
     return ids, dists
+
+
+# ---------------------------------------------------------------- serving
+def leafi_serve_start(index, kmax=1, max_batch=256, max_wait_ms=0.2, max_bytes=0):
+    """Start a request loop over `index`; returns the server handle."""
+    out = C.c_void_p()
+    p = ServeParams(max_batch, kmax, max_wait_ms, max_bytes)
+    _check(lib().leafi_serve_start(index, C.byref(p), C.byref(out)))
+    return out
+
+
+def leafi_serve_submit(server, queries, k, recall_target):
+    """Queue a request (host arrays); returns its ticket.  LeafiError with status
+    EAGAIN when the admission budget is full."""
+    t = C.c_int64()
+    _check(lib().leafi_serve_submit(server, _ptr(queries, np.float32, "queries"), queries.shape[0],
+                                    _ptr(k, np.int32, "k"), _ptr(recall_target, np.float64, "target"),
+                                    C.byref(t)))
+    return t.value
+
+
+def leafi_serve_poll(server, ticket, ids, dists, wait_ms=0.0):
+    """(done, latency_ms); when done the results are in ids / dists [nq][kmax]."""
+    done = C.c_int32()
+    lat = C.c_double()
+    _check(lib().leafi_serve_poll(server, ticket, _ptr(ids, np.int64, "ids", True),
+                                  _ptr(dists, np.float32, "dists", True), wait_ms, C.byref(done),
+                                  C.byref(lat)))
+    return bool(done.value), lat.value
+
+
+def leafi_serve_get_stats(server):
+    st = ServeStats()
+    _check(lib().leafi_serve_get_stats(server, C.byref(st)))
+    out = {f: getattr(st, f) for f, _ in ServeStats._fields_ if f != "search"}
+    out["search"] = {f: getattr(st.search, f) for f, _ in SearchStats._fields_}
+    return out
+
+
+def leafi_serve_stop(server):
+    _check(lib().leafi_serve_stop(server))

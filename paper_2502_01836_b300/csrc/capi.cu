@@ -1,6 +1,11 @@
 // C ABI (include/leafi.h): argument checks, host/device staging, and the
 // search driver that runs the LeaFi path (Alg. 2) on the GPU in waves.
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -501,51 +506,74 @@ struct LaneView {
 // one batch in flight on a lane
 struct InFlight {
   bool active = false;
-  int64_t b0 = 0;
   int nb = 0;
   bool use_f = false;
   BatchGraph* g = nullptr;
   int waves = 0;
+  int64_t* ids = nullptr;   // where its results go (host or device)
+  float* dists = nullptr;
 };
 
-// The search driver shared by leafi_search / _exact / _mixed (Alg. 2 over
-// batches of kBatch queries).  Batches alternate between two lanes, each
-// with its own scratch and stream, so the preparation of one batch (bounds,
-// filters, leaf order) and the host's wait for its wave count overlap the
-// other batch's scan.  A full batch replays a captured graph of its first two
-// waves; later waves are enqueued as the host learns that pairs remain.
-void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::vector<int32_t>& kq,
-                 const std::vector<double>& target, int kmax, int64_t* ids, float* dists,
-                 leafi_search_stats* stats) {
-  const HostTree& t = ix->tree;
-  const int L = t.n_leaves;
-  const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
-  if (any_filtered && (ix->nc == 0 || ix->F == 0))
-    fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
-  if (any_filtered) ensure_wsplit(ix);
-  leafi_search_stats st{};
-  const int W = ix->wave;
-  const int cap = std::max(W, 1) * max_parts(t) * kmax;
-  const int qb = kBatch;
-  const bool walk = true;  // visiting order by (LB^2, leaf id) for any number of leaves
-  const int nlanes = nq > qb ? 2 : 1;
-  const cudaStream_t user = ix->stream;
-  // every entry point after this one runs on lanes[0] and the caller's stream
-  struct Restore {
-    leafi_index* ix;
-    cudaStream_t user;
-    ~Restore() {
-      ix->sc = &ix->lanes[0];
-      ix->stream = user;
-      ix->capturing = nullptr;
-    }
-  } restore{ix, user};
+}  // namespace
 
-  // every buffer a batch touches is sized for a full batch up front, so a
-  // captured batch never sees a reallocation while it is replayed
+// The batch pipeline of Alg. 2: batches of up to kBatch queries alternate
+// between two lanes, each with its own scratch and stream, so the preparation
+// of one batch (bounds, filters, leaf order) and the host's wait for its wave
+// count overlap the other batch's scan.  A full batch replays a captured graph
+// of its first two waves; later waves are enqueued as the host learns that
+// pairs remain.  Used by the search entry points (one call, many batches) and
+// by the serving loop (batches formed from pending requests).
+struct Pipeline {
+  leafi_index* ix = nullptr;
+  Scratch* lanes = nullptr;
+  int nlanes = 1;
+  int kmax = 1, W = 1, L = 0, cap = 0, qb = kBatch;
+  bool walk = true;
+  unsigned long long* stat = nullptr;   // device counters of the pipeline's batches
+  leafi_search_stats st{};
   LaneView lv[2];
+  InFlight fl[2];
+  SelectArgs sa;
+  int cur_lane = 0;
+  cudaStream_t s = nullptr;
+
+  // size every buffer of a full batch on each lane (before any graph capture)
+  void setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k_max, bool any_filtered,
+             unsigned long long* counters);
+  void use_lane(int li);
+  void make_sa(const LaneView& v, int nb, bool use_f);
+  void select(const LaneView& v);
+  void round(const LaneView& v, int nb);
+  void enqueue_head(const LaneView& v, int nb, bool use_f);
+  BatchGraph* graph_for(const LaneView& v, int nb, bool use_f);
+  void post_np(const LaneView& v);
+  bool busy(int li) const { return fl[li].active; }
+  // stage nb queries (rows of m floats, host or device) with their k and targets
+  // (uniform: kq[0] / target[0] for all) and enqueue the batch on lane li
+  void start(int li, const float* queries, int nb, const int32_t* kq, const double* target,
+             bool uniform, int64_t* ids, float* dists);
+  // wait for lane li's batch, run its remaining waves, deliver its results
+  void finish(int li);
+};
+
+namespace {
+}  // namespace
+
+void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k_max,
+                     bool any_filtered, unsigned long long* counters) {
+  ix = index;
+  lanes = lane_array;
+  nlanes = n_lanes;
+  kmax = k_max;
+  stat = counters;
+  const HostTree& t = ix->tree;
+  L = t.n_leaves;
+  W = ix->wave;
+  cap = std::max(W, 1) * max_parts(t) * kmax;
+  qb = kBatch;
+  walk = true;  // visiting order by (LB^2, leaf id) for any number of leaves
   for (int li = 0; li < nlanes; ++li) {
-    Scratch& S = ix->lanes[li];
+    Scratch& S = lanes[li];
     if (!S.st) {
       LF_CUDA(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking));
       LF_CUDA(cudaEventCreateWithFlags(&S.ev_np, cudaEventDisableTiming));
@@ -572,9 +600,9 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     v.np = S.sNpairs.need(1);
     v.out_i = S.sOutI.need((size_t)qb * kmax);
     v.out_d = S.sOutD.need((size_t)qb * kmax);
-    v.ord = walk ? S.sOrd.need((size_t)qb * L) : nullptr;
+    v.ord = S.sOrd.need((size_t)qb * L);
+    v.cursor = S.sCursor.need(qb);
     v.order_tmp = L > calib_max_sort() ? S.sOrderTmp.need(leaf_order_scratch(qb, L)) : nullptr;
-    v.cursor = walk ? S.sCursor.need(qb) : nullptr;
     if (any_filtered && filter_tc(ix)) S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
     v.tq = TcQueries();
     if (ix->tc_ok && ix->scan_path == 0) {
@@ -596,7 +624,248 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       S.sPaa.need((size_t)qb * t.w);
     }
   }
+}
+
+void Pipeline::use_lane(int li) {
+  cur_lane = li;
+  ix->sc = &lanes[li];
+  s = lanes[li].st;
+  ix->stream = s;
+}
+
+void Pipeline::make_sa(const LaneView& v, int nb, bool use_f) {
+  sa = SelectArgs();
+  sa.L = L;
+  sa.W = W;
+  sa.nq = nb;
+  sa.lb2 = v.lb2;
+  sa.thr = v.thr;
+  sa.F = ix->F;
+  sa.leaf_filter = ix->d_leaf_filter.p;
+  sa.alpha = ix->alpha.p;
+  sa.nc = ix->nc;
+  sa.leaf_off = ix->leaf_off.p;
+  sa.scanned = v.scanned;
+  sa.cur_lb = v.cur_lb;
+  sa.cur_leaf = v.cur_leaf;
+  sa.done = v.done;
+  sa.pairs = v.pairs;
+  sa.npairs = v.np;
+  sa.stat = stat;
+  sa.P = use_f ? v.P : nullptr;
+  sa.jpos = use_f ? v.jpos : nullptr;
+}
+
+void Pipeline::select(const LaneView& v) {
+  LF_CUDA(cudaMemsetAsync(v.np, 0, sizeof(int32_t), s));
+  ix->tick(5);
+  if (walk)
+    launch_select_walk(sa, v.ord, v.cursor, s);
+  else
+    launch_select(sa, s);
+  ix->tock();
+}
+
+void Pipeline::round(const LaneView& v, int nb) {
+  run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb * W, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr,
+            v.cand, v.cand_cnt, cap, stat + 2, stat + 3);
+  select(v);
+}
+
+// everything of one batch up to (and including) the select of its first wave
+void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
+  make_sa(v, nb, use_f);
+  ix->tick(2);
+  compute_bounds(ix, v.gQ, nb, v.lb2, v.route);
+  ix->tock();
+  if (v.tq.Qh) launch_tc_query_prep(v.gQ, nb, ix->mp, ix->kp, v.tq.Qh, v.tq.Qk, s);
+  if (use_f) {
+    ix->tick(4);
+    filter_forward(ix, v.gQ, nb, v.P, qb);
+    ix->tock();
+    launch_jpos(nb, v.dK, v.dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, v.jpos, s);
+  }
+  LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
+  launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);
+  LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
+  search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, v.topk_cnt, v.thr, v.cand_cnt,
+                                                      v.cur_lb, v.cur_leaf, v.done);
+  LF_CHECK_LAUNCH();
+  // wave 0: every query searches its route leaf
+  launch_route_pairs(nb, v.route, L, v.scanned, ix->leaf_off.p, v.pairs, v.np, stat, s);
+  run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr, v.cand,
+            v.cand_cnt, cap, stat + 2, stat + 3);
+  select(v);
+}
+
+// a full batch of the same shape replays a captured graph of enqueue_head
+// followed by its second wave and the next select (captured per lane)
+BatchGraph* Pipeline::graph_for(const LaneView& v, int nb, bool use_f) {
+  if (!ix->graphs_ok || nb != qb) return nullptr;
+  std::vector<BatchGraph>& graphs = lanes[cur_lane].graphs;
+  const unsigned long long epoch0 = g_realloc_epoch;
+  for (auto& g : graphs)
+    if (g.nb == nb && g.kmax == kmax && g.use_f == (int)use_f && g.walk == (int)walk &&
+        g.profiling == (int)ix->profiling && g.epoch == epoch0 && g.gen == ix->graph_gen)
+      return &g;
+  // graphs of an older epoch point at freed scratch, of an older generation
+  // at replaced filters or tables: drop them
+  for (size_t i = 0; i < graphs.size();) {
+    BatchGraph& o = graphs[i];
+    if (o.epoch == epoch0 && o.gen == ix->graph_gen) {
+      ++i;
+      continue;
+    }
+    if (o.exec) cudaGraphExecDestroy(o.exec);
+    for (cudaEvent_t e : o.ev) cudaEventDestroy(e);
+    graphs.erase(graphs.begin() + i);
+  }
+  graphs.emplace_back();
+  BatchGraph& g = graphs.back();
+  g.nb = nb;
+  g.kmax = kmax;
+  g.use_f = use_f;
+  g.walk = walk;
+  g.profiling = ix->profiling;
+  g.epoch = epoch0;
+  g.gen = ix->graph_gen;
+  // the lane stream is the library's own (never the legacy default stream);
+  // nothing runs while capturing
+  cudaGraph_t graph = nullptr;
+  ix->capturing = &g;
+  const long long l0 = launches_so_far();
+  bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    try {
+      enqueue_head(v, nb, use_f);
+      round(v, nb);
+    } catch (...) {
+      ok = false;
+    }
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    ok = ok && e == cudaSuccess && graph;
+  }
+  g.launches = launches_so_far() - l0;
+  count_launches(-g.launches);
+  ix->capturing = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  // a scratch buffer that grew while capturing invalidates the capture
+  const bool stale = g_realloc_epoch != epoch0;
+  if (!ok || stale) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e2 : g.ev) cudaEventDestroy(e2);
+    graphs.pop_back();
+    // a failure without a reallocation means capture is not available here
+    if (!ok && !stale) ix->graphs_ok = false;
+    return nullptr;
+  }
+  return &g;
+}
+
+// the lane's pair count goes to its pinned word; the host waits on the event
+void Pipeline::post_np(const LaneView& v) {
+  Scratch& S = lanes[cur_lane];
+  LF_CUDA(cudaMemcpyAsync(S.h_np, v.np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaEventRecord(S.ev_np, s));
+}
+
+void Pipeline::start(int li, const float* queries, int nb, const int32_t* kq, const double* target,
+                     bool uniform, int64_t* ids, float* dists) {
+  use_lane(li);
+  const LaneView& v = lv[li];
+  const bool dev = on_device(queries);
+  if (ix->mp != ix->m) LF_CUDA(cudaMemsetAsync(v.gQ, 0, sizeof(float) * nb * ix->mp, s));
+  LF_CUDA(cudaMemcpy2DAsync(v.gQ, sizeof(float) * ix->mp, queries, sizeof(float) * ix->m,
+                            sizeof(float) * ix->m, (size_t)nb,
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (uniform) {
+    fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.dK, v.dT, kq[0], target[0]);
+    LF_CHECK_LAUNCH();
+  } else {
+    LF_CUDA(cudaMemcpyAsync(v.dK, kq, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(v.dT, target, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+  }
+  InFlight& f = fl[li];
+  f = InFlight();
+  f.active = true;
+  f.nb = nb;
+  f.ids = ids;
+  f.dists = dists;
+  f.use_f = false;
+  for (int i = 0; i < (uniform ? 1 : nb); ++i) f.use_f = f.use_f || target[i] < 1.0;
+  if (f.use_f) st.filter_evals += (int64_t)nb * ix->F;
+  f.g = graph_for(v, nb, f.use_f);
+  if (f.g) {
+    LF_CUDA(cudaGraphLaunch(f.g->exec, s));
+    count_launches(f.g->launches);
+    st.graph_batches += 1;
+    f.waves = 2;
+  } else {
+    enqueue_head(v, nb, f.use_f);
+    f.waves = 1;
+  }
+  post_np(v);
+}
+
+void Pipeline::finish(int li) {
+  InFlight& f = fl[li];
+  if (!f.active) return;
+  use_lane(li);
+  const LaneView& v = lv[li];
+  make_sa(v, f.nb, f.use_f);
+  Scratch& S = lanes[li];
+  for (;;) {
+    LF_CUDA(cudaEventSynchronize(S.ev_np));
+    if (f.g && ix->profiling) {
+      for (size_t i = 0; i < f.g->kind.size(); ++i) {
+        float ms = 0.0f;
+        LF_CUDA(cudaEventElapsedTime(&ms, f.g->ev[2 * i], f.g->ev[2 * i + 1]));
+        ix->clock.ms[f.g->kind[i]] += ms;
+        ix->clock.n[f.g->kind[i]] += 1;
+      }
+    }
+    f.g = nullptr;
+    if (*S.h_np == 0) break;
+    if (++f.waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
+    round(v, f.nb);
+    post_np(v);
+  }
+  st.waves += f.waves;
+  st.batches += 1;
+  launch_write_results(f.nb, kmax, v.dK, v.topk, kmax, v.topk_cnt, v.out_i, v.out_d, s);
+  deliver(f.ids, v.out_i, (size_t)f.nb * kmax, s);
+  deliver(f.dists, v.out_d, (size_t)f.nb * kmax, s);
+  f.active = false;
+}
+
+namespace {
+
+// the search entry points: one call, batches of kBatch through the index's pipeline
+void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::vector<int32_t>& kq,
+                 const std::vector<double>& target, int kmax, int64_t* ids, float* dists,
+                 leafi_search_stats* stats) {
+  const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
+  if (any_filtered && (ix->nc == 0 || ix->F == 0))
+    fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
+  if (any_filtered) ensure_wsplit(ix);
+  const int qb = kBatch;
+  const int nlanes = nq > qb ? 2 : 1;
+  const cudaStream_t user = ix->stream;
+  // every entry point after this one runs on lanes[0] and the caller's stream
+  struct Restore {
+    leafi_index* ix;
+    cudaStream_t user;
+    ~Restore() {
+      ix->sc = &ix->lanes[0];
+      ix->stream = user;
+      ix->capturing = nullptr;
+    }
+  } restore{ix, user};
   unsigned long long* stat = ix->sStat.need(4);
+  Pipeline pl;
+  pl.setup(ix, ix->lanes, nlanes, kmax, any_filtered, stat);
   const bool uniform =
       std::all_of(kq.begin(), kq.end(), [&](int32_t v) { return v == kq[0]; }) &&
       std::all_of(target.begin(), target.end(), [&](double v) { return v == target[0]; });
@@ -611,226 +880,17 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   LF_CUDA(cudaEventRecord(ev_start, user));
   for (int li = 0; li < nlanes; ++li) LF_CUDA(cudaStreamWaitEvent(ix->lanes[li].st, ev_start, 0));
 
-  int cur_lane = 0;
-  cudaStream_t s = user;
-  auto use_lane = [&](int li) {
-    cur_lane = li;
-    ix->sc = &ix->lanes[li];
-    s = ix->lanes[li].st;
-    ix->stream = s;
-  };
-  SelectArgs sa;
-  auto make_sa = [&](const LaneView& v, int nb, bool use_f) {
-    sa = SelectArgs();
-    sa.L = L;
-    sa.W = W;
-    sa.nq = nb;
-    sa.lb2 = v.lb2;
-    sa.thr = v.thr;
-    sa.F = ix->F;
-    sa.leaf_filter = ix->d_leaf_filter.p;
-    sa.alpha = ix->alpha.p;
-    sa.nc = ix->nc;
-    sa.leaf_off = ix->leaf_off.p;
-    sa.scanned = v.scanned;
-    sa.cur_lb = v.cur_lb;
-    sa.cur_leaf = v.cur_leaf;
-    sa.done = v.done;
-    sa.pairs = v.pairs;
-    sa.npairs = v.np;
-    sa.stat = stat;
-    sa.P = use_f ? v.P : nullptr;
-    sa.jpos = use_f ? v.jpos : nullptr;
-  };
-  auto select = [&](const LaneView& v) {
-    LF_CUDA(cudaMemsetAsync(v.np, 0, sizeof(int32_t), s));
-    ix->tick(5);
-    if (walk)
-      launch_select_walk(sa, v.ord, v.cursor, s);
-    else
-      launch_select(sa, s);
-    ix->tock();
-  };
-  auto round = [&](const LaneView& v, int nb) {
-    run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb * W, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr,
-              v.cand, v.cand_cnt, cap, stat + 2, stat + 3);
-    select(v);
-  };
-  // everything of one batch up to (and including) the select of its first wave
-  auto enqueue_head = [&](const LaneView& v, int nb, bool use_f) {
-    make_sa(v, nb, use_f);
-    ix->tick(2);
-    compute_bounds(ix, v.gQ, nb, v.lb2, v.route);
-    ix->tock();
-    if (v.tq.Qh) launch_tc_query_prep(v.gQ, nb, ix->mp, ix->kp, v.tq.Qh, v.tq.Qk, s);
-    if (use_f) {
-      ix->tick(4);
-      filter_forward(ix, v.gQ, nb, v.P, qb);
-      ix->tock();
-      launch_jpos(nb, v.dK, v.dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, v.jpos, s);
-    }
-    LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
-    if (walk) {
-      launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);
-      LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
-    }
-    search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, v.topk_cnt, v.thr, v.cand_cnt,
-                                                        v.cur_lb, v.cur_leaf, v.done);
-    LF_CHECK_LAUNCH();
-    // wave 0: every query searches its route leaf
-    launch_route_pairs(nb, v.route, L, v.scanned, ix->leaf_off.p, v.pairs, v.np, stat, s);
-    run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr, v.cand,
-              v.cand_cnt, cap, stat + 2, stat + 3);
-    select(v);
-  };
-  // a full batch of the same shape replays a captured graph of enqueue_head
-  // followed by its second wave and the next select (captured per lane)
-  auto graph_for = [&](const LaneView& v, int nb, bool use_f) -> BatchGraph* {
-    if (!ix->graphs_ok || nb != qb) return nullptr;
-    std::vector<BatchGraph>& graphs = ix->lanes[cur_lane].graphs;
-    const unsigned long long epoch0 = g_realloc_epoch;
-    for (auto& g : graphs)
-      if (g.nb == nb && g.kmax == kmax && g.use_f == (int)use_f && g.walk == (int)walk &&
-          g.profiling == (int)ix->profiling && g.epoch == epoch0)
-        return &g;
-    // graphs of an older epoch point at freed scratch: drop them
-    for (size_t i = 0; i < graphs.size();) {
-      BatchGraph& o = graphs[i];
-      if (o.epoch == epoch0) {
-        ++i;
-        continue;
-      }
-      if (o.exec) cudaGraphExecDestroy(o.exec);
-      for (cudaEvent_t e : o.ev) cudaEventDestroy(e);
-      graphs.erase(graphs.begin() + i);
-    }
-    graphs.emplace_back();
-    BatchGraph& g = graphs.back();
-    g.nb = nb;
-    g.kmax = kmax;
-    g.use_f = use_f;
-    g.walk = walk;
-    g.profiling = ix->profiling;
-    g.epoch = epoch0;
-    // the lane stream is the library's own (never the legacy default stream);
-    // nothing runs while capturing
-    cudaGraph_t graph = nullptr;
-    ix->capturing = &g;
-    const long long l0 = launches_so_far();
-    bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    if (ok) {
-      try {
-        enqueue_head(v, nb, use_f);
-        round(v, nb);
-      } catch (...) {
-        ok = false;
-      }
-      const cudaError_t e = cudaStreamEndCapture(s, &graph);
-      ok = ok && e == cudaSuccess && graph;
-    }
-    g.launches = launches_so_far() - l0;
-    count_launches(-g.launches);
-    ix->capturing = nullptr;
-    if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();
-    // a scratch buffer that grew while capturing invalidates the capture
-    const bool stale = g_realloc_epoch != epoch0;
-    if (!ok || stale) {
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-      for (cudaEvent_t e2 : g.ev) cudaEventDestroy(e2);
-      graphs.pop_back();
-      // a failure without a reallocation means capture is not available here
-      if (!ok && !stale) ix->graphs_ok = false;
-      return nullptr;
-    }
-    return &g;
-  };
-  // the lane's pair count goes to its pinned word; the host waits on the event
-  auto post_np = [&](const LaneView& v) {
-    Scratch& S = ix->lanes[cur_lane];
-    LF_CUDA(cudaMemcpyAsync(S.h_np, v.np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    LF_CUDA(cudaEventRecord(S.ev_np, s));
-  };
-  InFlight fl[2];
-  auto start = [&](int li, int64_t b0) {
-    use_lane(li);
-    const LaneView& v = lv[li];
-    const int nb = (int)std::min<int64_t>(qb, nq - b0);
-    // stage this batch's queries, k and targets into the lane's buffers
-    const float* src = queries + (size_t)b0 * ix->m;
-    const bool dev = on_device(src);
-    if (ix->mp != ix->m) LF_CUDA(cudaMemsetAsync(v.gQ, 0, sizeof(float) * nb * ix->mp, s));
-    LF_CUDA(cudaMemcpy2DAsync(v.gQ, sizeof(float) * ix->mp, src, sizeof(float) * ix->m,
-                              sizeof(float) * ix->m, (size_t)nb,
-                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (uniform) {
-      fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.dK, v.dT, kq[0], target[0]);
-      LF_CHECK_LAUNCH();
-    } else {
-      LF_CUDA(cudaMemcpyAsync(v.dK, kq.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-      LF_CUDA(cudaMemcpyAsync(v.dT, target.data() + b0, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
-    }
-    InFlight& f = fl[li];
-    f = InFlight();
-    f.active = true;
-    f.b0 = b0;
-    f.nb = nb;
-    f.use_f = std::any_of(target.begin() + b0, target.begin() + b0 + nb,
-                          [](double x) { return x < 1.0; });
-    if (f.use_f) st.filter_evals += (int64_t)nb * ix->F;
-    f.g = graph_for(v, nb, f.use_f);
-    if (f.g) {
-      LF_CUDA(cudaGraphLaunch(f.g->exec, s));
-      count_launches(f.g->launches);
-      st.graph_batches += 1;
-      f.waves = 2;
-      make_sa(v, nb, f.use_f);
-    } else {
-      enqueue_head(v, nb, f.use_f);
-      f.waves = 1;
-    }
-    post_np(v);
-  };
-  auto finish = [&](int li) {
-    InFlight& f = fl[li];
-    if (!f.active) return;
-    use_lane(li);
-    const LaneView& v = lv[li];
-    make_sa(v, f.nb, f.use_f);
-    Scratch& S = ix->lanes[li];
-    for (;;) {
-      LF_CUDA(cudaEventSynchronize(S.ev_np));
-      if (f.g && ix->profiling) {
-        for (size_t i = 0; i < f.g->kind.size(); ++i) {
-          float ms = 0.0f;
-          LF_CUDA(cudaEventElapsedTime(&ms, f.g->ev[2 * i], f.g->ev[2 * i + 1]));
-          ix->clock.ms[f.g->kind[i]] += ms;
-          ix->clock.n[f.g->kind[i]] += 1;
-        }
-      }
-      f.g = nullptr;
-      if (*S.h_np == 0) break;
-      if (++f.waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
-      round(v, f.nb);
-      post_np(v);
-    }
-    st.waves += f.waves;
-    st.batches += 1;
-    launch_write_results(f.nb, kmax, v.dK, v.topk, kmax, v.topk_cnt, v.out_i, v.out_d, s);
-    deliver(ids + (size_t)f.b0 * kmax, v.out_i, (size_t)f.nb * kmax, s);
-    deliver(dists + (size_t)f.b0 * kmax, v.out_d, (size_t)f.nb * kmax, s);
-    f.active = false;
-  };
-
   int bi = 0;
   for (int64_t b0 = 0; b0 < nq; b0 += qb, ++bi) {
     const int li = bi % nlanes;
-    finish(li);  // the lane's previous batch (two batches back)
-    start(li, b0);
+    const int nb = (int)std::min<int64_t>(qb, nq - b0);
+    pl.finish(li);  // the lane's previous batch (two batches back)
+    pl.start(li, queries + (size_t)b0 * ix->m, nb, kq.data() + (uniform ? 0 : b0),
+             target.data() + (uniform ? 0 : b0), uniform, ids + (size_t)b0 * kmax,
+             dists + (size_t)b0 * kmax);
   }
   // the remaining batches, oldest first
-  for (int i = 0; i < nlanes; ++i) finish((bi + i) % nlanes);
+  for (int i = 0; i < nlanes; ++i) pl.finish((bi + i) % nlanes);
 
   // the caller's stream continues after both lanes
   for (int li = 0; li < nlanes; ++li) {
@@ -843,6 +903,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, user));
   LF_CUDA(cudaStreamSynchronize(user));
   check_err_word(ix);
+  leafi_search_stats st = pl.st;
   st.leaves_scanned = (int64_t)h_stat[0];
   st.series_scanned = (int64_t)h_stat[1];
   st.distinct_series = (int64_t)h_stat[2];
@@ -882,6 +943,7 @@ leafi::DsTables leafi_index::ds() const {
 }
 
 void leafi_index::drop_graphs() {
+  ++graph_gen;  // graphs held elsewhere (a server's lanes) are re-captured
   for (auto& lane : lanes) {
     for (auto& g : lane.graphs) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -1709,6 +1771,331 @@ leafi_status leafi_search_mixed(leafi_index* index, const float* queries, int64_
       if (!(tg[i] > 0.0)) fail(LEAFI_EINVAL, "recall_target[%lld] must be > 0", (long long)i);
     }
     search_impl(index, queries, nq, kq, tg, kmax, ids, dists, stats);
+  });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- serving
+// A request loop over a resident index: pending queries of all requests form
+// batches that run through a two-lane pipeline of the server's own (the
+// index's entry points keep theirs); see include/leafi.h.
+struct leafi_server {
+  leafi_index* ix = nullptr;
+  leafi_serve_params p{};
+  leafi::Scratch lanes[2];
+  leafi::Pipeline pl;
+  leafi::DBuf<unsigned long long> stat;  // device counters of the server's batches
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;       // new work or stop (the worker waits)
+  std::condition_variable done_cv;  // a request finished (pollers wait)
+  bool stopping = false;
+  typedef std::chrono::steady_clock clock;
+  struct Request {
+    int nq = 0;
+    std::vector<float> q;    // [nq][m]
+    std::vector<int32_t> k;
+    std::vector<double> t;
+    std::vector<int64_t> ids;  // [nq][kmax]
+    std::vector<float> d;
+    int remaining = 0;
+    bool done = false;
+    size_t bytes = 0;
+    clock::time_point t_submit, t_done;
+  };
+  std::map<int64_t, Request> reqs;
+  std::deque<std::pair<int64_t, int>> pending;  // (ticket, query) not yet in a batch
+  std::deque<clock::time_point> pending_t;      // arrival of each pending query
+  int64_t next_ticket = 1;
+  size_t bytes = 0;
+  // per lane: the batch's members and its pinned host staging
+  std::vector<std::pair<int64_t, int>> members[2];
+  float* hq[2] = {nullptr, nullptr};
+  int32_t* hk[2] = {nullptr, nullptr};
+  double* ht[2] = {nullptr, nullptr};
+  int64_t* hi[2] = {nullptr, nullptr};
+  float* hd[2] = {nullptr, nullptr};
+  leafi_serve_stats counters{};
+  leafi_status failed = LEAFI_OK;
+  std::string fail_msg;
+};
+
+namespace {
+
+size_t serve_bytes_per_query(const leafi_server* sv) {
+  return (size_t)sv->ix->m * sizeof(float) + sizeof(int32_t) + sizeof(double) +
+         (size_t)sv->p.kmax * (sizeof(int64_t) + sizeof(float));
+}
+
+// run `fn` on the index (its mutex held, its device current); the index's
+// own entry points find their lane and stream restored afterwards
+template <class Fn>
+void on_index(leafi_server* sv, Fn&& fn) {
+  leafi_index* ix = sv->ix;
+  std::lock_guard<std::mutex> lk(ix->mu);
+  const cudaStream_t user = ix->stream;
+  struct Restore {
+    leafi_index* ix;
+    cudaStream_t user;
+    ~Restore() {
+      ix->sc = &ix->lanes[0];
+      ix->stream = user;
+      ix->capturing = nullptr;
+    }
+  } restore{ix, user};
+  fn();
+}
+
+void serve_loop(leafi_server* sv) {
+  leafi_index* ix = sv->ix;
+  cudaSetDevice(ix->device);
+  const int kmax = sv->p.kmax;
+  const auto wait = std::chrono::duration_cast<leafi_server::clock::duration>(
+      std::chrono::duration<double, std::milli>(sv->p.max_wait_ms));
+  int next = 0;  // lane of the next batch; when both lanes are busy it holds the older one
+  try {
+    for (;;) {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      const bool inflight = sv->pl.busy(0) || sv->pl.busy(1);
+      if (!inflight)
+        sv->cv.wait(lk, [&] { return sv->stopping || !sv->pending.empty(); });
+      if (sv->stopping && sv->pending.empty() && !inflight) break;
+      if (!sv->pending.empty() && !sv->pl.busy(next)) {
+        // launch a full batch at once; a partial one when the GPU is idle or
+        // its oldest query has waited long enough
+        const auto deadline = sv->pending_t.front() + wait;
+        if ((int)sv->pending.size() < sv->p.max_batch && inflight && !sv->stopping &&
+            leafi_server::clock::now() < deadline)
+          sv->cv.wait_until(lk, deadline, [&] {
+            return sv->stopping || (int)sv->pending.size() >= sv->p.max_batch;
+          });
+        const int nb = std::min<int>((int)sv->pending.size(), sv->p.max_batch);
+        auto& mem = sv->members[next];
+        mem.assign(sv->pending.begin(), sv->pending.begin() + nb);
+        sv->pending.erase(sv->pending.begin(), sv->pending.begin() + nb);
+        sv->pending_t.erase(sv->pending_t.begin(), sv->pending_t.begin() + nb);
+        bool use_f = false;
+        for (int j = 0; j < nb; ++j) {
+          const leafi_server::Request& r = sv->reqs.at(mem[j].first);
+          const int qi = mem[j].second;
+          std::memcpy(sv->hq[next] + (size_t)j * ix->m, r.q.data() + (size_t)qi * ix->m,
+                      sizeof(float) * ix->m);
+          sv->hk[next][j] = r.k[qi];
+          sv->ht[next][j] = r.t[qi];
+          use_f = use_f || r.t[qi] < 1.0;
+        }
+        lk.unlock();
+        const int li = next;
+        on_index(sv, [&] {
+          leafi::DeviceGuard dg(ix->device);
+          if (use_f) leafi::ensure_wsplit(ix);
+          sv->pl.setup(ix, sv->lanes, 2, kmax, ix->F > 0 && ix->nc > 0, sv->stat.p);
+          sv->pl.start(li, sv->hq[li], nb, sv->hk[li], sv->ht[li], false, sv->hi[li], sv->hd[li]);
+        });
+        next ^= 1;
+        continue;
+      }
+      if (!inflight) continue;
+      // collect the oldest batch in flight
+      const int li = sv->pl.busy(next) ? next : (next ^ 1);
+      lk.unlock();
+      on_index(sv, [&] {
+        leafi::DeviceGuard dg(ix->device);
+        sv->pl.finish(li);
+        LF_CUDA(cudaStreamSynchronize(sv->lanes[li].st));
+      });
+      lk.lock();
+      const auto now = leafi_server::clock::now();
+      const auto& mem = sv->members[li];
+      for (size_t j = 0; j < mem.size(); ++j) {
+        leafi_server::Request& r = sv->reqs.at(mem[j].first);
+        const int qi = mem[j].second;
+        std::memcpy(r.ids.data() + (size_t)qi * kmax, sv->hi[li] + j * kmax, sizeof(int64_t) * kmax);
+        std::memcpy(r.d.data() + (size_t)qi * kmax, sv->hd[li] + j * kmax, sizeof(float) * kmax);
+        if (--r.remaining == 0) {
+          r.done = true;
+          r.t_done = now;
+          sv->counters.requests += 1;
+          sv->counters.queries += r.nq;
+        }
+      }
+      sv->counters.batches += 1;
+      sv->done_cv.notify_all();
+    }
+  } catch (const Failure& e) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->failed = e.status;
+    sv->fail_msg = e.msg;
+    sv->done_cv.notify_all();
+  } catch (const std::exception& e) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->failed = LEAFI_EINTERNAL;
+    sv->fail_msg = e.what();
+    sv->done_cv.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+leafi_status leafi_serve_start(leafi_index* index, const leafi_serve_params* params,
+                               leafi_server** out) {
+  return guarded([&] {
+    require_device(index);
+    if (!out) fail(LEAFI_EINVAL, "out is NULL");
+    leafi_serve_params p{256, 1, 0.2, 0};
+    if (params) p = *params;
+    if (p.max_batch < 1 || p.max_batch > kBatch) fail(LEAFI_EINVAL, "max_batch must be in [1, %d]", kBatch);
+    if (p.kmax < 1 || p.kmax > LEAFI_MAX_K) fail(LEAFI_EINVAL, "kmax must be in [1, %d]", LEAFI_MAX_K);
+    if (!(p.max_wait_ms >= 0.0)) fail(LEAFI_EINVAL, "max_wait_ms must be >= 0");
+    if (p.max_bytes <= 0) p.max_bytes = (int64_t)1 << 30;
+    std::unique_ptr<leafi_server> sv(new leafi_server());
+    sv->ix = index;
+    sv->p = p;
+    {
+      DeviceGuard dg(index->device);
+      sv->stat.need(4);
+      LF_CUDA(cudaMemset(sv->stat.p, 0, 4 * sizeof(unsigned long long)));
+      for (int li = 0; li < 2; ++li) {
+        LF_CUDA(cudaMallocHost(&sv->hq[li], sizeof(float) * kBatch * index->m));
+        LF_CUDA(cudaMallocHost(&sv->hk[li], sizeof(int32_t) * kBatch));
+        LF_CUDA(cudaMallocHost(&sv->ht[li], sizeof(double) * kBatch));
+        LF_CUDA(cudaMallocHost(&sv->hi[li], sizeof(int64_t) * kBatch * p.kmax));
+        LF_CUDA(cudaMallocHost(&sv->hd[li], sizeof(float) * kBatch * p.kmax));
+      }
+    }
+    sv->worker = std::thread(serve_loop, sv.get());
+    *out = sv.release();
+  });
+}
+
+leafi_status leafi_serve_submit(leafi_server* sv, const float* queries, int64_t nq,
+                                const int32_t* k, const double* recall_target, int64_t* ticket) {
+  return guarded([&] {
+    if (!sv) fail(LEAFI_EINVAL, "server is NULL");
+    if (nq < 1 || nq > (int64_t)1 << 24) fail(LEAFI_EINVAL, "nq out of range");
+    if (!queries || !k || !recall_target || !ticket) fail(LEAFI_EINVAL, "NULL argument");
+    if (on_device(queries) || on_device(k) || on_device(recall_target))
+      fail(LEAFI_EINVAL, "serving takes host arrays");
+    bool filtered = false;
+    for (int64_t i = 0; i < nq; ++i) {
+      if (k[i] < 1 || k[i] > sv->p.kmax) fail(LEAFI_EINVAL, "k[%lld] out of [1, kmax]", (long long)i);
+      if (!(recall_target[i] > 0.0)) fail(LEAFI_EINVAL, "recall_target must be > 0");
+      filtered = filtered || recall_target[i] < 1.0;
+    }
+    const leafi_index* ix = sv->ix;
+    if (filtered && (ix->nc == 0 || ix->F == 0))
+      fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
+    const size_t need = (size_t)nq * serve_bytes_per_query(sv);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->failed != LEAFI_OK) fail(sv->failed, "server stopped: %s", sv->fail_msg.c_str());
+    if (sv->stopping) fail(LEAFI_EINVAL, "server is stopping");
+    if (sv->bytes + need > (size_t)sv->p.max_bytes)
+      fail(LEAFI_EAGAIN, "admission budget full (%zu of %lld bytes in use)", sv->bytes,
+           (long long)sv->p.max_bytes);
+    const int64_t t = sv->next_ticket++;
+    leafi_server::Request& r = sv->reqs[t];
+    r.nq = (int)nq;
+    r.q.assign(queries, queries + (size_t)nq * ix->m);
+    r.k.assign(k, k + nq);
+    r.t.assign(recall_target, recall_target + nq);
+    r.ids.assign((size_t)nq * sv->p.kmax, -1);
+    r.d.assign((size_t)nq * sv->p.kmax, std::numeric_limits<float>::infinity());
+    r.remaining = (int)nq;
+    r.bytes = need;
+    r.t_submit = leafi_server::clock::now();
+    sv->bytes += need;
+    for (int i = 0; i < (int)nq; ++i) {
+      sv->pending.emplace_back(t, i);
+      sv->pending_t.push_back(r.t_submit);
+    }
+    *ticket = t;
+    sv->cv.notify_one();
+  });
+}
+
+leafi_status leafi_serve_poll(leafi_server* sv, int64_t ticket, int64_t* ids, float* dists,
+                              double wait_ms, int32_t* done, double* latency_ms) {
+  return guarded([&] {
+    if (!sv || !done) fail(LEAFI_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) fail(LEAFI_EINVAL, "unknown ticket %lld", (long long)ticket);
+    if (!it->second.done && wait_ms > 0.0)
+      sv->done_cv.wait_for(lk, std::chrono::duration<double, std::milli>(wait_ms), [&] {
+        return sv->failed != LEAFI_OK || sv->reqs.at(ticket).done;
+      });
+    if (sv->failed != LEAFI_OK && !sv->reqs.at(ticket).done)
+      fail(sv->failed, "server stopped: %s", sv->fail_msg.c_str());
+    leafi_server::Request& r = sv->reqs.at(ticket);
+    *done = r.done ? 1 : 0;
+    if (!r.done) return;
+    if (ids) std::memcpy(ids, r.ids.data(), sizeof(int64_t) * r.ids.size());
+    if (dists) std::memcpy(dists, r.d.data(), sizeof(float) * r.d.size());
+    if (latency_ms)
+      *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+    sv->bytes -= r.bytes;
+    sv->reqs.erase(ticket);
+  });
+}
+
+leafi_status leafi_serve_get_stats(leafi_server* sv, leafi_serve_stats* stats) {
+  return guarded([&] {
+    if (!sv || !stats) fail(LEAFI_EINVAL, "NULL argument");
+    leafi_serve_stats c;
+    leafi_search_stats st;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      c = sv->counters;
+    }
+    unsigned long long h[4] = {0, 0, 0, 0};
+    on_index(sv, [&] {
+      DeviceGuard dg(sv->ix->device);
+      LF_CUDA(cudaMemcpy(h, sv->stat.p, sizeof(h), cudaMemcpyDeviceToHost));
+      st = sv->pl.st;
+    });
+    st.leaves_scanned = (int64_t)h[0];
+    st.series_scanned = (int64_t)h[1];
+    st.distinct_series = (int64_t)h[2];
+    st.rechecks = (int64_t)h[3];
+    c.graph_batches = st.graph_batches;
+    c.search = st;
+    *stats = c;
+  });
+}
+
+leafi_status leafi_serve_stop(leafi_server* sv) {
+  return guarded([&] {
+    if (!sv) return;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stopping = true;
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    const leafi_status failed = sv->failed;
+    const std::string msg = sv->fail_msg;
+    {
+      DeviceGuard dg(sv->ix->device);
+      for (int li = 0; li < 2; ++li) {
+        if (sv->lanes[li].st) cudaStreamSynchronize(sv->lanes[li].st);
+        for (auto& g : sv->lanes[li].graphs) {
+          if (g.exec) cudaGraphExecDestroy(g.exec);
+          for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+        }
+        sv->lanes[li].graphs.clear();
+        sv->lanes[li].release_lane();
+        cudaFreeHost(sv->hq[li]);
+        cudaFreeHost(sv->hk[li]);
+        cudaFreeHost(sv->ht[li]);
+        cudaFreeHost(sv->hi[li]);
+        cudaFreeHost(sv->hd[li]);
+      }
+      delete sv;
+    }
+    if (failed != LEAFI_OK) fail(failed, "server had stopped: %s", msg.c_str());
   });
 }
 

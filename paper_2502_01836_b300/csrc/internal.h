@@ -228,6 +228,7 @@ struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
   int nb = 0, kmax = 0, use_f = 0, walk = 0, profiling = 0;
   unsigned long long epoch = 0;
+  unsigned long long gen = 0;   // leafi_index::graph_gen at capture
   long long launches = 0;       // kernels in the graph (added to the launch counter per replay)
   std::vector<cudaEvent_t> ev;  // start/stop pairs recorded inside the graph
   std::vector<int> kind;
@@ -370,6 +371,7 @@ struct leafi_index {
   bool ticked = false;     // the last tick() recorded a start event
   leafi::BatchGraph* capturing = nullptr;  // entry being captured (tick/tock record into it)
   bool graphs_ok = true;                   // cleared if capture is not possible
+  unsigned long long graph_gen = 0;        // bumped by drop_graphs (filters, tables, profiling)
   void drop_graphs();
   leafi::DBuf<unsigned long long> scan_prof;  // tensor-core scan phase cycles (profiling)
   leafi::KernelClock clock;
