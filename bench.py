@@ -10,6 +10,14 @@ summarisation-bound search of the same index (exact mode) is timed beside it.
 
 Prints one JSON line (rank 0).  `--impl reference` times the oracle (plain C
 restatement, host cores) on bounded samples of the same workload instead.
+
+`--config` selects other measurement configurations, each printing its own
+JSON line (not the headline): `serving` (Poisson arrivals into the request
+loop, per-query k and recall target, p50/p99 latency), `mixed` (iSAX over
+uneven leaves, k in {1, 10, 100}, targets in {0.9, 0.95, 0.99}, with the
+training-target generation timed as a build phase) and `precision`
+(embedding-like m = 96, k = 10: tensor-core vs CUDA-core scan, error against
+float64, and the flat contraction over all series as the tensor-core case).
 """
 from __future__ import annotations
 
@@ -41,17 +49,29 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="leafi", choices=["leafi", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--config", default="batched",
+                    choices=["batched", "serving", "mixed", "precision"])
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--queries", type=int, default=10_000)
     ap.add_argument("--launch", type=int, default=256)
-    ap.add_argument("--filters", type=int, default=100)
-    ap.add_argument("--leaf-cap", type=int, default=10_000)
+    ap.add_argument("--filters", type=int, default=None)
+    ap.add_argument("--leaf-cap", type=int, default=None)
+    ap.add_argument("--rates", default="1000,5000,10000,20000,50000",
+                    help="serving: Poisson arrival rates, queries/s")
+    ap.add_argument("--seconds", type=float, default=1.0, help="serving: arrivals per rate")
+    ap.add_argument("--max-wait-ms", type=float, default=0.2)
     ap.add_argument("--epochs", type=int, default=1000)
     ap.add_argument("--wave", type=int, default=64)
     ap.add_argument("--target", type=float, default=0.99)
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    dflt = {"batched": (1_000_000, 10_000, 100), "serving": (50_000_000, 10_000, 1000),
+            "mixed": (25_000_000, 20_000, 1000), "precision": (10_000_000, 10_000, 0)}[a.config]
+    a.n = a.n if a.n is not None else dflt[0]
+    a.leaf_cap = a.leaf_cap if a.leaf_cap is not None else dflt[1]
+    a.filters = a.filters if a.filters is not None else dflt[2]
+    return a
 
 
 def peaks():
@@ -231,10 +251,288 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- other configurations
+def _gpu_setup():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2502_01836_b300 as lf
+    return torch, lf
+
+
+def _emit(line):
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(a):
+    """Poisson arrivals of single-query requests, k ~ U{1..100}, target in
+    {0.9, 0.95, 0.99, exact}, into the request loop over a resident index."""
+    torch, lf = _gpu_setup()
+    from paper_2502_01836_b300.workflow import enhance
+    t0 = time.perf_counter()
+    X = fx.random_walk(a.n, M)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=0))
+    t_build = time.perf_counter() - t0
+    info = lf.leafi_get_info(idx)
+    F = min(a.filters, info.n_leaves)
+    t0 = time.perf_counter()
+    enhance(idx, X, F, lf.TrainParams(max_epochs=a.epochs), kclasses=(1, 10, 100))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    kmax = 100
+    sv = lf.leafi_serve_start(idx, kmax=kmax, max_batch=a.launch, max_wait_ms=a.max_wait_ms)
+    rows = []
+    try:
+        for ri, lam in enumerate(float(x) for x in a.rates.split(",")):
+            n = int(min(40_000, max(200, lam * a.seconds)))
+            rng = np.random.default_rng(2502 + ri)
+            arrive = np.cumsum(rng.exponential(1.0 / lam, n))
+            ks = rng.integers(1, kmax + 1, n).astype(np.int32)
+            tg = rng.choice([0.9, 0.95, 0.99, 1.0], n).astype(np.float64)
+            Q = fx.test_queries(X, n, seed=fx.SEED_TEST + 100 + ri)
+            tickets = [None] * n
+            ready = threading.Event()
+            st0 = lf.leafi_serve_get_stats(sv)
+
+            def submitter():
+                base = time.perf_counter()
+                ready.set()
+                for i in range(n):
+                    while time.perf_counter() - base < arrive[i]:
+                        pass
+                    while True:
+                        try:
+                            tickets[i] = lf.leafi_serve_submit(sv, Q[i:i + 1], ks[i:i + 1],
+                                                               tg[i:i + 1])
+                            break
+                        except lf.LeafiError as e:
+                            if e.status != lf.EAGAIN:
+                                raise
+                            time.sleep(1e-4)
+                sub_done[0] = time.perf_counter() - base
+
+            sub_done = [0.0]
+            th = threading.Thread(target=submitter)
+            th.start()
+            ready.wait()
+            t_start = time.perf_counter()
+            ids = np.zeros((1, kmax), np.int64)
+            dd = np.zeros((1, kmax), np.float32)
+            lat = np.zeros(n)
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(1e-5)
+                while True:
+                    done, l_ms = lf.leafi_serve_poll(sv, tickets[i], ids, dd, wait_ms=100.0)
+                    if done:
+                        lat[i] = l_ms
+                        break
+            elapsed = time.perf_counter() - t_start
+            th.join()
+            st1 = lf.leafi_serve_get_stats(sv)
+            nb = st1["batches"] - st0["batches"]
+            rows.append({"offered_qps": lam, "requests": n, "achieved_qps": n / elapsed,
+                         "offered_span_s": float(arrive[-1]), "submit_span_s": sub_done[0],
+                         "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)),
+                         "batches": nb, "mean_batch": n / max(nb, 1)})
+    finally:
+        lf.leafi_serve_stop(sv)
+    _emit({"metric": "serving: latency and throughput under Poisson arrivals", "unit": "queries/s",
+           "config": {"workload": "DSTree over %d random walks x %d, leaf capacity %d, filters on "
+                                  "the %d largest leaves, single-query requests with k ~ U{1..100} "
+                                  "and target in {0.9, 0.95, 0.99, exact}" % (a.n, M, a.leaf_cap, F),
+                      "leaves": info.n_leaves, "max_batch": a.launch, "max_wait_ms": a.max_wait_ms},
+           "rates": rows, "data": "synthetic",
+           "build_s": {"data": t_data, "index": t_build, "train_and_tune": t_train},
+           "device_bytes": info.device_bytes})
+    lf.leafi_free(idx)
+
+
+def run_mixed(a):
+    """iSAX over uneven leaves; k in {1, 10, 100}, targets in {0.9, 0.95, 0.99};
+    training-target generation (per-query per-leaf nearest distance) timed."""
+    torch, lf = _gpu_setup()
+    from paper_2502_01836_b300.workflow import enhance
+    t0 = time.perf_counter()
+    X = fx.random_walk(a.n, M)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx = lf.leafi_build(X, lf.BuildParams(index_type=lf.ISAX, leaf_capacity=a.leaf_cap,
+                                           wave=a.wave, device=0))
+    t_build = time.perf_counter() - t0
+    info = lf.leafi_get_info(idx)
+    sizes = lf.leafi_leaf_sizes(idx)
+    F = min(a.filters, info.n_leaves)
+    fl = lf.leafi_select_leaves(idx, F)
+    lf.leafi_set_filters(idx, fl, *fx.filter_init(F, M, M))
+    members = fx.leaf_members_from(lf.leafi_leaf_of(idx), fl)
+    Qg, Ql = fx.training_queries(X, members, 1500, 500)
+    Tg = np.zeros((1500, F), np.float32)
+    Tl = np.zeros((F, 500), np.float32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lf.leafi_train_targets(idx, Qg, Ql, Tg, Tl)
+    torch.cuda.synchronize()
+    t_targets = time.perf_counter() - t0
+    pairs = (1500 + 500) * float(sizes[fl].sum())
+    t0 = time.perf_counter()
+    enhance(idx, X, F, lf.TrainParams(max_epochs=a.epochs), kclasses=(1, 10, 100))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    Q = fx.test_queries(X, a.queries)
+    rng = np.random.default_rng(2504)
+    ks = rng.choice([1, 10, 100], a.queries).astype(np.int32)
+    tg = rng.choice([0.9, 0.95, 0.99], a.queries).astype(np.float64)
+    Qd = torch.from_numpy(Q).cuda()
+    kd = torch.from_numpy(ks).cuda()
+    td = torch.from_numpy(tg).cuda()
+    ids = torch.zeros((a.queries, 100), dtype=torch.int64, device="cuda")
+    dd = torch.zeros((a.queries, 100), dtype=torch.float32, device="cuda")
+    one = torch.ones_like(td)
+    ex_i = torch.zeros_like(ids)
+    ex_d = torch.zeros_like(dd)
+
+    def timed(targets, oi, od):
+        for _ in range(a.warmup):
+            lf.leafi_search_mixed(idx, Qd, kd, targets, 100, oi, od)
+        torch.cuda.synchronize()
+        st = lf.SearchStats()
+        t0 = time.perf_counter()
+        for _ in range(max(1, a.steps // 10)):
+            lf.leafi_search_mixed(idx, Qd, kd, targets, 100, oi, od, st)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / max(1, a.steps // 10), st
+
+    ms_ex, st_ex = timed(one, ex_i, ex_d)
+    ms_lf, st_lf = timed(td, ids, dd)
+    a_ids, e_ids = ids.cpu().numpy(), ex_i.cpu().numpy()
+    rec = {}
+    for kc in (1, 10, 100):
+        for tv in (0.9, 0.95, 0.99):
+            sel = np.where((ks == kc) & (tg == tv))[0]
+            r = np.mean([len(set(a_ids[i, :kc]) & set(e_ids[i, :kc])) / kc for i in sel])
+            rec["k%d_t%.2f" % (kc, tv)] = float(r)
+    _emit({"metric": "mixed-k LeaFi-iSAX search: queries/s (and build-phase training targets)",
+           "value": a.queries / ms_lf, "unit": "queries/s",
+           "plain_lb_qps": a.queries / ms_ex, "recall_at_k_by_class": rec,
+           "series_scanned_per_query": st_lf.series_scanned / (a.queries * max(1, a.steps // 10)),
+           "plain_series_scanned_per_query": st_ex.series_scanned / (a.queries * max(1, a.steps // 10)),
+           "training_targets": {"seconds": t_targets, "global_queries": 1500,
+                                "local_queries_per_filter": 500, "filters": F,
+                                "pairs": pairs, "tflops_fp16_equiv": pairs * 2 * M / t_targets / 1e12},
+           "config": {"workload": "iSAX (16 segments, 8 bits) over %d random walks x %d, leaf "
+                                  "capacity %d, %d queries, k in {1,10,100}, targets in "
+                                  "{0.9,0.95,0.99}" % (a.n, M, a.leaf_cap, a.queries),
+                      "leaves": info.n_leaves, "leaf_size_min_median_max":
+                          [int(sizes.min()), float(np.median(sizes)), int(sizes.max())],
+                      "filters": F},
+           "build_s": {"data": t_data, "index": t_build, "train_and_tune": t_train},
+           "data": "synthetic"})
+    lf.leafi_free(idx)
+
+
+def run_precision(a):
+    """Embedding-like m = 96, k = 10 exact search: tensor-core (float16 products,
+    float32 re-check band) vs CUDA-core scan, error against float64; and the flat
+    contraction (one leaf holding every series) as the tensor-core case."""
+    torch, lf = _gpu_setup()
+    m, k = 96, 10
+    t0 = time.perf_counter()
+    X = fx.embedding_like(a.n, m)
+    t_data = time.perf_counter() - t0
+    Q = fx.test_queries(X, a.queries)
+    Qd = torch.from_numpy(Q).cuda()
+    out = {}
+    res = {}
+    for name, path, cap in (("tensor_core", 0, a.leaf_cap), ("cuda_core", 1, a.leaf_cap)):
+        idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=cap, wave=a.wave, device=0,
+                                               scan_path=path))
+        ids = torch.zeros((a.queries, k), dtype=torch.int64, device="cuda")
+        dd = torch.zeros((a.queries, k), dtype=torch.float32, device="cuda")
+        lf.leafi_exact_search(idx, Qd, k, ids, dd)
+        torch.cuda.synchronize()
+        st = lf.SearchStats()
+        reps = max(1, a.steps // 10)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            lf.leafi_exact_search(idx, Qd, k, ids, dd, st)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / reps
+        out[name] = {"qps": a.queries / sec, "series_scanned_per_query":
+                     st.series_scanned / (a.queries * reps),
+                     "rechecks_per_query": st.rechecks / (a.queries * reps),
+                     "band_hit_rate": st.rechecks / max(1, st.series_scanned)}
+        res[name] = (ids.cpu().numpy(), dd.cpu().numpy())
+        lf.leafi_free(idx)
+    same = bool(np.array_equal(res["tensor_core"][0], res["cuda_core"][0]) and
+                np.array_equal(res["tensor_core"][1], res["cuda_core"][1]))
+    # float64 reference on a sample: expanded-form distances rank candidates,
+    # the top 4k are re-ranked with direct float64 differences
+    rng = np.random.default_rng(2503)
+    smp = np.sort(rng.choice(a.queries, 64, replace=False))
+    X64 = X.astype(np.float64)
+    Q64 = Q[smp].astype(np.float64)
+    xx = np.einsum("ij,ij->i", X64, X64)
+    d2 = np.empty((len(smp), a.n))
+    for c0 in range(0, a.n, 1 << 20):
+        c1 = min(a.n, c0 + (1 << 20))
+        d2[:, c0:c1] = xx[c0:c1][None] - 2.0 * (Q64 @ X64[c0:c1].T)
+    d2 += np.einsum("ij,ij->i", Q64, Q64)[:, None]
+    cand = np.argpartition(d2, 4 * k, axis=1)[:, :4 * k]
+    recall, max_rel = [], 0.0
+    g_ids, g_d = res["tensor_core"]
+    for j, qi in enumerate(smp):
+        exact = np.sqrt(((X64[cand[j]] - Q64[j]) ** 2).sum(1))
+        truth = cand[j][np.lexsort((cand[j], exact))[:k]]
+        recall.append(len(set(g_ids[qi]) & set(truth)) / k)
+        dg = np.sqrt(((X64[g_ids[qi]] - Q64[j]) ** 2).sum(1))
+        max_rel = max(max_rel, float(np.max(np.abs(g_d[qi].astype(np.float64) - dg) / dg)))
+    # flat contraction: one leaf with every series, 256 queries, all pairs
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=a.n, wave=1, device=0))
+    lf.leafi_set_profiling(idx, 1)
+    ids = torch.zeros((256, k), dtype=torch.int64, device="cuda")
+    dd = torch.zeros((256, k), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        lf.leafi_exact_search(idx, Qd[:256], k, ids, dd)
+    lf.leafi_set_profiling(idx, 1)
+    reps = 5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        lf.leafi_exact_search(idx, Qd[:256], k, ids, dd)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / reps
+    kt = lf.leafi_get_kernel_times(idx)
+    scan_ms = kt["leaf_scan"][0] / max(1, kt["leaf_scan"][1])
+    flops = 2.0 * 256 * a.n * m
+    pk, pk_kind = peaks()
+    tc_peak = pk.get("bf16_tflops", 1800.0)
+    flat = {"qps": 256 / sec, "scan_ms_per_launch": scan_ms,
+            "achieved_tflops": flops / (scan_ms / 1e3) / 1e12, "peak_tflops": tc_peak,
+            "frac": flops / (scan_ms / 1e3) / 1e12 / tc_peak,
+            "peak_source": "fp16 dense = %s bf16 burst rate" % pk_kind,
+            "algorithmic_flop_per_launch": flops}
+    lf.leafi_free(idx)
+    _emit({"metric": "precision path, k = 10: exact search queries/s and error against float64",
+           "value": out["tensor_core"]["qps"], "unit": "queries/s", "paths": out,
+           "tensor_equals_cuda_core": same,
+           "vs_float64": {"sample": len(smp), "max_rel_distance_error": max_rel,
+                          "recall_at_10": float(np.mean(recall))},
+           "flat_contraction": flat,
+           "config": {"workload": "embedding-like (1,000 clusters, std 0.3) %d x %d, DSTree leaf "
+                                  "capacity %d, %d queries, k = 10" % (a.n, m, a.leaf_cap, a.queries)},
+           "build_s": {"data": t_data}, "data": "synthetic"})
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.config != "batched":
+        {"serving": run_serving, "mixed": run_mixed, "precision": run_precision}[a.config](a)
         return
     import torch
     rank, world, local, dist = dist_setup(a.gpus)
