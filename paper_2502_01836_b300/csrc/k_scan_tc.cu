@@ -72,6 +72,7 @@ struct TcShared {
   float4 qb[kTcG];     // per query: U_lo, U_hi, alpha, |q|^2 (see the epilogue)
   float qm[kTcG];      // |q|
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
+  int cnt4[4][kTcG];   // k > 1: entries of each TMEM lane quarter's list per query
   int ncb;             // buffered candidates of the current item
   unsigned long long rechecks;
 };
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   unsigned char* A1 = smem + tileA;
   unsigned char* B0 = smem + 2 * tileA;      // kTcG x Kp fp16, no swizzle
   unsigned char* B1 = B0 + (nbuf - 1) * tileB;
-  u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);  // [kTcG][a.k]
+  u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);  // [kTcG][a.k] (x4 quarters if k > 1)
   int* cb_pos = reinterpret_cast<int*>(lists + kTcG * a.k);
   int* cb_j = cb_pos + kCandCap;
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
@@ -510,10 +511,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           S.thrd[qq] = thd;
           S.H[qq] = thd;
           S.cnt[qq] = 0;
+          S.cnt4[0][qq] = S.cnt4[1][qq] = S.cnt4[2][qq] = S.cnt4[3][qq] = 0;
           S.wide[qq] = k1.y != 0.0f ? 1 : 0;
           S.qb[qq] = k0;
           S.qm[qq] = k1.x;
-          if (S.kq[qq] == 1) lists[qq * a.k] = th;
+          if (split) lists[qq * a.k] = th;
         } else {
           S.qb[qq] = make_float4(kInf, kInf, 0.0f, 0.0f);
           S.H[qq] = 0.0f;  // lo = inf > 0: never a candidate
@@ -611,55 +613,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
             }
           }
         } else {
-          // general k: immediate re-checks; warps 0-3 take turns inserting into
-          // the lists (warps 4-7 only join the barriers)
+          // general k: every TMEM lane quarter keeps its own top-k list per query
+          // (warps w and w + 4 share the quarter and split the 16-column groups),
+          // so no two warps ever write the same list; re-checks run at once,
+          // one candidate per lane, and the quarter lists merge at the item's end
+          const int qd = warp & 3;
+          u64* ql = lists + (size_t)qd * kTcG * a.k;  // this quarter's lists [kTcG][k]
           const float xnorm = sqrtf(xn);
-          for (int turn = 0; turn < 4; ++turn) {
-            for (int c0 = 0; okw && warp < 4 && c0 < N; c0 += 16) {
-              float d[16];
-              dev::tmem_ld16(tl + (uint32_t)c0, d);
+          const float vlo = xn * (1.0f - 1e-4f);
+          for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
+            float d[16];
+            dev::tmem_ld16(tl + (uint32_t)c0, d);
 #pragma unroll 1
-              for (int jj = 0; jj < 16; ++jj) {
-                const int j = c0 + jj;
-                if (j >= nqg) break;
-                const int kq = S.kq[j];
-                if (kq == 1 ? (turn != 0) : (turn != warp)) continue;
-                bool cand = false;
-                if (valid) {
-                  const float qss = S.qb[j].w, qm = S.qm[j];
-                  const float ap = qss + xn - 2.0f * d[jj];
-                  const float band = 2.0f * (cK * qm * xnorm + sm * (qm + xnorm)) + 1e-4f * (qss + xn);
-                  float T = S.thrd[j];
-                  if (kq == 1)
-                    T = fminf(T, dev::key_d2(*(volatile u64*)&lists[j * a.k]));
-                  else if (S.cnt[j] == kq)
-                    T = fminf(T, dev::key_d2(lists[j * a.k + kq - 1]));
-                  cand = S.wide[j] || !(ap - band > T);
-                }
-                u64 key = kNoKey;
-                if (cand) {
-                  const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
-                  key = dev::make_key(e, (uint32_t)a.ids[pos]);
-                  atomicAdd(&S.rechecks, 1ull);
-                }
-                if (kq == 1) {
-                  if (cand) atomicMin(&lists[j * a.k], key);
-                } else {
-                  unsigned mask = __ballot_sync(0xffffffffu, cand);
-                  int cc = S.cnt[j];
-                  while (mask) {
-                    const int src = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const u64 kk = __shfl_sync(0xffffffffu, key, src);
-                    const u64 kth = (cc == kq) ? lists[j * a.k + kq - 1] : S.thr[j];
-                    if (kk < kth) cc = dev::warp_insert(lists + j * a.k, cc, kq, kk, lane);
-                  }
-                  if (lane == 0) S.cnt[j] = cc;
-                  __syncwarp();
-                }
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = c0 + jj;
+              if (j >= nqg) break;
+              const int kq = S.kq[j];
+              int cc = S.cnt4[qd][j];
+              const float4 qb = S.qb[j];
+              const float lo = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
+              float T = S.thrd[j];
+              if (cc == kq) T = fminf(T, dev::key_d2(ql[j * a.k + kq - 1]));
+              const bool cand = valid && !(lo > T);
+              unsigned mask = __ballot_sync(0xffffffffu, cand);
+              if (!mask) continue;
+              u64 key = kNoKey;
+              if (cand) {
+                const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+                key = dev::make_key(e, (uint32_t)a.ids[pos]);
               }
+              if (lane == 0) atomicAdd(&S.rechecks, (unsigned long long)__popc(mask));
+              while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const u64 kk = __shfl_sync(0xffffffffu, key, src);
+                const u64 kth = (cc == kq) ? ql[j * a.k + kq - 1] : S.thr[j];
+                if (kk < kth) cc = dev::warp_insert(ql + j * a.k, cc, kq, kk, lane);
+              }
+              if (lane == 0) S.cnt4[qd][j] = cc;
+              __syncwarp();
             }
-            epi_sync();
           }
         }
         dev::tc_fence_before();
@@ -688,8 +681,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         epi_sync();
         if (tid == 0) S.ncb = 0;
       }
+      if (!split) {
+        // merge the quarter lists into quarter 0's, one warp per query
+        for (int q = warp; q < nqg; q += kEpiWarps) {
+          const int kq = S.kq[q];
+          int cc = S.cnt4[0][q];
+          for (int qd = 1; qd < 4; ++qd) {
+            const u64* src = lists + ((size_t)qd * kTcG + q) * a.k;
+            const int n = S.cnt4[qd][q];
+            for (int e = 0; e < n; ++e) {
+              const u64 kk = src[e];
+              const u64 kth = (cc == kq) ? lists[q * a.k + kq - 1] : S.thr[q];
+              if (kk < kth) cc = dev::warp_insert(lists + q * a.k, cc, kq, kk, lane);
+              else break;  // the rest of a sorted list is no better
+            }
+          }
+          if (lane == 0) S.cnt[q] = cc;
+          __syncwarp();
+        }
+        epi_sync();
+      }
       // k = 1 lists hold the part's best key if it beat the round's threshold
-      if (tid < nqg && S.kq[tid] == 1) S.cnt[tid] = (lists[tid * a.k] < S.thr[tid]) ? 1 : 0;
+      if (split && tid < nqg) S.cnt[tid] = (lists[tid * a.k] < S.thr[tid]) ? 1 : 0;
       epi_sync();
       for (int q = warp; q < nqg; q += kEpiWarps) {
         const int cc = S.cnt[q];
@@ -728,8 +741,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
 int tc_group_size() { return kTcG; }
 
 static size_t tc_dyn_smem(int kp, int k, int nbuf) {
-  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * kTcG * kp * 2 + (size_t)kTcG * k * 8 +
-         (k == 1 ? (size_t)kCandCap * 12 : 0);
+  // k = 1: one key per query plus the deferred re-check buffer; k > 1: one
+  // list per query and TMEM lane quarter
+  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * kTcG * kp * 2 +
+         (k == 1 ? (size_t)kTcG * 8 + (size_t)kCandCap * 12 : (size_t)4 * kTcG * k * 8);
 }
 
 int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem) {
