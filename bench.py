@@ -60,8 +60,10 @@ def parse():
                     help="serving: Poisson arrival rates, queries/s")
     ap.add_argument("--seconds", type=float, default=1.0, help="serving: arrivals per rate")
     ap.add_argument("--max-wait-ms", type=float, default=0.2)
+    ap.add_argument("--scan-path", type=int, default=0, help="0 tensor-core scan, 1 CUDA-core scan")
     ap.add_argument("--epochs", type=int, default=1000)
-    ap.add_argument("--wave", type=int, default=64)
+    ap.add_argument("--wave", type=int, default=None,
+                    help="leaves per wave (64; 512 for the iSAX configuration's small leaves)")
     ap.add_argument("--target", type=float, default=0.99)
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -71,6 +73,7 @@ def parse():
     a.n = a.n if a.n is not None else dflt[0]
     a.leaf_cap = a.leaf_cap if a.leaf_cap is not None else dflt[1]
     a.filters = a.filters if a.filters is not None else dflt[2]
+    a.wave = a.wave if a.wave is not None else (512 if a.config == "mixed" else 64)
     return a
 
 
@@ -360,7 +363,7 @@ def run_mixed(a):
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     idx = lf.leafi_build(X, lf.BuildParams(index_type=lf.ISAX, leaf_capacity=a.leaf_cap,
-                                           wave=a.wave, device=0))
+                                           wave=a.wave, device=0, scan_path=a.scan_path))
     t_build = time.perf_counter() - t0
     info = lf.leafi_get_info(idx)
     sizes = lf.leafi_leaf_sizes(idx)
@@ -394,19 +397,25 @@ def run_mixed(a):
     ex_i = torch.zeros_like(ids)
     ex_d = torch.zeros_like(dd)
 
+    reps = max(1, a.steps // 30)
+
     def timed(targets, oi, od):
-        for _ in range(a.warmup):
-            lf.leafi_search_mixed(idx, Qd, kd, targets, 100, oi, od)
+        lf.leafi_search_mixed(idx, Qd, kd, targets, 100, oi, od)   # warm-up (graphs, buffers)
         torch.cuda.synchronize()
         st = lf.SearchStats()
         t0 = time.perf_counter()
-        for _ in range(max(1, a.steps // 10)):
+        for _ in range(reps):
             lf.leafi_search_mixed(idx, Qd, kd, targets, 100, oi, od, st)
         torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / max(1, a.steps // 10), st
+        return (time.perf_counter() - t0) / reps, st
 
     ms_ex, st_ex = timed(one, ex_i, ex_d)
     ms_lf, st_lf = timed(td, ids, dd)
+    lf.leafi_set_profiling(idx, 2)
+    lf.leafi_search_mixed(idx, Qd, kd, td, 100, ids, dd)
+    torch.cuda.synchronize()
+    kt = lf.leafi_get_kernel_times(idx)
+    lf.leafi_set_profiling(idx, 0)
     a_ids, e_ids = ids.cpu().numpy(), ex_i.cpu().numpy()
     rec = {}
     for kc in (1, 10, 100):
@@ -417,8 +426,10 @@ def run_mixed(a):
     _emit({"metric": "mixed-k LeaFi-iSAX search: queries/s (and build-phase training targets)",
            "value": a.queries / ms_lf, "unit": "queries/s",
            "plain_lb_qps": a.queries / ms_ex, "recall_at_k_by_class": rec,
-           "series_scanned_per_query": st_lf.series_scanned / (a.queries * max(1, a.steps // 10)),
-           "plain_series_scanned_per_query": st_ex.series_scanned / (a.queries * max(1, a.steps // 10)),
+           "series_scanned_per_query": st_lf.series_scanned / (a.queries * reps),
+           "plain_series_scanned_per_query": st_ex.series_scanned / (a.queries * reps),
+           "waves_per_batch": st_lf.waves / max(1, st_lf.batches),
+           "kernel_ms_per_search": {k: [v[0], v[1]] for k, v in kt.items() if v[1]},
            "training_targets": {"seconds": t_targets, "global_queries": 1500,
                                 "local_queries_per_filter": 500, "filters": F,
                                 "pairs": pairs, "tflops_fp16_equiv": pairs * 2 * M / t_targets / 1e12},
@@ -427,7 +438,7 @@ def run_mixed(a):
                                   "{0.9,0.95,0.99}" % (a.n, M, a.leaf_cap, a.queries),
                       "leaves": info.n_leaves, "leaf_size_min_median_max":
                           [int(sizes.min()), float(np.median(sizes)), int(sizes.max())],
-                      "filters": F},
+                      "filters": F, "wave": a.wave, "scan_path": a.scan_path},
            "build_s": {"data": t_data, "index": t_build, "train_and_tune": t_train},
            "data": "synthetic"})
     lf.leafi_free(idx)

@@ -19,7 +19,7 @@ namespace {
 typedef unsigned long long u64;
 constexpr double kDeflate = 1.0 - 1e-4;
 constexpr int kMaxSortN = 4096;
-constexpr int kMaxWave = 64;
+constexpr int kMaxWave = 4096;
 
 __device__ __forceinline__ float key_d2(u64 k) { return __uint_as_float((uint32_t)(k >> 32)); }
 
@@ -225,8 +225,11 @@ __global__ void __launch_bounds__(kSimThreads) sim_kernel(CalibArgs a, long long
     long long h = ct[route];
     float bsf2 = (cnt == kc) ? key_d2(w[kc - 1]) : __int_as_float(0x7f800000);
     int cursor = 0;
-    int picks[kMaxWave];
     for (int guard = 0; guard <= L; ++guard) {
+      // pick the wave with the bound of its start, then walk the same range
+      // again to merge the picked leaves (no per-thread pick list)
+      const int c0 = cursor;
+      const double bsf = (double)__fsqrt_rn(bsf2);
       int np = 0;
       while (cursor < L && np < a.W) {
         const int leaf = ord[cursor];
@@ -241,18 +244,26 @@ __global__ void __launch_bounds__(kSimThreads) sim_kernel(CalibArgs a, long long
         const int f = a.leaf_filter[leaf];
         if (f >= 0) {
           const double df = __dsub_rn((double)a.P[(size_t)c * a.F + f], a.alpha[(size_t)f * a.nc + j]);
-          if (df > (double)__fsqrt_rn(bsf2)) {
+          if (df > bsf) {
             ++cursor;
             continue;
           }
         }
-        picks[np++] = leaf;
+        ++np;
         ++cursor;
       }
       if (np == 0) break;
-      for (int z = 0; z < np; ++z) {
-        merge_list(w, cnt, kc, lists + (size_t)picks[z] * a.lk_stride);
-        h += ct[picks[z]];
+      int taken = 0;
+      for (int p = c0; taken < np; ++p) {
+        const int leaf = ord[p];
+        if (leaf == route) continue;
+        const int f = a.leaf_filter[leaf];
+        if (f >= 0 &&
+            __dsub_rn((double)a.P[(size_t)c * a.F + f], a.alpha[(size_t)f * a.nc + j]) > bsf)
+          continue;
+        merge_list(w, cnt, kc, lists + (size_t)leaf * a.lk_stride);
+        h += ct[leaf];
+        ++taken;
       }
       bsf2 = (cnt == kc) ? key_d2(w[kc - 1]) : __int_as_float(0x7f800000);
     }

@@ -306,12 +306,14 @@ def test_captured_batches_match_eager(ds, tuned, k, target):
         assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
 
 
-def test_more_than_4096_leaves():
+@pytest.mark.parametrize("wave", [8, 300])
+def test_more_than_4096_leaves(wave):
     """The visiting order of more than one shared-memory tile of leaves (global
-    bitonic stages), in the search and in the auto-tuner's simulation."""
+    bitonic stages), in the search and in the auto-tuner's simulation; waves of
+    a few and of hundreds of (tiny) leaves."""
     X = fx.random_walk(60000, 64, seed=71)
     Q = fx.test_queries(X, 300, seed=72)        # two batches: both lanes
-    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=10, wave=8, device=0))
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=10, wave=wave, device=0))
     try:
         t = O.Tree(X, "dstree", leaf_cap=10, init_segments=4)
         assert t.L > 4096
@@ -322,7 +324,7 @@ def test_more_than_4096_leaves():
         lf.leafi_exact_search(idx, Q, 5, ids, d, st)
         bf_ids, bf_d2 = O.knn(X, Q, 5)
         assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
-        o_ids, _, o_st, _ = O.leafi_search(t, None, None, None, Q, 5, -1, 8)
+        o_ids, _, o_st, _ = O.leafi_search(t, None, None, None, Q, 5, -1, wave)
         assert int(o_st[:, 0].sum()) == st.leaves_scanned
         assert int(o_st[:, 1].sum()) == st.series_scanned
         # auto-tuner over all leaves with untrained filters on the 16 largest
@@ -335,7 +337,7 @@ def test_more_than_4096_leaves():
         alpha = np.zeros((16, 120))
         qp = np.zeros((1, 120))
         lf.leafi_get_autotuners(idx, alpha, qp)
-        o_alpha, o_qp = O.fit_autotuner(t, Wt, fl, Qc, 1, 8)
+        o_alpha, o_qp = O.fit_autotuner(t, Wt, fl, Qc, 1, wave)
         tol = 1e-5 * _pred_scale(Wt, Qc).max()
         assert np.abs(alpha - o_alpha).max() <= tol
         diff = np.abs(qp[0] - o_qp)
