@@ -284,6 +284,7 @@ def run_serving(a):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     kmax = 100
+    lf.leafi_set_profiling(idx, 2)
     sv = lf.leafi_serve_start(idx, kmax=kmax, max_batch=a.launch, max_wait_ms=a.max_wait_ms)
     rows = []
     try:
@@ -340,9 +341,14 @@ def run_serving(a):
                          "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)),
                          "batches": nb, "mean_batch": n / max(nb, 1)})
+        sst = lf.leafi_serve_get_stats(sv)
     finally:
         lf.leafi_serve_stop(sv)
+    kt = lf.leafi_get_kernel_times(idx)
+    lf.leafi_set_profiling(idx, 0)
     _emit({"metric": "serving: latency and throughput under Poisson arrivals", "unit": "queries/s",
+           "kernel_ms_total": {k: [v[0], v[1]] for k, v in kt.items() if v[1]},
+           "server_stats": sst,
            "config": {"workload": "DSTree over %d random walks x %d, leaf capacity %d, filters on "
                                   "the %d largest leaves, single-query requests with k ~ U{1..100} "
                                   "and target in {0.9, 0.95, 0.99, exact}" % (a.n, M, a.leaf_cap, F),

@@ -15,6 +15,9 @@ sigma < 1e-8 gives the all-zero series) and then stored as float32.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 __all__ = [
@@ -65,22 +68,38 @@ def znorm_rows(a: np.ndarray, out: np.ndarray | None = None) -> np.ndarray:
     return out
 
 
-def random_walk(n: int, m: int, seed: int = SEED_DATA, start: int = 0) -> np.ndarray:
-    """Series start..start+n-1 of the RandWalk collection (n x m float32)."""
-    out = np.empty((n, m), dtype=np.float32)
+def _random_walk_into(out: np.ndarray, m: int, seed: int, start: int, lo: int, hi_end: int):
     buf = np.empty((_BLOCK, m), dtype=np.float64)
-    i = start
-    end = start + n
-    while i < end:
+    i = lo
+    while i < hi_end:
         b = i // _BLOCK
         b0 = b * _BLOCK
-        hi = min(end, b0 + _BLOCK)
+        hi = min(hi_end, b0 + _BLOCK)
         g = _rng(seed, _TAG_WALK, b)
         blk = buf[:hi - b0]
         g.standard_normal(out=blk)
         np.cumsum(blk, axis=1, out=blk)
         znorm_rows(blk[i - b0:], out=out[i - start:hi - start])
         i = hi
+
+
+def random_walk(n: int, m: int, seed: int = SEED_DATA, start: int = 0) -> np.ndarray:
+    """Series start..start+n-1 of the RandWalk collection (n x m float32).
+
+    Every block of 4096 series has its own counter-based stream, so the
+    result does not depend on how the blocks are shared among threads."""
+    out = np.empty((n, m), dtype=np.float32)
+    end = start + n
+    workers = min(16, os.cpu_count() or 1) if n >= (1 << 20) else 1
+    if workers == 1:
+        _random_walk_into(out, m, seed, start, start, end)
+        return out
+    # block-aligned ranges, one per task
+    step = max(_BLOCK, ((n // (4 * workers)) // _BLOCK) * _BLOCK)
+    edges = [start] + [b for b in range((start // step + 1) * step, end, step)] + [end]
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(lambda r: _random_walk_into(out, m, seed, start, r[0], r[1]),
+                    zip(edges[:-1], edges[1:])))
     return out
 
 
