@@ -334,7 +334,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
   int32_t* item_leaf =
       use_tc ? ix->sc->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix->tree)) : nullptr;
   launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
-               use_tc ? tc_group_size() : scan_group_size(), cnt, goff, ioff, grouped, nitems,
+               use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped, nitems,
                distinct_stat, s, item_leaf);
   const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
   if (use_tc) {
@@ -353,6 +353,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.Qh = tq.Qh;
     t.Qk = tq.Qk;
     t.nbuf = nbuf;
+    t.G = tc_group_size(kstride);
     t.pairs = grouped;
     t.grp_off = goff;
     t.item_off = ioff;

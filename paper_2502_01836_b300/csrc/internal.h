@@ -166,6 +166,7 @@ struct TcScanArgs {
   const __half* Qh;                // [nq][kp] float16 queries (launch_tc_query_prep)
   const float4* Qk;                // [nq][2] band constants (launch_tc_query_prep)
   int nbuf;                        // query tiles in shared memory (tc_scan_plan)
+  int G;                           // queries per work item (tc_group_size)
   const Pair* pairs;
   const int32_t* grp_off;
   const int32_t* item_off;
@@ -179,7 +180,7 @@ struct TcScanArgs {
   unsigned long long* stat;        // nullable: [0] += canonical re-checks
   unsigned long long* prof;        // nullable: per-phase cycle counters (16)
 };
-int tc_group_size();
+int tc_group_size(int k);
 // query tiles (2 or 1) the tensor-core scan can keep for rows of kp halves and
 // top-k lists of k keys within `smem_optin` bytes; 0 if it does not fit
 int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem);

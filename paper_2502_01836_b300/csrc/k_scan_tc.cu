@@ -99,15 +99,16 @@ struct Item {
 __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
   const int leaf = a.item_leaf[item];
   const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
-  const int ngroups = (cnt + kTcG - 1) / kTcG;
+  const int G = a.G;
+  const int ngroups = (cnt + G - 1) / G;
   const int local = item - a.item_off[leaf];
   const int part = local / ngroups, grp = local % ngroups;
   Item it;
   it.p0 = a.leaf_off[leaf] + (int64_t)part * a.part;
   it.p1 = min(it.p0 + (int64_t)a.part, a.leaf_off[leaf + 1]);
-  it.nqg = min(kTcG, cnt - grp * kTcG);
+  it.nqg = min(G, cnt - grp * G);
   it.N = ((it.nqg + 15) / 16) * 16;
-  it.pr = a.pairs + a.grp_off[leaf] + grp * kTcG;
+  it.pr = a.pairs + a.grp_off[leaf] + grp * G;
   it.nchunks = (int)((it.p1 - it.p0 + kTcRows - 1) / kTcRows);
   return it;
 }
@@ -260,14 +261,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int Kp = a.kp;                       // fp16 row length (multiple of 64)
   const int tileA = kTcRows * Kp * 2;        // bytes per A stage
-  const int tileB = kTcG * Kp * 2;           // bytes per query tile
+  const int G = a.G;                         // queries per work item (64, or 16 for large k)
+  const int tileB = G * Kp * 2;              // bytes per query tile
   const int nbuf = a.nbuf;                   // query tiles (1 or 2)
   unsigned char* A0 = smem;
   unsigned char* A1 = smem + tileA;
-  unsigned char* B0 = smem + 2 * tileA;      // kTcG x Kp fp16, no swizzle
+  unsigned char* B0 = smem + 2 * tileA;      // G x Kp fp16, no swizzle
   unsigned char* B1 = B0 + (nbuf - 1) * tileB;
-  u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);  // [kTcG][a.k] (x4 quarters if k > 1)
-  int* cb_pos = reinterpret_cast<int*>(lists + kTcG * a.k);
+  u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);  // [G][a.k] (x4 quarters if k > 1)
+  int* cb_pos = reinterpret_cast<int*>(lists + G * a.k);
   int* cb_j = cb_pos + kCandCap;
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
   const bool split = (a.k == 1);             // k = 1: halves on alternate accumulators, deferred re-checks
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           // so no two warps ever write the same list; re-checks run at once,
           // one candidate per lane, and the quarter lists merge at the item's end
           const int qd = warp & 3;
-          u64* ql = lists + (size_t)qd * kTcG * a.k;  // this quarter's lists [kTcG][k]
+          u64* ql = lists + (size_t)qd * G * a.k;  // this quarter's lists [G][k]
           const float xnorm = sqrtf(xn);
           const float vlo = xn * (1.0f - 1e-4f);
           for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
@@ -687,7 +689,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           const int kq = S.kq[q];
           int cc = S.cnt4[0][q];
           for (int qd = 1; qd < 4; ++qd) {
-            const u64* src = lists + ((size_t)qd * kTcG + q) * a.k;
+            const u64* src = lists + ((size_t)qd * G + q) * a.k;
             const int n = S.cnt4[qd][q];
             for (int e = 0; e < n; ++e) {
               const u64 kk = src[e];
@@ -738,13 +740,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
 
 }  // namespace
 
-int tc_group_size() { return kTcG; }
+// queries per work item: 64, or 16 when per-quarter top-k lists of 64 queries
+// would not fit in shared memory (large k)
+int tc_group_size(int k) { return k > 32 ? 16 : kTcG; }
 
 static size_t tc_dyn_smem(int kp, int k, int nbuf) {
   // k = 1: one key per query plus the deferred re-check buffer; k > 1: one
   // list per query and TMEM lane quarter
-  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * kTcG * kp * 2 +
-         (k == 1 ? (size_t)kTcG * 8 + (size_t)kCandCap * 12 : (size_t)4 * kTcG * k * 8);
+  const size_t G = (size_t)tc_group_size(k);
+  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * G * kp * 2 +
+         (k == 1 ? G * 8 + (size_t)kCandCap * 12 : (size_t)4 * G * k * 8);
 }
 
 int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem) {
