@@ -41,6 +41,11 @@ M = 256
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}
 SMS = 148
 FP32_LANES = 128
+# DRAM bytes (read + write) per tensor-core leaf-scan launch on the default
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# eight consecutive launches of the timed region, averaged), valid only for the
+# kernel source it was taken on (SHA-1 of k_scan_tc.cu)
+SCAN_TRAFFIC = {"bytes_per_launch": 472.2e6, "kernel_sha1": "7bd0b0a903d32315e4b50290f8adc159b5208f7e"}
 
 
 def parse():
@@ -683,8 +688,21 @@ def main():
         # peak (2 m FLOP per pair), so the stream of distinct float16 rows is the bound
         tc_tf = per_launch_pairs * 2.0 * M / (scan_launch_ms / 1e3) / 1e12
         tc_peak = pk.get("bf16_tflops", 1800.0)
+        traffic = None
+        try:
+            import hashlib
+            src = os.path.join(ROOT, "paper_2502_01836_b300", "csrc", "k_scan_tc.cu")
+            with open(src, "rb") as f:
+                same_kernel = hashlib.sha1(f.read()).hexdigest() == SCAN_TRAFFIC["kernel_sha1"]
+            default_workload = (a.n, a.leaf_cap, a.filters, a.launch, a.wave) == \
+                (1_000_000, 10_000, 100, 256, 64)
+            if same_kernel and default_workload:
+                traffic = SCAN_TRAFFIC["bytes_per_launch"]
+        except OSError:
+            pass
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": roof_hbm, "traffic": None, "peak_source": pk_kind,
+                    "frac": roof_hbm, "traffic": traffic, "peak_source": pk_kind,
+                    "bytes_per_launch": bytes_launch,
                     "tensor_view": {"achieved_tflops": tc_tf, "peak": tc_peak,
                                     "frac": tc_tf / tc_peak,
                                     "peak_source": "fp16 dense = measured bf16 burst rate"}}
