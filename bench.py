@@ -197,6 +197,10 @@ def workload_config(a):
                   % (a.n * M * 4 / 1e9, a.n * M * 2 / 1e9)}
 
 
+def clock_mhz(clocks, fallback):
+    return clocks.get("sm_mhz") or fallback
+
+
 def cpu_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
@@ -715,6 +719,16 @@ def main():
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": roof_hbm, "traffic": None, "peak_source": pk_kind}
     roofline["kernel"] = "leaf_scan (tensor cores)" if info.tensor_scan else "leaf_scan (CUDA cores)"
+    span = kt_all.get("_phases", {}).get("epilogue_span", 0.0)
+    if info.tensor_scan and span > 0:
+        # the same bytes over the time a CTA is resident (per-SM cycle counter of
+        # the profiled step): separates the kernel's own rate from launch gaps and
+        # from waiting for SMs held by the other lane's scan
+        step_bytes = distinct * info.scan_row_bytes
+        resident_s = span / SMS / (clock_mhz(clocks, clk) * 1e6)
+        roofline["resident_view"] = {"achieved_gbs": step_bytes / resident_s / 1e9,
+                                     "frac": step_bytes / resident_s / 1e9 / hbm,
+                                     "resident_ms_per_step": resident_s * 1e3}
     roofline["bytes_per_series"] = info.scan_row_bytes
     roofline["hbm_view"] = {"achieved_gbs": achieved_gbs, "frac": roof_hbm}
     if not info.tensor_scan:

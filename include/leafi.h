@@ -128,7 +128,7 @@ leafi_status leafi_get_kernel_times(leafi_index* index, double* ms /* [6] */,
  * (the TMA thread); 5 wait for the query tile, 6 wait for a TMA load, 7 wait
  * for a free accumulator, 14 MMA issue, 8 commits (the MMA thread); 12 wait for a free
  * query tile, 13 gather (the query loader); 9 work items, 10 chunks read by
- * epilogue warp 0. */
+ * epilogue warp 0; 15 epilogue warp 0's cycles from kernel entry to exit. */
 leafi_status leafi_get_scan_phases(leafi_index* index, double* cycles);
 /* Series per leaf (host array of n_leaves). Leaves are numbered depth-first,
  * left child first. */

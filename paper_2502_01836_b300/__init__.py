@@ -213,7 +213,7 @@ def leafi_get_kernel_times(index):
 
 SCAN_PHASES = ["item_setup", "wait_accumulator", "epilogue", "flush_emit", "wait_stage_free",
                "wait_query_tile", "wait_tma", "wait_accumulator_free", "commit", "items", "chunks",
-               "tma_issue", "wait_tile_free", "gather", "mma_issue"]
+               "tma_issue", "wait_tile_free", "gather", "mma_issue", "epilogue_span"]
 
 
 def leafi_get_scan_phases(index):

@@ -81,7 +81,7 @@ struct TcShared {
 // epilogue warp 0 lane 0: 0 item set-up, 1 wait accumulator, 2 epilogue, 3 flush+emit;
 // MMA thread: 5 wait query tile, 6 wait TMA, 7 wait accumulator free, 14 MMA issue, 8 commits;
 // load thread: 4 wait stage free, 11 TMA issue; 9 items, 10 chunks (of warp 0);
-// query loader lane 0: 12 wait tile free, 13 gather
+// query loader lane 0: 12 wait tile free, 13 gather; 15 epilogue warp 0 from kernel entry to exit
 #define PROF_T0() long long _pt = clock64()
 #define PROF_ADD(i)                                              \
   do {                                                           \
@@ -254,6 +254,7 @@ __global__ void tc_query_prep_kernel(const float* __restrict__ Q, int nq, int mp
 __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     const __grid_constant__ CUtensorMap tmap, TcScanArgs a, const int32_t* __restrict__ n_items_dev,
     const int32_t* __restrict__ slot_k) {
+  const long long t_enter = clock64();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ TcShared S;
   // 128-byte swizzled tiles need 1024-byte aligned bases
@@ -728,6 +729,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       if (S.stop) break;
     }
   }
+  if (prof_on && tid == 0) pr[15] = (unsigned long long)(clock64() - t_enter);  // epilogue warp 0's span
   if (prof_on)
     for (int i = 0; i < 16; ++i)
       if (pr[i]) atomicAdd(&a.prof[i], pr[i]);
