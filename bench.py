@@ -643,6 +643,9 @@ def main():
     # exact (plain-bound) search: ground truth and the comparison arm
     ms_ex, lat_ex, st_ex, _, _, _ = timed(1.0, ex_ids, ex_d)
     ms, lat, st, launches, clocks, kt = timed(a.target, ids, dd, profile=True)
+    # Alg. 3 with this device's costs (the run above uses the configuration's
+    # 100 largest leaves, i.e. th = 0)
+    sel_fl, sel_rep = lf.leafi_select_leaves_auto(idx, a=2.0, mem_cap=8 << 30)
     # per-kind breakdown and scan phase counters from one more (untimed) step
     lf.leafi_set_profiling(idx, 2)
     run(a.target, ids, dd)
@@ -773,6 +776,7 @@ def main():
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
             "waves_per_launch": st["waves"] / max(st["batches"], 1),
             "graph_batch_fraction": st["graph_batches"] / max(st["batches"], 1),
+            "leaf_selection_alg3": dict(sel_rep, a=2.0, mem_cap_bytes=8 << 30),
             "kernel_ms_per_step": {k: v[0] for k, v in kt_all.items()
                                    if not k.startswith("_") and v[1]},
             "kernel_ms_note": "one extra untimed step with every kind timed",

@@ -172,6 +172,32 @@ leafi_status leafi_leaf_lower_bounds_noalloc(leafi_index* index, const float* qu
  * greedy selection of Alg. 3 with threshold th = 0 (out: int32 [n_filters]). */
 leafi_status leafi_select_leaves(const leafi_index* index, int32_t n_filters,
                                  int32_t* filter_leaf);
+/* Leaf selection of Alg. 3 with this device's costs: t^F = time of one
+ * (query, filter) prediction in the batched forward, t^S = time of one
+ * (query, series) distance in the batched leaf scan, both measured here on
+ * probe batches of 256 of the index's own series (probe filters of hidden
+ * width `hidden`, 0 = m, with zero weights); threshold th = a t^F / t^S; w =
+ * device bytes of one filter (weights, the tensor-core forward's tf32
+ * planes, one auto-tuner column of 300 offsets).  Leaves by non-increasing
+ * size (ties: lower id) are taken while size >= th and w^M + w <= mem_cap.
+ * filter_leaf (host) needs room for n_leaves entries; report (nullable)
+ * returns the measured costs, th, w and the count.  Does not change the
+ * index's filters. */
+typedef struct {
+  double a;         /* 1 / p^F, the expected filter pruning ratio's inverse (2 in the paper) */
+  int64_t mem_cap;  /* c^M: device bytes available to filters */
+  int32_t hidden;   /* hidden width of the filters to come (0 = m) */
+} leafi_select_params;
+typedef struct {
+  double t_filter_s;     /* t^F */
+  double t_series_s;     /* t^S */
+  double threshold;      /* th = a t^F / t^S (series) */
+  double filter_bytes;   /* w */
+  int32_t n_selected;
+} leafi_select_report;
+leafi_status leafi_select_leaves_auto(leafi_index* index, const leafi_select_params* params,
+                                      int32_t* filter_leaf, leafi_select_report* report);
+
 /* Install F filters on the given leaves with weights W1 [F][h][m], b1 [F][h],
  * w2 [F][h], b2 [F] (float32; h = hidden width).  Clears the auto-tuners. */
 leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F,

@@ -1237,6 +1237,39 @@ void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const 
   free(leaves);
 }
 
+/* Alg. 3 (leaf node selection), in its order: sort by size, then one pass */
+typedef struct {
+  int64_t size;
+  int32_t id;
+} sized_leaf;
+
+static int by_size_desc(const void* pa, const void* pb) {
+  const sized_leaf* a = (const sized_leaf*)pa;
+  const sized_leaf* b = (const sized_leaf*)pb;
+  if (a->size != b->size) return a->size > b->size ? -1 : 1;
+  return a->id - b->id;
+}
+
+int32_t or_select_leaves_alg3(const int64_t* sizes, int32_t L, double th, double w, double cap,
+                              int32_t* out) {
+  sized_leaf* v = (sized_leaf*)malloc(sizeof(sized_leaf) * (size_t)(L > 0 ? L : 1));
+  for (int32_t i = 0; i < L; ++i) {
+    v[i].size = sizes[i];
+    v[i].id = i;
+  }
+  qsort(v, (size_t)L, sizeof(sized_leaf), by_size_desc);
+  double used = 0.0;
+  int32_t n = 0;
+  for (int32_t j = 0; j < L; ++j) {
+    if ((double)v[j].size >= th && used + w <= cap) {
+      out[n++] = v[j].id;
+      used += w;
+    }
+  }
+  free(v);
+  return n;
+}
+
 int32_t or_offset_position(const double* qprime, int64_t nc, double target) {
   int32_t j = -1;
   for (int64_t i = 0; i < nc; ++i) {

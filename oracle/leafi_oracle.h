@@ -95,6 +95,13 @@ void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const 
                       const float* Qc, int64_t nc, int k, int wave,
                       double* alpha_sorted, double* qprime);
 
+/* Leaf selection (Alg. 3): leaves by non-increasing size (ties: lower id);
+ * a leaf is taken when its size is at least th = a t^F / t^S and one more
+ * filter of w bytes still fits in the budget cap (reading of the memory test:
+ * w^M + w <= c^M).  Writes the selected leaf ids to out, returns their count. */
+int32_t or_select_leaves_alg3(const int64_t* sizes, int32_t L, double th, double w, double cap,
+                              int32_t* out);
+
 /* Sorted position j* for a target (STEP reading): the largest j with
  * qprime[j] >= target; -1 means "no position meets it -> filters off". */
 int32_t or_offset_position(const double* qprime, int64_t nc, double target);

@@ -14,7 +14,7 @@ import numpy as np
 __all__ = [
     "build", "lib", "sqdist", "knn", "segment_stats", "Tree", "isax_breakpoints",
     "mlp_forward", "train_targets", "TrainParams", "train", "fit_autotuner",
-    "offset_position", "steffen_eval", "leafi_search", "recall_at_k",
+    "offset_position", "steffen_eval", "leafi_search", "recall_at_k", "select_leaves_alg3",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -81,6 +81,9 @@ def lib():
                                f32p, f32p, i32p, f32p, f32p, f32p, f32p, i32p, f64p]
         L.or_fit_autotuner.argtypes = [vp, f32p, f32p, f32p, f32p, i32p, C.c_int, C.c_int, f32p,
                                        C.c_int64, C.c_int, C.c_int, f64p, f64p]
+        L.or_select_leaves_alg3.argtypes = [C.POINTER(C.c_int64), C.c_int32, C.c_double,
+                                            C.c_double, C.c_double, C.POINTER(C.c_int32)]
+        L.or_select_leaves_alg3.restype = C.c_int32
         L.or_offset_position.argtypes = [f64p, C.c_int64, C.c_double]
         L.or_offset_position.restype = C.c_int32
         L.or_steffen_eval.argtypes = [f64p, f64p, C.c_int, C.c_double]
@@ -244,6 +247,16 @@ def fit_autotuner(tree: Tree, weights, filter_leaf, Qc, k, wave):
     lib().or_fit_autotuner(tree._h, W1, b1, w2, b2, np.ascontiguousarray(filter_leaf, np.int32),
                            F, h, Qc, nc, k, wave, alpha, qp)
     return alpha, qp
+
+
+def select_leaves_alg3(sizes, th, w, cap):
+    """Alg. 3: ids of the selected leaves (largest first)."""
+    sz = np.ascontiguousarray(sizes, np.int64)
+    out = np.zeros(max(1, sz.shape[0]), np.int32)
+    n = lib().or_select_leaves_alg3(sz.ctypes.data_as(C.POINTER(C.c_int64)), sz.shape[0],
+                                    float(th), float(w), float(cap),
+                                    out.ctypes.data_as(C.POINTER(C.c_int32)))
+    return out[:n]
 
 
 def offset_position(qprime, target):

@@ -25,7 +25,7 @@ __all__ = [
     "KERNEL_KINDS", "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases", "SCAN_PHASES",
     "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS", "EAGAIN", "ServeParams", "ServeStats",
     "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
-    "leafi_serve_stop",
+    "leafi_serve_stop", "leafi_select_leaves_auto", "SelectParams", "SelectReport",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,7 +47,7 @@ EXPORTED_SYMBOLS = [
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
     "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases",
     "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
-    "leafi_serve_stop",
+    "leafi_serve_stop", "leafi_select_leaves_auto",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -96,6 +96,16 @@ class SearchStats(C.Structure):
                 ("filter_evals", C.c_int64), ("waves", C.c_int64), ("batches", C.c_int64),
                 ("distinct_series", C.c_int64), ("rechecks", C.c_int64),
                 ("graph_batches", C.c_int64)]
+
+
+class SelectParams(C.Structure):
+    _fields_ = [("a", C.c_double), ("mem_cap", C.c_int64), ("hidden", C.c_int32)]
+
+
+class SelectReport(C.Structure):
+    _fields_ = [("t_filter_s", C.c_double), ("t_series_s", C.c_double),
+                ("threshold", C.c_double), ("filter_bytes", C.c_double),
+                ("n_selected", C.c_int32)]
 
 
 class ServeParams(C.Structure):
@@ -150,6 +160,7 @@ def lib():
             "leafi_serve_poll": [vp, i64, vp, vp, f64, C.POINTER(i32), C.POINTER(f64)],
             "leafi_serve_get_stats": [vp, C.POINTER(ServeStats)],
             "leafi_serve_stop": [vp],
+            "leafi_select_leaves_auto": [vp, C.POINTER(SelectParams), vp, C.POINTER(SelectReport)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -287,6 +298,15 @@ def leafi_select_leaves(index, n_filters):
     out = np.empty(n_filters, np.int32)
     _check(lib().leafi_select_leaves(index, n_filters, out.ctypes.data))
     return out
+
+
+def leafi_select_leaves_auto(index, a=2.0, mem_cap=8 << 30, hidden=0):
+    """Alg. 3 with this device's measured t^F and t^S: (filter_leaf, report dict)."""
+    out = np.zeros(max(1, leafi_get_info(index).n_leaves), np.int32)
+    rep = SelectReport()
+    _check(lib().leafi_select_leaves_auto(index, C.byref(SelectParams(a, mem_cap, hidden)),
+                                          out.ctypes.data, C.byref(rep)))
+    return out[:rep.n_selected].copy(), {f: getattr(rep, f) for f, _ in SelectReport._fields_}
 
 
 def leafi_set_filters(index, filter_leaf, W1, b1, w2, b2):

@@ -1336,6 +1336,106 @@ leafi_status leafi_select_leaves(const leafi_index* index, int32_t n_filters, in
   });
 }
 
+leafi_status leafi_select_leaves_auto(leafi_index* index, const leafi_select_params* params,
+                                      int32_t* filter_leaf, leafi_select_report* report) {
+  return guarded([&] {
+    require_device(index);
+    if (!params || !filter_leaf) fail(LEAFI_EINVAL, "NULL argument");
+    if (!(params->a > 0.0)) fail(LEAFI_EINVAL, "a must be > 0");
+    if (params->mem_cap < 0) fail(LEAFI_EINVAL, "mem_cap must be >= 0");
+    const int h = params->hidden > 0 ? params->hidden : index->m;
+    if (h > 4096) fail(LEAFI_EINVAL, "hidden width out of range");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    leafi_index* ix = index;
+    cudaStream_t s = ix->stream;
+    const HostTree& t = ix->tree;
+    const int m = ix->m, mp = ix->mp;
+    const int nq = (int)std::min<int64_t>(256, ix->n);
+    const float* dQ = ix->X.p;  // the first nq stored series serve as probe queries
+    cudaEvent_t e0, e1;
+    LF_CUDA(cudaEventCreate(&e0));
+    LF_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+      cudaEvent_t a, b;
+      ~Ev() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+      }
+    } evg{e0, e1};
+    auto timed = [&](auto&& body, int reps) {
+      for (int i = 0; i < 2; ++i) body();
+      LF_CUDA(cudaEventRecord(e0, s));
+      for (int i = 0; i < reps; ++i) body();
+      LF_CUDA(cudaEventRecord(e1, s));
+      LF_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      LF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return (double)ms / 1e3 / reps;
+    };
+    // t^F: 256 probe queries against 64 probe filters through the forward the
+    // index uses (tensor cores when the width fits one MMA)
+    const int Fp = 64;
+    const int hp = (h + 15) / 16 * 16, Kq = (m + 31) / 32 * 32;
+    const bool tc = ix->scan_path == 0 && filter_tc_fits(m, h, ix->smem_optin);
+    DBuf<float> W1t, b1, w2, b2, P, Ws, Qs;
+    LF_CUDA(cudaMemsetAsync(W1t.need((size_t)Fp * m * h), 0, sizeof(float) * Fp * m * h, s));
+    LF_CUDA(cudaMemsetAsync(b1.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
+    LF_CUDA(cudaMemsetAsync(w2.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
+    LF_CUDA(cudaMemsetAsync(b2.need(Fp), 0, sizeof(float) * Fp, s));
+    P.need((size_t)nq * Fp);
+    double t_f = 0.0;
+    if (tc) {
+      launch_wsplit(W1t.p, Fp, m, h, Ws.need((size_t)2 * Fp * hp * Kq), s);
+      CUtensorMap wm, qm;
+      const int nqp = (nq + 127) / 128 * 128;
+      Qs.need((size_t)2 * nqp * Kq);
+      if (!encode_2d(&wm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws.p, (uint64_t)Kq,
+                     (uint64_t)2 * Fp * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp) ||
+          !encode_2d(&qm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Qs.p, (uint64_t)Kq, (uint64_t)2 * nqp,
+                     (uint64_t)Kq * 4, 32, 128))
+        fail(LEAFI_ECUDA, "cannot encode the probe tensor maps");
+      t_f = timed([&] {
+        launch_filter_tc(qm, wm, dQ, nq, mp, m, Fp, h, Qs.p, b1.p, w2.p, b2.p, P.p, ix->sErr.p, s);
+      }, 10);
+    } else {
+      t_f = timed([&] {
+        launch_filter_forward(dQ, nq, mp, m, Fp, h, W1t.p, b1.p, w2.p, b2.p, P.p, s);
+      }, 10);
+    }
+    t_f /= (double)nq * Fp;
+    // t^S: the same probe queries against the largest leaf, through the scan
+    int big = 0;
+    for (int l = 1; l < t.n_leaves; ++l)
+      if (t.leaf_off[l + 1] - t.leaf_off[l] > t.leaf_off[big + 1] - t.leaf_off[big]) big = l;
+    const int64_t bigsz = t.leaf_off[big + 1] - t.leaf_off[big];
+    std::vector<int32_t> lv(nq, big);
+    DBuf<int32_t> dl;
+    dl.upload(lv, s);
+    DBuf<unsigned long long> keys;
+    DBuf<int32_t> cnt;
+    double t_s = timed([&] { leaf_knn_device(ix, dQ, nq, dl.p, 1, 1, keys, cnt); }, 5);
+    t_s /= (double)nq * (double)bigsz;
+    const double th = params->a * t_f / t_s;
+    const double w = (double)((size_t)h * m + 2 * (size_t)h + 1) * 4.0 +
+                     (tc ? 2.0 * hp * Kq * 4.0 : 0.0) + 300.0 * 8.0;
+    std::vector<int32_t> idx(t.n_leaves);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+      return (t.leaf_off[x + 1] - t.leaf_off[x]) > (t.leaf_off[y + 1] - t.leaf_off[y]);
+    });
+    double used = 0.0;
+    int32_t n = 0;
+    for (int j : idx) {
+      if ((double)(t.leaf_off[j + 1] - t.leaf_off[j]) >= th && used + w <= (double)params->mem_cap) {
+        filter_leaf[n++] = j;
+        used += w;
+      }
+    }
+    if (report) *report = leafi_select_report{t_f, t_s, th, w, n};
+  });
+}
+
 leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F, int32_t h,
                                const float* W1, const float* b1, const float* w2, const float* b2) {
   return guarded([&] {

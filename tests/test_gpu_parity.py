@@ -437,3 +437,17 @@ def test_end_to_end_recall_meets_target():
         assert np.array_equal(e_ids, bf)
     finally:
         lf.leafi_free(idx)
+
+
+def test_leaf_selection_alg3_with_measured_costs(ds):
+    """Alg. 3 on the device: the measured t^F and t^S give th = a t^F / t^S, and
+    the selection equals the oracle's Alg. 3 on the same sizes, th, w and budget."""
+    X, Q, idx, t = ds
+    sizes = t.leaf_sizes()
+    for a, cap in ((2.0, 8 << 30), (2.0, 5 * 800_000), (50.0, 8 << 30)):
+        fl, rep = lf.leafi_select_leaves_auto(idx, a=a, mem_cap=cap)
+        assert rep["t_filter_s"] > 0 and rep["t_series_s"] > 0
+        assert abs(rep["threshold"] - a * rep["t_filter_s"] / rep["t_series_s"]) <= 1e-9 * rep["threshold"]
+        expect = O.select_leaves_alg3(sizes, rep["threshold"], rep["filter_bytes"], cap)
+        assert np.array_equal(fl, expect)
+        assert rep["n_selected"] == len(fl)

@@ -383,3 +383,22 @@ def test_train_targets_are_leaf_minima(small_index):
         for i in range(5):
             d = min(O.sqdist(Ql[f, i], X[s]) for s in mem)
             assert Tl[f, i] == np.sqrt(np.float32(d))
+
+
+def test_select_leaves_alg3_pins():
+    """Alg. 3 on a hand example: leaves by size (ties: lower id), the size
+    threshold, and the memory budget read as w^M + w <= c^M."""
+    sizes = [5, 9, 9, 2, 7]
+    # th = 6: the leaves of size 9, 9 and 7 qualify; a budget of two filters takes the two largest
+    assert list(O.select_leaves_alg3(sizes, 6, 1, 2)) == [1, 2]
+    assert list(O.select_leaves_alg3(sizes, 6, 1, 1e9)) == [1, 2, 4]
+    # th = 0 and room for all: every leaf, largest first, equal sizes by id
+    assert list(O.select_leaves_alg3(sizes, 0, 1, 1e9)) == [1, 2, 4, 0, 3]
+    # 1.5 + 1.5 <= 3 admits two filters; a third would overshoot the budget
+    assert list(O.select_leaves_alg3(sizes, 0, 1.5, 3.0)) == [1, 2]
+    assert list(O.select_leaves_alg3(sizes, 10, 1, 1e9)) == []
+    # th = 0 and a budget of F filters: the F largest (the configurations' rule)
+    rng = np.random.default_rng(5)
+    sz = rng.integers(1, 50, 200)
+    order = sorted(range(200), key=lambda i: (-sz[i], i))
+    assert list(O.select_leaves_alg3(sz, 0, 3.0, 3.0 * 17)) == order[:17]
