@@ -587,7 +587,7 @@ def main():
 
     def run(target, out_i, out_d, lat=None, stats=None, per_launch=False):
         # one call over all queries (the library runs them in launches of
-        # a.launch, two in flight), or one call per launch for the latencies
+        # a.launch, several in flight), or one call per launch for the latencies
         spans = ([(b * a.launch, min(a.queries, (b + 1) * a.launch)) for b in range(nl)]
                  if per_launch else [(0, a.queries)])
         for s0, s1 in spans:

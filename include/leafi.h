@@ -311,7 +311,7 @@ leafi_status leafi_search_mixed(leafi_index* index, const float* queries, int64_
  * by the index mutex).  Requests carry their own k and recall target per
  * query.  Pending queries of all requests form batches of up to `max_batch`
  * (continuous batching: a request that arrives while batches are on the GPU
- * joins the next batch; two batches are in flight, so one's preparation
+ * joins the next batch; up to four batches are in flight, so one's preparation
  * overlaps the other's scan), and each batch groups its (query, leaf) pairs
  * by leaf, so requests share leaf scans.  A partial batch launches when
  * nothing is in flight or its oldest query has waited `max_wait_ms`.

@@ -27,6 +27,8 @@ namespace {
 thread_local std::string g_last_error;
 constexpr int kPart = 2048;       // series per scan work item
 constexpr int kBatch = 256;       // queries per search batch
+constexpr int kSearchLanes = 8;   // batches of one search call in flight
+constexpr int kServeLanes = 4;    // batches of a server in flight
 constexpr size_t kKnnBudget = 256ull << 20;  // bytes of candidate buffer per leaf-knn batch
 }  // namespace
 
@@ -518,7 +520,8 @@ struct InFlight {
 }  // namespace
 
 // The batch pipeline of Alg. 2: batches of up to kBatch queries alternate
-// between two lanes, each with its own scratch and stream, so the preparation
+// between lanes (up to kSearchLanes for a search call, kServeLanes for a
+// server), each with its own scratch and stream, so the preparation
 // of one batch (bounds, filters, leaf order) and the host's wait for its wave
 // count overlap the other batch's scan.  A full batch replays a captured graph
 // of its first two waves; later waves are enqueued as the host learns that
@@ -532,8 +535,8 @@ struct Pipeline {
   bool walk = true;
   unsigned long long* stat = nullptr;   // device counters of the pipeline's batches
   leafi_search_stats st{};
-  LaneView lv[2];
-  InFlight fl[2];
+  LaneView lv[kMaxLanes];
+  InFlight fl[kMaxLanes];
   SelectArgs sa;
   int cur_lane = 0;
   cudaStream_t s = nullptr;
@@ -852,7 +855,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
   if (any_filtered) ensure_wsplit(ix);
   const int qb = kBatch;
-  const int nlanes = nq > qb ? 2 : 1;
+  const int nlanes = (int)std::min<int64_t>(kSearchLanes, (nq + qb - 1) / qb);
   const cudaStream_t user = ix->stream;
   // every entry point after this one runs on lanes[0] and the caller's stream
   struct Restore {
@@ -885,7 +888,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   for (int64_t b0 = 0; b0 < nq; b0 += qb, ++bi) {
     const int li = bi % nlanes;
     const int nb = (int)std::min<int64_t>(qb, nq - b0);
-    pl.finish(li);  // the lane's previous batch (two batches back)
+    pl.finish(li);  // the lane's previous batch (nlanes batches back)
     pl.start(li, queries + (size_t)b0 * ix->m, nb, kq.data() + (uniform ? 0 : b0),
              target.data() + (uniform ? 0 : b0), uniform, ids + (size_t)b0 * kmax,
              dists + (size_t)b0 * kmax);
@@ -1879,12 +1882,12 @@ leafi_status leafi_search_mixed(leafi_index* index, const float* queries, int64_
 
 // ---------------------------------------------------------------- serving
 // A request loop over a resident index: pending queries of all requests form
-// batches that run through a two-lane pipeline of the server's own (the
+// batches that run through a multi-lane pipeline of the server's own (the
 // index's entry points keep theirs); see include/leafi.h.
 struct leafi_server {
   leafi_index* ix = nullptr;
   leafi_serve_params p{};
-  leafi::Scratch lanes[2];
+  leafi::Scratch lanes[kServeLanes];
   leafi::Pipeline pl;
   leafi::DBuf<unsigned long long> stat;  // device counters of the server's batches
   std::thread worker;
@@ -1911,12 +1914,12 @@ struct leafi_server {
   int64_t next_ticket = 1;
   size_t bytes = 0;
   // per lane: the batch's members and its pinned host staging
-  std::vector<std::pair<int64_t, int>> members[2];
-  float* hq[2] = {nullptr, nullptr};
-  int32_t* hk[2] = {nullptr, nullptr};
-  double* ht[2] = {nullptr, nullptr};
-  int64_t* hi[2] = {nullptr, nullptr};
-  float* hd[2] = {nullptr, nullptr};
+  std::vector<std::pair<int64_t, int>> members[kServeLanes];
+  float* hq[kServeLanes] = {};
+  int32_t* hk[kServeLanes] = {};
+  double* ht[kServeLanes] = {};
+  int64_t* hi[kServeLanes] = {};
+  float* hd[kServeLanes] = {};
   leafi_serve_stats counters{};
   leafi_status failed = LEAFI_OK;
   std::string fail_msg;
@@ -1954,11 +1957,17 @@ void serve_loop(leafi_server* sv) {
   const int kmax = sv->p.kmax;
   const auto wait = std::chrono::duration_cast<leafi_server::clock::duration>(
       std::chrono::duration<double, std::milli>(sv->p.max_wait_ms));
-  int next = 0;  // lane of the next batch; when both lanes are busy it holds the older one
+  int next = 0;  // lane of the next batch; batches start on the lanes in turn, so the
+                 // oldest batch in flight is the first busy lane from `next` on
+  auto any_busy = [&] {
+    for (int i = 0; i < kServeLanes; ++i)
+      if (sv->pl.busy(i)) return true;
+    return false;
+  };
   try {
     for (;;) {
       std::unique_lock<std::mutex> lk(sv->mu);
-      const bool inflight = sv->pl.busy(0) || sv->pl.busy(1);
+      const bool inflight = any_busy();
       if (!inflight)
         sv->cv.wait(lk, [&] { return sv->stopping || !sv->pending.empty(); });
       if (sv->stopping && sv->pending.empty() && !inflight) break;
@@ -1991,15 +2000,16 @@ void serve_loop(leafi_server* sv) {
         on_index(sv, [&] {
           leafi::DeviceGuard dg(ix->device);
           if (use_f) leafi::ensure_wsplit(ix);
-          sv->pl.setup(ix, sv->lanes, 2, kmax, ix->F > 0 && ix->nc > 0, sv->stat.p);
+          sv->pl.setup(ix, sv->lanes, kServeLanes, kmax, ix->F > 0 && ix->nc > 0, sv->stat.p);
           sv->pl.start(li, sv->hq[li], nb, sv->hk[li], sv->ht[li], false, sv->hi[li], sv->hd[li]);
         });
-        next ^= 1;
+        next = (next + 1) % kServeLanes;
         continue;
       }
       if (!inflight) continue;
       // collect the oldest batch in flight
-      const int li = sv->pl.busy(next) ? next : (next ^ 1);
+      int li = next;
+      while (!sv->pl.busy(li)) li = (li + 1) % kServeLanes;
       lk.unlock();
       on_index(sv, [&] {
         leafi::DeviceGuard dg(ix->device);
@@ -2059,7 +2069,7 @@ leafi_status leafi_serve_start(leafi_index* index, const leafi_serve_params* par
       DeviceGuard dg(index->device);
       sv->stat.need(4);
       LF_CUDA(cudaMemset(sv->stat.p, 0, 4 * sizeof(unsigned long long)));
-      for (int li = 0; li < 2; ++li) {
+      for (int li = 0; li < kServeLanes; ++li) {
         LF_CUDA(cudaMallocHost(&sv->hq[li], sizeof(float) * kBatch * index->m));
         LF_CUDA(cudaMallocHost(&sv->hk[li], sizeof(int32_t) * kBatch));
         LF_CUDA(cudaMallocHost(&sv->ht[li], sizeof(double) * kBatch));
@@ -2180,7 +2190,7 @@ leafi_status leafi_serve_stop(leafi_server* sv) {
     const std::string msg = sv->fail_msg;
     {
       DeviceGuard dg(sv->ix->device);
-      for (int li = 0; li < 2; ++li) {
+      for (int li = 0; li < kServeLanes; ++li) {
         if (sv->lanes[li].st) cudaStreamSynchronize(sv->lanes[li].st);
         for (auto& g : sv->lanes[li].graphs) {
           if (g.exec) cudaGraphExecDestroy(g.exec);

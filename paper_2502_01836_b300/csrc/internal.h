@@ -291,6 +291,7 @@ void launch_calib_sim(const CalibArgs& a, cudaStream_t s);
 }  // namespace leafi
 
 namespace leafi {
+constexpr int kMaxLanes = 8;  // search lanes an index (or a server) may use
 // Per-lane scratch of the search driver and the other entry points.
 struct Scratch {
   DBuf<float> sQ;
@@ -358,8 +359,8 @@ struct leafi_index {
   leafi::DBuf<int32_t> d_kclasses;
 
   // scratch (grown on demand): lanes[0] serves every entry point; a search of
-  // more than one batch alternates batches between the two lanes
-  leafi::Scratch lanes[2];
+  // more than one batch spreads its batches over several lanes in turn
+  leafi::Scratch lanes[leafi::kMaxLanes];
   leafi::Scratch* sc = &lanes[0];  // lane in use
   leafi::DBuf<int32_t> sErr;       // error word shared by all launches
   leafi::DBuf<unsigned long long> sStat;  // search counters of one call

@@ -6,7 +6,7 @@ leaf, Alg. 1), 100 test queries, recall target 0.99, and exact mode.
 
 Batched configuration: 1,000,000 random walks x 256, capacity 10,000, filters
 on the 100 largest leaves, 10,000 test queries searched in one call (launches
-of 256 queries, two in flight) - the launch configuration bench.py times.
+of 256 queries, several in flight) - the launch configuration bench.py times.
 Mixed-k configuration (reduced from 25M series): iSAX, 16 PAA segments,
 cardinality 256, uneven leaves; k drawn from {1, 10, 100}, recall targets from
 {0.9, 0.95, 0.99}; training targets (the build phase) bit-exact.
@@ -184,7 +184,7 @@ def test_mixed_k_isax_config_reduced():
 def test_precision_config_reduced(path):
     m, n, k = 96, 300_000, 10
     X = fx.embedding_like(n, m)
-    Q = fx.test_queries(X, 300, seed=fx.SEED_TEST + 3)   # two batches: both lanes
+    Q = fx.test_queries(X, 300, seed=fx.SEED_TEST + 3)   # two batches: two lanes
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=10_000, wave=W_WAVE, device=0,
                                            scan_path=path))
     try:

@@ -312,7 +312,7 @@ def test_more_than_4096_leaves(wave):
     bitonic stages), in the search and in the auto-tuner's simulation; waves of
     a few and of hundreds of (tiny) leaves."""
     X = fx.random_walk(60000, 64, seed=71)
-    Q = fx.test_queries(X, 300, seed=72)        # two batches: both lanes
+    Q = fx.test_queries(X, 300, seed=72)        # two batches: two lanes
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=10, wave=wave, device=0))
     try:
         t = O.Tree(X, "dstree", leaf_cap=10, init_segments=4)
