@@ -44,8 +44,19 @@ FP32_LANES = 128
 # DRAM bytes (read + write) per tensor-core leaf-scan launch on the default
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # eight consecutive launches of the timed region, averaged), valid only for the
-# kernel source it was taken on (SHA-1 of k_scan_tc.cu)
-SCAN_TRAFFIC = {"bytes_per_launch": 471.9e6, "kernel_sha1": "d3cb2a5031a5eb043c23906728477ddb0e7242e0"}
+# kernel code it was taken on (SHA-1 of k_scan_tc.cu without comments and blank lines)
+SCAN_TRAFFIC = {"bytes_per_launch": 471.9e6, "kernel_sha1": "cec7dffe00c808a4390cc62d08b8ad5102c91348"}
+
+
+def code_sha1(path):
+    import hashlib
+    import re
+    with open(path, encoding="utf-8") as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+    return hashlib.sha1(src.encode()).hexdigest()
 
 
 def parse():
@@ -697,10 +708,8 @@ def main():
         tc_peak = pk.get("bf16_tflops", 1800.0)
         traffic = None
         try:
-            import hashlib
             src = os.path.join(ROOT, "paper_2502_01836_b300", "csrc", "k_scan_tc.cu")
-            with open(src, "rb") as f:
-                same_kernel = hashlib.sha1(f.read()).hexdigest() == SCAN_TRAFFIC["kernel_sha1"]
+            same_kernel = code_sha1(src) == SCAN_TRAFFIC["kernel_sha1"]
             default_workload = (a.n, a.leaf_cap, a.filters, a.launch, a.wave) == \
                 (1_000_000, 10_000, 100, 256, 64)
             if same_kernel and default_workload:

@@ -532,7 +532,6 @@ struct Pipeline {
   Scratch* lanes = nullptr;
   int nlanes = 1;
   int kmax = 1, W = 1, L = 0, cap = 0, qb = kBatch;
-  bool walk = true;
   unsigned long long* stat = nullptr;   // device counters of the pipeline's batches
   leafi_search_stats st{};
   LaneView lv[kMaxLanes];
@@ -575,7 +574,6 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
   W = ix->wave;
   cap = std::max(W, 1) * max_parts(t) * kmax;
   qb = kBatch;
-  walk = true;  // visiting order by (LB^2, leaf id) for any number of leaves
   for (int li = 0; li < nlanes; ++li) {
     Scratch& S = lanes[li];
     if (!S.st) {
@@ -663,10 +661,7 @@ void Pipeline::make_sa(const LaneView& v, int nb, bool use_f) {
 void Pipeline::select(const LaneView& v) {
   LF_CUDA(cudaMemsetAsync(v.np, 0, sizeof(int32_t), s));
   ix->tick(5);
-  if (walk)
-    launch_select_walk(sa, v.ord, v.cursor, s);
-  else
-    launch_select(sa, s);
+  launch_select_walk(sa, v.ord, v.cursor, s);
   ix->tock();
 }
 
@@ -709,7 +704,7 @@ BatchGraph* Pipeline::graph_for(const LaneView& v, int nb, bool use_f) {
   std::vector<BatchGraph>& graphs = lanes[cur_lane].graphs;
   const unsigned long long epoch0 = g_realloc_epoch;
   for (auto& g : graphs)
-    if (g.nb == nb && g.kmax == kmax && g.use_f == (int)use_f && g.walk == (int)walk &&
+    if (g.nb == nb && g.kmax == kmax && g.use_f == (int)use_f &&
         g.profiling == (int)ix->profiling && g.epoch == epoch0 && g.gen == ix->graph_gen)
       return &g;
   // graphs of an older epoch point at freed scratch, of an older generation
@@ -729,7 +724,6 @@ BatchGraph* Pipeline::graph_for(const LaneView& v, int nb, bool use_f) {
   g.nb = nb;
   g.kmax = kmax;
   g.use_f = use_f;
-  g.walk = walk;
   g.profiling = ix->profiling;
   g.epoch = epoch0;
   g.gen = ix->graph_gen;

@@ -227,7 +227,7 @@ struct SelectArgs {
 // one captured search batch (full 256-query batch, route round + one wave)
 struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
-  int nb = 0, kmax = 0, use_f = 0, walk = 0, profiling = 0;
+  int nb = 0, kmax = 0, use_f = 0, profiling = 0;
   unsigned long long epoch = 0;
   unsigned long long gen = 0;   // leafi_index::graph_gen at capture
   long long launches = 0;       // kernels in the graph (added to the launch counter per replay)
@@ -242,8 +242,8 @@ struct KernelClock {
   double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
-void launch_select(const SelectArgs& a, cudaStream_t s);
-// the same selection walking a precomputed visiting order (`ord`, cursor = position)
+// wave selection (Alg. 2 lines 3-7) walking a precomputed visiting order
+// (`ord` [nq][L] ascending (LB^2, leaf id), cursor = next position per query)
 void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s);
 void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
                         const int64_t* leaf_off, Pair* pairs, int32_t* npairs,

@@ -414,84 +414,11 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(
 // (Alg. 2 line 6) against the best-so-far of the wave's start.
 constexpr int kSelThreads = 128;
 
-__global__ void __launch_bounds__(kSelThreads) select_kernel(SelectArgs a) {
-  const int q = blockIdx.x;
-  if (a.done[q]) return;
-  __shared__ double s_lb[kSelThreads];
-  __shared__ int s_leaf[kSelThreads];
-  const int L = a.L;
-  const u64 thr = a.thr[q];
-  const float bsf2 = (thr == kNoKey) ? __int_as_float(0x7f800000) : key_d2(thr);
-  const double bsf2d = (double)bsf2;
-  const double bsf = (double)__fsqrt_rn(bsf2);
-  const bool filt = a.P != nullptr && a.jpos != nullptr && a.jpos[q] >= 0;
-  const int jp = filt ? a.jpos[q] : 0;
-  double cl = a.cur_lb[q];
-  int cf = a.cur_leaf[q];
-  const double* lb = a.lb2 + (size_t)q * L;
-  unsigned char* sc = a.scanned + (size_t)q * L;
-  int picked = 0;
-  for (int it = 0; it < a.W; ++it) {
-    double best = DBL_MAX;
-    int bl = INT_MAX;
-    for (int l = threadIdx.x; l < L; l += blockDim.x) {
-      if (sc[l]) continue;
-      const double v = lb[l];
-      if (!(v > cl || (v == cl && l > cf))) continue;
-      if (__dmul_rn(v, kDeflate) > bsf2d) continue;
-      if (filt) {
-        const int f = a.leaf_filter[l];
-        if (f >= 0) {
-          const double df = __dsub_rn((double)a.P[(size_t)q * a.F + f], a.alpha[(size_t)f * a.nc + jp]);
-          if (df > bsf) continue;
-        }
-      }
-      if (v < best || (v == best && l < bl)) {
-        best = v;
-        bl = l;
-      }
-    }
-    s_lb[threadIdx.x] = best;
-    s_leaf[threadIdx.x] = bl;
-    __syncthreads();
-    for (int off = kSelThreads / 2; off > 0; off >>= 1) {
-      if (threadIdx.x < off) {
-        const double o = s_lb[threadIdx.x + off];
-        const int ol = s_leaf[threadIdx.x + off];
-        if (o < s_lb[threadIdx.x] || (o == s_lb[threadIdx.x] && ol < s_leaf[threadIdx.x])) {
-          s_lb[threadIdx.x] = o;
-          s_leaf[threadIdx.x] = ol;
-        }
-      }
-      __syncthreads();
-    }
-    best = s_lb[0];
-    bl = s_leaf[0];
-    __syncthreads();
-    if (bl == INT_MAX) break;
-    if (threadIdx.x == 0) {
-      sc[bl] = 1;
-      const int idx = atomicAdd(a.npairs, 1);
-      a.pairs[idx] = Pair{q, q, bl, 0};
-      atomicAdd(&a.stat[0], 1ull);
-      atomicAdd(&a.stat[1], (u64)(a.leaf_off[bl + 1] - a.leaf_off[bl]));
-    }
-    cl = best;
-    cf = bl;
-    ++picked;
-  }
-  if (threadIdx.x == 0) {
-    a.cur_lb[q] = cl;
-    a.cur_leaf[q] = cf;
-    if (picked < a.W) a.done[q] = 1;
-  }
-}
-
 // Walk of the precomputed visiting order from the query's cursor: the next W
 // positions that are neither searched nor filter-pruned, stopping at the first
 // bound-pruned leaf (the order ascends in LB^2, so every later leaf is pruned
-// too).  Equivalent to select_kernel; one block of 128 threads per query
-// examines 128 positions per step with a block-wide prefix count.
+// too).  One block of 128 threads per query examines 128 positions per step
+// with a block-wide prefix count.
 __global__ void __launch_bounds__(kSelThreads) select_walk_kernel(SelectArgs a,
                                                                  const int32_t* __restrict__ ord,
                                                                  int32_t* __restrict__ cursor) {
@@ -729,11 +656,6 @@ void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long 
   LF_CHECK_LAUNCH();
 }
 
-void launch_select(const SelectArgs& a, cudaStream_t s) {
-  if (a.nq <= 0) return;
-  select_kernel<<<a.nq, kSelThreads, 0, s>>>(a);
-  LF_CHECK_LAUNCH();
-}
 
 void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s) {
   if (a.nq <= 0) return;

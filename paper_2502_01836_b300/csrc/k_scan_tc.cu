@@ -28,7 +28,9 @@
 // split into two halves that take alternate accumulators (warps 0-3 even
 // chunks, 4-7 odd chunks), so all eight warps work even for small query
 // groups; the re-checks are deferred to the end of the item.  For k > 1 all
-// eight warps walk every chunk and warps 0-3 insert into the lists in turns.
+// eight warps read every chunk; each TMEM lane quarter keeps its own top-k
+// list per query (the quarter's two warps split the columns), re-checks run
+// at once, and the quarter lists merge at the end of the item.
 #include <cfloat>
 
 #include "device_util.cuh"
