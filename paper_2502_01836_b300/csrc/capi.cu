@@ -152,18 +152,14 @@ __global__ void sqrt_kernel(const float* __restrict__ in, float* __restrict__ ou
   if (i < n) out[i] = __fsqrt_rn(in[i]);
 }
 
-__global__ void search_init_kernel(int nq, int kstride, int32_t* topk_cnt,
-                                   unsigned long long* thr, int32_t* cand_cnt, double* cur_lb,
-                                   int32_t* cur_leaf, int32_t* done) {
+__global__ void search_init_kernel(int nq, int32_t* topk_cnt, unsigned long long* thr,
+                                   int32_t* cand_cnt, int32_t* done) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
   topk_cnt[q] = 0;
   thr[q] = kNoKey;
   cand_cnt[q] = 0;
-  cur_lb[q] = -__longlong_as_double(0x7ff0000000000000ll);
-  cur_leaf[q] = -1;
   done[q] = 0;
-  (void)kstride;
 }
 
 __global__ void slots_init_kernel(int nslots, int32_t* topk_cnt, unsigned long long* thr,
@@ -495,8 +491,8 @@ __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, 
 // Device pointers of one lane's batch scratch, sized for a full batch.
 struct LaneView {
   float* gQ;
-  int32_t *dK, *jpos, *route, *topk_cnt, *cand_cnt, *cur_leaf, *done, *np, *ord, *cursor;
-  double *dT, *lb2, *cur_lb;
+  int32_t *dK, *jpos, *route, *topk_cnt, *cand_cnt, *done, *np, *ord, *cursor;
+  double *dT, *lb2;
   float *P, *out_d;
   unsigned char* scanned;
   unsigned long long *topk, *thr, *cand;
@@ -595,8 +591,6 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     v.thr = S.sThr.need(qb);
     v.cand = S.sCand.need((size_t)qb * cap);
     v.cand_cnt = S.sCandCnt.need(qb);
-    v.cur_lb = S.sCurLb.need(qb);
-    v.cur_leaf = S.sCurLeaf.need(qb);
     v.done = S.sDone.need(qb);
     v.pairs = S.sPairs.need((size_t)qb * std::max(W, 1));
     v.np = S.sNpairs.need(1);
@@ -648,8 +642,6 @@ void Pipeline::make_sa(const LaneView& v, int nb, bool use_f) {
   sa.nc = ix->nc;
   sa.leaf_off = ix->leaf_off.p;
   sa.scanned = v.scanned;
-  sa.cur_lb = v.cur_lb;
-  sa.cur_leaf = v.cur_leaf;
   sa.done = v.done;
   sa.pairs = v.pairs;
   sa.npairs = v.np;
@@ -687,8 +679,7 @@ void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
   LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
   launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);
   LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
-  search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, kmax, v.topk_cnt, v.thr, v.cand_cnt,
-                                                      v.cur_lb, v.cur_leaf, v.done);
+  search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.topk_cnt, v.thr, v.cand_cnt, v.done);
   LF_CHECK_LAUNCH();
   // wave 0: every query searches its route leaf
   launch_route_pairs(nb, v.route, L, v.scanned, ix->leaf_off.p, v.pairs, v.np, stat, s);

@@ -216,8 +216,6 @@ struct SelectArgs {
   const int64_t* leaf_off;
   // state
   unsigned char* scanned;         // [nq][L]
-  double* cur_lb;                 // [nq] cursor
-  int32_t* cur_leaf;              // [nq]
   int32_t* done;                  // [nq]
   Pair* pairs;
   int32_t* npairs;
@@ -302,8 +300,7 @@ struct Scratch {
   DBuf<int32_t> sWork;     // work-item counter of the tensor-core scan
   DBuf<double> sP, sIv, sNode, sLb, sPaa, sTarget;
   DBuf<int32_t> sRoute, sK, sJpos, sCnt, sGrpOff, sItemOff, sNpairs, sCandCnt, sTopkCnt, sDone,
-      sCurLeaf, sLeaves, sNItems, sOrd, sCursor;
-  DBuf<double> sCurLb;
+      sNItems, sOrd, sCursor;
   DBuf<unsigned char> sScanned, sOrderTmp;
   DBuf<Pair> sPairs, sGrouped;
   DBuf<unsigned long long> sTopk, sThr, sCand;
