@@ -386,6 +386,38 @@ def test_k_larger_than_n_pads():
         lf.leafi_free(idx)
 
 
+@pytest.mark.parametrize("m,cap,k", [(512, 300, 4), (64, 1, 128), (96, 5000, 128)])
+def test_edge_shapes_exact(m, cap, k):
+    """m = 512 (rows wider than the tensor-core scan takes: CUDA-core path),
+    leaves of one series, the largest k, one leaf holding everything; 300
+    queries (two lanes), one of them an exact copy of a series (distance 0)."""
+    X = fx.random_walk(3000, m, seed=91)
+    Q = fx.test_queries(X, 300, seed=92)
+    Q[7] = X[1234]
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=cap, wave=4, device=0))
+    try:
+        ids, d, st = _exact(idx, Q, k)
+        bf_ids, bf_d2 = O.knn(X, Q, k)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+        assert ids[7, 0] == 1234 and d[7, 0] == 0.0
+        assert bool(lf.leafi_get_info(idx).tensor_scan) == (m <= 256)
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_single_series_index():
+    X = fx.random_walk(1, 32, seed=93)
+    Q = fx.test_queries(fx.random_walk(50, 32, seed=94), 5, seed=95)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=10, wave=1, device=0))
+    try:
+        ids, d, _ = _exact(idx, Q, 3)
+        assert (ids[:, 0] == 0).all() and (ids[:, 1:] == -1).all()
+        assert np.array_equal(d[:, 0], np.sqrt(O.knn(X, Q, 1)[1][:, 0]))
+        assert np.isinf(d[:, 1:]).all()
+    finally:
+        lf.leafi_free(idx)
+
+
 def test_search_before_tuning_is_refused(ds):
     X, Q, idx, t = ds
     fl, W = _filters(t, 3)
