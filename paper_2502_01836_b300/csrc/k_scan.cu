@@ -212,6 +212,33 @@ __global__ void count_kernel(const Pair* __restrict__ pairs, const int32_t* __re
   if (p < *npairs) atomicAdd(&cnt[pairs[p].leaf], 1);
 }
 
+// Small-leaf packing (tensor-core scan only): the leaves are cut into windows
+// of kPackWin consecutive ids; a window whose series fit one 128-row chunk,
+// with at least two searched leaves whose pairs fit one query group, becomes a
+// single work item (every pair only meets the rows of its own leaf);
+// otherwise each searched leaf gives parts x groups items.
+constexpr int kPackWin = 8;
+constexpr int kPackRows = 128;
+
+template <class CountT>
+__device__ __forceinline__ bool window_packs(const CountT* cnt, const int64_t* __restrict__ leaf_off,
+                                             int w0, int w1, int g) {
+  if (leaf_off[w1] - leaf_off[w0] > kPackRows) return false;
+  int picked = 0, pairs = 0;
+  for (int l = w0; l < w1; ++l) {
+    picked += cnt[l] > 0;
+    pairs += cnt[l];
+  }
+  return picked >= 2 && pairs <= g;
+}
+
+__device__ __forceinline__ int leaf_items(int c, const int64_t* __restrict__ leaf_off, int l, int part,
+                                          int g) {
+  if (c == 0) return 0;
+  const int64_t size = leaf_off[l + 1] - leaf_off[l];
+  return (int)((size + part - 1) / part) * ((c + g - 1) / g);
+}
+
 // exclusive scans of per-leaf pair counts and work-item counts (one block)
 __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part, int g,
                                int32_t* __restrict__ cnt, int32_t* __restrict__ grp_off,
@@ -220,18 +247,22 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
                                int32_t* __restrict__ item_leaf) {
   __shared__ int s_a[1024], s_b[1024];
   const int T = blockDim.x;
-  const int per = (L + T - 1) / T;
-  const int l0 = threadIdx.x * per, l1 = min(L, l0 + per);
+  const bool pack = item_leaf != nullptr;
+  // whole windows per thread
+  const int per = ((L + T - 1) / T + kPackWin - 1) / kPackWin * kPackWin;
+  const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
   int sa = 0, sb = 0;
   unsigned long long distinct = 0;
-  for (int l = l0; l < l1; ++l) {
-    const int c = cnt[l];
-    sa += c;
-    if (c > 0) {
-      const int64_t size = leaf_off[l + 1] - leaf_off[l];
-      const int parts = (int)((size + part - 1) / part);
-      sb += parts * ((c + g - 1) / g);
-      distinct += (unsigned long long)size;
+  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
+    const int w1 = min(l1, w0 + kPackWin);
+    for (int l = w0; l < w1; ++l) {
+      sa += cnt[l];
+      if (cnt[l] > 0) distinct += (unsigned long long)(leaf_off[l + 1] - leaf_off[l]);
+    }
+    if (pack && window_packs(cnt, leaf_off, w0, w1, g)) {
+      sb += 1;
+    } else {
+      for (int l = w0; l < w1; ++l) sb += leaf_items(cnt[l], leaf_off, l, part, g);
     }
   }
   if (stat && distinct) atomicAdd(stat, distinct);
@@ -248,20 +279,26 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
     __syncthreads();
   }
   int ra = s_a[threadIdx.x] - sa, rb = s_b[threadIdx.x] - sb;
-  for (int l = l0; l < l1; ++l) {
-    const int c = cnt[l];
-    grp_off[l] = ra;
-    item_off[l] = rb;
-    ra += c;
-    if (c > 0) {
-      const int64_t size = leaf_off[l + 1] - leaf_off[l];
-      const int parts = (int)((size + part - 1) / part);
-      const int ni = parts * ((c + g - 1) / g);
-      if (item_leaf)
-        for (int i = 0; i < ni; ++i) item_leaf[rb + i] = l;
-      rb += ni;
+  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
+    const int w1 = min(l1, w0 + kPackWin);
+    const bool packed = pack && window_packs(cnt, leaf_off, w0, w1, g);
+    for (int l = w0; l < w1; ++l) {
+      const int c = cnt[l];
+      grp_off[l] = ra;
+      item_off[l] = rb;
+      ra += c;
+      if (!packed) {
+        const int ni = leaf_items(c, leaf_off, l, part, g);
+        if (item_leaf)
+          for (int i = 0; i < ni; ++i) item_leaf[rb + i] = l;
+        rb += ni;
+      }
     }
-    cnt[l] = 0;  // reused as the scatter fill counter
+    if (packed) {
+      item_leaf[rb] = -1 - w0;  // a packed window [w0, w0 + kPackWin)
+      rb += 1;
+    }
+    for (int l = w0; l < w1; ++l) cnt[l] = 0;  // reused as the scatter fill counter
   }
   if (threadIdx.x == T - 1) {
     grp_off[L] = s_a[T - 1];
@@ -287,17 +324,22 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
   __syncthreads();
   for (int p = threadIdx.x; p < np; p += T) atomicAdd(&cnt[pairs[p].leaf], 1);
   __syncthreads();
-  const int per = (L + T - 1) / T;
-  const int l0 = threadIdx.x * per, l1 = min(L, l0 + per);
+  const bool pack = item_leaf != nullptr;
+  // whole windows per thread
+  const int per = ((L + T - 1) / T + kPackWin - 1) / kPackWin * kPackWin;
+  const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
   int sa = 0, sb = 0;
   unsigned long long distinct = 0;
-  for (int l = l0; l < l1; ++l) {
-    const int c = cnt[l];
-    sa += c;
-    if (c > 0) {
-      const int64_t size = leaf_off[l + 1] - leaf_off[l];
-      sb += (int)((size + part - 1) / part) * ((c + g - 1) / g);
-      distinct += (unsigned long long)size;
+  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
+    const int w1 = min(l1, w0 + kPackWin);
+    for (int l = w0; l < w1; ++l) {
+      sa += cnt[l];
+      if (cnt[l] > 0) distinct += (unsigned long long)(leaf_off[l + 1] - leaf_off[l]);
+    }
+    if (pack && window_packs(cnt, leaf_off, w0, w1, g)) {
+      sb += 1;
+    } else {
+      for (int l = w0; l < w1; ++l) sb += leaf_items(cnt[l], leaf_off, l, part, g);
     }
   }
   if (stat && distinct) atomicAdd(stat, distinct);
@@ -313,18 +355,25 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
     __syncthreads();
   }
   int ra = s_a[threadIdx.x] - sa, rb = s_b[threadIdx.x] - sb;
-  for (int l = l0; l < l1; ++l) {
-    const int c = cnt[l];
-    grp_off[l] = ra;
-    item_off[l] = rb;
-    cnt[l] = ra;  // becomes the leaf's fill cursor
-    ra += c;
-    if (c > 0) {
-      const int64_t size = leaf_off[l + 1] - leaf_off[l];
-      const int ni = (int)((size + part - 1) / part) * ((c + g - 1) / g);
-      if (item_leaf)
-        for (int i = 0; i < ni; ++i) item_leaf[rb + i] = l;
-      rb += ni;
+  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
+    const int w1 = min(l1, w0 + kPackWin);
+    const bool packed = pack && window_packs(cnt, leaf_off, w0, w1, g);
+    for (int l = w0; l < w1; ++l) {
+      const int c = cnt[l];
+      grp_off[l] = ra;
+      item_off[l] = rb;
+      if (!packed) {
+        const int ni = leaf_items(c, leaf_off, l, part, g);
+        if (item_leaf)
+          for (int i = 0; i < ni; ++i) item_leaf[rb + i] = l;
+        rb += ni;
+      }
+      cnt[l] = ra;  // becomes the leaf's fill cursor (the window's test already ran)
+      ra += c;
+    }
+    if (packed) {
+      item_leaf[rb] = -1 - w0;  // a packed window [w0, w0 + kPackWin)
+      rb += 1;
     }
   }
   if (threadIdx.x == T - 1) {

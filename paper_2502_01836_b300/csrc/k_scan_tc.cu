@@ -75,6 +75,7 @@ struct TcShared {
   float qm[kTcG];      // |q|
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
   int cnt4[4][kTcG];   // k > 1: entries of each TMEM lane quarter's list per query
+  int rs[kTcG], re[kTcG];  // packed item: the chunk rows of each pair's own leaf
   int ncb;             // buffered candidates of the current item
   unsigned long long rechecks;
 };
@@ -95,23 +96,40 @@ struct TcShared {
 struct Item {
   int64_t p0, p1;
   int nqg, N, nchunks;
+  bool packed;       // several small leaves in one chunk (pairs meet their own leaf's rows)
   const Pair* pr;
 };
 
+constexpr int kPackWin = 8;  // leaves per packed window (the grouping pass's windows)
+
 __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
-  const int leaf = a.item_leaf[item];
+  const int lf = a.item_leaf[item];
+  Item it;
+  if (lf < 0) {
+    // a packed window of consecutive leaves [w0, w1): one chunk, one group
+    const int w0 = -1 - lf, w1 = min(w0 + kPackWin, a.L);
+    it.p0 = a.leaf_off[w0];
+    it.p1 = a.leaf_off[w1];
+    it.nqg = a.grp_off[w1] - a.grp_off[w0];
+    it.N = ((it.nqg + 15) / 16) * 16;
+    it.pr = a.pairs + a.grp_off[w0];
+    it.nchunks = 1;
+    it.packed = true;
+    return it;
+  }
+  const int leaf = lf;
   const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
   const int G = a.G;
   const int ngroups = (cnt + G - 1) / G;
   const int local = item - a.item_off[leaf];
   const int part = local / ngroups, grp = local % ngroups;
-  Item it;
   it.p0 = a.leaf_off[leaf] + (int64_t)part * a.part;
   it.p1 = min(it.p0 + (int64_t)a.part, a.leaf_off[leaf + 1]);
   it.nqg = min(G, cnt - grp * G);
   it.N = ((it.nqg + 15) / 16) * 16;
   it.pr = a.pairs + a.grp_off[leaf] + grp * G;
   it.nchunks = (int)((it.p1 - it.p0 + kTcRows - 1) / kTcRows);
+  it.packed = false;
   return it;
 }
 
@@ -520,10 +538,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           S.wide[qq] = k1.y != 0.0f ? 1 : 0;
           S.qb[qq] = k0;
           S.qm[qq] = k1.x;
+          if (I.packed) {
+            const int lf = I.pr[qq].leaf;
+            S.rs[qq] = (int)(a.leaf_off[lf] - I.p0);
+            S.re[qq] = (int)(a.leaf_off[lf + 1] - I.p0);
+          }
           if (split) lists[qq * a.k] = th;
         } else {
           S.qb[qq] = make_float4(kInf, kInf, 0.0f, 0.0f);
           S.H[qq] = 0.0f;  // lo = inf > 0: never a candidate
+          S.rs[qq] = S.re[qq] = 0;
         }
       }
       epi_sync();
@@ -562,6 +586,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               const float4 qb = S.qb[c0 + jj];
               lov[jj] = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
               hw[jj] = fmaxf(fmaf(-2.0f, d[jj], fmaf(qb.z, xnorm, qb.y + vhi)), 0.0f);
+            }
+            if (I.packed) {
+              // a pair only meets the rows of its own leaf
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj)
+                if (r < S.rs[c0 + jj] || r >= S.re[c0 + jj]) {
+                  lov[jj] = kInf;
+                  hw[jj] = kInf;
+                }
             }
             // warp minimum of the (non-negative) upper bounds: one REDUX per column
 #pragma unroll
@@ -639,7 +672,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               const float lo = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
               float T = S.thrd[j];
               if (cc == kq) T = fminf(T, dev::key_d2(ql[j * a.k + kq - 1]));
-              const bool cand = valid && !(lo > T);
+              const bool cand = valid && !(lo > T) && (!I.packed || (r >= S.rs[j] && r < S.re[j]));
               unsigned mask = __ballot_sync(0xffffffffu, cand);
               if (!mask) continue;
               u64 key = kNoKey;
