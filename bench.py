@@ -178,8 +178,10 @@ def dist_setup(gpus):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        # one process per GPU over NCCL; gloo where there is no GPU (host-side tests)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, world, local, dist
 
 
@@ -187,7 +189,8 @@ def max_over_ranks(x, dist, device):
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
