@@ -333,7 +333,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
       use_tc ? ix->sc->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix->tree)) : nullptr;
   launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
                use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped, nitems,
-               distinct_stat, s, item_leaf);
+               distinct_stat, s, item_leaf, use_tc && ix->pack_small);
   const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
   if (use_tc) {
     TcScanArgs t;
@@ -1141,6 +1141,9 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
       float fmx;
       std::memcpy(&fmx, &h_mx, sizeof(fmx));
       ix->tc_ok = fmx < 30000.0f && encode_xh_map(ix.get());  // float16 is safe and TMA is available
+      // small-leaf packing pays only where a window of 8 leaves fits one chunk
+      for (int w0 = 0; w0 < t.n_leaves && !ix->pack_small; w0 += 8)
+        ix->pack_small = t.leaf_off[std::min(w0 + 8, t.n_leaves)] - t.leaf_off[w0] <= 128;
       if (!ix->tc_ok) {
         ix->Xh.release();
         ix->xn.release();

@@ -196,7 +196,8 @@ void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* s
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
-                  unsigned long long* stat, cudaStream_t s, int32_t* item_leaf = nullptr);
+                  unsigned long long* stat, cudaStream_t s, int32_t* item_leaf = nullptr,
+                  bool pack_small = false);
 
 void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
                   int32_t* topk_cnt, unsigned long long* thr, const unsigned long long* cand,
@@ -330,6 +331,7 @@ struct leafi_index {
   leafi::DBuf<float> xn;         // [n] squared norms
   int kp = 0;                    // float16 row length (multiple of 64)
   bool tc_ok = false;            // tensor-core scan usable for this index
+  bool pack_small = false;       // some window of 8 consecutive leaves fits one 128-row chunk
   CUtensorMap xh_map;            // 2-D TMA map of Xh: {kp columns, n rows}, box {64, 128}
   int smem_optin = 0;            // opt-in shared memory per block of the device
   leafi::DBuf<int32_t> ids;      // position -> original id

@@ -244,17 +244,18 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
                                int32_t* __restrict__ cnt, int32_t* __restrict__ grp_off,
                                int32_t* __restrict__ item_off, int32_t* __restrict__ n_items,
                                unsigned long long* __restrict__ stat,
-                               int32_t* __restrict__ item_leaf) {
+                               int32_t* __restrict__ item_leaf, bool pack_small) {
   __shared__ int s_a[1024], s_b[1024];
   const int T = blockDim.x;
-  const bool pack = item_leaf != nullptr;
-  // whole windows per thread
-  const int per = ((L + T - 1) / T + kPackWin - 1) / kPackWin * kPackWin;
+  const bool pack = item_leaf != nullptr && pack_small;
+  // whole windows per thread when packing
+  const int win = pack ? kPackWin : 1;
+  const int per = ((L + T - 1) / T + win - 1) / win * win;
   const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
   int sa = 0, sb = 0;
   unsigned long long distinct = 0;
-  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
-    const int w1 = min(l1, w0 + kPackWin);
+  for (int w0 = l0; w0 < l1; w0 += win) {
+    const int w1 = min(l1, w0 + win);
     for (int l = w0; l < w1; ++l) {
       sa += cnt[l];
       if (cnt[l] > 0) distinct += (unsigned long long)(leaf_off[l + 1] - leaf_off[l]);
@@ -279,8 +280,8 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
     __syncthreads();
   }
   int ra = s_a[threadIdx.x] - sa, rb = s_b[threadIdx.x] - sb;
-  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
-    const int w1 = min(l1, w0 + kPackWin);
+  for (int w0 = l0; w0 < l1; w0 += win) {
+    const int w1 = min(l1, w0 + win);
     const bool packed = pack && window_packs(cnt, leaf_off, w0, w1, g);
     for (int l = w0; l < w1; ++l) {
       const int c = cnt[l];
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
     const Pair* __restrict__ pairs, const int32_t* __restrict__ npairs, int L,
     const int64_t* __restrict__ leaf_off, int part, int g, int32_t* __restrict__ grp_off,
     int32_t* __restrict__ item_off, int32_t* __restrict__ n_items, Pair* __restrict__ grouped,
-    unsigned long long* __restrict__ stat, int32_t* __restrict__ item_leaf) {
+    unsigned long long* __restrict__ stat, int32_t* __restrict__ item_leaf, bool pack_small) {
   __shared__ int cnt[kFuseLeaves];
   __shared__ int s_a[1024], s_b[1024];
   const int T = blockDim.x;
@@ -324,14 +325,15 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
   __syncthreads();
   for (int p = threadIdx.x; p < np; p += T) atomicAdd(&cnt[pairs[p].leaf], 1);
   __syncthreads();
-  const bool pack = item_leaf != nullptr;
-  // whole windows per thread
-  const int per = ((L + T - 1) / T + kPackWin - 1) / kPackWin * kPackWin;
+  const bool pack = item_leaf != nullptr && pack_small;
+  // whole windows per thread when packing
+  const int win = pack ? kPackWin : 1;
+  const int per = ((L + T - 1) / T + win - 1) / win * win;
   const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
   int sa = 0, sb = 0;
   unsigned long long distinct = 0;
-  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
-    const int w1 = min(l1, w0 + kPackWin);
+  for (int w0 = l0; w0 < l1; w0 += win) {
+    const int w1 = min(l1, w0 + win);
     for (int l = w0; l < w1; ++l) {
       sa += cnt[l];
       if (cnt[l] > 0) distinct += (unsigned long long)(leaf_off[l + 1] - leaf_off[l]);
@@ -355,8 +357,8 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
     __syncthreads();
   }
   int ra = s_a[threadIdx.x] - sa, rb = s_b[threadIdx.x] - sb;
-  for (int w0 = l0; w0 < l1; w0 += kPackWin) {
-    const int w1 = min(l1, w0 + kPackWin);
+  for (int w0 = l0; w0 < l1; w0 += win) {
+    const int w1 = min(l1, w0 + win);
     const bool packed = pack && window_packs(cnt, leaf_off, w0, w1, g);
     for (int l = w0; l < w1; ++l) {
       const int c = cnt[l];
@@ -674,10 +676,12 @@ void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* s
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
-                  unsigned long long* stat, cudaStream_t s, int32_t* item_leaf) {
+                  unsigned long long* stat, cudaStream_t s, int32_t* item_leaf,
+                  bool pack_small) {
   if (L <= kFuseLeaves) {
     group_fused_kernel<<<1, 1024, 0, s>>>(pairs, npairs_dev, L, leaf_off, part, g, grp_off,
-                                          item_off, n_items_dev, grouped, stat, item_leaf);
+                                          item_off, n_items_dev, grouped, stat, item_leaf,
+                                          pack_small);
     LF_CHECK_LAUNCH();
     return;
   }
@@ -687,7 +691,7 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
     LF_CHECK_LAUNCH();
   }
   offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, g, cnt, grp_off, item_off, n_items_dev,
-                                    stat, item_leaf);
+                                    stat, item_leaf, pack_small);
   LF_CHECK_LAUNCH();
   if (npairs_max > 0) {
     scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
