@@ -145,7 +145,7 @@ struct ScanArgs {
   const Pair* pairs;     // grouped by leaf
   const int32_t* grp_off;   // L + 1: pair offsets per leaf
   const int32_t* item_off;  // L + 1: work-item offsets per leaf
-  const unsigned long long* thr;  // per slot: admission threshold key
+  unsigned long long* thr;        // per slot: admission threshold key (lowered by finished items)
   unsigned long long* cand;       // per slot: candidate keys (cap each)
   int32_t* cand_cnt;              // per slot
   int cand_cap;
@@ -172,7 +172,7 @@ struct TcScanArgs {
   const int32_t* item_off;
   const int32_t* item_leaf;        // leaf of every work item
   int32_t* work;                   // work-item counter (zero at launch)
-  const unsigned long long* thr;
+  unsigned long long* thr;         // per slot k-th best key; lowered by finished work items
   unsigned long long* cand;
   int32_t* cand_cnt;
   int cand_cap;

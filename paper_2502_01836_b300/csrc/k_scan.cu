@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a,
       if (tid < nqg) {
         const int slot = pr[tid].slot;
         s_slot[tid] = slot;
-        s_thr[tid] = a.thr[slot];
+        s_thr[tid] = __ldcg(&a.thr[slot]);  // as finished items of the round lowered it
         s_k[tid] = slot_k ? slot_k[slot] : a.k;
       }
     }
@@ -193,7 +193,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a,
       if (c == 0) continue;
       const int slot = s_slot[q];
       int base = 0;
-      if (lane == 0) base = atomicAdd(&a.cand_cnt[slot], c);
+      if (lane == 0) {
+        base = atomicAdd(&a.cand_cnt[slot], c);
+        // a full list's k-th key bounds the slot's final k-th key (each pair is
+        // in one item only), so later items of the round may admit against it
+        if (c == s_k[q]) atomicMin(&a.thr[slot], lists[q * a.k + c - 1]);
+      }
       base = __shfl_sync(0xffffffffu, base, 0);
       if (base + c > a.cand_cap) {
         if (lane == 0) atomicOr(a.err, 1);

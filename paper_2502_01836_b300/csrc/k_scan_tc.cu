@@ -31,6 +31,14 @@
 // eight warps read every chunk; each TMEM lane quarter keeps its own top-k
 // list per query (the quarter's two warps split the columns), re-checks run
 // at once, and the quarter lists merge at the end of the item.
+//
+// Work items of one round share their progress: an item reads each query's
+// threshold when it starts and, when it ends, lowers it (atomic minimum of
+// keys) to its own k-th best key once it holds k series.  Every (query,
+// series) pair belongs to exactly one item, so a series of the final top-k
+// has a smaller key than any other item's k-th key and is never dropped by
+// the lowered threshold; the merge after the scan recomputes the threshold
+// from all candidates, so the results do not depend on the order of items.
 #include <cfloat>
 
 #include "device_util.cuh"
@@ -75,6 +83,7 @@ struct TcShared {
   float qm[kTcG];      // |q|
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
   int cnt4[4][kTcG];   // k > 1: entries of each TMEM lane quarter's list per query
+  float Tq[kTcG];      // k > 1: admission bound (thrd, any full quarter list's k-th, refreshed threshold)
   int rs[kTcG], re[kTcG];  // packed item: the chunk rows of each pair's own leaf
   int ncb;             // buffered candidates of the current item
   unsigned long long rechecks;
@@ -206,6 +215,38 @@ __device__ __forceinline__ float warp_canonical_d2(const float4* __restrict__ q,
       acc = __fmaf_rn(tz, tz, acc);
       acc = __fmaf_rn(tw, tw, acc);
     }
+  }
+  return acc;
+}
+
+constexpr int kIlp = 8;
+
+// Canonical squared distance by one thread (the operations and order of
+// dev::canonical_d2) with the row loads issued eight float4 words at a time,
+// so a re-check waits for a few memory round trips instead of one per word.
+__device__ __forceinline__ float canonical_d2_ilp(const float4* __restrict__ q,
+                                                  const float4* __restrict__ x, int m4) {
+  float acc = 0.0f;
+  for (int c0 = 0; c0 < m4; c0 += kIlp) {
+    float4 xa[kIlp], qa[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u)
+      if (c0 + u < m4) {
+        xa[u] = x[c0 + u];
+        qa[u] = q[c0 + u];
+      }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u)
+      if (c0 + u < m4) {
+        float t = __fsub_rn(qa[u].x, xa[u].x);
+        acc = __fmaf_rn(t, t, acc);
+        t = __fsub_rn(qa[u].y, xa[u].y);
+        acc = __fmaf_rn(t, t, acc);
+        t = __fsub_rn(qa[u].z, xa[u].z);
+        acc = __fmaf_rn(t, t, acc);
+        t = __fsub_rn(qa[u].w, xa[u].w);
+        acc = __fmaf_rn(t, t, acc);
+      }
   }
   return acc;
 }
@@ -525,7 +566,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         if (qq < nqg) {
           const int slot = I.pr[qq].slot, qrow = I.pr[qq].q;
           const float4 k0 = a.Qk[2 * (size_t)qrow], k1 = a.Qk[2 * (size_t)qrow + 1];
-          const u64 th = a.thr[slot];
+          // the slot's threshold as other work items of this round have lowered it
+          const u64 th = __ldcg(&a.thr[slot]);
           const float thd = (th == kNoKey) ? kInf : dev::key_d2(th);
           S.slot[qq] = slot;
           S.qrow[qq] = qrow;
@@ -535,6 +577,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           S.H[qq] = thd;
           S.cnt[qq] = 0;
           S.cnt4[0][qq] = S.cnt4[1][qq] = S.cnt4[2][qq] = S.cnt4[3][qq] = 0;
+          S.Tq[qq] = thd;
           S.wide[qq] = k1.y != 0.0f ? 1 : 0;
           S.qb[qq] = k0;
           S.qm[qq] = k1.x;
@@ -547,6 +590,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         } else {
           S.qb[qq] = make_float4(kInf, kInf, 0.0f, 0.0f);
           S.H[qq] = 0.0f;  // lo = inf > 0: never a candidate
+          S.Tq[qq] = 0.0f;
           S.rs[qq] = S.re[qq] = 0;
         }
       }
@@ -596,10 +640,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                   hw[jj] = kInf;
                 }
             }
-            // warp minimum of the (non-negative) upper bounds: one REDUX per column
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj)
-              hw[jj] = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(hw[jj])));
             const float4* H4 = reinterpret_cast<const float4*>(&S.H[c0]);
             float T[16];
 #pragma unroll
@@ -611,18 +651,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               T[4 * v4 + 2] = h.z;
               T[4 * v4 + 3] = h.w;
             }
-            unsigned lower = 0, cand = 0;
+            unsigned cand = 0;
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              if (hw[jj] < T[jj]) lower |= 1u << jj;
-              T[jj] = fminf(T[jj], hw[jj]);
+            for (int jj = 0; jj < 16; ++jj)
               if (valid && !(lov[jj] > T[jj])) cand |= 1u << jj;
-            }
-            // a tighter upper bound is rare once the part is under way
-            if (lane == 0 && lower) {
+            // an upper bound a + band below T needs a - band <= T first, so the
+            // warp minimum of the upper bounds (one REDUX per column) is only
+            // formed for the columns where some row is admitted
+            const unsigned act = __reduce_or_sync(0xffffffffu, cand);
+            if (act) {
+              unsigned lower = 0;
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj)
-                if (lower & (1u << jj)) atomic_min_float_nonneg(&S.H[c0 + jj], hw[jj]);
+              for (int jj = 0; jj < 16; ++jj) {
+                if (!(act & (1u << jj))) continue;
+                const float hm = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(hw[jj])));
+                if (hm < T[jj]) {
+                  lower |= 1u << jj;
+                  T[jj] = hm;
+                  if (lov[jj] > hm) cand &= ~(1u << jj);
+                }
+              }
+              // a tighter upper bound is rare once the part is under way
+              if (lane == 0 && lower) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj)
+                  if (lower & (1u << jj)) atomic_min_float_nonneg(&S.H[c0 + jj], T[jj]);
+              }
             }
             if (__any_sync(0xffffffffu, cand != 0u)) {
               while (cand) {
@@ -653,34 +707,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         } else {
           // general k: every TMEM lane quarter keeps its own top-k list per query
           // (warps w and w + 4 share the quarter and split the 16-column groups),
-          // so no two warps ever write the same list; re-checks run at once,
-          // one candidate per lane, and the quarter lists merge at the item's end
+          // so no two warps ever write the same list.  The admission bound Tq
+          // of a query is shared by the quarters and by the round's other work
+          // items: it falls to any quarter's k-th best distance and to the
+          // slot's threshold as other items lower it (re-read every other
+          // chunk).  Admission compares distances (a - band <= Tq, ties
+          // admitted); insertion compares keys against the quarter's own k-th
+          // or the threshold read at the item's start, so a key this item
+          // published itself never excludes one of its own series.  16 columns
+          // are tested at once, re-checks run at once (one candidate per lane),
+          // and the quarter lists merge at the item's end.
           const int qd = warp & 3;
           u64* ql = lists + (size_t)qd * G * a.k;  // this quarter's lists [G][k]
           const float xnorm = sqrtf(xn);
           const float vlo = xn * (1.0f - 1e-4f);
+          const bool refresh = (c & 1) == 1;
           for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
+            // the slot thresholds of these 16 columns, consumed after the tests
+            u64 gth = kNoKey;
+            if (refresh && lane < 16 && c0 + lane < nqg) gth = __ldcg(&a.thr[S.slot[c0 + lane]]);
             float d[16];
             dev::tmem_ld16(tl + (uint32_t)c0, d);
-#pragma unroll 1
-            for (int jj = 0; jj < 16; ++jj) {
+            const float4* T4v = reinterpret_cast<const float4*>(&S.Tq[c0]);
+            unsigned cand = 0;
+#pragma unroll
+            for (int v4 = 0; v4 < 4; ++v4) {
+              const float4 tv = T4v[v4];
+              const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int jj = 4 * v4 + u;
+                const float4 qb = S.qb[c0 + jj];
+                const float lo = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
+                if (!(lo > tt[u])) cand |= 1u << jj;
+              }
+            }
+            if (!valid) cand = 0u;
+            if (I.packed) {
+              // a pair only meets the rows of its own leaf
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj)
+                if (r < S.rs[c0 + jj] || r >= S.re[c0 + jj]) cand &= ~(1u << jj);
+            }
+            unsigned any = __reduce_or_sync(0xffffffffu, cand);
+            while (any) {
+              const int jj = __ffs(any) - 1;
+              any &= any - 1;
               const int j = c0 + jj;
-              if (j >= nqg) break;
+              const bool cj = (cand >> jj) & 1u;
+              unsigned mask = __ballot_sync(0xffffffffu, cj);
               const int kq = S.kq[j];
               int cc = S.cnt4[qd][j];
-              const float4 qb = S.qb[j];
-              const float lo = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
-              float T = S.thrd[j];
-              if (cc == kq) T = fminf(T, dev::key_d2(ql[j * a.k + kq - 1]));
-              const bool cand = valid && !(lo > T) && (!I.packed || (r >= S.rs[j] && r < S.re[j]));
-              unsigned mask = __ballot_sync(0xffffffffu, cand);
-              if (!mask) continue;
               u64 key = kNoKey;
-              if (cand) {
-                const float e = dev::canonical_d2(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+              if (cj) {
+                const float e = canonical_d2_ilp(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
                 key = dev::make_key(e, (uint32_t)a.ids[pos]);
               }
               if (lane == 0) atomicAdd(&S.rechecks, (unsigned long long)__popc(mask));
+              const int cc0 = cc;
+              u64 kth0 = (cc == kq) ? ql[j * a.k + kq - 1] : kNoKey;
               while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
@@ -688,8 +773,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                 const u64 kth = (cc == kq) ? ql[j * a.k + kq - 1] : S.thr[j];
                 if (kk < kth) cc = dev::warp_insert(ql + j * a.k, cc, kq, kk, lane);
               }
-              if (lane == 0) S.cnt4[qd][j] = cc;
+              if (lane == 0) {
+                S.cnt4[qd][j] = cc;
+                if (cc == kq) {
+                  const u64 kth = ql[j * a.k + kq - 1];
+                  if (cc0 < kq || kth < kth0) {
+                    // a full quarter list: its k-th bounds the item's and the slot's
+                    atomic_min_float_nonneg(&S.Tq[j], dev::key_d2(kth));
+                    atomicMin(&a.thr[S.slot[j]], kth);
+                  }
+                }
+              }
               __syncwarp();
+            }
+            if (refresh && lane < 16 && gth != kNoKey) {
+              const float g = dev::key_d2(gth);
+              if (g < S.Tq[c0 + lane]) atomic_min_float_nonneg(&S.Tq[c0 + lane], g);
             }
           }
         }
@@ -734,13 +833,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               else break;  // the rest of a sorted list is no better
             }
           }
-          if (lane == 0) S.cnt[q] = cc;
+          if (lane == 0) {
+            S.cnt[q] = cc;
+            // a full list's k-th key bounds the slot's final k-th key: later work
+            // items of the round admit against it
+            if (cc == kq) atomicMin(&a.thr[S.slot[q]], lists[q * a.k + kq - 1]);
+          }
           __syncwarp();
         }
         epi_sync();
       }
       // k = 1 lists hold the part's best key if it beat the round's threshold
-      if (split && tid < nqg) S.cnt[tid] = (lists[tid * a.k] < S.thr[tid]) ? 1 : 0;
+      if (split && tid < nqg) {
+        const u64 best = lists[tid * a.k];
+        S.cnt[tid] = (best < S.thr[tid]) ? 1 : 0;
+        if (best < S.thr[tid]) atomicMin(&a.thr[S.slot[tid]], best);
+      }
       epi_sync();
       for (int q = warp; q < nqg; q += kEpiWarps) {
         const int cc = S.cnt[q];
