@@ -359,6 +359,14 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.work = ix->sc->sWork.need(1);
     LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
     t.thr = thr;
+    t.gs = nullptr;
+    t.glock = nullptr;
+    if (kstride > 1) {
+      t.gs = ix->sc->sGs.need((size_t)nslots * kstride);
+      t.glock = ix->sc->sGlock.need(nslots);
+      LF_CUDA(cudaMemsetAsync(t.gs, 0xFF, sizeof(unsigned long long) * (size_t)nslots * kstride, s));
+      LF_CUDA(cudaMemsetAsync(t.glock, 0, sizeof(int32_t) * (size_t)nslots, s));
+    }
     t.cand = cand;
     t.cand_cnt = cand_cnt;
     t.cand_cap = cap;
@@ -606,6 +614,10 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
       v.tq.Qk = S.sQk.need((size_t)2 * qb);
       S.sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(t));
       S.sWork.need(1);
+      if (kmax > 1) {
+        S.sGs.need((size_t)qb * kmax);
+        S.sGlock.need(qb);
+      }
     }
     S.sCnt.need(L);
     S.sGrpOff.need(L + 1);

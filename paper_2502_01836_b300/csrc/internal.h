@@ -173,6 +173,9 @@ struct TcScanArgs {
   const int32_t* item_leaf;        // leaf of every work item
   int32_t* work;                   // work-item counter (zero at launch)
   unsigned long long* thr;         // per slot k-th best key; lowered by finished work items
+  unsigned long long* gs;          // k > 1: per slot the round's shared list [nslots][k] (kNoKey
+                                   // filled at the round's start), or null
+  int32_t* glock;                  // its per-slot locks (zero at the round's start)
   unsigned long long* cand;
   int32_t* cand_cnt;
   int cand_cap;
@@ -305,6 +308,8 @@ struct Scratch {
   DBuf<unsigned char> sScanned, sOrderTmp;
   DBuf<Pair> sPairs, sGrouped;
   DBuf<unsigned long long> sTopk, sThr, sCand;
+  DBuf<unsigned long long> sGs;   // round's shared per-slot lists of the tensor-core scan (k > 1)
+  DBuf<int32_t> sGlock;           // their locks
   DBuf<float> sPred, sOutD;
   DBuf<int64_t> sOutI;
   // search lane

@@ -219,7 +219,7 @@ __device__ __forceinline__ float warp_canonical_d2(const float4* __restrict__ q,
   return acc;
 }
 
-constexpr int kIlp = 8;
+constexpr int kIlp = 4;
 
 // Canonical squared distance by one thread (the operations and order of
 // dev::canonical_d2) with the row loads issued eight float4 words at a time,
@@ -249,6 +249,114 @@ __device__ __forceinline__ float canonical_d2_ilp(const float4* __restrict__ q,
       }
   }
   return acc;
+}
+
+// Merge the keys held one per lane (kNoKey: none) that lie below `bound`
+// into the ascending list L (cc entries, capacity kq): the warp sorts the
+// keys (bitonic exchange over shuffles), every key and list entry finds its
+// merged position by binary search in the other sequence, and the first kq
+// are written back.  All lanes call it; keys are distinct from the list's.
+__device__ __forceinline__ int warp_merge_keys(u64* L, int cc, int kq, u64 key, u64 bound,
+                                               int lane) {
+  u64 v = key < bound ? key : kNoKey;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const u64 o = __shfl_xor_sync(0xffffffffu, v, stride);
+      const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+      v = keep_min ? (o < v ? o : v) : (o < v ? v : o);
+    }
+  }
+  const int nnew = __popc(__ballot_sync(0xffffffffu, v != kNoKey));
+  if (nnew == 0) return cc;
+  int rv = kq;
+  if (lane < nnew) {
+    int lo = 0, hi = cc;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (L[mid] < v) lo = mid + 1;
+      else hi = mid;
+    }
+    rv = lane + lo;
+  }
+  u64 xv[LEAFI_MAX_K / 32];
+  int rx[LEAFI_MAX_K / 32];
+#pragma unroll
+  for (int u = 0; u < LEAFI_MAX_K / 32; ++u) {
+    xv[u] = kNoKey;
+    rx[u] = kq;
+    if (32 * u < cc) {  // warp-uniform
+      const int p = lane + 32 * u;
+      const u64 x = p < cc ? L[p] : kNoKey;
+      int pos = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const u64 pv = __shfl_sync(0xffffffffu, v, pos + step - 1);
+        if (pv < x) pos += step;
+      }
+      const u64 last = __shfl_sync(0xffffffffu, v, 31);
+      if (pos == 31 && last < x) pos = 32;
+      xv[u] = x;
+      if (p < cc) rx[u] = p + pos;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < LEAFI_MAX_K / 32; ++u)
+    if (rx[u] < kq) L[rx[u]] = xv[u];
+  if (rv < kq) L[rv] = v;
+  __syncwarp();
+  return min(kq, cc + nnew);
+}
+
+constexpr int kShareTries = 16;  // lock attempts before an item gives up sharing its list
+
+// Merge an item's ascending list B (cb entries) into the round's shared list
+// gl of the slot (kq entries, kNoKey padded, ascending, keys of other items)
+// under the slot's lock.  The lock is only tried a bounded number of times:
+// sharing tightens later items' admission and is skipped when contended.
+// Readers take gl[kq - 1] without the lock; it is written once per merge, and
+// both its old and its new value are the k-th key of k distinct scanned series.
+__device__ __forceinline__ void share_list(u64* gl, int32_t* lock, const u64* B, int cb, int kq,
+                                           u64* scratch, int lane) {
+  const u64 gk = __ldcg(&gl[kq - 1]);
+  if (!(B[0] < gk)) return;  // nothing of this item enters the shared list
+  int got = 0;
+  if (lane == 0) {
+    for (int t = 0; t < kShareTries && !got; ++t) {
+      got = atomicCAS(lock, 0, 1) == 0 ? 1 : 0;
+      if (!got) __nanosleep(64);
+    }
+  }
+  got = __shfl_sync(0xffffffffu, got, 0);
+  if (!got) return;
+  __threadfence();
+  for (int p = lane; p < kq; p += 32) scratch[p] = __ldcg(&gl[p]);
+  __syncwarp();
+  for (int p = lane; p < kq; p += 32) {
+    const u64 x = scratch[p];
+    int lo = 0, hi = cb;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (B[mid] < x) lo = mid + 1;
+      else hi = mid;
+    }
+    if (p + lo < kq) gl[p + lo] = x;
+  }
+  for (int p = lane; p < cb; p += 32) {
+    const u64 x = B[p];
+    int lo = 0, hi = kq;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (scratch[mid] < x) lo = mid + 1;
+      else hi = mid;
+    }
+    if (p + lo < kq) gl[p + lo] = x;
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicExch(lock, 0);
 }
 
 // Work items are claimed dynamically: the TMA thread takes the next index
@@ -567,11 +675,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           const int slot = I.pr[qq].slot, qrow = I.pr[qq].q;
           const float4 k0 = a.Qk[2 * (size_t)qrow], k1 = a.Qk[2 * (size_t)qrow + 1];
           // the slot's threshold as other work items of this round have lowered it
-          const u64 th = __ldcg(&a.thr[slot]);
+          // (k > 1: also the k-th key of the round's shared list of the slot)
+          const int kqs = slot_k ? slot_k[slot] : a.k;
+          u64 th = __ldcg(&a.thr[slot]);
+          if (a.gs) {
+            const u64 gk = __ldcg(&a.gs[(size_t)slot * a.k + kqs - 1]);
+            th = gk < th ? gk : th;
+          }
           const float thd = (th == kNoKey) ? kInf : dev::key_d2(th);
           S.slot[qq] = slot;
           S.qrow[qq] = qrow;
-          S.kq[qq] = slot_k ? slot_k[slot] : a.k;
+          S.kq[qq] = kqs;
           S.thr[qq] = th;
           S.thrd[qq] = thd;
           S.H[qq] = thd;
@@ -725,7 +839,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
             // the slot thresholds of these 16 columns, consumed after the tests
             u64 gth = kNoKey;
-            if (refresh && lane < 16 && c0 + lane < nqg) gth = __ldcg(&a.thr[S.slot[c0 + lane]]);
+            if (refresh && a.gs && lane < 16 && c0 + lane < nqg)
+              gth = __ldcg(&a.gs[(size_t)S.slot[c0 + lane] * a.k + S.kq[c0 + lane] - 1]);
             float d[16];
             dev::tmem_ld16(tl + (uint32_t)c0, d);
             const float4* T4v = reinterpret_cast<const float4*>(&S.Tq[c0]);
@@ -764,25 +879,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                 key = dev::make_key(e, (uint32_t)a.ids[pos]);
               }
               if (lane == 0) atomicAdd(&S.rechecks, (unsigned long long)__popc(mask));
-              const int cc0 = cc;
-              u64 kth0 = (cc == kq) ? ql[j * a.k + kq - 1] : kNoKey;
-              while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const u64 kk = __shfl_sync(0xffffffffu, key, src);
-                const u64 kth = (cc == kq) ? ql[j * a.k + kq - 1] : S.thr[j];
-                if (kk < kth) cc = dev::warp_insert(ql + j * a.k, cc, kq, kk, lane);
+              u64* lj = ql + j * a.k;
+              if (__popc(mask) > 3) {
+                cc = warp_merge_keys(lj, cc, kq, key, (cc == kq) ? lj[kq - 1] : S.thr[j], lane);
+              } else {
+                while (mask) {
+                  const int src = __ffs(mask) - 1;
+                  mask &= mask - 1;
+                  const u64 kk = __shfl_sync(0xffffffffu, key, src);
+                  const u64 kth = (cc == kq) ? lj[kq - 1] : S.thr[j];
+                  if (kk < kth) cc = dev::warp_insert(lj, cc, kq, kk, lane);
+                }
               }
               if (lane == 0) {
                 S.cnt4[qd][j] = cc;
-                if (cc == kq) {
-                  const u64 kth = ql[j * a.k + kq - 1];
-                  if (cc0 < kq || kth < kth0) {
-                    // a full quarter list: its k-th bounds the item's and the slot's
-                    atomic_min_float_nonneg(&S.Tq[j], dev::key_d2(kth));
-                    atomicMin(&a.thr[S.slot[j]], kth);
-                  }
-                }
+                // a full quarter list's k-th bounds the item's k-th
+                if (cc == kq) atomic_min_float_nonneg(&S.Tq[j], dev::key_d2(lj[kq - 1]));
               }
               __syncwarp();
             }
@@ -833,12 +945,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               else break;  // the rest of a sorted list is no better
             }
           }
-          if (lane == 0) {
-            S.cnt[q] = cc;
-            // a full list's k-th key bounds the slot's final k-th key: later work
-            // items of the round admit against it
-            if (cc == kq) atomicMin(&a.thr[S.slot[q]], lists[q * a.k + kq - 1]);
-          }
+          if (lane == 0) S.cnt[q] = cc;
+          // the item's list joins the round's shared list of the slot, whose
+          // k-th key later work items admit against
+          if (a.gs && cc > 0)
+            share_list(a.gs + (size_t)S.slot[q] * a.k, a.glock + S.slot[q], lists + q * a.k, cc, kq,
+                       lists + ((size_t)G + q) * a.k, lane);
           __syncwarp();
         }
         epi_sync();
