@@ -89,7 +89,10 @@ def parse():
     a.n = a.n if a.n is not None else dflt[0]
     a.leaf_cap = a.leaf_cap if a.leaf_cap is not None else dflt[1]
     a.filters = a.filters if a.filters is not None else dflt[2]
-    a.wave = a.wave if a.wave is not None else (512 if a.config == "mixed" else 64)
+    # waves: 64 leaves per query on the 1M random walks; the exact precision
+    # search takes every leaf after the route leaf in one wave (its bounds
+    # prune about 5% of the series, so narrow waves only re-read the data)
+    a.wave = a.wave if a.wave is not None else {"mixed": 512, "precision": 4096}.get(a.config, 64)
     return a
 
 

@@ -62,7 +62,7 @@ typedef struct {
   int32_t dstree_init_segments; /* DSTree root segmentation: equal segments (4) */
   int32_t isax_segments;        /* iSAX PAA segments w (16); m % w == 0 */
   int32_t isax_card_bits;       /* iSAX full cardinality 2^bits (8) */
-  int32_t wave;                 /* leaves taken per query per search wave (>= 1); the
+  int32_t wave;                 /* leaves taken per query per search wave (1..65536); the
                                    auto-tuner calibrates this same schedule */
   int32_t device;               /* CUDA device ordinal (-1: host-only tree) */
   int32_t scan_path;            /* 0: tensor-core scan (float16 dot products on tcgen05

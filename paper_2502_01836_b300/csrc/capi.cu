@@ -358,18 +358,9 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.item_leaf = item_leaf;
     t.work = ix->sc->sWork.need(1);
     LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
-    t.thr = thr;
-    t.gs = nullptr;
-    t.glock = nullptr;
-    if (kstride > 1) {
-      t.gs = ix->sc->sGs.need((size_t)nslots * kstride);
-      t.glock = ix->sc->sGlock.need(nslots);
-      LF_CUDA(cudaMemsetAsync(t.gs, 0xFF, sizeof(unsigned long long) * (size_t)nslots * kstride, s));
-      LF_CUDA(cudaMemsetAsync(t.glock, 0, sizeof(int32_t) * (size_t)nslots, s));
-    }
-    t.cand = cand;
-    t.cand_cnt = cand_cnt;
-    t.cand_cap = cap;
+    t.topk = topk;
+    t.glock = ix->sc->sGlock.need(nslots);
+    launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, s);
     t.err = ix->sErr.p;
     t.stat = recheck_stat;
     t.prof = ix->profiling >= 2 ? ix->scan_prof.p : nullptr;
@@ -377,7 +368,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     launch_tc_scan(ix->xh_map, t, nitems, slot_k, grid, s);
     ix->tock();
     ix->tick(1);
-    launch_merge(nslots, kstride, slot_k, topk, topk_cnt, thr, cand, cand_cnt, cap, s);
+    launch_tc_round_finish(nslots, kstride, slot_k, topk, topk_cnt, thr, s);
     ix->tock();
     return;
   }
@@ -447,14 +438,16 @@ void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dL
   if (nslots == 0) return;
   slots_init_kernel<<<(nslots + 255) / 256, 256, 0, s>>>(nslots, topk_cnt.p, thr, cand_cnt);
   LF_CHECK_LAUNCH();
-  // batches of queries keep the candidate buffer bounded
+  const TcQueries tq = prep_tc_queries(ix, dQ, nq, 0);
+  // batches of queries keep the CUDA-core scan's candidate buffer bounded
+  // (the tensor-core scan merges into the lists directly)
+  const bool direct = tq.Qh && tc_nbuf(ix, k) > 0;
   const size_t per_query = (size_t)nl * cap * sizeof(unsigned long long);
   int qb = (int)std::max<size_t>(1, kKnnBudget / std::max<size_t>(per_query, 1));
-  qb = std::min(qb, nq);
-  unsigned long long* cand = ix->sc->sCand.need((size_t)qb * nl * cap);
+  qb = direct ? nq : std::min(qb, nq);
+  unsigned long long* cand = direct ? nullptr : ix->sc->sCand.need((size_t)qb * nl * cap);
   Pair* pairs = ix->sc->sPairs.need((size_t)qb * nl);
   int32_t* np = ix->sc->sNpairs.need(1);
-  const TcQueries tq = prep_tc_queries(ix, dQ, nq, 0);
   for (int q0 = 0; q0 < nq; q0 += qb) {
     const int nb = std::min(qb, nq - q0);
     const int ns = nb * nl;
@@ -575,8 +568,10 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
   stat = counters;
   const HostTree& t = ix->tree;
   L = t.n_leaves;
-  W = ix->wave;
-  cap = std::max(W, 1) * max_parts(t) * kmax;
+  W = std::min(ix->wave, std::max(L, 1));  // wider waves take every leaf all the same
+  // the tensor-core scan merges into the top-k lists directly; the CUDA-core
+  // scan appends every work item's list to a candidate buffer
+  cap = tc_nbuf(ix, kmax) > 0 ? 0 : std::max(W, 1) * max_parts(t) * kmax;
   qb = kBatch;
   for (int li = 0; li < nlanes; ++li) {
     Scratch& S = lanes[li];
@@ -597,7 +592,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     v.topk = S.sTopk.need((size_t)qb * kmax);
     v.topk_cnt = S.sTopkCnt.need(qb);
     v.thr = S.sThr.need(qb);
-    v.cand = S.sCand.need((size_t)qb * cap);
+    v.cand = cap ? S.sCand.need((size_t)qb * cap) : nullptr;
     v.cand_cnt = S.sCandCnt.need(qb);
     v.done = S.sDone.need(qb);
     v.pairs = S.sPairs.need((size_t)qb * std::max(W, 1));
@@ -614,10 +609,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
       v.tq.Qk = S.sQk.need((size_t)2 * qb);
       S.sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(t));
       S.sWork.need(1);
-      if (kmax > 1) {
-        S.sGs.need((size_t)qb * kmax);
-        S.sGlock.need(qb);
-      }
+      S.sGlock.need(qb);
     }
     S.sCnt.need(L);
     S.sGrpOff.need(L + 1);

@@ -172,13 +172,9 @@ struct TcScanArgs {
   const int32_t* item_off;
   const int32_t* item_leaf;        // leaf of every work item
   int32_t* work;                   // work-item counter (zero at launch)
-  unsigned long long* thr;         // per slot k-th best key; lowered by finished work items
-  unsigned long long* gs;          // k > 1: per slot the round's shared list [nslots][k] (kNoKey
-                                   // filled at the round's start), or null
-  int32_t* glock;                  // its per-slot locks (zero at the round's start)
-  unsigned long long* cand;
-  int32_t* cand_cnt;
-  int cand_cap;
+  unsigned long long* topk;        // [nslots][k] ascending keys, kNoKey padded
+                                   // (launch_tc_round_prep); work items merge into it
+  int32_t* glock;                  // per slot lock of its list (zero at the round's start)
   int32_t* err;
   unsigned long long* stat;        // nullable: [0] += canonical re-checks
   unsigned long long* prof;        // nullable: per-phase cycle counters (16)
@@ -191,6 +187,14 @@ void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, fl
                           cudaStream_t s);
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s);
+// before a tensor-core round: pad every slot's list (entries [cnt, k)) with
+// kNoKey and release the slot locks; after it: count the list entries and
+// set each slot's threshold (its k-th key, kNoKey while fewer than k)
+void launch_tc_round_prep(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
+                          const int32_t* topk_cnt, int32_t* glock, cudaStream_t s);
+void launch_tc_round_finish(int nslots, int kstride, const int32_t* slot_k,
+                            const unsigned long long* topk, int32_t* topk_cnt,
+                            unsigned long long* thr, cudaStream_t s);
 void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k, int grid,
                  cudaStream_t s);
 
@@ -308,8 +312,7 @@ struct Scratch {
   DBuf<unsigned char> sScanned, sOrderTmp;
   DBuf<Pair> sPairs, sGrouped;
   DBuf<unsigned long long> sTopk, sThr, sCand;
-  DBuf<unsigned long long> sGs;   // round's shared per-slot lists of the tensor-core scan (k > 1)
-  DBuf<int32_t> sGlock;           // their locks
+  DBuf<int32_t> sGlock;           // per slot locks of the tensor-core scan's top-k lists
   DBuf<float> sPred, sOutD;
   DBuf<int64_t> sOutI;
   // search lane

@@ -19,7 +19,7 @@ namespace {
 typedef unsigned long long u64;
 constexpr double kDeflate = 1.0 - 1e-4;
 constexpr int kMaxSortN = 4096;
-constexpr int kMaxWave = 4096;
+constexpr int kMaxWave = 65536;
 
 __device__ __forceinline__ float key_d2(u64 k) { return __uint_as_float((uint32_t)(k >> 32)); }
 

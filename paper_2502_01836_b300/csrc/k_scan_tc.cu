@@ -32,13 +32,13 @@
 // list per query (the quarter's two warps split the columns), re-checks run
 // at once, and the quarter lists merge at the end of the item.
 //
-// Work items of one round share their progress: an item reads each query's
-// threshold when it starts and, when it ends, lowers it (atomic minimum of
-// keys) to its own k-th best key once it holds k series.  Every (query,
-// series) pair belongs to exactly one item, so a series of the final top-k
-// has a smaller key than any other item's k-th key and is never dropped by
-// the lowered threshold; the merge after the scan recomputes the threshold
-// from all candidates, so the results do not depend on the order of items.
+// Work items merge their results straight into each query's top-k list (an
+// atomic minimum for k = 1; for k > 1 a warp-wide merge under the slot's
+// lock), and every item admits against the list's current k-th key, read
+// when it starts and again every other chunk.  Every (query, series) pair
+// belongs to exactly one item, so a series of the final top-k has a smaller
+// key than the k-th key of any list that does not contain it and is never
+// dropped; the final lists do not depend on the order of items.
 #include <cfloat>
 
 #include "device_util.cuh"
@@ -310,27 +310,34 @@ __device__ __forceinline__ int warp_merge_keys(u64* L, int cc, int kq, u64 key, 
   return min(kq, cc + nnew);
 }
 
-constexpr int kShareTries = 16;  // lock attempts before an item gives up sharing its list
+// Attempts at a slot's lock before a work item reports a timeout.  The lock
+// is held for one warp-wide merge of at most 2k keys, so the limit (tens of
+// milliseconds with the back-off) is only reached if something is broken.
+constexpr int kLockTries = 1 << 16;
 
-// Merge an item's ascending list B (cb entries) into the round's shared list
-// gl of the slot (kq entries, kNoKey padded, ascending, keys of other items)
-// under the slot's lock.  The lock is only tried a bounded number of times:
-// sharing tightens later items' admission and is skipped when contended.
-// Readers take gl[kq - 1] without the lock; it is written once per merge, and
-// both its old and its new value are the k-th key of k distinct scanned series.
-__device__ __forceinline__ void share_list(u64* gl, int32_t* lock, const u64* B, int cb, int kq,
+// Merge an item's ascending list B (cb entries) into the slot's top-k list gl
+// (kq entries, ascending, kNoKey padded; keys of other items and of earlier
+// rounds) under the slot's lock.  Readers take gl[kq - 1] without the lock:
+// it is written once per merge, and both its old and its new value are the
+// k-th key of k distinct scanned series (or kNoKey).  Returns false if the
+// lock could not be taken (the list is then left unchanged).
+__device__ __forceinline__ bool share_list(u64* gl, int32_t* lock, const u64* B, int cb, int kq,
                                            u64* scratch, int lane) {
   const u64 gk = __ldcg(&gl[kq - 1]);
-  if (!(B[0] < gk)) return;  // nothing of this item enters the shared list
+  if (!(B[0] < gk)) return true;  // nothing of this item enters the list
   int got = 0;
   if (lane == 0) {
-    for (int t = 0; t < kShareTries && !got; ++t) {
+    unsigned ns = 32;
+    for (int t = 0; t < kLockTries && !got; ++t) {
       got = atomicCAS(lock, 0, 1) == 0 ? 1 : 0;
-      if (!got) __nanosleep(64);
+      if (!got) {
+        __nanosleep(ns);
+        ns = ns < 1024 ? 2 * ns : ns;
+      }
     }
   }
   got = __shfl_sync(0xffffffffu, got, 0);
-  if (!got) return;
+  if (!got) return false;
   __threadfence();
   for (int p = lane; p < kq; p += 32) scratch[p] = __ldcg(&gl[p]);
   __syncwarp();
@@ -357,6 +364,7 @@ __device__ __forceinline__ void share_list(u64* gl, int32_t* lock, const u64* B,
   __threadfence();
   __syncwarp();
   if (lane == 0) atomicExch(lock, 0);
+  return true;
 }
 
 // Work items are claimed dynamically: the TMA thread takes the next index
@@ -674,14 +682,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         if (qq < nqg) {
           const int slot = I.pr[qq].slot, qrow = I.pr[qq].q;
           const float4 k0 = a.Qk[2 * (size_t)qrow], k1 = a.Qk[2 * (size_t)qrow + 1];
-          // the slot's threshold as other work items of this round have lowered it
-          // (k > 1: also the k-th key of the round's shared list of the slot)
+          // the slot's k-th best key so far: earlier rounds and the work items
+          // of this round that have finished (kNoKey while fewer than k)
           const int kqs = slot_k ? slot_k[slot] : a.k;
-          u64 th = __ldcg(&a.thr[slot]);
-          if (a.gs) {
-            const u64 gk = __ldcg(&a.gs[(size_t)slot * a.k + kqs - 1]);
-            th = gk < th ? gk : th;
-          }
+          const u64 th = __ldcg(&a.topk[(size_t)slot * a.k + kqs - 1]);
           const float thd = (th == kNoKey) ? kInf : dev::key_d2(th);
           S.slot[qq] = slot;
           S.qrow[qq] = qrow;
@@ -823,12 +827,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           // (warps w and w + 4 share the quarter and split the 16-column groups),
           // so no two warps ever write the same list.  The admission bound Tq
           // of a query is shared by the quarters and by the round's other work
-          // items: it falls to any quarter's k-th best distance and to the
-          // slot's threshold as other items lower it (re-read every other
-          // chunk).  Admission compares distances (a - band <= Tq, ties
+          // items: it falls to any quarter's k-th best distance and to the k-th
+          // key of the slot's list as other items merge into it (re-read every
+          // other chunk).  Admission compares distances (a - band <= Tq, ties
           // admitted); insertion compares keys against the quarter's own k-th
-          // or the threshold read at the item's start, so a key this item
-          // published itself never excludes one of its own series.  16 columns
+          // or the list's k-th read at the item's start (the item merges its
+          // own series only when it ends).  16 columns
           // are tested at once, re-checks run at once (one candidate per lane),
           // and the quarter lists merge at the item's end.
           const int qd = warp & 3;
@@ -839,8 +843,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
             // the slot thresholds of these 16 columns, consumed after the tests
             u64 gth = kNoKey;
-            if (refresh && a.gs && lane < 16 && c0 + lane < nqg)
-              gth = __ldcg(&a.gs[(size_t)S.slot[c0 + lane] * a.k + S.kq[c0 + lane] - 1]);
+            if (refresh && lane < 16 && c0 + lane < nqg)
+              gth = __ldcg(&a.topk[(size_t)S.slot[c0 + lane] * a.k + S.kq[c0 + lane] - 1]);
             float d[16];
             dev::tmem_ld16(tl + (uint32_t)c0, d);
             const float4* T4v = reinterpret_cast<const float4*>(&S.Tq[c0]);
@@ -945,36 +949,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               else break;  // the rest of a sorted list is no better
             }
           }
-          if (lane == 0) S.cnt[q] = cc;
-          // the item's list joins the round's shared list of the slot, whose
-          // k-th key later work items admit against
-          if (a.gs && cc > 0)
-            share_list(a.gs + (size_t)S.slot[q] * a.k, a.glock + S.slot[q], lists + q * a.k, cc, kq,
-                       lists + ((size_t)G + q) * a.k, lane);
+          // the item's list joins the slot's top-k list, whose k-th key later
+          // work items admit against
+          if (cc > 0 &&
+              !share_list(a.topk + (size_t)S.slot[q] * a.k, a.glock + S.slot[q], lists + q * a.k, cc,
+                          kq, lists + ((size_t)G + q) * a.k, lane) &&
+              lane == 0)
+            atomicOr(a.err, 2);
           __syncwarp();
         }
         epi_sync();
       }
-      // k = 1 lists hold the part's best key if it beat the round's threshold
+      // k = 1: the part's best key enters the slot's list if it beats it
       if (split && tid < nqg) {
         const u64 best = lists[tid * a.k];
-        S.cnt[tid] = (best < S.thr[tid]) ? 1 : 0;
-        if (best < S.thr[tid]) atomicMin(&a.thr[S.slot[tid]], best);
-      }
-      epi_sync();
-      for (int q = warp; q < nqg; q += kEpiWarps) {
-        const int cc = S.cnt[q];
-        if (cc == 0) continue;
-        const int slot = S.slot[q];
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&a.cand_cnt[slot], cc);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base + cc > a.cand_cap) {
-          if (lane == 0) atomicOr(a.err, 1);
-          continue;
-        }
-        for (int e = lane; e < cc; e += 32)
-          a.cand[(size_t)slot * a.cand_cap + base + e] = lists[q * a.k + e];
+        if (best < S.thr[tid]) atomicMin(&a.topk[S.slot[tid]], best);
       }
       // one thread snapshots the abort flag before the barrier so that every
       // epilogue thread leaves the item loop at the same item
@@ -1020,6 +1009,54 @@ int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem) {
     }
   }
   return 0;
+}
+
+namespace {
+__global__ void round_prep_kernel(int nslots, int kstride, const int32_t* __restrict__ slot_k,
+                                  u64* __restrict__ topk, const int32_t* __restrict__ topk_cnt,
+                                  int32_t* __restrict__ glock) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nslots * kstride) return;
+  const int slot = (int)(t / kstride), z = (int)(t % kstride);
+  if (z >= topk_cnt[slot]) topk[t] = kNoKey;
+  if (z == 0) glock[slot] = 0;
+  (void)slot_k;
+}
+
+__global__ void round_finish_kernel(int nslots, int kstride, const int32_t* __restrict__ slot_k,
+                                    const u64* __restrict__ topk, int32_t* __restrict__ topk_cnt,
+                                    u64* __restrict__ thr) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nslots) return;
+  const int kq = slot_k ? slot_k[slot] : kstride;
+  const u64* l = topk + (size_t)slot * kstride;
+  int lo = 0, hi = kq;  // the list ascends, padding last: count the keys
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (l[mid] != kNoKey) lo = mid + 1;
+    else hi = mid;
+  }
+  topk_cnt[slot] = lo;
+  thr[slot] = lo == kq ? l[kq - 1] : kNoKey;
+}
+}  // namespace
+
+void launch_tc_round_prep(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
+                          const int32_t* topk_cnt, int32_t* glock, cudaStream_t s) {
+  const int64_t tot = (int64_t)nslots * kstride;
+  if (tot == 0) return;
+  round_prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nslots, kstride, slot_k, topk,
+                                                                   topk_cnt, glock);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_tc_round_finish(int nslots, int kstride, const int32_t* slot_k,
+                            const unsigned long long* topk, int32_t* topk_cnt,
+                            unsigned long long* thr, cudaStream_t s) {
+  if (nslots == 0) return;
+  round_finish_kernel<<<(nslots + 255) / 256, 256, 0, s>>>(nslots, kstride, slot_k, topk, topk_cnt,
+                                                           thr);
+  LF_CHECK_LAUNCH();
 }
 
 void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, float4* Qk,
