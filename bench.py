@@ -89,10 +89,12 @@ def parse():
     a.n = a.n if a.n is not None else dflt[0]
     a.leaf_cap = a.leaf_cap if a.leaf_cap is not None else dflt[1]
     a.filters = a.filters if a.filters is not None else dflt[2]
-    # waves: 64 leaves per query on the 1M random walks; the exact precision
-    # search takes every leaf after the route leaf in one wave (its bounds
-    # prune about 5% of the series, so narrow waves only re-read the data)
-    a.wave = a.wave if a.wave is not None else {"mixed": 512, "precision": 4096}.get(a.config, 64)
+    # waves: 64 leaves per query on the 1M random walks; the precision,
+    # mixed-k and serving searches take every remaining leaf after the route
+    # leaf in one wave (measured: narrow waves re-read the same leaves for few
+    # queries each)
+    a.wave = a.wave if a.wave is not None else {"mixed": 65536, "precision": 4096,
+                                                "serving": 4096}.get(a.config, 64)
     return a
 
 
