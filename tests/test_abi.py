@@ -46,6 +46,11 @@ def test_bad_arguments_rejected_without_device():
     assert L.leafi_build(None, 4, 8, ctypes.byref(p), ctypes.byref(h)) == 1
     bad = lf.BuildParams(wave=0, device=-1)
     assert L.leafi_build(X.ctypes.data, 4, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
+    bad = lf.BuildParams(wave=65537, device=-1)
+    assert L.leafi_build(X.ctypes.data, 4, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
+    ok = lf.BuildParams(wave=65536, device=-1)
+    assert L.leafi_build(X.ctypes.data, 4, 8, ctypes.byref(ok), ctypes.byref(h)) == 0
+    L.leafi_free(h)
     bad = lf.BuildParams(index_type=7, device=-1)
     assert L.leafi_build(X.ctypes.data, 4, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
     bad = lf.BuildParams(index_type=lf.ISAX, isax_segments=3, device=-1)

@@ -346,6 +346,73 @@ def test_more_than_4096_leaves(wave):
         lf.leafi_free(idx)
 
 
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_single_leaf_many_work_items_bit_exact(k):
+    """One leaf holding every series: hundreds of work items of one round merge
+    into the same queries' top-k lists concurrently (atomic minimum for k = 1,
+    the slot lock for k > 1); two batches run on two lanes.  Mixed k per query
+    (entries beyond a query's k stay padding) through the mixed entry point."""
+    n, m = 200_000, 96
+    X = fx.embedding_like(n, m, seed=301)
+    Q = fx.test_queries(X, 300, seed=302)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=n, wave=1, device=0))
+    try:
+        assert lf.leafi_get_info(idx).n_leaves == 1
+        ids, d, _ = _exact(idx, Q, k)
+        bf_ids, bf_d2 = O.knn(X, Q, k)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+        if k == 100:
+            rng = np.random.default_rng(303)
+            kq = rng.choice([1, 10, 100], len(Q)).astype(np.int32)
+            tg = np.ones(len(Q))
+            mi = np.zeros((len(Q), k), np.int64)
+            md = np.zeros((len(Q), k), np.float32)
+            lf.leafi_search_mixed(idx, Q, kq, tg, k, mi, md)
+            for i in range(len(Q)):
+                assert np.array_equal(mi[i, :kq[i]], bf_ids[i, :kq[i]])
+                assert np.array_equal(md[i, :kq[i]], np.sqrt(bf_d2[i, :kq[i]]))
+                assert (mi[i, kq[i]:] == -1).all()
+    finally:
+        lf.leafi_free(idx)
+
+
+def test_wave_wider_than_the_index():
+    """A wave width above the number of leaves takes every remaining leaf at
+    once: the search's scan statistics and the auto-tuner equal the oracle's
+    wave semantics with the same width."""
+    X = fx.random_walk(20000, 64, seed=311)
+    Q = fx.test_queries(X, 300, seed=312)
+    wave = 65536
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=400, wave=wave, device=0))
+    try:
+        t = O.Tree(X, "dstree", leaf_cap=400, init_segments=4)
+        assert t.L < wave
+        ids = np.zeros((300, 5), np.int64)
+        d = np.zeros((300, 5), np.float32)
+        st = lf.SearchStats()
+        lf.leafi_exact_search(idx, Q, 5, ids, d, st)
+        bf_ids, bf_d2 = O.knn(X, Q, 5)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+        o_ids, _, o_st, _ = O.leafi_search(t, None, None, None, Q, 5, -1, wave)
+        assert int(o_st[:, 0].sum()) == st.leaves_scanned
+        assert int(o_st[:, 1].sum()) == st.series_scanned
+        sizes = t.leaf_sizes()
+        fl = np.array(sorted(range(t.L), key=lambda l: (-sizes[l], l))[:8], np.int32)
+        Wt = fx.filter_init(8, 64, 64, seed=313)
+        lf.leafi_set_filters(idx, fl, *Wt)
+        Qc = fx.test_queries(X, 100, seed=314)
+        lf.leafi_fit_autotuners(idx, Qc, [1])
+        alpha = np.zeros((8, 100))
+        qp = np.zeros((1, 100))
+        lf.leafi_get_autotuners(idx, alpha, qp)
+        o_alpha, o_qp = O.fit_autotuner(t, Wt, fl, Qc, 1, wave)
+        assert np.abs(alpha - o_alpha).max() <= 1e-5 * _pred_scale(Wt, Qc).max()
+        diff = np.abs(qp[0] - o_qp)
+        assert (diff == 0).mean() >= 0.9 and diff.max() <= 3.0 / 100
+    finally:
+        lf.leafi_free(idx)
+
+
 def test_device_pointers_match_host(ds):
     torch = pytest.importorskip("torch")
     X, Q, idx, t = ds
