@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           // other chunk).  Admission compares distances (a - band <= Tq, ties
           // admitted); insertion compares keys against the quarter's own k-th
           // or the list's k-th read at the item's start (the item merges its
-          // own series only when it ends).  16 columns
+          // own series only when it ends).  32 columns
           // are tested at once, re-checks run at once (one candidate per lane),
           // and the quarter lists merge at the item's end.
           const int qd = warp & 3;
@@ -840,17 +840,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           const float xnorm = sqrtf(xn);
           const float vlo = xn * (1.0f - 1e-4f);
           const bool refresh = (c & 1) == 1;
-          for (int c0 = (warp >> 2) * 16; okw && c0 < N; c0 += 32) {
-            // the slot thresholds of these 16 columns, consumed after the tests
+          // warp w reads columns 32 (w / 4) .. + 31 of its lane quarter in one load
+          const int c0 = (warp >> 2) * 32;
+          if (okw && c0 < N) {
+            // the slot thresholds of these 32 columns, consumed after the tests
             u64 gth = kNoKey;
-            if (refresh && lane < 16 && c0 + lane < nqg)
+            if (refresh && c0 + lane < nqg)
               gth = __ldcg(&a.topk[(size_t)S.slot[c0 + lane] * a.k + S.kq[c0 + lane] - 1]);
-            float d[16];
-            dev::tmem_ld16(tl + (uint32_t)c0, d);
+            float d[32];
+            dev::tmem_ld32(tl + (uint32_t)c0, d);
             const float4* T4v = reinterpret_cast<const float4*>(&S.Tq[c0]);
             unsigned cand = 0;
 #pragma unroll
-            for (int v4 = 0; v4 < 4; ++v4) {
+            for (int v4 = 0; v4 < 8; ++v4) {
               const float4 tv = T4v[v4];
               const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
 #pragma unroll
@@ -861,11 +863,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                 if (!(lo > tt[u])) cand |= 1u << jj;
               }
             }
+            // columns at or past N belong to no query of this item
+            if (N - c0 < 32) cand &= (1u << (N - c0)) - 1u;
             if (!valid) cand = 0u;
             if (I.packed) {
               // a pair only meets the rows of its own leaf
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj)
+              for (int jj = 0; jj < 32; ++jj)
                 if (r < S.rs[c0 + jj] || r >= S.re[c0 + jj]) cand &= ~(1u << jj);
             }
             unsigned any = __reduce_or_sync(0xffffffffu, cand);
@@ -902,7 +906,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               }
               __syncwarp();
             }
-            if (refresh && lane < 16 && gth != kNoKey) {
+            if (refresh && gth != kNoKey) {
               const float g = dev::key_d2(gth);
               if (g < S.Tq[c0 + lane]) atomic_min_float_nonneg(&S.Tq[c0 + lane], g);
             }
