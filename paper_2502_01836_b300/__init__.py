@@ -63,12 +63,13 @@ class BuildParams(C.Structure):
     _fields_ = [("index_type", C.c_int32), ("leaf_capacity", C.c_int32),
                 ("dstree_init_segments", C.c_int32), ("isax_segments", C.c_int32),
                 ("isax_card_bits", C.c_int32), ("wave", C.c_int32), ("device", C.c_int32),
-                ("scan_path", C.c_int32)]
+                ("scan_path", C.c_int32), ("host_build", C.c_int32)]
 
     def __init__(self, index_type=DSTREE, leaf_capacity=10000, dstree_init_segments=4,
-                 isax_segments=16, isax_card_bits=8, wave=64, device=0, scan_path=0):
+                 isax_segments=16, isax_card_bits=8, wave=64, device=0, scan_path=0,
+                 host_build=0):
         super().__init__(index_type, leaf_capacity, dstree_init_segments, isax_segments,
-                         isax_card_bits, wave, device, scan_path)
+                         isax_card_bits, wave, device, scan_path, host_build)
 
 
 class IndexInfo(C.Structure):

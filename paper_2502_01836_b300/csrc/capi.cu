@@ -1039,6 +1039,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     if (p->leaf_capacity < 1) fail(LEAFI_EINVAL, "leaf_capacity < 1");
     if (p->wave < 1 || p->wave > calib_max_wave()) fail(LEAFI_EINVAL, "wave must be in [1, %d]", calib_max_wave());
     if (p->scan_path < 0 || p->scan_path > 1) fail(LEAFI_EINVAL, "scan_path must be 0 or 1");
+    if (p->host_build < 0 || p->host_build > 1) fail(LEAFI_EINVAL, "host_build must be 0 or 1");
     if (p->index_type == LEAFI_DSTREE) {
       if (p->dstree_init_segments < 1 || p->dstree_init_segments > m)
         fail(LEAFI_EINVAL, "dstree_init_segments must be in [1, m]");
@@ -1075,21 +1076,37 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     ix->n = n;
     ix->wave = p->wave;
     cudaStream_t s = ix->stream;
-    // the tree is built on the host from a host copy of the series
-    std::vector<float> hostX;
-    const float* hx = series;
-    if (on_device(series)) {
-      to_host(hostX, series, (size_t)n * m, s);
-      hx = hostX.data();
-    }
-    if (p->index_type == LEAFI_DSTREE)
-      ix->tree = build_dstree(hx, n, m, p->leaf_capacity, p->dstree_init_segments);
-    else
-      ix->tree = build_isax(hx, n, m, p->leaf_capacity, p->isax_segments, p->isax_card_bits);
-    HostTree& t = ix->tree;
-    // leaf-major, 16-byte aligned rows of mp floats, uploaded in chunks
-    float* X = ix->X.need((size_t)n * ix->mp);
-    {
+    float* X = nullptr;
+    if (p->index_type == LEAFI_DSTREE && !p->host_build) {
+      // the tree is built on the device from the series in id order
+      DBuf<float> idX;
+      const float* dX = series;
+      if (!on_device(series)) {
+        idX.upload(series, (size_t)n * m, s);
+        dX = idX.p;
+      }
+      ix->tree = build_dstree_device(dX, n, m, p->leaf_capacity, p->dstree_init_segments, s);
+      HostTree& t = ix->tree;
+      // leaf-major, 16-byte aligned rows of mp floats, gathered on the device
+      ix->ids.upload(t.order, s);
+      X = ix->X.need((size_t)n * ix->mp);
+      launch_gather_rows(dX, n, m, ix->ids.p, ix->mp, X, s);
+      LF_CUDA(cudaStreamSynchronize(s));
+    } else {
+      // the tree is built on the host from a host copy of the series
+      std::vector<float> hostX;
+      const float* hx = series;
+      if (on_device(series)) {
+        to_host(hostX, series, (size_t)n * m, s);
+        hx = hostX.data();
+      }
+      if (p->index_type == LEAFI_DSTREE)
+        ix->tree = build_dstree(hx, n, m, p->leaf_capacity, p->dstree_init_segments);
+      else
+        ix->tree = build_isax(hx, n, m, p->leaf_capacity, p->isax_segments, p->isax_card_bits);
+      HostTree& t = ix->tree;
+      // leaf-major, 16-byte aligned rows of mp floats, uploaded in chunks
+      X = ix->X.need((size_t)n * ix->mp);
       const int64_t chunk = 1 << 16;
       std::vector<float> stage((size_t)std::min<int64_t>(chunk, n) * ix->mp, 0.0f);
       for (int64_t p0 = 0; p0 < n; p0 += chunk) {
@@ -1099,8 +1116,9 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
         LF_CUDA(cudaMemcpy(X + (size_t)p0 * ix->mp, stage.data(), sizeof(float) * cnt * ix->mp,
                            cudaMemcpyHostToDevice));
       }
+      ix->ids.upload(t.order, s);
     }
-    ix->ids.upload(t.order, s);
+    HostTree& t = ix->tree;
     ix->leaf_off.upload(t.leaf_off, s);
     ix->left.upload(t.node_left, s);
     ix->right.upload(t.node_right, s);

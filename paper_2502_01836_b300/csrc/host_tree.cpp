@@ -66,31 +66,13 @@ inline MeanSd interval_stat(const double* p1, const double* p2, int s, int e) {
   return {mean, std::sqrt(var)};
 }
 
-struct Ranges {
-  double mlo = kInf, mhi = -kInf, slo = kInf, shi = -kInf;
-  void add(const MeanSd& v) {
-    mlo = std::min(mlo, v.mu);
-    mhi = std::max(mhi, v.mu);
-    slo = std::min(slo, v.sd);
-    shi = std::max(shi, v.sd);
-  }
-};
+using Ranges = SegRanges;
+inline void add_stat(Ranges& g, const MeanSd& v) { g.add(v.mu, v.sd); }
 
 // --------------------------------------------------------------------------
 // DSTree
 // --------------------------------------------------------------------------
 
-struct DsNode {
-  std::vector<int> ends;  // own segmentation (segment end points)
-  std::vector<Ranges> syn;
-  bool leaf = true;
-  int parent = -1, left = -1, right = -1;
-  std::vector<int> child_ends;
-  int split_seg = -1;
-  bool split_sd = false;
-  double thresh = 0.0;
-  std::vector<int32_t> members;
-};
 
 inline int seg_start(const std::vector<int>& ends, int r) { return r == 0 ? 0 : ends[r - 1]; }
 
@@ -122,7 +104,7 @@ class DsBuilder {
     for (;;) {
       DsNode& nd = nodes_[at];
       for (size_t r = 0; r < nd.ends.size(); ++r)
-        nd.syn[r].add(interval_stat(p1, p2, seg_start(nd.ends, static_cast<int>(r)), nd.ends[r]));
+        add_stat(nd.syn[r], interval_stat(p1, p2, seg_start(nd.ends, static_cast<int>(r)), nd.ends[r]));
       if (nd.leaf) {
         nd.members.push_back(id);
         if (static_cast<int64_t>(nd.members.size()) > cap_) split(at);
@@ -214,8 +196,8 @@ class DsBuilder {
         std::vector<Ranges>& side = goes_left ? lft : rgt;
         for (int q = 0; q < cn; ++q) {
           const MeanSd v = child_stat(c, whole, halves, S, d, q);
-          all[q].add(v);
-          side[q].add(v);
+          add_stat(all[q], v);
+          add_stat(side[q], v);
         }
       }
       const size_t nr = nD - nl;
@@ -255,7 +237,7 @@ class DsBuilder {
       const MeanSd st = child_stat(c, whole, halves, S, d, q_split);
       DsNode& side = ((c.sd ? st.sd : st.mu) < thresh[best]) ? L : R;
       side.members.push_back(mem[d]);
-      for (int q = 0; q < cn; ++q) side.syn[q].add(child_stat(c, whole, halves, S, d, q));
+      for (int q = 0; q < cn; ++q) add_stat(side.syn[q], child_stat(c, whole, halves, S, d, q));
     }
     const int li = static_cast<int>(nodes_.size());
     nodes_.push_back(std::move(L));
@@ -425,16 +407,7 @@ class IsaxBuilder {
 
 }  // namespace
 
-HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_segments) {
-  DsBuilder b(X, n, m, leaf_cap);
-  b.make_root(init_segments);
-  std::vector<double> p(2 * (m + 1));
-  for (int64_t id = 0; id < n; ++id) {
-    prefix_sums(X + id * m, m, p.data(), p.data() + m + 1);
-    b.insert(static_cast<int32_t>(id), p.data(), p.data() + m + 1);
-  }
-  std::vector<DsNode>& nodes = b.nodes();
-
+HostTree dstree_from_nodes(std::vector<DsNode>& nodes, int64_t n, int m) {
   HostTree t;
   t.type = LEAFI_DSTREE;
   t.m = m;
@@ -493,6 +466,17 @@ HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_s
   layout_leaves(t, leaf_members);
   build_paths(t);
   return t;
+}
+
+HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_segments) {
+  DsBuilder b(X, n, m, leaf_cap);
+  b.make_root(init_segments);
+  std::vector<double> p(2 * (m + 1));
+  for (int64_t id = 0; id < n; ++id) {
+    prefix_sums(X + id * m, m, p.data(), p.data() + m + 1);
+    b.insert(static_cast<int32_t>(id), p.data(), p.data() + m + 1);
+  }
+  return dstree_from_nodes(b.nodes(), n, m);
 }
 
 HostTree build_isax(const float* X, int64_t n, int m, int leaf_cap, int w, int card_bits) {

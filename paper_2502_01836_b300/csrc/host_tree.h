@@ -3,6 +3,7 @@
 // leafi_build; every per-query step runs on the GPU.
 #pragma once
 #include <cstdint>
+#include <limits>
 #include <vector>
 
 namespace leafi {
@@ -47,9 +48,46 @@ struct HostTree {
   std::vector<int32_t> node_bits, node_sym;  // node x w
 };
 
+// Range of the members' segment means and standard deviations.
+struct SegRanges {
+  double mlo = std::numeric_limits<double>::infinity();
+  double mhi = -std::numeric_limits<double>::infinity();
+  double slo = std::numeric_limits<double>::infinity();
+  double shi = -std::numeric_limits<double>::infinity();
+  void add(double mu, double sd) {
+    mlo = mu < mlo ? mu : mlo;
+    mhi = mhi < mu ? mu : mhi;
+    slo = sd < slo ? sd : slo;
+    shi = shi < sd ? sd : shi;
+  }
+};
+
+// DSTree node as the builders produce it (any creation order; the tree's
+// numbering is the depth-first preorder of dstree_from_nodes).
+struct DsNode {
+  std::vector<int> ends;  // own segmentation (segment end points)
+  std::vector<SegRanges> syn;
+  bool leaf = true;
+  int parent = -1, left = -1, right = -1;
+  std::vector<int> child_ends;
+  int split_seg = -1;
+  bool split_sd = false;
+  double thresh = 0.0;
+  std::vector<int32_t> members;  // leaves: ascending ids
+};
+
+// Flat tables of a DSTree from its nodes (node 0 is the root).
+HostTree dstree_from_nodes(std::vector<DsNode>& nodes, int64_t n, int m);
+
 // Deterministic builds; both follow the readings documented with the oracle
 // and produce identical trees for identical inputs.
 HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_segments);
+// The same DSTree built level by level on the GPU from the series in id order
+// on the device (dX: n rows of m floats).  Equal to build_dstree: a node's
+// split is decided on its first members in id order, exactly when sequential
+// insertion would decide it (see build_device.cu).  `stream` is a cudaStream_t.
+HostTree build_dstree_device(const float* dX, int64_t n, int m, int leaf_cap, int init_segments,
+                             void* stream);
 HostTree build_isax(const float* X, int64_t n, int m, int leaf_cap, int w, int card_bits);
 
 }  // namespace leafi

@@ -183,6 +183,9 @@ int tc_group_size(int k);
 // query tiles (2 or 1) the tensor-core scan can keep for rows of kp halves and
 // top-k lists of k keys within `smem_optin` bytes; 0 if it does not fit
 int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem);
+// out[p][i] = X[order[p]][i] for i < m, 0 for m <= i < mp (leaf-major rows)
+void launch_gather_rows(const float* X, int64_t n, int m, const int32_t* order, int mp, float* out,
+                        cudaStream_t s);
 void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, float4* Qk,
                           cudaStream_t s);
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
