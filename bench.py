@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="leafi", choices=["leafi", "reference"])
     ap.add_argument("--config", default="batched",
-                    choices=["batched", "serving", "mixed", "precision"])
+                    choices=["batched", "serving", "mixed", "precision", "ablation"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--queries", type=int, default=10_000)
     ap.add_argument("--launch", type=int, default=256)
@@ -84,7 +84,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
-    dflt = {"batched": (1_000_000, 10_000, 100), "serving": (50_000_000, 10_000, 1000),
+    dflt = {"batched": (1_000_000, 10_000, 100), "ablation": (1_000_000, 10_000, 100),
+            "serving": (50_000_000, 10_000, 1000),
             "mixed": (25_000_000, 20_000, 1000), "precision": (10_000_000, 10_000, 0)}[a.config]
     a.n = a.n if a.n is not None else dflt[0]
     a.leaf_cap = a.leaf_cap if a.leaf_cap is not None else dflt[1]
@@ -575,13 +576,62 @@ def run_precision(a):
            "build_s": {"data": t_data}, "data": "synthetic"})
 
 
+def run_ablation(a):
+    """Without local training data (Sec. 5, the -Local study): the batched
+    random-walk workload searched exactly, with filters trained on global
+    queries only (-Local) and on global plus local queries (+Local, LeaFi),
+    recall target 0.99; throughput, series scanned and recall against exact."""
+    torch, lf = _gpu_setup()
+    from paper_2502_01836_b300.workflow import enhance
+    X = fx.random_walk(a.n, M)
+    Q = fx.test_queries(X, a.queries)
+    Qd = torch.from_numpy(Q).cuda()
+    ids = torch.zeros((a.queries, 1), dtype=torch.int64, device="cuda")
+    dd = torch.zeros((a.queries, 1), dtype=torch.float32, device="cuda")
+
+    def timed(idx, target):
+        for _ in range(a.warmup):
+            lf.leafi_search(idx, Qd, 1, target, ids, dd)
+        st = lf.SearchStats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = max(1, a.steps // 3)
+        for _ in range(reps):
+            lf.leafi_search(idx, Qd, 1, target, ids, dd, st)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / reps
+        return a.queries / sec, ids[:, 0].cpu().numpy().copy(), st.series_scanned / a.queries
+
+    rows = {}
+    bp = lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=0)
+    idx = lf.leafi_build(X, bp)
+    qps, exact, ser = timed(idx, 1.0)
+    rows["exact"] = {"qps": qps, "series_scanned_per_query": ser, "recall_at_1": 1.0}
+    lf.leafi_free(idx)
+    for name, (ltr, lval) in (("-Local", (0, 0)), ("+Local", (400, 100))):
+        idx = lf.leafi_build(X, bp)
+        enhance(idx, X, a.filters, lf.TrainParams(n_ltrain=ltr, n_lval=lval, max_epochs=a.epochs))
+        qps, got, ser = timed(idx, a.target)
+        rows[name] = {"qps": qps, "series_scanned_per_query": ser,
+                      "recall_at_1": float(np.mean(got == exact)),
+                      "meets_target": bool(np.mean(got == exact) >= a.target)}
+        lf.leafi_free(idx)
+    _emit({"metric": "LeaFi without and with local training data: queries/s and recall@1",
+           "unit": "queries/s", "value": rows["+Local"]["qps"], "rows": rows,
+           "config": {"workload": "DSTree over %d random walks x %d, leaf capacity %d, filters on "
+                                  "the %d largest leaves, %d queries, 1-NN, target %.2f, wave %d"
+                                  % (a.n, M, a.leaf_cap, a.filters, a.queries, a.target, a.wave)},
+           "data": "synthetic"})
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
         return
     if a.config != "batched":
-        {"serving": run_serving, "mixed": run_mixed, "precision": run_precision}[a.config](a)
+        {"serving": run_serving, "mixed": run_mixed, "precision": run_precision,
+         "ablation": run_ablation}[a.config](a)
         return
     import torch
     rank, world, local, dist = dist_setup(a.gpus)

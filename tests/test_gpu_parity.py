@@ -157,24 +157,27 @@ def test_filter_forward_paths_ragged(path):
         lf.leafi_free(idx)
 
 
-def test_one_epoch_of_sgd_matches_oracle(ds):
+@pytest.mark.parametrize("ltrain,lval", [(24, 6), (0, 0)])
+def test_one_epoch_of_sgd_matches_oracle(ds, ltrain, lval):
+    """One epoch of SGD on the GPU equals the oracle's; (0, 0) is training
+    without local queries (the -Local study)."""
     X, Q, idx, t = ds
     F = 4
     fl, W = _filters(t, F, seed=9)
     lf.leafi_set_filters(idx, fl, *W)
     members = fx.leaf_members_from(t.leaf_of(), fl)
-    Qg, Ql = fx.training_queries(X, members, 100, 30, seed=77)
+    Qg, Ql = fx.training_queries(X, members, 100, ltrain + lval, seed=77)
     # a small learning rate keeps this short run away from SGD divergence, which
     # would make the comparison meaningless
-    p = lf.TrainParams(n_gtrain=80, n_gval=20, n_ltrain=24, n_lval=6, batch=16, max_epochs=1,
-                       patience=5, lr0=1e-3, lr_min=1e-5)
-    perms = fx.epoch_permutations(1, 104, seed=78)
+    p = lf.TrainParams(n_gtrain=80, n_gval=20, n_ltrain=ltrain, n_lval=lval, batch=16,
+                       max_epochs=1, patience=5, lr0=1e-3, lr_min=1e-5)
+    perms = fx.epoch_permutations(1, 80 + ltrain, seed=78)
     lf.leafi_train_filters(idx, p, Qg, Ql, perms)
     got = tuple(np.zeros_like(a) for a in W)
     lf.leafi_get_filters(idx, *got)
     Tg, Tl = O.train_targets(t, fl, Qg, Ql)
-    op = O.TrainParams(n_gtrain=80, n_gval=20, n_ltrain=24, n_lval=6, batch=16, max_epochs=1,
-                       patience=5, lr0=1e-3, lr_min=1e-5)
+    op = O.TrainParams(n_gtrain=80, n_gval=20, n_ltrain=ltrain, n_lval=lval, batch=16,
+                       max_epochs=1, patience=5, lr0=1e-3, lr_min=1e-5)
     ref, _, _ = O.train(op, Qg, Tg, Ql, Tl, perms, *W)
     for g, r, w0 in zip(got, ref, W):
         moved = np.abs(r.astype(np.float64) - w0)
