@@ -69,11 +69,11 @@ typedef struct {
                                    with a proven error band and a canonical float32
                                    re-check); 1: CUDA-core scan (canonical float32 for
                                    every pair).  Both give identical results. */
-  int32_t host_build;           /* DSTree only.  0: built level by level on the GPU (the
+  int32_t host_build;           /* 0: the tree is built level by level on the GPU (the
                                    series in id order are copied to the device once);
                                    1: sequential insertion on the host.  Both give the
-                                   same tree.  iSAX trees and host-only indexes (device
-                                   -1) are always built on the host. */
+                                   same tree.  Host-only indexes (device -1) are always
+                                   built on the host. */
 } leafi_build_params;
 
 /* Build an index over n series of length m.  Copies `series` into

@@ -418,6 +418,87 @@ __global__ void iota_kernel(int32_t* p, int64_t n) {
   if (i < n) p[i] = (int32_t)i;
 }
 
+// iSAX: full-cardinality symbols (PAA from the float64 prefix sums, then the
+// number of breakpoints beta_1 .. beta_{C-1} at or below it) and root keys
+__global__ void isax_symbols_kernel(const float* __restrict__ X, int64_t n, int m, int w, int l,
+                                    const double* __restrict__ beta, int C, int bits,
+                                    uint16_t* __restrict__ full, int32_t* __restrict__ key) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n) return;
+  const float* row = X + id * m;
+  double a = 0.0, ps = 0.0;
+  int k = 0;
+  for (int j = 0; j < w; ++j) {
+    for (int i = j * l; i < (j + 1) * l; ++i) a = __dadd_rn(a, (double)row[i]);
+    const double paa = __ddiv_rn(__dsub_rn(a, ps), (double)l);
+    ps = a;
+    int lo = 1, hi = C;  // first index in [1, C) with beta > paa
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (beta[mid] <= paa) lo = mid + 1;
+      else hi = mid;
+    }
+    const int sym = lo - 1;
+    full[id * w + j] = (uint16_t)sym;
+    k = (k << 1) | (sym >> (bits - 1));
+  }
+  key[id] = k;
+}
+
+struct IsaxJob {
+  int64_t off;
+  int j;          // members the decision uses
+  int bits[20];   // the node's cardinality bits per segment
+};
+
+// per node: ones among the first j members' next bit of every segment
+__global__ void __launch_bounds__(kBuildThreads) isax_count_kernel(
+    const uint16_t* __restrict__ full, int w, int card_bits, const int32_t* __restrict__ perm,
+    const IsaxJob* __restrict__ jobs, int32_t* __restrict__ ones) {
+  __shared__ int cnt[20];
+  const IsaxJob J = jobs[blockIdx.x];
+  if (threadIdx.x < w) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int loc[20];
+  for (int q = 0; q < w; ++q) loc[q] = 0;
+  for (int d = threadIdx.x; d < J.j; d += blockDim.x) {
+    const uint16_t* fs = full + (int64_t)perm[J.off + d] * w;
+    for (int q = 0; q < w; ++q)
+      if (J.bits[q] < card_bits) loc[q] += (fs[q] >> (card_bits - J.bits[q] - 1)) & 1;
+  }
+  for (int q = 0; q < w; ++q) {
+    const int v = __reduce_add_sync(0xffffffffu, loc[q]);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&cnt[q], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < w) ones[(size_t)blockIdx.x * w + threadIdx.x] = cnt[threadIdx.x];
+}
+
+struct IsaxRoute {
+  int seg, have;  // refined segment and its bits before the split
+};
+
+// left (next bit 0) flags of a split node's members and the per-block counts
+__global__ void __launch_bounds__(kBuildThreads) isax_flag_kernel(
+    const uint16_t* __restrict__ full, int w, int card_bits, const int32_t* __restrict__ perm,
+    const RouteJob* __restrict__ jobs, const IsaxRoute* __restrict__ how,
+    const RouteBlock* __restrict__ blocks, unsigned char* __restrict__ left_flag,
+    int32_t* __restrict__ block_left) {
+  __shared__ int ired[kBuildThreads / 32];
+  const RouteBlock B = blocks[blockIdx.x];
+  const RouteJob J = jobs[B.job];
+  const IsaxRoute H = how[B.job];
+  const int64_t d = B.start + threadIdx.x;
+  int left = 0;
+  if (d < J.cnt) {
+    const int bit = (full[(int64_t)perm[J.off + d] * w + H.seg] >> (card_bits - H.have - 1)) & 1;
+    left = bit == 0;
+    left_flag[J.off + d] = (unsigned char)left;
+  }
+  const int nl = block_sum(left, ired);
+  if (threadIdx.x == 0) block_left[blockIdx.x] = nl;
+}
+
 double from_key(unsigned long long k) {
   const unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
   double x;
@@ -710,6 +791,177 @@ HostTree build_dstree_device(const float* dX, int64_t n, int m, int leaf_cap, in
   for (const Open& o : leaves)
     nodes[o.node].members.assign(perm_h.begin() + o.off, perm_h.begin() + o.off + o.cnt);
   return dstree_from_nodes(nodes, n, m);
+}
+
+HostTree build_isax_device(const float* dX, int64_t n, int m, int leaf_cap, int w, int card_bits,
+                           void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t cap = leaf_cap;
+  const int C = 1 << card_bits;
+  const int l = m / w;
+  const std::vector<double> beta = isax_breakpoints(card_bits);
+  DBuf<double> d_beta;
+  d_beta.upload(beta, s);
+  DBuf<uint16_t> full;
+  full.need((size_t)n * w);
+  DBuf<int32_t> keys;
+  keys.need((size_t)n);
+  isax_symbols_kernel<<<nblocks(n, 128), 128, 0, s>>>(dX, n, m, w, l, d_beta.p, C, card_bits, full.p,
+                                                      keys.p);
+  LF_CHECK_LAUNCH();
+  // root children: ids grouped by root key, ascending within a key
+  std::vector<int32_t> key_h((size_t)n);
+  LF_CUDA(cudaMemcpyAsync(key_h.data(), keys.p, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaStreamSynchronize(s));
+  const size_t K = size_t(1) << w;
+  std::vector<int64_t> kstart(K + 1, 0);
+  for (int64_t id = 0; id < n; ++id) ++kstart[(size_t)key_h[id] + 1];
+  for (size_t k = 0; k < K; ++k) kstart[k + 1] += kstart[k];
+  std::vector<int32_t> perm_h((size_t)n);
+  {
+    std::vector<int64_t> fill(kstart.begin(), kstart.end() - 1);
+    for (int64_t id = 0; id < n; ++id) perm_h[(size_t)fill[(size_t)key_h[id]]++] = (int32_t)id;
+  }
+  std::vector<IsaxNode> nodes;
+  std::vector<int> root_child(K, -1);
+  std::vector<Open> frontier, leaves;
+  for (size_t k = 0; k < K; ++k) {
+    if (kstart[k + 1] == kstart[k]) continue;
+    IsaxNode nd;
+    nd.bits.assign(w, 1);
+    nd.sym.resize(w);
+    for (int j = 0; j < w; ++j) nd.sym[j] = (int)((k >> (w - 1 - j)) & 1);
+    root_child[k] = (int)nodes.size();
+    frontier.push_back({(int)nodes.size(), kstart[k], kstart[k + 1] - kstart[k]});
+    nodes.push_back(std::move(nd));
+  }
+  DBuf<int32_t> permA, permB;
+  int32_t* pin = permA.need((size_t)n);
+  int32_t* pout = permB.need((size_t)n);
+  LF_CUDA(cudaMemcpyAsync(pin, perm_h.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+  DBuf<unsigned char> flags;
+  flags.need((size_t)n);
+  DBuf<IsaxJob> d_jobs;
+  DBuf<int32_t> d_ones, d_bleft;
+  DBuf<RouteJob> d_rjobs;
+  DBuf<IsaxRoute> d_how;
+  DBuf<RouteBlock> d_rblocks;
+  DBuf<int64_t> d_lbase, d_rbase;
+  while (!frontier.empty()) {
+    std::vector<Open> split;
+    for (const Open& o : frontier) (o.cnt > cap ? split : leaves).push_back(o);
+    std::vector<Open> next;
+    if (!split.empty()) {
+      // decisions on the first cap + 1 members (the insertion that overflows the leaf)
+      std::vector<IsaxJob> jobs(split.size());
+      for (size_t i = 0; i < split.size(); ++i) {
+        jobs[i].off = split[i].off;
+        jobs[i].j = (int)(cap + 1);
+        for (int q = 0; q < w; ++q) jobs[i].bits[q] = nodes[split[i].node].bits[q];
+      }
+      d_jobs.upload(jobs, s);
+      d_ones.need(split.size() * w);
+      isax_count_kernel<<<(unsigned)split.size(), kBuildThreads, 0, s>>>(full.p, w, card_bits, pin,
+                                                                         d_jobs.p, d_ones.p);
+      LF_CHECK_LAUNCH();
+      std::vector<int32_t> ones(split.size() * w);
+      LF_CUDA(cudaMemcpyAsync(ones.data(), d_ones.p, sizeof(int32_t) * ones.size(),
+                              cudaMemcpyDeviceToHost, s));
+      LF_CUDA(cudaStreamSynchronize(s));
+      std::vector<RouteJob> rj;
+      std::vector<IsaxRoute> how;
+      std::vector<int> of;
+      for (size_t i = 0; i < split.size(); ++i) {
+        const IsaxNode& nd = nodes[split[i].node];
+        const int64_t total = cap + 1;
+        int pick = -1, first = -1;
+        int64_t pick_bal = 0;
+        for (int q = 0; q < w; ++q) {
+          if (nd.bits[q] >= card_bits) continue;
+          if (first < 0) first = q;
+          const int64_t o1 = ones[i * w + q], z = total - o1;
+          if (o1 == 0 || z == 0) continue;
+          const int64_t bal = o1 > z ? o1 - z : z - o1;
+          if (pick < 0 || bal < pick_bal) {
+            pick = q;
+            pick_bal = bal;
+          }
+        }
+        if (pick < 0) pick = first;
+        if (pick < 0) {  // every segment at full cardinality: the leaf stays over capacity
+          leaves.push_back(split[i]);
+          continue;
+        }
+        RouteJob J{};
+        J.off = split[i].off;
+        J.cnt = split[i].cnt;
+        rj.push_back(J);
+        how.push_back({pick, nd.bits[pick]});
+        of.push_back((int)i);
+      }
+      if (!rj.empty()) {
+        std::vector<RouteBlock> rb;
+        for (size_t i = 0; i < rj.size(); ++i)
+          for (int64_t st = 0; st < rj[i].cnt; st += kBuildThreads) rb.push_back({(int)i, st});
+        d_rjobs.upload(rj, s);
+        d_how.upload(how, s);
+        d_rblocks.upload(rb, s);
+        d_bleft.need(rb.size());
+        isax_flag_kernel<<<(unsigned)rb.size(), kBuildThreads, 0, s>>>(
+            full.p, w, card_bits, pin, d_rjobs.p, d_how.p, d_rblocks.p, flags.p, d_bleft.p);
+        LF_CHECK_LAUNCH();
+        std::vector<int32_t> bl(rb.size());
+        LF_CUDA(cudaMemcpyAsync(bl.data(), d_bleft.p, sizeof(int32_t) * rb.size(),
+                                cudaMemcpyDeviceToHost, s));
+        LF_CUDA(cudaStreamSynchronize(s));
+        std::vector<int64_t> nl(rj.size(), 0), lb(rb.size()), rbs(rb.size()), accl(rj.size(), 0),
+            accr(rj.size(), 0);
+        for (size_t b = 0; b < rb.size(); ++b) nl[rb[b].job] += bl[b];
+        for (size_t b = 0; b < rb.size(); ++b) {
+          const int jb = rb[b].job;
+          const int64_t live = std::min<int64_t>(kBuildThreads, rj[jb].cnt - rb[b].start);
+          lb[b] = accl[jb];
+          rbs[b] = nl[jb] + accr[jb];
+          accl[jb] += bl[b];
+          accr[jb] += live - bl[b];
+        }
+        d_lbase.upload(lb, s);
+        d_rbase.upload(rbs, s);
+        LF_CUDA(cudaMemcpyAsync(pout, pin, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        scatter_kernel<<<(unsigned)rb.size(), kBuildThreads, 0, s>>>(pin, pout, d_rjobs.p, d_rblocks.p,
+                                                                    flags.p, d_lbase.p, d_rbase.p);
+        LF_CHECK_LAUNCH();
+        std::swap(pin, pout);
+        for (size_t k = 0; k < rj.size(); ++k) {
+          const Open& o = split[of[k]];
+          const int at = o.node, pick = how[k].seg;
+          const int li = (int)nodes.size();
+          for (int side = 0; side < 2; ++side) {
+            IsaxNode ch;
+            ch.bits = nodes[at].bits;
+            ch.sym = nodes[at].sym;
+            ch.bits[pick] += 1;
+            ch.sym[pick] = nodes[at].sym[pick] * 2 + side;
+            ch.parent = at;
+            nodes.push_back(std::move(ch));
+          }
+          IsaxNode& nd = nodes[at];
+          nd.leaf = false;
+          nd.split = pick;
+          nd.left = li;
+          nd.right = li + 1;
+          next.push_back({li, o.off, nl[k]});
+          next.push_back({li + 1, o.off + nl[k], o.cnt - nl[k]});
+        }
+      }
+    }
+    frontier.swap(next);
+  }
+  LF_CUDA(cudaMemcpyAsync(perm_h.data(), pin, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaStreamSynchronize(s));
+  for (const Open& o : leaves)
+    nodes[o.node].members.assign(perm_h.begin() + o.off, perm_h.begin() + o.off + o.cnt);
+  return isax_from_nodes(nodes, root_child, n, m, w, card_bits);
 }
 
 void launch_gather_rows(const float* X, int64_t n, int m, const int32_t* order, int mp, float* out,

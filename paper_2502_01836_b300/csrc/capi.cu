@@ -1077,7 +1077,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     ix->wave = p->wave;
     cudaStream_t s = ix->stream;
     float* X = nullptr;
-    if (p->index_type == LEAFI_DSTREE && !p->host_build) {
+    if (!p->host_build) {
       // the tree is built on the device from the series in id order
       DBuf<float> idX;
       const float* dX = series;
@@ -1085,7 +1085,11 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
         idX.upload(series, (size_t)n * m, s);
         dX = idX.p;
       }
-      ix->tree = build_dstree_device(dX, n, m, p->leaf_capacity, p->dstree_init_segments, s);
+      if (p->index_type == LEAFI_DSTREE)
+        ix->tree = build_dstree_device(dX, n, m, p->leaf_capacity, p->dstree_init_segments, s);
+      else
+        ix->tree = build_isax_device(dX, n, m, p->leaf_capacity, p->isax_segments,
+                                     p->isax_card_bits, s);
       HostTree& t = ix->tree;
       // leaf-major, 16-byte aligned rows of mp floats, gathered on the device
       ix->ids.upload(t.order, s);

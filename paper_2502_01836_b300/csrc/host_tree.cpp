@@ -333,13 +333,6 @@ std::vector<double> sax_breakpoints(int bits) {
   return beta;
 }
 
-struct IsaxNode {
-  std::vector<int> bits, sym;
-  bool leaf = true;
-  int parent = -1, left = -1, right = -1;
-  int split = -1;
-  std::vector<int32_t> members;
-};
 
 class IsaxBuilder {
  public:
@@ -406,6 +399,8 @@ class IsaxBuilder {
 };
 
 }  // namespace
+
+std::vector<double> isax_breakpoints(int bits) { return sax_breakpoints(bits); }
 
 HostTree dstree_from_nodes(std::vector<DsNode>& nodes, int64_t n, int m) {
   HostTree t;
@@ -479,51 +474,9 @@ HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_s
   return dstree_from_nodes(b.nodes(), n, m);
 }
 
-HostTree build_isax(const float* X, int64_t n, int m, int leaf_cap, int w, int card_bits) {
+HostTree isax_from_nodes(std::vector<IsaxNode>& nodes, const std::vector<int>& root_child,
+                         int64_t n, int m, int w, int card_bits) {
   const std::vector<double> beta = sax_breakpoints(card_bits);
-  const int C = 1 << card_bits;
-  const int l = m / w;
-  std::vector<uint16_t> full(static_cast<size_t>(n) * w);
-#pragma omp parallel
-  {
-    std::vector<double> p(2 * (m + 1));
-#pragma omp for schedule(static)
-    for (long long id = 0; id < n; ++id) {
-      prefix_sums(X + id * m, m, p.data(), p.data() + m + 1);
-      for (int j = 0; j < w; ++j) {
-        const double paa = (p[(j + 1) * l] - p[j * l]) / static_cast<double>(l);
-        // number of breakpoints beta_1..beta_{C-1} that are <= paa
-        const int sym = static_cast<int>(std::upper_bound(beta.begin() + 1, beta.begin() + C, paa) -
-                                         (beta.begin() + 1));
-        full[static_cast<size_t>(id) * w + j] = static_cast<uint16_t>(sym);
-      }
-    }
-  }
-  IsaxBuilder b(w, card_bits, leaf_cap, full);
-  std::vector<int> root_child(static_cast<size_t>(1) << w, -1);
-  std::vector<IsaxNode>& nodes = b.nodes();
-  for (int64_t id = 0; id < n; ++id) {
-    const uint16_t* fs = &full[static_cast<size_t>(id) * w];
-    int key = 0;
-    for (int j = 0; j < w; ++j) key = (key << 1) | (fs[j] >> (card_bits - 1));
-    int at = root_child[key];
-    if (at < 0) {
-      IsaxNode nd;
-      nd.bits.assign(w, 1);
-      nd.sym.resize(w);
-      for (int j = 0; j < w; ++j) nd.sym[j] = fs[j] >> (card_bits - 1);
-      at = static_cast<int>(nodes.size());
-      nodes.push_back(std::move(nd));
-      root_child[key] = at;
-    }
-    while (!nodes[at].leaf)
-      at = b.next_bit(static_cast<int32_t>(id), nodes[at].split, nodes[at].bits[nodes[at].split])
-               ? nodes[at].right
-               : nodes[at].left;
-    nodes[at].members.push_back(static_cast<int32_t>(id));
-    if (static_cast<int64_t>(nodes[at].members.size()) > leaf_cap) b.split(at);
-  }
-
   HostTree t;
   t.type = LEAFI_ISAX;
   t.m = m;
@@ -582,6 +535,54 @@ HostTree build_isax(const float* X, int64_t n, int m, int leaf_cap, int w, int c
   }
   build_paths(t);
   return t;
+}
+
+HostTree build_isax(const float* X, int64_t n, int m, int leaf_cap, int w, int card_bits) {
+  const std::vector<double> beta = sax_breakpoints(card_bits);
+  const int C = 1 << card_bits;
+  const int l = m / w;
+  std::vector<uint16_t> full(static_cast<size_t>(n) * w);
+#pragma omp parallel
+  {
+    std::vector<double> p(2 * (m + 1));
+#pragma omp for schedule(static)
+    for (long long id = 0; id < n; ++id) {
+      prefix_sums(X + id * m, m, p.data(), p.data() + m + 1);
+      for (int j = 0; j < w; ++j) {
+        const double paa = (p[(j + 1) * l] - p[j * l]) / static_cast<double>(l);
+        // number of breakpoints beta_1..beta_{C-1} that are <= paa
+        const int sym = static_cast<int>(std::upper_bound(beta.begin() + 1, beta.begin() + C, paa) -
+                                         (beta.begin() + 1));
+        full[static_cast<size_t>(id) * w + j] = static_cast<uint16_t>(sym);
+      }
+    }
+  }
+  IsaxBuilder b(w, card_bits, leaf_cap, full);
+  std::vector<int> root_child(static_cast<size_t>(1) << w, -1);
+  std::vector<IsaxNode>& nodes = b.nodes();
+  for (int64_t id = 0; id < n; ++id) {
+    const uint16_t* fs = &full[static_cast<size_t>(id) * w];
+    int key = 0;
+    for (int j = 0; j < w; ++j) key = (key << 1) | (fs[j] >> (card_bits - 1));
+    int at = root_child[key];
+    if (at < 0) {
+      IsaxNode nd;
+      nd.bits.assign(w, 1);
+      nd.sym.resize(w);
+      for (int j = 0; j < w; ++j) nd.sym[j] = fs[j] >> (card_bits - 1);
+      at = static_cast<int>(nodes.size());
+      nodes.push_back(std::move(nd));
+      root_child[key] = at;
+    }
+    while (!nodes[at].leaf)
+      at = b.next_bit(static_cast<int32_t>(id), nodes[at].split, nodes[at].bits[nodes[at].split])
+               ? nodes[at].right
+               : nodes[at].left;
+    nodes[at].members.push_back(static_cast<int32_t>(id));
+    if (static_cast<int64_t>(nodes[at].members.size()) > leaf_cap) b.split(at);
+  }
+
+  return isax_from_nodes(nodes, root_child, n, m, w, card_bits);
 }
 
 }  // namespace leafi

@@ -79,6 +79,21 @@ struct DsNode {
 // Flat tables of a DSTree from its nodes (node 0 is the root).
 HostTree dstree_from_nodes(std::vector<DsNode>& nodes, int64_t n, int m);
 
+// iSAX node as the builders produce it; root children are listed by root key.
+struct IsaxNode {
+  std::vector<int> bits, sym;  // per segment: cardinality bits and symbol at that cardinality
+  bool leaf = true;
+  int parent = -1, left = -1, right = -1;
+  int split = -1;  // refined segment of an internal node
+  std::vector<int32_t> members;  // leaves: ascending ids
+};
+
+// Flat tables of an iSAX tree; root_child[key] = node or -1 (2^w keys).
+HostTree isax_from_nodes(std::vector<IsaxNode>& nodes, const std::vector<int>& root_child,
+                         int64_t n, int m, int w, int card_bits);
+// N(0,1) breakpoints: 2^bits + 1 entries, -inf, beta_1 .. beta_{2^bits - 1}, +inf
+std::vector<double> isax_breakpoints(int bits);
+
 // Deterministic builds; both follow the readings documented with the oracle
 // and produce identical trees for identical inputs.
 HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_segments);
@@ -88,6 +103,11 @@ HostTree build_dstree(const float* X, int64_t n, int m, int leaf_cap, int init_s
 // insertion would decide it (see build_device.cu).  `stream` is a cudaStream_t.
 HostTree build_dstree_device(const float* dX, int64_t n, int m, int leaf_cap, int init_segments,
                              void* stream);
+// The same iSAX tree from the series on the device: symbols on the GPU, then
+// the nodes level by level (a split is decided on the node's first cap + 1
+// members in id order, as insertion decides it).
+HostTree build_isax_device(const float* dX, int64_t n, int m, int leaf_cap, int w, int card_bits,
+                           void* stream);
 HostTree build_isax(const float* X, int64_t n, int m, int leaf_cap, int w, int card_bits);
 
 }  // namespace leafi

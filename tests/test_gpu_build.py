@@ -1,6 +1,7 @@
-"""DSTree built on the GPU (level by level) vs the sequential host build and
+"""Trees built on the GPU (level by level) vs the sequential host build and
 the oracle's tree: identical leaves, identical node ranges (the leaf lower
 bounds of the same queries agree bit for bit) and identical search results.
+DSTree and iSAX.
 
 Cases: random walks with several leaf capacities and root segmentations (odd
 lengths, segments of one point), embedding-like data, data whose first
@@ -99,3 +100,39 @@ def test_device_build_from_device_pointer():
     finally:
         lf.leafi_free(a)
         lf.leafi_free(b)
+
+
+def _same_isax(X, cap, w, bits, Q):
+    kw = dict(index_type=lf.ISAX, leaf_capacity=cap, isax_segments=w, isax_card_bits=bits, wave=8,
+              device=0)
+    dev = lf.leafi_build(X, lf.BuildParams(host_build=0, **kw))
+    host = lf.leafi_build(X, lf.BuildParams(host_build=1, **kw))
+    try:
+        t = O.Tree(X, "isax", leaf_cap=cap, isax_w=w, isax_bits=bits)
+        assert np.array_equal(lf.leafi_leaf_of(dev), t.leaf_of())
+        assert np.array_equal(lf.leafi_leaf_of(dev), lf.leafi_leaf_of(host))
+        assert lf.leafi_get_info(dev).n_nodes == lf.leafi_get_info(host).n_nodes
+        L = lf.leafi_get_info(dev).n_leaves
+        lb_d = np.zeros((len(Q), L), np.float64)
+        lb_h = np.zeros((len(Q), L), np.float64)
+        lf.leafi_leaf_lower_bounds(dev, Q, lb_d)
+        lf.leafi_leaf_lower_bounds(host, Q, lb_h)
+        assert np.array_equal(lb_d, lb_h)
+        k = 3
+        ids = np.zeros((len(Q), k), np.int64)
+        d = np.zeros((len(Q), k), np.float32)
+        lf.leafi_exact_search(dev, Q, k, ids, d)
+        bf_ids, bf_d2 = O.knn(X, Q, k)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+    finally:
+        lf.leafi_free(dev)
+        lf.leafi_free(host)
+
+
+@pytest.mark.parametrize("n,m,cap,w,bits", [(60000, 256, 500, 16, 8), (20000, 64, 50, 8, 4),
+                                            (5000, 96, 20, 4, 2)])
+def test_device_build_isax(n, m, cap, w, bits):
+    """Includes saturated segments (2-bit cardinality: leaves that cannot split
+    further stay over capacity) and one-sided refinements."""
+    X = fx.random_walk(n, m, seed=420 + w)
+    _same_isax(X, cap, w, bits, fx.test_queries(X, 30, seed=421))
