@@ -657,7 +657,10 @@ void Pipeline::make_sa(const LaneView& v, int nb, bool use_f) {
 void Pipeline::select(const LaneView& v) {
   LF_CUDA(cudaMemsetAsync(v.np, 0, sizeof(int32_t), s));
   ix->tick(5);
-  launch_select_walk(sa, v.ord, v.cursor, s);
+  if (W >= L)
+    launch_select_all(sa, s);
+  else
+    launch_select_walk(sa, v.ord, v.cursor, s);
   ix->tock();
 }
 
@@ -681,7 +684,7 @@ void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
     launch_jpos(nb, v.dK, v.dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, v.jpos, s);
   }
   LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
-  launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);
+  if (W < L) launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);  // a wave of W >= L needs no order
   LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
   search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.topk_cnt, v.thr, v.cand_cnt, v.done);
   LF_CHECK_LAUNCH();

@@ -254,6 +254,8 @@ struct KernelClock {
 // wave selection (Alg. 2 lines 3-7) walking a precomputed visiting order
 // (`ord` [nq][L] ascending (LB^2, leaf id), cursor = next position per query)
 void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s);
+// the same picks for a wave at least as wide as the index (a.W >= a.L): no order needed
+void launch_select_all(const SelectArgs& a, cudaStream_t s);
 void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
                         const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
                         unsigned long long* stat, cudaStream_t s);

@@ -563,6 +563,42 @@ __global__ void __launch_bounds__(kSelThreads) select_walk_kernel(SelectArgs a,
   }
 }
 
+// A wave at least as wide as the index (W >= L) takes every leaf that the
+// walk of the visiting order would reach: the order ascends in LB^2 and the
+// walk stops at the first bound-pruned leaf, so its picks are exactly the
+// leaves that are not searched, not bound-pruned and not filter-pruned - a
+// set that needs no order.  One thread per (query, leaf); the caller marks
+// the queries done afterwards (no second wave can pick anything).
+__global__ void select_all_kernel(SelectArgs a) {
+  const int q = blockIdx.y;
+  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= a.L || a.done[q]) return;
+  unsigned char* sc = a.scanned + (size_t)q * a.L;
+  if (sc[leaf]) return;
+  const u64 thr = a.thr[q];
+  const float bsf2 = (thr == kNoKey) ? __int_as_float(0x7f800000) : key_d2(thr);
+  if (__dmul_rn(a.lb2[(size_t)q * a.L + leaf], kDeflate) > (double)bsf2) return;
+  if (a.P != nullptr && a.jpos != nullptr && a.jpos[q] >= 0) {
+    const int f = a.leaf_filter[leaf];
+    if (f >= 0) {
+      const double bsf = (double)__fsqrt_rn(bsf2);
+      const double df =
+          __dsub_rn((double)a.P[(size_t)q * a.F + f], a.alpha[(size_t)f * a.nc + a.jpos[q]]);
+      if (df > bsf) return;
+    }
+  }
+  sc[leaf] = 1;
+  const int idx = atomicAdd(a.npairs, 1);
+  a.pairs[idx] = Pair{q, q, leaf, 0};
+  atomicAdd(&a.stat[0], 1ull);
+  atomicAdd(&a.stat[1], (u64)(a.leaf_off[leaf + 1] - a.leaf_off[leaf]));
+}
+
+__global__ void done_all_kernel(int nq, int32_t* __restrict__ done) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nq) done[q] = 1;
+}
+
 __global__ void route_pairs_kernel(int nq, const int32_t* __restrict__ route, int L,
                                    unsigned char* __restrict__ scanned,
                                    const int64_t* __restrict__ leaf_off, Pair* __restrict__ pairs,
@@ -714,6 +750,14 @@ void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long 
   LF_CHECK_LAUNCH();
 }
 
+
+void launch_select_all(const SelectArgs& a, cudaStream_t s) {
+  if (a.nq <= 0 || a.L <= 0) return;
+  select_all_kernel<<<dim3(nblk(a.L, 256), a.nq), 256, 0, s>>>(a);
+  LF_CHECK_LAUNCH();
+  done_all_kernel<<<nblk(a.nq, 256), 256, 0, s>>>(a.nq, a.done);
+  LF_CHECK_LAUNCH();
+}
 
 void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s) {
   if (a.nq <= 0) return;

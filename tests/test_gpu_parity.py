@@ -412,6 +412,16 @@ def test_wave_wider_than_the_index():
         assert np.abs(alpha - o_alpha).max() <= 1e-5 * _pred_scale(Wt, Qc).max()
         diff = np.abs(qp[0] - o_qp)
         assert (diff == 0).mean() >= 0.9 and diff.max() <= 3.0 / 100
+        # LeaFi mode with the GPU's tables: the one wide wave after the route leaf
+        for target in (0.9, 0.95):
+            ids1 = np.zeros((300, 1), np.int64)
+            d1 = np.zeros((300, 1), np.float32)
+            lf.leafi_search(idx, Q, 1, target, ids1, d1)
+            j = O.offset_position(qp[0], target)
+            o_ids1, o_d2, _, margin = O.leafi_search(t, Wt, fl, alpha, Q, 1, j, wave)
+            same = (ids1 == o_ids1).all(1)
+            assert (same | (margin <= 2e-5 * _pred_scale(Wt, Q).max())).all()
+            assert same.mean() >= 0.95
     finally:
         lf.leafi_free(idx)
 
