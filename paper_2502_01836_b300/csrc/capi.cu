@@ -288,13 +288,16 @@ void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_
 
 // One scan round: group pairs by leaf, scan, merge candidates into slots.
 // query tiles of the tensor-core scan for top-k lists of k keys (0: CUDA-core scan)
-int tc_nbuf(leafi_index* ix, int k) {
+int tc_nbuf(leafi_index* ix, int k, int* qkeys = nullptr) {
   if (!ix->tc_ok || ix->scan_path != 0) return 0;
   auto it = ix->tc_plan.find(k);
-  if (it != ix->tc_plan.end()) return it->second;
-  const int nb = tc_scan_plan(ix->kp, k, ix->smem_optin, nullptr);
-  ix->tc_plan[k] = nb;
-  return nb;
+  if (it == ix->tc_plan.end()) {
+    int qk = 0;
+    const int nb = tc_scan_plan(ix->kp, k, ix->smem_optin, nullptr, &qk);
+    it = ix->tc_plan.emplace(k, std::make_pair(nb, qk)).first;
+  }
+  if (qkeys) *qkeys = it->second.second;
+  return it->second.first;
 }
 
 // float16 rows and band constants of nq queries for the tensor-core scan
@@ -327,13 +330,24 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
   int32_t* ioff = ix->sc->sItemOff.need(L + 1);
   Pair* grouped = ix->sc->sGrouped.need(std::max(npairs_max, 1));
   int32_t* nitems = ix->sc->sNItems.need(1);
-  const int nbuf = tq.Qh ? tc_nbuf(ix, kstride) : 0;
+  int qkeys = 0;
+  const int nbuf = tq.Qh ? tc_nbuf(ix, kstride, &qkeys) : 0;
   const bool use_tc = nbuf > 0;
+  const bool var_groups = use_tc && kstride > 1;  // groups bounded by the sum of their k
   int32_t* item_leaf =
       use_tc ? ix->sc->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix->tree)) : nullptr;
   launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
                use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped, nitems,
-               distinct_stat, s, item_leaf, use_tc && ix->pack_small);
+               distinct_stat, s, var_groups ? nullptr : item_leaf,
+               use_tc && !var_groups && ix->pack_small);
+  int32_t *gfirst = nullptr, *gbound = nullptr;
+  if (var_groups) {
+    int32_t* ngr = ix->sc->sNGroups.need(L);
+    gfirst = ix->sc->sGFirst.need(L + 1);
+    gbound = ix->sc->sGBound.need((size_t)std::max(npairs_max, 1) + 1);
+    launch_var_groups(L, ix->leaf_off.p, kPart, goff, grouped, slot_k, kstride, qkeys, ngr, gfirst,
+                      gbound, ioff, item_leaf, nitems, s);
+  }
   const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
   if (use_tc) {
     TcScanArgs t;
@@ -356,6 +370,9 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.grp_off = goff;
     t.item_off = ioff;
     t.item_leaf = item_leaf;
+    t.gfirst = gfirst;
+    t.gbound = gbound;
+    t.qkeys = qkeys;
     t.work = ix->sc->sWork.need(1);
     LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
     t.topk = topk;
@@ -610,6 +627,11 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
       S.sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(t));
       S.sWork.need(1);
       S.sGlock.need(qb);
+      if (kmax > 1) {
+        S.sNGroups.need(L);
+        S.sGFirst.need(L + 1);
+        S.sGBound.need((size_t)qb * std::max(W, 1) + 1);
+      }
     }
     S.sCnt.need(L);
     S.sGrpOff.need(L + 1);

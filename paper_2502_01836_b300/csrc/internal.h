@@ -166,11 +166,14 @@ struct TcScanArgs {
   const __half* Qh;                // [nq][kp] float16 queries (launch_tc_query_prep)
   const float4* Qk;                // [nq][2] band constants (launch_tc_query_prep)
   int nbuf;                        // query tiles in shared memory (tc_scan_plan)
-  int G;                           // queries per work item (tc_group_size)
+  int G;                           // queries per work item of the fixed grouping (tc_group_size)
   const Pair* pairs;
   const int32_t* grp_off;
   const int32_t* item_off;
   const int32_t* item_leaf;        // leaf of every work item
+  const int32_t* gfirst;           // k > 1: first query group of each leaf (launch_var_groups),
+  const int32_t* gbound;           //   group starts in `pairs`; null: groups of G queries
+  int qkeys;                       // k > 1: keys per TMEM lane quarter's lists (tc_scan_plan)
   int32_t* work;                   // work-item counter (zero at launch)
   unsigned long long* topk;        // [nslots][k] ascending keys, kNoKey padded
                                    // (launch_tc_round_prep); work items merge into it
@@ -181,8 +184,9 @@ struct TcScanArgs {
 };
 int tc_group_size(int k);
 // query tiles (2 or 1) the tensor-core scan can keep for rows of kp halves and
-// top-k lists of k keys within `smem_optin` bytes; 0 if it does not fit
-int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem);
+// top-k lists of k keys within `smem_optin` bytes (0 if it does not fit);
+// qkeys: for k > 1 the keys of each lane quarter's lists (a group's sum of k)
+int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem, int* qkeys);
 // out[p][i] = X[order[p]][i] for i < m, 0 for m <= i < mp (leaf-major rows)
 void launch_gather_rows(const float* X, int64_t n, int m, const int32_t* order, int mp, float* out,
                         cudaStream_t s);
@@ -201,6 +205,14 @@ void launch_tc_round_finish(int nslots, int kstride, const int32_t* slot_k,
 void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* slot_k, int grid,
                  cudaStream_t s);
 
+// k > 1 on the tensor-core scan: each leaf's grouped pairs cut into groups of
+// at most 64 queries whose k sum to at most `budget`; gfirst [L + 1] = first
+// group of each leaf, gbound [groups + 1] = group starts in the grouped pairs,
+// item_off [L + 1] / item_leaf / n_items for the (part, group) work items
+void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* grp_off,
+                       const Pair* grouped, const int32_t* slot_k, int kstride, int budget,
+                       int32_t* ngroups, int32_t* gfirst, int32_t* gbound, int32_t* item_off,
+                       int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s);
 // stat (nullable): stat[0] += series of the distinct leaves in this round;
 // g = queries per work item of the scan kernel that follows
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
@@ -318,6 +330,7 @@ struct Scratch {
   DBuf<Pair> sPairs, sGrouped;
   DBuf<unsigned long long> sTopk, sThr, sCand;
   DBuf<int32_t> sGlock;           // per slot locks of the tensor-core scan's top-k lists
+  DBuf<int32_t> sNGroups, sGFirst, sGBound;  // k > 1: query groups sized by k (launch_var_groups)
   DBuf<float> sPred, sOutD;
   DBuf<int64_t> sOutI;
   // search lane
@@ -379,7 +392,8 @@ struct leafi_index {
   leafi::DBuf<float> Ws;         // tf32 hi/lo weight planes of the tensor-core filter forward
   CUtensorMap wmap;              // TMA descriptor of Ws
   bool ws_dirty = true;          // weights changed since Ws was built
-  std::map<int, int> tc_plan;    // k -> query tiles of the tensor-core scan (0: does not fit)
+  std::map<int, std::pair<int, int>> tc_plan;  // k -> (query tiles of the tensor-core scan (0: does
+                                               // not fit), keys per lane quarter's lists)
 
   int profiling = 0;       // 0 off, 1 leaf-scan kernel times, 2 every kind + scan phases
   bool ticked = false;     // the last tick() recorded a start event

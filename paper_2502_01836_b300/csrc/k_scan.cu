@@ -395,6 +395,103 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
   }
 }
 
+// ------------------------------------------------ query groups sized by k
+// For k > 1 the tensor-core scan keeps one top-k list per query and lane
+// quarter in shared memory, so a work item's group of queries is bounded by
+// the sum of their k (`budget` keys) as well as by 64 (the MMA's N).  Each
+// leaf's pairs are cut greedily, in their grouped order, into such groups;
+// the items of a leaf are (part, group) as before.
+__device__ __forceinline__ int pair_k(const Pair& p, const int32_t* slot_k, int kstride) {
+  return slot_k ? slot_k[p.slot] : kstride;
+}
+
+__global__ void vgroup_count_kernel(int L, const int32_t* __restrict__ grp_off,
+                                    const Pair* __restrict__ grouped,
+                                    const int32_t* __restrict__ slot_k, int kstride, int budget,
+                                    int32_t* __restrict__ ngroups) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  int n = 0, sum = 0, g = 0;
+  for (int p = grp_off[l]; p < grp_off[l + 1]; ++p) {
+    const int k = pair_k(grouped[p], slot_k, kstride);
+    if (n == 64 || sum + k > budget) {
+      ++g;
+      n = 0;
+      sum = 0;
+    }
+    ++n;
+    sum += k;
+  }
+  ngroups[l] = g + (n > 0 ? 1 : 0);
+}
+
+// exclusive scans of per-leaf group counts and work-item counts (one block)
+__global__ void vgroup_offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part,
+                                      const int32_t* __restrict__ ngroups,
+                                      int32_t* __restrict__ gfirst, int32_t* __restrict__ item_off,
+                                      int32_t* __restrict__ n_items) {
+  __shared__ int s_a[1024], s_b[1024];
+  const int T = blockDim.x;
+  const int per = (L + T - 1) / T;
+  const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
+  int sa = 0, sb = 0;
+  for (int l = l0; l < l1; ++l) {
+    const int64_t size = leaf_off[l + 1] - leaf_off[l];
+    sa += ngroups[l];
+    sb += ngroups[l] * (int)((size + part - 1) / part);
+  }
+  s_a[threadIdx.x] = sa;
+  s_b[threadIdx.x] = sb;
+  __syncthreads();
+  for (int off = 1; off < T; off <<= 1) {
+    const int va = threadIdx.x >= off ? s_a[threadIdx.x - off] : 0;
+    const int vb = threadIdx.x >= off ? s_b[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_a[threadIdx.x] += va;
+    s_b[threadIdx.x] += vb;
+    __syncthreads();
+  }
+  int ra = s_a[threadIdx.x] - sa, rb = s_b[threadIdx.x] - sb;
+  for (int l = l0; l < l1; ++l) {
+    const int64_t size = leaf_off[l + 1] - leaf_off[l];
+    gfirst[l] = ra;
+    item_off[l] = rb;
+    ra += ngroups[l];
+    rb += ngroups[l] * (int)((size + part - 1) / part);
+  }
+  if (threadIdx.x == T - 1) {
+    gfirst[L] = s_a[T - 1];
+    item_off[L] = s_b[T - 1];
+    *n_items = s_b[T - 1];
+  }
+}
+
+// group starts (gbound[gfirst[l] + g], with gbound[gfirst[L]] = all pairs)
+// and the item -> leaf table
+__global__ void vgroup_fill_kernel(int L, const int64_t* __restrict__ leaf_off, int part,
+                                   const int32_t* __restrict__ grp_off,
+                                   const Pair* __restrict__ grouped,
+                                   const int32_t* __restrict__ slot_k, int kstride, int budget,
+                                   const int32_t* __restrict__ gfirst,
+                                   const int32_t* __restrict__ item_off,
+                                   int32_t* __restrict__ gbound, int32_t* __restrict__ item_leaf) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l == 0) gbound[gfirst[L]] = grp_off[L];
+  if (l >= L) return;
+  int n = 0, sum = 0, g = gfirst[l];
+  for (int p = grp_off[l]; p < grp_off[l + 1]; ++p) {
+    const int k = pair_k(grouped[p], slot_k, kstride);
+    if (n == 0 || n == 64 || sum + k > budget) {
+      gbound[g++] = p;
+      n = 0;
+      sum = 0;
+    }
+    ++n;
+    sum += k;
+  }
+  for (int i = item_off[l]; i < item_off[l + 1]; ++i) item_leaf[i] = l;
+}
+
 __global__ void scatter_kernel(const Pair* __restrict__ pairs, const int32_t* __restrict__ npairs,
                                const int32_t* __restrict__ grp_off, int32_t* __restrict__ fill,
                                Pair* __restrict__ grouped) {
@@ -738,6 +835,22 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
     scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
     LF_CHECK_LAUNCH();
   }
+}
+
+void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* grp_off,
+                       const Pair* grouped, const int32_t* slot_k, int kstride, int budget,
+                       int32_t* ngroups, int32_t* gfirst, int32_t* gbound, int32_t* item_off,
+                       int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s) {
+  if (L <= 0) return;
+  vgroup_count_kernel<<<nblk(L, 256), 256, 0, s>>>(L, grp_off, grouped, slot_k, kstride, budget,
+                                                   ngroups);
+  LF_CHECK_LAUNCH();
+  vgroup_offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, ngroups, gfirst, item_off, n_items_dev);
+  LF_CHECK_LAUNCH();
+  vgroup_fill_kernel<<<nblk(L, 256), 256, 0, s>>>(L, leaf_off, part, grp_off, grouped, slot_k,
+                                                  kstride, budget, gfirst, item_off, gbound,
+                                                  item_leaf);
+  LF_CHECK_LAUNCH();
 }
 
 void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,

@@ -39,6 +39,7 @@
 // belongs to exactly one item, so a series of the final top-k has a smaller
 // key than the k-th key of any list that does not contain it and is never
 // dropped; the final lists do not depend on the order of items.
+#include <algorithm>
 #include <cfloat>
 
 #include "device_util.cuh"
@@ -83,6 +84,7 @@ struct TcShared {
   float qm[kTcG];      // |q|
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
   int cnt4[4][kTcG];   // k > 1: entries of each TMEM lane quarter's list per query
+  int loff[kTcG];      // k > 1: offset of each query's list in a quarter's lists (sum of earlier k)
   float Tq[kTcG];      // k > 1: admission bound (thrd, any full quarter list's k-th, refreshed threshold)
   int rs[kTcG], re[kTcG];  // packed item: the chunk rows of each pair's own leaf
   int ncb;             // buffered candidates of the current item
@@ -127,16 +129,27 @@ __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
     return it;
   }
   const int leaf = lf;
-  const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
-  const int G = a.G;
-  const int ngroups = (cnt + G - 1) / G;
   const int local = item - a.item_off[leaf];
-  const int part = local / ngroups, grp = local % ngroups;
+  int part;
+  if (a.gbound) {
+    // groups bounded by the sum of their queries' k (launch_var_groups)
+    const int gf = a.gfirst[leaf], ng = a.gfirst[leaf + 1] - gf;
+    part = local / ng;
+    const int grp = gf + local % ng;
+    it.nqg = a.gbound[grp + 1] - a.gbound[grp];
+    it.pr = a.pairs + a.gbound[grp];
+  } else {
+    const int cnt = a.grp_off[leaf + 1] - a.grp_off[leaf];
+    const int G = a.G;
+    const int ngroups = (cnt + G - 1) / G;
+    part = local / ngroups;
+    const int grp = local % ngroups;
+    it.nqg = min(G, cnt - grp * G);
+    it.pr = a.pairs + a.grp_off[leaf] + grp * G;
+  }
   it.p0 = a.leaf_off[leaf] + (int64_t)part * a.part;
   it.p1 = min(it.p0 + (int64_t)a.part, a.leaf_off[leaf + 1]);
-  it.nqg = min(G, cnt - grp * G);
   it.N = ((it.nqg + 15) / 16) * 16;
-  it.pr = a.pairs + a.grp_off[leaf] + grp * G;
   it.nchunks = (int)((it.p1 - it.p0 + kTcRows - 1) / kTcRows);
   it.packed = false;
   return it;
@@ -446,7 +459,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   unsigned char* A1 = smem + tileA;
   unsigned char* B0 = smem + 2 * tileA;      // G x Kp fp16, no swizzle
   unsigned char* B1 = B0 + (nbuf - 1) * tileB;
-  u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);  // [G][a.k] (x4 quarters if k > 1)
+  // k = 1: [G] best keys; k > 1: four quarters of a.qkeys keys, query j's list at S.loff[j]
+  u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);
   int* cb_pos = reinterpret_cast<int*>(lists + G * a.k);
   int* cb_j = cb_pos + kCandCap;
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
@@ -713,6 +727,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         }
       }
       epi_sync();
+      if (!split && warp == 0) {
+        // list offsets: exclusive prefix of the group's k (64 queries, two per lane)
+        int k0 = lane < nqg ? S.kq[lane] : 0, k1 = lane + 32 < nqg ? S.kq[lane + 32] : 0;
+        int s0 = k0, s1 = k1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u0 = __shfl_up_sync(0xffffffffu, s0, o), u1 = __shfl_up_sync(0xffffffffu, s1, o);
+          if (lane >= o) {
+            s0 += u0;
+            s1 += u1;
+          }
+        }
+        const int tot0 = __shfl_sync(0xffffffffu, s0, 31);
+        S.loff[lane] = s0 - k0;
+        S.loff[lane + 32] = tot0 + s1 - k1;
+      }
+      if (!split) epi_sync();
       PROF_ADD(0);
 
       for (int c = 0; c < I.nchunks; ++c, ++g) {
@@ -836,7 +867,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           // are tested at once, re-checks run at once (one candidate per lane),
           // and the quarter lists merge at the item's end.
           const int qd = warp & 3;
-          u64* ql = lists + (size_t)qd * G * a.k;  // this quarter's lists [G][k]
+          u64* ql = lists + (size_t)qd * a.qkeys;  // this quarter's lists
           const float xnorm = sqrtf(xn);
           const float vlo = xn * (1.0f - 1e-4f);
           const bool refresh = (c & 1) == 1;
@@ -887,7 +918,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                 key = dev::make_key(e, (uint32_t)a.ids[pos]);
               }
               if (lane == 0) atomicAdd(&S.rechecks, (unsigned long long)__popc(mask));
-              u64* lj = ql + j * a.k;
+              u64* lj = ql + S.loff[j];
               if (__popc(mask) > 3) {
                 cc = warp_merge_keys(lj, cc, kq, key, (cc == kq) ? lj[kq - 1] : S.thr[j], lane);
               } else {
@@ -944,20 +975,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           const int kq = S.kq[q];
           int cc = S.cnt4[0][q];
           for (int qd = 1; qd < 4; ++qd) {
-            const u64* src = lists + ((size_t)qd * G + q) * a.k;
+            const u64* src = lists + (size_t)qd * a.qkeys + S.loff[q];
             const int n = S.cnt4[qd][q];
             for (int e = 0; e < n; ++e) {
               const u64 kk = src[e];
-              const u64 kth = (cc == kq) ? lists[q * a.k + kq - 1] : S.thr[q];
-              if (kk < kth) cc = dev::warp_insert(lists + q * a.k, cc, kq, kk, lane);
+              u64* l0 = lists + S.loff[q];
+              const u64 kth = (cc == kq) ? l0[kq - 1] : S.thr[q];
+              if (kk < kth) cc = dev::warp_insert(l0, cc, kq, kk, lane);
               else break;  // the rest of a sorted list is no better
             }
           }
           // the item's list joins the slot's top-k list, whose k-th key later
           // work items admit against
           if (cc > 0 &&
-              !share_list(a.topk + (size_t)S.slot[q] * a.k, a.glock + S.slot[q], lists + q * a.k, cc,
-                          kq, lists + ((size_t)G + q) * a.k, lane) &&
+              !share_list(a.topk + (size_t)S.slot[q] * a.k, a.glock + S.slot[q], lists + S.loff[q],
+                          cc, kq, lists + a.qkeys + S.loff[q], lane) &&
               lane == 0)
             atomicOr(a.err, 2);
           __syncwarp();
@@ -990,29 +1022,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
 
 }  // namespace
 
-// queries per work item: 64, or 16 when per-quarter top-k lists of 64 queries
-// would not fit in shared memory (large k)
-int tc_group_size(int k) { return k > 32 ? 16 : kTcG; }
-
-static size_t tc_dyn_smem(int kp, int k, int nbuf) {
-  // k = 1: one key per query plus the deferred re-check buffer; k > 1: one
-  // list per query and TMEM lane quarter
-  const size_t G = (size_t)tc_group_size(k);
-  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * G * kp * 2 +
-         (k == 1 ? G * 8 + (size_t)kCandCap * 12 : (size_t)4 * G * k * 8);
+// queries per work item of the fixed grouping (k = 1): 64; for k > 1 the
+// groups are cut by launch_var_groups with at most 64 queries
+int tc_group_size(int k) {
+  (void)k;
+  return kTcG;
 }
 
-int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem) {
+static size_t tc_dyn_smem(int kp, int k, int nbuf, int qkeys) {
+  // k = 1: one key per query plus the deferred re-check buffer; k > 1: four
+  // lane quarters' lists of qkeys keys each
+  const size_t G = (size_t)kTcG;
+  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * G * kp * 2 +
+         (k == 1 ? G * 8 + (size_t)kCandCap * 12 : (size_t)4 * qkeys * 8);
+}
+
+int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem, int* qkeys) {
   cudaFuncAttributes fa;
   LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel));
-  for (int nbuf = 2; nbuf >= 1; --nbuf) {
-    const size_t dyn = tc_dyn_smem(kp, k, nbuf);
-    if (dyn + fa.sharedSizeBytes <= (size_t)smem_optin) {
-      if (smem) *smem = dyn;
-      return nbuf;
+  const size_t avail = (size_t)smem_optin > fa.sharedSizeBytes ? smem_optin - fa.sharedSizeBytes : 0;
+  if (k == 1) {
+    for (int nbuf = 2; nbuf >= 1; --nbuf) {
+      const size_t dyn = tc_dyn_smem(kp, k, nbuf, 0);
+      if (dyn <= avail) {
+        if (smem) *smem = dyn;
+        if (qkeys) *qkeys = 0;
+        return nbuf;
+      }
     }
+    return 0;
   }
-  return 0;
+  // k > 1: lists for 64 queries of the largest k if they fit; otherwise as
+  // many keys as fit (a group then holds fewer queries), preferring two query
+  // tiles unless one tile leaves clearly more room for lists
+  const size_t target = (size_t)kTcG * k;
+  size_t q[3] = {0, 0, 0};
+  for (int nbuf = 1; nbuf <= 2; ++nbuf) {
+    const size_t base = tc_dyn_smem(kp, k, nbuf, 0);
+    if (base < avail) q[nbuf] = std::min(target, (avail - base) / 32 / 8 * 8);
+  }
+  int nbuf = 0;
+  if (q[2] >= (size_t)k && 5 * q[2] >= 4 * q[1]) nbuf = 2;
+  else if (q[1] >= (size_t)k) nbuf = 1;
+  if (nbuf == 0) return 0;
+  if (smem) *smem = tc_dyn_smem(kp, k, nbuf, (int)q[nbuf]);
+  if (qkeys) *qkeys = (int)q[nbuf];
+  return nbuf;
 }
 
 namespace {
@@ -1072,7 +1127,7 @@ void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, fl
 
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s) {
-  const size_t smem = tc_dyn_smem(a.kp, a.k, a.nbuf);
+  const size_t smem = tc_dyn_smem(a.kp, a.k, a.nbuf, a.qkeys);
   LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   tc_scan_kernel<<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
   LF_CHECK_LAUNCH();
