@@ -95,7 +95,7 @@ def parse():
     # leaf in one wave (measured: narrow waves re-read the same leaves for few
     # queries each)
     a.wave = a.wave if a.wave is not None else {"mixed": 65536, "precision": 4096,
-                                                "serving": 4096}.get(a.config, 64)
+                                                "serving": 16384}.get(a.config, 64)
     return a
 
 
