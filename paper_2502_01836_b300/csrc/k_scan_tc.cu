@@ -113,6 +113,7 @@ struct Item {
 
 constexpr int kPackWin = 8;  // leaves per packed window (the grouping pass's windows)
 
+template <bool kVarGroups>
 __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
   const int lf = a.item_leaf[item];
   Item it;
@@ -131,7 +132,7 @@ __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
   const int leaf = lf;
   const int local = item - a.item_off[leaf];
   int part;
-  if (a.gbound) {
+  if (kVarGroups) {
     // groups bounded by the sum of their queries' k (launch_var_groups)
     const int gf = a.gfirst[leaf], ng = a.gfirst[leaf + 1] - gf;
     part = local / ng;
@@ -441,6 +442,10 @@ __global__ void tc_query_prep_kernel(const float* __restrict__ Q, int nq, int mp
   }
 }
 
+// kSplit: k = 1 (one best key per query, fixed groups of 64); otherwise top-k
+// lists per lane quarter and groups sized by k.  Two instantiations, so each
+// path is compiled and scheduled on its own.
+template <bool kSplit>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     const __grid_constant__ CUtensorMap tmap, TcScanArgs a, const int32_t* __restrict__ n_items_dev,
     const int32_t* __restrict__ slot_k) {
@@ -464,7 +469,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   int* cb_pos = reinterpret_cast<int*>(lists + G * a.k);
   int* cb_j = cb_pos + kCandCap;
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
-  const bool split = (a.k == 1);             // k = 1: halves on alternate accumulators, deferred re-checks
+  constexpr bool split = kSplit;             // k = 1: halves on alternate accumulators, deferred re-checks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sbo = 16u * Kp;             // B: bytes between 8-row groups
   const int m4 = a.mp / 4;
@@ -525,7 +530,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       int cur = publish(0);
       for (int n = 0; cur >= 0 && alive && !*abort; ++n) {
         const int nxt = publish(n + 1);
-        const Item I = decode_item(a, cur);
+        const Item I = decode_item<!kSplit>(a, cur);
         for (int c = 0; c < I.nchunks; ++c) {
           const int st = (int)(g_ld & 1);
           if (g_ld >= 2) {
@@ -562,7 +567,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       if (lane == 0) item = ring_take(S, li, abort);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item < 0) break;
-      const Item I = decode_item(a, item);
+      const Item I = decode_item<!kSplit>(a, item);
       const int b = li % nbuf;
       if (li >= nbuf) {
         bool ok = true;
@@ -624,7 +629,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       for (;; ++li) {
         const int item = ring_take(S, li, abort);
         if (item < 0) break;
-        const Item I = decode_item(a, item);
+        const Item I = decode_item<!kSplit>(a, item);
         const int b = li % nbuf;
         bool ok = wait_phase(&S.bready[b], bready_ph[b], abort);
         bready_ph[b] ^= 1u;
@@ -687,7 +692,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       epi_sync();
       const int item = S.eitem;
       if (item < 0) break;
-      const Item I = decode_item(a, item);
+      const Item I = decode_item<!kSplit>(a, item);
       const int nqg = I.nqg, N = I.N;
       if (prof_on) pr[9] += 1;
       // per-query state of the item (padding columns never admit a series)
@@ -1039,7 +1044,8 @@ static size_t tc_dyn_smem(int kp, int k, int nbuf, int qkeys) {
 
 int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem, int* qkeys) {
   cudaFuncAttributes fa;
-  LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel));
+  if (k == 1) LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel<true>));
+  else LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel<false>));
   const size_t avail = (size_t)smem_optin > fa.sharedSizeBytes ? smem_optin - fa.sharedSizeBytes : 0;
   if (k == 1) {
     for (int nbuf = 2; nbuf >= 1; --nbuf) {
@@ -1128,8 +1134,15 @@ void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, fl
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s) {
   const size_t smem = tc_dyn_smem(a.kp, a.k, a.nbuf, a.qkeys);
-  LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tc_scan_kernel<<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
+  if (a.k == 1) {
+    LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    tc_scan_kernel<true><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
+  } else {
+    LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    tc_scan_kernel<false><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
+  }
   LF_CHECK_LAUNCH();
 }
 
