@@ -234,6 +234,7 @@ __device__ __forceinline__ float warp_canonical_d2(const float4* __restrict__ q,
 }
 
 constexpr int kIlp = 4;
+constexpr int kCoopRechecks = 2;  // k > 1: columns with at most this many candidates re-check warp-wide
 
 // Canonical squared distance by one thread (the operations and order of
 // dev::canonical_d2) with the row loads issued eight float4 words at a time,
@@ -918,8 +919,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               const int kq = S.kq[j];
               int cc = S.cnt4[qd][j];
               u64 key = kNoKey;
-              if (cj) {
-                const float e = canonical_d2_ilp(Q4 + (size_t)S.qrow[j] * m4, X4 + (size_t)pos * m4, m4);
+              const float4* qrow4 = Q4 + (size_t)S.qrow[j] * m4;
+              if (__popc(mask) <= kCoopRechecks) {
+                // few candidates: the whole warp loads each row at once (one
+                // memory round trip) and runs the canonical chain on shuffles
+                unsigned mm = mask;
+                while (mm) {
+                  const int src = __ffs(mm) - 1;
+                  mm &= mm - 1;
+                  const int64_t ps = __shfl_sync(0xffffffffu, pos, src);
+                  const float e = warp_canonical_d2(qrow4, X4 + (size_t)ps * m4, m4, lane);
+                  if (lane == src) key = dev::make_key(e, (uint32_t)a.ids[pos]);
+                }
+              } else if (cj) {
+                // many: one row per lane, loads issued kIlp words at a time
+                const float e = canonical_d2_ilp(qrow4, X4 + (size_t)pos * m4, m4);
                 key = dev::make_key(e, (uint32_t)a.ids[pos]);
               }
               if (lane == 0) atomicAdd(&S.rechecks, (unsigned long long)__popc(mask));
