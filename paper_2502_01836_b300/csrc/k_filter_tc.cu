@@ -9,10 +9,10 @@
 // the dropped a_lo b_lo term and the rounding of the low parts are below
 // 2^-21 |a b|, the float32 accumulation is the same order as a CUDA-core dot
 // product.  One CTA per (filter, 128-query tile): the K dimension streams in
-// 32-column slices (one 128-byte swizzled TMA box per operand plane), two
-// stages deep; one thread issues TMA and MMA, the accumulator (128 queries x
-// h hidden units) sits in TMEM and four warps read it back for the ReLU and
-// output layer.
+// 32-column slices (one 128-byte swizzled TMA box per operand plane) through
+// kFStages stages; one thread issues TMA and MMA, the accumulator (128
+// queries x h hidden units) sits in TMEM and four warps read it back for the
+// ReLU and output layer.
 #include <cfloat>
 
 #include "device_util.cuh"
@@ -28,6 +28,9 @@ constexpr int kSlice = 32;           // K columns per stage (128 bytes of float3
 constexpr int kAPlane = kFRows * kSlice * 4;   // 16 KB
 constexpr int kBPlane = 256 * kSlice * 4;      // 32 KB (h <= 256)
 constexpr int kStage = 2 * kAPlane + 2 * kBPlane;
+// one stage of 96 KB per CTA, so two CTAs share an SM (their loads and MMAs
+// overlap each other) and the 2 x F CTAs of a 256-query batch run in one wave
+constexpr int kFStages = 1;
 constexpr long long kFWait = 1ll << 26;
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -77,13 +80,13 @@ __global__ void wsplit_kernel(const float* __restrict__ W1t, int F, int m, int h
 }
 
 struct FShared {
-  u64 full[2], empty[2], done;
+  u64 full[kFStages], empty[kFStages], done;
   uint32_t tmem_base;
   int fail;
   float b1[256], w2[256];
 };
 
-__global__ void __launch_bounds__(kFThreads, 1) filter_tc_kernel(
+__global__ void __launch_bounds__(kFThreads, 2) filter_tc_kernel(
     const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap wmap, int nq,
     int nqp, int F, int h, int hp, int Kq, const float* __restrict__ b1,
     const float* __restrict__ w2, const float* __restrict__ b2, float* __restrict__ out,
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kFThreads, 1) filter_tc_kernel(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nK = Kq / kSlice;
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kFStages; ++i) {
       dev::mbar_init(&S.full[i], 1);
       dev::mbar_init(&S.empty[i], 1);
     }
@@ -117,20 +120,21 @@ __global__ void __launch_bounds__(kFThreads, 1) filter_tc_kernel(
   if (tid == 0) {
     const uint32_t bytes = (uint32_t)(2 * kAPlane + 2 * hp * kSlice * 4);
     auto issue = [&](int kc) {
-      unsigned char* st = sm + (kc & 1) * kStage;
-      dev::mbar_expect_tx(&S.full[kc & 1], bytes);
-      dev::tma_load_2d(st, &qmap, kc * kSlice, tile * kFRows, &S.full[kc & 1]);
-      dev::tma_load_2d(st + kAPlane, &qmap, kc * kSlice, nqp + tile * kFRows, &S.full[kc & 1]);
-      dev::tma_load_2d(st + 2 * kAPlane, &wmap, kc * kSlice, (2 * f) * hp, &S.full[kc & 1]);
+      const int sx = kc % kFStages;
+      unsigned char* st = sm + sx * kStage;
+      dev::mbar_expect_tx(&S.full[sx], bytes);
+      dev::tma_load_2d(st, &qmap, kc * kSlice, tile * kFRows, &S.full[sx]);
+      dev::tma_load_2d(st + kAPlane, &qmap, kc * kSlice, nqp + tile * kFRows, &S.full[sx]);
+      dev::tma_load_2d(st + 2 * kAPlane, &wmap, kc * kSlice, (2 * f) * hp, &S.full[sx]);
       dev::tma_load_2d(st + 2 * kAPlane + kBPlane, &wmap, kc * kSlice, (2 * f + 1) * hp,
-                       &S.full[kc & 1]);
+                       &S.full[sx]);
     };
     const uint32_t idesc = idesc_tf32(kFRows, hp);
     bool ok = true;
-    for (int kc = 0; kc < nK && kc < 2; ++kc) issue(kc);
+    for (int kc = 0; kc < nK && kc < kFStages; ++kc) issue(kc);
     for (int kc = 0; kc < nK && ok; ++kc) {
-      const int s = kc & 1;
-      const uint32_t ph = (uint32_t)((kc >> 1) & 1);
+      const int s = kc % kFStages;
+      const uint32_t ph = (uint32_t)((kc / kFStages) & 1);
       ok = dev::mbar_wait(&S.full[s], ph, kFWait);
       if (!ok) break;
       dev::tc_fence_after();
@@ -147,9 +151,9 @@ __global__ void __launch_bounds__(kFThreads, 1) filter_tc_kernel(
         mma_tf32(tmem, alo + o, bhi + o, idesc, 1u);
       }
       dev::mma_commit(&S.empty[s]);
-      if (kc + 2 < nK) {
+      if (kc + kFStages < nK) {
         ok = dev::mbar_wait(&S.empty[s], ph, kFWait);
-        if (ok) issue(kc + 2);
+        if (ok) issue(kc + kFStages);
       }
     }
     if (!ok) {
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(kFThreads, 1) filter_tc_kernel(
 bool filter_tc_fits(int m, int h, int smem_optin) {
   const int hp = (h + 15) / 16 * 16;
   (void)m;
-  return h >= 1 && hp <= 256 && (size_t)(1024 + 2 * kStage) + sizeof(FShared) <= (size_t)smem_optin;
+  return h >= 1 && hp <= 256 && (size_t)(1024 + kFStages * kStage) + sizeof(FShared) <= (size_t)smem_optin;
 }
 
 void launch_wsplit(const float* W1t, int F, int m, int h, float* Ws, cudaStream_t s) {
@@ -207,7 +211,7 @@ void launch_filter_tc(const CUtensorMap& qmap, const CUtensorMap& wmap, const fl
   const int64_t tot = (int64_t)nqp * Kq;
   qsplit_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Q, nq, mp, m, Kq, nqp, Qs);
   LF_CHECK_LAUNCH();
-  const size_t smem = 1024 + 2 * (size_t)kStage;
+  const size_t smem = 1024 + kFStages * (size_t)kStage;
   LF_CUDA(cudaFuncSetAttribute(filter_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   dim3 grid(F, nqp / kFRows);
