@@ -156,16 +156,21 @@ leafi_status leafi_route(leafi_index* index, const float* queries, int64_t nq, i
 
 /* Same bounds as leafi_leaf_lower_bounds, computed without allocating any
  * device memory.  The paper has no counterpart: this is a library facility for
- * callers that cannot call cudaMalloc (work recorded while a CUDA graph is
- * being captured, or a serving loop that keeps the allocator off its path).
- * queries [nq][m] and lb2 [nq][n_leaves] must be device arrays; the work is
- * queued on the index's stream and the call returns without synchronising.
- * Scratch is one static device array of 16 MiB per GPU, held until the
- * process exits; requests that need more (roughly nq*(2m+2) + nq*(2*intervals
- * + nodes) doubles for a DSTree) are rejected with LEAFI_EINVAL naming the
- * largest nq that fits.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress), so make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race. */
+ * callers that cannot call cudaMalloc -- a program whose GPU memory is reserved
+ * up front by another allocator (a framework's caching pool that owns the
+ * device), or a latency-critical loop that cannot take cudaMalloc's implicit
+ * device-wide synchronisation.  queries [nq][m] float32 and lb2 [nq][n_leaves]
+ * float64 must be device (or managed) arrays on the index's GPU; anything else
+ * is LEAFI_EINVAL before any launch.  The shapes cannot be checked here: the
+ * caller guarantees them.  The work is queued on the index's stream and the
+ * call returns without synchronising.  Scratch is one static device array of
+ * 16 MiB per GPU, held until the process exits; requests that need more
+ * (roughly nq*(2m+2) + nq*(2*intervals + nodes) doubles for a DSTree) are
+ * rejected with LEAFI_EINVAL naming the largest nq that fits.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make it before any stream capture.  Every call shares the array and keeps
+ * nothing from the previous one (each scratch word read is written earlier in
+ * the same call): calls that overlap on the GPU race. */
 leafi_status leafi_leaf_lower_bounds_noalloc(leafi_index* index, const float* queries,
                                              int64_t nq, double* lb2);
 

@@ -280,9 +280,24 @@ def leafi_leaf_lower_bounds(index, queries, out):
 def leafi_leaf_lower_bounds_noalloc(index, queries, out):
     """Leaf bounds with no device allocation: `queries` and `out` must be CUDA tensors.
 
-    For callers that cannot allocate device memory; the library's static
-    scratch array (16 MiB per GPU) bounds nq.  Returns without synchronising.
+    For callers that cannot allocate device memory (their GPU memory is held by
+    another allocator, or their loop cannot take cudaMalloc's device-wide
+    synchronisation); the library's static scratch array (16 MiB per GPU)
+    bounds nq.  Returns without synchronising.  Shapes are checked here because
+    the C side receives bare pointers: queries [nq, m] float32 and out
+    [nq, n_leaves] float64, both on the index's device.
     """
+    info = leafi_get_info(index)
+    for name, a in (("queries", queries), ("out", out)):
+        if not type(a).__module__.startswith("torch") or not a.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+    if queries.ndim != 2 or queries.shape[1] != info.m:
+        raise ValueError("queries must have shape (nq, %d), got %s" % (info.m, tuple(queries.shape)))
+    if tuple(out.shape) != (queries.shape[0], info.n_leaves):
+        raise ValueError("out must have shape (%d, %d), got %s"
+                         % (queries.shape[0], info.n_leaves, tuple(out.shape)))
+    if queries.device != out.device:
+        raise ValueError("queries and out must be on the same device")
     _check(lib().leafi_leaf_lower_bounds_noalloc(index, _ptr(queries, np.float32, "queries"),
                                                  queries.shape[0],
                                                  _ptr(out, np.float64, "out", True)))

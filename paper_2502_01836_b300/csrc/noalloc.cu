@@ -1,7 +1,8 @@
 // leafi_leaf_lower_bounds_noalloc: the leaf lower bounds without any device
-// allocation, for callers that must not call cudaMalloc (for instance code
-// that runs while a CUDA graph is being captured, or a latency-critical loop
-// that has to keep the allocator out of its path).
+// allocation, for callers that must not call cudaMalloc: a host program whose
+// GPU memory is reserved up front by another allocator (a framework's caching
+// pool that owns the device), or a latency-critical loop that cannot accept
+// cudaMalloc's implicit device-wide synchronisation on its path.
 //
 // The bound kernels need scratch memory (float64 prefix sums of the queries,
 // per-interval query statistics, per-node bounds).  Here that scratch is a
@@ -44,13 +45,17 @@ unsigned char* scratch_on(int dev) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-bool is_device_pointer(const void* p) {
+// true iff p is device (or managed) memory of GPU `dev`: the kernels read and
+// write it in place, so memory of another GPU is refused rather than reached
+// through peer access (or faulting without it)
+bool is_device_pointer_on(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -66,6 +71,11 @@ extern "C" leafi_status leafi_leaf_lower_bounds_noalloc(leafi_index* index, cons
     if (nq < 0) fail(LEAFI_EINVAL, "nq < 0");
     if (nq == 0) return LEAFI_OK;
     if (!queries || !lb2) fail(LEAFI_EINVAL, "queries / lb2 is NULL");
+    // every query needs at least 16 bytes of prefix sums, so this bound keeps
+    // the size arithmetic below far from overflow and nq within int range
+    if ((uint64_t)nq > kNoAllocScratchBytes / 16)
+      fail(LEAFI_EINVAL, "nq = %lld exceeds the no-allocation scratch (%zu bytes)",
+           (long long)nq, kNoAllocScratchBytes);
     std::lock_guard<std::mutex> lk(index->mu);
     int prev = -1;
     cudaGetDevice(&prev);
@@ -76,8 +86,11 @@ extern "C" leafi_status leafi_leaf_lower_bounds_noalloc(leafi_index* index, cons
         if (dev >= 0) cudaSetDevice(dev);
       }
     } restore{prev != index->device ? prev : -1};
-    if (!is_device_pointer(queries) || !is_device_pointer(lb2))
-      fail(LEAFI_EINVAL, "queries and lb2 must be device arrays (nothing is staged)");
+    if (!is_device_pointer_on(queries, index->device) ||
+        !is_device_pointer_on(lb2, index->device))
+      fail(LEAFI_EINVAL,
+           "queries and lb2 must be device arrays on the index's GPU %d (nothing is staged)",
+           index->device);
     if (reinterpret_cast<uintptr_t>(queries) % 4 || reinterpret_cast<uintptr_t>(lb2) % 8)
       fail(LEAFI_EINVAL, "misaligned queries / lb2");
     const HostTree& t = index->tree;
