@@ -104,6 +104,21 @@ def test_dstree_split_hand_example():
     assert t.route(X).tolist() == g["leaf_of"]
 
 
+def test_dstree_split_score_hand_example():
+    """The QoS score decides among candidates of every kind: a horizontal split
+    on sigma wins by 41/6 against 6, and each plausible misreading of the score
+    (sigma range, unweighted children, no interval lengths) picks another
+    partition (tests/golden/dstree_split_score_hand.json)."""
+    g = _golden("dstree_split_score_hand.json")
+    X = np.array(g["series"], np.float32)
+    t = O.Tree(X, "dstree", leaf_cap=g["leaf_cap"], init_segments=g["init_segments"])
+    assert t.L == g["n_leaves"] and t.n_nodes == g["n_nodes"]
+    assert t.leaf_of().tolist() == g["leaf_of"]
+    assert t.route(X).tolist() == g["leaf_of"]
+    # the children's synopses are over the winner's segmentation
+    assert t.lb2(X).tolist() == g["lb2_of_series"]
+
+
 @pytest.fixture(scope="module")
 def rw():
     X = fx.random_walk(6000, 64, seed=11)
@@ -254,6 +269,33 @@ def test_training_reduces_validation_loss_and_plateau_stops():
     assert (ep < 400).all()
 
 
+@pytest.mark.parametrize("case", ["constant", "constant_capped", "halving", "one_step"])
+def test_sgd_plateau_schedule_hand_counted(case):
+    """Epoch counts of the plateau schedule, the strict-improvement rule and the
+    kept best-validation weights on cases counted by hand
+    (tests/golden/sgd_plateau_hand.json)."""
+    c = _golden("sgd_plateau_hand.json")["cases"][case]
+    m = h = 2
+    Qg = np.array([[1, 2], [-1, 0.5], [0.25, -2], [3, 1]], np.float32)
+    Ql = np.array([[[2, 2], [-3, 1], [0, 1], [1, -1]]], np.float32)
+    Tg = np.array([[c["train_target"]]] * 2 + [[c["val_target"]]] * 2, np.float32)
+    Tl = np.array([[c["train_target"]] * 2 + [c["val_target"]] * 2], np.float32)
+    W1 = np.zeros((1, h, m), np.float32)
+    b1 = np.full((1, h), -1.0, np.float32)
+    w2 = np.array([[0.5, -0.25]], np.float32)
+    b2 = np.array([c["b2"]], np.float32)
+    p = O.TrainParams(n_gtrain=2, n_gval=2, n_ltrain=2, n_lval=2, batch=4,
+                      max_epochs=c["max_epochs"], patience=c["patience"], lr0=c["lr0"],
+                      lr_min=c["lr_min"])
+    perms = np.tile(np.array([2, 0, 3, 1], np.int32), (c["max_epochs"], 1))
+    (W1n, b1n, w2n, b2n), ep, bv = O.train(p, Qg, Tg, Ql, Tl, perms, W1, b1, w2, b2)
+    assert int(ep[0]) == c["epochs"]
+    assert float(bv[0]) == c["best_val"]
+    assert float(b2n[0]) == np.float32(c["b2_kept"])
+    # dead hidden units: nothing else moves
+    assert np.array_equal(W1n, W1) and np.array_equal(b1n, b1) and np.array_equal(w2n, w2)
+
+
 # ---------------------------------------------------------------- Steffen
 
 def test_steffen_properties():
@@ -331,25 +373,60 @@ def test_wave_one_is_the_sequential_algorithm(small_index):
                 assert ids[i, :len(ref)].tolist() == ref
 
 
-def test_autotuner_table_matches_search_recall(small_index):
-    """Alg. 4's simulated quality at each position equals the recall that the
-    search itself reaches with those offsets (measured against brute force)."""
-    X, t, Q = small_index
+def test_autotuner_hand_example():
+    """Alg. 4 on a case worked by hand: the alpha table element by element and
+    the quality at every sorted position, for k = 1 and 2 and two wave widths
+    (tests/golden/alg4_autotuner_hand.json)."""
+    g = _golden("alg4_autotuner_hand.json")
+    X = np.array(g["series"], np.float32)
+    t = O.Tree(X, "dstree", leaf_cap=g["leaf_cap"], init_segments=g["init_segments"])
+    assert t.leaf_of().tolist() == g["leaf_of"]
+    Qc = np.array(g["calibration"], np.float32)
+    assert t.route(Qc).tolist() == g["route"]
+    W = tuple(np.array(g[k], np.float32) for k in ("W1", "b1", "w2", "b2"))
+    assert O.mlp_forward(*W, Qc).tolist() == g["predictions"]
+    fl = np.array(g["filter_leaf"], np.int32)
+    for k, qp_hand in g["qprime"].items():
+        for wave in g["waves"]:
+            alpha, qp = O.fit_autotuner(t, W, fl, Qc, int(k), wave)
+            assert alpha.tolist() == g["alpha_sorted"]
+            assert qp.tolist() == qp_hand, (k, wave)
+
+
+def _informative_filters(t, Qc, seed):
+    """Random filters whose output bias sits near each leaf's typical d^L, so
+    that the offsets decide what is pruned."""
     F = t.L
-    W = fx.filter_init(F, 32, 32, seed=8)
-    fl = np.arange(F, dtype=np.int32)
-    Qc = Q[:12]
-    for k in (1, 3):
-        alpha, qp = O.fit_autotuner(t, W, fl, Qc, k, 2)
-        assert (np.diff(alpha, axis=1) <= 0).all()          # descending per filter
-        assert (np.diff(qp) <= 0).all() and qp[0] == 1.0     # largest offsets are safe
-        bf, _ = O.knn(X, Qc, k)
-        run = np.inf
-        for j in range(Qc.shape[0]):
-            ids, _, _, _ = O.leafi_search(t, W, fl, alpha, Qc, k, j, 2)
-            r = O.recall_at_k(ids, bf, k).mean()
-            run = min(run, r)
-            assert qp[j] == pytest.approx(run, abs=1e-12)
+    W1, b1, w2, b2 = fx.filter_init(F, t.m, t.m, seed=100 + seed)
+    leaves = np.tile(np.arange(t.L, dtype=np.int32), (Qc.shape[0], 1))
+    d2, _ = t.leaf_topk(Qc, leaves, 1)
+    med = np.median(np.sqrt(d2[:, :, 0]), 0)
+    b2 = (med + np.random.default_rng(seed).normal(0, 1.0, F)).astype(np.float32)
+    return (W1, b1, w2 * 3, b2)
+
+
+@pytest.mark.parametrize("seed,k,wave", [(21, 3, 1), (24, 3, 2), (3, 1, 2)])
+def test_autotuner_table_matches_search_recall(seed, k, wave):
+    """Alg. 4's simulated quality at each position, monotonised by the running
+    minimum, equals the running minimum of the recall that the search itself
+    reaches with those offsets, measured against brute force.  The first two
+    cases have a non-monotone measured recall, so they exercise the running
+    minimum."""
+    X = fx.random_walk(3000, 32, seed=21)
+    t = O.Tree(X, "dstree", leaf_cap=150, init_segments=4)
+    Qc = fx.test_queries(X, 60, seed=22)[:24]
+    W = _informative_filters(t, Qc, seed)
+    fl = np.arange(t.L, dtype=np.int32)
+    alpha, qp = O.fit_autotuner(t, W, fl, Qc, k, wave)
+    assert (np.diff(alpha, axis=1) <= 0).all()          # descending per filter
+    assert (np.diff(qp) <= 0).all() and qp[0] == 1.0
+    bf, _ = O.knn(X, Qc, k)
+    rec = np.array([O.recall_at_k(O.leafi_search(t, W, fl, alpha, Qc, k, j, wave)[0], bf,
+                                  k).mean() for j in range(Qc.shape[0])])
+    assert rec.min() < 0.9                                # the offsets matter here
+    assert np.allclose(qp, np.minimum.accumulate(rec), rtol=0, atol=1e-12)
+    if seed in (21, 24):
+        assert (np.diff(rec) > 0).any()
 
 
 def test_offset_position_step_rule():
