@@ -1270,10 +1270,22 @@ int32_t or_select_leaves_alg3(const int64_t* sizes, int32_t L, double th, double
   return n;
 }
 
+/* STEP rule with the inductive-conformal rank of Sec. 3: with nc calibration
+ * queries the confidence levels a sorted position can certify are steps of
+ * 1/(nc + 1) (delta = j_s / (l - m + 1)), so a target t is met when the
+ * calibration quality reaches r = ceil((nc + 1) t) / nc; a target above
+ * nc / (nc + 1) has r > 1 and no position (the search runs exactly).  The
+ * position is the largest j (smallest offsets) whose running-minimum quality
+ * still meets r. */
+double or_required_quality(int64_t nc, double target) {
+  return ceil((double)(nc + 1) * target) / (double)nc;
+}
+
 int32_t or_offset_position(const double* qprime, int64_t nc, double target) {
+  const double r = or_required_quality(nc, target);
   int32_t j = -1;
   for (int64_t i = 0; i < nc; ++i) {
-    if (qprime[i] >= target) j = (int32_t)i; else break;
+    if (qprime[i] >= r) j = (int32_t)i; else break;
   }
   return j;
 }

@@ -102,8 +102,14 @@ void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const 
 int32_t or_select_leaves_alg3(const int64_t* sizes, int32_t L, double th, double w, double cap,
                               int32_t* out);
 
-/* Sorted position j* for a target (STEP reading): the largest j with
- * qprime[j] >= target; -1 means "no position meets it -> filters off". */
+/* Calibration quality a target needs with nc calibration queries (Sec. 3,
+ * inductive conformal regression: confidence steps of 1/(nc + 1)):
+ * r = ceil((nc + 1) target) / nc, above 1 for targets no position can certify. */
+double or_required_quality(int64_t nc, double target);
+
+/* Sorted position j* for a target (STEP reading with the conformal rank): the
+ * largest j with qprime[j] >= or_required_quality(nc, target); -1 means "no
+ * position meets it -> filters off". */
 int32_t or_offset_position(const double* qprime, int64_t nc, double target);
 
 /* Steffen (1990) monotone interpolation through (x_i, y_i), x strictly increasing,

@@ -14,7 +14,7 @@ import numpy as np
 __all__ = [
     "build", "lib", "sqdist", "knn", "segment_stats", "Tree", "isax_breakpoints",
     "mlp_forward", "train_targets", "TrainParams", "train", "fit_autotuner",
-    "offset_position", "steffen_eval", "leafi_search", "recall_at_k", "select_leaves_alg3",
+    "offset_position", "required_quality", "steffen_eval", "leafi_search", "recall_at_k", "select_leaves_alg3",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -86,6 +86,8 @@ def lib():
         L.or_select_leaves_alg3.restype = C.c_int32
         L.or_offset_position.argtypes = [f64p, C.c_int64, C.c_double]
         L.or_offset_position.restype = C.c_int32
+        L.or_required_quality.argtypes = [C.c_int64, C.c_double]
+        L.or_required_quality.restype = C.c_double
         L.or_steffen_eval.argtypes = [f64p, f64p, C.c_int, C.c_double]
         L.or_steffen_eval.restype = C.c_double
         L.or_leafi_search.argtypes = [vp, f32p, f32p, f32p, f32p, i32p, C.c_int, C.c_int, f64p,
@@ -257,6 +259,11 @@ def select_leaves_alg3(sizes, th, w, cap):
                                     float(th), float(w), float(cap),
                                     out.ctypes.data_as(C.POINTER(C.c_int32)))
     return out[:n]
+
+
+def required_quality(nc, target):
+    """Calibration quality that certifies `target` with nc calibration queries."""
+    return float(lib().or_required_quality(int(nc), float(target)))
 
 
 def offset_position(qprime, target):

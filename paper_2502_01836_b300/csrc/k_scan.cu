@@ -726,7 +726,10 @@ __global__ void fill_u64_kernel(u64* p, u64 v, size_t n) {
 
 // sorted position per query (Sec. 4.4.2 with the STEP reading): the query's
 // k picks the smallest calibrated class >= k; the position is the largest j
-// whose calibrated quality qprime[class][j] still meets the target.
+// whose calibrated quality qprime[class][j] still reaches the quality that
+// certifies the target with nc calibration queries, r = ceil((nc+1) t) / nc
+// (the 1/(nc+1) confidence steps of inductive conformal regression, Sec. 3);
+// r > 1 leaves no position (exact search).
 __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double* __restrict__ target,
                             int nk, const int32_t* __restrict__ kclasses,
                             const double* __restrict__ qprime, int nc, int32_t* __restrict__ jpos) {
@@ -743,12 +746,13 @@ __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double*
       break;
     }
   int j = -1;
-  if (c >= 0 && t < 1.0) {
+  const double r = __ddiv_rn(ceil(__dmul_rn((double)(nc + 1), t)), (double)nc);
+  if (c >= 0 && t < 1.0 && r <= 1.0) {
     const double* qp = qprime + (size_t)c * nc;
     j = nc - 1;
     for (int base = 0; base < nc; base += 32) {
       const int i = base + lane;
-      const unsigned below = __ballot_sync(0xffffffffu, i < nc && !(qp[i] >= t));
+      const unsigned below = __ballot_sync(0xffffffffu, i < nc && !(qp[i] >= r));
       if (below) {
         j = base + __ffs(below) - 2;
         break;

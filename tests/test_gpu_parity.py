@@ -544,7 +544,7 @@ def test_end_to_end_recall_meets_target():
             st = lf.SearchStats()
             lf.leafi_search(idx, Qt, 1, target, ids, d, st)
             rec = (ids[:, 0] == bf[:, 0]).mean()
-            assert rec >= target - 0.03, (target, rec)
+            assert rec >= target, (target, rec)
         e_ids, _, est = _exact(idx, Qt, 1)
         assert np.array_equal(e_ids, bf)
     finally:

@@ -430,11 +430,20 @@ def test_autotuner_table_matches_search_recall(seed, k, wave):
 
 
 def test_offset_position_step_rule():
-    qp = np.array([1.0, 1.0, 0.99, 0.97, 0.97, 0.9])
-    assert O.offset_position(qp, 0.99) == 2
-    assert O.offset_position(qp, 0.95) == 4
-    assert O.offset_position(qp, 1.0) == 1
-    assert O.offset_position(np.array([0.9, 0.8]), 0.95) == -1
+    """STEP with the conformal rank of Sec. 3: with nc calibration queries the
+    target t needs calibration quality ceil((nc + 1) t) / nc (hand values)."""
+    assert O.required_quality(300, 0.99) == 298 / 300
+    assert O.required_quality(300, 0.9) == 271 / 300
+    assert O.required_quality(300, 0.95) == 286 / 300
+    assert O.required_quality(300, 300 / 301 + 1e-6) > 1.0
+    qp = np.array([1.0, 1.0, 0.9, 0.9, 0.8, 0.7, 0.7, 0.6, 0.5, 0.5])   # nc = 10
+    assert O.offset_position(qp, 0.8) == 3       # 11 * 0.8 = 8.8 -> needs 9/10
+    assert O.offset_position(qp, 0.72) == 4      # 7.92 -> 8/10
+    assert O.offset_position(qp, 0.9) == 1       # 9.9 -> 10/10
+    assert O.offset_position(qp, 0.5) == 7       # 5.5 -> 6/10
+    assert O.offset_position(qp, 0.45) == 9      # 4.95 -> 5/10
+    assert O.offset_position(qp, 0.95) == -1     # 10.45 -> 11/10: no position certifies it
+    assert O.offset_position(np.array([0.9, 0.8]), 0.5) == -1   # needs 2/2
 
 
 def test_huge_offsets_give_the_exact_answer(small_index):
