@@ -819,6 +819,179 @@ void or_train_targets(const or_tree* t, const int32_t* filter_leaf, int F, const
 }
 
 /* ------------------------------------------------------------------ */
+/* Alg. 1 random draws: GenerateGlobalQueries / GenerateLocalQueries    */
+/* (lines 2 and 6), initial weights and per-epoch shuffles.            */
+/*                                                                     */
+/* Counter-based generator: Philox4x32-10 as published by Salmon,      */
+/* Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2,   */
+/* 3" (SC 2011): ten rounds of two 32x32->64 multiplications on a      */
+/* 4-word counter with a 2-word key bumped by the Weyl constants.       */
+/* Counter = (i, j, tag, stream), key = (seed low, seed high).          */
+/* Readings (the paper states the query protocol, not its random       */
+/* draws): picks without replacement by Floyd's algorithm (with        */
+/* replacement when a leaf is smaller than the count); sigma ~ U[lo,   */
+/* hi] per query; Gaussian noise by Box-Muller; re-z-normalisation in  */
+/* float64 (population sigma, rows with sigma < 1e-8 become zeros).    */
+/* ------------------------------------------------------------------ */
+
+enum { OR_TAG_GPICK = 1, OR_TAG_LPICK = 2, OR_TAG_SIGMA = 3, OR_TAG_NOISE = 4, OR_TAG_W1 = 5,
+       OR_TAG_B1 = 6, OR_TAG_W2 = 7, OR_TAG_B2 = 8, OR_TAG_PERM = 9 };
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void draw(uint64_t seed, uint32_t i, uint32_t j, uint32_t tag, uint32_t stream,
+                 uint32_t out[4]) {
+  uint32_t ctr[4] = {i, j, tag, stream};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  or_philox4x32_10(ctr, key, out);
+}
+
+/* 53-bit uniform in [0, 1) from two words */
+static double unif53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+/* integer in [0, n) from two words: floor(u64 * n / 2^64) */
+static uint64_t below(uint32_t a, uint32_t b, uint64_t n) {
+  unsigned __int128 v = ((unsigned __int128)(((uint64_t)a << 32) | b)) * n;
+  return (uint64_t)(v >> 64);
+}
+
+/* Floyd's sampling of k distinct values of [0, n) in insertion order */
+static void floyd(uint64_t seed, uint32_t tag, uint32_t stream, uint64_t n, int64_t k,
+                  int64_t* out) {
+  for (int64_t s = 0; s < k; ++s) {
+    uint64_t j = n - (uint64_t)k + (uint64_t)s;
+    uint32_t w[4];
+    draw(seed, (uint32_t)s, 0, tag, stream, w);
+    int64_t t = (int64_t)below(w[0], w[1], j + 1);
+    for (int64_t z = 0; z < s; ++z)
+      if (out[z] == t) { t = (int64_t)j; break; }
+    out[s] = t;
+  }
+}
+
+/* one noisy, re-z-normalised query from series x */
+static void noisy_query(const float* x, int m, uint64_t seed, uint32_t i, uint32_t stream,
+                        double lo, double hi, double* tmp, float* out) {
+  uint32_t w[4];
+  draw(seed, i, 0, OR_TAG_SIGMA, stream, w);
+  double sigma = lo + (hi - lo) * unif53(w[0], w[1]);
+  for (int p = 0; 2 * p < m; ++p) {
+    draw(seed, i, (uint32_t)p, OR_TAG_NOISE, stream, w);
+    double u1 = unif53(w[0], w[1]), u2 = unif53(w[2], w[3]);
+    double r = sqrt(-2.0 * log(1.0 - u1));
+    double th = 6.283185307179586 * u2;
+    tmp[2 * p] = (double)x[2 * p] + sigma * (r * cos(th));
+    if (2 * p + 1 < m) tmp[2 * p + 1] = (double)x[2 * p + 1] + sigma * (r * sin(th));
+  }
+  double mu = 0.0;
+  for (int t = 0; t < m; ++t) mu += tmp[t];
+  mu /= (double)m;
+  double ss = 0.0;
+  for (int t = 0; t < m; ++t) ss += (tmp[t] - mu) * (tmp[t] - mu);
+  double sd = sqrt(ss / (double)m);
+  for (int t = 0; t < m; ++t) out[t] = sd < 1e-8 ? 0.0f : (float)((tmp[t] - mu) / sd);
+}
+
+void or_training_queries(const or_tree* t, const int32_t* filter_leaf, int F, int64_t n_global,
+                         int64_t n_local, double noise_lo, double noise_hi, uint64_t seed,
+                         float* Qg, float* Ql, int64_t* gpick, int64_t* lpick) {
+  const int m = t->m;
+  double* tmp = (double*)malloc(sizeof(double) * (m + 1));
+  /* line 2: global queries from uniformly drawn dataset series (original ids) */
+  floyd(seed, OR_TAG_GPICK, 0, (uint64_t)t->n, n_global, gpick);
+  for (int64_t i = 0; i < n_global; ++i)
+    noisy_query(t->X + gpick[i] * m, m, seed, (uint32_t)i, 0, noise_lo, noise_hi, tmp,
+                Qg + i * m);
+  /* line 6: local queries from the members of each filtered leaf (ascending ids) */
+  for (int f = 0; f < F; ++f) {
+    const node_t* nd = &t->nodes[t->leaf_node[filter_leaf[f]]];
+    const uint64_t sz = (uint64_t)nd->nids;
+    int64_t* r = lpick + (int64_t)f * n_local;
+    if ((int64_t)sz >= n_local) {
+      floyd(seed, OR_TAG_LPICK, (uint32_t)(1 + f), sz, n_local, r);
+    } else {
+      for (int64_t i = 0; i < n_local; ++i) {
+        uint32_t w[4];
+        draw(seed, (uint32_t)i, 0, OR_TAG_LPICK, (uint32_t)(1 + f), w);
+        r[i] = (int64_t)below(w[0], w[1], sz);
+      }
+    }
+    for (int64_t i = 0; i < n_local; ++i) {
+      r[i] = nd->ids[r[i]];   /* rank among the leaf's members -> original id */
+      noisy_query(t->X + r[i] * m, m, seed, (uint32_t)i, (uint32_t)(1 + f), noise_lo, noise_hi,
+                  tmp, Ql + ((int64_t)f * n_local + i) * m);
+    }
+  }
+  free(tmp);
+}
+
+/* Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initial weights, W1 [F][h][m] */
+void or_filter_init(int F, int h, int m, uint64_t seed, float* W1, float* b1, float* w2,
+                    float* b2) {
+  const double a1 = 1.0 / sqrt((double)m), a2 = 1.0 / sqrt((double)h);
+  uint32_t w[4];
+  for (int f = 0; f < F; ++f) {
+    for (int64_t e = 0; e < (int64_t)h * m; ++e) {
+      draw(seed, (uint32_t)e, (uint32_t)f, OR_TAG_W1, 0, w);
+      W1[(int64_t)f * h * m + e] = (float)((2.0 * unif53(w[0], w[1]) - 1.0) * a1);
+    }
+    for (int j = 0; j < h; ++j) {
+      draw(seed, (uint32_t)j, (uint32_t)f, OR_TAG_B1, 0, w);
+      b1[(int64_t)f * h + j] = (float)((2.0 * unif53(w[0], w[1]) - 1.0) * a1);
+      draw(seed, (uint32_t)j, (uint32_t)f, OR_TAG_W2, 0, w);
+      w2[(int64_t)f * h + j] = (float)((2.0 * unif53(w[0], w[1]) - 1.0) * a2);
+    }
+    draw(seed, 0, (uint32_t)f, OR_TAG_B2, 0, w);
+    b2[f] = (float)((2.0 * unif53(w[0], w[1]) - 1.0) * a2);
+  }
+}
+
+typedef struct {
+  uint64_t key;
+  int32_t i;
+} keyed;
+
+static int by_key(const void* pa, const void* pb) {
+  const keyed* a = (const keyed*)pa;
+  const keyed* b = (const keyed*)pb;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->i - b->i;
+}
+
+/* one shuffle of [0, n) per epoch: indices ordered by their 64-bit keys */
+void or_epoch_perms(int epochs, int n, uint64_t seed, int32_t* perms) {
+  keyed* v = (keyed*)malloc(sizeof(keyed) * (size_t)(n > 0 ? n : 1));
+  for (int e = 0; e < epochs; ++e) {
+    for (int i = 0; i < n; ++i) {
+      uint32_t w[4];
+      draw(seed, (uint32_t)i, (uint32_t)e, OR_TAG_PERM, 0, w);
+      v[i].key = ((uint64_t)w[0] << 32) | w[1];
+      v[i].i = i;
+    }
+    qsort(v, (size_t)n, sizeof(keyed), by_key);
+    for (int i = 0; i < n; ++i) perms[(size_t)e * n + i] = v[i].i;
+  }
+  free(v);
+}
+
+/* ------------------------------------------------------------------ */
 /* MLP filters                                                         */
 /* ------------------------------------------------------------------ */
 

@@ -102,6 +102,22 @@ void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const 
 int32_t or_select_leaves_alg3(const int64_t* sizes, int32_t L, double th, double w, double cap,
                               int32_t* out);
 
+/* Philox4x32-10 (Salmon et al., SC 2011): out = bijection(ctr) under key. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Alg. 1 lines 2 and 6: n_global queries from distinct dataset series (gpick,
+ * original ids) and n_local queries per filtered leaf from its members (lpick
+ * [F][n_local], original ids), each + Gaussian noise of sigma ~ U[lo, hi] and
+ * re-z-normalised.  Qg [n_global][m], Ql [F][n_local][m]. */
+void or_training_queries(const or_tree* t, const int32_t* filter_leaf, int F, int64_t n_global,
+                         int64_t n_local, double noise_lo, double noise_hi, uint64_t seed,
+                         float* Qg, float* Ql, int64_t* gpick, int64_t* lpick);
+/* Initial filter weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)); W1 [F][h][m]. */
+void or_filter_init(int F, int h, int m, uint64_t seed, float* W1, float* b1, float* w2,
+                    float* b2);
+/* One shuffle of [0, n) per epoch (int32 [epochs][n]). */
+void or_epoch_perms(int epochs, int n, uint64_t seed, int32_t* perms);
+
 /* Calibration quality a target needs with nc calibration queries (Sec. 3,
  * inductive conformal regression: confidence steps of 1/(nc + 1)):
  * r = ceil((nc + 1) target) / nc, above 1 for targets no position can certify. */

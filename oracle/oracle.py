@@ -14,7 +14,8 @@ import numpy as np
 __all__ = [
     "build", "lib", "sqdist", "knn", "segment_stats", "Tree", "isax_breakpoints",
     "mlp_forward", "train_targets", "TrainParams", "train", "fit_autotuner",
-    "offset_position", "required_quality", "steffen_eval", "leafi_search", "recall_at_k", "select_leaves_alg3",
+    "offset_position", "required_quality", "philox4x32_10", "training_queries",
+    "filter_init", "epoch_perms", "steffen_eval", "leafi_search", "recall_at_k", "select_leaves_alg3",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -86,6 +87,12 @@ def lib():
         L.or_select_leaves_alg3.restype = C.c_int32
         L.or_offset_position.argtypes = [f64p, C.c_int64, C.c_double]
         L.or_offset_position.restype = C.c_int32
+        u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_training_queries.argtypes = [vp, i32p, C.c_int, C.c_int64, C.c_int64, C.c_double,
+                                          C.c_double, C.c_uint64, f32p, f32p, i64p, i64p]
+        L.or_filter_init.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, f32p, f32p, f32p, f32p]
+        L.or_epoch_perms.argtypes = [C.c_int, C.c_int, C.c_uint64, i32p]
         L.or_required_quality.argtypes = [C.c_int64, C.c_double]
         L.or_required_quality.restype = C.c_double
         L.or_steffen_eval.argtypes = [f64p, f64p, C.c_int, C.c_double]
@@ -193,6 +200,44 @@ class Tree:
         ids = np.empty((nq, nl, k), np.int64)
         lib().or_leaf_topk(self._h, Q, nq, leaves, nl, k, d2, ids)
         return d2, ids
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of a 4-word counter under a 2-word key (uint32 words)."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(c, k, out)
+    return out
+
+
+def training_queries(tree: Tree, filter_leaf, n_global, n_local, noise_lo, noise_hi, seed):
+    """Alg. 1 lines 2 and 6 -> (Qg [ng, m], Ql [F, nl, m], gpick [ng], lpick [F, nl])."""
+    fl = np.ascontiguousarray(filter_leaf, np.int32)
+    F = fl.shape[0]
+    Qg = np.zeros((n_global, tree.m), np.float32)
+    Ql = np.zeros((F, n_local, tree.m), np.float32)
+    gp = np.zeros(max(n_global, 1), np.int64)
+    lp = np.zeros((max(F * n_local, 1),), np.int64)
+    lib().or_training_queries(tree._h, fl, F, n_global, n_local, float(noise_lo),
+                              float(noise_hi), int(seed), Qg, Ql, gp, lp)
+    return Qg, Ql, gp[:n_global], lp[:F * n_local].reshape(F, n_local)
+
+
+def filter_init(F, h, m, seed):
+    """Initial weights (W1 [F,h,m], b1 [F,h], w2 [F,h], b2 [F])."""
+    W1 = np.zeros((F, h, m), np.float32)
+    b1 = np.zeros((F, h), np.float32)
+    w2 = np.zeros((F, h), np.float32)
+    b2 = np.zeros(F, np.float32)
+    lib().or_filter_init(F, h, m, int(seed), W1, b1, w2, b2)
+    return W1, b1, w2, b2
+
+
+def epoch_perms(epochs, n, seed):
+    out = np.zeros((epochs, n), np.int32)
+    lib().or_epoch_perms(epochs, n, int(seed), out)
+    return out
 
 
 def mlp_forward(W1, b1, w2, b2, Q):

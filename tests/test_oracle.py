@@ -296,6 +296,83 @@ def test_sgd_plateau_schedule_hand_counted(case):
     assert np.array_equal(W1n, W1) and np.array_equal(b1n, b1) and np.array_equal(w2n, w2)
 
 
+# ---------------------------------------------------------------- Alg. 1 random draws
+
+def test_philox_known_answers():
+    """The oracle's Philox4x32-10 reproduces the generator's published
+    known-answer vectors (tests/golden/philox4x32_kat.json)."""
+    for v in _golden("philox4x32_kat.json")["vectors"]:
+        out = O.philox4x32_10([int(w, 16) for w in v["ctr"]], [int(w, 16) for w in v["key"]])
+        assert [int(w) for w in out] == [int(w, 16) for w in v["out"]]
+
+
+@pytest.fixture(scope="module")
+def gen_tree():
+    X = fx.random_walk(4000, 64, seed=31)
+    return X, O.Tree(X, "dstree", leaf_cap=300, init_segments=4)
+
+
+def test_training_queries_picks(gen_tree):
+    """Global picks are distinct dataset ids; local picks are members of their
+    leaf, distinct when the leaf is large enough, drawn with replacement
+    otherwise (Alg. 1 lines 2 and 6)."""
+    X, t = gen_tree
+    sizes = t.leaf_sizes()
+    small = int(np.argmin(sizes))
+    big = int(np.argmax(sizes))
+    nl = int(sizes[small]) + 5
+    assert sizes[big] >= nl
+    Qg, Ql, gp, lp = O.training_queries(t, [big, small], 700, nl, 0.1, 0.4, seed=5)
+    assert len(set(gp.tolist())) == 700 and gp.min() >= 0 and gp.max() < X.shape[0]
+    lo = t.leaf_of()
+    assert (lo[lp[0]] == big).all() and len(set(lp[0].tolist())) == nl
+    assert (lo[lp[1]] == small).all()          # more picks than members: repeats
+    # deterministic, and another seed draws other series
+    assert np.array_equal(O.training_queries(t, [big, small], 700, nl, 0.1, 0.4, seed=5)[2], gp)
+    assert not np.array_equal(O.training_queries(t, [big, small], 700, nl, 0.1, 0.4, seed=6)[2],
+                              gp)
+
+
+def test_training_queries_noise_and_normalisation(gen_tree):
+    """Every query is z-normalised (mean 0, population sigma 1) and its
+    correlation with its source series is 1 / sqrt(1 + sigma^2) for unit-variance
+    series plus N(0, sigma^2) noise (checked on the mean over many queries)."""
+    X, t = gen_tree
+    for sig in (0.1, 0.4):
+        Qg, _, gp, _ = O.training_queries(t, [0], 3000, 1, sig, sig, seed=9)
+        q = Qg.astype(np.float64)
+        assert np.abs(q.mean(1)).max() < 1e-6
+        assert np.abs(q.std(1) - 1.0).max() < 1e-6
+        x = X[gp].astype(np.float64)
+        corr = (q * x).mean(1)                      # both rows z-normalised
+        expect = 1.0 / np.sqrt(1.0 + sig * sig)
+        assert abs(corr.mean() - expect) < 0.002, (sig, corr.mean(), expect)
+
+
+def test_floyd_picks_are_uniform():
+    """Each of 10 ids is drawn with probability 3/10 over many seeds."""
+    X = fx.random_walk(10, 8, seed=3)
+    t = O.Tree(X, "dstree", leaf_cap=20, init_segments=2)
+    counts = np.zeros(10)
+    for seed in range(2000):
+        gp = O.training_queries(t, [0], 3, 1, 0.1, 0.1, seed=seed)[2]
+        assert len(set(gp.tolist())) == 3
+        counts[gp] += 1
+    assert np.abs(counts - 600).max() < 5 * np.sqrt(2000 * 0.3 * 0.7)
+
+
+def test_filter_init_and_epoch_perms():
+    W1, b1, w2, b2 = O.filter_init(3, 16, 64, seed=4)
+    a1, a2 = 1 / np.sqrt(64), 1 / np.sqrt(16)
+    assert np.abs(W1).max() <= a1 and np.abs(b1).max() <= a1
+    assert np.abs(w2).max() <= a2 and np.abs(b2).max() <= a2
+    assert abs(W1.mean()) < 0.05 * a1 and abs(W1.var() / (a1 * a1 / 3) - 1) < 0.05
+    assert np.array_equal(O.filter_init(3, 16, 64, seed=4)[0], W1)
+    P = O.epoch_perms(5, 100, seed=4)
+    assert all(sorted(p.tolist()) == list(range(100)) for p in P)
+    assert len({tuple(p.tolist()) for p in P}) == 5
+
+
 # ---------------------------------------------------------------- Steffen
 
 def test_steffen_properties():
