@@ -251,12 +251,13 @@ def run_reference(a):
     sizes = t.leaf_sizes()
     F = min(a.filters, t.L)
     fl = np.array(sorted(range(t.L), key=lambda l: (-sizes[l], l))[:F], np.int32)
-    W = fx.filter_init(F, M, M)
-    members = fx.leaf_members_from(t.leaf_of(), fl)
-    Qg, Ql = fx.training_queries(X, members, 1500, 500)
+    # Alg. 1's draws from the oracle's own generator, with the library's default seed
+    seed = 2502018361
+    W = O.filter_init(F, M, M, seed)
+    Qg, Ql, _, _ = O.training_queries(t, fl, 1500, 500, 0.1, 0.4, seed)
     Tg, Tl = O.train_targets(t, fl, Qg, Ql)
     p = O.TrainParams(max_epochs=3)
-    Wt, _, _ = O.train(p, Qg, Tg, Ql, Tl, fx.epoch_permutations(3, 1600), *W)
+    Wt, _, _ = O.train(p, Qg, Tg, Ql, Tl, O.epoch_perms(3, 1600, seed), *W)
     alpha, qp = O.fit_autotuner(t, Wt, fl, Qg[1200:], 1, a.wave)
     j = O.offset_position(qp, a.target)
     per = max(4, min(a.cpu_sample, 64))
@@ -309,7 +310,7 @@ def run_serving(a):
     info = lf.leafi_get_info(idx)
     F = min(a.filters, info.n_leaves)
     t0 = time.perf_counter()
-    enhance(idx, X, F, lf.TrainParams(max_epochs=a.epochs), kclasses=(1, 10, 100))
+    enhance(idx, F, kclasses=(1, 10, 100), max_epochs=a.epochs)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     kmax = 100
@@ -404,9 +405,8 @@ def run_mixed(a):
     sizes = lf.leafi_leaf_sizes(idx)
     F = min(a.filters, info.n_leaves)
     fl = lf.leafi_select_leaves(idx, F)
-    lf.leafi_set_filters(idx, fl, *fx.filter_init(F, M, M))
-    members = fx.leaf_members_from(lf.leafi_leaf_of(idx), fl)
-    Qg, Ql = fx.training_queries(X, members, 1500, 500)
+    lf.leafi_set_filters(idx, fl, *lf.leafi_initial_weights(idx, F, M, 2502018361))
+    Qg, Ql, _, _ = lf.leafi_training_queries(idx, lf.TrainParams(), fl)
     Tg = np.zeros((1500, F), np.float32)
     Tl = np.zeros((F, 500), np.float32)
     torch.cuda.synchronize()
@@ -416,7 +416,7 @@ def run_mixed(a):
     t_targets = time.perf_counter() - t0
     pairs = (1500 + 500) * float(sizes[fl].sum())
     t0 = time.perf_counter()
-    enhance(idx, X, F, lf.TrainParams(max_epochs=a.epochs), kclasses=(1, 10, 100))
+    enhance(idx, F, kclasses=(1, 10, 100), max_epochs=a.epochs)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     Q = fx.test_queries(X, a.queries)
@@ -611,9 +611,10 @@ def run_ablation(a):
     qps, exact, ser = timed(idx, 1.0)
     rows["exact"] = {"qps": qps, "series_scanned_per_query": ser, "recall_at_1": 1.0}
     lf.leafi_free(idx)
-    for name, (ltr, lval) in (("-Local", (0, 0)), ("+Local", (400, 100))):
+    # -Local: the 1,500 global queries only; +Local: 500 local queries per filter added
+    for name, (n_train, ratio) in (("-Local", (1500, float("inf"))), ("+Local", (2000, 3.0))):
         idx = lf.leafi_build(X, bp)
-        enhance(idx, X, a.filters, lf.TrainParams(n_ltrain=ltr, n_lval=lval, max_epochs=a.epochs))
+        enhance(idx, a.filters, n_train=n_train, global_local_ratio=ratio, max_epochs=a.epochs)
         qps, got, ser = timed(idx, a.target)
         rows[name] = {"qps": qps, "series_scanned_per_query": ser,
                       "recall_at_1": float(np.mean(got == exact)),
@@ -647,9 +648,8 @@ def main():
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=local))
     stream = torch.cuda.current_stream(dev)
     lf.leafi_set_stream(idx, stream.cuda_stream)
-    tp = lf.TrainParams(max_epochs=a.epochs)
     t_train = time.perf_counter()
-    enh = enhance(idx, X, a.filters, tp, kclasses=(1,))
+    enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t_train
     info = lf.leafi_get_info(idx)
@@ -814,7 +814,8 @@ def main():
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         try:
-            W = tuple(np.zeros_like(w) for w in enh.init_weights)
+            W = (np.zeros((a.filters, M, M), np.float32), np.zeros((a.filters, M), np.float32),
+                 np.zeros((a.filters, M), np.float32), np.zeros(a.filters, np.float32))
             lf.leafi_get_filters(idx, *W)
             alpha = np.zeros((a.filters, info.n_calib))
             qp = np.zeros((1, info.n_calib))

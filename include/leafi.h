@@ -213,6 +213,8 @@ leafi_status leafi_select_leaves_auto(leafi_index* index, const leafi_select_par
 leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F,
                                int32_t h, const float* W1, const float* b1, const float* w2,
                                const float* b2);
+/* The filtered leaves, filter by filter (int32 [n_filters], host). */
+leafi_status leafi_get_filter_leaves(const leafi_index* index, int32_t* filter_leaf);
 /* Copy the current filter weights out (same layouts as leafi_set_filters). */
 leafi_status leafi_get_filters(leafi_index* index, float* W1, float* b1, float* w2, float* b2);
 /* d^f(q, M_f) for every query and filter (float32, nq x F). */
@@ -236,6 +238,65 @@ leafi_status leafi_leaf_knn(leafi_index* index, const float* queries, int64_t nq
 leafi_status leafi_train_targets(leafi_index* index, const float* Qg, int64_t ng,
                                  const float* Ql, int64_t nl, float* Tg, float* Tl);
 
+/* LeaFi-enhanced index building, Alg. 1 end to end (lines 1-10): select the
+ * filtered leaves (Alg. 3), generate the global and local training queries,
+ * compute their targets d^L, train every filter by SGD and fit the auto-tuners
+ * on the calibration set.  Every random draw (which series a query comes from,
+ * its noise, the initial weights, the epoch shuffles) is taken from the
+ * library's counter-based generator (Philox4x32-10) under `seed`, so a build is
+ * reproducible bit for bit on the same device. */
+typedef struct {
+  int32_t n_filters;        /* > 0: the n_filters largest leaves (Alg. 3 with th = 0);
+                               -1: Alg. 3 with this device's measured t^F, t^S (a, mem_cap) */
+  double a;                 /* Alg. 3: 1 / p^F (2 in the paper) */
+  int64_t mem_cap;          /* Alg. 3: device bytes available to filters */
+  int32_t hidden;           /* hidden width h (0 = m, Sec. 5.1) */
+  int32_t n_train;          /* training queries per filter, global + local (2000) */
+  double global_local_ratio;/* global : local (3 -> 1500 global, 500 local per leaf);
+                               +inf: global queries only (the ablation without local data) */
+  double val_frac;          /* validation share of both kinds (0.2); the global validation
+                               queries are the calibration set of Alg. 4 */
+  double noise_lo, noise_hi;/* per-query noise sigma ~ U[noise_lo, noise_hi] (0.1, 0.4) */
+  int32_t batch;            /* SGD minibatch (64) */
+  int32_t max_epochs;       /* (1000) */
+  int32_t patience;         /* epochs without a lower validation loss before lr /= 10 (10) */
+  double lr0, lr_min;       /* 0.01, 1e-5 */
+  int32_t n_kclasses;       /* auto-tuner k-classes, ascending, 1..LEAFI_MAX_KCLASSES */
+  int32_t kclasses[LEAFI_MAX_KCLASSES];
+  uint64_t seed;
+} leafi_train_params;
+
+typedef struct {
+  int32_t n_filters;                      /* filters installed */
+  int32_t n_gtrain, n_gval, n_ltrain, n_lval;
+  double select_threshold;                /* Alg. 3's th (series) when n_filters = -1, else 0 */
+  double seconds_select, seconds_generate, seconds_train, seconds_calibrate;
+} leafi_train_report;
+
+/* Alg. 1 on the index (the index's previous filters and auto-tuners are
+ * replaced).  Counts: n_global = round(n_train * r / (r + 1)), n_local =
+ * n_train - n_global, validation = round(val_frac * count) of each kind
+ * (n_gval >= 1).  epochs_run / best_val (nullable host arrays with room for
+ * n_leaves entries) receive each filter's epochs and best validation loss.
+ * LEAFI_EINVAL for bad parameters (nothing is changed). */
+leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* params,
+                                 int32_t* epochs_run, double* best_val,
+                                 leafi_train_report* report);
+
+/* Inspection exports of Alg. 1's draws, for parity checks.  The training
+ * queries leafi_train_filters generates for the filtered leaves filter_leaf[F]:
+ * Qg [n_global][m], Ql [F][n_local][m] (float32, host or device) and, nullable,
+ * the original ids they come from, gpick [n_global], lpick [F][n_local]. */
+leafi_status leafi_training_queries(leafi_index* index, const leafi_train_params* params,
+                                    const int32_t* filter_leaf, int32_t F, float* Qg, float* Ql,
+                                    int64_t* gpick, int64_t* lpick);
+/* Initial weights of F filters of width h (layouts of leafi_set_filters). */
+leafi_status leafi_initial_weights(leafi_index* index, int32_t F, int32_t h, uint64_t seed,
+                                   float* W1, float* b1, float* w2, float* b2);
+/* The SGD shuffles: int32 [epochs][n], each row a permutation of [0, n). */
+leafi_status leafi_epoch_permutations(int32_t epochs, int32_t n, uint64_t seed, int32_t* perms);
+
+/* SGD parameters of leafi_train_filters_on. */
 typedef struct {
   int32_t n_gtrain, n_gval; /* global queries: first n_gtrain train, next n_gval validate */
   int32_t n_ltrain, n_lval; /* local queries per filter, same split */
@@ -243,16 +304,24 @@ typedef struct {
   int32_t max_epochs;       /* <= 1000 in the paper */
   int32_t patience;         /* epochs without a lower validation loss before lr /= 10 */
   double lr0, lr_min;       /* 0.01 and 1e-5 in the paper */
-} leafi_train_params;
+} leafi_sgd_params;
 
-/* Alg. 1 lines 3-9: computes the targets of Qg [n_gtrain+n_gval][m] and
- * Ql [F][n_ltrain+n_lval][m] on the device, then trains every filter by SGD
- * on the MSE loss from the currently installed weights, one shuffle
+/* Alg. 1 lines 3-9 on queries the caller supplies (inspection export for
+ * parity checks): computes the targets of Qg [n_gtrain+n_gval][m] and
+ * Ql [F][n_ltrain+n_lval][m] on the device, then trains every installed
+ * filter by SGD on the MSE loss from its current weights, one shuffle
  * perms [max_epochs][n_gtrain+n_ltrain] per epoch; keeps the weights of the
  * lowest validation loss.  epochs_run / best_val (nullable, host, [F]). */
-leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p,
-                                 const float* Qg, const float* Ql, const int32_t* perms,
-                                 int32_t* epochs_run, double* best_val);
+leafi_status leafi_train_filters_on(leafi_index* index, const leafi_sgd_params* p,
+                                    const float* Qg, const float* Ql, const int32_t* perms,
+                                    int32_t* epochs_run, double* best_val);
+
+/* float64 z-normalisation (population sigma; a row whose sigma is below 1e-8
+ * becomes zeros) of n rows of m floats on `device`: out = (x - mean) / sigma.
+ * x and out may be host or device arrays and may be the same array.  The
+ * paper's series and queries are z-normalised; this is the library's way to
+ * meet that input contract. */
+leafi_status leafi_znormalize(const float* x, int64_t n, int32_t m, float* out, int32_t device);
 
 /* ------------------------------------------------------------------ */
 /* Conformal auto-tuners (Sec. 4.4, Alg. 4)                            */

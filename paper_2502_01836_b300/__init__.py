@@ -26,6 +26,9 @@ __all__ = [
     "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS", "EAGAIN", "ServeParams", "ServeStats",
     "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
     "leafi_serve_stop", "leafi_select_leaves_auto", "SelectParams", "SelectReport",
+    "SgdParams", "TrainReport", "leafi_train_filters_on", "leafi_training_queries",
+    "leafi_initial_weights", "leafi_epoch_permutations", "leafi_znormalize",
+    "leafi_get_filter_leaves",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,7 +50,9 @@ EXPORTED_SYMBOLS = [
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
     "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases",
     "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
-    "leafi_serve_stop", "leafi_select_leaves_auto",
+    "leafi_serve_stop", "leafi_select_leaves_auto", "leafi_train_filters_on",
+    "leafi_training_queries", "leafi_initial_weights", "leafi_epoch_permutations",
+    "leafi_znormalize", "leafi_get_filter_leaves",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -82,6 +87,33 @@ class IndexInfo(C.Structure):
 
 
 class TrainParams(C.Structure):
+    """Alg. 1 parameters of leafi_train_filters (defaults: the paper's setup)."""
+    _fields_ = [("n_filters", C.c_int32), ("a", C.c_double), ("mem_cap", C.c_int64),
+                ("hidden", C.c_int32), ("n_train", C.c_int32), ("global_local_ratio", C.c_double),
+                ("val_frac", C.c_double), ("noise_lo", C.c_double), ("noise_hi", C.c_double),
+                ("batch", C.c_int32), ("max_epochs", C.c_int32), ("patience", C.c_int32),
+                ("lr0", C.c_double), ("lr_min", C.c_double), ("n_kclasses", C.c_int32),
+                ("kclasses", C.c_int32 * 4), ("seed", C.c_uint64)]
+
+    def __init__(self, n_filters=100, a=2.0, mem_cap=8 << 30, hidden=0, n_train=2000,
+                 global_local_ratio=3.0, val_frac=0.2, noise_lo=0.1, noise_hi=0.4, batch=64,
+                 max_epochs=1000, patience=10, lr0=0.01, lr_min=1e-5, kclasses=(1,),
+                 seed=2502018361):
+        kc = (C.c_int32 * 4)(*(list(kclasses) + [0] * (4 - len(kclasses))))
+        super().__init__(n_filters, a, mem_cap, hidden, n_train, global_local_ratio, val_frac,
+                         noise_lo, noise_hi, batch, max_epochs, patience, lr0, lr_min,
+                         len(kclasses), kc, seed)
+
+
+class TrainReport(C.Structure):
+    _fields_ = [("n_filters", C.c_int32), ("n_gtrain", C.c_int32), ("n_gval", C.c_int32),
+                ("n_ltrain", C.c_int32), ("n_lval", C.c_int32), ("select_threshold", C.c_double),
+                ("seconds_select", C.c_double), ("seconds_generate", C.c_double),
+                ("seconds_train", C.c_double), ("seconds_calibrate", C.c_double)]
+
+
+class SgdParams(C.Structure):
+    """SGD parameters of leafi_train_filters_on (queries supplied by the caller)."""
     _fields_ = [("n_gtrain", C.c_int32), ("n_gval", C.c_int32), ("n_ltrain", C.c_int32),
                 ("n_lval", C.c_int32), ("batch", C.c_int32), ("max_epochs", C.c_int32),
                 ("patience", C.c_int32), ("lr0", C.c_double), ("lr_min", C.c_double)]
@@ -146,7 +178,13 @@ def lib():
             "leafi_filter_predict": [vp, vp, i64, vp],
             "leafi_leaf_knn": [vp, vp, i64, vp, i32, i32, vp, vp],
             "leafi_train_targets": [vp, vp, i64, vp, i64, vp, vp],
-            "leafi_train_filters": [vp, C.POINTER(TrainParams), vp, vp, vp, vp, vp],
+            "leafi_train_filters": [vp, C.POINTER(TrainParams), vp, vp, C.POINTER(TrainReport)],
+            "leafi_train_filters_on": [vp, C.POINTER(SgdParams), vp, vp, vp, vp, vp],
+            "leafi_training_queries": [vp, C.POINTER(TrainParams), vp, i32, vp, vp, vp, vp],
+            "leafi_initial_weights": [vp, i32, i32, C.c_uint64, vp, vp, vp, vp],
+            "leafi_epoch_permutations": [i32, i32, C.c_uint64, vp],
+            "leafi_znormalize": [vp, i64, i32, vp, i32],
+            "leafi_get_filter_leaves": [vp, vp],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
@@ -332,6 +370,12 @@ def leafi_set_filters(index, filter_leaf, W1, b1, w2, b2):
                                    _ptr(w2, np.float32, "w2"), _ptr(b2, np.float32, "b2")))
 
 
+def leafi_get_filter_leaves(index):
+    out = np.zeros(max(1, leafi_get_info(index).n_filters), np.int32)
+    _check(lib().leafi_get_filter_leaves(index, out.ctypes.data))
+    return out[:leafi_get_info(index).n_filters].copy()
+
+
 def leafi_get_filters(index, W1, b1, w2, b2):
     _check(lib().leafi_get_filters(index, _ptr(W1, np.float32, "W1", True),
                                    _ptr(b1, np.float32, "b1", True),
@@ -363,13 +407,79 @@ def leafi_train_targets(index, Qg, Ql, Tg, Tl):
     return Tg, Tl
 
 
-def leafi_train_filters(index, params: TrainParams, Qg, Ql, perms, epochs_run=None,
-                        best_val=None):
-    _check(lib().leafi_train_filters(index, C.byref(params), _ptr(Qg, np.float32, "Qg"),
-                                     _ptr(Ql, np.float32, "Ql"), _ptr(perms, np.int32, "perms"),
-                                     _ptr(epochs_run, np.int32, "epochs_run", True),
-                                     _ptr(best_val, np.float64, "best_val", True)))
+def leafi_train_filters(index, params: TrainParams | None = None):
+    """Alg. 1 end to end: returns (epochs_run [F], best_val [F], report dict)."""
+    params = params or TrainParams()
+    L = leafi_get_info(index).n_leaves
+    ep = np.zeros(max(L, 1), np.int32)
+    bv = np.zeros(max(L, 1), np.float64)
+    rep = TrainReport()
+    _check(lib().leafi_train_filters(index, C.byref(params), ep.ctypes.data, bv.ctypes.data,
+                                     C.byref(rep)))
+    F = rep.n_filters
+    return ep[:F].copy(), bv[:F].copy(), {f: getattr(rep, f) for f, _ in TrainReport._fields_}
+
+
+def _alg1_counts(params: TrainParams):
+    """(n_global, n_local) as leafi_train_filters derives them."""
+    r = params.global_local_ratio
+    if np.isinf(r):
+        ng = params.n_train
+    else:
+        ng = int(np.floor(params.n_train * r / (r + 1.0) + 0.5))
+    ng = min(max(ng, 2), params.n_train)
+    return ng, params.n_train - ng
+
+
+def leafi_training_queries(index, params: TrainParams, filter_leaf):
+    """The training queries Alg. 1 generates for these leaves:
+    (Qg [ng, m], Ql [F, nl, m], gpick [ng], lpick [F, nl])."""
+    fl = np.ascontiguousarray(filter_leaf, np.int32)
+    m = leafi_get_info(index).m
+    ng, nl = _alg1_counts(params)
+    F = fl.shape[0]
+    Qg = np.zeros((ng, m), np.float32)
+    Ql = np.zeros((F, nl, m), np.float32)
+    gp = np.zeros(ng, np.int64)
+    lp = np.zeros((F, nl), np.int64)
+    _check(lib().leafi_training_queries(index, C.byref(params), fl.ctypes.data, F,
+                                        Qg.ctypes.data, Ql.ctypes.data, gp.ctypes.data,
+                                        lp.ctypes.data))
+    return Qg, Ql, gp, lp
+
+
+def leafi_initial_weights(index, F, h, seed):
+    """Initial weights (W1 [F,h,m], b1 [F,h], w2 [F,h], b2 [F]) drawn by the library."""
+    m = leafi_get_info(index).m
+    W = (np.zeros((F, h, m), np.float32), np.zeros((F, h), np.float32),
+         np.zeros((F, h), np.float32), np.zeros(F, np.float32))
+    _check(lib().leafi_initial_weights(index, F, h, seed, *(w.ctypes.data for w in W)))
+    return W
+
+
+def leafi_epoch_permutations(epochs, n, seed):
+    out = np.zeros((epochs, n), np.int32)
+    _check(lib().leafi_epoch_permutations(epochs, n, seed, out.ctypes.data))
+    return out
+
+
+def leafi_train_filters_on(index, params: SgdParams, Qg, Ql, perms, epochs_run=None,
+                           best_val=None):
+    """Alg. 1 lines 3-9 on caller-supplied queries and shuffles (parity checks)."""
+    _check(lib().leafi_train_filters_on(index, C.byref(params), _ptr(Qg, np.float32, "Qg"),
+                                        _ptr(Ql, np.float32, "Ql"), _ptr(perms, np.int32, "perms"),
+                                        _ptr(epochs_run, np.int32, "epochs_run", True),
+                                        _ptr(best_val, np.float64, "best_val", True)))
     return epochs_run, best_val
+
+
+def leafi_znormalize(x, out=None, device=0):
+    """float64 z-normalisation of the rows of x [n, m] on `device` (out may be x)."""
+    out = np.empty_like(x) if out is None else out
+    n, m = x.shape
+    _check(lib().leafi_znormalize(_ptr(x, np.float32, "x"), n, m, _ptr(out, np.float32, "out", True),
+                                  device))
+    return out
 
 
 def leafi_fit_autotuners(index, Qc, kclasses):

@@ -6,6 +6,7 @@
 #include <deque>
 #include <map>
 #include <thread>
+#include <unordered_map>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -1378,6 +1379,110 @@ leafi_status leafi_select_leaves(const leafi_index* index, int32_t n_filters, in
   });
 }
 
+}  // extern "C"
+
+namespace leafi {
+namespace {
+
+// Alg. 3 with this device's measured costs; the caller holds the index mutex
+// and has made the index's device current
+void select_auto_core(leafi_index* index, const leafi_select_params* params,
+                      int32_t* filter_leaf, leafi_select_report* report) {
+  const int h = params->hidden > 0 ? params->hidden : index->m;
+  if (h > 4096) fail(LEAFI_EINVAL, "hidden width out of range");
+  leafi_index* ix = index;
+  cudaStream_t s = ix->stream;
+  const HostTree& t = ix->tree;
+  const int m = ix->m, mp = ix->mp;
+  const int nq = (int)std::min<int64_t>(256, ix->n);
+  const float* dQ = ix->X.p;  // the first nq stored series serve as probe queries
+  cudaEvent_t e0, e1;
+  LF_CUDA(cudaEventCreate(&e0));
+  LF_CUDA(cudaEventCreate(&e1));
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{e0, e1};
+  auto timed = [&](auto&& body, int reps) {
+    for (int i = 0; i < 2; ++i) body();
+    LF_CUDA(cudaEventRecord(e0, s));
+    for (int i = 0; i < reps; ++i) body();
+    LF_CUDA(cudaEventRecord(e1, s));
+    LF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    LF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return (double)ms / 1e3 / reps;
+  };
+  // t^F: 256 probe queries against 64 probe filters through the forward the
+  // index uses (tensor cores when the width fits one MMA)
+  const int Fp = 64;
+  const int hp = (h + 15) / 16 * 16, Kq = (m + 31) / 32 * 32;
+  const bool tc = ix->scan_path == 0 && filter_tc_fits(m, h, ix->smem_optin);
+  DBuf<float> W1t, b1, w2, b2, P, Ws, Qs;
+  LF_CUDA(cudaMemsetAsync(W1t.need((size_t)Fp * m * h), 0, sizeof(float) * Fp * m * h, s));
+  LF_CUDA(cudaMemsetAsync(b1.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
+  LF_CUDA(cudaMemsetAsync(w2.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
+  LF_CUDA(cudaMemsetAsync(b2.need(Fp), 0, sizeof(float) * Fp, s));
+  P.need((size_t)nq * Fp);
+  double t_f = 0.0;
+  if (tc) {
+    launch_wsplit(W1t.p, Fp, m, h, Ws.need((size_t)2 * Fp * hp * Kq), s);
+    CUtensorMap wm, qm;
+    const int nqp = (nq + 127) / 128 * 128;
+    Qs.need((size_t)2 * nqp * Kq);
+    if (!encode_2d(&wm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws.p, (uint64_t)Kq,
+                   (uint64_t)2 * Fp * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp) ||
+        !encode_2d(&qm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Qs.p, (uint64_t)Kq, (uint64_t)2 * nqp,
+                   (uint64_t)Kq * 4, 32, 128))
+      fail(LEAFI_ECUDA, "cannot encode the probe tensor maps");
+    t_f = timed([&] {
+      launch_filter_tc(qm, wm, dQ, nq, mp, m, Fp, h, Qs.p, b1.p, w2.p, b2.p, P.p, ix->sErr.p, s);
+    }, 10);
+  } else {
+    t_f = timed([&] {
+      launch_filter_forward(dQ, nq, mp, m, Fp, h, W1t.p, b1.p, w2.p, b2.p, P.p, s);
+    }, 10);
+  }
+  t_f /= (double)nq * Fp;
+  // t^S: the same probe queries against the largest leaf, through the scan
+  int big = 0;
+  for (int l = 1; l < t.n_leaves; ++l)
+    if (t.leaf_off[l + 1] - t.leaf_off[l] > t.leaf_off[big + 1] - t.leaf_off[big]) big = l;
+  const int64_t bigsz = t.leaf_off[big + 1] - t.leaf_off[big];
+  std::vector<int32_t> lv(nq, big);
+  DBuf<int32_t> dl;
+  dl.upload(lv, s);
+  DBuf<unsigned long long> keys;
+  DBuf<int32_t> cnt;
+  double t_s = timed([&] { leaf_knn_device(ix, dQ, nq, dl.p, 1, 1, keys, cnt); }, 5);
+  t_s /= (double)nq * (double)bigsz;
+  const double th = params->a * t_f / t_s;
+  const double w = (double)((size_t)h * m + 2 * (size_t)h + 1) * 4.0 +
+                   (tc ? 2.0 * hp * Kq * 4.0 : 0.0) + 300.0 * 8.0;
+  std::vector<int32_t> idx(t.n_leaves);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    return (t.leaf_off[x + 1] - t.leaf_off[x]) > (t.leaf_off[y + 1] - t.leaf_off[y]);
+  });
+  double used = 0.0;
+  int32_t n = 0;
+  for (int j : idx) {
+    if ((double)(t.leaf_off[j + 1] - t.leaf_off[j]) >= th && used + w <= (double)params->mem_cap) {
+      filter_leaf[n++] = j;
+      used += w;
+    }
+  }
+  if (report) *report = leafi_select_report{t_f, t_s, th, w, n};
+}
+
+}  // namespace
+}  // namespace leafi
+
+extern "C" {
+
 leafi_status leafi_select_leaves_auto(leafi_index* index, const leafi_select_params* params,
                                       int32_t* filter_leaf, leafi_select_report* report) {
   return guarded([&] {
@@ -1385,143 +1490,91 @@ leafi_status leafi_select_leaves_auto(leafi_index* index, const leafi_select_par
     if (!params || !filter_leaf) fail(LEAFI_EINVAL, "NULL argument");
     if (!(params->a > 0.0)) fail(LEAFI_EINVAL, "a must be > 0");
     if (params->mem_cap < 0) fail(LEAFI_EINVAL, "mem_cap must be >= 0");
-    const int h = params->hidden > 0 ? params->hidden : index->m;
-    if (h > 4096) fail(LEAFI_EINVAL, "hidden width out of range");
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
-    leafi_index* ix = index;
-    cudaStream_t s = ix->stream;
-    const HostTree& t = ix->tree;
-    const int m = ix->m, mp = ix->mp;
-    const int nq = (int)std::min<int64_t>(256, ix->n);
-    const float* dQ = ix->X.p;  // the first nq stored series serve as probe queries
-    cudaEvent_t e0, e1;
-    LF_CUDA(cudaEventCreate(&e0));
-    LF_CUDA(cudaEventCreate(&e1));
-    struct Ev {
-      cudaEvent_t a, b;
-      ~Ev() {
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-      }
-    } evg{e0, e1};
-    auto timed = [&](auto&& body, int reps) {
-      for (int i = 0; i < 2; ++i) body();
-      LF_CUDA(cudaEventRecord(e0, s));
-      for (int i = 0; i < reps; ++i) body();
-      LF_CUDA(cudaEventRecord(e1, s));
-      LF_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.0f;
-      LF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      return (double)ms / 1e3 / reps;
-    };
-    // t^F: 256 probe queries against 64 probe filters through the forward the
-    // index uses (tensor cores when the width fits one MMA)
-    const int Fp = 64;
-    const int hp = (h + 15) / 16 * 16, Kq = (m + 31) / 32 * 32;
-    const bool tc = ix->scan_path == 0 && filter_tc_fits(m, h, ix->smem_optin);
-    DBuf<float> W1t, b1, w2, b2, P, Ws, Qs;
-    LF_CUDA(cudaMemsetAsync(W1t.need((size_t)Fp * m * h), 0, sizeof(float) * Fp * m * h, s));
-    LF_CUDA(cudaMemsetAsync(b1.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
-    LF_CUDA(cudaMemsetAsync(w2.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
-    LF_CUDA(cudaMemsetAsync(b2.need(Fp), 0, sizeof(float) * Fp, s));
-    P.need((size_t)nq * Fp);
-    double t_f = 0.0;
-    if (tc) {
-      launch_wsplit(W1t.p, Fp, m, h, Ws.need((size_t)2 * Fp * hp * Kq), s);
-      CUtensorMap wm, qm;
-      const int nqp = (nq + 127) / 128 * 128;
-      Qs.need((size_t)2 * nqp * Kq);
-      if (!encode_2d(&wm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws.p, (uint64_t)Kq,
-                     (uint64_t)2 * Fp * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp) ||
-          !encode_2d(&qm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Qs.p, (uint64_t)Kq, (uint64_t)2 * nqp,
-                     (uint64_t)Kq * 4, 32, 128))
-        fail(LEAFI_ECUDA, "cannot encode the probe tensor maps");
-      t_f = timed([&] {
-        launch_filter_tc(qm, wm, dQ, nq, mp, m, Fp, h, Qs.p, b1.p, w2.p, b2.p, P.p, ix->sErr.p, s);
-      }, 10);
-    } else {
-      t_f = timed([&] {
-        launch_filter_forward(dQ, nq, mp, m, Fp, h, W1t.p, b1.p, w2.p, b2.p, P.p, s);
-      }, 10);
-    }
-    t_f /= (double)nq * Fp;
-    // t^S: the same probe queries against the largest leaf, through the scan
-    int big = 0;
-    for (int l = 1; l < t.n_leaves; ++l)
-      if (t.leaf_off[l + 1] - t.leaf_off[l] > t.leaf_off[big + 1] - t.leaf_off[big]) big = l;
-    const int64_t bigsz = t.leaf_off[big + 1] - t.leaf_off[big];
-    std::vector<int32_t> lv(nq, big);
-    DBuf<int32_t> dl;
-    dl.upload(lv, s);
-    DBuf<unsigned long long> keys;
-    DBuf<int32_t> cnt;
-    double t_s = timed([&] { leaf_knn_device(ix, dQ, nq, dl.p, 1, 1, keys, cnt); }, 5);
-    t_s /= (double)nq * (double)bigsz;
-    const double th = params->a * t_f / t_s;
-    const double w = (double)((size_t)h * m + 2 * (size_t)h + 1) * 4.0 +
-                     (tc ? 2.0 * hp * Kq * 4.0 : 0.0) + 300.0 * 8.0;
-    std::vector<int32_t> idx(t.n_leaves);
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-      return (t.leaf_off[x + 1] - t.leaf_off[x]) > (t.leaf_off[y + 1] - t.leaf_off[y]);
-    });
-    double used = 0.0;
-    int32_t n = 0;
-    for (int j : idx) {
-      if ((double)(t.leaf_off[j + 1] - t.leaf_off[j]) >= th && used + w <= (double)params->mem_cap) {
-        filter_leaf[n++] = j;
-        used += w;
-      }
-    }
-    if (report) *report = leafi_select_report{t_f, t_s, th, w, n};
+    select_auto_core(index, params, filter_leaf, report);
   });
 }
+
+}  // extern "C"
+
+namespace leafi {
+namespace {
+
+// installs filters on the leaves fl (host) with hidden width h: validates the
+// leaves, sizes the weight buffers (contents left to the caller), uploads the
+// leaf <-> filter tables and clears training and auto-tuner state.  The caller
+// holds the index mutex with the device current.
+void install_filters(leafi_index* index, const std::vector<int32_t>& fl, int h) {
+  const int F = (int)fl.size();
+  if (F < 1 || F > index->tree.n_leaves) fail(LEAFI_EINVAL, "F out of range");
+  if (h < 1 || h > 4096) fail(LEAFI_EINVAL, "h out of range");
+  if (index->m > 1024) fail(LEAFI_EINVAL, "filters support m <= 1024");
+  std::vector<int32_t> leaf_filter(index->tree.n_leaves, -1);
+  for (int f = 0; f < F; ++f) {
+    if (fl[f] < 0 || fl[f] >= index->tree.n_leaves) fail(LEAFI_EINVAL, "filter leaf out of range");
+    if (leaf_filter[fl[f]] >= 0) fail(LEAFI_EINVAL, "leaf %d has two filters", fl[f]);
+    leaf_filter[fl[f]] = f;
+  }
+  index->drop_graphs();
+  cudaStream_t s = index->stream;
+  const int m = index->m;
+  index->W1t.need((size_t)F * m * h);
+  index->b1.need((size_t)F * h);
+  index->w2.need((size_t)F * h);
+  index->b2.need(F);
+  index->d_filter_leaf.upload(fl, s);
+  index->d_leaf_filter.upload(leaf_filter, s);
+  LF_CUDA(cudaStreamSynchronize(s));
+  index->filter_leaf = fl;
+  index->F = F;
+  index->h = h;
+  index->ws_dirty = true;
+  index->trained = false;
+  index->nc = 0;
+  index->nk = 0;
+}
+
+}  // namespace
+}  // namespace leafi
+
+extern "C" {
 
 leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F, int32_t h,
                                const float* W1, const float* b1, const float* w2, const float* b2) {
   return guarded([&] {
     require_device(index);
     if (F < 1 || F > index->tree.n_leaves) fail(LEAFI_EINVAL, "F out of range");
-    if (h < 1 || h > 4096) fail(LEAFI_EINVAL, "h out of range");
-    if (index->m > 1024) fail(LEAFI_EINVAL, "filters support m <= 1024");
     if (!filter_leaf || !W1 || !b1 || !w2 || !b2) fail(LEAFI_EINVAL, "NULL filter argument");
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
-    index->drop_graphs();
     cudaStream_t s = index->stream;
     std::vector<int32_t> fl;
     to_host(fl, filter_leaf, F, s);
-    std::vector<int32_t> leaf_filter(index->tree.n_leaves, -1);
-    for (int f = 0; f < F; ++f) {
-      if (fl[f] < 0 || fl[f] >= index->tree.n_leaves) fail(LEAFI_EINVAL, "filter leaf out of range");
-      if (leaf_filter[fl[f]] >= 0) fail(LEAFI_EINVAL, "leaf %d has two filters", fl[f]);
-      leaf_filter[fl[f]] = f;
-    }
+    install_filters(index, fl, h);
     const int m = index->m;
     DBuf<float> tmp;
     const float* dW = to_device(W1, (size_t)F * h * m, tmp, s);
-    float* Wt = index->W1t.need((size_t)F * m * h);
     const size_t tot = (size_t)F * h * m;
-    transpose_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dW, Wt, F, h, m);
+    transpose_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dW, index->W1t.p, F, h, m);
     LF_CHECK_LAUNCH();
     DBuf<float> t1, t2, t3;
     const float* db1 = to_device(b1, (size_t)F * h, t1, s);
     const float* dw2 = to_device(w2, (size_t)F * h, t2, s);
     const float* db2 = to_device(b2, (size_t)F, t3, s);
-    LF_CUDA(cudaMemcpyAsync(index->b1.need((size_t)F * h), db1, sizeof(float) * F * h, cudaMemcpyDeviceToDevice, s));
-    LF_CUDA(cudaMemcpyAsync(index->w2.need((size_t)F * h), dw2, sizeof(float) * F * h, cudaMemcpyDeviceToDevice, s));
-    LF_CUDA(cudaMemcpyAsync(index->b2.need(F), db2, sizeof(float) * F, cudaMemcpyDeviceToDevice, s));
-    index->d_filter_leaf.upload(fl, s);
-    index->d_leaf_filter.upload(leaf_filter, s);
+    LF_CUDA(cudaMemcpyAsync(index->b1.p, db1, sizeof(float) * F * h, cudaMemcpyDeviceToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(index->w2.p, dw2, sizeof(float) * F * h, cudaMemcpyDeviceToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(index->b2.p, db2, sizeof(float) * F, cudaMemcpyDeviceToDevice, s));
     LF_CUDA(cudaStreamSynchronize(s));
-    index->filter_leaf = fl;
-    index->F = F;
-    index->h = h;
-    index->ws_dirty = true;
-    index->trained = false;
-    index->nc = 0;
-    index->nk = 0;
+  });
+}
+
+leafi_status leafi_get_filter_leaves(const leafi_index* index, int32_t* filter_leaf) {
+  return guarded([&] {
+    require_device(index);
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    if (!filter_leaf) fail(LEAFI_EINVAL, "NULL output");
+    std::memcpy(filter_leaf, index->filter_leaf.data(), sizeof(int32_t) * index->F);
   });
 }
 
@@ -1663,92 +1716,190 @@ leafi_status leafi_train_targets(leafi_index* index, const float* Qg, int64_t ng
   });
 }
 
-leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p, const float* Qg,
-                                 const float* Ql, const int32_t* perms, int32_t* epochs_run,
-                                 double* best_val) {
+}  // extern "C"
+
+namespace leafi {
+namespace {
+
+// Alg. 1 lines 3-9 on staged queries: targets of Qg [ng][mp] and Ql
+// [F][nl][mp] on the device, then SGD of every filter from its installed
+// weights with one shuffle per epoch (hperm [max_epochs][n_gtrain + n_ltrain]).
+// The caller holds the index mutex with the device current.
+void train_core(leafi_index* index, const leafi_sgd_params* p, const float* dQg, const float* dQl,
+                const std::vector<int32_t>& hperm, int32_t* epochs_run, double* best_val) {
+  index->drop_graphs();
+  cudaStream_t s = index->stream;
+  const int F = index->F, h = index->h, m = index->m;
+  const int ng = p->n_gtrain + p->n_gval, nl = p->n_ltrain + p->n_lval;
+  DBuf<float> tg, tl;
+  float* dTg = tg.need((size_t)ng * F);
+  float* dTl = tl.need((size_t)std::max(nl, 1) * F);
+  train_targets_device(index, dQg, ng, dQl, nl, dTg, dTl);
+  const size_t ntr = (size_t)p->n_gtrain + p->n_ltrain;
+  for (int32_t v : hperm)
+    if (v < 0 || (size_t)v >= ntr) fail(LEAFI_EINVAL, "perms entry %d outside [0, %zu)", v, ntr);
+  DBuf<int32_t> dperm;
+  dperm.upload(hperm, s);
+  DBuf<float> bW, bb1, bw2, bb2;
+  DBuf<int32_t> dep;
+  DBuf<double> dbv;
+  // number of lr divisions before stopping: the last one keeping lr >= lr_min
+  int max_decays = 0;
+  {
+    double lr = p->lr0;
+    for (;;) {
+      lr /= 10.0;
+      if (lr < p->lr_min * (1.0 - 1e-9)) break;
+      ++max_decays;
+    }
+  }
+  TrainArgs a;
+  a.F = F;
+  a.h = h;
+  a.m = m;
+  a.mp = index->mp;
+  a.n_gtrain = p->n_gtrain;
+  a.n_gval = p->n_gval;
+  a.n_ltrain = p->n_ltrain;
+  a.n_lval = p->n_lval;
+  a.batch = p->batch;
+  a.max_epochs = p->max_epochs;
+  a.patience = p->patience;
+  a.max_decays = max_decays;
+  a.lr0 = (float)p->lr0;
+  a.Qg = dQg;
+  a.Ql = dQl;
+  a.Tg = dTg;
+  a.Tl = dTl;
+  a.perms = dperm.p;
+  a.W1t = index->W1t.p;
+  a.b1 = index->b1.p;
+  a.w2 = index->w2.p;
+  a.b2 = index->b2.p;
+  a.bW1t = bW.need((size_t)F * m * h);
+  a.bb1 = bb1.need((size_t)F * h);
+  a.bw2 = bw2.need((size_t)F * h);
+  a.bb2 = bb2.need(F);
+  a.epochs_run = dep.need(F);
+  a.best_val = dbv.need(F);
+  launch_train(a, s);
+  index->ws_dirty = true;
+  std::vector<int32_t> hep(F);
+  std::vector<double> hbv(F);
+  LF_CUDA(cudaMemcpyAsync(hep.data(), a.epochs_run, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaMemcpyAsync(hbv.data(), a.best_val, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaStreamSynchronize(s));
+  if (epochs_run) std::memcpy(epochs_run, hep.data(), sizeof(int32_t) * F);
+  if (best_val) std::memcpy(best_val, hbv.data(), sizeof(double) * F);
+  index->trained = true;
+  index->nc = 0;
+  index->nk = 0;
+}
+
+void check_sgd_params(const leafi_sgd_params* p) {
+  if (p->n_gtrain < 0 || p->n_gval < 1 || p->n_ltrain < 0 || p->n_lval < 0 ||
+      p->n_gtrain + p->n_ltrain < 1 || p->batch < 1 || p->max_epochs < 1 || p->patience < 1 ||
+      !(p->lr0 > 0) || !(p->lr_min > 0) || p->lr_min > p->lr0)
+    fail(LEAFI_EINVAL, "bad training parameters");
+}
+
+void check_kclasses(const int32_t* kclasses, int32_t nk) {
+  if (nk < 1 || nk > LEAFI_MAX_KCLASSES || !kclasses) fail(LEAFI_EINVAL, "bad k-classes");
+  for (int i = 0; i < nk; ++i) {
+    if (kclasses[i] < 1 || kclasses[i] > LEAFI_MAX_K) fail(LEAFI_EINVAL, "k-class out of range");
+    if (i && kclasses[i] <= kclasses[i - 1]) fail(LEAFI_EINVAL, "k-classes must ascend");
+  }
+}
+
+// Alg. 4 on staged calibration queries dQ [nc][mp] for the k-classes; the
+// caller holds the index mutex with the device current
+void fit_core(leafi_index* index, const float* dQ, int64_t nc, const int32_t* kclasses,
+              int32_t nk) {
+  if (nc < 1 || nc > calib_max_sort()) fail(LEAFI_EINVAL, "nc must be in [1, %d]", calib_max_sort());
+  check_kclasses(kclasses, nk);
+  const int L = index->tree.n_leaves;
+  index->drop_graphs();
+  cudaStream_t s = index->stream;
+  const int F = index->F;
+  const int kmax = kclasses[nk - 1];
+  DBuf<double> lb2;
+  DBuf<int32_t> route;
+  compute_bounds(index, dQ, (int)nc, lb2.need((size_t)nc * L), route.need(nc));
+  std::vector<int32_t> lv((size_t)nc * L);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int l = 0; l < L; ++l) lv[(size_t)c * L + l] = l;
+  DBuf<int32_t> dl;
+  dl.upload(lv, s);
+  DBuf<unsigned long long> lk_keys;
+  DBuf<int32_t> lk_cnt;
+  leaf_knn_device(index, dQ, (int)nc, dl.p, L, kmax, lk_keys, lk_cnt);
+  DBuf<float> P;
+  ensure_wsplit(index);
+  filter_forward(index, dQ, (int)nc, P.need((size_t)nc * F));
+  double* alpha = index->alpha.need((size_t)F * nc);
+  double* qprime = index->qprime.need((size_t)nk * nc);
+  DBuf<int32_t> ord, cnt_true;
+  DBuf<unsigned long long> work;
+  DBuf<long long> hits;
+  DBuf<unsigned char> order_tmp;
+  CalibArgs a;
+  a.order_scratch = L > calib_max_sort() ? order_tmp.need(leaf_order_scratch((int)nc, L)) : nullptr;
+  a.nc = (int)nc;
+  a.L = L;
+  a.F = F;
+  a.W = index->wave;
+  a.lb2 = lb2.p;
+  a.route = route.p;
+  a.lk = lk_keys.p;
+  a.lk_stride = kmax;
+  a.P = P.p;
+  a.filter_leaf = index->d_filter_leaf.p;
+  a.leaf_filter = index->d_leaf_filter.p;
+  a.alpha = alpha;
+  a.ord = ord.need((size_t)nc * L);
+  a.cnt_true = cnt_true.need((size_t)nc * L);
+  a.hits = hits.need(nc);
+  a.kc = 1;
+  launch_calib_alpha(a, s);
+  for (int ci = 0; ci < nk; ++ci) {
+    a.kc = kclasses[ci];
+    a.kk = (int)std::min<int64_t>(a.kc, index->n);
+    a.work = work.need(std::max((size_t)nc * nc * a.kc, (size_t)nc * L / 2 + 1));
+    a.qprime = qprime + (size_t)ci * nc;
+    launch_calib_sim(a, s);
+  }
+  std::vector<int32_t> kc(kclasses, kclasses + nk);
+  index->d_kclasses.upload(kc, s);
+  LF_CUDA(cudaStreamSynchronize(s));
+  index->nc = (int)nc;
+  index->nk = nk;
+  for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? kclasses[i] : 0;
+}
+
+}  // namespace
+}  // namespace leafi
+
+extern "C" {
+
+leafi_status leafi_train_filters_on(leafi_index* index, const leafi_sgd_params* p, const float* Qg,
+                                    const float* Ql, const int32_t* perms, int32_t* epochs_run,
+                                    double* best_val) {
   return guarded([&] {
     require_device(index);
     if (!p || !Qg || !Ql || !perms) fail(LEAFI_EINVAL, "NULL argument");
     if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
-    if (p->n_gtrain < 0 || p->n_gval < 1 || p->n_ltrain < 0 || p->n_lval < 0 ||
-        p->n_gtrain + p->n_ltrain < 1 || p->batch < 1 || p->max_epochs < 1 || p->patience < 1 ||
-        !(p->lr0 > 0) || !(p->lr_min > 0) || p->lr_min > p->lr0)
-      fail(LEAFI_EINVAL, "bad training parameters");
+    check_sgd_params(p);
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
-    index->drop_graphs();
     cudaStream_t s = index->stream;
-    const int F = index->F, h = index->h, m = index->m;
+    const int F = index->F;
     const int ng = p->n_gtrain + p->n_gval, nl = p->n_ltrain + p->n_lval;
-    DBuf<float> qg, ql, tg, tl;
+    DBuf<float> qg, ql;
     const float* dQg = stage_queries(index, Qg, ng, qg);
     const float* dQl = stage_queries(index, Ql, (int64_t)F * nl, ql);
-    float* dTg = tg.need((size_t)ng * F);
-    float* dTl = tl.need((size_t)std::max(nl, 1) * F);
-    train_targets_device(index, dQg, ng, dQl, nl, dTg, dTl);
-    // every shuffle entry must index the training set: checked on the host
-    const size_t ntr = (size_t)p->n_gtrain + p->n_ltrain;
     std::vector<int32_t> hperm;
-    to_host(hperm, perms, (size_t)p->max_epochs * ntr, s);
-    for (int32_t v : hperm)
-      if (v < 0 || (size_t)v >= ntr) fail(LEAFI_EINVAL, "perms entry %d outside [0, %zu)", v, ntr);
-    DBuf<int32_t> dperm;
-    dperm.upload(hperm, s);
-    const int32_t* dP = dperm.p;
-    DBuf<float> bW, bb1, bw2, bb2;
-    DBuf<int32_t> dep;
-    DBuf<double> dbv;
-    // number of lr divisions before stopping: the last one keeping lr >= lr_min
-    int max_decays = 0;
-    {
-      double lr = p->lr0;
-      for (;;) {
-        lr /= 10.0;
-        if (lr < p->lr_min * (1.0 - 1e-9)) break;
-        ++max_decays;
-      }
-    }
-    TrainArgs a;
-    a.F = F;
-    a.h = h;
-    a.m = m;
-    a.mp = index->mp;
-    a.n_gtrain = p->n_gtrain;
-    a.n_gval = p->n_gval;
-    a.n_ltrain = p->n_ltrain;
-    a.n_lval = p->n_lval;
-    a.batch = p->batch;
-    a.max_epochs = p->max_epochs;
-    a.patience = p->patience;
-    a.max_decays = max_decays;
-    a.lr0 = (float)p->lr0;
-    a.Qg = dQg;
-    a.Ql = dQl;
-    a.Tg = dTg;
-    a.Tl = dTl;
-    a.perms = dP;
-    a.W1t = index->W1t.p;
-    a.b1 = index->b1.p;
-    a.w2 = index->w2.p;
-    a.b2 = index->b2.p;
-    a.bW1t = bW.need((size_t)F * m * h);
-    a.bb1 = bb1.need((size_t)F * h);
-    a.bw2 = bw2.need((size_t)F * h);
-    a.bb2 = bb2.need(F);
-    a.epochs_run = dep.need(F);
-    a.best_val = dbv.need(F);
-    launch_train(a, s);
-    index->ws_dirty = true;
-    std::vector<int32_t> hep(F);
-    std::vector<double> hbv(F);
-    LF_CUDA(cudaMemcpyAsync(hep.data(), a.epochs_run, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
-    LF_CUDA(cudaMemcpyAsync(hbv.data(), a.best_val, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
-    LF_CUDA(cudaStreamSynchronize(s));
-    if (epochs_run) std::memcpy(epochs_run, hep.data(), sizeof(int32_t) * F);
-    if (best_val) std::memcpy(best_val, hbv.data(), sizeof(double) * F);
-    index->trained = true;
-    index->nc = 0;
-    index->nk = 0;
+    to_host(hperm, perms, (size_t)p->max_epochs * (p->n_gtrain + p->n_ltrain), s);
+    train_core(index, p, dQg, dQl, hperm, epochs_run, best_val);
   });
 }
 
@@ -1759,72 +1910,273 @@ leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t n
     if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
     check_queries(index, Qc, nc);
     if (nc < 1 || nc > calib_max_sort()) fail(LEAFI_EINVAL, "nc must be in [1, %d]", calib_max_sort());
-    if (nk < 1 || nk > LEAFI_MAX_KCLASSES || !kclasses) fail(LEAFI_EINVAL, "bad k-classes");
-    for (int i = 0; i < nk; ++i) {
-      if (kclasses[i] < 1 || kclasses[i] > LEAFI_MAX_K) fail(LEAFI_EINVAL, "k-class out of range");
-      if (i && kclasses[i] <= kclasses[i - 1]) fail(LEAFI_EINVAL, "k-classes must ascend");
-    }
-    const int L = index->tree.n_leaves;
+    check_kclasses(kclasses, nk);
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
-    index->drop_graphs();
-    cudaStream_t s = index->stream;
-    const int F = index->F;
-    const int kmax = kclasses[nk - 1];
     DBuf<float> qtmp;
     const float* dQ = stage_queries(index, Qc, nc, qtmp);
-    DBuf<double> lb2;
-    DBuf<int32_t> route;
-    compute_bounds(index, dQ, (int)nc, lb2.need((size_t)nc * L), route.need(nc));
-    std::vector<int32_t> lv((size_t)nc * L);
-    for (int64_t c = 0; c < nc; ++c)
-      for (int l = 0; l < L; ++l) lv[(size_t)c * L + l] = l;
-    DBuf<int32_t> dl;
-    dl.upload(lv, s);
-    DBuf<unsigned long long> lk_keys;
-    DBuf<int32_t> lk_cnt;
-    leaf_knn_device(index, dQ, (int)nc, dl.p, L, kmax, lk_keys, lk_cnt);
-    DBuf<float> P;
-    ensure_wsplit(index);
-    filter_forward(index, dQ, (int)nc, P.need((size_t)nc * F));
-    double* alpha = index->alpha.need((size_t)F * nc);
-    double* qprime = index->qprime.need((size_t)nk * nc);
-    DBuf<int32_t> ord, cnt_true;
-    DBuf<unsigned long long> work;
-    DBuf<long long> hits;
-    DBuf<unsigned char> order_tmp;
-    CalibArgs a;
-    a.order_scratch = L > calib_max_sort() ? order_tmp.need(leaf_order_scratch((int)nc, L)) : nullptr;
-    a.nc = (int)nc;
-    a.L = L;
-    a.F = F;
-    a.W = index->wave;
-    a.lb2 = lb2.p;
-    a.route = route.p;
-    a.lk = lk_keys.p;
-    a.lk_stride = kmax;
-    a.P = P.p;
-    a.filter_leaf = index->d_filter_leaf.p;
-    a.leaf_filter = index->d_leaf_filter.p;
-    a.alpha = alpha;
-    a.ord = ord.need((size_t)nc * L);
-    a.cnt_true = cnt_true.need((size_t)nc * L);
-    a.hits = hits.need(nc);
-    a.kc = 1;
-    launch_calib_alpha(a, s);
-    for (int ci = 0; ci < nk; ++ci) {
-      a.kc = kclasses[ci];
-      a.kk = (int)std::min<int64_t>(a.kc, index->n);
-      a.work = work.need(std::max((size_t)nc * nc * a.kc, (size_t)nc * L / 2 + 1));
-      a.qprime = qprime + (size_t)ci * nc;
-      launch_calib_sim(a, s);
+    fit_core(index, dQ, nc, kclasses, nk);
+  });
+}
+
+}  // extern "C"
+
+namespace leafi {
+namespace {
+
+struct Alg1Counts {
+  int ng, nl, n_gtrain, n_gval, n_ltrain, n_lval;
+};
+
+Alg1Counts alg1_counts(const leafi_train_params* p) {
+  if (p->n_train < 2 || !(p->global_local_ratio > 0.0) || !(p->val_frac > 0.0) ||
+      !(p->val_frac < 1.0) || !(p->noise_lo >= 0.0) || !(p->noise_hi >= p->noise_lo))
+    fail(LEAFI_EINVAL, "bad training-query parameters");
+  Alg1Counts c;
+  const double r = p->global_local_ratio;
+  // an infinite ratio means global queries only (the paper's ablation without local data)
+  c.ng = std::isinf(r) ? p->n_train : (int)std::floor((double)p->n_train * r / (r + 1.0) + 0.5);
+  c.ng = std::min(std::max(c.ng, 2), p->n_train);
+  c.nl = p->n_train - c.ng;
+  c.n_gval = std::min(std::max((int)std::floor(p->val_frac * c.ng + 0.5), 1), c.ng - 1);
+  c.n_gtrain = c.ng - c.n_gval;
+  c.n_lval = std::min((int)std::floor(p->val_frac * c.nl + 0.5), c.nl);
+  c.n_ltrain = c.nl - c.n_lval;
+  return c;
+}
+
+// Alg. 1 lines 2 and 6 for the leaves fl: rows [ng + F*nl][mp] of out, the
+// global queries first, then filter by filter; picks (original ids) to gpick
+// [ng] and lpick [F][nl] when given.  Caller holds the mutex, device current.
+void generate_training_queries(leafi_index* ix, const leafi_train_params* p, const Alg1Counts& c,
+                               const std::vector<int32_t>& fl, DBuf<float>& out,
+                               std::vector<int64_t>* gpick, std::vector<int64_t>* lpick) {
+  const HostTree& t = ix->tree;
+  const int F = (int)fl.size();
+  cudaStream_t s = ix->stream;
+  const int64_t rows = (int64_t)c.ng + (int64_t)F * c.nl;
+  if (rows > (int64_t)std::numeric_limits<int32_t>::max() / 2)
+    fail(LEAFI_EINVAL, "too many training queries");
+  if ((int64_t)c.ng > t.n) fail(LEAFI_EINVAL, "more global queries (%d) than series", c.ng);
+  std::vector<int64_t> pos((size_t)rows);
+  // global picks: distinct original ids, then their storage positions
+  std::vector<int64_t> g((size_t)c.ng);
+  gen_floyd(p->seed, kTagGPick, 0, (uint64_t)t.n, c.ng, g.data());
+  {
+    std::unordered_map<int64_t, std::vector<int>> want;
+    want.reserve((size_t)c.ng * 2);
+    for (int i = 0; i < c.ng; ++i) want[g[i]].push_back(i);
+    for (int64_t q = 0; q < t.n; ++q) {
+      auto it = want.find(t.order[q]);
+      if (it != want.end())
+        for (int i : it->second) pos[i] = q;
     }
-    std::vector<int32_t> kc(kclasses, kclasses + nk);
-    index->d_kclasses.upload(kc, s);
+  }
+  // local picks: ranks among a leaf's members (ascending ids = storage order)
+  std::vector<int64_t> r((size_t)c.nl);
+  if (lpick) lpick->assign((size_t)F * c.nl, 0);
+  for (int f = 0; f < F; ++f) {
+    const int64_t lo = t.leaf_off[fl[f]], sz = t.leaf_off[fl[f] + 1] - lo;
+    if (sz >= c.nl)
+      gen_floyd(p->seed, kTagLPick, (uint32_t)(1 + f), (uint64_t)sz, c.nl, r.data());
+    else
+      gen_with_replacement(p->seed, kTagLPick, (uint32_t)(1 + f), (uint64_t)sz, c.nl, r.data());
+    for (int i = 0; i < c.nl; ++i) {
+      pos[(size_t)c.ng + (size_t)f * c.nl + i] = lo + r[i];
+      if (lpick) (*lpick)[(size_t)f * c.nl + i] = t.order[lo + r[i]];
+    }
+  }
+  if (gpick) *gpick = g;
+  DBuf<int64_t> dpos;
+  dpos.upload(pos, s);
+  launch_gen_queries(ix->X.p, ix->mp, ix->m, dpos.p, c.ng, c.nl, F, p->seed, p->noise_lo,
+                     p->noise_hi, out.need((size_t)std::max<int64_t>(rows, 1) * ix->mp), s);
+  LF_CUDA(cudaStreamSynchronize(s));
+}
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+}  // namespace leafi
+
+extern "C" {
+
+leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p,
+                                 int32_t* epochs_run, double* best_val,
+                                 leafi_train_report* report) {
+  return guarded([&] {
+    require_device(index);
+    if (!p) fail(LEAFI_EINVAL, "params is NULL");
+    const Alg1Counts c = alg1_counts(p);
+    leafi_sgd_params sp{c.n_gtrain, c.n_gval, c.n_ltrain, c.n_lval, p->batch, p->max_epochs,
+                        p->patience, p->lr0, p->lr_min};
+    check_sgd_params(&sp);
+    check_kclasses(p->kclasses, p->n_kclasses);
+    if (c.n_gval > calib_max_sort())
+      fail(LEAFI_EINVAL, "calibration set of %d queries exceeds %d", c.n_gval, calib_max_sort());
+    const int L = index->tree.n_leaves;
+    if (p->n_filters == 0 || p->n_filters < -1 || p->n_filters > L)
+      fail(LEAFI_EINVAL, "n_filters must be -1 or in [1, %d]", L);
+    const int h = p->hidden > 0 ? p->hidden : index->m;
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    leafi_train_report rep{};
+    auto t0 = std::chrono::steady_clock::now();
+    // line 1: SelectLeafNodes
+    std::vector<int32_t> fl;
+    if (p->n_filters > 0) {
+      std::vector<int32_t> idx(L);
+      std::iota(idx.begin(), idx.end(), 0);
+      const HostTree& t = index->tree;
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        return (t.leaf_off[x + 1] - t.leaf_off[x]) > (t.leaf_off[y + 1] - t.leaf_off[y]);
+      });
+      fl.assign(idx.begin(), idx.begin() + p->n_filters);
+    } else {
+      if (!(p->a > 0.0) || p->mem_cap < 0) fail(LEAFI_EINVAL, "bad Alg. 3 parameters");
+      leafi_select_params sel{p->a, p->mem_cap, h};
+      leafi_select_report sr{};
+      std::vector<int32_t> all(L);
+      select_auto_core(index, &sel, all.data(), &sr);
+      if (sr.n_selected < 1) fail(LEAFI_EINVAL, "Alg. 3 selected no leaf (threshold %.1f)", sr.threshold);
+      fl.assign(all.begin(), all.begin() + sr.n_selected);
+      rep.select_threshold = sr.threshold;
+    }
+    rep.seconds_select = seconds_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    install_filters(index, fl, h);
+    const int F = (int)fl.size();
+    launch_gen_weights(F, h, index->m, p->seed, index->W1t.p, index->b1.p, index->w2.p,
+                       index->b2.p, s);
+    // lines 2 and 6: GenerateGlobalQueries / GenerateLocalQueries
+    DBuf<float> Q;
+    generate_training_queries(index, p, c, fl, Q, nullptr, nullptr);
+    std::vector<int32_t> hperm((size_t)p->max_epochs * (c.n_gtrain + c.n_ltrain));
+    gen_epoch_perms(p->max_epochs, c.n_gtrain + c.n_ltrain, p->seed, hperm.data());
+    rep.seconds_generate = seconds_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    // lines 3-9: targets and training
+    const float* dQg = Q.p;
+    const float* dQl = Q.p + (size_t)c.ng * index->mp;
+    std::vector<int32_t> ep(F);
+    std::vector<double> bv(F);
+    train_core(index, &sp, dQg, dQl, hperm, ep.data(), bv.data());
+    rep.seconds_train = seconds_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    // line 10: auto-tuners on the calibration set (the global validation queries)
+    fit_core(index, dQg + (size_t)c.n_gtrain * index->mp, c.n_gval, p->kclasses, p->n_kclasses);
+    rep.seconds_calibrate = seconds_since(t0);
+    rep.n_filters = F;
+    rep.n_gtrain = c.n_gtrain;
+    rep.n_gval = c.n_gval;
+    rep.n_ltrain = c.n_ltrain;
+    rep.n_lval = c.n_lval;
+    if (epochs_run) std::memcpy(epochs_run, ep.data(), sizeof(int32_t) * F);
+    if (best_val) std::memcpy(best_val, bv.data(), sizeof(double) * F);
+    if (report) *report = rep;
+  });
+}
+
+leafi_status leafi_training_queries(leafi_index* index, const leafi_train_params* p,
+                                    const int32_t* filter_leaf, int32_t F, float* Qg, float* Ql,
+                                    int64_t* gpick, int64_t* lpick) {
+  return guarded([&] {
+    require_device(index);
+    if (!p || !Qg || (F > 0 && (!filter_leaf || !Ql))) fail(LEAFI_EINVAL, "NULL argument");
+    const Alg1Counts c = alg1_counts(p);
+    if (F < 0 || F > index->tree.n_leaves) fail(LEAFI_EINVAL, "F out of range");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    std::vector<int32_t> fl;
+    to_host(fl, filter_leaf, F, s);
+    for (int32_t l : fl)
+      if (l < 0 || l >= index->tree.n_leaves) fail(LEAFI_EINVAL, "filter leaf out of range");
+    DBuf<float> Q;
+    std::vector<int64_t> gp, lp;
+    generate_training_queries(index, p, c, fl, Q, &gp, &lp);
+    const int m = index->m, mp = index->mp;
+    LF_CUDA(cudaMemcpy2DAsync(Qg, sizeof(float) * m, Q.p, sizeof(float) * mp, sizeof(float) * m,
+                              (size_t)c.ng, on_device(Qg) ? cudaMemcpyDeviceToDevice
+                                                          : cudaMemcpyDeviceToHost, s));
+    if (F > 0 && c.nl > 0)
+      LF_CUDA(cudaMemcpy2DAsync(Ql, sizeof(float) * m, Q.p + (size_t)c.ng * mp, sizeof(float) * mp,
+                                sizeof(float) * m, (size_t)F * c.nl,
+                                on_device(Ql) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                s));
     LF_CUDA(cudaStreamSynchronize(s));
-    index->nc = (int)nc;
-    index->nk = nk;
-    for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? kclasses[i] : 0;
+    if (gpick) std::memcpy(gpick, gp.data(), sizeof(int64_t) * gp.size());
+    if (lpick && !lp.empty()) std::memcpy(lpick, lp.data(), sizeof(int64_t) * lp.size());
+  });
+}
+
+leafi_status leafi_initial_weights(leafi_index* index, int32_t F, int32_t h, uint64_t seed,
+                                   float* W1, float* b1, float* w2, float* b2) {
+  return guarded([&] {
+    require_device(index);
+    if (F < 1 || h < 1 || h > 4096) fail(LEAFI_EINVAL, "F / h out of range");
+    if (!W1 || !b1 || !w2 || !b2) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    const int m = index->m;
+    const size_t tot = (size_t)F * h * m;
+    DBuf<float> wt, w, bb1, ww2, bb2;
+    launch_gen_weights(F, h, m, seed, wt.need(tot), bb1.need((size_t)F * h),
+                       ww2.need((size_t)F * h), bb2.need(F), s);
+    transpose_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(wt.p, w.need(tot), F, m, h);
+    LF_CHECK_LAUNCH();
+    deliver(W1, w.p, tot, s);
+    deliver(b1, bb1.p, (size_t)F * h, s);
+    deliver(w2, ww2.p, (size_t)F * h, s);
+    deliver(b2, bb2.p, (size_t)F, s);
+    LF_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+leafi_status leafi_epoch_permutations(int32_t epochs, int32_t n, uint64_t seed, int32_t* perms) {
+  return guarded([&] {
+    if (epochs < 0 || n < 0 || (epochs > 0 && n > 0 && !perms)) fail(LEAFI_EINVAL, "bad arguments");
+    if (on_device(perms)) fail(LEAFI_EINVAL, "perms must be host memory");
+    gen_epoch_perms(epochs, n, seed, perms);
+  });
+}
+
+leafi_status leafi_znormalize(const float* x, int64_t n, int32_t m, float* out, int32_t device) {
+  return guarded([&] {
+    if (n < 0 || m < 1 || (n > 0 && (!x || !out))) fail(LEAFI_EINVAL, "bad arguments");
+    int ndev = 0;
+    LF_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) fail(LEAFI_EINVAL, "device %d out of range", device);
+    if (n == 0) return;
+    DeviceGuard dg(device);
+    cudaStream_t s = nullptr;
+    LF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct St {
+      cudaStream_t s;
+      ~St() { cudaStreamDestroy(s); }
+    } st{s};
+    // host rows go through the device in slabs of up to 256 MiB
+    const int64_t per = std::max<int64_t>(1, (int64_t)(256 << 20) / ((int64_t)m * 8));
+    DBuf<float> a, b;
+    const bool din = on_device(x), dout = on_device(out);
+    for (int64_t r0 = 0; r0 < n; r0 += per) {
+      const int64_t nb = std::min(per, n - r0);
+      const float* src = x + r0 * m;
+      if (!din) {
+        a.upload(src, (size_t)nb * m, s);
+        src = a.p;
+      }
+      float* dst = dout ? out + r0 * m : b.need((size_t)nb * m);
+      launch_znorm(src, m, nb, m, dst, m, s);
+      if (!dout)
+        LF_CUDA(cudaMemcpyAsync(out + r0 * m, dst, sizeof(float) * nb * m, cudaMemcpyDeviceToHost,
+                                s));
+      LF_CUDA(cudaStreamSynchronize(s));
+    }
   });
 }
 

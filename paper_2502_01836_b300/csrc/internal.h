@@ -122,6 +122,27 @@ void launch_filter_forward(const float* Q, int nq, int mp, int m, int F, int h, 
                            const float* b1, const float* w2, const float* b2, float* out,
                            cudaStream_t s);
 
+// Alg. 1 random draws (k_gen.cu): Philox4x32-10 addressed by (i, j, tag,
+// stream) under the key (seed low, seed high)
+enum : uint32_t {
+  kTagGPick = 1, kTagLPick = 2, kTagSigma = 3, kTagNoise = 4, kTagW1 = 5, kTagB1 = 6,
+  kTagW2 = 7, kTagB2 = 8, kTagPerm = 9
+};
+// k distinct values of [0, n) by Floyd's algorithm, in insertion order
+void gen_floyd(uint64_t seed, uint32_t tag, uint32_t stream, uint64_t n, int64_t k, int64_t* out);
+// k values of [0, n) drawn independently
+void gen_with_replacement(uint64_t seed, uint32_t tag, uint32_t stream, uint64_t n, int64_t k,
+                          int64_t* out);
+// one shuffle of [0, n) per epoch: indices ordered by their 64-bit draws
+void gen_epoch_perms(int epochs, int n, uint64_t seed, int32_t* perms);
+// rows [ng + F*nl][mp]: source row pos[q] of X + noise, re-z-normalised
+void launch_gen_queries(const float* X, int mp, int m, const int64_t* pos, int ng, int nl, int F,
+                        uint64_t seed, double lo, double hi, float* out, cudaStream_t s);
+void launch_gen_weights(int F, int h, int m, uint64_t seed, float* W1t, float* b1, float* w2,
+                        float* b2, cudaStream_t s);
+void launch_znorm(const float* in, int64_t in_stride, int64_t n, int m, float* out,
+                  int64_t out_stride, cudaStream_t s);
+
 struct TrainArgs {
   int F, h, m, mp;
   int n_gtrain, n_gval, n_ltrain, n_lval, batch, max_epochs, patience, max_decays;

@@ -109,3 +109,11 @@ def test_select_leaves_is_largest_first():
         assert sel.tolist() == ref
     finally:
         lf.leafi_free(idx)
+
+
+def test_epoch_permutations_equal_the_oracle():
+    """The SGD shuffles are drawn on the host by the library's Philox4x32-10:
+    bit-identical to the oracle's independent implementation."""
+    for epochs, n, seed in ((3, 1, 1), (5, 1600, 2502018361), (2, 97, 2 ** 63 + 5)):
+        got = lf.leafi_epoch_permutations(epochs, n, seed)
+        assert np.array_equal(got, O.epoch_perms(epochs, n, seed))

@@ -88,7 +88,7 @@ def test_correctness_config_100k():
             assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
         # LeaFi mode: one filter per leaf
         L = lf.leafi_get_info(idx).n_leaves
-        enh = enhance(idx, X, L, lf.TrainParams())
+        enh = enhance(idx, L)
         ids, d, st = _search(idx, Q, 1, 0.99)
         ex_ids, _ = O.knn(X, Q, 1)
         assert (ids[:, 0] == ex_ids[:, 0]).mean() >= 0.99
@@ -116,7 +116,7 @@ def test_batched_config_1m_sampled():
         bf10, bf10_d2 = O.knn(X, Q[:32], 10)
         assert np.array_equal(ids10[:32], bf10) and np.array_equal(d10[:32], np.sqrt(bf10_d2))
         # LeaFi mode, filters on the 100 largest leaves
-        enh = enhance(idx, X, 100, lf.TrainParams())
+        enh = enhance(idx, 100)
         ids, _, st = _search(idx, Q, 1, 0.99)
         assert (ids[:, 0] == ex_ids[:, 0]).mean() >= 0.99
         assert st.filter_evals == len(Q) * 100
@@ -138,8 +138,7 @@ def test_mixed_k_isax_config_reduced():
         sizes = lf.leafi_leaf_sizes(idx)
         assert sizes.max() >= 3 * max(1.0, float(np.median(sizes)))   # uneven leaves
         F = 24
-        p = lf.TrainParams(max_epochs=60, patience=5)
-        enh = enhance(idx, X, F, p, kclasses=(1, 10, 100))
+        enh = enhance(idx, F, kclasses=(1, 10, 100), keep_queries=True, max_epochs=60, patience=5)
         # the build phase: node-wise nearest-neighbour targets, bit for bit
         Ql = np.ascontiguousarray(enh.Ql[:, :40])
         Qg = np.ascontiguousarray(enh.Qg[:300])

@@ -169,10 +169,10 @@ def test_one_epoch_of_sgd_matches_oracle(ds, ltrain, lval):
     Qg, Ql = fx.training_queries(X, members, 100, ltrain + lval, seed=77)
     # a small learning rate keeps this short run away from SGD divergence, which
     # would make the comparison meaningless
-    p = lf.TrainParams(n_gtrain=80, n_gval=20, n_ltrain=ltrain, n_lval=lval, batch=16,
+    p = lf.SgdParams(n_gtrain=80, n_gval=20, n_ltrain=ltrain, n_lval=lval, batch=16,
                        max_epochs=1, patience=5, lr0=1e-3, lr_min=1e-5)
     perms = fx.epoch_permutations(1, 80 + ltrain, seed=78)
-    lf.leafi_train_filters(idx, p, Qg, Ql, perms)
+    lf.leafi_train_filters_on(idx, p, Qg, Ql, perms)
     got = tuple(np.zeros_like(a) for a in W)
     lf.leafi_get_filters(idx, *got)
     Tg, Tl = O.train_targets(t, fl, Qg, Ql)
@@ -534,8 +534,7 @@ def test_end_to_end_recall_meets_target():
     X = fx.random_walk(30000, 128, seed=51)
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=1500, wave=4))
     try:
-        p = lf.TrainParams(max_epochs=150, patience=8)
-        enh = enhance(idx, X, 12, p, kclasses=(1,))
+        enh = enhance(idx, 12, kclasses=(1,), max_epochs=150, patience=8)
         Qt = fx.test_queries(X, 400, seed=53)
         bf, _ = O.knn(X, Qt, 1)
         for target in (0.9, 0.99):

@@ -20,7 +20,7 @@ KMAX = 20
 def served():
     X = fx.random_walk(30000, M, seed=81)
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=800, wave=8, device=0))
-    enhance(idx, X, 12, lf.TrainParams(max_epochs=40, patience=4), kclasses=(1, 10, 20))
+    enhance(idx, 12, kclasses=(1, 10, 20), max_epochs=40, patience=4)
     yield X, idx
     lf.leafi_free(idx)
 

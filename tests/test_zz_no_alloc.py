@@ -46,9 +46,12 @@ def test_noalloc_rejects_oversize_and_host_arrays():
         with pytest.raises(lf.LeafiError) as e:
             lf.leafi_leaf_lower_bounds_noalloc(idx, big, out)
         assert e.value.status == 1 and "scratch" in str(e.value)
-        with pytest.raises(lf.LeafiError) as e:
+        # host arrays: refused by the wrapper, and by the C entry point itself
+        with pytest.raises(TypeError):
             lf.leafi_leaf_lower_bounds_noalloc(idx, X[:4].copy(), np.zeros((4, L)))
-        assert e.value.status == 1
+        q, o = X[:4].copy(), np.zeros((4, L))
+        st = lf.lib().leafi_leaf_lower_bounds_noalloc(idx, q.ctypes.data, 4, o.ctypes.data)
+        assert st == 1 and "device" in lf.lib().leafi_last_error().decode()
     finally:
         lf.leafi_free(idx)
 
