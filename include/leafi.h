@@ -23,7 +23,9 @@
  *     Results are ordered by (distance, original id) ascending; ties go to
  *     the lowest id; missing entries (k > n) are id -1 / +inf.
  *   - On any error nothing is written to the outputs, the status is returned
- *     and leafi_last_error() describes it.  No entry point aborts the process.
+ *     and leafi_last_error() describes it.  The one exception: a search that
+ *     returns LEAFI_ETIMEOUT may already have written some result rows, whose
+ *     contents are then unspecified.  No entry point aborts the process.
  *   - Calls on one index are serialised by an internal mutex.
  */
 #ifndef LEAFI_H
@@ -93,6 +95,20 @@ const char* leafi_last_error(void);
 /* Kernels this library has launched in this process (all indexes); a
  * diagnostic for counting device work between two points. */
 int64_t leafi_launch_count(void);
+
+/* Diagnostics for failure-detection tests (no counterpart in the paper).
+ * leafi_debug_set_lock_tries: attempts a tensor-core scan work item makes at a
+ * query's result-list lock before it gives up, sets the error word and lets the
+ * call return LEAFI_ETIMEOUT (the kernel still leaves through its normal exits
+ * and the index stays usable); 0 exhausts the budget at the first merge that
+ * needs the lock, -1 restores the default (65,536 attempts with back-off).
+ * Used by k > 1 searches.
+ * leafi_debug_fail_allocations: the `after`-th allocation from now (0 = the
+ * next one) of a device buffer, or of a host step that gates on it (host tree
+ * builds), fails as if memory were exhausted: the call returns LEAFI_ENOMEM
+ * without writing its outputs.  -1 disarms; a fired injection disarms itself. */
+leafi_status leafi_debug_set_lock_tries(leafi_index* index, int32_t tries);
+leafi_status leafi_debug_fail_allocations(int64_t after);
 
 /* Launch all later work of this index on `cuda_stream` (a cudaStream_t);
  * NULL selects the legacy default stream. */

@@ -28,7 +28,7 @@ __all__ = [
     "leafi_serve_stop", "leafi_select_leaves_auto", "SelectParams", "SelectReport",
     "SgdParams", "TrainReport", "leafi_train_filters_on", "leafi_training_queries",
     "leafi_initial_weights", "leafi_epoch_permutations", "leafi_znormalize",
-    "leafi_get_filter_leaves",
+    "leafi_get_filter_leaves", "leafi_debug_set_lock_tries", "leafi_debug_fail_allocations",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -52,7 +52,8 @@ EXPORTED_SYMBOLS = [
     "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
     "leafi_serve_stop", "leafi_select_leaves_auto", "leafi_train_filters_on",
     "leafi_training_queries", "leafi_initial_weights", "leafi_epoch_permutations",
-    "leafi_znormalize", "leafi_get_filter_leaves",
+    "leafi_znormalize", "leafi_get_filter_leaves", "leafi_debug_set_lock_tries",
+    "leafi_debug_fail_allocations",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -185,6 +186,8 @@ def lib():
             "leafi_epoch_permutations": [i32, i32, C.c_uint64, vp],
             "leafi_znormalize": [vp, i64, i32, vp, i32],
             "leafi_get_filter_leaves": [vp, vp],
+            "leafi_debug_set_lock_tries": [vp, i32],
+            "leafi_debug_fail_allocations": [i64],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
@@ -368,6 +371,16 @@ def leafi_set_filters(index, filter_leaf, W1, b1, w2, b2):
     _check(lib().leafi_set_filters(index, _ptr(filter_leaf, np.int32, "filter_leaf"), F, h,
                                    _ptr(W1, np.float32, "W1"), _ptr(b1, np.float32, "b1"),
                                    _ptr(w2, np.float32, "w2"), _ptr(b2, np.float32, "b2")))
+
+
+def leafi_debug_set_lock_tries(index, tries):
+    """Failure-detection diagnostic: result-list lock attempts (-1 = default)."""
+    _check(lib().leafi_debug_set_lock_tries(index, int(tries)))
+
+
+def leafi_debug_fail_allocations(after):
+    """Failure-detection diagnostic: make the after-th allocation from now fail (-1 disarms)."""
+    _check(lib().leafi_debug_fail_allocations(int(after)))
 
 
 def leafi_get_filter_leaves(index):

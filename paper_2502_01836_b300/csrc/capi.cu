@@ -38,6 +38,21 @@ void set_last_error(const std::string& s) { g_last_error = s; }
 namespace {
 std::atomic<long long> g_launches{0};
 }
+std::atomic<long long> g_fail_alloc_countdown{-1};
+
+bool injected_alloc_failure() {
+  long long v = g_fail_alloc_countdown.load(std::memory_order_relaxed);
+  while (v >= 0) {
+    if (g_fail_alloc_countdown.compare_exchange_weak(v, v - 1, std::memory_order_relaxed))
+      return v == 0;  // the armed allocation fails; the countdown then stays at -1
+  }
+  return false;
+}
+
+void host_alloc_gate() {
+  if (injected_alloc_failure()) throw std::bad_alloc();
+}
+
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(long long delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(); }
@@ -378,6 +393,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
     t.topk = topk;
     t.glock = ix->sc->sGlock.need(nslots);
+    t.lock_tries = ix->lock_tries;
     launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, s);
     t.err = ix->sErr.p;
     t.stat = recheck_stat;
@@ -1078,6 +1094,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     }
     if (p->device == -1) {
       // host-only: the tree alone, for inspection (series must be host memory)
+      host_alloc_gate();
       std::unique_ptr<leafi_index> ix(new leafi_index);
       ix->device = -1;
       ix->m = m;
@@ -1124,6 +1141,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
       LF_CUDA(cudaStreamSynchronize(s));
     } else {
       // the tree is built on the host from a host copy of the series
+      host_alloc_gate();
       std::vector<float> hostX;
       const float* hx = series;
       if (on_device(series)) {
@@ -1226,6 +1244,25 @@ void leafi_free(leafi_index* index) {
     delete index;
     if (prev >= 0) cudaSetDevice(prev);
   }
+}
+
+leafi_status leafi_debug_set_lock_tries(leafi_index* index, int32_t tries) {
+  return guarded([&] {
+    require_device(index);
+    if (tries < -1) fail(LEAFI_EINVAL, "tries must be >= -1");
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->drop_graphs();
+    index->lock_tries = tries < 0 ? kDefaultLockTries : tries;
+  });
+}
+
+leafi_status leafi_debug_fail_allocations(int64_t after) {
+  if (after < -1) {
+    set_last_error("after must be >= -1");
+    return LEAFI_EINVAL;
+  }
+  g_fail_alloc_countdown.store(after, std::memory_order_relaxed);
+  return LEAFI_OK;
 }
 
 leafi_status leafi_set_stream(leafi_index* index, void* cuda_stream) {

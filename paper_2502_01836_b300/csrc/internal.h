@@ -41,6 +41,14 @@ long long launches_so_far();
     LF_CUDA(cudaGetLastError());     \
   } while (0)
 
+// ------------------------------------------------ injected allocation failures
+// Diagnostics (leafi_debug_fail_allocations): when armed, the allocation that
+// finds the countdown at zero fails as if memory were exhausted (device
+// buffers: LEAFI_ENOMEM before the buffer is touched; host steps that call
+// host_alloc_gate: std::bad_alloc, reported as LEAFI_ENOMEM).
+bool injected_alloc_failure();
+void host_alloc_gate();
+
 // ------------------------------------------------------ device buffers
 // bumped whenever any DBuf reallocates: captured CUDA graphs that hold buffer
 // addresses compare it to know whether they are still valid
@@ -62,6 +70,8 @@ struct DBuf {
   // grow to at least `count` elements (contents not preserved)
   T* need(size_t count) {
     if (count <= n && p) return p;
+    if (injected_alloc_failure())
+      fail(LEAFI_ENOMEM, "device allocation of %zu bytes failed (injected)", count * sizeof(T));
     release();
     size_t c = count ? count : 1;
     LF_CUDA(cudaMalloc(&p, c * sizeof(T)));
@@ -80,6 +90,10 @@ struct DBuf {
 // keys of candidate results: (float bits of d^2) << 32 | original id.  d^2 >= 0
 // so the float bits order like the values; ties break on the lower id.
 constexpr unsigned long long kNoKey = ~0ull;
+
+// attempts a tensor-core scan work item makes at a query's result-list lock
+// before it reports a timeout (leafi_debug_set_lock_tries changes it per index)
+constexpr int kDefaultLockTries = 1 << 16;
 
 // ----------------------------------------------------------------- tables
 struct DsTables {  // device view of a DSTree
@@ -199,6 +213,7 @@ struct TcScanArgs {
   unsigned long long* topk;        // [nslots][k] ascending keys, kNoKey padded
                                    // (launch_tc_round_prep); work items merge into it
   int32_t* glock;                  // per slot lock of its list (zero at the round's start)
+  int lock_tries;                  // attempts at a slot's lock before the item reports a timeout
   int32_t* err;
   unsigned long long* stat;        // nullable: [0] += canonical re-checks
   unsigned long long* prof;        // nullable: per-phase cycle counters (16)
@@ -416,6 +431,7 @@ struct leafi_index {
   std::map<int, std::pair<int, int>> tc_plan;  // k -> (query tiles of the tensor-core scan (0: does
                                                // not fit), keys per lane quarter's lists)
 
+  int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries
   int profiling = 0;       // 0 off, 1 leaf-scan kernel times, 2 every kind + scan phases
   bool ticked = false;     // the last tick() recorded a start event
   leafi::BatchGraph* capturing = nullptr;  // entry being captured (tick/tock record into it)

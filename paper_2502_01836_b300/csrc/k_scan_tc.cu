@@ -325,10 +325,10 @@ __device__ __forceinline__ int warp_merge_keys(u64* L, int cc, int kq, u64 key, 
   return min(kq, cc + nnew);
 }
 
-// Attempts at a slot's lock before a work item reports a timeout.  The lock
-// is held for one warp-wide merge of at most 2k keys, so the limit (tens of
-// milliseconds with the back-off) is only reached if something is broken.
-constexpr int kLockTries = 1 << 16;
+// Attempts at a slot's lock before a work item reports a timeout come in
+// TcScanArgs::lock_tries (kDefaultLockTries).  The lock is held for one
+// warp-wide merge of at most 2k keys, so the default (tens of milliseconds
+// with the back-off) is only reached if something is broken.
 
 // Merge an item's ascending list B (cb entries) into the slot's top-k list gl
 // (kq entries, ascending, kNoKey padded; keys of other items and of earlier
@@ -337,13 +337,13 @@ constexpr int kLockTries = 1 << 16;
 // k-th key of k distinct scanned series (or kNoKey).  Returns false if the
 // lock could not be taken (the list is then left unchanged).
 __device__ __forceinline__ bool share_list(u64* gl, int32_t* lock, const u64* B, int cb, int kq,
-                                           u64* scratch, int lane) {
+                                           u64* scratch, int lane, int tries) {
   const u64 gk = __ldcg(&gl[kq - 1]);
   if (!(B[0] < gk)) return true;  // nothing of this item enters the list
   int got = 0;
   if (lane == 0) {
     unsigned ns = 32;
-    for (int t = 0; t < kLockTries && !got; ++t) {
+    for (int t = 0; t < tries && !got; ++t) {
       got = atomicCAS(lock, 0, 1) == 0 ? 1 : 0;
       if (!got) {
         __nanosleep(ns);
@@ -512,6 +512,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     if (lane == 0) {
       PROF_T0();
       long long g_ld = 0;
+      long long ld_cnt[2] = {0, 0};  // loads issued per stage
       uint32_t empty_ph[2] = {0u, 0u};
       bool alive = true;
       auto publish = [&](int n) -> int {
@@ -551,10 +552,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           for (int kb = 0; kb < Kp / 64; ++kb)
             dev::tma_load_2d(dst + kb * 16384, &tmap, kb * 64, r0, &S.full[st]);
           ++g_ld;
+          ++ld_cnt[st];
         }
         cur = nxt;
       }
       PROF_ADD(11);
+      // after a timeout the loads already issued may still be landing: wait
+      // (bounded) until the last one of each stage has, so that no copy writes
+      // shared memory after the block exits
+      if (*abort)
+        for (int st = 0; st < 2; ++st)
+          if (ld_cnt[st] > 0)
+            dev::mbar_wait(&S.full[st], (uint32_t)((ld_cnt[st] - 1) & 1), kWaitLimit);
     }
   } else if (warp == kQueryWarp) {
     // ------------------------------------------------ query-tile loader
@@ -621,6 +630,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     if (lane == 0) {
       PROF_T0();
       long long g_mm = 0;
+      long long bc_cnt[2] = {0, 0};  // commits to each query tile's barrier
+      int last_b = -1;
       int li = 0;
       uint32_t full_ph[2] = {0u, 0u}, bready_ph[2] = {0u, 0u}, tempty_ph[kAcc] = {0u, 0u, 0u, 0u};
       const uint64_t adesc[2] = {dev::smem_desc(dev::smem_addr(A0), 16, 1024, 2),
@@ -669,11 +680,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         }
         // the query tile is free once this item's MMAs have completed
         dev::mma_commit(&S.bempty[b]);
+        ++bc_cnt[b];
+        last_b = b;
         if (!ok) {
           atomicOr(a.err, 2);
           S.abort = 1;
         }
       }
+      // after a timeout, wait (bounded) for the last commit: every MMA issued
+      // before it has then finished reading shared memory and writing TMEM,
+      // which the block releases on exit
+      if (*abort && last_b >= 0)
+        dev::mbar_wait(&S.bempty[last_b], (uint32_t)((bc_cnt[last_b] - 1) & 1), kWaitLimit);
     }
   } else {
     // ------------------------------------------------ epilogue warps 0-7
@@ -1008,7 +1026,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           // work items admit against
           if (cc > 0 &&
               !share_list(a.topk + (size_t)S.slot[q] * a.k, a.glock + S.slot[q], lists + S.loff[q],
-                          cc, kq, lists + a.qkeys + S.loff[q], lane) &&
+                          cc, kq, lists + a.qkeys + S.loff[q], lane, a.lock_tries) &&
               lane == 0)
             atomicOr(a.err, 2);
           __syncwarp();
