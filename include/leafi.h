@@ -129,6 +129,7 @@ typedef struct {
   int64_t device_bytes;  /* device memory held by the index */
   int32_t tensor_scan;   /* 1 if leaf scans run on the tensor cores */
   int32_t scan_row_bytes;/* bytes the leaf scan streams per series (fp16 row or fp32 row) */
+  double calib_confidence;/* see leafi_set_calibration_confidence */
 } leafi_index_info;
 
 leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info);
@@ -280,6 +281,8 @@ typedef struct {
   int32_t n_kclasses;       /* auto-tuner k-classes, ascending, 1..LEAFI_MAX_KCLASSES */
   int32_t kclasses[LEAFI_MAX_KCLASSES];
   uint64_t seed;
+  double confidence;        /* calibration confidence of the search's offsets (0.95; see
+                               leafi_set_calibration_confidence) */
 } leafi_train_params;
 
 typedef struct {
@@ -350,6 +353,17 @@ leafi_status leafi_znormalize(const float* x, int64_t n, int32_t m, float* out, 
  * qprime[c][j] = running minimum over j of the mean recall@k. */
 leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t nc,
                                   const int32_t* kclasses, int32_t nk);
+/* How the search turns a recall target t into a sorted position (Sec. 4.4.2,
+ * STEP reading).  Position j of a k-class table misses M_j = N (1 - qprime_j)
+ * of the N = min(k, n) nc true neighbours of the calibration queries; it is
+ * accepted when the binomial tail P(Bin(N, 1 - t) <= M_j) is at most
+ * 1 - confidence, and the positions are tested in order of decreasing
+ * offsets, the first failure ending the sequence.  The chosen position then
+ * has recall below t with probability at most 1 - confidence (over the draw of
+ * the calibration queries); a target no position can certify runs exactly.
+ * confidence 0 uses the point estimate qprime_j >= t.  Default 0.95. */
+leafi_status leafi_set_calibration_confidence(leafi_index* index, double confidence);
+
 /* Read (alpha_sorted [F][nc] float64, qprime [nk][nc] float64) back. */
 leafi_status leafi_get_autotuners(leafi_index* index, double* alpha_sorted, double* qprime);
 /* Install auto-tuner tables computed elsewhere (same layouts). */
@@ -376,9 +390,10 @@ typedef struct {
 /* k-NN of nq queries (1 <= k <= LEAFI_MAX_K).  recall_target >= 1 runs the
  * exact search (filters off); recall_target in (0, 1) uses the auto-tuned
  * offsets: the query's k picks the smallest calibrated k-class >= k, the
- * target picks the largest sorted position j whose calibrated quality meets
- * it, and leaf f is pruned when d^f - alpha_f,(j) > best-so-far.  A query
- * whose class or target has no calibrated position runs exactly.
+ * target picks the largest sorted position j whose calibrated quality
+ * certifies it (leafi_set_calibration_confidence), and leaf f is pruned when
+ * d^f - alpha_f,(j) > best-so-far.  A query whose class or target has no
+ * certified position runs exactly.
  * LEAFI_ENOTTRAINED if recall_target < 1 and no auto-tuners exist.
  * ids [nq][k] int64, dists [nq][k] float32 Euclidean. stats nullable. */
 leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,

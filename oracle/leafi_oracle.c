@@ -1443,19 +1443,43 @@ int32_t or_select_leaves_alg3(const int64_t* sizes, int32_t L, double th, double
   return n;
 }
 
-/* STEP rule with the inductive-conformal rank of Sec. 3: with nc calibration
- * queries the confidence levels a sorted position can certify are steps of
- * 1/(nc + 1) (delta = j_s / (l - m + 1)), so a target t is met when the
- * calibration quality reaches r = ceil((nc + 1) t) / nc; a target above
- * nc / (nc + 1) has r > 1 and no position (the search runs exactly).  The
- * position is the largest j (smallest offsets) whose running-minimum quality
- * still meets r. */
-double or_required_quality(int64_t nc, double target) {
-  return ceil((double)(nc + 1) * target) / (double)nc;
+/* STEP rule with a high-probability certificate (reading of Sec. 3 and
+ * Sec. 4.4.2).  At sorted position j the calibration set of nc queries misses
+ * M_j = N (1 - qprime_j) of its N = k nc true neighbours.  Position j is
+ * accepted when the binomial tail P(Bin(N, 1 - t) <= M_j) is at most
+ * delta = 1 - confidence: were the recall at j below t, so few misses would
+ * occur with probability at most delta.  Positions are tested in order of
+ * decreasing offsets and the first one that fails ends the sequence (qprime is
+ * non-increasing, so this is the largest accepted j); the probability that
+ * the chosen position's recall is below t is then at most delta.  In counts:
+ * accept iff M_j <= M*, the largest M whose tail is <= delta, i.e. iff
+ * qprime_j >= (N - M*) / N.  confidence <= 0 gives the point estimate
+ * (qprime_j >= t); a target of 1 or more, or one no position can certify,
+ * returns 2 (exact search). */
+double or_required_quality(int64_t n_trials, double target, double confidence) {
+  if (!(target < 1.0) || n_trials < 1) return 2.0;
+  if (confidence <= 0.0) return target;
+  const double p = 1.0 - target;
+  const double ldelta = log(1.0 - confidence);
+  const double n = (double)n_trials;
+  double lcdf = -INFINITY;
+  int64_t best = -1;
+  for (int64_t i = 0; i <= n_trials; ++i) {
+    const double lp = lgamma(n + 1.0) - lgamma((double)i + 1.0) - lgamma(n - (double)i + 1.0) +
+                      (double)i * log(p) + (n - (double)i) * log1p(-p);
+    /* log(exp(lcdf) + exp(lp)) */
+    const double hi = lcdf > lp ? lcdf : lp, lo = lcdf > lp ? lp : lcdf;
+    lcdf = hi + log1p(exp(lo - hi));
+    if (lcdf > ldelta) break;
+    best = i;
+  }
+  if (best < 0) return 2.0;
+  return (double)(n_trials - best) / n;
 }
 
-int32_t or_offset_position(const double* qprime, int64_t nc, double target) {
-  const double r = or_required_quality(nc, target);
+int32_t or_offset_position(const double* qprime, int64_t nc, int64_t kk, double target,
+                           double confidence) {
+  const double r = or_required_quality(kk * nc, target, confidence);
   int32_t j = -1;
   for (int64_t i = 0; i < nc; ++i) {
     if (qprime[i] >= r) j = (int32_t)i; else break;

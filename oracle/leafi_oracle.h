@@ -118,15 +118,18 @@ void or_filter_init(int F, int h, int m, uint64_t seed, float* W1, float* b1, fl
 /* One shuffle of [0, n) per epoch (int32 [epochs][n]). */
 void or_epoch_perms(int epochs, int n, uint64_t seed, int32_t* perms);
 
-/* Calibration quality a target needs with nc calibration queries (Sec. 3,
- * inductive conformal regression: confidence steps of 1/(nc + 1)):
- * r = ceil((nc + 1) target) / nc, above 1 for targets no position can certify. */
-double or_required_quality(int64_t nc, double target);
+/* Calibration quality that certifies recall target t with probability
+ * `confidence` from n_trials = k nc calibration neighbours (binomial tail of
+ * the misses; Sec. 3 / Sec. 4.4 reading): (N - M*) / N with M* the most misses
+ * whose tail P(Bin(N, 1 - t) <= M*) is at most 1 - confidence; 2 if none;
+ * confidence <= 0: t itself. */
+double or_required_quality(int64_t n_trials, double target, double confidence);
 
-/* Sorted position j* for a target (STEP reading with the conformal rank): the
- * largest j with qprime[j] >= or_required_quality(nc, target); -1 means "no
- * position meets it -> filters off". */
-int32_t or_offset_position(const double* qprime, int64_t nc, double target);
+/* Sorted position j* for a target (STEP reading): the largest j with
+ * qprime[j] >= or_required_quality(kk nc, target, confidence) (qprime is
+ * non-increasing); -1 means "no position -> filters off". */
+int32_t or_offset_position(const double* qprime, int64_t nc, int64_t kk, double target,
+                           double confidence);
 
 /* Steffen (1990) monotone interpolation through (x_i, y_i), x strictly increasing,
  * evaluated at xs (clamped to the end points). */

@@ -85,7 +85,7 @@ def lib():
         L.or_select_leaves_alg3.argtypes = [C.POINTER(C.c_int64), C.c_int32, C.c_double,
                                             C.c_double, C.c_double, C.POINTER(C.c_int32)]
         L.or_select_leaves_alg3.restype = C.c_int32
-        L.or_offset_position.argtypes = [f64p, C.c_int64, C.c_double]
+        L.or_offset_position.argtypes = [f64p, C.c_int64, C.c_int64, C.c_double, C.c_double]
         L.or_offset_position.restype = C.c_int32
         u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
         L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
@@ -93,7 +93,7 @@ def lib():
                                           C.c_double, C.c_uint64, f32p, f32p, i64p, i64p]
         L.or_filter_init.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, f32p, f32p, f32p, f32p]
         L.or_epoch_perms.argtypes = [C.c_int, C.c_int, C.c_uint64, i32p]
-        L.or_required_quality.argtypes = [C.c_int64, C.c_double]
+        L.or_required_quality.argtypes = [C.c_int64, C.c_double, C.c_double]
         L.or_required_quality.restype = C.c_double
         L.or_steffen_eval.argtypes = [f64p, f64p, C.c_int, C.c_double]
         L.or_steffen_eval.restype = C.c_double
@@ -306,14 +306,20 @@ def select_leaves_alg3(sizes, th, w, cap):
     return out[:n]
 
 
-def required_quality(nc, target):
-    """Calibration quality that certifies `target` with nc calibration queries."""
-    return float(lib().or_required_quality(int(nc), float(target)))
+CONFIDENCE = 0.95   # the library's default calibration confidence
 
 
-def offset_position(qprime, target):
+def required_quality(n_trials, target, confidence=CONFIDENCE):
+    """Calibration quality that certifies `target` with probability `confidence`
+    from n_trials = k * nc calibration neighbours."""
+    return float(lib().or_required_quality(int(n_trials), float(target), float(confidence)))
+
+
+def offset_position(qprime, target, kk=1, confidence=CONFIDENCE):
+    """STEP position for `target` on a k-class table qprime [nc] (kk = min(k, n))."""
     qp = np.ascontiguousarray(qprime, np.float64)
-    return int(lib().or_offset_position(qp, qp.shape[0], float(target)))
+    return int(lib().or_offset_position(qp, qp.shape[0], int(kk), float(target),
+                                        float(confidence)))
 
 
 def steffen_eval(x, y, xs):

@@ -29,6 +29,7 @@ __all__ = [
     "SgdParams", "TrainReport", "leafi_train_filters_on", "leafi_training_queries",
     "leafi_initial_weights", "leafi_epoch_permutations", "leafi_znormalize",
     "leafi_get_filter_leaves", "leafi_debug_set_lock_tries", "leafi_debug_fail_allocations",
+    "leafi_set_calibration_confidence",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -53,7 +54,7 @@ EXPORTED_SYMBOLS = [
     "leafi_serve_stop", "leafi_select_leaves_auto", "leafi_train_filters_on",
     "leafi_training_queries", "leafi_initial_weights", "leafi_epoch_permutations",
     "leafi_znormalize", "leafi_get_filter_leaves", "leafi_debug_set_lock_tries",
-    "leafi_debug_fail_allocations",
+    "leafi_debug_fail_allocations", "leafi_set_calibration_confidence",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -84,7 +85,8 @@ class IndexInfo(C.Structure):
                 ("n_filters", C.c_int32), ("filters_trained", C.c_int32),
                 ("n_calib", C.c_int32), ("n_kclasses", C.c_int32),
                 ("kclasses", C.c_int32 * 4), ("device_bytes", C.c_int64),
-                ("tensor_scan", C.c_int32), ("scan_row_bytes", C.c_int32)]
+                ("tensor_scan", C.c_int32), ("scan_row_bytes", C.c_int32),
+                ("calib_confidence", C.c_double)]
 
 
 class TrainParams(C.Structure):
@@ -94,16 +96,16 @@ class TrainParams(C.Structure):
                 ("val_frac", C.c_double), ("noise_lo", C.c_double), ("noise_hi", C.c_double),
                 ("batch", C.c_int32), ("max_epochs", C.c_int32), ("patience", C.c_int32),
                 ("lr0", C.c_double), ("lr_min", C.c_double), ("n_kclasses", C.c_int32),
-                ("kclasses", C.c_int32 * 4), ("seed", C.c_uint64)]
+                ("kclasses", C.c_int32 * 4), ("seed", C.c_uint64), ("confidence", C.c_double)]
 
     def __init__(self, n_filters=100, a=2.0, mem_cap=8 << 30, hidden=0, n_train=2000,
                  global_local_ratio=3.0, val_frac=0.2, noise_lo=0.1, noise_hi=0.4, batch=64,
                  max_epochs=1000, patience=10, lr0=0.01, lr_min=1e-5, kclasses=(1,),
-                 seed=2502018361):
+                 seed=2502018361, confidence=0.95):
         kc = (C.c_int32 * 4)(*(list(kclasses) + [0] * (4 - len(kclasses))))
         super().__init__(n_filters, a, mem_cap, hidden, n_train, global_local_ratio, val_frac,
                          noise_lo, noise_hi, batch, max_epochs, patience, lr0, lr_min,
-                         len(kclasses), kc, seed)
+                         len(kclasses), kc, seed, confidence)
 
 
 class TrainReport(C.Structure):
@@ -188,6 +190,7 @@ def lib():
             "leafi_get_filter_leaves": [vp, vp],
             "leafi_debug_set_lock_tries": [vp, i32],
             "leafi_debug_fail_allocations": [i64],
+            "leafi_set_calibration_confidence": [vp, f64],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
@@ -381,6 +384,11 @@ def leafi_debug_set_lock_tries(index, tries):
 def leafi_debug_fail_allocations(after):
     """Failure-detection diagnostic: make the after-th allocation from now fail (-1 disarms)."""
     _check(lib().leafi_debug_fail_allocations(int(after)))
+
+
+def leafi_set_calibration_confidence(index, confidence):
+    """Probability that a certified sorted position meets its recall target (0: point estimate)."""
+    _check(lib().leafi_set_calibration_confidence(index, float(confidence)))
 
 
 def leafi_get_filter_leaves(index):

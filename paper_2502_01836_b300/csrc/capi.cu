@@ -515,6 +515,59 @@ void check_queries(const leafi_index* ix, const float* q, int64_t nq) {
   (void)ix;
 }
 
+// Calibration quality that certifies recall target t with probability `conf`
+// from N calibration neighbours: a position whose misses M satisfy
+// P(Bin(N, 1 - t) <= M) <= 1 - conf is accepted, and since the calibrated
+// quality only falls along the sorted positions, testing them in order and
+// stopping at the first failure bounds the chance that the chosen position's
+// recall is below t by 1 - conf.  Returns (N - M*) / N for the largest such
+// M*, 2 (no position: exact search) if even M = 0 fails or t >= 1, and t itself
+// for conf <= 0 (the point estimate).
+double required_quality(int64_t N, double t, double conf) {
+  if (!(t < 1.0) || N < 1) return 2.0;
+  if (conf <= 0.0) return t;
+  const double p = 1.0 - t, log_delta = std::log(1.0 - conf);
+  const double lratio = std::log(p) - std::log1p(-p);
+  double lpmf = (double)N * std::log1p(-p);  // log P(Bin = 0)
+  double lcdf = lpmf;
+  int64_t m_star = -1;
+  for (int64_t i = 0; i <= N && lcdf <= log_delta; ++i) {
+    m_star = i;
+    // next term: pmf(i + 1) = pmf(i) (N - i) / (i + 1) p / (1 - p)
+    lpmf += std::log((double)(N - i)) - std::log((double)(i + 1)) + lratio;
+    const double hi = std::max(lcdf, lpmf), lo = std::min(lcdf, lpmf);
+    lcdf = hi + std::log1p(std::exp(lo - hi));
+  }
+  if (m_star < 0) return 2.0;
+  return (double)(N - m_star) / (double)N;
+}
+
+// per query: the quality its k-class table must reach for its target (2 when
+// the query runs exactly); cached per (N, target) on the index
+void required_qualities(leafi_index* ix, int nb, const int32_t* kq, const double* target,
+                        bool uniform, std::vector<double>& out) {
+  out.resize(uniform ? 1 : nb);
+  for (size_t i = 0; i < out.size(); ++i) {
+    const double t = target[i];
+    int c = -1;
+    for (int z = 0; z < ix->nk; ++z)
+      if (ix->kclasses[z] >= kq[i]) {
+        c = z;
+        break;
+      }
+    if (c < 0 || !(t < 1.0) || ix->nc == 0) {
+      out[i] = 2.0;
+      continue;
+    }
+    const int64_t N = std::min<int64_t>(ix->kclasses[c], ix->n) * ix->nc;
+    const auto key = std::make_pair(N, t);
+    auto it = ix->rq_cache.find(key);
+    if (it == ix->rq_cache.end())
+      it = ix->rq_cache.emplace(key, required_quality(N, t, ix->calib_confidence)).first;
+    out[i] = it->second;
+  }
+}
+
 __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, double tval) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nb) {
@@ -527,7 +580,7 @@ __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, 
 struct LaneView {
   float* gQ;
   int32_t *dK, *jpos, *route, *topk_cnt, *cand_cnt, *done, *np, *ord, *cursor;
-  double *dT, *lb2;
+  double *dT, *lb2;  // dT: the calibration quality each query's target needs
   float *P, *out_d;
   unsigned char* scanned;
   unsigned long long *topk, *thr, *cand;
@@ -567,6 +620,8 @@ struct Pipeline {
   leafi_search_stats st{};
   LaneView lv[kMaxLanes];
   InFlight fl[kMaxLanes];
+  std::vector<double> rq_host[kMaxLanes];  // required qualities copied to each lane (kept alive
+                                           // until the lane's next batch)
   SelectArgs sa;
   int cur_lane = 0;
   cudaStream_t s = nullptr;
@@ -815,12 +870,15 @@ void Pipeline::start(int li, const float* queries, int nb, const int32_t* kq, co
   LF_CUDA(cudaMemcpy2DAsync(v.gQ, sizeof(float) * ix->mp, queries, sizeof(float) * ix->m,
                             sizeof(float) * ix->m, (size_t)nb,
                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  // the position kernel compares the tables with the quality each target needs
+  std::vector<double>& rq = rq_host[li];
+  required_qualities(ix, nb, kq, target, uniform, rq);
   if (uniform) {
-    fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.dK, v.dT, kq[0], target[0]);
+    fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.dK, v.dT, kq[0], rq[0]);
     LF_CHECK_LAUNCH();
   } else {
     LF_CUDA(cudaMemcpyAsync(v.dK, kq, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-    LF_CUDA(cudaMemcpyAsync(v.dT, target, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    LF_CUDA(cudaMemcpyAsync(v.dT, rq.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
   }
   InFlight& f = fl[li];
   f = InFlight();
@@ -1337,6 +1395,7 @@ leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info) {
                                index->ids.bytes() + index->W1t.bytes());
     r.tensor_scan = (index->tc_ok && index->scan_path == 0) ? 1 : 0;
     r.scan_row_bytes = r.tensor_scan ? index->kp * 2 : index->mp * 4;
+    r.calib_confidence = index->calib_confidence;
     *info = r;
   });
 }
@@ -2051,6 +2110,7 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
                         p->patience, p->lr0, p->lr_min};
     check_sgd_params(&sp);
     check_kclasses(p->kclasses, p->n_kclasses);
+    if (!(p->confidence >= 0.0 && p->confidence < 1.0)) fail(LEAFI_EINVAL, "confidence must be in [0, 1)");
     if (c.n_gval > calib_max_sort())
       fail(LEAFI_EINVAL, "calibration set of %d queries exceeds %d", c.n_gval, calib_max_sort());
     const int L = index->tree.n_leaves;
@@ -2105,6 +2165,8 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     t0 = std::chrono::steady_clock::now();
     // line 10: auto-tuners on the calibration set (the global validation queries)
     fit_core(index, dQg + (size_t)c.n_gtrain * index->mp, c.n_gval, p->kclasses, p->n_kclasses);
+    index->calib_confidence = p->confidence;
+    index->rq_cache.clear();
     rep.seconds_calibrate = seconds_since(t0);
     rep.n_filters = F;
     rep.n_gtrain = c.n_gtrain;
@@ -2214,6 +2276,16 @@ leafi_status leafi_znormalize(const float* x, int64_t n, int32_t m, float* out, 
                                 s));
       LF_CUDA(cudaStreamSynchronize(s));
     }
+  });
+}
+
+leafi_status leafi_set_calibration_confidence(leafi_index* index, double confidence) {
+  return guarded([&] {
+    require_device(index);
+    if (!(confidence >= 0.0 && confidence < 1.0)) fail(LEAFI_EINVAL, "confidence must be in [0, 1)");
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->calib_confidence = confidence;
+    index->rq_cache.clear();
   });
 }
 

@@ -127,6 +127,10 @@ void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double*
 void launch_isax_bounds(const IsaxTables& T, const double* P, int nq, int m, double* paa,
                         double* leaf_lb, int32_t* route, cudaStream_t s);
 
+// route leaf of every query from its prefix sums (scheduling keys of a
+// multi-batch search; iSAX queries without a leaf on their path get n_leaves)
+void launch_route_keys(const leafi_index* ix, const double* P, int nq, int32_t* key,
+                       cudaStream_t s);
 bool filter_tc_fits(int m, int h, int smem_optin);
 void launch_wsplit(const float* W1t, int F, int m, int h, float* Ws, cudaStream_t s);
 void launch_filter_tc(const CUtensorMap& qmap, const CUtensorMap& wmap, const float* Q, int nq,
@@ -432,6 +436,8 @@ struct leafi_index {
                                                // not fit), keys per lane quarter's lists)
 
   int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries
+  double calib_confidence = 0.95;  // probability that a certified position meets its target
+  std::map<std::pair<int64_t, double>, double> rq_cache;  // (N, target) -> required quality
   int profiling = 0;       // 0 off, 1 leaf-scan kernel times, 2 every kind + scan phases
   bool ticked = false;     // the last tick() recorded a start event
   leafi::BatchGraph* capturing = nullptr;  // entry being captured (tick/tock record into it)

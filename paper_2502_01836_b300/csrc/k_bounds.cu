@@ -235,6 +235,48 @@ __global__ void isax_route_kernel(IsaxTables T, const double* __restrict__ paa,
   if (threadIdx.x == 0) route[q] = s_id[0];
 }
 
+// Scheduling keys: the route leaf of every query from its prefix sums, one
+// thread per query walking the tree (no per-interval or per-leaf tables).  An
+// iSAX query whose own path ends at no leaf gets key n_leaves (the search
+// itself then routes it to its smallest-bound leaf).
+__global__ void ds_route_key_kernel(DsTables T, const double* __restrict__ P, int nq, int m,
+                                    int32_t* __restrict__ key) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const double* p1 = P + (size_t)q * 2 * (m + 1);
+  int v = T.root;
+  for (int guard = 0; guard < T.n_nodes && T.node_leaf[v] < 0; ++guard) {
+    const int iv = T.split_iv[v];
+    double mu, sd;
+    interval_stat(p1, p1 + m + 1, T.iv_s[iv], T.iv_e[iv], mu, sd);
+    const double val = T.split_sd[v] ? sd : mu;
+    v = (val < T.thresh[v]) ? T.left[v] : T.right[v];
+  }
+  key[q] = T.node_leaf[v];
+}
+
+__global__ void isax_route_key_kernel(IsaxTables T, const double* __restrict__ P, int nq, int m,
+                                      int32_t* __restrict__ key) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const double* p1 = P + (size_t)q * 2 * (m + 1);
+  const int l = m / T.w, C = 1 << T.bits;
+  int sym[32];
+  int rk = 0;
+  for (int j = 0; j < T.w; ++j) {
+    const double a = __ddiv_rn(__dsub_rn(p1[(j + 1) * l], p1[j * l]), (double)l);
+    sym[j] = sax_symbol(T.beta, C, a);
+    rk = (rk << 1) | (sym[j] >> (T.bits - 1));
+  }
+  int v = T.root_child[rk];
+  for (int guard = 0; v >= 0 && guard < T.n_nodes && T.isplit[v] >= 0; ++guard) {
+    const int j = T.isplit[v];
+    const int have = T.node_bits[(size_t)v * T.w + j];
+    v = ((sym[j] >> (T.bits - have - 1)) & 1) ? T.right[v] : T.left[v];
+  }
+  key[q] = (v >= 0 && T.node_leaf[v] >= 0) ? T.node_leaf[v] : T.n_leaves;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -281,6 +323,16 @@ void launch_isax_bounds(const IsaxTables& T, const double* P, int nq, int m, dou
     isax_route_kernel<<<nq, kThreads, 0, s>>>(T, paa, leaf_lb, nq, route);
     LF_CHECK_LAUNCH();
   }
+}
+
+void launch_route_keys(const leafi_index* ix, const double* P, int nq, int32_t* key,
+                       cudaStream_t s) {
+  if (nq <= 0) return;
+  if (ix->tree.type == LEAFI_DSTREE)
+    ds_route_key_kernel<<<blocks_for(nq, 64), 64, 0, s>>>(ix->ds(), P, nq, ix->m, key);
+  else
+    isax_route_key_kernel<<<blocks_for(nq, 64), 64, 0, s>>>(ix->isax(), P, nq, ix->m, key);
+  LF_CHECK_LAUNCH();
 }
 
 }  // namespace leafi

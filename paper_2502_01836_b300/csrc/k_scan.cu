@@ -726,11 +726,10 @@ __global__ void fill_u64_kernel(u64* p, u64 v, size_t n) {
 
 // sorted position per query (Sec. 4.4.2 with the STEP reading): the query's
 // k picks the smallest calibrated class >= k; the position is the largest j
-// whose calibrated quality qprime[class][j] still reaches the quality that
-// certifies the target with nc calibration queries, r = ceil((nc+1) t) / nc
-// (the 1/(nc+1) confidence steps of inductive conformal regression, Sec. 3);
-// r > 1 leaves no position (exact search).
-__global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double* __restrict__ target,
+// whose calibrated quality qprime[class][j] still reaches rq[q], the quality
+// that certifies the query's recall target (computed on the host from the
+// binomial tail of the calibration misses); rq > 1 leaves no position (exact).
+__global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double* __restrict__ rq,
                             int nk, const int32_t* __restrict__ kclasses,
                             const double* __restrict__ qprime, int nc, int32_t* __restrict__ jpos) {
   // one warp per query; the table is read 32 entries at a time and the
@@ -738,7 +737,7 @@ __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double*
   const int q = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (q >= nq) return;
-  const double t = target[q];
+  const double r = rq[q];
   int c = -1;
   for (int i = 0; i < nk; ++i)
     if (kclasses[i] >= k[q]) {
@@ -746,8 +745,7 @@ __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double*
       break;
     }
   int j = -1;
-  const double r = __ddiv_rn(ceil(__dmul_rn((double)(nc + 1), t)), (double)nc);
-  if (c >= 0 && t < 1.0 && r <= 1.0) {
+  if (c >= 0 && r <= 1.0) {
     const double* qp = qprime + (size_t)c * nc;
     j = nc - 1;
     for (int base = 0; base < nc; base += 32) {

@@ -163,7 +163,7 @@ def test_mixed_k_isax_config_reduced():
         qp = np.zeros((3, nc))
         lf.leafi_get_autotuners(idx, alpha, qp)
         cls = {1: 0, 10: 1, 100: 2}
-        jpos = np.array([-1 if tg[i] >= 1 else O.offset_position(qp[cls[kq[i]]], tg[i])
+        jpos = np.array([-1 if tg[i] >= 1 else O.offset_position(qp[cls[kq[i]]], tg[i], kk=kq[i])
                          for i in range(len(Q))], np.int32)
         o_ids, o_d2, _, margin = O.leafi_search(t, W, enh.filter_leaf, alpha, Q, kq, jpos, 16,
                                                 kmax=100)

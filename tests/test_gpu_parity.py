@@ -229,11 +229,15 @@ def test_leafi_search_matches_oracle(ds, tuned, k, target):
     alpha = tables[1][0]
     qp = np.stack([tables[1][1], tables[10][1]])
     lf.leafi_set_autotuners(idx, alpha, qp, [1, 10])
+    # 80 calibration queries certify little at 95% confidence: the point
+    # estimate keeps the filters in play for this comparison of the search
+    lf.leafi_set_calibration_confidence(idx, 0.0)
     ids = np.zeros((NQ, k), np.int64)
     d = np.zeros((NQ, k), np.float32)
     st = lf.SearchStats()
     lf.leafi_search(idx, Q, k, target, ids, d, st)
-    j = O.offset_position(tables[k][1], target)
+    lf.leafi_set_calibration_confidence(idx, 0.95)
+    j = O.offset_position(tables[k][1], target, kk=k, confidence=0.0)
     o_ids, o_d2, o_st, margin = O.leafi_search(t, Wt, fl, alpha, Q, k, j, 4)
     tol = 2e-5 * _pred_scale(Wt, Q).max()
     same = (ids == o_ids).all(1)
@@ -253,18 +257,24 @@ def test_search_mixed_matches_oracle(ds, tuned):
     rng = np.random.default_rng(8)
     kq = rng.choice([1, 5, 10, 20], NQ).astype(np.int32)
     tg = rng.choice([0.9, 0.95, 0.99, 1.0], NQ).astype(np.float64)
-    ids = np.zeros((NQ, 20), np.int64)
-    d = np.zeros((NQ, 20), np.float32)
-    lf.leafi_search_mixed(idx, Q, kq, tg, 20, ids, d)
-    jpos = np.array([(-1 if (tg[i] >= 1 or kq[i] > 10) else
-                      O.offset_position(tables[1 if kq[i] <= 1 else 10][1], tg[i]))
-                     for i in range(NQ)], np.int32)
-    o_ids, o_d2, _, margin = O.leafi_search(t, Wt, fl, alpha, Q, kq, jpos, 4, kmax=20)
-    tol = 2e-5 * _pred_scale(Wt, Q).max()
-    same = (ids == o_ids).all(1)
-    assert (same | (margin <= tol)).all()
-    # exact queries (target 1 or k above every class) always agree
-    assert same[jpos < 0].all()
+    for conf in (0.0, 0.95):
+        lf.leafi_set_calibration_confidence(idx, conf)
+        ids = np.zeros((NQ, 20), np.int64)
+        d = np.zeros((NQ, 20), np.float32)
+        lf.leafi_search_mixed(idx, Q, kq, tg, 20, ids, d)
+        jpos = np.array([(-1 if (tg[i] >= 1 or kq[i] > 10) else
+                          O.offset_position(tables[1 if kq[i] <= 1 else 10][1], tg[i],
+                                            kk=1 if kq[i] <= 1 else 10, confidence=conf))
+                         for i in range(NQ)], np.int32)
+        if conf == 0.0:
+            assert (jpos >= 0).sum() >= NQ // 4      # the filters are in play
+        o_ids, o_d2, _, margin = O.leafi_search(t, Wt, fl, alpha, Q, kq, jpos, 4, kmax=20)
+        tol = 2e-5 * _pred_scale(Wt, Q).max()
+        same = (ids == o_ids).all(1)
+        assert (same | (margin <= tol)).all()
+        # exact queries (target 1 or k above every class) always agree
+        assert same[jpos < 0].all()
+    lf.leafi_set_calibration_confidence(idx, 0.95)
 
 
 @pytest.mark.parametrize("k,target", [(1, 0.95), (10, 1.0)])
@@ -413,11 +423,12 @@ def test_wave_wider_than_the_index():
         diff = np.abs(qp[0] - o_qp)
         assert (diff == 0).mean() >= 0.9 and diff.max() <= 3.0 / 100
         # LeaFi mode with the GPU's tables: the one wide wave after the route leaf
+        lf.leafi_set_calibration_confidence(idx, 0.0)
         for target in (0.9, 0.95):
             ids1 = np.zeros((300, 1), np.int64)
             d1 = np.zeros((300, 1), np.float32)
             lf.leafi_search(idx, Q, 1, target, ids1, d1)
-            j = O.offset_position(qp[0], target)
+            j = O.offset_position(qp[0], target, confidence=0.0)
             o_ids1, o_d2, _, margin = O.leafi_search(t, Wt, fl, alpha, Q, 1, j, wave)
             same = (ids1 == o_ids1).all(1)
             assert (same | (margin <= 2e-5 * _pred_scale(Wt, Q).max())).all()

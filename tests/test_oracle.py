@@ -506,21 +506,43 @@ def test_autotuner_table_matches_search_recall(seed, k, wave):
         assert (np.diff(rec) > 0).any()
 
 
+def test_required_quality_is_the_binomial_tail_bound():
+    """The quality that certifies target t with probability 0.95 from N
+    calibration neighbours: (N - M*) / N where M* is the most misses whose
+    binomial tail P(Bin(N, 1 - t) <= M*) stays at or below 0.05 (scipy's
+    binomial distribution as the independent reference)."""
+    for N, t in ((300, 0.99), (300, 0.95), (300, 0.9), (3000, 0.99), (80, 0.9), (30000, 0.95),
+                 (1000, 0.5)):
+        r = O.required_quality(N, t, 0.95)
+        cdf = scipy.stats.binom.cdf(np.arange(N + 1), N, 1 - t)
+        ok = np.nonzero(cdf <= 0.05)[0]
+        if len(ok) == 0:
+            assert r == 2.0
+        else:
+            assert r == (N - ok.max()) / N, (N, t, r)
+    # hand values: 300 calibration queries at 0.99 allow no miss (0.99^300 = 0.049 <= 0.05,
+    # one miss has tail 0.197); 80 queries cannot certify 0.99 (0.99^80 = 0.45)
+    assert O.required_quality(300, 0.99, 0.95) == 1.0
+    assert O.required_quality(80, 0.99, 0.95) == 2.0
+    assert O.required_quality(300, 0.99, 0.0) == 0.99        # point estimate
+    assert O.required_quality(300, 1.0, 0.95) == 2.0
+
+
 def test_offset_position_step_rule():
-    """STEP with the conformal rank of Sec. 3: with nc calibration queries the
-    target t needs calibration quality ceil((nc + 1) t) / nc (hand values)."""
-    assert O.required_quality(300, 0.99) == 298 / 300
-    assert O.required_quality(300, 0.9) == 271 / 300
-    assert O.required_quality(300, 0.95) == 286 / 300
-    assert O.required_quality(300, 300 / 301 + 1e-6) > 1.0
-    qp = np.array([1.0, 1.0, 0.9, 0.9, 0.8, 0.7, 0.7, 0.6, 0.5, 0.5])   # nc = 10
-    assert O.offset_position(qp, 0.8) == 3       # 11 * 0.8 = 8.8 -> needs 9/10
-    assert O.offset_position(qp, 0.72) == 4      # 7.92 -> 8/10
-    assert O.offset_position(qp, 0.9) == 1       # 9.9 -> 10/10
-    assert O.offset_position(qp, 0.5) == 7       # 5.5 -> 6/10
-    assert O.offset_position(qp, 0.45) == 9      # 4.95 -> 5/10
-    assert O.offset_position(qp, 0.95) == -1     # 10.45 -> 11/10: no position certifies it
-    assert O.offset_position(np.array([0.9, 0.8]), 0.5) == -1   # needs 2/2
+    """STEP: the largest sorted position whose (non-increasing) quality reaches
+    the required one; none -> -1 (exact search)."""
+    qp = np.array([1.0, 1.0, 0.99, 0.97, 0.97, 0.9])
+    assert O.offset_position(qp, 0.99, confidence=0.0) == 2
+    assert O.offset_position(qp, 0.95, confidence=0.0) == 4
+    assert O.offset_position(qp, 1.0, confidence=0.0) == -1
+    assert O.offset_position(np.array([0.9, 0.8]), 0.95, confidence=0.0) == -1
+    # 300 calibration queries at 0.95 with confidence 0.95 allow 8 misses (0.97333)
+    qp = np.linspace(1.0, 0.9, 300)
+    r = O.required_quality(300, 0.95)
+    assert r == 292 / 300
+    assert O.offset_position(qp, 0.95) == int(np.nonzero(qp >= r)[0].max())
+    # k = 10: ten neighbours per query, 3000 trials
+    assert O.offset_position(qp, 0.99, kk=10) == int(np.nonzero(qp >= O.required_quality(3000, 0.99))[0].max())
 
 
 def test_huge_offsets_give_the_exact_answer(small_index):
