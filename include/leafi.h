@@ -399,6 +399,14 @@ typedef struct {
 leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
                           double recall_target, int64_t* ids, float* dists,
                           leafi_search_stats* stats);
+/* Query scheduling of calls with more than one internal batch (on by
+ * default): the batches are cut from the queries in order of their route
+ * leaf, so that each batch's queries need largely the same leaves and the
+ * batch reads fewer distinct series.  Results and their order are the same
+ * either way (every query is searched on its own terms); off keeps the
+ * caller's order. */
+leafi_status leafi_set_query_schedule(leafi_index* index, int32_t on);
+
 /* Exact k-NN with summarisation-bound pruning only (the plain index). */
 leafi_status leafi_exact_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
                                 int64_t* ids, float* dists, leafi_search_stats* stats);

@@ -568,6 +568,17 @@ void required_qualities(leafi_index* ix, int nb, const int32_t* kq, const double
   }
 }
 
+// dst row i = src row rows[i] (rows of mp floats)
+__global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ rows,
+                                   int nb, int mp, float* __restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int mp4 = mp / 4;
+  if (t >= (int64_t)nb * mp4) return;
+  const int i = (int)(t / mp4), c = (int)(t % mp4);
+  reinterpret_cast<float4*>(dst)[t] =
+      reinterpret_cast<const float4*>(src)[(int64_t)rows[i] * mp4 + c];
+}
+
 __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, double tval) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nb) {
@@ -599,6 +610,8 @@ struct InFlight {
   int waves = 0;
   int64_t* ids = nullptr;   // where its results go (host or device)
   float* dists = nullptr;
+  const int32_t* rows = nullptr;  // scheduled batch: output row of each query (device);
+                                  // ids / dists are then the call's device arrays
 };
 
 }  // namespace
@@ -641,6 +654,11 @@ struct Pipeline {
   // (uniform: kq[0] / target[0] for all) and enqueue the batch on lane li
   void start(int li, const float* queries, int nb, const int32_t* kq, const double* target,
              bool uniform, int64_t* ids, float* dists);
+  // the same for a scheduled batch: its queries are rows `rows` (device) of the
+  // staged query array dQall and its results go to those rows of out_i / out_d
+  void start_rows(int li, const float* dQall, const int32_t* rows, int nb, const int32_t* kq,
+                  const double* target, bool uniform, int64_t* out_i, float* out_d);
+  void launch_batch(int li, int nb, const int32_t* kq, const double* target, bool uniform);
   // wait for lane li's batch, run its remaining waves, deliver its results
   void finish(int li);
 };
@@ -870,6 +888,31 @@ void Pipeline::start(int li, const float* queries, int nb, const int32_t* kq, co
   LF_CUDA(cudaMemcpy2DAsync(v.gQ, sizeof(float) * ix->mp, queries, sizeof(float) * ix->m,
                             sizeof(float) * ix->m, (size_t)nb,
                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  fl[li] = InFlight();
+  fl[li].ids = ids;
+  fl[li].dists = dists;
+  launch_batch(li, nb, kq, target, uniform);
+}
+
+void Pipeline::start_rows(int li, const float* dQall, const int32_t* rows, int nb,
+                          const int32_t* kq, const double* target, bool uniform, int64_t* out_i,
+                          float* out_d) {
+  use_lane(li);
+  const LaneView& v = lv[li];
+  const int64_t n4 = (int64_t)nb * (ix->mp / 4);
+  gather_rows_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(dQall, rows, nb, ix->mp, v.gQ);
+  LF_CHECK_LAUNCH();
+  fl[li] = InFlight();
+  fl[li].ids = out_i;
+  fl[li].dists = out_d;
+  fl[li].rows = rows;
+  launch_batch(li, nb, kq, target, uniform);
+}
+
+// k, targets and the batch's head (graph replay or eager) on the current lane
+void Pipeline::launch_batch(int li, int nb, const int32_t* kq, const double* target,
+                            bool uniform) {
+  const LaneView& v = lv[li];
   // the position kernel compares the tables with the quality each target needs
   std::vector<double>& rq = rq_host[li];
   required_qualities(ix, nb, kq, target, uniform, rq);
@@ -881,11 +924,8 @@ void Pipeline::start(int li, const float* queries, int nb, const int32_t* kq, co
     LF_CUDA(cudaMemcpyAsync(v.dT, rq.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
   }
   InFlight& f = fl[li];
-  f = InFlight();
   f.active = true;
   f.nb = nb;
-  f.ids = ids;
-  f.dists = dists;
   f.use_f = false;
   for (int i = 0; i < (uniform ? 1 : nb); ++i) f.use_f = f.use_f || target[i] < 1.0;
   if (f.use_f) st.filter_evals += (int64_t)nb * ix->F;
@@ -927,9 +967,13 @@ void Pipeline::finish(int li) {
   }
   st.waves += f.waves;
   st.batches += 1;
-  launch_write_results(f.nb, kmax, v.dK, v.topk, kmax, v.topk_cnt, v.out_i, v.out_d, s);
-  deliver(f.ids, v.out_i, (size_t)f.nb * kmax, s);
-  deliver(f.dists, v.out_d, (size_t)f.nb * kmax, s);
+  if (f.rows) {
+    launch_write_results(f.nb, kmax, v.dK, v.topk, kmax, v.topk_cnt, f.ids, f.dists, s, f.rows);
+  } else {
+    launch_write_results(f.nb, kmax, v.dK, v.topk, kmax, v.topk_cnt, v.out_i, v.out_d, s);
+    deliver(f.ids, v.out_i, (size_t)f.nb * kmax, s);
+    deliver(f.dists, v.out_d, (size_t)f.nb * kmax, s);
+  }
   f.active = false;
 }
 
@@ -970,6 +1014,46 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     cudaEvent_t e;
     ~EvGuard() { cudaEventDestroy(e); }
   } evg{ev_start};
+  // Scheduling (a call of more than one batch): queries that route to the same
+  // leaf need mostly the same leaves, so batches are cut from the queries in
+  // order of their route leaf (original order among equals); each batch then
+  // reads a smaller union of leaves.  Results go back to the callers' rows.
+  const bool sched = ix->schedule && nq > qb;
+  const float* dQall = nullptr;
+  const int32_t* dperm = nullptr;
+  int64_t* out_i = ids;
+  float* out_d = dists;
+  std::vector<int32_t> kq_s;
+  std::vector<double> tg_s;
+  if (sched) {
+    Schedule& sc = ix->sched;
+    dQall = stage_queries(ix, queries, nq, sc.Q);
+    double* P = sc.P.need((size_t)nq * 2 * (ix->m + 1));
+    int32_t* keys = sc.key.need(nq);
+    launch_prefix(dQall, (int)nq, ix->mp, ix->m, P, user);
+    launch_route_keys(ix, P, (int)nq, keys, user);
+    std::vector<int32_t> hkey(nq);
+    LF_CUDA(cudaMemcpyAsync(hkey.data(), keys, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, user));
+    LF_CUDA(cudaStreamSynchronize(user));
+    std::vector<int32_t> perm(nq);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return hkey[a] < hkey[b]; });
+    sc.perm.upload(perm, user);
+    dperm = sc.perm.p;
+    if (!uniform) {
+      kq_s.resize(nq);
+      tg_s.resize(nq);
+      for (int64_t i = 0; i < nq; ++i) {
+        kq_s[i] = kq[perm[i]];
+        tg_s[i] = target[perm[i]];
+      }
+    }
+    if (!on_device(ids) || !on_device(dists)) {
+      out_i = sc.out_i.need((size_t)nq * kmax);
+      out_d = sc.out_d.need((size_t)nq * kmax);
+    }
+    LF_CUDA(cudaStreamSynchronize(user));  // the host's permuted copies are read below
+  }
   LF_CUDA(cudaEventRecord(ev_start, user));
   for (int li = 0; li < nlanes; ++li) LF_CUDA(cudaStreamWaitEvent(ix->lanes[li].st, ev_start, 0));
 
@@ -978,9 +1062,13 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     const int li = bi % nlanes;
     const int nb = (int)std::min<int64_t>(qb, nq - b0);
     pl.finish(li);  // the lane's previous batch (nlanes batches back)
-    pl.start(li, queries + (size_t)b0 * ix->m, nb, kq.data() + (uniform ? 0 : b0),
-             target.data() + (uniform ? 0 : b0), uniform, ids + (size_t)b0 * kmax,
-             dists + (size_t)b0 * kmax);
+    if (sched)
+      pl.start_rows(li, dQall, dperm + b0, nb, (uniform ? kq.data() : kq_s.data() + b0),
+                    (uniform ? target.data() : tg_s.data() + b0), uniform, out_i, out_d);
+    else
+      pl.start(li, queries + (size_t)b0 * ix->m, nb, kq.data() + (uniform ? 0 : b0),
+               target.data() + (uniform ? 0 : b0), uniform, ids + (size_t)b0 * kmax,
+               dists + (size_t)b0 * kmax);
   }
   // the remaining batches, oldest first
   for (int i = 0; i < nlanes; ++i) pl.finish((bi + i) % nlanes);
@@ -992,6 +1080,10 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   }
   ix->sc = &ix->lanes[0];
   ix->stream = user;
+  if (sched && out_i != ids) {
+    deliver(ids, out_i, (size_t)nq * kmax, user);
+    deliver(dists, out_d, (size_t)nq * kmax, user);
+  }
   unsigned long long h_stat[4] = {0, 0, 0, 0};
   LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, user));
   LF_CUDA(cudaStreamSynchronize(user));
@@ -2276,6 +2368,14 @@ leafi_status leafi_znormalize(const float* x, int64_t n, int32_t m, float* out, 
                                 s));
       LF_CUDA(cudaStreamSynchronize(s));
     }
+  });
+}
+
+leafi_status leafi_set_query_schedule(leafi_index* index, int32_t on) {
+  return guarded([&] {
+    require_device(index);
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->schedule = on != 0;
   });
 }
 

@@ -318,7 +318,8 @@ void launch_jpos(int nq, const int32_t* k, const double* target, int nk, const i
                  const double* qprime, int nc, int32_t* jpos, cudaStream_t s);
 void launch_write_results(int nq, int kmax, const int32_t* kq, const unsigned long long* topk,
                           int kstride, const int32_t* topk_cnt, int64_t* ids, float* dists,
-                          cudaStream_t s);
+                          cudaStream_t s,
+                          const int32_t* rows = nullptr);
 void launch_leafknn_out(int nslots, int k, const unsigned long long* topk, const int32_t* topk_cnt,
                         float* d2, int64_t* ids, cudaStream_t s);
 
@@ -380,6 +381,15 @@ struct Scratch {
   std::vector<BatchGraph> graphs;  // captured batches of this lane
   void release_lane();
 };
+// query scheduling of a multi-batch search call (search_impl)
+struct Schedule {
+  DBuf<float> Q;       // the call's queries, staged [nq][mp]
+  DBuf<double> P;      // their prefix sums
+  DBuf<int32_t> key;   // route leaf per query
+  DBuf<int32_t> perm;  // queries in batch order
+  DBuf<int64_t> out_i; // results in the caller's row order (host outputs)
+  DBuf<float> out_d;
+};
 }  // namespace leafi
 
 // ----------------------------------------------------------------- index
@@ -435,6 +445,8 @@ struct leafi_index {
   std::map<int, std::pair<int, int>> tc_plan;  // k -> (query tiles of the tensor-core scan (0: does
                                                // not fit), keys per lane quarter's lists)
 
+  bool schedule = true;    // multi-batch calls cut batches in route-leaf order
+  leafi::Schedule sched;
   int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries
   double calib_confidence = 0.95;  // probability that a certified position meets its target
   std::map<std::pair<int64_t, double>, double> rq_cache;  // (N, target) -> required quality

@@ -760,21 +760,24 @@ __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double*
   if (lane == 0) jpos[q] = j;
 }
 
+// results of batch query q go to row rows[q] of ids / dists (row q without rows)
 __global__ void write_results_kernel(int nq, int kmax, const int32_t* __restrict__ kq,
                                      const u64* __restrict__ topk, int kstride,
-                                     const int32_t* __restrict__ topk_cnt, int64_t* __restrict__ ids,
+                                     const int32_t* __restrict__ topk_cnt,
+                                     const int32_t* __restrict__ rows, int64_t* __restrict__ ids,
                                      float* __restrict__ dists) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nq * kmax) return;
   const int q = t / kmax, z = t % kmax;
+  const size_t o = (size_t)(rows ? rows[q] : q) * kmax + z;
   const int lim = min(kq ? kq[q] : kmax, topk_cnt[q]);
   if (z < lim) {
     const u64 key = topk[(size_t)q * kstride + z];
-    ids[t] = (int64_t)(uint32_t)(key & 0xffffffffull);
-    dists[t] = __fsqrt_rn(key_d2(key));
+    ids[o] = (int64_t)(uint32_t)(key & 0xffffffffull);
+    dists[o] = __fsqrt_rn(key_d2(key));
   } else {
-    ids[t] = -1;
-    dists[t] = __int_as_float(0x7f800000);
+    ids[o] = -1;
+    dists[o] = __int_as_float(0x7f800000);
   }
 }
 
@@ -911,10 +914,10 @@ void launch_jpos(int nq, const int32_t* k, const double* target, int nk, const i
 
 void launch_write_results(int nq, int kmax, const int32_t* kq, const unsigned long long* topk,
                           int kstride, const int32_t* topk_cnt, int64_t* ids, float* dists,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int32_t* rows) {
   if (nq * kmax == 0) return;
   write_results_kernel<<<nblk((int64_t)nq * kmax, 256), 256, 0, s>>>(nq, kmax, kq, topk, kstride,
-                                                                     topk_cnt, ids, dists);
+                                                                     topk_cnt, rows, ids, dists);
   LF_CHECK_LAUNCH();
 }
 

@@ -573,3 +573,47 @@ def test_leaf_selection_alg3_with_measured_costs(ds):
         expect = O.select_leaves_alg3(sizes, rep["threshold"], rep["filter_bytes"], cap)
         assert np.array_equal(fl, expect)
         assert rep["n_selected"] == len(fl)
+
+
+def test_query_schedule_keeps_every_result(ds, tuned):
+    """A call of several batches cut in route-leaf order returns, row for row,
+    what the caller's order returns: exact, LeaFi and mixed requests, with host
+    and device output arrays."""
+    torch = pytest.importorskip("torch")
+    X, Q, idx, t = ds
+    fl, Wt, Qc, tables = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_set_autotuners(idx, tables[1][0], np.stack([tables[1][1], tables[10][1]]), [1, 10])
+    lf.leafi_set_calibration_confidence(idx, 0.0)
+    Qm = fx.test_queries(X, 700, seed=404)        # three batches
+    rng = np.random.default_rng(405)
+    kq = rng.choice([1, 3, 10], 700).astype(np.int32)
+    tg = rng.choice([0.9, 0.95, 1.0], 700).astype(np.float64)
+    runs = {}
+    try:
+        for on in (False, True):
+            lf.leafi_set_query_schedule(idx, on)
+            r = []
+            for k, target in ((5, 1.0), (1, 0.9), (10, 0.95)):
+                ids = np.zeros((700, k), np.int64)
+                d = np.zeros((700, k), np.float32)
+                st = lf.SearchStats()
+                lf.leafi_search(idx, Qm, k, target, ids, d, st)
+                r += [ids, d, st.series_scanned, st.leaves_scanned]
+            ids = np.zeros((700, 10), np.int64)
+            d = np.zeros((700, 10), np.float32)
+            lf.leafi_search_mixed(idx, Qm, kq, tg, 10, ids, d)
+            r += [ids, d]
+            di = torch.zeros((700, 5), dtype=torch.int64, device="cuda")
+            dd = torch.zeros((700, 5), dtype=torch.float32, device="cuda")
+            lf.leafi_search(idx, torch.from_numpy(Qm).cuda(), 5, 1.0, di, dd)
+            torch.cuda.synchronize()
+            r += [di.cpu().numpy(), dd.cpu().numpy()]
+            runs[on] = r
+        for a, b in zip(runs[False], runs[True]):
+            assert np.array_equal(a, b)
+        bf, _ = O.knn(X, Qm[:50], 5)
+        assert np.array_equal(runs[True][0][:50], bf)
+    finally:
+        lf.leafi_set_query_schedule(idx, True)
+        lf.leafi_set_calibration_confidence(idx, 0.95)
