@@ -45,7 +45,9 @@ FP32_LANES = 128
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # eight consecutive launches of the timed region, averaged), valid only for the
 # kernel code it was taken on (SHA-1 of k_scan_tc.cu without comments and blank lines)
-SCAN_TRAFFIC = {"bytes_per_launch": 418.2e6, "kernel_sha1": "934ae00f3214b2480e6b5d7011d0e1b581bb29d0"}
+SCAN_TRAFFIC = {"bytes_per_launch": 418.2e6, "kernel_sha1": "934ae00f3214b2480e6b5d7011d0e1b581bb29d0",
+                "source": "stored ncu capture (profiles/leaf_scan_tc_dram_1M.md), not measured "
+                          "in this run"}
 
 
 def code_sha1(path):
@@ -83,6 +85,9 @@ def parse():
     ap.add_argument("--target", type=float, default=0.99)
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-schedule", action="store_true",
+                    help="batches in the callers' query order (no route-leaf scheduling)")
+    ap.add_argument("--lanes", type=int, default=8, help="batches of one call in flight")
     a = ap.parse_args()
     dflt = {"batched": (1_000_000, 10_000, 100), "ablation": (1_000_000, 10_000, 100),
             "serving": (50_000_000, 10_000, 1000),
@@ -213,6 +218,8 @@ def workload_config(a):
             "n_series": a.n, "length": M, "leaf_capacity": a.leaf_cap, "filters": a.filters,
             "queries": a.queries, "launch": a.launch, "recall_target": a.target,
             "k": 1, "wave": a.wave,
+            "schedule": "route-leaf order" if not getattr(a, "no_schedule", False) else "caller order",
+            "lanes": getattr(a, "lanes", 8),
             "l2": "inputs larger than L2 (%.2f GB float32 series, %.2f GB float16 copy)"
                   % (a.n * M * 4 / 1e9, a.n * M * 2 / 1e9)}
 
@@ -648,6 +655,8 @@ def main():
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=local))
     stream = torch.cuda.current_stream(dev)
     lf.leafi_set_stream(idx, stream.cuda_stream)
+    lf.leafi_set_query_schedule(idx, not a.no_schedule)
+    lf.leafi_set_search_lanes(idx, a.lanes)
     t_train = time.perf_counter()
     enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs)
     torch.cuda.synchronize()
@@ -718,7 +727,27 @@ def main():
 
     # exact (plain-bound) search: ground truth and the comparison arm
     ms_ex, lat_ex, st_ex, _, _, _ = timed(1.0, ex_ids, ex_d)
-    ms, lat, st, launches, clocks, kt = timed(a.target, ids, dd, profile=True)
+    ms, lat, st, launches, clocks, kt = timed(a.target, ids, dd, profile=False)
+    # the scan alone: the same steps with one lane (batches one after another,
+    # so no scan launch waits for SMs held by another lane's), every leaf-scan
+    # launch timed with CUDA events on the lane stream it runs on
+    lf.leafi_set_search_lanes(idx, 1)
+    run(a.target, ids, dd)
+    lf.leafi_set_profiling(idx, 1)
+    ser_stats = {}
+    torch.cuda.synchronize()
+    e0s = torch.cuda.Event(enable_timing=True)
+    e1s = torch.cuda.Event(enable_timing=True)
+    ser_steps = max(3, a.steps // 4)
+    e0s.record(stream)
+    for _ in range(ser_steps):
+        run(a.target, ids, dd, None, ser_stats)
+    e1s.record(stream)
+    torch.cuda.synchronize()
+    ser_ms = e0s.elapsed_time(e1s) / ser_steps
+    kt = lf.leafi_get_kernel_times(idx)
+    lf.leafi_set_profiling(idx, 0)
+    lf.leafi_set_search_lanes(idx, a.lanes)
     # Alg. 3 with this device's costs (the run above uses the configuration's
     # 100 largest leaves, i.e. th = 0)
     sel_fl, sel_rep = lf.leafi_select_leaves_auto(idx, a=2.0, mem_cap=8 << 30)
@@ -750,66 +779,70 @@ def main():
     e2e = {"value": world * a.queries / (e2e_ms / 1e3), "unit": "queries/s",
            "h2d_bytes_per_step": a.queries * M * 4, "d2h_bytes_per_step": a.queries * (8 + 4)}
 
-    # roofline of the dominant kernel (leaf scan), from per-launch CUDA events
+    # roofline of the dominant kernel (leaf scan).  Algorithmic bytes per launch:
+    # the series of the distinct leaves each scan round reads x the bytes of one
+    # scanned row (float16 rows of kp halves on the tensor-core path).  Duration:
+    # the mean CUDA-event time of the leaf-scan launches in the serialised pass.
     pk, pk_kind = peaks()
-    scan_ms, scan_n = kt["leaf_scan"]
-    pairs = st["series_scanned"] / a.steps          # (query, series) distances per step
-    distinct = st["distinct_series"] / a.steps      # series of distinct leaves per round, per step
-    scan_launch_ms = scan_ms / max(scan_n, 1)
-    per_launch_pairs = pairs / max(scan_n / a.steps, 1)
-    flops_launch = per_launch_pairs * M * 3.0       # t = q - x; acc = fma(t, t, acc)
-    achieved_tf = flops_launch / (scan_launch_ms / 1e3) / 1e12
-    clk = pk.get("sm_max_mhz", 2032.0)
-    alu_peak = SMS * FP32_LANES * clk * 1e6 * 1.5 / 1e12   # FSUB+FFMA issue 3 FLOP per 2 instr
-    bytes_launch = distinct * info.scan_row_bytes / max(scan_n / a.steps, 1)
-    achieved_gbs = bytes_launch / (scan_launch_ms / 1e3) / 1e9
     hbm = pk.get("hbm_gbs", 6400.0)
-    roof_alu = achieved_tf / alu_peak
+    clk = pk.get("sm_max_mhz", 2032.0)
+    scan_ms, scan_n = kt["leaf_scan"]
+    scan_launch_ms = scan_ms / max(scan_n, 1)
+    bytes_launch = ser_stats["distinct_series"] * info.scan_row_bytes / max(scan_n, 1)
+    pairs_launch = ser_stats["series_scanned"] / max(scan_n, 1)
+    achieved_gbs = bytes_launch / (scan_launch_ms / 1e3) / 1e9
     roof_hbm = achieved_gbs / hbm
+    # the whole timed (eight-lane) step charged to the scan: a lower bound
+    step_bytes = st["distinct_series"] / a.steps * info.scan_row_bytes
+    step_view = {"achieved_gbs": step_bytes / (ms / 1e3) / 1e9,
+                 "frac": step_bytes / (ms / 1e3) / 1e9 / hbm,
+                 "bytes_per_step": step_bytes, "ms_per_step": ms}
+    cross = {"scan_ms_per_step": scan_ms / ser_steps, "serialised_ms_per_step": ser_ms,
+             "scan_share": scan_ms / ser_steps / ser_ms}
+    traffic, traffic_src = None, None
+    try:
+        src = os.path.join(ROOT, "paper_2502_01836_b300", "csrc", "k_scan_tc.cu")
+        same_kernel = code_sha1(src) == SCAN_TRAFFIC["kernel_sha1"]
+        default_workload = (a.n, a.leaf_cap, a.filters, a.launch, a.wave) == \
+            (1_000_000, 10_000, 100, 256, 64)
+        if info.tensor_scan and same_kernel and default_workload:
+            traffic = SCAN_TRAFFIC["bytes_per_launch"]
+            traffic_src = SCAN_TRAFFIC["source"]
+    except OSError:
+        pass
     if info.tensor_scan:
-        # float16 dot products on tcgen05: the contraction is far below the tensor
-        # peak (2 m FLOP per pair), so the stream of distinct float16 rows is the bound
-        tc_tf = per_launch_pairs * 2.0 * M / (scan_launch_ms / 1e3) / 1e12
+        tc_tf = pairs_launch * 2.0 * M / (scan_launch_ms / 1e3) / 1e12
         tc_peak = pk.get("bf16_tflops", 1800.0)
-        traffic = None
-        try:
-            src = os.path.join(ROOT, "paper_2502_01836_b300", "csrc", "k_scan_tc.cu")
-            same_kernel = code_sha1(src) == SCAN_TRAFFIC["kernel_sha1"]
-            default_workload = (a.n, a.leaf_cap, a.filters, a.launch, a.wave) == \
-                (1_000_000, 10_000, 100, 256, 64)
-            if same_kernel and default_workload:
-                traffic = SCAN_TRAFFIC["bytes_per_launch"]
-        except OSError:
-            pass
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": roof_hbm, "traffic": traffic, "peak_source": pk_kind,
-                    "bytes_per_launch": bytes_launch,
+                    "frac": roof_hbm, "traffic": traffic, "traffic_source": traffic_src,
+                    "peak_source": pk_kind, "bytes_per_launch": bytes_launch,
+                    "launch_ms": scan_launch_ms,
+                    "measured": "leaf-scan launches of %d one-lane steps (serialised), CUDA "
+                                "events on the launching stream" % ser_steps,
                     "tensor_view": {"achieved_tflops": tc_tf, "peak": tc_peak,
                                     "frac": tc_tf / tc_peak,
                                     "peak_source": "fp16 dense = measured bf16 burst rate"}}
-    elif roof_alu >= roof_hbm:
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": roof_alu, "traffic": None,
-                    "peak_source": "148 SMs x 128 FP32 lanes x %.0f MHz x 1.5 FLOP/instr (%s clocks)"
-                                   % (clk, pk_kind)}
     else:
-        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": roof_hbm, "traffic": None, "peak_source": pk_kind}
+        alu_peak = SMS * FP32_LANES * clk * 1e6 * 1.5 / 1e12   # FSUB+FFMA: 3 FLOP per 2 instr
+        achieved_tf = pairs_launch * M * 3.0 / (scan_launch_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved_tf / alu_peak, "traffic": None,
+                    "peak_source": "148 SMs x 128 FP32 lanes x %.0f MHz x 1.5 FLOP/instr (%s clocks)"
+                                   % (clk, pk_kind),
+                    "hbm_view": {"achieved_gbs": achieved_gbs, "frac": roof_hbm}}
     roofline["kernel"] = "leaf_scan (tensor cores)" if info.tensor_scan else "leaf_scan (CUDA cores)"
+    roofline["step_view"] = step_view
+    roofline["cross_check"] = cross
+    roofline["bytes_per_series"] = info.scan_row_bytes
     span = kt_all.get("_phases", {}).get("epilogue_span", 0.0)
     if info.tensor_scan and span > 0:
         # the same bytes over the time a CTA is resident (per-SM cycle counter of
-        # the profiled step): separates the kernel's own rate from launch gaps and
-        # from waiting for SMs held by the other lane's scan
-        step_bytes = distinct * info.scan_row_bytes
+        # the profiled eight-lane step)
         resident_s = span / SMS / (clock_mhz(clocks, clk) * 1e6)
-        roofline["resident_view"] = {"achieved_gbs": step_bytes / resident_s / 1e9,
-                                     "frac": step_bytes / resident_s / 1e9 / hbm,
+        distinct = st["distinct_series"] / a.steps
+        roofline["resident_view"] = {"achieved_gbs": distinct * info.scan_row_bytes / resident_s / 1e9,
+                                     "frac": distinct * info.scan_row_bytes / resident_s / 1e9 / hbm,
                                      "resident_ms_per_step": resident_s * 1e3}
-    roofline["bytes_per_series"] = info.scan_row_bytes
-    roofline["hbm_view"] = {"achieved_gbs": achieved_gbs, "frac": roof_hbm}
-    if not info.tensor_scan:
-        roofline["alu_view"] = {"achieved_tflops": achieved_tf, "frac": roof_alu}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:

@@ -399,6 +399,12 @@ typedef struct {
 leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
                           double recall_target, int64_t* ids, float* dists,
                           leafi_search_stats* stats);
+/* Batches of one search call in flight, 1..8 (default 8): each has its own
+ * scratch and stream, so one batch's bounds, filters and host round trips
+ * overlap another's scan.  One lane runs the batches one after another (the
+ * scan launches are then serialised, e.g. to time them alone). */
+leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes);
+
 /* Query scheduling of calls with more than one internal batch (on by
  * default): the batches are cut from the queries in order of their route
  * leaf, so that each batch's queries need largely the same leaves and the

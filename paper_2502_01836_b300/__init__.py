@@ -29,7 +29,7 @@ __all__ = [
     "SgdParams", "TrainReport", "leafi_train_filters_on", "leafi_training_queries",
     "leafi_initial_weights", "leafi_epoch_permutations", "leafi_znormalize",
     "leafi_get_filter_leaves", "leafi_debug_set_lock_tries", "leafi_debug_fail_allocations",
-    "leafi_set_calibration_confidence", "leafi_set_query_schedule",
+    "leafi_set_calibration_confidence", "leafi_set_query_schedule", "leafi_set_search_lanes",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -55,7 +55,7 @@ EXPORTED_SYMBOLS = [
     "leafi_training_queries", "leafi_initial_weights", "leafi_epoch_permutations",
     "leafi_znormalize", "leafi_get_filter_leaves", "leafi_debug_set_lock_tries",
     "leafi_debug_fail_allocations", "leafi_set_calibration_confidence",
-    "leafi_set_query_schedule",
+    "leafi_set_query_schedule", "leafi_set_search_lanes",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -193,6 +193,7 @@ def lib():
             "leafi_debug_fail_allocations": [i64],
             "leafi_set_calibration_confidence": [vp, f64],
             "leafi_set_query_schedule": [vp, i32],
+            "leafi_set_search_lanes": [vp, i32],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
@@ -396,6 +397,11 @@ def leafi_set_calibration_confidence(index, confidence):
 def leafi_set_query_schedule(index, on=True):
     """Cut multi-batch calls' batches in route-leaf order (results unchanged)."""
     _check(lib().leafi_set_query_schedule(index, int(bool(on))))
+
+
+def leafi_set_search_lanes(index, lanes):
+    """Batches of one search call in flight (1..8)."""
+    _check(lib().leafi_set_search_lanes(index, int(lanes)))
 
 
 def leafi_get_filter_leaves(index):

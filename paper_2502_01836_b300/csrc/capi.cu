@@ -443,11 +443,13 @@ void check_err_word(leafi_index* ix) {
 }
 
 // bounds and routes for nq padded device queries
-void compute_bounds(leafi_index* ix, const float* dQ, int nq, double* lb2, int32_t* route) {
+// (have_p: the prefix sums are already in the lane's sP)
+void compute_bounds(leafi_index* ix, const float* dQ, int nq, double* lb2, int32_t* route,
+                    bool have_p = false) {
   cudaStream_t s = ix->stream;
   const HostTree& t = ix->tree;
   double* P = ix->sc->sP.need((size_t)nq * 2 * (ix->m + 1));
-  launch_prefix(dQ, nq, ix->mp, ix->m, P, s);
+  if (!have_p) launch_prefix(dQ, nq, ix->mp, ix->m, P, s);
   if (t.type == LEAFI_DSTREE) {
     double* iv = ix->sc->sIv.need((size_t)nq * t.iv_s.size() * 2);
     double* nodes = ix->sc->sNode.need((size_t)nq * t.n_nodes);
@@ -579,6 +581,16 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t*
       reinterpret_cast<const float4*>(src)[(int64_t)rows[i] * mp4 + c];
 }
 
+// dst row i = src row rows[i] (rows of w doubles)
+__global__ void gather_rows_f64_kernel(const double* __restrict__ src,
+                                       const int32_t* __restrict__ rows, int nb, int w,
+                                       double* __restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nb * w) return;
+  const int i = (int)(t / w), c = (int)(t % w);
+  dst[t] = src[(int64_t)rows[i] * w + c];
+}
+
 __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, double tval) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nb) {
@@ -630,6 +642,7 @@ struct Pipeline {
   int nlanes = 1;
   int kmax = 1, W = 1, L = 0, cap = 0, qb = kBatch;
   unsigned long long* stat = nullptr;   // device counters of the pipeline's batches
+  bool pre_p = false;                   // scheduled batches: prefix sums gathered, not computed
   leafi_search_stats st{};
   LaneView lv[kMaxLanes];
   InFlight fl[kMaxLanes];
@@ -656,8 +669,9 @@ struct Pipeline {
              bool uniform, int64_t* ids, float* dists);
   // the same for a scheduled batch: its queries are rows `rows` (device) of the
   // staged query array dQall and its results go to those rows of out_i / out_d
-  void start_rows(int li, const float* dQall, const int32_t* rows, int nb, const int32_t* kq,
-                  const double* target, bool uniform, int64_t* out_i, float* out_d);
+  void start_rows(int li, const float* dQall, const double* Pall, const int32_t* rows, int nb,
+                  const int32_t* kq, const double* target, bool uniform, int64_t* out_i,
+                  float* out_d);
   void launch_batch(int li, int nb, const int32_t* kq, const double* target, bool uniform);
   // wait for lane li's batch, run its remaining waves, deliver its results
   void finish(int li);
@@ -786,7 +800,7 @@ void Pipeline::round(const LaneView& v, int nb) {
 void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
   make_sa(v, nb, use_f);
   ix->tick(2);
-  compute_bounds(ix, v.gQ, nb, v.lb2, v.route);
+  compute_bounds(ix, v.gQ, nb, v.lb2, v.route, pre_p);
   ix->tock();
   if (v.tq.Qh) launch_tc_query_prep(v.gQ, nb, ix->mp, ix->kp, v.tq.Qh, v.tq.Qk, s);
   if (use_f) {
@@ -815,7 +829,8 @@ BatchGraph* Pipeline::graph_for(const LaneView& v, int nb, bool use_f) {
   const unsigned long long epoch0 = g_realloc_epoch;
   for (auto& g : graphs)
     if (g.nb == nb && g.kmax == kmax && g.use_f == (int)use_f &&
-        g.profiling == (int)ix->profiling && g.epoch == epoch0 && g.gen == ix->graph_gen)
+        g.profiling == (int)ix->profiling && g.pre_p == (int)pre_p && g.epoch == epoch0 &&
+        g.gen == ix->graph_gen)
       return &g;
   // graphs of an older epoch point at freed scratch, of an older generation
   // at replaced filters or tables: drop them
@@ -835,6 +850,7 @@ BatchGraph* Pipeline::graph_for(const LaneView& v, int nb, bool use_f) {
   g.kmax = kmax;
   g.use_f = use_f;
   g.profiling = ix->profiling;
+  g.pre_p = pre_p;
   g.epoch = epoch0;
   g.gen = ix->graph_gen;
   // the lane stream is the library's own (never the legacy default stream);
@@ -894,13 +910,19 @@ void Pipeline::start(int li, const float* queries, int nb, const int32_t* kq, co
   launch_batch(li, nb, kq, target, uniform);
 }
 
-void Pipeline::start_rows(int li, const float* dQall, const int32_t* rows, int nb,
-                          const int32_t* kq, const double* target, bool uniform, int64_t* out_i,
-                          float* out_d) {
+void Pipeline::start_rows(int li, const float* dQall, const double* Pall, const int32_t* rows,
+                          int nb, const int32_t* kq, const double* target, bool uniform,
+                          int64_t* out_i, float* out_d) {
   use_lane(li);
   const LaneView& v = lv[li];
   const int64_t n4 = (int64_t)nb * (ix->mp / 4);
   gather_rows_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(dQall, rows, nb, ix->mp, v.gQ);
+  LF_CHECK_LAUNCH();
+  // the call's prefix sums, computed once for scheduling, serve the bounds
+  const int w = 2 * (ix->m + 1);
+  const int64_t np = (int64_t)nb * w;
+  gather_rows_f64_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
+      Pall, rows, nb, w, lanes[li].sP.p);
   LF_CHECK_LAUNCH();
   fl[li] = InFlight();
   fl[li].ids = out_i;
@@ -988,7 +1010,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
   if (any_filtered) ensure_wsplit(ix);
   const int qb = kBatch;
-  const int nlanes = (int)std::min<int64_t>(kSearchLanes, (nq + qb - 1) / qb);
+  const int nlanes = (int)std::min<int64_t>(ix->search_lanes, (nq + qb - 1) / qb);
   const cudaStream_t user = ix->stream;
   // every entry point after this one runs on lanes[0] and the caller's stream
   struct Restore {
@@ -1019,6 +1041,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   // order of their route leaf (original order among equals); each batch then
   // reads a smaller union of leaves.  Results go back to the callers' rows.
   const bool sched = ix->schedule && nq > qb;
+  pl.pre_p = sched;
   const float* dQall = nullptr;
   const int32_t* dperm = nullptr;
   int64_t* out_i = ids;
@@ -1063,7 +1086,8 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     const int nb = (int)std::min<int64_t>(qb, nq - b0);
     pl.finish(li);  // the lane's previous batch (nlanes batches back)
     if (sched)
-      pl.start_rows(li, dQall, dperm + b0, nb, (uniform ? kq.data() : kq_s.data() + b0),
+      pl.start_rows(li, dQall, ix->sched.P.p, dperm + b0, nb,
+                    (uniform ? kq.data() : kq_s.data() + b0),
                     (uniform ? target.data() : tg_s.data() + b0), uniform, out_i, out_d);
     else
       pl.start(li, queries + (size_t)b0 * ix->m, nb, kq.data() + (uniform ? 0 : b0),
@@ -2368,6 +2392,15 @@ leafi_status leafi_znormalize(const float* x, int64_t n, int32_t m, float* out, 
                                 s));
       LF_CUDA(cudaStreamSynchronize(s));
     }
+  });
+}
+
+leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes) {
+  return guarded([&] {
+    require_device(index);
+    if (lanes < 1 || lanes > kSearchLanes) fail(LEAFI_EINVAL, "lanes must be in [1, %d]", kSearchLanes);
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->search_lanes = lanes;
   });
 }
 

@@ -288,7 +288,7 @@ struct SelectArgs {
 // one captured search batch (full 256-query batch, route round + one wave)
 struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
-  int nb = 0, kmax = 0, use_f = 0, profiling = 0;
+  int nb = 0, kmax = 0, use_f = 0, profiling = 0, pre_p = 0;
   unsigned long long epoch = 0;
   unsigned long long gen = 0;   // leafi_index::graph_gen at capture
   long long launches = 0;       // kernels in the graph (added to the launch counter per replay)
@@ -446,6 +446,7 @@ struct leafi_index {
                                                // not fit), keys per lane quarter's lists)
 
   bool schedule = true;    // multi-batch calls cut batches in route-leaf order
+  int search_lanes = 8;    // batches of one search call in flight (leafi_set_search_lanes)
   leafi::Schedule sched;
   int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries
   double calib_confidence = 0.95;  // probability that a certified position meets its target

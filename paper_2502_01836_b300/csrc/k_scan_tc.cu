@@ -1166,15 +1166,29 @@ void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, fl
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s) {
   const size_t smem = tc_dyn_smem(a.kp, a.k, a.nbuf, a.qkeys);
-  if (a.k == 1) {
-    LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    tc_scan_kernel<true><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
-  } else {
-    LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    tc_scan_kernel<false><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
+  // the opt-in shared-memory size is raised only when a launch needs more than
+  // any earlier one on this device (the attribute persists)
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, size_t> set;  // (device, instantiation) -> bytes
+  int dev = 0;
+  LF_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& have = set[{dev, a.k == 1 ? 1 : 0}];
+    if (smem > have) {
+      if (a.k == 1)
+        LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      else
+        LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      have = smem;
+    }
   }
+  if (a.k == 1)
+    tc_scan_kernel<true><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
+  else
+    tc_scan_kernel<false><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
   LF_CHECK_LAUNCH();
 }
 
