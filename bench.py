@@ -88,6 +88,7 @@ def parse():
     ap.add_argument("--no-schedule", action="store_true",
                     help="batches in the callers' query order (no route-leaf scheduling)")
     ap.add_argument("--lanes", type=int, default=8, help="batches of one call in flight")
+    ap.add_argument("--part", type=int, default=2048, help="series per leaf-scan work item")
     a = ap.parse_args()
     dflt = {"batched": (1_000_000, 10_000, 100), "ablation": (1_000_000, 10_000, 100),
             "serving": (50_000_000, 10_000, 1000),
@@ -219,7 +220,7 @@ def workload_config(a):
             "queries": a.queries, "launch": a.launch, "recall_target": a.target,
             "k": 1, "wave": a.wave,
             "schedule": "route-leaf order" if not getattr(a, "no_schedule", False) else "caller order",
-            "lanes": getattr(a, "lanes", 8),
+            "lanes": getattr(a, "lanes", 8), "part": getattr(a, "part", 2048),
             "l2": "inputs larger than L2 (%.2f GB float32 series, %.2f GB float16 copy)"
                   % (a.n * M * 4 / 1e9, a.n * M * 2 / 1e9)}
 
@@ -657,6 +658,7 @@ def main():
     lf.leafi_set_stream(idx, stream.cuda_stream)
     lf.leafi_set_query_schedule(idx, not a.no_schedule)
     lf.leafi_set_search_lanes(idx, a.lanes)
+    lf.leafi_set_scan_part(idx, a.part)
     t_train = time.perf_counter()
     enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs)
     torch.cuda.synchronize()

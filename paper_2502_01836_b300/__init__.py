@@ -30,6 +30,7 @@ __all__ = [
     "leafi_initial_weights", "leafi_epoch_permutations", "leafi_znormalize",
     "leafi_get_filter_leaves", "leafi_debug_set_lock_tries", "leafi_debug_fail_allocations",
     "leafi_set_calibration_confidence", "leafi_set_query_schedule", "leafi_set_search_lanes",
+    "leafi_set_scan_part",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -55,7 +56,7 @@ EXPORTED_SYMBOLS = [
     "leafi_training_queries", "leafi_initial_weights", "leafi_epoch_permutations",
     "leafi_znormalize", "leafi_get_filter_leaves", "leafi_debug_set_lock_tries",
     "leafi_debug_fail_allocations", "leafi_set_calibration_confidence",
-    "leafi_set_query_schedule", "leafi_set_search_lanes",
+    "leafi_set_query_schedule", "leafi_set_search_lanes", "leafi_set_scan_part",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -194,6 +195,7 @@ def lib():
             "leafi_set_calibration_confidence": [vp, f64],
             "leafi_set_query_schedule": [vp, i32],
             "leafi_set_search_lanes": [vp, i32],
+            "leafi_set_scan_part": [vp, i32],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
@@ -402,6 +404,11 @@ def leafi_set_query_schedule(index, on=True):
 def leafi_set_search_lanes(index, lanes):
     """Batches of one search call in flight (1..8)."""
     _check(lib().leafi_set_search_lanes(index, int(lanes)))
+
+
+def leafi_set_scan_part(index, rows):
+    """Series per leaf-scan work item (multiple of 128)."""
+    _check(lib().leafi_set_scan_part(index, int(rows)))
 
 
 def leafi_get_filter_leaves(index):

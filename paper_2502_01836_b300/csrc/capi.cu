@@ -26,7 +26,6 @@ unsigned long long g_realloc_epoch = 0;
 
 namespace {
 thread_local std::string g_last_error;
-constexpr int kPart = 2048;       // series per scan work item
 constexpr int kBatch = 256;       // queries per search batch
 constexpr int kSearchLanes = 8;   // batches of one search call in flight
 constexpr int kServeLanes = 4;    // batches of a server in flight
@@ -161,7 +160,10 @@ int64_t max_leaf_size(const HostTree& t) {
   return mx;
 }
 
-int max_parts(const HostTree& t) { return (int)((max_leaf_size(t) + kPart - 1) / kPart); }
+// parts (work items of ix->part series) of the largest leaf
+int max_parts(const leafi_index* ix) {
+  return (int)((max_leaf_size(ix->tree) + ix->part - 1) / ix->part);
+}
 
 __global__ void sqrt_kernel(const float* __restrict__ in, float* __restrict__ out, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -351,8 +353,8 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
   const bool use_tc = nbuf > 0;
   const bool var_groups = use_tc && kstride > 1;  // groups bounded by the sum of their k
   int32_t* item_leaf =
-      use_tc ? ix->sc->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix->tree)) : nullptr;
-  launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, kPart,
+      use_tc ? ix->sc->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix)) : nullptr;
+  launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, ix->part,
                use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped, nitems,
                distinct_stat, s, var_groups ? nullptr : item_leaf,
                use_tc && !var_groups && ix->pack_small);
@@ -361,7 +363,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     int32_t* ngr = ix->sc->sNGroups.need(L);
     gfirst = ix->sc->sGFirst.need(L + 1);
     gbound = ix->sc->sGBound.need((size_t)std::max(npairs_max, 1) + 1);
-    launch_var_groups(L, ix->leaf_off.p, kPart, goff, grouped, slot_k, kstride, qkeys, ngr, gfirst,
+    launch_var_groups(L, ix->leaf_off.p, ix->part, goff, grouped, slot_k, kstride, qkeys, ngr, gfirst,
                       gbound, ioff, item_leaf, nitems, s);
   }
   const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
@@ -376,7 +378,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.mp = ix->mp;
     t.kp = ix->kp;
     t.k = kstride;
-    t.part = kPart;
+    t.part = ix->part;
     t.Q = dQ;
     t.Qh = tq.Qh;
     t.Qk = tq.Qk;
@@ -413,7 +415,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
   a.L = L;
   a.mp = ix->mp;
   a.k = kstride;
-  a.part = kPart;
+  a.part = ix->part;
   a.Q = dQ;
   a.pairs = grouped;
   a.grp_off = goff;
@@ -466,7 +468,7 @@ void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dL
   cudaStream_t s = ix->stream;
   const int L = ix->tree.n_leaves;
   const int nslots = nq * nl;
-  const int cap = max_parts(ix->tree) * k;
+  const int cap = max_parts(ix) * k;
   topk.need((size_t)nslots * k);
   topk_cnt.need(nslots);
   unsigned long long* thr = ix->sc->sThr.need(nslots);
@@ -692,7 +694,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
   W = std::min(ix->wave, std::max(L, 1));  // wider waves take every leaf all the same
   // the tensor-core scan merges into the top-k lists directly; the CUDA-core
   // scan appends every work item's list to a candidate buffer
-  cap = tc_nbuf(ix, kmax) > 0 ? 0 : std::max(W, 1) * max_parts(t) * kmax;
+  cap = tc_nbuf(ix, kmax) > 0 ? 0 : std::max(W, 1) * max_parts(ix) * kmax;
   qb = kBatch;
   for (int li = 0; li < nlanes; ++li) {
     Scratch& S = lanes[li];
@@ -728,7 +730,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     if (ix->tc_ok && ix->scan_path == 0) {
       v.tq.Qh = S.sQh.need((size_t)qb * ix->kp);
       v.tq.Qk = S.sQk.need((size_t)2 * qb);
-      S.sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(t));
+      S.sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(ix));
       S.sWork.need(1);
       S.sGlock.need(qb);
       if (kmax > 1) {
@@ -2401,6 +2403,16 @@ leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes) {
     if (lanes < 1 || lanes > kSearchLanes) fail(LEAFI_EINVAL, "lanes must be in [1, %d]", kSearchLanes);
     std::lock_guard<std::mutex> lk(index->mu);
     index->search_lanes = lanes;
+  });
+}
+
+leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows) {
+  return guarded([&] {
+    require_device(index);
+    if (rows < 128 || rows > 8192 || rows % 128) fail(LEAFI_EINVAL, "rows must be a multiple of 128 in [128, 8192]");
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->drop_graphs();
+    index->part = rows;
   });
 }
 

@@ -447,6 +447,7 @@ struct leafi_index {
 
   bool schedule = true;    // multi-batch calls cut batches in route-leaf order
   int search_lanes = 8;    // batches of one search call in flight (leafi_set_search_lanes)
+  int part = 2048;         // series per scan work item (leafi_set_scan_part)
   leafi::Schedule sched;
   int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries
   double calib_confidence = 0.95;  // probability that a certified position meets its target
