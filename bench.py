@@ -89,6 +89,8 @@ def parse():
                     help="batches in the callers' query order (no route-leaf scheduling)")
     ap.add_argument("--lanes", type=int, default=8, help="batches of one call in flight")
     ap.add_argument("--part", type=int, default=2048, help="series per leaf-scan work item")
+    ap.add_argument("--items-per-sm", type=int, default=4,
+                    help="scan work items per SM a round aims at (0: fixed part)")
     a = ap.parse_args()
     dflt = {"batched": (1_000_000, 10_000, 100), "ablation": (1_000_000, 10_000, 100),
             "serving": (50_000_000, 10_000, 1000),
@@ -221,6 +223,7 @@ def workload_config(a):
             "k": 1, "wave": a.wave,
             "schedule": "route-leaf order" if not getattr(a, "no_schedule", False) else "caller order",
             "lanes": getattr(a, "lanes", 8), "part": getattr(a, "part", 2048),
+            "items_per_sm": getattr(a, "items_per_sm", 4),
             "l2": "inputs larger than L2 (%.2f GB float32 series, %.2f GB float16 copy)"
                   % (a.n * M * 4 / 1e9, a.n * M * 2 / 1e9)}
 
@@ -658,7 +661,7 @@ def main():
     lf.leafi_set_stream(idx, stream.cuda_stream)
     lf.leafi_set_query_schedule(idx, not a.no_schedule)
     lf.leafi_set_search_lanes(idx, a.lanes)
-    lf.leafi_set_scan_part(idx, a.part)
+    lf.leafi_set_scan_part(idx, a.part, a.items_per_sm)
     t_train = time.perf_counter()
     enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs)
     torch.cuda.synchronize()

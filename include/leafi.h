@@ -405,11 +405,14 @@ leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, 
  * scan launches are then serialised, e.g. to time them alone). */
 leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes);
 
-/* Series per leaf-scan work item (a multiple of 128 in [128, 8192], default
- * 2048).  A work item is (leaf, part of `rows` series, group of queries);
- * smaller parts balance a scan launch's items better across the SMs, larger
- * ones cost less per item.  Results do not depend on it. */
-leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows);
+/* Work items of the leaf scan.  A work item is (leaf, part of at most `rows`
+ * series, group of queries); rows is a multiple of 128 in [128, 8192]
+ * (default 2048).  The tensor-core scan picks each round's part on the device:
+ * the largest of rows, rows / 2, ... (>= 128) that gives the round at least
+ * items_per_sm items per SM (default 4; 0 always uses rows), since a launch
+ * lasts as long as its most loaded SM.  Smaller parts balance better, larger
+ * ones cost less per item.  Results do not depend on either. */
+leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm);
 
 /* Query scheduling of calls with more than one internal batch (on by
  * default): the batches are cut from the queries in order of their route

@@ -195,7 +195,7 @@ def lib():
             "leafi_set_calibration_confidence": [vp, f64],
             "leafi_set_query_schedule": [vp, i32],
             "leafi_set_search_lanes": [vp, i32],
-            "leafi_set_scan_part": [vp, i32],
+            "leafi_set_scan_part": [vp, i32, i32],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
@@ -406,9 +406,10 @@ def leafi_set_search_lanes(index, lanes):
     _check(lib().leafi_set_search_lanes(index, int(lanes)))
 
 
-def leafi_set_scan_part(index, rows):
-    """Series per leaf-scan work item (multiple of 128)."""
-    _check(lib().leafi_set_scan_part(index, int(rows)))
+def leafi_set_scan_part(index, rows=2048, items_per_sm=4):
+    """Leaf-scan work items: at most `rows` series (multiple of 128); rounds aim at
+    items_per_sm items per SM (0: always `rows`)."""
+    _check(lib().leafi_set_scan_part(index, int(rows), int(items_per_sm)))
 
 
 def leafi_get_filter_leaves(index):

@@ -352,19 +352,26 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
   const int nbuf = tq.Qh ? tc_nbuf(ix, kstride, &qkeys) : 0;
   const bool use_tc = nbuf > 0;
   const bool var_groups = use_tc && kstride > 1;  // groups bounded by the sum of their k
+  // the tensor-core scan's rounds pick their work-item size on the device: the
+  // largest of part, part / 2, ... that gives every SM several items
+  const int target = use_tc ? ix->items_per_sm * sm_count(ix->device) : 0;
+  int32_t* part_dev = use_tc ? ix->sc->sPart.need(1) : nullptr;
   int32_t* item_leaf =
-      use_tc ? ix->sc->sItemLeaf.need((size_t)std::max(npairs_max, 1) * max_parts(ix)) : nullptr;
+      use_tc ? ix->sc->sItemLeaf.need(std::max((size_t)std::max(npairs_max, 1) * max_parts(ix),
+                                               (size_t)3 * target + 1))
+             : nullptr;
   launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, ix->part,
                use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped, nitems,
                distinct_stat, s, var_groups ? nullptr : item_leaf,
-               use_tc && !var_groups && ix->pack_small);
+               use_tc && !var_groups && ix->pack_small, var_groups ? 0 : target,
+               var_groups ? nullptr : part_dev);
   int32_t *gfirst = nullptr, *gbound = nullptr;
   if (var_groups) {
     int32_t* ngr = ix->sc->sNGroups.need(L);
     gfirst = ix->sc->sGFirst.need(L + 1);
     gbound = ix->sc->sGBound.need((size_t)std::max(npairs_max, 1) + 1);
     launch_var_groups(L, ix->leaf_off.p, ix->part, goff, grouped, slot_k, kstride, qkeys, ngr, gfirst,
-                      gbound, ioff, item_leaf, nitems, s);
+                      gbound, ioff, item_leaf, nitems, s, target, part_dev);
   }
   const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
   if (use_tc) {
@@ -379,6 +386,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.kp = ix->kp;
     t.k = kstride;
     t.part = ix->part;
+    t.part_dev = part_dev;
     t.Q = dQ;
     t.Qh = tq.Qh;
     t.Qk = tq.Qk;
@@ -730,7 +738,9 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     if (ix->tc_ok && ix->scan_path == 0) {
       v.tq.Qh = S.sQh.need((size_t)qb * ix->kp);
       v.tq.Qk = S.sQk.need((size_t)2 * qb);
-      S.sItemLeaf.need((size_t)qb * std::max(W, 1) * max_parts(ix));
+      S.sItemLeaf.need(std::max((size_t)qb * std::max(W, 1) * max_parts(ix),
+                                (size_t)3 * ix->items_per_sm * sm_count(ix->device) + 1));
+      S.sPart.need(1);
       S.sWork.need(1);
       S.sGlock.need(qb);
       if (kmax > 1) {
@@ -2406,13 +2416,15 @@ leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes) {
   });
 }
 
-leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows) {
+leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm) {
   return guarded([&] {
     require_device(index);
     if (rows < 128 || rows > 8192 || rows % 128) fail(LEAFI_EINVAL, "rows must be a multiple of 128 in [128, 8192]");
+    if (items_per_sm < 0 || items_per_sm > 64) fail(LEAFI_EINVAL, "items_per_sm must be in [0, 64]");
     std::lock_guard<std::mutex> lk(index->mu);
     index->drop_graphs();
     index->part = rows;
+    index->items_per_sm = items_per_sm;
   });
 }
 

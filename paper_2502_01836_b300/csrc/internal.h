@@ -213,6 +213,8 @@ struct TcScanArgs {
   const int32_t* gfirst;           // k > 1: first query group of each leaf (launch_var_groups),
   const int32_t* gbound;           //   group starts in `pairs`; null: groups of G queries
   int qkeys;                       // k > 1: keys per TMEM lane quarter's lists (tc_scan_plan)
+  const int32_t* part_dev;         // the round's part size, chosen by the grouping kernels
+                                   // (nullptr: `part`)
   int32_t* work;                   // work-item counter (zero at launch)
   unsigned long long* topk;        // [nslots][k] ascending keys, kNoKey padded
                                    // (launch_tc_round_prep); work items merge into it
@@ -249,17 +251,21 @@ void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* s
 // at most 64 queries whose k sum to at most `budget`; gfirst [L + 1] = first
 // group of each leaf, gbound [groups + 1] = group starts in the grouped pairs,
 // item_off [L + 1] / item_leaf / n_items for the (part, group) work items
+// target_items > 0 (tensor-core scan): the round's part size is chosen on the
+// device among part, part / 2, ... (>= 128 rows) so that the round has at least
+// target_items work items if it can, and written to *part_out
 void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* grp_off,
                        const Pair* grouped, const int32_t* slot_k, int kstride, int budget,
                        int32_t* ngroups, int32_t* gfirst, int32_t* gbound, int32_t* item_off,
-                       int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s);
+                       int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s,
+                       int target_items = 0, int32_t* part_out = nullptr);
 // stat (nullable): stat[0] += series of the distinct leaves in this round;
 // g = queries per work item of the scan kernel that follows
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s, int32_t* item_leaf = nullptr,
-                  bool pack_small = false);
+                  bool pack_small = false, int target_items = 0, int32_t* part_out = nullptr);
 
 void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
                   int32_t* topk_cnt, unsigned long long* thr, const unsigned long long* cand,
@@ -371,6 +377,7 @@ struct Scratch {
   DBuf<Pair> sPairs, sGrouped;
   DBuf<unsigned long long> sTopk, sThr, sCand;
   DBuf<int32_t> sGlock;           // per slot locks of the tensor-core scan's top-k lists
+  DBuf<int32_t> sPart;            // the round's work-item rows (chosen by the grouping kernels)
   DBuf<int32_t> sNGroups, sGFirst, sGBound;  // k > 1: query groups sized by k (launch_var_groups)
   DBuf<float> sPred, sOutD;
   DBuf<int64_t> sOutI;
@@ -447,7 +454,9 @@ struct leafi_index {
 
   bool schedule = true;    // multi-batch calls cut batches in route-leaf order
   int search_lanes = 8;    // batches of one search call in flight (leafi_set_search_lanes)
-  int part = 2048;         // series per scan work item (leafi_set_scan_part)
+  int part = 2048;         // series per scan work item (leafi_set_scan_part); the tensor-core
+                           // scan's rounds may take part / 2, ... (>= 128) for balance
+  int items_per_sm = 4;    // work items per SM a tensor-core round aims at
   leafi::Schedule sched;
   int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries
   double calib_confidence = 0.95;  // probability that a certified position meets its target

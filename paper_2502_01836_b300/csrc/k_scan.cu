@@ -244,20 +244,42 @@ __device__ __forceinline__ int leaf_items(int c, const int64_t* __restrict__ lea
   return (int)((size + part - 1) / part) * ((c + g - 1) / g);
 }
 
+// Work-item size of a round (tensor-core scan): candidate parts part_max,
+// part_max / 2, ... (multiples of 128 rows); the largest whose item count
+// reaches `target` (a few items per SM, so that a launch's items balance)
+// is taken, else the smallest.  target 0 keeps part_max.
+constexpr int kPartLevels = 5;
+
+__device__ __forceinline__ int part_level(int part_max, int c) {
+  const int p = part_max >> c;
+  return p >= 128 ? (p / 128) * 128 : 128;
+}
+
+// thread's item counts per level have been added to tot[]; returns the level
+__device__ __forceinline__ int pick_part_level(const int* tot, int target) {
+  int c = 0;
+  while (c + 1 < kPartLevels && tot[c] < target) ++c;
+  return c;
+}
+
 // exclusive scans of per-leaf pair counts and work-item counts (one block)
-__global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part, int g,
+__global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part_max, int g,
                                int32_t* __restrict__ cnt, int32_t* __restrict__ grp_off,
                                int32_t* __restrict__ item_off, int32_t* __restrict__ n_items,
                                unsigned long long* __restrict__ stat,
-                               int32_t* __restrict__ item_leaf, bool pack_small) {
+                               int32_t* __restrict__ item_leaf, bool pack_small, int target,
+                               int32_t* __restrict__ part_out) {
   __shared__ int s_a[1024], s_b[1024];
+  __shared__ int tot[kPartLevels];
   const int T = blockDim.x;
   const bool pack = item_leaf != nullptr && pack_small;
   // whole windows per thread when packing
   const int win = pack ? kPackWin : 1;
   const int per = ((L + T - 1) / T + win - 1) / win * win;
   const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
-  int sa = 0, sb = 0;
+  if (threadIdx.x < kPartLevels) tot[threadIdx.x] = 0;
+  __syncthreads();
+  int sa = 0, sbl[kPartLevels] = {0, 0, 0, 0, 0};
   unsigned long long distinct = 0;
   for (int w0 = l0; w0 < l1; w0 += win) {
     const int w1 = min(l1, w0 + win);
@@ -266,12 +288,27 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
       if (cnt[l] > 0) distinct += (unsigned long long)(leaf_off[l + 1] - leaf_off[l]);
     }
     if (pack && window_packs(cnt, leaf_off, w0, w1, g)) {
-      sb += 1;
+#pragma unroll
+      for (int c = 0; c < kPartLevels; ++c) sbl[c] += 1;
     } else {
-      for (int l = w0; l < w1; ++l) sb += leaf_items(cnt[l], leaf_off, l, part, g);
+      for (int l = w0; l < w1; ++l)
+#pragma unroll
+        for (int c = 0; c < kPartLevels; ++c)
+          sbl[c] += leaf_items(cnt[l], leaf_off, l, part_level(part_max, c), g);
     }
   }
   if (stat && distinct) atomicAdd(stat, distinct);
+#pragma unroll
+  for (int c = 0; c < kPartLevels; ++c)
+    if (sbl[c]) atomicAdd(&tot[c], sbl[c]);
+  __syncthreads();
+  const int lev = pick_part_level(tot, target);
+  const int part = part_level(part_max, lev);
+  int sb = 0;
+#pragma unroll
+  for (int c = 0; c < kPartLevels; ++c)
+    if (c == lev) sb = sbl[c];
+  if (threadIdx.x == 0 && part_out) *part_out = part;
   s_a[threadIdx.x] = sa;
   s_b[threadIdx.x] = sb;
   __syncthreads();
@@ -319,14 +356,17 @@ constexpr int kFuseLeaves = 8192;
 
 __global__ void __launch_bounds__(1024) group_fused_kernel(
     const Pair* __restrict__ pairs, const int32_t* __restrict__ npairs, int L,
-    const int64_t* __restrict__ leaf_off, int part, int g, int32_t* __restrict__ grp_off,
+    const int64_t* __restrict__ leaf_off, int part_max, int g, int32_t* __restrict__ grp_off,
     int32_t* __restrict__ item_off, int32_t* __restrict__ n_items, Pair* __restrict__ grouped,
-    unsigned long long* __restrict__ stat, int32_t* __restrict__ item_leaf, bool pack_small) {
+    unsigned long long* __restrict__ stat, int32_t* __restrict__ item_leaf, bool pack_small,
+    int target, int32_t* __restrict__ part_out) {
   __shared__ int cnt[kFuseLeaves];
   __shared__ int s_a[1024], s_b[1024];
+  __shared__ int tot[kPartLevels];
   const int T = blockDim.x;
   const int np = *npairs;
   for (int l = threadIdx.x; l < L; l += T) cnt[l] = 0;
+  if (threadIdx.x < kPartLevels) tot[threadIdx.x] = 0;
   __syncthreads();
   for (int p = threadIdx.x; p < np; p += T) atomicAdd(&cnt[pairs[p].leaf], 1);
   __syncthreads();
@@ -335,7 +375,7 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
   const int win = pack ? kPackWin : 1;
   const int per = ((L + T - 1) / T + win - 1) / win * win;
   const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
-  int sa = 0, sb = 0;
+  int sa = 0, sbl[kPartLevels] = {0, 0, 0, 0, 0};
   unsigned long long distinct = 0;
   for (int w0 = l0; w0 < l1; w0 += win) {
     const int w1 = min(l1, w0 + win);
@@ -344,12 +384,27 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
       if (cnt[l] > 0) distinct += (unsigned long long)(leaf_off[l + 1] - leaf_off[l]);
     }
     if (pack && window_packs(cnt, leaf_off, w0, w1, g)) {
-      sb += 1;
+#pragma unroll
+      for (int c = 0; c < kPartLevels; ++c) sbl[c] += 1;
     } else {
-      for (int l = w0; l < w1; ++l) sb += leaf_items(cnt[l], leaf_off, l, part, g);
+      for (int l = w0; l < w1; ++l)
+#pragma unroll
+        for (int c = 0; c < kPartLevels; ++c)
+          sbl[c] += leaf_items(cnt[l], leaf_off, l, part_level(part_max, c), g);
     }
   }
   if (stat && distinct) atomicAdd(stat, distinct);
+#pragma unroll
+  for (int c = 0; c < kPartLevels; ++c)
+    if (sbl[c]) atomicAdd(&tot[c], sbl[c]);
+  __syncthreads();
+  const int lev = pick_part_level(tot, target);
+  const int part = part_level(part_max, lev);
+  int sb = 0;
+#pragma unroll
+  for (int c = 0; c < kPartLevels; ++c)
+    if (c == lev) sb = sbl[c];
+  if (threadIdx.x == 0 && part_out) *part_out = part;
   s_a[threadIdx.x] = sa;
   s_b[threadIdx.x] = sb;
   __syncthreads();
@@ -426,20 +481,39 @@ __global__ void vgroup_count_kernel(int L, const int32_t* __restrict__ grp_off,
 }
 
 // exclusive scans of per-leaf group counts and work-item counts (one block)
-__global__ void vgroup_offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part,
+__global__ void vgroup_offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part_max,
                                       const int32_t* __restrict__ ngroups,
                                       int32_t* __restrict__ gfirst, int32_t* __restrict__ item_off,
-                                      int32_t* __restrict__ n_items) {
+                                      int32_t* __restrict__ n_items, int target,
+                                      int32_t* __restrict__ part_out) {
   __shared__ int s_a[1024], s_b[1024];
+  __shared__ int tot[kPartLevels];
   const int T = blockDim.x;
   const int per = (L + T - 1) / T;
   const int l0 = min(L, (int)threadIdx.x * per), l1 = min(L, l0 + per);
-  int sa = 0, sb = 0;
+  if (threadIdx.x < kPartLevels) tot[threadIdx.x] = 0;
+  __syncthreads();
+  int sa = 0, sbl[kPartLevels] = {0, 0, 0, 0, 0};
   for (int l = l0; l < l1; ++l) {
     const int64_t size = leaf_off[l + 1] - leaf_off[l];
     sa += ngroups[l];
-    sb += ngroups[l] * (int)((size + part - 1) / part);
+#pragma unroll
+    for (int c = 0; c < kPartLevels; ++c) {
+      const int p = part_level(part_max, c);
+      sbl[c] += ngroups[l] * (int)((size + p - 1) / p);
+    }
   }
+#pragma unroll
+  for (int c = 0; c < kPartLevels; ++c)
+    if (sbl[c]) atomicAdd(&tot[c], sbl[c]);
+  __syncthreads();
+  const int lev = pick_part_level(tot, target);
+  const int part = part_level(part_max, lev);
+  int sb = 0;
+#pragma unroll
+  for (int c = 0; c < kPartLevels; ++c)
+    if (c == lev) sb = sbl[c];
+  if (threadIdx.x == 0 && part_out) *part_out = part;
   s_a[threadIdx.x] = sa;
   s_b[threadIdx.x] = sb;
   __syncthreads();
@@ -820,11 +894,11 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s, int32_t* item_leaf,
-                  bool pack_small) {
+                  bool pack_small, int target_items, int32_t* part_out) {
   if (L <= kFuseLeaves) {
     group_fused_kernel<<<1, 1024, 0, s>>>(pairs, npairs_dev, L, leaf_off, part, g, grp_off,
                                           item_off, n_items_dev, grouped, stat, item_leaf,
-                                          pack_small);
+                                          pack_small, target_items, part_out);
     LF_CHECK_LAUNCH();
     return;
   }
@@ -834,7 +908,7 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
     LF_CHECK_LAUNCH();
   }
   offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, g, cnt, grp_off, item_off, n_items_dev,
-                                    stat, item_leaf, pack_small);
+                                    stat, item_leaf, pack_small, target_items, part_out);
   LF_CHECK_LAUNCH();
   if (npairs_max > 0) {
     scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
@@ -845,12 +919,14 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
 void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* grp_off,
                        const Pair* grouped, const int32_t* slot_k, int kstride, int budget,
                        int32_t* ngroups, int32_t* gfirst, int32_t* gbound, int32_t* item_off,
-                       int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s) {
+                       int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s,
+                       int target_items, int32_t* part_out) {
   if (L <= 0) return;
   vgroup_count_kernel<<<nblk(L, 256), 256, 0, s>>>(L, grp_off, grouped, slot_k, kstride, budget,
                                                    ngroups);
   LF_CHECK_LAUNCH();
-  vgroup_offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, ngroups, gfirst, item_off, n_items_dev);
+  vgroup_offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, ngroups, gfirst, item_off, n_items_dev,
+                                           target_items, part_out);
   LF_CHECK_LAUNCH();
   vgroup_fill_kernel<<<nblk(L, 256), 256, 0, s>>>(L, leaf_off, part, grp_off, grouped, slot_k,
                                                   kstride, budget, gfirst, item_off, gbound,

@@ -114,7 +114,7 @@ struct Item {
 constexpr int kPackWin = 8;  // leaves per packed window (the grouping pass's windows)
 
 template <bool kVarGroups>
-__device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
+__device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item, int part_rows) {
   const int lf = a.item_leaf[item];
   Item it;
   if (lf < 0) {
@@ -148,8 +148,8 @@ __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item) {
     it.nqg = min(G, cnt - grp * G);
     it.pr = a.pairs + a.grp_off[leaf] + grp * G;
   }
-  it.p0 = a.leaf_off[leaf] + (int64_t)part * a.part;
-  it.p1 = min(it.p0 + (int64_t)a.part, a.leaf_off[leaf + 1]);
+  it.p0 = a.leaf_off[leaf] + (int64_t)part * part_rows;
+  it.p1 = min(it.p0 + (int64_t)part_rows, a.leaf_off[leaf + 1]);
   it.N = ((it.nqg + 15) / 16) * 16;
   it.nchunks = (int)((it.p1 - it.p0 + kTcRows - 1) / kTcRows);
   it.packed = false;
@@ -502,6 +502,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   dev::tc_fence_after();
   const uint32_t tmem = S.tmem_base;
   const int n_items = *n_items_dev;
+  const int part_rows = a.part_dev ? *a.part_dev : a.part;  // this round's work-item rows
   unsigned long long pr[16];
   for (int i = 0; i < 16; ++i) pr[i] = 0;
   const bool prof_on = a.prof != nullptr &&
@@ -532,7 +533,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       int cur = publish(0);
       for (int n = 0; cur >= 0 && alive && !*abort; ++n) {
         const int nxt = publish(n + 1);
-        const Item I = decode_item<!kSplit>(a, cur);
+        const Item I = decode_item<!kSplit>(a, cur, part_rows);
         for (int c = 0; c < I.nchunks; ++c) {
           const int st = (int)(g_ld & 1);
           if (g_ld >= 2) {
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       if (lane == 0) item = ring_take(S, li, abort);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item < 0) break;
-      const Item I = decode_item<!kSplit>(a, item);
+      const Item I = decode_item<!kSplit>(a, item, part_rows);
       const int b = li % nbuf;
       if (li >= nbuf) {
         bool ok = true;
@@ -641,7 +642,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       for (;; ++li) {
         const int item = ring_take(S, li, abort);
         if (item < 0) break;
-        const Item I = decode_item<!kSplit>(a, item);
+        const Item I = decode_item<!kSplit>(a, item, part_rows);
         const int b = li % nbuf;
         bool ok = wait_phase(&S.bready[b], bready_ph[b], abort);
         bready_ph[b] ^= 1u;
@@ -711,7 +712,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       epi_sync();
       const int item = S.eitem;
       if (item < 0) break;
-      const Item I = decode_item<!kSplit>(a, item);
+      const Item I = decode_item<!kSplit>(a, item, part_rows);
       const int nqg = I.nqg, N = I.N;
       if (prof_on) pr[9] += 1;
       // per-query state of the item (padding columns never admit a series)
