@@ -102,6 +102,9 @@ def parse():
     # mixed-k and serving searches take every remaining leaf after the route
     # leaf in one wave (measured: narrow waves re-read the same leaves for few
     # queries each)
+    # wave width: given, or chosen by the library's search-schedule autotuner
+    # while the filters are built (the initial width below is only its start)
+    a.tune = a.wave is None
     a.wave = a.wave if a.wave is not None else {"mixed": 65536, "precision": 4096,
                                                 "serving": 16384}.get(a.config, 64)
     return a
@@ -220,7 +223,7 @@ def workload_config(a):
                         % (a.n, M, a.leaf_cap, a.filters, a.queries, a.launch, a.target),
             "n_series": a.n, "length": M, "leaf_capacity": a.leaf_cap, "filters": a.filters,
             "queries": a.queries, "launch": a.launch, "recall_target": a.target,
-            "k": 1, "wave": a.wave,
+            "k": 1, "wave": a.wave if not getattr(a, "tune", False) else "autotuned",
             "schedule": "route-leaf order" if not getattr(a, "no_schedule", False) else "caller order",
             "lanes": getattr(a, "lanes", 8), "part": getattr(a, "part", 2048),
             "items_per_sm": getattr(a, "items_per_sm", 4),
@@ -321,7 +324,7 @@ def run_serving(a):
     info = lf.leafi_get_info(idx)
     F = min(a.filters, info.n_leaves)
     t0 = time.perf_counter()
-    enhance(idx, F, kclasses=(1, 10, 100), max_epochs=a.epochs)
+    enhance(idx, F, kclasses=(1, 10, 100), max_epochs=a.epochs, tune_search=int(a.tune))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     kmax = 100
@@ -427,7 +430,7 @@ def run_mixed(a):
     t_targets = time.perf_counter() - t0
     pairs = (1500 + 500) * float(sizes[fl].sum())
     t0 = time.perf_counter()
-    enhance(idx, F, kclasses=(1, 10, 100), max_epochs=a.epochs)
+    enhance(idx, F, kclasses=(1, 10, 100), max_epochs=a.epochs, tune_search=int(a.tune))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     Q = fx.test_queries(X, a.queries)
@@ -625,7 +628,8 @@ def run_ablation(a):
     # -Local: the 1,500 global queries only; +Local: 500 local queries per filter added
     for name, (n_train, ratio) in (("-Local", (1500, float("inf"))), ("+Local", (2000, 3.0))):
         idx = lf.leafi_build(X, bp)
-        enhance(idx, a.filters, n_train=n_train, global_local_ratio=ratio, max_epochs=a.epochs)
+        enhance(idx, a.filters, n_train=n_train, global_local_ratio=ratio, max_epochs=a.epochs,
+                tune_search=int(a.tune))
         qps, got, ser = timed(idx, a.target)
         rows[name] = {"qps": qps, "series_scanned_per_query": ser,
                       "recall_at_1": float(np.mean(got == exact)),
@@ -663,7 +667,7 @@ def main():
     lf.leafi_set_search_lanes(idx, a.lanes)
     lf.leafi_set_scan_part(idx, a.part, a.items_per_sm)
     t_train = time.perf_counter()
-    enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs)
+    enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs, tune_search=int(a.tune))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t_train
     info = lf.leafi_get_info(idx)
@@ -859,7 +863,7 @@ def main():
             qp = np.zeros((1, info.n_calib))
             lf.leafi_get_autotuners(idx, alpha, qp)
             rate, dt, _ = oracle_leafi_rate(X, enh.filter_leaf, W, alpha, qp[0], Q, a.leaf_cap,
-                                            a.wave, a.target, a.cpu_sample)
+                                            info.wave, a.target, a.cpu_sample)
             cpu = {"value": rate, "unit": "queries/s", "cores": cpu_threads(), "kind": "oracle",
                    "sample": "%d of the %d queries, LeaFi search with the same filters and "
                              "auto-tuner tables (%.1f s)" % (a.cpu_sample, a.queries, dt)}
@@ -897,7 +901,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
             "build": {"leaves": info.n_leaves, "filters": info.n_filters,
-                      "train_and_tune_s": t_train,
+                      "wave": info.wave, "train_and_tune_s": t_train,
                       "epochs_run_mean": float(np.mean(enh.epochs_run))},
         }
         print(json.dumps(line), flush=True)

@@ -283,6 +283,8 @@ typedef struct {
   uint64_t seed;
   double confidence;        /* calibration confidence of the search's offsets (0.95; see
                                leafi_set_calibration_confidence) */
+  int32_t tune_search;      /* 1: before the auto-tuners are fitted, leafi_tune_search picks
+                               the wave width and work-item balance (its defaults) */
 } leafi_train_params;
 
 typedef struct {
@@ -399,6 +401,38 @@ typedef struct {
 leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
                           double recall_target, int64_t* ids, float* dists,
                           leafi_search_stats* stats);
+/* Search-schedule autotuner (no counterpart in the paper; the wave width W is
+ * this implementation's batching parameter).  Times exact k-NN searches of
+ * n_probe probe queries (dataset series drawn by the library's generator plus
+ * Gaussian noise of sigma in [noise_lo, noise_hi], z-normalised) for every
+ * candidate (wave width, work items per SM), `reps` timed runs after one
+ * warm-up each, and keeps the fastest on the index.  The wave width is part
+ * of what the auto-tuners calibrate, so an index with fitted auto-tuners is
+ * refused (LEAFI_EINVAL): tune first (leafi_train_filters does when
+ * tune_search is set).  Zero-length candidate lists take the defaults: waves
+ * {16, 32, 64, 128, 256, 1024, n_leaves}, items per SM {2, 4, 8}. */
+typedef struct {
+  int32_t n_probe;          /* probe queries (2048: eight batches) */
+  int32_t k;                /* k of the probe searches (1) */
+  double noise_lo, noise_hi;/* (0.1, 0.4) */
+  uint64_t seed;
+  int32_t reps;             /* timed runs per candidate (2) */
+  int32_t n_waves;          /* candidates (<= 8; 0 = defaults) */
+  int32_t waves[8];
+  int32_t n_items;          /* candidates (<= 4; 0 = defaults) */
+  int32_t items_per_sm[4];
+} leafi_tune_params;
+typedef struct {
+  int32_t wave, items_per_sm;  /* chosen and installed */
+  double ms_best;              /* probe search time of the choice (best of reps) */
+  double ms_before;            /* ... of the index's settings before tuning */
+  int32_t n_tried;
+  int32_t tried_wave[32], tried_items[32];
+  double tried_ms[32];
+} leafi_tune_report;
+leafi_status leafi_tune_search(leafi_index* index, const leafi_tune_params* params,
+                               leafi_tune_report* report);
+
 /* Batches of one search call in flight, 1..8 (default 8): each has its own
  * scratch and stream, so one batch's bounds, filters and host round trips
  * overlap another's scan.  One lane runs the batches one after another (the

@@ -30,7 +30,7 @@ __all__ = [
     "leafi_initial_weights", "leafi_epoch_permutations", "leafi_znormalize",
     "leafi_get_filter_leaves", "leafi_debug_set_lock_tries", "leafi_debug_fail_allocations",
     "leafi_set_calibration_confidence", "leafi_set_query_schedule", "leafi_set_search_lanes",
-    "leafi_set_scan_part",
+    "leafi_set_scan_part", "leafi_tune_search", "TuneParams", "TuneReport",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -57,6 +57,7 @@ EXPORTED_SYMBOLS = [
     "leafi_znormalize", "leafi_get_filter_leaves", "leafi_debug_set_lock_tries",
     "leafi_debug_fail_allocations", "leafi_set_calibration_confidence",
     "leafi_set_query_schedule", "leafi_set_search_lanes", "leafi_set_scan_part",
+    "leafi_tune_search",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -98,16 +99,38 @@ class TrainParams(C.Structure):
                 ("val_frac", C.c_double), ("noise_lo", C.c_double), ("noise_hi", C.c_double),
                 ("batch", C.c_int32), ("max_epochs", C.c_int32), ("patience", C.c_int32),
                 ("lr0", C.c_double), ("lr_min", C.c_double), ("n_kclasses", C.c_int32),
-                ("kclasses", C.c_int32 * 4), ("seed", C.c_uint64), ("confidence", C.c_double)]
+                ("kclasses", C.c_int32 * 4), ("seed", C.c_uint64), ("confidence", C.c_double),
+                ("tune_search", C.c_int32)]
 
     def __init__(self, n_filters=100, a=2.0, mem_cap=8 << 30, hidden=0, n_train=2000,
                  global_local_ratio=3.0, val_frac=0.2, noise_lo=0.1, noise_hi=0.4, batch=64,
                  max_epochs=1000, patience=10, lr0=0.01, lr_min=1e-5, kclasses=(1,),
-                 seed=2502018361, confidence=0.95):
+                 seed=2502018361, confidence=0.95, tune_search=1):
         kc = (C.c_int32 * 4)(*(list(kclasses) + [0] * (4 - len(kclasses))))
         super().__init__(n_filters, a, mem_cap, hidden, n_train, global_local_ratio, val_frac,
                          noise_lo, noise_hi, batch, max_epochs, patience, lr0, lr_min,
-                         len(kclasses), kc, seed, confidence)
+                         len(kclasses), kc, seed, confidence, tune_search)
+
+
+class TuneParams(C.Structure):
+    """leafi_tune_search parameters (empty candidate lists take the defaults)."""
+    _fields_ = [("n_probe", C.c_int32), ("k", C.c_int32), ("noise_lo", C.c_double),
+                ("noise_hi", C.c_double), ("seed", C.c_uint64), ("reps", C.c_int32),
+                ("n_waves", C.c_int32), ("waves", C.c_int32 * 8), ("n_items", C.c_int32),
+                ("items_per_sm", C.c_int32 * 4)]
+
+    def __init__(self, n_probe=2048, k=1, noise_lo=0.1, noise_hi=0.4, seed=2502018361, reps=2,
+                 waves=(), items_per_sm=()):
+        w = (C.c_int32 * 8)(*(list(waves) + [0] * (8 - len(waves))))
+        it = (C.c_int32 * 4)(*(list(items_per_sm) + [0] * (4 - len(items_per_sm))))
+        super().__init__(n_probe, k, noise_lo, noise_hi, seed, reps, len(waves), w,
+                         len(items_per_sm), it)
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("wave", C.c_int32), ("items_per_sm", C.c_int32), ("ms_best", C.c_double),
+                ("ms_before", C.c_double), ("n_tried", C.c_int32), ("tried_wave", C.c_int32 * 32),
+                ("tried_items", C.c_int32 * 32), ("tried_ms", C.c_double * 32)]
 
 
 class TrainReport(C.Structure):
@@ -196,6 +219,7 @@ def lib():
             "leafi_set_query_schedule": [vp, i32],
             "leafi_set_search_lanes": [vp, i32],
             "leafi_set_scan_part": [vp, i32, i32],
+            "leafi_tune_search": [vp, C.POINTER(TuneParams), C.POINTER(TuneReport)],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
@@ -410,6 +434,16 @@ def leafi_set_scan_part(index, rows=2048, items_per_sm=4):
     """Leaf-scan work items: at most `rows` series (multiple of 128); rounds aim at
     items_per_sm items per SM (0: always `rows`)."""
     _check(lib().leafi_set_scan_part(index, int(rows), int(items_per_sm)))
+
+
+def leafi_tune_search(index, params: TuneParams | None = None):
+    """Search-schedule autotuner: returns the report as a dict (the choice is installed)."""
+    rep = TuneReport()
+    _check(lib().leafi_tune_search(index, C.byref(params or TuneParams()), C.byref(rep)))
+    n = rep.n_tried
+    return {"wave": rep.wave, "items_per_sm": rep.items_per_sm, "ms_best": rep.ms_best,
+            "ms_before": rep.ms_before,
+            "tried": [(rep.tried_wave[i], rep.tried_items[i], rep.tried_ms[i]) for i in range(n)]}
 
 
 def leafi_get_filter_leaves(index):

@@ -2222,6 +2222,109 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// the search-schedule autotuner (leafi_tune_search); caller holds the mutex
+void tune_core(leafi_index* ix, const leafi_tune_params* p, leafi_tune_report* rep) {
+  if (ix->nc > 0) fail(LEAFI_EINVAL, "tune the search before fitting the auto-tuners");
+  if (p->n_probe < 1 || p->k < 1 || p->k > LEAFI_MAX_K || p->reps < 1 || p->n_waves < 0 ||
+      p->n_waves > 8 || p->n_items < 0 || p->n_items > 4)
+    fail(LEAFI_EINVAL, "bad tuning parameters");
+  const int L = ix->tree.n_leaves;
+  std::vector<int> waves, items;
+  if (p->n_waves) waves.assign(p->waves, p->waves + p->n_waves);
+  else waves = {16, 32, 64, 128, 256, 1024, L};
+  if (p->n_items) items.assign(p->items_per_sm, p->items_per_sm + p->n_items);
+  else items = {2, 4, 8};
+  for (int& w : waves) {
+    if (w < 1 || w > calib_max_wave()) fail(LEAFI_EINVAL, "wave %d out of range", w);
+    w = std::min(w, std::max(L, 1));  // wider waves all take every leaf
+  }
+  std::sort(waves.begin(), waves.end());
+  waves.erase(std::unique(waves.begin(), waves.end()), waves.end());
+  for (int v : items)
+    if (v < 0 || v > 64) fail(LEAFI_EINVAL, "items per SM %d out of range", v);
+  // probe queries: the generator's global draw under a seed of their own
+  leafi_train_params gp{};
+  gp.n_train = p->n_probe;
+  gp.global_local_ratio = std::numeric_limits<double>::infinity();
+  gp.noise_lo = p->noise_lo;
+  gp.noise_hi = p->noise_hi;
+  gp.seed = p->seed ^ 0x6a09e667f3bcc909ull;
+  Alg1Counts c{p->n_probe, 0, p->n_probe, 0, 0, 0};
+  DBuf<float> Qp, Qm;
+  generate_training_queries(ix, &gp, c, {}, Qp, nullptr, nullptr);
+  const float* dQ = Qp.p;
+  if (ix->mp != ix->m) {
+    LF_CUDA(cudaMemcpy2DAsync(Qm.need((size_t)p->n_probe * ix->m), sizeof(float) * ix->m, Qp.p,
+                              sizeof(float) * ix->mp, sizeof(float) * ix->m, (size_t)p->n_probe,
+                              cudaMemcpyDeviceToDevice, ix->stream));
+    dQ = Qm.p;
+  }
+  DBuf<int64_t> oi;
+  DBuf<float> od;
+  oi.need((size_t)p->n_probe * p->k);
+  od.need((size_t)p->n_probe * p->k);
+  std::vector<int32_t> kq(p->n_probe, p->k);
+  std::vector<double> tg(p->n_probe, 1.0);
+  const int w0 = ix->wave, i0 = ix->items_per_sm;
+  auto time_it = [&](int w, int ips) {
+    if (w != ix->wave || ips != ix->items_per_sm) ix->drop_graphs();
+    ix->wave = w;
+    ix->items_per_sm = ips;
+    search_impl(ix, dQ, p->n_probe, kq, tg, p->k, oi.p, od.p, nullptr);  // warm-up
+    double best = std::numeric_limits<double>::infinity();
+    for (int r = 0; r < p->reps; ++r) {
+      const auto t0 = std::chrono::steady_clock::now();
+      search_impl(ix, dQ, p->n_probe, kq, tg, p->k, oi.p, od.p, nullptr);
+      best = std::min(best, seconds_since(t0) * 1e3);
+    }
+    return best;
+  };
+  leafi_tune_report r{};
+  try {
+    r.ms_before = time_it(w0, i0);
+    int bw = w0, bi = i0;
+    double bms = r.ms_before;
+    for (int w : waves)
+      for (int v : items) {
+        const double ms = time_it(w, v);
+        if (r.n_tried < 32) {
+          r.tried_wave[r.n_tried] = w;
+          r.tried_items[r.n_tried] = v;
+          r.tried_ms[r.n_tried] = ms;
+          ++r.n_tried;
+        }
+        if (ms < bms) {
+          bms = ms;
+          bw = w;
+          bi = v;
+        }
+      }
+    if (bw != ix->wave || bi != ix->items_per_sm) ix->drop_graphs();
+    ix->wave = bw;
+    ix->items_per_sm = bi;
+    r.wave = bw;
+    r.items_per_sm = bi;
+    r.ms_best = bms;
+  } catch (...) {
+    ix->drop_graphs();
+    ix->wave = w0;
+    ix->items_per_sm = i0;
+    throw;
+  }
+  if (rep) *rep = r;
+}
+
+leafi_tune_params default_tune_params(uint64_t seed) {
+  leafi_tune_params t{};
+  t.n_probe = 2048;
+  t.k = 1;
+  t.noise_lo = 0.1;
+  t.noise_hi = 0.4;
+  t.seed = seed;
+  t.reps = 2;
+  return t;
+}
+
 }  // namespace
 }  // namespace leafi
 
@@ -2291,6 +2394,11 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     train_core(index, &sp, dQg, dQl, hperm, ep.data(), bv.data());
     rep.seconds_train = seconds_since(t0);
     t0 = std::chrono::steady_clock::now();
+    // the search schedule the auto-tuners will calibrate
+    if (p->tune_search) {
+      const leafi_tune_params tp = default_tune_params(p->seed);
+      tune_core(index, &tp, nullptr);
+    }
     // line 10: auto-tuners on the calibration set (the global validation queries)
     fit_core(index, dQg + (size_t)c.n_gtrain * index->mp, c.n_gval, p->kclasses, p->n_kclasses);
     index->calib_confidence = p->confidence;
@@ -2304,6 +2412,17 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     if (epochs_run) std::memcpy(epochs_run, ep.data(), sizeof(int32_t) * F);
     if (best_val) std::memcpy(best_val, bv.data(), sizeof(double) * F);
     if (report) *report = rep;
+  });
+}
+
+leafi_status leafi_tune_search(leafi_index* index, const leafi_tune_params* params,
+                               leafi_tune_report* report) {
+  return guarded([&] {
+    require_device(index);
+    if (!params) fail(LEAFI_EINVAL, "params is NULL");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    tune_core(index, params, report);
   });
 }
 

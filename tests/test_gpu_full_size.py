@@ -66,7 +66,8 @@ def _leafi_vs_oracle(idx, t, enh, Q, ids_gpu):
     nc = lf.leafi_get_info(idx).n_calib
     W, alpha, qp = _gpu_model(idx, F, nc)
     j = O.offset_position(qp, 0.99)
-    o_ids, o_d2, _, margin = O.leafi_search(t, W, enh.filter_leaf, alpha, Q, 1, j, W_WAVE)
+    wave = lf.leafi_get_info(idx).wave      # the schedule the autotuner chose
+    o_ids, o_d2, _, margin = O.leafi_search(t, W, enh.filter_leaf, alpha, Q, 1, j, wave)
     tol = 2e-5 * _pred_scale(W, Q).max()
     same = (ids_gpu == o_ids).all(1)
     # a query may differ only where a filter decision sits within the prediction tolerance
@@ -165,8 +166,8 @@ def test_mixed_k_isax_config_reduced():
         cls = {1: 0, 10: 1, 100: 2}
         jpos = np.array([-1 if tg[i] >= 1 else O.offset_position(qp[cls[kq[i]]], tg[i], kk=kq[i])
                          for i in range(len(Q))], np.int32)
-        o_ids, o_d2, _, margin = O.leafi_search(t, W, enh.filter_leaf, alpha, Q, kq, jpos, 16,
-                                                kmax=100)
+        o_ids, o_d2, _, margin = O.leafi_search(t, W, enh.filter_leaf, alpha, Q, kq, jpos,
+                                                lf.leafi_get_info(idx).wave, kmax=100)
         tol = 2e-5 * _pred_scale(W, Q).max()
         same = (ids == o_ids).all(1)
         assert (same | (margin <= tol)).all()

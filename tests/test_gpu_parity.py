@@ -617,3 +617,32 @@ def test_query_schedule_keeps_every_result(ds, tuned):
     finally:
         lf.leafi_set_query_schedule(idx, True)
         lf.leafi_set_calibration_confidence(idx, 0.95)
+
+
+def test_search_schedule_autotuner():
+    """leafi_tune_search times exact searches of probe queries for every
+    (wave, items per SM) candidate and installs the fastest; exact results do
+    not depend on the choice; an index with fitted auto-tuners is refused."""
+    X = fx.random_walk(40000, 128, seed=131)
+    Q = fx.test_queries(X, 300, seed=132)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=1500, wave=4, device=0))
+    try:
+        bf, bf_d2 = O.knn(X, Q, 3)
+        rep = lf.leafi_tune_search(idx, lf.TuneParams(n_probe=600, waves=(2, 8, 64),
+                                                      items_per_sm=(0, 4), reps=1))
+        assert len(rep["tried"]) == 6
+        best = min(rep["tried"], key=lambda r: r[2])
+        assert rep["ms_best"] <= best[2] and rep["ms_best"] <= rep["ms_before"]
+        info = lf.leafi_get_info(idx)
+        assert info.wave == rep["wave"] and rep["wave"] in (2, 4, 8, 64)
+        ids, d, _ = _exact(idx, Q, 3)
+        assert np.array_equal(ids, bf) and np.array_equal(d, np.sqrt(bf_d2))
+        L = info.n_leaves
+        lf.leafi_set_filters(idx, lf.leafi_select_leaves(idx, 4),
+                             *fx.filter_init(4, 128, 128, seed=133))
+        lf.leafi_fit_autotuners(idx, Q[:50], [1])
+        with pytest.raises(lf.LeafiError) as e:
+            lf.leafi_tune_search(idx, lf.TuneParams(n_probe=64, reps=1))
+        assert e.value.status == 1 and L > 4
+    finally:
+        lf.leafi_free(idx)
