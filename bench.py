@@ -734,6 +734,7 @@ def main():
         lats = [x.elapsed_time(y) for x, y in lat]
         return ms, lats, stats, launches, ck.summary(), kt
 
+    pk0, _ = peaks()
     # exact (plain-bound) search: ground truth and the comparison arm
     ms_ex, lat_ex, st_ex, _, _, _ = timed(1.0, ex_ids, ex_d)
     ms, lat, st, launches, clocks, kt = timed(a.target, ids, dd, profile=False)
@@ -755,8 +756,19 @@ def main():
     torch.cuda.synchronize()
     ser_ms = e0s.elapsed_time(e1s) / ser_steps
     kt = lf.leafi_get_kernel_times(idx)
+    # one more one-lane step with the scan's in-kernel launch timeline
+    lf.leafi_set_profiling(idx, 2)
+    run(a.target, ids, dd)
+    torch.cuda.synchronize()
+    ph1 = lf.leafi_get_scan_phases(idx)
     lf.leafi_set_profiling(idx, 0)
     lf.leafi_set_search_lanes(idx, a.lanes)
+    nl1 = max(ph1["launches"], 1)
+    timeline = {"launches": ph1["launches"],
+                "span_us": ph1["launch_span_ns"] / nl1 / 1e3,
+                "start_skew_us": ph1["start_skew_ns"] / nl1 / 1e3,
+                "end_skew_us": ph1["end_skew_ns"] / nl1 / 1e3,
+                "block_resident_us": ph1["epilogue_span"] / SMS / nl1 / (pk0.get("sm_max_mhz", 2032.0))}
     # Alg. 3 with this device's costs (the run above uses the configuration's
     # 100 largest leaves, i.e. th = 0)
     sel_fl, sel_rep = lf.leafi_select_leaves_auto(idx, a=2.0, mem_cap=8 << 30)
@@ -842,6 +854,7 @@ def main():
     roofline["kernel"] = "leaf_scan (tensor cores)" if info.tensor_scan else "leaf_scan (CUDA cores)"
     roofline["step_view"] = step_view
     roofline["cross_check"] = cross
+    roofline["timeline_one_lane"] = timeline
     roofline["bytes_per_series"] = info.scan_row_bytes
     span = kt_all.get("_phases", {}).get("epilogue_span", 0.0)
     if info.tensor_scan and span > 0:
@@ -897,7 +910,8 @@ def main():
             "kernel_ms_per_step": {k: v[0] for k, v in kt_all.items()
                                    if not k.startswith("_") and v[1]},
             "kernel_ms_note": "one extra untimed step with every kind timed",
-            "scan_phase_cycles_per_block": {k: v / SMS for k, v in kt_all["_phases"].items()},
+            "scan_phase_cycles_per_block": {k: v / SMS for k, v in kt_all["_phases"].items()
+                                            if not k.endswith("_ns") and k != "launches"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
             "build": {"leaves": info.n_leaves, "filters": info.n_filters,

@@ -144,13 +144,15 @@ enum { LEAFI_KERNEL_KINDS = 6 };
 leafi_status leafi_set_profiling(leafi_index* index, int32_t level);
 leafi_status leafi_get_kernel_times(leafi_index* index, double* ms /* [6] */,
                                     int64_t* launches /* [6] */);
-/* Tensor-core scan phase cycles summed over blocks while profiling is on
- * (16 doubles): 0 item set-up, 1 wait for an accumulator, 2 epilogue, 3 flush
+/* Tensor-core scan phase cycles summed over blocks while profiling is on: 0 item set-up, 1 wait for an accumulator, 2 epilogue, 3 flush
  * and emit (epilogue warp 0, lane 0); 4 wait for a free stage, 11 TMA issue
  * (the TMA thread); 5 wait for the query tile, 6 wait for a TMA load, 7 wait
  * for a free accumulator, 14 MMA issue, 8 commits (the MMA thread); 12 wait for a free
  * query tile, 13 gather (the query loader); 9 work items, 10 chunks read by
- * epilogue warp 0; 15 epilogue warp 0's cycles from kernel entry to exit. */
+ * epilogue warp 0; 15 epilogue warp 0's cycles from kernel entry to exit;
+ * then the launch timeline in ns of the global timer, summed over launches:
+ * 16 first block start to last block end, 17 first to last block start, 18
+ * first to last block end, 19 launches (20 doubles in all). */
 leafi_status leafi_get_scan_phases(leafi_index* index, double* cycles);
 /* Series per leaf (host array of n_leaves). Leaves are numbered depth-first,
  * left child first. */

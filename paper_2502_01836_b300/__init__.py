@@ -298,12 +298,13 @@ def leafi_get_kernel_times(index):
 
 SCAN_PHASES = ["item_setup", "wait_accumulator", "epilogue", "flush_emit", "wait_stage_free",
                "wait_query_tile", "wait_tma", "wait_accumulator_free", "commit", "items", "chunks",
-               "tma_issue", "wait_tile_free", "gather", "mma_issue", "epilogue_span"]
+               "tma_issue", "wait_tile_free", "gather", "mma_issue", "epilogue_span",
+               "launch_span_ns", "start_skew_ns", "end_skew_ns", "launches"]
 
 
 def leafi_get_scan_phases(index):
     """Tensor-core scan phase cycle totals recorded while profiling was on."""
-    c = np.zeros(16, np.float64)
+    c = np.zeros(20, np.float64)
     _check(lib().leafi_get_scan_phases(index, c.ctypes.data))
     return {k: float(c[i]) for i, k in enumerate(SCAN_PHASES)}
 

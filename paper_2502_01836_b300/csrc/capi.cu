@@ -1467,8 +1467,11 @@ leafi_status leafi_set_profiling(leafi_index* index, int32_t on) {
     index->drop_graphs();
     index->settle();
     index->profiling = on < 0 ? 0 : (on > 2 ? 2 : on);
-    index->scan_prof.need(16);
-    LF_CUDA(cudaMemset(index->scan_prof.p, 0, 16 * sizeof(unsigned long long)));
+    index->scan_prof.need(24);
+    LF_CUDA(cudaMemset(index->scan_prof.p, 0, 20 * sizeof(unsigned long long)));
+    // the current launch's timeline: min slots at the largest value, max slots at 0
+    const unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};
+    LF_CUDA(cudaMemcpy(index->scan_prof.p + 20, init, sizeof(init), cudaMemcpyHostToDevice));
     for (int i = 0; i < 8; ++i) {
       index->clock.ms[i] = 0.0;
       index->clock.n[i] = 0;
@@ -1496,10 +1499,10 @@ leafi_status leafi_get_scan_phases(leafi_index* index, double* cycles) {
     if (!cycles) fail(LEAFI_EINVAL, "NULL output");
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
-    unsigned long long h[16] = {0};
+    unsigned long long h[20] = {0};
     if (index->scan_prof.p)
       LF_CUDA(cudaMemcpy(h, index->scan_prof.p, sizeof(h), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < 16; ++i) cycles[i] = (double)h[i];
+    for (int i = 0; i < 20; ++i) cycles[i] = (double)h[i];
   });
 }
 

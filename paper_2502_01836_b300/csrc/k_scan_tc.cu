@@ -91,7 +91,9 @@ struct TcShared {
   unsigned long long rechecks;
 };
 
-// optional per-phase cycle counters (TcScanArgs::prof, 16 entries):
+// optional per-phase cycle counters (TcScanArgs::prof, 24 entries; 16-19 are
+// the launch timeline totals in ns, 20-23 the current launch's, see
+// tc_timeline_kernel):
 // epilogue warp 0 lane 0: 0 item set-up, 1 wait accumulator, 2 epilogue, 3 flush+emit;
 // MMA thread: 5 wait query tile, 6 wait TMA, 7 wait accumulator free, 14 MMA issue, 8 commits;
 // load thread: 4 wait stage free, 11 TMA issue; 9 items, 10 chunks (of warp 0);
@@ -451,6 +453,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     const __grid_constant__ CUtensorMap tmap, TcScanArgs a, const int32_t* __restrict__ n_items_dev,
     const int32_t* __restrict__ slot_k) {
   const long long t_enter = clock64();
+  if (a.prof && threadIdx.x == 0) {
+    // launch timeline (ns): first and last block start
+    unsigned long long g;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g));
+    atomicMin(&a.prof[20], g);
+    atomicMax(&a.prof[21], g);
+  }
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ TcShared S;
   // 128-byte swizzled tiles need 1024-byte aligned bases
@@ -595,32 +604,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       }
       PROF_ADD(12);
       unsigned char* Bt = b ? B1 : B0;
-      // rows beyond the group are zero; four rows in flight per lane
-      for (int q0 = 0; q0 < I.N; q0 += 4) {
-        uint4 v[4][2];
+      // every 16-byte piece of the tile is an asynchronous copy (rows beyond the
+      // group are zero-filled), so all of them are in flight at once
+      for (int qq = 0; qq < I.N; ++qq) {
+        const int row = qq < I.nqg ? I.pr[qq].q : -1;
+        const __half* src = a.Qh + (size_t)(row >= 0 ? row : 0) * Kp;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int qq = q0 + u;
-          const int row = qq < I.nqg ? I.pr[qq].q : -1;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int piece = lane + 32 * h;
-            v[u][h] = make_uint4(0u, 0u, 0u, 0u);
-            if (row >= 0 && piece < pieces)
-              v[u][h] = *reinterpret_cast<const uint4*>(a.Qh + (size_t)row * Kp + piece * 8);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int qq = q0 + u;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int piece = lane + 32 * h;
-            if (piece < pieces)
-              *reinterpret_cast<uint4*>(Bt + (qq / 8) * sbo + piece * 128 + (qq % 8) * 16) = v[u][h];
-          }
+        for (int h = 0; h < 2; ++h) {
+          const int piece = lane + 32 * h;
+          if (piece < pieces)
+            dev::cp_async16_zfill(Bt + (qq / 8) * sbo + piece * 128 + (qq % 8) * 16,
+                                  src + piece * 8, row >= 0 ? 16 : 0);
         }
       }
+      dev::cp_async_commit();
+      dev::cp_async_wait_all();
       dev::fence_async_smem();
       __syncwarp();
       mbar_arrive(&S.bready[b]);
@@ -1056,6 +1054,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   dev::tc_fence_after();
   if (tid == 0 && a.stat && S.rechecks) atomicAdd(a.stat, S.rechecks);
   if (warp == 0) dev::tmem_dealloc(tmem, kTmemCols);
+  if (a.prof && tid == 0) {
+    // first and last block end
+    unsigned long long g;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g));
+    atomicMin(&a.prof[22], g);
+    atomicMax(&a.prof[23], g);
+  }
+}
+
+// after a profiled launch: fold its timeline into the totals (16 launch span,
+// 17 start skew, 18 end skew, 19 launches) and reset it for the next one
+__global__ void tc_timeline_kernel(unsigned long long* prof) {
+  if (prof[21] >= prof[20] && prof[23] >= prof[22]) {
+    prof[16] += prof[23] - prof[20];
+    prof[17] += prof[21] - prof[20];
+    prof[18] += prof[23] - prof[22];
+    prof[19] += 1;
+  }
+  prof[20] = ~0ull;
+  prof[21] = 0;
+  prof[22] = ~0ull;
+  prof[23] = 0;
 }
 
 }  // namespace
@@ -1191,6 +1211,10 @@ void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t*
   else
     tc_scan_kernel<false><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
   LF_CHECK_LAUNCH();
+  if (a.prof) {
+    tc_timeline_kernel<<<1, 1, 0, s>>>(a.prof);
+    LF_CHECK_LAUNCH();
+  }
 }
 
 }  // namespace leafi
