@@ -447,8 +447,12 @@ leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes);
  * the largest of rows, rows / 2, ... (>= 128) that gives the round at least
  * items_per_sm items per SM (default 4; 0 always uses rows), since a launch
  * lasts as long as its most loaded SM.  Smaller parts balance better, larger
- * ones cost less per item.  Results do not depend on either. */
-leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm);
+ * ones cost less per item.  `blocks`: thread blocks of a tensor-core scan
+ * launch (0 = one per SM); fewer blocks leave SMs to the scans of other batches
+ * in flight, which then run side by side.  Results do not depend on any of
+ * them. */
+leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm,
+                                 int32_t blocks);
 
 /* Query scheduling of calls with more than one internal batch (on by
  * default): the batches are cut from the queries in order of their route

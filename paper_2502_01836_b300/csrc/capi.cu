@@ -373,7 +373,8 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     launch_var_groups(L, ix->leaf_off.p, ix->part, goff, grouped, slot_k, kstride, qkeys, ngr, gfirst,
                       gbound, ioff, item_leaf, nitems, s, target, part_dev);
   }
-  const int grid = sm_count(ix->device) * (use_tc ? 1 : 2);
+  const int grid = use_tc ? (ix->scan_blocks > 0 ? ix->scan_blocks : sm_count(ix->device))
+                          : sm_count(ix->device) * 2;
   if (use_tc) {
     TcScanArgs t;
     t.X = ix->X.p;
@@ -2538,15 +2539,18 @@ leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes) {
   });
 }
 
-leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm) {
+leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm,
+                                 int32_t blocks) {
   return guarded([&] {
     require_device(index);
     if (rows < 128 || rows > 8192 || rows % 128) fail(LEAFI_EINVAL, "rows must be a multiple of 128 in [128, 8192]");
     if (items_per_sm < 0 || items_per_sm > 64) fail(LEAFI_EINVAL, "items_per_sm must be in [0, 64]");
+    if (blocks < 0 || blocks > 4096) fail(LEAFI_EINVAL, "blocks must be in [0, 4096]");
     std::lock_guard<std::mutex> lk(index->mu);
     index->drop_graphs();
     index->part = rows;
     index->items_per_sm = items_per_sm;
+    index->scan_blocks = blocks;
   });
 }
 

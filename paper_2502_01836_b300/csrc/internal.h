@@ -457,6 +457,7 @@ struct leafi_index {
   int part = 2048;         // series per scan work item (leafi_set_scan_part); the tensor-core
                            // scan's rounds may take part / 2, ... (>= 128) for balance
   int items_per_sm = 4;    // work items per SM a tensor-core round aims at
+  int scan_blocks = 0;     // blocks of a tensor-core scan launch (0: one per SM)
   leafi::Schedule sched;
   int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries
   double calib_confidence = 0.95;  // probability that a certified position meets its target
