@@ -497,7 +497,9 @@ typedef struct {
   int32_t kmax;         /* largest k of any request, 1..LEAFI_MAX_K; results are [nq][kmax] */
   double max_wait_ms;   /* a partial batch waits at most this long for company (default 0.2) */
   int64_t max_bytes;    /* admission budget: host bytes of queries and results of the requests
-                           admitted and not yet collected (0 = 1 GiB) */
+                           admitted and not yet collected (0 = 1 GiB).  Device memory does not
+                           grow with admitted work: each lane's scratch is sized for a full
+                           batch at leafi_serve_start */
 } leafi_serve_params;
 
 /* Start serving `index` (device index, built and, for targets < 1, tuned).
@@ -522,11 +524,16 @@ leafi_status leafi_serve_poll(leafi_server* server, int64_t ticket, int64_t* ids
                               double wait_ms, int32_t* done, double* latency_ms);
 
 /* Counters since the start: requests and queries completed, batches run,
- * batches that replayed a captured graph, and the search statistics summed
- * over the batches. */
+ * batches that replayed a captured graph, the search statistics summed over
+ * the batches, requests admitted while at least one batch was on the GPU
+ * (continuous batching), and the device bytes the server's lanes hold (fixed
+ * per lane and reserved at leafi_serve_start; admitted requests wait in host
+ * memory, which is why the admission budget counts host bytes). */
 typedef struct {
   int64_t requests, queries, batches, graph_batches;
   leafi_search_stats search;
+  int64_t admitted_in_flight;
+  int64_t device_bytes;
 } leafi_serve_stats;
 leafi_status leafi_serve_get_stats(leafi_server* server, leafi_serve_stats* stats);
 

@@ -176,7 +176,8 @@ class ServeParams(C.Structure):
 
 class ServeStats(C.Structure):
     _fields_ = [("requests", C.c_int64), ("queries", C.c_int64), ("batches", C.c_int64),
-                ("graph_batches", C.c_int64), ("search", SearchStats)]
+                ("graph_batches", C.c_int64), ("search", SearchStats),
+                ("admitted_in_flight", C.c_int64), ("device_bytes", C.c_int64)]
 
 
 _lib = None

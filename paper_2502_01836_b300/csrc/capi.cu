@@ -1175,6 +1175,18 @@ void leafi_index::drop_graphs() {
   }
 }
 
+size_t leafi::Scratch::bytes() const {
+  return sQ.bytes() + sQh.bytes() + sQk.bytes() + sQs.bytes() + sItemLeaf.bytes() +
+         sWork.bytes() + sP.bytes() + sIv.bytes() + sNode.bytes() + sLb.bytes() + sPaa.bytes() +
+         sTarget.bytes() + sRoute.bytes() + sK.bytes() + sJpos.bytes() + sCnt.bytes() +
+         sGrpOff.bytes() + sItemOff.bytes() + sNpairs.bytes() + sCandCnt.bytes() +
+         sTopkCnt.bytes() + sDone.bytes() + sNItems.bytes() + sOrd.bytes() + sCursor.bytes() +
+         sScanned.bytes() + sOrderTmp.bytes() + sPairs.bytes() + sGrouped.bytes() +
+         sTopk.bytes() + sThr.bytes() + sCand.bytes() + sGlock.bytes() + sPart.bytes() +
+         sNGroups.bytes() + sGFirst.bytes() + sGBound.bytes() + sPred.bytes() + sOutD.bytes() +
+         sOutI.bytes();
+}
+
 void leafi::Scratch::release_lane() {
   if (st) cudaStreamDestroy(st);
   if (ev_np) cudaEventDestroy(ev_np);
@@ -2704,6 +2716,7 @@ struct leafi_server {
   int64_t* hi[kServeLanes] = {};
   float* hd[kServeLanes] = {};
   leafi_serve_stats counters{};
+  int inflight = 0;  // batches on the GPU (worker thread, under mu)
   leafi_status failed = LEAFI_OK;
   std::string fail_msg;
 };
@@ -2764,6 +2777,7 @@ void serve_loop(leafi_server* sv) {
             return sv->stopping || (int)sv->pending.size() >= sv->p.max_batch;
           });
         const int nb = std::min<int>((int)sv->pending.size(), sv->p.max_batch);
+        sv->inflight += 1;
         auto& mem = sv->members[next];
         mem.assign(sv->pending.begin(), sv->pending.begin() + nb);
         sv->pending.erase(sv->pending.begin(), sv->pending.begin() + nb);
@@ -2800,6 +2814,7 @@ void serve_loop(leafi_server* sv) {
         LF_CUDA(cudaStreamSynchronize(sv->lanes[li].st));
       });
       lk.lock();
+      sv->inflight -= 1;
       const auto now = leafi_server::clock::now();
       const auto& mem = sv->members[li];
       for (size_t j = 0; j < mem.size(); ++j) {
@@ -2901,6 +2916,7 @@ leafi_status leafi_serve_submit(leafi_server* sv, const float* queries, int64_t 
     r.bytes = need;
     r.t_submit = leafi_server::clock::now();
     sv->bytes += need;
+    if (sv->inflight > 0) sv->counters.admitted_in_flight += 1;
     for (int i = 0; i < (int)nq; ++i) {
       sv->pending.emplace_back(t, i);
       sv->pending_t.push_back(r.t_submit);
@@ -2956,6 +2972,8 @@ leafi_status leafi_serve_get_stats(leafi_server* sv, leafi_serve_stats* stats) {
     st.rechecks = (int64_t)h[3];
     c.graph_batches = st.graph_batches;
     c.search = st;
+    c.device_bytes = 0;
+    for (int i = 0; i < kServeLanes; ++i) c.device_bytes += (int64_t)sv->lanes[i].bytes();
     *stats = c;
   });
 }

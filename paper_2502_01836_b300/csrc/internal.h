@@ -387,6 +387,7 @@ struct Scratch {
   int32_t* h_np = nullptr;         // pinned host word
   std::vector<BatchGraph> graphs;  // captured batches of this lane
   void release_lane();
+  size_t bytes() const;            // device bytes held by the lane's buffers
 };
 // query scheduling of a multi-batch search call (search_impl)
 struct Schedule {

@@ -104,3 +104,43 @@ def test_admission_budget(served):
         assert np.array_equal(ids, a_ids) and np.array_equal(d, a_d)
     finally:
         lf.leafi_serve_stop(sv)
+
+
+def test_requests_admitted_while_batches_are_in_flight(served):
+    """Continuous batching: requests submitted while earlier batches are on the
+    GPU are admitted (counted by the server) and join later batches; their
+    results equal what the same queries return alone."""
+    X, idx = served
+    big = fx.test_queries(X, 2000, seed=84)              # eight batches of 256
+    kb = np.full(2000, 10, np.int32)
+    tb = np.full(2000, 0.95)
+    small = [fx.test_queries(X, 5, seed=85 + i) for i in range(20)]
+    ks = [np.full(5, 1 + i % KMAX, np.int32) for i in range(20)]
+    ts = [np.full(5, (0.9, 0.99, 1.0)[i % 3]) for i in range(20)]
+    sv = lf.leafi_serve_start(idx, kmax=KMAX, max_batch=256, max_wait_ms=0.2)
+    try:
+        tb_ticket = lf.leafi_serve_submit(sv, big, kb, tb)
+        tickets = [lf.leafi_serve_submit(sv, small[i], ks[i], ts[i]) for i in range(20)]
+        st = None
+
+        def collect(ticket, nq):
+            ids = np.zeros((nq, KMAX), np.int64)
+            d = np.zeros((nq, KMAX), np.float32)
+            for _ in range(400):
+                done, _ = lf.leafi_serve_poll(sv, ticket, ids, d, wait_ms=50.0)
+                if done:
+                    return ids, d
+            raise AssertionError("request did not finish")
+
+        got = [collect(t, 5) for t in tickets]
+        gb = collect(tb_ticket, 2000)
+        st = lf.leafi_serve_get_stats(sv)
+        assert st["admitted_in_flight"] >= 1
+        assert st["device_bytes"] > 0
+        for i in range(20):
+            a_ids, a_d = _alone(idx, small[i], ks[i], ts[i])
+            assert np.array_equal(got[i][0], a_ids) and np.array_equal(got[i][1], a_d), i
+        a_ids, a_d = _alone(idx, big[:300], kb[:300], tb[:300])
+        assert np.array_equal(gb[0][:300], a_ids) and np.array_equal(gb[1][:300], a_d)
+    finally:
+        lf.leafi_serve_stop(sv)
