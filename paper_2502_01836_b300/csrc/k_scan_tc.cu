@@ -594,6 +594,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       if (lane == 0) item = ring_take(S, li, abort, &S.qitem);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item < 0) break;
+      __syncwarp();  // lane 0's shared-memory copy of the item is visible to the warp
       const Item I = S.qitem;
       const int b = li % nbuf;
       if (li >= nbuf) {
