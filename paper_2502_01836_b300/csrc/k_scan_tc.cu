@@ -63,13 +63,6 @@ constexpr long long kWaitLimit = 1ll << 26;
 constexpr int kCandCap = 2048;    // deferred re-check buffer (k = 1 rounds)
 constexpr int kRing = 4;          // work items handed from the TMA thread to the other roles
 
-struct Item {
-  int64_t p0, p1;
-  int nqg, N, nchunks;
-  bool packed;       // several small leaves in one chunk (pairs meet their own leaf's rows)
-  const Pair* pr;
-};
-
 struct TcShared {
   u64 full[2];      // TMA of stage s landed (1 arrival + bytes)
   u64 empty[2];     // MMAs reading stage s finished (tcgen05.commit)
@@ -80,10 +73,7 @@ struct TcShared {
   u64 iready[kRing];  // ring slot holds the next work item (TMA thread)
   u64 ifree[kRing];   // ring slot read by the loader, the MMA thread and the epilogue
   int ring[kRing];    // work item index, -1 = no more work
-  Item ritem[kRing];  // ... decoded once by the TMA thread when it claims it
   int eitem;          // epilogue's current item (broadcast through shared memory)
-  Item eitem_full;    // ... decoded
-  Item qitem;         // the query loader's current item (lane 0 -> warp)
   uint32_t tmem_base;
   int abort;
   int stop;            // epilogue warps' uniform snapshot of `abort`
@@ -115,6 +105,13 @@ struct TcShared {
     if (prof_on) pr[i] += (unsigned long long)(_nw - _pt);       \
     _pt = _nw;                                                   \
   } while (0)
+
+struct Item {
+  int64_t p0, p1;
+  int nqg, N, nchunks;
+  bool packed;       // several small leaves in one chunk (pairs meet their own leaf's rows)
+  const Pair* pr;
+};
 
 constexpr int kPackWin = 8;  // leaves per packed window (the grouping pass's windows)
 
@@ -391,11 +388,10 @@ __device__ __forceinline__ bool share_list(u64* gl, int32_t* lock, const u64* B,
 // from a global counter (one item ahead of the one it is loading) and hands
 // it to the other roles through a ring of kRing slots, so every role of the
 // CTA walks the same sequence and CTAs that finish early take more work.
-__device__ __forceinline__ int ring_take(TcShared& S, int n, volatile int* abort, Item* out) {
+__device__ __forceinline__ int ring_take(TcShared& S, int n, volatile int* abort) {
   const int s = n % kRing;
   const bool ok = wait_phase(&S.iready[s], (uint32_t)((n / kRing) & 1), abort);
   const int item = ok ? *reinterpret_cast<volatile int*>(&S.ring[s]) : -1;
-  if (item >= 0) *out = S.ritem[s];  // the slot is reused only after every role arrived
   mbar_arrive(&S.ifree[s]);
   return item;
 }
@@ -540,16 +536,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         int item = atomicAdd(a.work, 1);
         if (item >= n_items) item = -1;
         S.ring[sl] = item;
-        // decoded here, one item ahead of its loads, so the other roles read
-        // it from shared memory instead of chasing the item tables themselves
-        if (item >= 0) S.ritem[sl] = decode_item<!kSplit>(a, item, part_rows);
         mbar_arrive(&S.iready[sl]);
         return item;
       };
       int cur = publish(0);
       for (int n = 0; cur >= 0 && alive && !*abort; ++n) {
-        const Item I = S.ritem[n % kRing];  // before publishing n + 1 (another slot)
         const int nxt = publish(n + 1);
+        const Item I = decode_item<!kSplit>(a, cur, part_rows);
         for (int c = 0; c < I.nchunks; ++c) {
           const int st = (int)(g_ld & 1);
           if (g_ld >= 2) {
@@ -591,11 +584,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     const int pieces = Kp / 8;                 // 16-byte pieces per query row
     for (;; ++li) {
       int item = -1;
-      if (lane == 0) item = ring_take(S, li, abort, &S.qitem);
+      if (lane == 0) item = ring_take(S, li, abort);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item < 0) break;
-      __syncwarp();  // lane 0's shared-memory copy of the item is visible to the warp
-      const Item I = S.qitem;
+      const Item I = decode_item<!kSplit>(a, item, part_rows);
       const int b = li % nbuf;
       if (li >= nbuf) {
         bool ok = true;
@@ -646,9 +638,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       const uint64_t bdesc[2] = {dev::smem_desc(dev::smem_addr(B0), 128, sbo),
                                  dev::smem_desc(dev::smem_addr(B1), 128, sbo)};
       for (;; ++li) {
-        Item I;
-        const int item = ring_take(S, li, abort, &I);
+        const int item = ring_take(S, li, abort);
         if (item < 0) break;
+        const Item I = decode_item<!kSplit>(a, item, part_rows);
         const int b = li % nbuf;
         bool ok = wait_phase(&S.bready[b], bready_ph[b], abort);
         bready_ph[b] ^= 1u;
@@ -714,11 +706,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     long long g = 0;
     PROF_T0();
     for (int n = 0;; ++n) {
-      if (tid == 0) S.eitem = ring_take(S, n, abort, &S.eitem_full);
+      if (tid == 0) S.eitem = ring_take(S, n, abort);
       epi_sync();
       const int item = S.eitem;
       if (item < 0) break;
-      const Item I = S.eitem_full;
+      const Item I = decode_item<!kSplit>(a, item, part_rows);
       const int nqg = I.nqg, N = I.N;
       if (prof_on) pr[9] += 1;
       // per-query state of the item (padding columns never admit a series)
