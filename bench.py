@@ -908,6 +908,9 @@ def main():
             "pruning_ratio": 1.0 - st["series_scanned"] / (a.steps * a.queries * a.n),
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
             "waves_per_launch": st["waves"] / max(st["batches"], 1),
+            "host_ms_per_step": {"call": st["host_ms"] / a.steps,
+                                 "waiting_for_gpu": st["host_wait_ms"] / a.steps,
+                                 "busy": (st["host_ms"] - st["host_wait_ms"]) / a.steps},
             "graph_batch_fraction": st["graph_batches"] / max(st["batches"], 1),
             "leaf_selection_alg3": dict(sel_rep, a=2.0, mem_cap_bytes=8 << 30),
             "kernel_ms_per_step": {k: v[0] for k, v in kt_all.items()

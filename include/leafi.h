@@ -389,6 +389,9 @@ typedef struct {
   int64_t distinct_series; /* series of the distinct leaves each round read, summed */
   int64_t rechecks;        /* canonical float32 re-checks by the tensor-core scan */
   int64_t graph_batches;   /* batches replayed from a captured CUDA graph */
+  double host_wait_ms;     /* host time the call spent waiting for the GPU (batch pair
+                              counts, its end) */
+  double host_ms;          /* host time of the whole call */
 } leafi_search_stats;
 
 /* k-NN of nq queries (1 <= k <= LEAFI_MAX_K).  recall_target >= 1 runs the

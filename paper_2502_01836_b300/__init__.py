@@ -156,7 +156,8 @@ class SearchStats(C.Structure):
     _fields_ = [("leaves_scanned", C.c_int64), ("series_scanned", C.c_int64),
                 ("filter_evals", C.c_int64), ("waves", C.c_int64), ("batches", C.c_int64),
                 ("distinct_series", C.c_int64), ("rechecks", C.c_int64),
-                ("graph_batches", C.c_int64)]
+                ("graph_batches", C.c_int64), ("host_wait_ms", C.c_double),
+                ("host_ms", C.c_double)]
 
 
 class SelectParams(C.Structure):

@@ -985,7 +985,10 @@ void Pipeline::finish(int li) {
   make_sa(v, f.nb, f.use_f);
   Scratch& S = lanes[li];
   for (;;) {
+    const auto w0 = std::chrono::steady_clock::now();
     LF_CUDA(cudaEventSynchronize(S.ev_np));
+    st.host_wait_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
     if (f.g && ix->profiling) {
       for (size_t i = 0; i < f.g->kind.size(); ++i) {
         float ms = 0.0f;
@@ -1018,6 +1021,7 @@ namespace {
 void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::vector<int32_t>& kq,
                  const std::vector<double>& target, int kmax, int64_t* ids, float* dists,
                  leafi_search_stats* stats) {
+  const auto t_call = std::chrono::steady_clock::now();
   const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
   if (any_filtered && (ix->nc == 0 || ix->F == 0))
     fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
@@ -1123,9 +1127,13 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   }
   unsigned long long h_stat[4] = {0, 0, 0, 0};
   LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, user));
+  const auto w_end = std::chrono::steady_clock::now();
   LF_CUDA(cudaStreamSynchronize(user));
+  pl.st.host_wait_ms +=
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w_end).count();
   check_err_word(ix);
   leafi_search_stats st = pl.st;
+  st.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_call).count();
   st.leaves_scanned = (int64_t)h_stat[0];
   st.series_scanned = (int64_t)h_stat[1];
   st.distinct_series = (int64_t)h_stat[2];
