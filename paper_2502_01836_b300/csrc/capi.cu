@@ -686,6 +686,9 @@ struct Pipeline {
   void launch_batch(int li, int nb, const int32_t* kq, const double* target, bool uniform);
   // wait for lane li's batch, run its remaining waves, deliver its results
   void finish(int li);
+  // lane li's pair count has reached the host (its event completed): enqueue the
+  // next wave, or deliver the results; returns true when the batch is done
+  bool step(int li);
 };
 
 namespace {
@@ -977,31 +980,26 @@ void Pipeline::launch_batch(int li, int nb, const int32_t* kq, const double* tar
   post_np(v);
 }
 
-void Pipeline::finish(int li) {
+bool Pipeline::step(int li) {
   InFlight& f = fl[li];
-  if (!f.active) return;
   use_lane(li);
   const LaneView& v = lv[li];
   make_sa(v, f.nb, f.use_f);
   Scratch& S = lanes[li];
-  for (;;) {
-    const auto w0 = std::chrono::steady_clock::now();
-    LF_CUDA(cudaEventSynchronize(S.ev_np));
-    st.host_wait_ms +=
-        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
-    if (f.g && ix->profiling) {
-      for (size_t i = 0; i < f.g->kind.size(); ++i) {
-        float ms = 0.0f;
-        LF_CUDA(cudaEventElapsedTime(&ms, f.g->ev[2 * i], f.g->ev[2 * i + 1]));
-        ix->clock.ms[f.g->kind[i]] += ms;
-        ix->clock.n[f.g->kind[i]] += 1;
-      }
+  if (f.g && ix->profiling) {
+    for (size_t i = 0; i < f.g->kind.size(); ++i) {
+      float ms = 0.0f;
+      LF_CUDA(cudaEventElapsedTime(&ms, f.g->ev[2 * i], f.g->ev[2 * i + 1]));
+      ix->clock.ms[f.g->kind[i]] += ms;
+      ix->clock.n[f.g->kind[i]] += 1;
     }
-    f.g = nullptr;
-    if (*S.h_np == 0) break;
+  }
+  f.g = nullptr;
+  if (*S.h_np != 0) {
     if (++f.waves > L + 2) fail(LEAFI_EINTERNAL, "wave loop did not terminate");
     round(v, f.nb);
     post_np(v);
+    return false;
   }
   st.waves += f.waves;
   st.batches += 1;
@@ -1013,6 +1011,18 @@ void Pipeline::finish(int li) {
     deliver(f.dists, v.out_d, (size_t)f.nb * kmax, s);
   }
   f.active = false;
+  return true;
+}
+
+void Pipeline::finish(int li) {
+  if (!fl[li].active) return;
+  for (;;) {
+    const auto w0 = std::chrono::steady_clock::now();
+    LF_CUDA(cudaEventSynchronize(lanes[li].ev_np));
+    st.host_wait_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+    if (step(li)) return;
+  }
 }
 
 namespace {
@@ -1097,11 +1107,14 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   LF_CUDA(cudaEventRecord(ev_start, user));
   for (int li = 0; li < nlanes; ++li) LF_CUDA(cudaStreamWaitEvent(ix->lanes[li].st, ev_start, 0));
 
-  int bi = 0;
-  for (int64_t b0 = 0; b0 < nq; b0 += qb, ++bi) {
-    const int li = bi % nlanes;
+  // The host serves whichever lane is ready: a lane whose pair count has
+  // arrived gets its next wave (or delivers its results and takes the next
+  // batch) at once, so no lane waits while the host is busy with another.
+  int64_t next_b0 = 0;
+  auto start_next = [&](int li) {
+    const int64_t b0 = next_b0;
     const int nb = (int)std::min<int64_t>(qb, nq - b0);
-    pl.finish(li);  // the lane's previous batch (nlanes batches back)
+    next_b0 += nb;
     if (sched)
       pl.start_rows(li, dQall, ix->sched.P.p, dperm + b0, nb,
                     (uniform ? kq.data() : kq_s.data() + b0),
@@ -1110,9 +1123,28 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       pl.start(li, queries + (size_t)b0 * ix->m, nb, kq.data() + (uniform ? 0 : b0),
                target.data() + (uniform ? 0 : b0), uniform, ids + (size_t)b0 * kmax,
                dists + (size_t)b0 * kmax);
+  };
+  for (int li = 0; li < nlanes && next_b0 < nq; ++li) start_next(li);
+  for (;;) {
+    const auto t_it = std::chrono::steady_clock::now();
+    bool active = false, progress = false;
+    for (int li = 0; li < nlanes; ++li) {
+      if (!pl.busy(li)) continue;
+      active = true;
+      const cudaError_t q = cudaEventQuery(ix->lanes[li].ev_np);
+      if (q == cudaErrorNotReady) continue;
+      LF_CUDA(q);
+      progress = true;
+      if (pl.step(li) && next_b0 < nq) start_next(li);
+    }
+    if (!active) break;
+    if (!progress) {
+      // nothing ready: every lane waits for the GPU
+      std::this_thread::yield();
+      pl.st.host_wait_ms +=
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_it).count();
+    }
   }
-  // the remaining batches, oldest first
-  for (int i = 0; i < nlanes; ++i) pl.finish((bi + i) % nlanes);
 
   // the caller's stream continues after both lanes
   for (int li = 0; li < nlanes; ++li) {
