@@ -581,26 +581,32 @@ void required_qualities(leafi_index* ix, int nb, const int32_t* kq, const double
   }
 }
 
-// dst row i = src row rows[i] (rows of mp floats)
-__global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ rows,
-                                   int nb, int mp, float* __restrict__ dst) {
+
+// a scheduled batch's inputs in one launch: query rows and prefix-sum rows
+// gathered from the call's staged arrays, and (uniform batches) every query's k
+// and required quality
+__global__ void batch_prep_kernel(const float* __restrict__ Qall, const double* __restrict__ Pall,
+                                  const int32_t* __restrict__ rows, int nb, int mp, int w,
+                                  float* __restrict__ gQ, double* __restrict__ P, int uniform,
+                                  int32_t* __restrict__ k, double* __restrict__ rq, int kval,
+                                  double rqval) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int mp4 = mp / 4;
-  if (t >= (int64_t)nb * mp4) return;
-  const int i = (int)(t / mp4), c = (int)(t % mp4);
-  reinterpret_cast<float4*>(dst)[t] =
-      reinterpret_cast<const float4*>(src)[(int64_t)rows[i] * mp4 + c];
+  const int64_t nq4 = (int64_t)nb * mp4, np = (int64_t)nb * w;
+  if (t < nq4) {
+    const int i = (int)(t / mp4), c = (int)(t % mp4);
+    reinterpret_cast<float4*>(gQ)[t] = reinterpret_cast<const float4*>(Qall)[(int64_t)rows[i] * mp4 + c];
+  } else if (t < nq4 + np) {
+    const int64_t u = t - nq4;
+    const int i = (int)(u / w), c = (int)(u % w);
+    P[u] = Pall[(int64_t)rows[i] * w + c];
+  } else if (uniform && t < nq4 + np + nb) {
+    const int i = (int)(t - nq4 - np);
+    k[i] = kval;
+    rq[i] = rqval;
+  }
 }
 
-// dst row i = src row rows[i] (rows of w doubles)
-__global__ void gather_rows_f64_kernel(const double* __restrict__ src,
-                                       const int32_t* __restrict__ rows, int nb, int w,
-                                       double* __restrict__ dst) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nb * w) return;
-  const int i = (int)(t / w), c = (int)(t % w);
-  dst[t] = src[(int64_t)rows[i] * w + c];
-}
 
 __global__ void fill_batch_kernel(int nb, int32_t* k, double* target, int kval, double tval) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -683,7 +689,8 @@ struct Pipeline {
   void start_rows(int li, const float* dQall, const double* Pall, const int32_t* rows, int nb,
                   const int32_t* kq, const double* target, bool uniform, int64_t* out_i,
                   float* out_d);
-  void launch_batch(int li, int nb, const int32_t* kq, const double* target, bool uniform);
+  void launch_batch(int li, int nb, const int32_t* kq, const double* target, bool uniform,
+                    bool inputs_ready = false);
   // wait for lane li's batch, run its remaining waves, deliver its results
   void finish(int li);
   // lane li's pair count has reached the host (its event completed): enqueue the
@@ -931,35 +938,39 @@ void Pipeline::start_rows(int li, const float* dQall, const double* Pall, const 
                           int64_t* out_i, float* out_d) {
   use_lane(li);
   const LaneView& v = lv[li];
-  const int64_t n4 = (int64_t)nb * (ix->mp / 4);
-  gather_rows_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(dQall, rows, nb, ix->mp, v.gQ);
-  LF_CHECK_LAUNCH();
-  // the call's prefix sums, computed once for scheduling, serve the bounds
+  // query rows and the call's prefix sums (computed once for scheduling) in one
+  // launch, with the k and required quality of a uniform batch
+  std::vector<double>& rq = rq_host[li];
+  required_qualities(ix, nb, kq, target, uniform, rq);
   const int w = 2 * (ix->m + 1);
-  const int64_t np = (int64_t)nb * w;
-  gather_rows_f64_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
-      Pall, rows, nb, w, lanes[li].sP.p);
+  const int64_t tot = (int64_t)nb * (ix->mp / 4) + (int64_t)nb * w + (uniform ? nb : 0);
+  batch_prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      dQall, Pall, rows, nb, ix->mp, w, v.gQ, lanes[li].sP.p, uniform ? 1 : 0, v.dK, v.dT, kq[0],
+      rq[0]);
   LF_CHECK_LAUNCH();
   fl[li] = InFlight();
   fl[li].ids = out_i;
   fl[li].dists = out_d;
   fl[li].rows = rows;
-  launch_batch(li, nb, kq, target, uniform);
+  launch_batch(li, nb, kq, target, uniform, /*inputs_ready=*/uniform);
 }
 
-// k, targets and the batch's head (graph replay or eager) on the current lane
+// k, targets and the batch's head (graph replay or eager) on the current lane;
+// inputs_ready: k and the required qualities are already on the device
 void Pipeline::launch_batch(int li, int nb, const int32_t* kq, const double* target,
-                            bool uniform) {
+                            bool uniform, bool inputs_ready) {
   const LaneView& v = lv[li];
   // the position kernel compares the tables with the quality each target needs
   std::vector<double>& rq = rq_host[li];
-  required_qualities(ix, nb, kq, target, uniform, rq);
-  if (uniform) {
-    fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.dK, v.dT, kq[0], rq[0]);
-    LF_CHECK_LAUNCH();
-  } else {
-    LF_CUDA(cudaMemcpyAsync(v.dK, kq, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-    LF_CUDA(cudaMemcpyAsync(v.dT, rq.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+  if (!inputs_ready) {
+    required_qualities(ix, nb, kq, target, uniform, rq);
+    if (uniform) {
+      fill_batch_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.dK, v.dT, kq[0], rq[0]);
+      LF_CHECK_LAUNCH();
+    } else {
+      LF_CUDA(cudaMemcpyAsync(v.dK, kq, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+      LF_CUDA(cudaMemcpyAsync(v.dT, rq.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    }
   }
   InFlight& f = fl[li];
   f.active = true;
@@ -1085,9 +1096,11 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     std::vector<int32_t> hkey(nq);
     LF_CUDA(cudaMemcpyAsync(hkey.data(), keys, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, user));
     LF_CUDA(cudaStreamSynchronize(user));
-    std::vector<int32_t> perm(nq);
-    std::iota(perm.begin(), perm.end(), 0);
-    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return hkey[a] < hkey[b]; });
+    // counting sort by route leaf (keys in [0, n_leaves]), stable
+    std::vector<int32_t> perm(nq), start(ix->tree.n_leaves + 2, 0);
+    for (int64_t i = 0; i < nq; ++i) start[hkey[i] + 1] += 1;
+    for (size_t l = 1; l < start.size(); ++l) start[l] += start[l - 1];
+    for (int64_t i = 0; i < nq; ++i) perm[start[hkey[i]]++] = (int32_t)i;
     sc.perm.upload(perm, user);
     dperm = sc.perm.p;
     if (!uniform) {
