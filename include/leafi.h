@@ -53,6 +53,9 @@ typedef enum {
 enum { LEAFI_DSTREE = 0, LEAFI_ISAX = 1 };
 
 enum { LEAFI_MAX_K = 128, LEAFI_MAX_KCLASSES = 4 };
+/* Filter models: the MLP of Sec. 5.1 (default) and the CNN of the model-type
+ * study in Sec. 5.2 (see leafi_set_cnn_filters). */
+enum { LEAFI_FILTER_MLP = 0, LEAFI_FILTER_CNN = 1 };
 
 /* ------------------------------------------------------------------ */
 /* Index building (Sec. 3 "Tree-based indexes"; Alg. 1 input I)        */
@@ -130,6 +133,8 @@ typedef struct {
   int32_t tensor_scan;   /* 1 if leaf scans run on the tensor cores */
   int32_t scan_row_bytes;/* bytes the leaf scan streams per series (fp16 row or fp32 row) */
   double calib_confidence;/* see leafi_set_calibration_confidence */
+  int32_t filter_model;  /* LEAFI_FILTER_MLP or LEAFI_FILTER_CNN */
+  int32_t filter_width;  /* MLP hidden width h, or CNN channels C */
 } leafi_index_info;
 
 leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info);
@@ -215,7 +220,8 @@ leafi_status leafi_select_leaves(const leafi_index* index, int32_t n_filters,
 typedef struct {
   double a;         /* 1 / p^F, the expected filter pruning ratio's inverse (2 in the paper) */
   int64_t mem_cap;  /* c^M: device bytes available to filters */
-  int32_t hidden;   /* hidden width of the filters to come (0 = m) */
+  int32_t hidden;   /* hidden width (MLP) or channels (CNN) of the filters to come (0 = m) */
+  int32_t model;    /* LEAFI_FILTER_MLP or LEAFI_FILTER_CNN: whose forward t^F times */
 } leafi_select_params;
 typedef struct {
   double t_filter_s;     /* t^F */
@@ -232,11 +238,33 @@ leafi_status leafi_select_leaves_auto(leafi_index* index, const leafi_select_par
 leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F,
                                int32_t h, const float* W1, const float* b1, const float* w2,
                                const float* b2);
+/* CNN filters (Sec. 5.2, model-type study: two convolutional layers, kernel
+ * size 3, latent channels C = m).  Readings of what the paper leaves open: one
+ * input channel; stride 1 and zero padding 1, so every layer keeps length m;
+ * bias and ReLU after both convolutions; each channel averaged over the m
+ * positions, then a linear layer C -> 1 without activation predicting the
+ * Euclidean d^L.  Parameters of one filter, flat float32, P =
+ * leafi_cnn_params(C) = 3C^2 + 6C + 1 values: w1 [C][3], b1 [C], w2 [C][C][3]
+ * (output channel, input channel, tap; tap t meets position i + t - 1), b2
+ * [C], wo [C], bo.  theta [F][P], host or device.  LEAFI_EINVAL when the
+ * activations of one query (3 planes of C x (m + 2) floats for training) do
+ * not fit the device's shared memory (C = m up to about 128).  Installing
+ * clears the auto-tuners. */
+int64_t leafi_cnn_params(int32_t C);
+leafi_status leafi_set_cnn_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F,
+                                   int32_t C, const float* theta);
+/* Copy the CNN parameters out (theta [F][P]); LEAFI_EINVAL for MLP filters. */
+leafi_status leafi_get_cnn_filters(leafi_index* index, float* theta);
+/* Initial CNN parameters of F filters of C channels (Philox draws, U(-a, a)
+ * with a = 1/sqrt(fan in): 3 for w1/b1, 3C for w2/b2, C for wo/bo). */
+leafi_status leafi_initial_cnn_weights(leafi_index* index, int32_t F, int32_t C, uint64_t seed,
+                                       float* theta);
 /* The filtered leaves, filter by filter (int32 [n_filters], host). */
 leafi_status leafi_get_filter_leaves(const leafi_index* index, int32_t* filter_leaf);
-/* Copy the current filter weights out (same layouts as leafi_set_filters). */
+/* Copy the current MLP filter weights out (same layouts as leafi_set_filters;
+ * LEAFI_EINVAL for CNN filters). */
 leafi_status leafi_get_filters(leafi_index* index, float* W1, float* b1, float* w2, float* b2);
-/* d^f(q, M_f) for every query and filter (float32, nq x F). */
+/* d^f(q, M_f) for every query and filter (float32, nq x F), either model. */
 leafi_status leafi_filter_predict(leafi_index* index, const float* queries, int64_t nq,
                                   float* out);
 
@@ -287,6 +315,8 @@ typedef struct {
                                leafi_set_calibration_confidence) */
   int32_t tune_search;      /* 1: before the auto-tuners are fitted, leafi_tune_search picks
                                the wave width and work-item balance (its defaults) */
+  int32_t model;            /* LEAFI_FILTER_MLP (Sec. 5.1) or LEAFI_FILTER_CNN (Sec. 5.2;
+                               `hidden` is then the channel count C, 0 = m) */
 } leafi_train_params;
 
 typedef struct {
@@ -332,7 +362,7 @@ typedef struct {
 /* Alg. 1 lines 3-9 on queries the caller supplies (inspection export for
  * parity checks): computes the targets of Qg [n_gtrain+n_gval][m] and
  * Ql [F][n_ltrain+n_lval][m] on the device, then trains every installed
- * filter by SGD on the MSE loss from its current weights, one shuffle
+ * filter (either model) by SGD on the MSE loss from its current weights, one shuffle
  * perms [max_epochs][n_gtrain+n_ltrain] per epoch; keeps the weights of the
  * lowest validation loss.  epochs_run / best_val (nullable, host, [F]). */
 leafi_status leafi_train_filters_on(leafi_index* index, const leafi_sgd_params* p,

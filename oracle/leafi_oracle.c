@@ -835,7 +835,7 @@ void or_train_targets(const or_tree* t, const int32_t* filter_leaf, int F, const
 /* ------------------------------------------------------------------ */
 
 enum { OR_TAG_GPICK = 1, OR_TAG_LPICK = 2, OR_TAG_SIGMA = 3, OR_TAG_NOISE = 4, OR_TAG_W1 = 5,
-       OR_TAG_B1 = 6, OR_TAG_W2 = 7, OR_TAG_B2 = 8, OR_TAG_PERM = 9 };
+       OR_TAG_B1 = 6, OR_TAG_W2 = 7, OR_TAG_B2 = 8, OR_TAG_PERM = 9, OR_TAG_CNN = 10 };
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
   uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
@@ -1141,6 +1141,232 @@ void or_train(const or_train_params* p, int F, int h, int m, const float* Qg, co
 }
 
 /* ------------------------------------------------------------------ */
+/* CNN filters (Sec. 5.2, model-type study): two convolutional layers  */
+/* of kernel size 3 whose latent channel count C equals the series     */
+/* length.  Readings (the paper states only the two layers, k = 3 and  */
+/* C = m): one input channel; stride 1 and zero padding 1 so every     */
+/* layer keeps length m; bias and ReLU after both convolutions; the    */
+/* head averages each channel over the m positions and a linear layer */
+/* C -> 1 (no output activation) predicts the Euclidean d^L like the   */
+/* MLP.  Parameters of one filter, flat float32:                       */
+/*   w1 [C][3], b1 [C], w2 [C][C][3] (out, in, tap), b2 [C], wo [C], bo */
+/* Initial values ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) with fan_in 3,   */
+/* 3C and C for the three layers (biases take their layer's bound).    */
+/* ------------------------------------------------------------------ */
+
+int64_t or_cnn_params(int C) { return 3 * (int64_t)C * C + 6 * (int64_t)C + 1; }
+
+typedef struct {
+  const double *w1, *b1, *w2, *b2, *wo, *bo;
+} cnn_view;
+
+static cnn_view cnn_at(const double* th, int C) {
+  cnn_view v;
+  v.w1 = th;
+  v.b1 = v.w1 + 3 * C;
+  v.w2 = v.b1 + C;
+  v.b2 = v.w2 + 3 * (size_t)C * C;
+  v.wo = v.b2 + C;
+  v.bo = v.wo + C;
+  return v;
+}
+
+/* Forward of one query x (length m): z1, z2 [C][m] (pre-activations) and the
+ * pooled means p [C] are kept for the backward pass; returns the prediction. */
+static double cnn_one(const double* th, int C, int m, const float* x, double* z1, double* z2,
+                      double* p) {
+  const cnn_view v = cnn_at(th, C);
+  for (int c = 0; c < C; ++c)
+    for (int i = 0; i < m; ++i) {
+      double z = v.b1[c];
+      for (int t = 0; t < 3; ++t) {
+        const int j = i + t - 1;
+        if (j >= 0 && j < m) z += v.w1[c * 3 + t] * (double)x[j];
+      }
+      z1[(size_t)c * m + i] = z;
+    }
+  for (int c = 0; c < C; ++c) {
+    double sum = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double z = v.b2[c];
+      for (int cp = 0; cp < C; ++cp)
+        for (int t = 0; t < 3; ++t) {
+          const int j = i + t - 1;
+          if (j < 0 || j >= m) continue;
+          const double a = z1[(size_t)cp * m + j];
+          if (a > 0.0) z += v.w2[((size_t)c * C + cp) * 3 + t] * a;
+        }
+      z2[(size_t)c * m + i] = z;
+      if (z > 0.0) sum += z;
+    }
+    p[c] = sum / (double)m;
+  }
+  double y = v.bo[0];
+  for (int c = 0; c < C; ++c) y += v.wo[c] * p[c];
+  return y;
+}
+
+/* Gradient of y (times dy) accumulated into g (layout of the parameters). */
+static void cnn_back(const double* th, int C, int m, const float* x, const double* z1,
+                     const double* z2, const double* p, double dy, double* g, double* da1) {
+  const cnn_view v = cnn_at(th, C);
+  double* gw1 = g;
+  double* gb1 = gw1 + 3 * C;
+  double* gw2 = gb1 + C;
+  double* gb2 = gw2 + 3 * (size_t)C * C;
+  double* gwo = gb2 + C;
+  double* gbo = gwo + C;
+  gbo[0] += dy;
+  for (size_t e = 0; e < (size_t)C * m; ++e) da1[e] = 0.0;
+  for (int c = 0; c < C; ++c) {
+    gwo[c] += dy * p[c];
+    const double dp = dy * v.wo[c] / (double)m;  /* d y / d z2 for a positive z2 */
+    for (int i = 0; i < m; ++i) {
+      if (!(z2[(size_t)c * m + i] > 0.0)) continue;
+      gb2[c] += dp;
+      for (int cp = 0; cp < C; ++cp)
+        for (int t = 0; t < 3; ++t) {
+          const int j = i + t - 1;
+          if (j < 0 || j >= m) continue;
+          const double a = z1[(size_t)cp * m + j];
+          if (a > 0.0) gw2[((size_t)c * C + cp) * 3 + t] += dp * a;
+          da1[(size_t)cp * m + j] += dp * v.w2[((size_t)c * C + cp) * 3 + t];
+        }
+    }
+  }
+  for (int c = 0; c < C; ++c)
+    for (int j = 0; j < m; ++j) {
+      if (!(z1[(size_t)c * m + j] > 0.0)) continue;
+      const double d = da1[(size_t)c * m + j];
+      gb1[c] += d;
+      for (int t = 0; t < 3; ++t) {
+        const int i = j + t - 1;
+        if (i >= 0 && i < m) gw1[c * 3 + t] += d * (double)x[i];
+      }
+    }
+}
+
+void or_cnn_forward(const float* theta, int F, int C, int m, const float* Q, int64_t nq,
+                    double* out) {
+  const int64_t P = or_cnn_params(C);
+#pragma omp parallel
+  {
+    double* th = (double*)malloc(sizeof(double) * (size_t)P);
+    double* z1 = (double*)malloc(sizeof(double) * (size_t)C * m);
+    double* z2 = (double*)malloc(sizeof(double) * (size_t)C * m);
+    double* p = (double*)malloc(sizeof(double) * (size_t)C);
+#pragma omp for schedule(static)
+    for (int f = 0; f < F; ++f) {
+      for (int64_t e = 0; e < P; ++e) th[e] = (double)theta[(size_t)f * P + e];
+      for (int64_t i = 0; i < nq; ++i)
+        out[i * F + f] = cnn_one(th, C, m, Q + i * m, z1, z2, p);
+    }
+    free(th);
+    free(z1);
+    free(z2);
+    free(p);
+  }
+}
+
+void or_cnn_init(int F, int C, uint64_t seed, float* theta) {
+  const int64_t P = or_cnn_params(C);
+  const double a1 = 1.0 / sqrt(3.0), a2 = 1.0 / sqrt(3.0 * C), ao = 1.0 / sqrt((double)C);
+  const int64_t e_b1 = 3 * (int64_t)C, e_w2 = e_b1 + C, e_b2 = e_w2 + 3 * (int64_t)C * C,
+                e_wo = e_b2 + C;
+  uint32_t w[4];
+  for (int f = 0; f < F; ++f)
+    for (int64_t e = 0; e < P; ++e) {
+      const double a = e < e_w2 ? a1 : (e < e_wo ? a2 : ao);
+      draw(seed, (uint32_t)e, (uint32_t)f, OR_TAG_CNN, 0, w);
+      theta[(size_t)f * P + e] = (float)((2.0 * unif53(w[0], w[1]) - 1.0) * a);
+    }
+}
+
+/* SGD of every CNN filter: the protocol of or_train (minibatch MSE, plateau
+ * schedule, best-validation parameters kept) with the CNN's gradients. */
+void or_cnn_train(const or_train_params* p, int F, int C, int m, const float* Qg,
+                  const float* Tg, const float* Ql, const float* Tl, const int32_t* perms,
+                  float* theta, int32_t* epochs_run, double* best_val) {
+  const int ntr = p->n_gtrain + p->n_ltrain;
+  const int nval = p->n_gval + p->n_lval;
+  const int nlq = p->n_ltrain + p->n_lval;
+  const int64_t P = or_cnn_params(C);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int f = 0; f < F; ++f) {
+    double* A = (double*)malloc(sizeof(double) * (size_t)P * 3);
+    double* G = A + P;
+    double* BEST = G + P;
+    double* z1 = (double*)malloc(sizeof(double) * (size_t)C * m);
+    double* z2 = (double*)malloc(sizeof(double) * (size_t)C * m);
+    double* da1 = (double*)malloc(sizeof(double) * (size_t)C * m);
+    double* pc = (double*)malloc(sizeof(double) * (size_t)C);
+    for (int64_t e = 0; e < P; ++e) A[e] = (double)theta[(size_t)f * P + e];
+    memcpy(BEST, A, sizeof(double) * (size_t)P);
+    double lr = p->lr0, best = INFINITY;
+    int bad = 0, ep = 0;
+    for (ep = 0; ep < p->max_epochs; ++ep) {
+      const int32_t* perm = perms + (size_t)ep * ntr;
+      for (int st = 0; st < ntr; st += p->batch) {
+        const int bs = (ntr - st < p->batch) ? ntr - st : p->batch;
+        memset(G, 0, sizeof(double) * (size_t)P);
+        for (int b = 0; b < bs; ++b) {
+          const int s = perm[st + b];
+          const float* x;
+          double tgt;
+          if (s < p->n_gtrain) {
+            x = Qg + (size_t)s * m;
+            tgt = Tg[(size_t)s * F + f];
+          } else {
+            const int l = s - p->n_gtrain;
+            x = Ql + ((size_t)f * nlq + l) * m;
+            tgt = Tl[(size_t)f * nlq + l];
+          }
+          const double y = cnn_one(A, C, m, x, z1, z2, pc);
+          cnn_back(A, C, m, x, z1, z2, pc, 2.0 * (y - tgt) / (double)bs, G, da1);
+        }
+        for (int64_t e = 0; e < P; ++e) A[e] -= lr * G[e];
+      }
+      double vl = 0.0;
+      for (int v = 0; v < nval; ++v) {
+        const float* x;
+        double tgt;
+        if (v < p->n_gval) {
+          x = Qg + (size_t)(p->n_gtrain + v) * m;
+          tgt = Tg[(size_t)(p->n_gtrain + v) * F + f];
+        } else {
+          const int l = p->n_ltrain + (v - p->n_gval);
+          x = Ql + ((size_t)f * nlq + l) * m;
+          tgt = Tl[(size_t)f * nlq + l];
+        }
+        const double y = cnn_one(A, C, m, x, z1, z2, pc);
+        vl += (y - tgt) * (y - tgt);
+      }
+      vl /= (double)nval;
+      if (vl < best) {
+        best = vl;
+        memcpy(BEST, A, sizeof(double) * (size_t)P);
+        bad = 0;
+      } else if (++bad >= p->patience) {
+        lr /= 10.0;
+        bad = 0;
+        if (lr < p->lr_min * (1.0 - 1e-9)) {
+          ++ep;
+          break;
+        }
+      }
+    }
+    for (int64_t e = 0; e < P; ++e) theta[(size_t)f * P + e] = (float)BEST[e];
+    if (epochs_run) epochs_run[f] = ep;
+    if (best_val) best_val[f] = best;
+    free(A);
+    free(z1);
+    free(z2);
+    free(da1);
+    free(pc);
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* Search in wave semantics (Alg. 2)                                   */
 /*                                                                     */
 /* Reading of "ordered by I^F": the query's route leaf is searched     */
@@ -1236,11 +1462,12 @@ static int wave_search(int L, const double* lb2, const int* ord, int route,
   return nscanned;
 }
 
-void or_leafi_search(const or_tree* t, const float* W1, const float* b1, const float* w2,
-                     const float* b2, const int32_t* filter_leaf, int F, int h,
-                     const double* alpha_sorted, int64_t nc, const float* Q, int64_t nq,
-                     const int32_t* k, const int32_t* jpos, int kmax, int wave, int64_t* ids,
-                     float* d2, int64_t* stats, double* min_margin) {
+/* The search on given filter predictions P [nq][F] (d^f of every query and
+ * filter, float64), whatever the filters' model. */
+void or_leafi_search_pred(const or_tree* t, const double* P, const int32_t* filter_leaf, int F,
+                          const double* alpha_sorted, int64_t nc, const float* Q, int64_t nq,
+                          const int32_t* k, const int32_t* jpos, int kmax, int wave,
+                          int64_t* ids, float* d2, int64_t* stats, double* min_margin) {
   const int L = t->nleaves, m = t->m;
   double* lb2 = (double*)malloc(sizeof(double) * (size_t)nq * L);
   int32_t* route = (int32_t*)malloc(sizeof(int32_t) * nq);
@@ -1259,11 +1486,8 @@ void or_leafi_search(const or_tree* t, const float* W1, const float* b1, const f
       int use_f = (jpos && jpos[i] >= 0 && F > 0);
       if (use_f) {
         for (int l = 0; l < L; ++l) df[l] = NAN;
-        for (int f = 0; f < F; ++f) {
-          double pred = mlp_one(W1 + (size_t)f * h * m, b1 + (size_t)f * h, w2 + (size_t)f * h,
-                                b2[f], h, m, q);
-          df[filter_leaf[f]] = pred - alpha_sorted[(size_t)f * nc + jpos[i]];
-        }
+        for (int f = 0; f < F; ++f)
+          df[filter_leaf[f]] = P[(size_t)i * F + f] - alpha_sorted[(size_t)f * nc + jpos[i]];
       }
       leaf_source src = {t, q, NULL, NULL, 0};
       int cnt = 0;
@@ -1298,6 +1522,18 @@ void or_leafi_search(const or_tree* t, const float* W1, const float* b1, const f
   free(route);
 }
 
+void or_leafi_search(const or_tree* t, const float* W1, const float* b1, const float* w2,
+                     const float* b2, const int32_t* filter_leaf, int F, int h,
+                     const double* alpha_sorted, int64_t nc, const float* Q, int64_t nq,
+                     const int32_t* k, const int32_t* jpos, int kmax, int wave, int64_t* ids,
+                     float* d2, int64_t* stats, double* min_margin) {
+  double* P = (double*)malloc(sizeof(double) * (size_t)(nq > 0 ? nq : 1) * (F > 0 ? F : 1));
+  if (F > 0) or_mlp_forward(W1, b1, w2, b2, F, h, t->m, Q, nq, P);
+  or_leafi_search_pred(t, P, filter_leaf, F, alpha_sorted, nc, Q, nq, k, jpos, kmax, wave, ids,
+                       d2, stats, min_margin);
+  free(P);
+}
+
 /* ------------------------------------------------------------------ */
 /* Auto-tuner learning (Alg. 4) and query-time offsets (Sec. 4.4.2)    */
 /*                                                                     */
@@ -1314,11 +1550,11 @@ static int cmp_desc(const void* a, const void* b) {
   return (x < y) - (x > y);
 }
 
-void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const float* w2,
-                      const float* b2, const int32_t* filter_leaf, int F, int h,
-                      const float* Qc, int64_t nc, int k, int wave, double* alpha_sorted,
-                      double* qprime) {
-  const int L = t->nleaves, m = t->m;
+/* Alg. 4 on given predictions Pc [nc][F] of the calibration queries. */
+void or_fit_autotuner_pred(const or_tree* t, const double* Pc, const int32_t* filter_leaf, int F,
+                           const float* Qc, int64_t nc, int k, int wave, double* alpha_sorted,
+                           double* qprime) {
+  const int L = t->nleaves;
   int32_t* leaves = (int32_t*)malloc(sizeof(int32_t) * (size_t)nc * L);
   for (int64_t c = 0; c < nc; ++c)
     for (int l = 0; l < L; ++l) leaves[c * L + l] = l;
@@ -1329,8 +1565,7 @@ void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const 
   int32_t* route = (int32_t*)malloc(sizeof(int32_t) * nc);
   or_leaf_lb2(t, Qc, nc, lb2);
   or_route(t, Qc, nc, route);
-  double* P = (double*)malloc(sizeof(double) * (size_t)nc * F);
-  or_mlp_forward(W1, b1, w2, b2, F, h, m, Qc, nc, P);
+  const double* P = Pc;
   /* step 1: absolute errors, sorted descending per filter */
   for (int f = 0; f < F; ++f) {
     double* a = alpha_sorted + (size_t)f * nc;
@@ -1402,12 +1637,21 @@ void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const 
   free(ordc);
   free(cnt_true);
   free(leaf_of);
-  free(P);
   free(lb2);
   free(route);
   free(LD);
   free(LI);
   free(leaves);
+}
+
+void or_fit_autotuner(const or_tree* t, const float* W1, const float* b1, const float* w2,
+                      const float* b2, const int32_t* filter_leaf, int F, int h,
+                      const float* Qc, int64_t nc, int k, int wave, double* alpha_sorted,
+                      double* qprime) {
+  double* P = (double*)malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1) * (F > 0 ? F : 1));
+  if (F > 0) or_mlp_forward(W1, b1, w2, b2, F, h, t->m, Qc, nc, P);
+  or_fit_autotuner_pred(t, P, filter_leaf, F, Qc, nc, k, wave, alpha_sorted, qprime);
+  free(P);
 }
 
 /* Alg. 3 (leaf node selection), in its order: sort by size, then one pass */

@@ -87,6 +87,31 @@ void or_train(const or_train_params* p, int F, int h, int m,
               const int32_t* perms, float* W1, float* b1, float* w2, float* b2,
               int32_t* epochs_run, double* best_val);
 
+/* CNN filters (Sec. 5.2 model-type study): conv(1->C, k=3) + ReLU, conv(C->C,
+ * k=3) + ReLU (stride 1, zero padding 1), mean over positions, linear C -> 1.
+ * Flat float32 parameters per filter: w1 [C][3], b1 [C], w2 [C][C][3], b2 [C],
+ * wo [C], bo; or_cnn_params(C) = 3C^2 + 6C + 1 values.  Forward in float64. */
+int64_t or_cnn_params(int C);
+void or_cnn_forward(const float* theta, int F, int C, int m, const float* Q, int64_t nq,
+                    double* out);
+/* U(-1/sqrt(fan_in), 1/sqrt(fan_in)) initial parameters (fan_in 3, 3C, C). */
+void or_cnn_init(int F, int C, uint64_t seed, float* theta);
+/* SGD of the CNN filters: the protocol of or_train; theta [F][P] in/out. */
+void or_cnn_train(const or_train_params* p, int F, int C, int m,
+                  const float* Qg, const float* Tg, const float* Ql, const float* Tl,
+                  const int32_t* perms, float* theta, int32_t* epochs_run, double* best_val);
+
+/* Alg. 4 and Alg. 2 on given filter predictions (float64, [nc][F] / [nq][F]),
+ * for any filter model; or_fit_autotuner / or_leafi_search take MLP weights. */
+void or_fit_autotuner_pred(const or_tree* t, const double* Pc, const int32_t* filter_leaf, int F,
+                           const float* Qc, int64_t nc, int k, int wave,
+                           double* alpha_sorted, double* qprime);
+void or_leafi_search_pred(const or_tree* t, const double* P, const int32_t* filter_leaf, int F,
+                          const double* alpha_sorted, int64_t nc,
+                          const float* Q, int64_t nq, const int32_t* k, const int32_t* jpos,
+                          int kmax, int wave, int64_t* ids, float* d2, int64_t* stats,
+                          double* min_margin);
+
 /* Auto-tuner learning (Alg. 4) for one k: calibration queries Qc (nc).
  * Outputs alpha_sorted [F][nc] (descending) and qprime [nc] (running-min
  * of the calibration recall at each sorted position). */

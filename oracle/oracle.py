@@ -16,6 +16,7 @@ __all__ = [
     "mlp_forward", "train_targets", "TrainParams", "train", "fit_autotuner",
     "offset_position", "required_quality", "philox4x32_10", "training_queries",
     "filter_init", "epoch_perms", "steffen_eval", "leafi_search", "recall_at_k", "select_leaves_alg3",
+    "cnn_params", "cnn_forward", "cnn_init", "cnn_train", "fit_autotuner_pred", "leafi_search_pred",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -100,6 +101,17 @@ def lib():
         L.or_leafi_search.argtypes = [vp, f32p, f32p, f32p, f32p, i32p, C.c_int, C.c_int, f64p,
                                       C.c_int64, f32p, C.c_int64, i32p, i32p, C.c_int, C.c_int,
                                       i64p, f32p, i64p, f64p]
+        L.or_leafi_search_pred.argtypes = [vp, f64p, i32p, C.c_int, f64p, C.c_int64, f32p,
+                                           C.c_int64, i32p, i32p, C.c_int, C.c_int, i64p, f32p,
+                                           i64p, f64p]
+        L.or_fit_autotuner_pred.argtypes = [vp, f64p, i32p, C.c_int, f32p, C.c_int64, C.c_int,
+                                            C.c_int, f64p, f64p]
+        L.or_cnn_params.argtypes = [C.c_int]
+        L.or_cnn_params.restype = C.c_int64
+        L.or_cnn_forward.argtypes = [f32p, C.c_int, C.c_int, C.c_int, f32p, C.c_int64, f64p]
+        L.or_cnn_init.argtypes = [C.c_int, C.c_int, C.c_uint64, f32p]
+        L.or_cnn_train.argtypes = [C.POINTER(_TrainParams), C.c_int, C.c_int, C.c_int, f32p,
+                                   f32p, f32p, f32p, i32p, f32p, i32p, f64p]
         _lib = L
     return _lib
 
@@ -367,3 +379,72 @@ def recall_at_k(ids, true_ids, k):
     true_ids = np.asarray(true_ids)[:, :k]
     return np.array([len(set(a.tolist()) & set(b.tolist())) / float(k)
                      for a, b in zip(ids, true_ids)])
+
+
+# ---------------------------------------------------------------- CNN filters
+
+def cnn_params(C_):
+    """Parameters of one CNN filter of C channels: 3C^2 + 6C + 1."""
+    return int(lib().or_cnn_params(int(C_)))
+
+
+def cnn_forward(theta, C_, Q):
+    """theta [F, P] flat CNN parameters -> predictions [nq, F] (float64)."""
+    theta = _f32(theta)
+    Q = _f32(Q)
+    F = theta.shape[0]
+    assert theta.shape[1] == cnn_params(C_)
+    out = np.empty((Q.shape[0], F), np.float64)
+    lib().or_cnn_forward(theta, F, int(C_), Q.shape[1], Q, Q.shape[0], out)
+    return out
+
+
+def cnn_init(F, C_, seed):
+    theta = np.zeros((F, cnn_params(C_)), np.float32)
+    lib().or_cnn_init(F, int(C_), int(seed), theta)
+    return theta
+
+
+def cnn_train(p: TrainParams, C_, Qg, Tg, Ql, Tl, perms, theta):
+    """Returns the trained theta [F, P], epochs run and best validation loss per filter."""
+    theta = np.array(theta, dtype=np.float32, copy=True)
+    F = theta.shape[0]
+    Qg = _f32(Qg)
+    m = Qg.shape[1]
+    ep = np.zeros(F, np.int32)
+    bv = np.zeros(F, np.float64)
+    cp = p.c()
+    lib().or_cnn_train(C.byref(cp), F, int(C_), m, Qg, _f32(Tg), _f32(Ql), _f32(Tl),
+                       np.ascontiguousarray(perms, np.int32), theta, ep, bv)
+    return theta, ep, bv
+
+
+def fit_autotuner_pred(tree: Tree, Pc, filter_leaf, Qc, k, wave):
+    """Alg. 4 on the calibration queries' predictions Pc [nc, F]."""
+    Pc = np.ascontiguousarray(Pc, np.float64)
+    Qc = _f32(Qc)
+    nc, F = Pc.shape
+    alpha = np.empty((F, nc), np.float64)
+    qp = np.empty(nc, np.float64)
+    lib().or_fit_autotuner_pred(tree._h, Pc, np.ascontiguousarray(filter_leaf, np.int32), F, Qc,
+                                nc, k, wave, alpha, qp)
+    return alpha, qp
+
+
+def leafi_search_pred(tree: Tree, P, filter_leaf, alpha_sorted, Q, k, jpos, wave, kmax=None):
+    """leafi_search on given predictions P [nq, F] (any filter model)."""
+    Q = _f32(Q)
+    nq = Q.shape[0]
+    P = np.ascontiguousarray(P, np.float64)
+    k = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    jpos = np.ascontiguousarray(np.broadcast_to(np.asarray(jpos, np.int32), (nq,)))
+    kmax = int(k.max()) if kmax is None else kmax
+    alpha = np.ascontiguousarray(alpha_sorted, np.float64)
+    F = P.shape[1]
+    ids = np.empty((nq, kmax), np.int64)
+    d2 = np.empty((nq, kmax), np.float32)
+    st = np.empty((nq, 4), np.int64)
+    mm = np.empty(nq, np.float64)
+    lib().or_leafi_search_pred(tree._h, P, np.ascontiguousarray(filter_leaf, np.int32), F, alpha,
+                               alpha.shape[1], Q, nq, k, jpos, kmax, wave, ids, d2, st, mm)
+    return ids, d2, st, mm

@@ -37,6 +37,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libleafi.so")
 
 DSTREE, ISAX = 0, 1
+FILTER_MLP, FILTER_CNN = 0, 1
 MAX_K = 128
 _STATUS = {0: "LEAFI_OK", 1: "LEAFI_EINVAL", 2: "LEAFI_ENOMEM", 3: "LEAFI_ECUDA",
            4: "LEAFI_ETIMEOUT", 5: "LEAFI_ENOTTRAINED", 6: "LEAFI_EINTERNAL",
@@ -57,7 +58,8 @@ EXPORTED_SYMBOLS = [
     "leafi_znormalize", "leafi_get_filter_leaves", "leafi_debug_set_lock_tries",
     "leafi_debug_fail_allocations", "leafi_set_calibration_confidence",
     "leafi_set_query_schedule", "leafi_set_search_lanes", "leafi_set_scan_part",
-    "leafi_tune_search",
+    "leafi_tune_search", "leafi_cnn_params", "leafi_set_cnn_filters", "leafi_get_cnn_filters",
+    "leafi_initial_cnn_weights",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -89,7 +91,8 @@ class IndexInfo(C.Structure):
                 ("n_calib", C.c_int32), ("n_kclasses", C.c_int32),
                 ("kclasses", C.c_int32 * 4), ("device_bytes", C.c_int64),
                 ("tensor_scan", C.c_int32), ("scan_row_bytes", C.c_int32),
-                ("calib_confidence", C.c_double)]
+                ("calib_confidence", C.c_double), ("filter_model", C.c_int32),
+                ("filter_width", C.c_int32)]
 
 
 class TrainParams(C.Structure):
@@ -100,16 +103,16 @@ class TrainParams(C.Structure):
                 ("batch", C.c_int32), ("max_epochs", C.c_int32), ("patience", C.c_int32),
                 ("lr0", C.c_double), ("lr_min", C.c_double), ("n_kclasses", C.c_int32),
                 ("kclasses", C.c_int32 * 4), ("seed", C.c_uint64), ("confidence", C.c_double),
-                ("tune_search", C.c_int32)]
+                ("tune_search", C.c_int32), ("model", C.c_int32)]
 
     def __init__(self, n_filters=100, a=2.0, mem_cap=8 << 30, hidden=0, n_train=2000,
                  global_local_ratio=3.0, val_frac=0.2, noise_lo=0.1, noise_hi=0.4, batch=64,
                  max_epochs=1000, patience=10, lr0=0.01, lr_min=1e-5, kclasses=(1,),
-                 seed=2502018361, confidence=0.95, tune_search=1):
+                 seed=2502018361, confidence=0.95, tune_search=1, model=0):
         kc = (C.c_int32 * 4)(*(list(kclasses) + [0] * (4 - len(kclasses))))
         super().__init__(n_filters, a, mem_cap, hidden, n_train, global_local_ratio, val_frac,
                          noise_lo, noise_hi, batch, max_epochs, patience, lr0, lr_min,
-                         len(kclasses), kc, seed, confidence, tune_search)
+                         len(kclasses), kc, seed, confidence, tune_search, model)
 
 
 class TuneParams(C.Structure):
@@ -161,7 +164,8 @@ class SearchStats(C.Structure):
 
 
 class SelectParams(C.Structure):
-    _fields_ = [("a", C.c_double), ("mem_cap", C.c_int64), ("hidden", C.c_int32)]
+    _fields_ = [("a", C.c_double), ("mem_cap", C.c_int64), ("hidden", C.c_int32),
+                ("model", C.c_int32)]
 
 
 class SelectReport(C.Structure):
@@ -205,6 +209,9 @@ def lib():
             "leafi_select_leaves": [vp, i32, vp],
             "leafi_set_filters": [vp, vp, i32, i32, vp, vp, vp, vp],
             "leafi_get_filters": [vp, vp, vp, vp, vp],
+            "leafi_set_cnn_filters": [vp, vp, i32, i32, vp],
+            "leafi_get_cnn_filters": [vp, vp],
+            "leafi_initial_cnn_weights": [vp, i32, i32, C.c_uint64, vp],
             "leafi_filter_predict": [vp, vp, i64, vp],
             "leafi_leaf_knn": [vp, vp, i64, vp, i32, i32, vp, vp],
             "leafi_train_targets": [vp, vp, i64, vp, i64, vp, vp],
@@ -244,6 +251,8 @@ def lib():
             fn.restype = C.c_int
         L.leafi_free.argtypes = [vp]
         L.leafi_free.restype = None
+        L.leafi_cnn_params.argtypes = [i32]
+        L.leafi_cnn_params.restype = C.c_int64
         L.leafi_launch_count.argtypes = []
         L.leafi_launch_count.restype = C.c_int64
         L.leafi_last_error.argtypes = []
@@ -392,11 +401,11 @@ def leafi_select_leaves(index, n_filters):
     return out
 
 
-def leafi_select_leaves_auto(index, a=2.0, mem_cap=8 << 30, hidden=0):
+def leafi_select_leaves_auto(index, a=2.0, mem_cap=8 << 30, hidden=0, model=0):
     """Alg. 3 with this device's measured t^F and t^S: (filter_leaf, report dict)."""
     out = np.zeros(max(1, leafi_get_info(index).n_leaves), np.int32)
     rep = SelectReport()
-    _check(lib().leafi_select_leaves_auto(index, C.byref(SelectParams(a, mem_cap, hidden)),
+    _check(lib().leafi_select_leaves_auto(index, C.byref(SelectParams(a, mem_cap, hidden, model)),
                                           out.ctypes.data, C.byref(rep)))
     return out[:rep.n_selected].copy(), {f: getattr(rep, f) for f, _ in SelectReport._fields_}
 
@@ -406,6 +415,34 @@ def leafi_set_filters(index, filter_leaf, W1, b1, w2, b2):
     _check(lib().leafi_set_filters(index, _ptr(filter_leaf, np.int32, "filter_leaf"), F, h,
                                    _ptr(W1, np.float32, "W1"), _ptr(b1, np.float32, "b1"),
                                    _ptr(w2, np.float32, "w2"), _ptr(b2, np.float32, "b2")))
+
+
+def leafi_cnn_params(C_):
+    """Parameters of one CNN filter of C_ channels (3 C^2 + 6 C + 1)."""
+    return int(lib().leafi_cnn_params(int(C_)))
+
+
+def leafi_set_cnn_filters(index, filter_leaf, C_, theta):
+    """Install CNN filters: theta [F, leafi_cnn_params(C_)] float32 (host or device)."""
+    F = theta.shape[0]
+    if theta.ndim != 2 or theta.shape[1] != leafi_cnn_params(C_):
+        raise ValueError("theta must be [F, leafi_cnn_params(C)]")
+    _check(lib().leafi_set_cnn_filters(index, _ptr(filter_leaf, np.int32, "filter_leaf"), F,
+                                       int(C_), _ptr(theta, np.float32, "theta")))
+
+
+def leafi_get_cnn_filters(index):
+    info = leafi_get_info(index)
+    out = np.zeros((info.n_filters, leafi_cnn_params(info.filter_width)), np.float32)
+    _check(lib().leafi_get_cnn_filters(index, out.ctypes.data))
+    return out
+
+
+def leafi_initial_cnn_weights(index, F, C_, seed):
+    """Initial CNN parameters [F, leafi_cnn_params(C_)] drawn by the library."""
+    out = np.zeros((F, leafi_cnn_params(C_)), np.float32)
+    _check(lib().leafi_initial_cnn_weights(index, F, int(C_), seed, out.ctypes.data))
+    return out
 
 
 def leafi_debug_set_lock_tries(index, tries):

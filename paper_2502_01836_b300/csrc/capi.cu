@@ -267,7 +267,8 @@ bool encode_xh_map(leafi_index* ix) {
 // The tensor-core forward (3xTF32) serves indexes on the tensor-core scan path
 // whose hidden width fits one MMA (h <= 256); the CUDA-core forward the rest.
 bool filter_tc(const leafi_index* ix) {
-  return ix->scan_path == 0 && ix->F > 0 && filter_tc_fits(ix->m, ix->h, ix->smem_optin);
+  return ix->model == LEAFI_FILTER_MLP && ix->scan_path == 0 && ix->F > 0 &&
+         filter_tc_fits(ix->m, ix->h, ix->smem_optin);
 }
 
 // (re)build the tf32 weight planes after the weights changed
@@ -286,6 +287,10 @@ void ensure_wsplit(leafi_index* ix) {
 // scratch for later calls of up to that many queries
 void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_rows = 0) {
   if (nq <= 0 || ix->F <= 0) return;
+  if (ix->model == LEAFI_FILTER_CNN) {
+    launch_cnn_forward(dQ, nq, ix->mp, ix->m, ix->F, ix->h, ix->cnn.p, P, ix->stream);
+    return;
+  }
   if (!filter_tc(ix)) {
     launch_filter_forward(dQ, nq, ix->mp, ix->m, ix->F, ix->h, ix->W1t.p, ix->b1.p, ix->w2.p,
                           ix->b2.p, P, ix->stream);
@@ -404,8 +409,9 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
     t.topk = topk;
     t.glock = ix->sc->sGlock.need(nslots);
+    t.ub = kstride == 1 ? ix->sc->sUb.need(nslots) : nullptr;
     t.lock_tries = ix->lock_tries;
-    launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, s);
+    launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, t.ub, s);
     t.err = ix->sErr.p;
     t.stat = recheck_stat;
     t.prof = ix->profiling >= 2 ? ix->scan_prof.p : nullptr;
@@ -754,6 +760,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
       S.sPart.need(1);
       S.sWork.need(1);
       S.sGlock.need(qb);
+      S.sUb.need(qb);
       if (kmax > 1) {
         S.sNGroups.need(L);
         S.sGFirst.need(L + 1);
@@ -1589,10 +1596,12 @@ leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info) {
     r.n_kclasses = index->nk;
     for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) r.kclasses[i] = index->kclasses[i];
     r.device_bytes = (int64_t)(index->X.bytes() + index->Xh.bytes() + index->xn.bytes() +
-                               index->ids.bytes() + index->W1t.bytes());
+                               index->ids.bytes() + index->W1t.bytes() + index->cnn.bytes());
     r.tensor_scan = (index->tc_ok && index->scan_path == 0) ? 1 : 0;
     r.scan_row_bytes = r.tensor_scan ? index->kp * 2 : index->mp * 4;
     r.calib_confidence = index->calib_confidence;
+    r.filter_model = index->model;
+    r.filter_width = index->F ? index->h : 0;
     *info = r;
   });
 }
@@ -1713,15 +1722,26 @@ void select_auto_core(leafi_index* index, const leafi_select_params* params,
   // index uses (tensor cores when the width fits one MMA)
   const int Fp = 64;
   const int hp = (h + 15) / 16 * 16, Kq = (m + 31) / 32 * 32;
-  const bool tc = ix->scan_path == 0 && filter_tc_fits(m, h, ix->smem_optin);
-  DBuf<float> W1t, b1, w2, b2, P, Ws, Qs;
-  LF_CUDA(cudaMemsetAsync(W1t.need((size_t)Fp * m * h), 0, sizeof(float) * Fp * m * h, s));
-  LF_CUDA(cudaMemsetAsync(b1.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
-  LF_CUDA(cudaMemsetAsync(w2.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
-  LF_CUDA(cudaMemsetAsync(b2.need(Fp), 0, sizeof(float) * Fp, s));
+  const bool cnn = params->model == LEAFI_FILTER_CNN;
+  if (params->model != LEAFI_FILTER_MLP && !cnn) fail(LEAFI_EINVAL, "unknown filter model");
+  if (cnn && !cnn_fits(m, h, ix->smem_optin))
+    fail(LEAFI_EINVAL, "CNN filters of %d channels at m = %d exceed shared memory", h, m);
+  const bool tc = !cnn && ix->scan_path == 0 && filter_tc_fits(m, h, ix->smem_optin);
+  DBuf<float> W1t, b1, w2, b2, P, Ws, Qs, theta;
   P.need((size_t)nq * Fp);
   double t_f = 0.0;
-  if (tc) {
+  if (cnn) {
+    const size_t np = (size_t)Fp * cnn_params(h);
+    LF_CUDA(cudaMemsetAsync(theta.need(np), 0, sizeof(float) * np, s));
+  } else {
+    LF_CUDA(cudaMemsetAsync(W1t.need((size_t)Fp * m * h), 0, sizeof(float) * Fp * m * h, s));
+    LF_CUDA(cudaMemsetAsync(b1.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
+    LF_CUDA(cudaMemsetAsync(w2.need((size_t)Fp * h), 0, sizeof(float) * Fp * h, s));
+    LF_CUDA(cudaMemsetAsync(b2.need(Fp), 0, sizeof(float) * Fp, s));
+  }
+  if (cnn) {
+    t_f = timed([&] { launch_cnn_forward(dQ, nq, mp, m, Fp, h, theta.p, P.p, s); }, 3);
+  } else if (tc) {
     launch_wsplit(W1t.p, Fp, m, h, Ws.need((size_t)2 * Fp * hp * Kq), s);
     CUtensorMap wm, qm;
     const int nqp = (nq + 127) / 128 * 128;
@@ -1753,8 +1773,9 @@ void select_auto_core(leafi_index* index, const leafi_select_params* params,
   double t_s = timed([&] { leaf_knn_device(ix, dQ, nq, dl.p, 1, 1, keys, cnt); }, 5);
   t_s /= (double)nq * (double)bigsz;
   const double th = params->a * t_f / t_s;
-  const double w = (double)((size_t)h * m + 2 * (size_t)h + 1) * 4.0 +
-                   (tc ? 2.0 * hp * Kq * 4.0 : 0.0) + 300.0 * 8.0;
+  const double w = cnn ? (double)cnn_params(h) * 4.0 + 300.0 * 8.0
+                      : (double)((size_t)h * m + 2 * (size_t)h + 1) * 4.0 +
+                            (tc ? 2.0 * hp * Kq * 4.0 : 0.0) + 300.0 * 8.0;
   std::vector<int32_t> idx(t.n_leaves);
   std::iota(idx.begin(), idx.end(), 0);
   std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
@@ -1794,15 +1815,21 @@ leafi_status leafi_select_leaves_auto(leafi_index* index, const leafi_select_par
 namespace leafi {
 namespace {
 
-// installs filters on the leaves fl (host) with hidden width h: validates the
-// leaves, sizes the weight buffers (contents left to the caller), uploads the
-// leaf <-> filter tables and clears training and auto-tuner state.  The caller
-// holds the index mutex with the device current.
-void install_filters(leafi_index* index, const std::vector<int32_t>& fl, int h) {
+// installs filters of `model` on the leaves fl (host) with hidden width (MLP)
+// or channel count (CNN) h: validates the leaves, sizes the weight buffers
+// (contents left to the caller), uploads the leaf <-> filter tables and clears
+// training and auto-tuner state.  The caller holds the index mutex with the
+// device current.
+void install_filters(leafi_index* index, const std::vector<int32_t>& fl, int h,
+                     int model = LEAFI_FILTER_MLP) {
   const int F = (int)fl.size();
   if (F < 1 || F > index->tree.n_leaves) fail(LEAFI_EINVAL, "F out of range");
   if (h < 1 || h > 4096) fail(LEAFI_EINVAL, "h out of range");
   if (index->m > 1024) fail(LEAFI_EINVAL, "filters support m <= 1024");
+  if (model != LEAFI_FILTER_MLP && model != LEAFI_FILTER_CNN)
+    fail(LEAFI_EINVAL, "unknown filter model %d", model);
+  if (model == LEAFI_FILTER_CNN && !cnn_fits(index->m, h, index->smem_optin))
+    fail(LEAFI_EINVAL, "CNN filters of %d channels at m = %d exceed shared memory", h, index->m);
   std::vector<int32_t> leaf_filter(index->tree.n_leaves, -1);
   for (int f = 0; f < F; ++f) {
     if (fl[f] < 0 || fl[f] >= index->tree.n_leaves) fail(LEAFI_EINVAL, "filter leaf out of range");
@@ -1812,16 +1839,21 @@ void install_filters(leafi_index* index, const std::vector<int32_t>& fl, int h) 
   index->drop_graphs();
   cudaStream_t s = index->stream;
   const int m = index->m;
-  index->W1t.need((size_t)F * m * h);
-  index->b1.need((size_t)F * h);
-  index->w2.need((size_t)F * h);
-  index->b2.need(F);
+  if (model == LEAFI_FILTER_CNN) {
+    index->cnn.need((size_t)F * cnn_params(h));
+  } else {
+    index->W1t.need((size_t)F * m * h);
+    index->b1.need((size_t)F * h);
+    index->w2.need((size_t)F * h);
+    index->b2.need(F);
+  }
   index->d_filter_leaf.upload(fl, s);
   index->d_leaf_filter.upload(leaf_filter, s);
   LF_CUDA(cudaStreamSynchronize(s));
   index->filter_leaf = fl;
   index->F = F;
   index->h = h;
+  index->model = model;
   index->ws_dirty = true;
   index->trained = false;
   index->nc = 0;
@@ -1862,6 +1894,57 @@ leafi_status leafi_set_filters(leafi_index* index, const int32_t* filter_leaf, i
   });
 }
 
+int64_t leafi_cnn_params(int32_t C) { return C >= 1 ? cnn_params(C) : 0; }
+
+leafi_status leafi_set_cnn_filters(leafi_index* index, const int32_t* filter_leaf, int32_t F,
+                                   int32_t C, const float* theta) {
+  return guarded([&] {
+    require_device(index);
+    if (F < 1 || F > index->tree.n_leaves) fail(LEAFI_EINVAL, "F out of range");
+    if (!filter_leaf || !theta) fail(LEAFI_EINVAL, "NULL filter argument");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    cudaStream_t s = index->stream;
+    std::vector<int32_t> fl;
+    to_host(fl, filter_leaf, F, s);
+    install_filters(index, fl, C, LEAFI_FILTER_CNN);
+    const size_t n = (size_t)F * cnn_params(C);
+    DBuf<float> tmp;
+    const float* d = to_device(theta, n, tmp, s);
+    LF_CUDA(cudaMemcpyAsync(index->cnn.p, d, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    LF_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+leafi_status leafi_get_cnn_filters(leafi_index* index, float* theta) {
+  return guarded([&] {
+    require_device(index);
+    if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
+    if (!theta) fail(LEAFI_EINVAL, "NULL output");
+    if (index->model != LEAFI_FILTER_CNN) fail(LEAFI_EINVAL, "the filters are not CNNs");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    deliver(theta, index->cnn.p, (size_t)index->F * cnn_params(index->h), index->stream);
+    LF_CUDA(cudaStreamSynchronize(index->stream));
+  });
+}
+
+leafi_status leafi_initial_cnn_weights(leafi_index* index, int32_t F, int32_t C, uint64_t seed,
+                                       float* theta) {
+  return guarded([&] {
+    require_device(index);
+    if (F < 1 || C < 1 || C > 4096) fail(LEAFI_EINVAL, "F / C out of range");
+    if (!theta) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    DBuf<float> t;
+    const size_t n = (size_t)F * cnn_params(C);
+    launch_gen_cnn_weights(F, C, seed, t.need(n), index->stream);
+    deliver(theta, t.p, n, index->stream);
+    LF_CUDA(cudaStreamSynchronize(index->stream));
+  });
+}
+
 leafi_status leafi_get_filter_leaves(const leafi_index* index, int32_t* filter_leaf) {
   return guarded([&] {
     require_device(index);
@@ -1876,6 +1959,7 @@ leafi_status leafi_get_filters(leafi_index* index, float* W1, float* b1, float* 
     require_device(index);
     if (index->F == 0) fail(LEAFI_ENOTTRAINED, "no filters installed");
     if (!W1 || !b1 || !w2 || !b2) fail(LEAFI_EINVAL, "NULL output");
+    if (index->model != LEAFI_FILTER_MLP) fail(LEAFI_EINVAL, "the filters are not MLPs");
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
     cudaStream_t s = index->stream;
@@ -2014,6 +2098,23 @@ leafi_status leafi_train_targets(leafi_index* index, const float* Qg, int64_t ng
 namespace leafi {
 namespace {
 
+// after a training launch: per-filter statistics to the host, state flags
+void finish_training(leafi_index* index, int F, const int32_t* d_ep, const double* d_bv,
+                     int32_t* epochs_run, double* best_val) {
+  cudaStream_t s = index->stream;
+  index->ws_dirty = true;
+  std::vector<int32_t> hep(F);
+  std::vector<double> hbv(F);
+  LF_CUDA(cudaMemcpyAsync(hep.data(), d_ep, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaMemcpyAsync(hbv.data(), d_bv, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
+  LF_CUDA(cudaStreamSynchronize(s));
+  if (epochs_run) std::memcpy(epochs_run, hep.data(), sizeof(int32_t) * F);
+  if (best_val) std::memcpy(best_val, hbv.data(), sizeof(double) * F);
+  index->trained = true;
+  index->nc = 0;
+  index->nk = 0;
+}
+
 // Alg. 1 lines 3-9 on staged queries: targets of Qg [ng][mp] and Ql
 // [F][nl][mp] on the device, then SGD of every filter from its installed
 // weights with one shuffle per epoch (hperm [max_epochs][n_gtrain + n_ltrain]).
@@ -2034,8 +2135,6 @@ void train_core(leafi_index* index, const leafi_sgd_params* p, const float* dQg,
   DBuf<int32_t> dperm;
   dperm.upload(hperm, s);
   DBuf<float> bW, bb1, bw2, bb2;
-  DBuf<int32_t> dep;
-  DBuf<double> dbv;
   // number of lr divisions before stopping: the last one keeping lr >= lr_min
   int max_decays = 0;
   {
@@ -2045,6 +2144,39 @@ void train_core(leafi_index* index, const leafi_sgd_params* p, const float* dQg,
       if (lr < p->lr_min * (1.0 - 1e-9)) break;
       ++max_decays;
     }
+  }
+  DBuf<int32_t> dep;
+  DBuf<double> dbv;
+  if (index->model == LEAFI_FILTER_CNN) {
+    DBuf<float> bt, gr;
+    const size_t np = (size_t)F * cnn_params(h);
+    CnnTrainArgs c;
+    c.F = F;
+    c.C = h;
+    c.m = m;
+    c.mp = index->mp;
+    c.n_gtrain = p->n_gtrain;
+    c.n_gval = p->n_gval;
+    c.n_ltrain = p->n_ltrain;
+    c.n_lval = p->n_lval;
+    c.batch = p->batch;
+    c.max_epochs = p->max_epochs;
+    c.patience = p->patience;
+    c.max_decays = max_decays;
+    c.lr0 = (float)p->lr0;
+    c.Qg = dQg;
+    c.Ql = dQl;
+    c.Tg = dTg;
+    c.Tl = dTl;
+    c.perms = dperm.p;
+    c.theta = index->cnn.p;
+    c.btheta = bt.need(np);
+    c.grad = gr.need(np);
+    c.epochs_run = dep.need(F);
+    c.best_val = dbv.need(F);
+    launch_cnn_train(c, s);
+    finish_training(index, F, c.epochs_run, c.best_val, epochs_run, best_val);
+    return;
   }
   TrainArgs a;
   a.F = F;
@@ -2076,17 +2208,7 @@ void train_core(leafi_index* index, const leafi_sgd_params* p, const float* dQg,
   a.epochs_run = dep.need(F);
   a.best_val = dbv.need(F);
   launch_train(a, s);
-  index->ws_dirty = true;
-  std::vector<int32_t> hep(F);
-  std::vector<double> hbv(F);
-  LF_CUDA(cudaMemcpyAsync(hep.data(), a.epochs_run, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
-  LF_CUDA(cudaMemcpyAsync(hbv.data(), a.best_val, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
-  LF_CUDA(cudaStreamSynchronize(s));
-  if (epochs_run) std::memcpy(epochs_run, hep.data(), sizeof(int32_t) * F);
-  if (best_val) std::memcpy(best_val, hbv.data(), sizeof(double) * F);
-  index->trained = true;
-  index->nc = 0;
-  index->nk = 0;
+  finish_training(index, F, a.epochs_run, a.best_val, epochs_run, best_val);
 }
 
 void check_sgd_params(const leafi_sgd_params* p) {
@@ -2417,6 +2539,10 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     if (p->n_filters == 0 || p->n_filters < -1 || p->n_filters > L)
       fail(LEAFI_EINVAL, "n_filters must be -1 or in [1, %d]", L);
     const int h = p->hidden > 0 ? p->hidden : index->m;
+    if (p->model != LEAFI_FILTER_MLP && p->model != LEAFI_FILTER_CNN)
+      fail(LEAFI_EINVAL, "unknown filter model %d", p->model);
+    if (p->model == LEAFI_FILTER_CNN && !cnn_fits(index->m, h, index->smem_optin))
+      fail(LEAFI_EINVAL, "CNN filters of %d channels at m = %d exceed shared memory", h, index->m);
     std::lock_guard<std::mutex> lk(index->mu);
     DeviceGuard dg(index->device);
     cudaStream_t s = index->stream;
@@ -2434,7 +2560,7 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
       fl.assign(idx.begin(), idx.begin() + p->n_filters);
     } else {
       if (!(p->a > 0.0) || p->mem_cap < 0) fail(LEAFI_EINVAL, "bad Alg. 3 parameters");
-      leafi_select_params sel{p->a, p->mem_cap, h};
+      leafi_select_params sel{p->a, p->mem_cap, h, p->model};
       leafi_select_report sr{};
       std::vector<int32_t> all(L);
       select_auto_core(index, &sel, all.data(), &sr);
@@ -2444,10 +2570,13 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     }
     rep.seconds_select = seconds_since(t0);
     t0 = std::chrono::steady_clock::now();
-    install_filters(index, fl, h);
+    install_filters(index, fl, h, p->model);
     const int F = (int)fl.size();
-    launch_gen_weights(F, h, index->m, p->seed, index->W1t.p, index->b1.p, index->w2.p,
-                       index->b2.p, s);
+    if (p->model == LEAFI_FILTER_CNN)
+      launch_gen_cnn_weights(F, h, p->seed, index->cnn.p, s);
+    else
+      launch_gen_weights(F, h, index->m, p->seed, index->W1t.p, index->b1.p, index->w2.p,
+                         index->b2.p, s);
     // lines 2 and 6: GenerateGlobalQueries / GenerateLocalQueries
     DBuf<float> Q;
     generate_training_queries(index, p, c, fl, Q, nullptr, nullptr);

@@ -144,7 +144,7 @@ void launch_filter_forward(const float* Q, int nq, int mp, int m, int F, int h, 
 // stream) under the key (seed low, seed high)
 enum : uint32_t {
   kTagGPick = 1, kTagLPick = 2, kTagSigma = 3, kTagNoise = 4, kTagW1 = 5, kTagB1 = 6,
-  kTagW2 = 7, kTagB2 = 8, kTagPerm = 9
+  kTagW2 = 7, kTagB2 = 8, kTagPerm = 9, kTagCnn = 10
 };
 // k distinct values of [0, n) by Floyd's algorithm, in insertion order
 void gen_floyd(uint64_t seed, uint32_t tag, uint32_t stream, uint64_t n, int64_t k, int64_t* out);
@@ -173,6 +173,26 @@ struct TrainArgs {
   double* best_val;
 };
 void launch_train(const TrainArgs& a, cudaStream_t s);
+
+// CNN filters (k_cnn.cu): flat parameters [F][cnn_params(C)]
+struct CnnTrainArgs {
+  int F, C, m, mp;
+  int n_gtrain, n_gval, n_ltrain, n_lval, batch, max_epochs, patience, max_decays;
+  float lr0;
+  const float *Qg, *Ql, *Tg, *Tl;
+  const int32_t* perms;
+  float* theta;   // trained in place
+  float* btheta;  // best-validation copy
+  float* grad;    // minibatch gradient accumulators
+  int32_t* epochs_run;
+  double* best_val;
+};
+int64_t cnn_params(int C);
+bool cnn_fits(int m, int C, int smem_optin);
+void launch_cnn_forward(const float* Q, int nq, int mp, int m, int F, int C, const float* theta,
+                        float* out, cudaStream_t s);
+void launch_cnn_train(const CnnTrainArgs& a, cudaStream_t s);
+void launch_gen_cnn_weights(int F, int C, uint64_t seed, float* theta, cudaStream_t s);
 
 struct ScanArgs {
   const float* X;        // [n][mp] leaf-major
@@ -219,6 +239,9 @@ struct TcScanArgs {
   unsigned long long* topk;        // [nslots][k] ascending keys, kNoKey padded
                                    // (launch_tc_round_prep); work items merge into it
   int32_t* glock;                  // per slot lock of its list (zero at the round's start)
+  float* ub;                       // k = 1: per slot upper bound of the best canonical distance
+                                   // over the rows scanned so far in the round (+inf at its
+                                   // start), shared by the work items; null for k > 1
   int lock_tries;                  // attempts at a slot's lock before the item reports a timeout
   int32_t* err;
   unsigned long long* stat;        // nullable: [0] += canonical re-checks
@@ -240,7 +263,7 @@ void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t*
 // kNoKey and release the slot locks; after it: count the list entries and
 // set each slot's threshold (its k-th key, kNoKey while fewer than k)
 void launch_tc_round_prep(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
-                          const int32_t* topk_cnt, int32_t* glock, cudaStream_t s);
+                          const int32_t* topk_cnt, int32_t* glock, float* ub, cudaStream_t s);
 void launch_tc_round_finish(int nslots, int kstride, const int32_t* slot_k,
                             const unsigned long long* topk, int32_t* topk_cnt,
                             unsigned long long* thr, cudaStream_t s);
@@ -377,6 +400,7 @@ struct Scratch {
   DBuf<Pair> sPairs, sGrouped;
   DBuf<unsigned long long> sTopk, sThr, sCand;
   DBuf<int32_t> sGlock;           // per slot locks of the tensor-core scan's top-k lists
+  DBuf<float> sUb;                // k = 1: per slot upper bounds shared by a round's work items
   DBuf<int32_t> sPart;            // the round's work-item rows (chosen by the grouping kernels)
   DBuf<int32_t> sNGroups, sGFirst, sGBound;  // k > 1: query groups sized by k (launch_var_groups)
   DBuf<float> sPred, sOutD;
@@ -429,11 +453,13 @@ struct leafi_index {
   leafi::DBuf<int32_t> root_child, isplit, node_bits, lo_sym, hi_sym;
 
   // filters
-  int F = 0, h = 0;
+  int F = 0, h = 0;                    // h: MLP hidden width, or CNN channels C
+  int model = LEAFI_FILTER_MLP;
   bool trained = false;
   std::vector<int32_t> filter_leaf;
   leafi::DBuf<int32_t> d_filter_leaf, d_leaf_filter;
-  leafi::DBuf<float> W1t, b1, w2, b2;  // W1t [F][m][h]
+  leafi::DBuf<float> W1t, b1, w2, b2;  // MLP: W1t [F][m][h]
+  leafi::DBuf<float> cnn;              // CNN: [F][cnn_params(h)]
 
   // auto-tuners
   int nc = 0, nk = 0;

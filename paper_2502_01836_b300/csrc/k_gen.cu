@@ -193,6 +193,22 @@ __global__ void gen_weights_kernel(int F, int h, int m, uint64_t seed, float* __
   }
 }
 
+// CNN filters' initial parameters (flat layout w1, b1, w2, b2, wo, bo):
+// U(-a, a) with a = 1/sqrt(fan in), fan in 3 (w1, b1), 3C (w2, b2), C (wo, bo)
+__global__ void gen_cnn_weights_kernel(int F, int C, int64_t P, uint64_t seed,
+                                       float* __restrict__ theta) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P * F) return;
+  const int f = (int)(t / P);
+  const int64_t e = t % P;
+  const int64_t e_w2 = 4 * (int64_t)C, e_wo = e_w2 + 3 * (int64_t)C * C + C;
+  const double a = e < e_w2 ? 1.0 / sqrt(3.0)
+                            : (e < e_wo ? 1.0 / sqrt(3.0 * (double)C) : 1.0 / sqrt((double)C));
+  uint32_t w[4];
+  gen_draw(seed, (uint32_t)e, (uint32_t)f, kTagCnn, 0, w);
+  theta[t] = (float)__dmul_rn(__dsub_rn(__dmul_rn(2.0, gen_unit(w[0], w[1])), 1.0), a);
+}
+
 // float64 z-normalisation of rows of m floats (row strides in / out), one warp
 // per row, two passes; sigma < 1e-8 gives zeros
 __global__ void znorm_kernel(const float* __restrict__ in, int64_t in_stride, int64_t n, int m,
@@ -233,6 +249,13 @@ void launch_gen_weights(int F, int h, int m, uint64_t seed, float* W1t, float* b
                         float* b2, cudaStream_t s) {
   const int64_t n = (int64_t)F * h * m;
   gen_weights_kernel<<<grid_for(n, 256), 256, 0, s>>>(F, h, m, seed, W1t, b1, w2, b2);
+  LF_CHECK_LAUNCH();
+}
+
+void launch_gen_cnn_weights(int F, int C, uint64_t seed, float* theta, cudaStream_t s) {
+  const int64_t P = cnn_params(C), n = P * F;
+  if (n <= 0) return;
+  gen_cnn_weights_kernel<<<grid_for(n, 256), 256, 0, s>>>(F, C, P, seed, theta);
   LF_CHECK_LAUNCH();
 }
 

@@ -729,7 +729,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           S.kq[qq] = kqs;
           S.thr[qq] = th;
           S.thrd[qq] = thd;
-          S.H[qq] = thd;
+          // k = 1: the round's shared upper bound of the query's best distance
+          S.H[qq] = (split && a.ub) ? fminf(thd, __ldcg(&a.ub[slot])) : thd;
           S.cnt[qq] = 0;
           S.cnt4[0][qq] = S.cnt4[1][qq] = S.cnt4[2][qq] = S.cnt4[3][qq] = 0;
           S.Tq[qq] = thd;
@@ -776,6 +777,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         const int64_t pos = I.p0 + (int64_t)c * kTcRows + r;
         const bool valid = pos < I.p1;
         const float xn = valid ? a.xn[pos] : 0.0f;
+        // k = 1: bounds other work items of the round have published since
+        // the item started (thread r refreshes query column r)
+        const float ubr = (split && a.ub && r < nqg) ? __ldcg(&a.ub[S.slot[r]]) : kInf;
         // on a timeout every later wait returns at once; the loop still reaches
         // all arrivals and barriers, and the error word reports the failure
         const bool ok = wait_phase(&S.tfull[t], tfull_ph[t], abort);
@@ -785,6 +789,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           S.abort = 1;
         }
         PROF_ADD(1);
+        if (ubr < S.H[r]) atomic_min_float_nonneg(&S.H[r], ubr);
         const bool okw = __all_sync(0xffffffffu, ok);  // warp-uniform for tcgen05.ld
         dev::tc_fence_after();
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kTcG);
@@ -843,11 +848,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
                   if (lov[jj] > hm) cand &= ~(1u << jj);
                 }
               }
-              // a tighter upper bound is rare once the part is under way
+              // a tighter upper bound is rare once the part is under way; it
+              // is published to the round's other work items as well
               if (lane == 0 && lower) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj)
-                  if (lower & (1u << jj)) atomic_min_float_nonneg(&S.H[c0 + jj], T[jj]);
+                  if (lower & (1u << jj)) {
+                    atomic_min_float_nonneg(&S.H[c0 + jj], T[jj]);
+                    if (a.ub) atomic_min_float_nonneg(&a.ub[S.slot[c0 + jj]], T[jj]);
+                  }
               }
             }
             if (__any_sync(0xffffffffu, cand != 0u)) {
@@ -982,6 +991,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         dev::tc_fence_before();
         mbar_arrive(&S.tempty[t]);
         PROF_ADD(2);
+      }
+      if (split && a.ub && tid < nqg) {
+        const float u = __ldcg(&a.ub[S.slot[tid]]);
+        if (u < S.H[tid]) atomic_min_float_nonneg(&S.H[tid], u);
       }
       epi_sync();
       if (split) {
@@ -1132,12 +1145,15 @@ int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem, int* qkeys) {
 namespace {
 __global__ void round_prep_kernel(int nslots, int kstride, const int32_t* __restrict__ slot_k,
                                   u64* __restrict__ topk, const int32_t* __restrict__ topk_cnt,
-                                  int32_t* __restrict__ glock) {
+                                  int32_t* __restrict__ glock, float* __restrict__ ub) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nslots * kstride) return;
   const int slot = (int)(t / kstride), z = (int)(t % kstride);
   if (z >= topk_cnt[slot]) topk[t] = kNoKey;
-  if (z == 0) glock[slot] = 0;
+  if (z == 0) {
+    glock[slot] = 0;
+    if (ub) ub[slot] = __int_as_float(0x7f800000);
+  }
   (void)slot_k;
 }
 
@@ -1160,11 +1176,11 @@ __global__ void round_finish_kernel(int nslots, int kstride, const int32_t* __re
 }  // namespace
 
 void launch_tc_round_prep(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
-                          const int32_t* topk_cnt, int32_t* glock, cudaStream_t s) {
+                          const int32_t* topk_cnt, int32_t* glock, float* ub, cudaStream_t s) {
   const int64_t tot = (int64_t)nslots * kstride;
   if (tot == 0) return;
   round_prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nslots, kstride, slot_k, topk,
-                                                                   topk_cnt, glock);
+                                                                   topk_cnt, glock, ub);
   LF_CHECK_LAUNCH();
 }
 

@@ -4,8 +4,11 @@ Bars: exact-mode ids bit-exact with ties on the lowest id, distances bit-exact
 (both sides use the canonical float32 distance); lower bounds and routes
 bit-exact (both sides evaluate the same float64 operations); filter
 predictions within 1e-5 of the float64 forward, scaled by |b2| + sum_j
-|w2_j| relu(z_j); LeaFi-mode results equal except where a filter decision lies
-within the prediction tolerance of the best-so-far.
+|w2_j| relu(z_j); Alg. 4 tables and LeaFi-mode results bit-exact (scanned
+leaves and series included) when the oracle takes the GPU's own predictions;
+against the oracle's own float64 predictions, LeaFi-mode results equal except
+for queries with a filter decision within the prediction tolerance (each
+query's own scale) of the best-so-far.
 """
 import numpy as np
 import pytest
@@ -221,6 +224,57 @@ def test_autotuner_matches_oracle(ds, tuned):
         assert (diff == 0).mean() >= 0.9 and diff.max() <= 3.0 / nc, (k, diff.max())
 
 
+def test_autotuner_bit_exact_on_gpu_predictions(ds, tuned):
+    """Alg. 4 on the GPU equals the oracle's Alg. 4 fed the GPU's predictions:
+    alpha and every q' position, for both k-classes."""
+    X, Q, idx, t = ds
+    fl, Wt, Qc, _ = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_fit_autotuners(idx, Qc, [1, 10])
+    F, nc = Wt[0].shape[0], Qc.shape[0]
+    alpha = np.zeros((F, nc))
+    qp = np.zeros((2, nc))
+    lf.leafi_get_autotuners(idx, alpha, qp)
+    Pc = np.zeros((nc, F), np.float32)
+    lf.leafi_filter_predict(idx, Qc, Pc)
+    for i, k in enumerate((1, 10)):
+        a_ref, q_ref = O.fit_autotuner_pred(t, Pc.astype(np.float64), fl, Qc, k, 4)
+        assert np.array_equal(alpha, a_ref)
+        assert np.array_equal(qp[i], q_ref), k
+
+
+@pytest.mark.parametrize("k,target", [(1, 0.99), (1, 0.9), (10, 0.95)])
+def test_leafi_search_bit_exact_on_gpu_predictions(ds, tuned, k, target):
+    """Alg. 2 with filters on the GPU equals the oracle's fed the GPU's
+    predictions and tables: ids, distances, scanned leaves and series."""
+    X, Q, idx, t = ds
+    fl, Wt, Qc, _ = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_fit_autotuners(idx, Qc, [1, 10])
+    F, nc = Wt[0].shape[0], Qc.shape[0]
+    alpha = np.zeros((F, nc))
+    qp = np.zeros((2, nc))
+    lf.leafi_get_autotuners(idx, alpha, qp)
+    P = np.zeros((NQ, F), np.float32)
+    lf.leafi_filter_predict(idx, Q, P)
+    lf.leafi_set_calibration_confidence(idx, 0.0)
+    try:
+        ids = np.zeros((NQ, k), np.int64)
+        d = np.zeros((NQ, k), np.float32)
+        st = lf.SearchStats()
+        lf.leafi_search(idx, Q, k, target, ids, d, st)
+    finally:
+        lf.leafi_set_calibration_confidence(idx, 0.95)
+    j = O.offset_position(qp[0 if k == 1 else 1], target, kk=k, confidence=0.0)
+    o_ids, o_d2, o_st, _ = O.leafi_search_pred(t, P.astype(np.float64), fl, alpha, Q, k, j, 4)
+    assert np.array_equal(ids, o_ids)
+    assert np.array_equal(d, np.sqrt(o_d2))
+    assert st.leaves_scanned == o_st[:, 0].sum()
+    assert st.series_scanned == o_st[:, 1].sum()
+    if j >= 0:
+        assert o_st[:, 3].sum() > 0     # some filter pruned a leaf: the comparison covers it
+
+
 @pytest.mark.parametrize("k,target", [(1, 0.99), (1, 0.9), (10, 0.95)])
 def test_leafi_search_matches_oracle(ds, tuned, k, target):
     X, Q, idx, t = ds
@@ -239,7 +293,7 @@ def test_leafi_search_matches_oracle(ds, tuned, k, target):
     lf.leafi_set_calibration_confidence(idx, 0.95)
     j = O.offset_position(tables[k][1], target, kk=k, confidence=0.0)
     o_ids, o_d2, o_st, margin = O.leafi_search(t, Wt, fl, alpha, Q, k, j, 4)
-    tol = 2e-5 * _pred_scale(Wt, Q).max()
+    tol = 2e-5 * _pred_scale(Wt, Q).max(axis=1)
     same = (ids == o_ids).all(1)
     assert (same | (margin <= tol)).all()
     assert same.mean() >= 0.95
@@ -269,7 +323,7 @@ def test_search_mixed_matches_oracle(ds, tuned):
         if conf == 0.0:
             assert (jpos >= 0).sum() >= NQ // 4      # the filters are in play
         o_ids, o_d2, _, margin = O.leafi_search(t, Wt, fl, alpha, Q, kq, jpos, 4, kmax=20)
-        tol = 2e-5 * _pred_scale(Wt, Q).max()
+        tol = 2e-5 * _pred_scale(Wt, Q).max(axis=1)
         same = (ids == o_ids).all(1)
         assert (same | (margin <= tol)).all()
         # exact queries (target 1 or k above every class) always agree

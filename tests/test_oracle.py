@@ -587,3 +587,131 @@ def test_select_leaves_alg3_pins():
     sz = rng.integers(1, 50, 200)
     order = sorted(range(200), key=lambda i: (-sz[i], i))
     assert list(O.select_leaves_alg3(sz, 0, 3.0, 3.0 * 17)) == order[:17]
+
+
+# ---------------------------------------------------------------- CNN filters (Sec. 5.2)
+
+def _cnn_theta(C, m, w1, b1, w2, b2, wo, bo):
+    """Pack per-layer arrays into the flat layout w1, b1, w2, b2, wo, bo."""
+    th = np.concatenate([np.asarray(w1, np.float32).ravel(), np.asarray(b1, np.float32).ravel(),
+                         np.asarray(w2, np.float32).ravel(), np.asarray(b2, np.float32).ravel(),
+                         np.asarray(wo, np.float32).ravel(), np.float32([bo])])
+    assert th.size == O.cnn_params(C) == 3 * C * C + 6 * C + 1
+    return th[None]
+
+
+@pytest.mark.parametrize("tap", [0, 2])
+def test_cnn_forward_hand_weights(tap):
+    """Two channels: the first layer passes relu(x) and relu(-x); the second
+    sums them (|x|) on channel 0 and shifts relu(x) by one position on channel
+    1 (tap 0 meets position i - 1, tap 2 position i + 1; zero padding drops the
+    series' last / first value).  With wo = (1, 2), bo = 0.5 and mean pooling:
+        y = 0.5 + mean|x| + 2 (sum of relu(x) over the kept positions) / m."""
+    C, m = 2, 5
+    w1 = [[0, 1, 0], [0, -1, 0]]
+    b1 = [0, 0]
+    w2 = np.zeros((2, 2, 3), np.float32)
+    w2[0, 0, 1] = w2[0, 1, 1] = 1.0
+    w2[1, 0, tap] = 1.0
+    th = _cnn_theta(C, m, w1, b1, w2, [0, 0], [1, 2], 0.5)
+    x = np.array([[1.5, -2.0, 3.0, -0.5, 0.25]], np.float32)
+    x64 = x.astype(np.float64)
+    kept = x64[0, :-1] if tap == 0 else x64[0, 1:]
+    want = 0.5 + np.abs(x64).sum() / m + 2 * np.maximum(kept, 0).sum() / m
+    assert O.cnn_forward(th, C, x)[0, 0] == pytest.approx(want, abs=1e-15)
+    # biases: b1 = -1 cuts both channels (|x| > 1 survives on channel 0 only
+    # through relu(x - 1) + relu(-x - 1)); b2 = -10 silences channel 1
+    th2 = _cnn_theta(C, m, w1, [-1, -1], w2, [0, -10], [1, 2], 0.5)
+    want2 = 0.5 + (np.maximum(x64 - 1, 0) + np.maximum(-x64 - 1, 0)).sum() / m
+    assert O.cnn_forward(th2, C, x)[0, 0] == pytest.approx(want2, abs=1e-15)
+
+
+def test_cnn_sgd_step_matches_finite_difference_gradient():
+    """One full-batch SGD step moves every CNN parameter by -lr dLoss/dtheta,
+    the loss (the minibatch MSE) evaluated through the oracle forward that the
+    hand-weight test pins.  Parameters sit on a 2^-12 grid so theta +- 2^-12 is
+    exact in float32; along one parameter the prediction is piecewise linear
+    (ReLU kinks) and the loss piecewise quadratic, so the central difference is
+    exact up to rounding when no kink lies within the step (a coarser step,
+    2^-8, does meet kinks on these data and is off by up to 30%)."""
+    rng = np.random.default_rng(11)
+    C, m, n = 3, 7, 6
+    P = O.cnn_params(C)
+    th = (np.round(rng.uniform(-0.6, 0.6, (1, P)) * 4096) / 4096).astype(np.float32)
+    Qg = rng.standard_normal((n + 1, m)).astype(np.float32)
+    Tg = rng.uniform(0.5, 2.0, (n + 1, 1)).astype(np.float32)
+    Ql = np.zeros((1, 1, m), np.float32)
+    Tl = np.zeros((1, 1), np.float32)
+    lr = 0.0625
+    p = O.TrainParams(n_gtrain=n, n_gval=1, n_ltrain=0, n_lval=0, batch=n, max_epochs=1,
+                      patience=10, lr0=lr, lr_min=1e-5)
+    perms = np.arange(n, dtype=np.int32)[None]
+    th1, ep, _ = O.cnn_train(p, C, Qg, Tg, Ql, Tl, perms, th)
+    assert int(ep[0]) == 1
+
+    def loss(t):
+        y = O.cnn_forward(t, C, Qg[:n])[:, 0]
+        return np.mean((y - Tg[:n, 0].astype(np.float64)) ** 2)
+
+    eps = 2.0 ** -12
+    moved = th1[0].astype(np.float64) - th[0].astype(np.float64)
+    for e in range(P):
+        tp, tm = th.copy(), th.copy()
+        tp[0, e] += np.float32(eps)
+        tm[0, e] -= np.float32(eps)
+        g = (loss(tp) - loss(tm)) / (2 * eps)
+        assert moved[e] == pytest.approx(-lr * g, abs=2e-7, rel=1e-5), e
+
+
+@pytest.mark.parametrize("case", ["constant", "constant_capped", "halving", "one_step"])
+def test_cnn_sgd_plateau_schedule_hand_counted(case):
+    """The CNN trainer keeps the MLP trainer's protocol: with both convolutions
+    dead (b1 = b2 = -1, w1 = w2 = 0) the prediction is bo and only bo moves, so
+    the hand-counted epochs, best loss and kept bias of the MLP cases hold
+    (tests/golden/sgd_plateau_hand.json)."""
+    c = _golden("sgd_plateau_hand.json")["cases"][case]
+    C, m = 2, 2
+    Qg = np.array([[1, 2], [-1, 0.5], [0.25, -2], [3, 1]], np.float32)
+    Ql = np.array([[[2, 2], [-3, 1], [0, 1], [1, -1]]], np.float32)
+    Tg = np.array([[c["train_target"]]] * 2 + [[c["val_target"]]] * 2, np.float32)
+    Tl = np.array([[c["train_target"]] * 2 + [c["val_target"]] * 2], np.float32)
+    th = _cnn_theta(C, m, np.zeros((2, 3)), [-1, -1], np.zeros((2, 2, 3)), [-1, -1],
+                    [0.5, -0.25], c["b2"])
+    p = O.TrainParams(n_gtrain=2, n_gval=2, n_ltrain=2, n_lval=2, batch=4,
+                      max_epochs=c["max_epochs"], patience=c["patience"], lr0=c["lr0"],
+                      lr_min=c["lr_min"])
+    perms = np.tile(np.array([2, 0, 3, 1], np.int32), (c["max_epochs"], 1))
+    th1, ep, bv = O.cnn_train(p, C, Qg, Tg, Ql, Tl, perms, th)
+    assert int(ep[0]) == c["epochs"]
+    assert float(bv[0]) == c["best_val"]
+    assert float(th1[0, -1]) == np.float32(c["b2_kept"])
+    assert np.array_equal(th1[0, :-1], th[0, :-1])
+
+
+def test_cnn_init_bounds_and_determinism():
+    C = 24
+    th = O.cnn_init(3, C, seed=6)
+    a1, a2, ao = 1 / np.sqrt(3), 1 / np.sqrt(3 * C), 1 / np.sqrt(C)
+    w1b1, w2b2, wobo = th[:, :4 * C], th[:, 4 * C:4 * C + 3 * C * C + C], th[:, -(C + 1):]
+    assert np.abs(w1b1).max() <= a1 and np.abs(w2b2).max() <= a2 and np.abs(wobo).max() <= ao
+    assert np.abs(w1b1).max() > 0.9 * a1 and np.abs(w2b2).max() > 0.99 * a2
+    assert abs(w2b2.var() / (a2 * a2 / 3) - 1) < 0.05
+    assert np.array_equal(O.cnn_init(3, C, seed=6), th)
+    assert not np.array_equal(O.cnn_init(3, C, seed=7), th)
+
+
+def test_prediction_entry_points_equal_the_mlp_ones(small_index):
+    """Alg. 4 and Alg. 2 on given predictions are the MLP entry points with the
+    MLP's predictions (the CNN parity checks run through the former)."""
+    X, t, _ = small_index
+    Q = fx.test_queries(X, 80, seed=23)
+    fl = np.arange(min(4, t.L), dtype=np.int32)
+    W = O.filter_init(len(fl), 16, t.m, seed=2)
+    a1, q1 = O.fit_autotuner(t, W, fl, Q[:40], 1, 4)
+    a2, q2 = O.fit_autotuner_pred(t, O.mlp_forward(*W, Q[:40]), fl, Q[:40], 1, 4)
+    assert np.array_equal(a1, a2) and np.array_equal(q1, q2)
+    jp = np.full(len(Q) - 40, 10, np.int32)
+    r1 = O.leafi_search(t, W, fl, a1, Q[40:], 1, jp, 4)
+    r2 = O.leafi_search_pred(t, O.mlp_forward(*W, Q[40:]), fl, a1, Q[40:], 1, jp, 4)
+    for u, v in zip(r1, r2):
+        assert np.array_equal(u, v)
