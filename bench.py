@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="leafi", choices=["leafi", "reference"])
     ap.add_argument("--config", default="batched",
-                    choices=["batched", "serving", "mixed", "precision", "ablation"])
+                    choices=["batched", "serving", "mixed", "precision", "ablation", "cnn"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--queries", type=int, default=10_000)
     ap.add_argument("--launch", type=int, default=256)
@@ -95,6 +95,7 @@ def parse():
                     help="thread blocks per tensor-core scan launch (0: one per SM)")
     a = ap.parse_args()
     dflt = {"batched": (1_000_000, 10_000, 100), "ablation": (1_000_000, 10_000, 100),
+            "cnn": (1_000_000, 10_000, 100),
             "serving": (50_000_000, 10_000, 1000),
             "mixed": (25_000_000, 20_000, 1000), "precision": (10_000_000, 10_000, 0)}[a.config]
     a.n = a.n if a.n is not None else dflt[0]
@@ -500,9 +501,10 @@ def run_mixed(a):
 
 
 def run_precision(a):
-    """Embedding-like m = 96, k = 10 exact search: tensor-core (float16 products,
-    float32 re-check band) vs CUDA-core scan, error against float64; and the flat
-    contraction (one leaf holding every series) as the tensor-core case."""
+    """Embedding-like m = 96, k = 10 exact search: tensor-core scans (float16 or
+    e4m3 products with per-series scales, float32 re-check band) vs CUDA-core
+    scan, error against float64; and the flat contraction (one leaf holding
+    every series) as the tensor-core case."""
     torch, lf = _gpu_setup()
     m, k = 96, 10
     t0 = time.perf_counter()
@@ -512,7 +514,8 @@ def run_precision(a):
     Qd = torch.from_numpy(Q).cuda()
     out = {}
     res = {}
-    for name, path, cap in (("tensor_core", 0, a.leaf_cap), ("cuda_core", 1, a.leaf_cap)):
+    for name, path, cap in (("tensor_core", 0, a.leaf_cap), ("cuda_core", 1, a.leaf_cap),
+                            ("tensor_core_e4m3", 2, a.leaf_cap)):
         idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=cap, wave=a.wave, device=0,
                                                scan_path=path))
         ids = torch.zeros((a.queries, k), dtype=torch.int64, device="cuda")
@@ -534,7 +537,9 @@ def run_precision(a):
         res[name] = (ids.cpu().numpy(), dd.cpu().numpy())
         lf.leafi_free(idx)
     same = bool(np.array_equal(res["tensor_core"][0], res["cuda_core"][0]) and
-                np.array_equal(res["tensor_core"][1], res["cuda_core"][1]))
+                np.array_equal(res["tensor_core"][1], res["cuda_core"][1]) and
+                np.array_equal(res["tensor_core"][0], res["tensor_core_e4m3"][0]) and
+                np.array_equal(res["tensor_core"][1], res["tensor_core_e4m3"][1]))
     # float64 reference on a sample: expanded-form distances rank candidates,
     # the top 4k are re-ranked with direct float64 differences
     rng = np.random.default_rng(2503)
@@ -587,7 +592,7 @@ def run_precision(a):
     lf.leafi_free(idx)
     _emit({"metric": "precision path, k = 10: exact search queries/s and error against float64",
            "value": out["tensor_core"]["qps"], "unit": "queries/s", "paths": out,
-           "tensor_equals_cuda_core": same,
+           "all_paths_equal": same,
            "vs_float64": {"sample": len(smp), "max_rel_distance_error": max_rel,
                           "recall_at_10": float(np.mean(recall))},
            "flat_contraction": flat,
@@ -646,6 +651,64 @@ def run_ablation(a):
            "data": "synthetic"})
 
 
+def run_cnn(a):
+    """The model-type study (Sec. 5.2, Table 1): MLP and CNN filters (two k = 3
+    convolutions with C = m channels) on the embedding-like series of length 96
+    that stand in for Deep; for each model, Alg. 3's measured t^F and
+    threshold th, then filters on the a.filters largest leaves: training time,
+    queries/s, recall@1 and series scanned at the recall target, beside exact
+    search."""
+    torch, lf = _gpu_setup()
+    from paper_2502_01836_b300.workflow import enhance
+    m = 96
+    X = fx.embedding_like(a.n, m)
+    Q = fx.test_queries(X, a.queries)
+    Qd = torch.from_numpy(Q).cuda()
+    ids = torch.zeros((a.queries, 1), dtype=torch.int64, device="cuda")
+    dd = torch.zeros((a.queries, 1), dtype=torch.float32, device="cuda")
+
+    def timed(idx, target):
+        for _ in range(a.warmup):
+            lf.leafi_search(idx, Qd, 1, target, ids, dd)
+        st = lf.SearchStats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = max(1, a.steps // 3)
+        for _ in range(reps):
+            lf.leafi_search(idx, Qd, 1, target, ids, dd, st)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / reps
+        return a.queries / sec, ids[:, 0].cpu().numpy().copy(), st.series_scanned / a.queries / reps
+
+    bp = lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=0)
+    idx = lf.leafi_build(X, bp)
+    L = lf.leafi_get_info(idx).n_leaves
+    qps, exact, ser = timed(idx, 1.0)
+    rows = {"exact": {"qps": qps, "series_scanned_per_query": ser, "recall_at_1": 1.0}}
+    for name, model in (("MLP", lf.FILTER_MLP), ("CNN", lf.FILTER_CNN)):
+        sel, rep = lf.leafi_select_leaves_auto(idx, a=2.0, model=model)
+        t0 = time.perf_counter()
+        enh = enhance(idx, a.filters, max_epochs=a.epochs, tune_search=int(a.tune), model=model)
+        t_train = time.perf_counter() - t0
+        qps, got, ser = timed(idx, a.target)
+        rec = float(np.mean(got == exact))
+        rows[name] = {"alg3": {"t_filter_s": rep["t_filter_s"], "t_series_s": rep["t_series_s"],
+                               "threshold": rep["threshold"], "n_selected": rep["n_selected"]},
+                      "train_and_tune_s": t_train,
+                      "epochs_run_mean": float(np.mean(enh.epochs_run)),
+                      "qps": qps, "series_scanned_per_query": ser, "recall_at_1": rec,
+                      "meets_target": bool(rec >= a.target),
+                      "wave": lf.leafi_get_info(idx).wave}
+    lf.leafi_free(idx)
+    _emit({"metric": "filter model study: queries/s, recall@1 and Alg. 3 threshold, MLP vs CNN",
+           "unit": "queries/s", "value": rows["CNN"]["qps"], "rows": rows,
+           "config": {"workload": "DSTree over %d embedding-like series x %d (1,000 clusters, "
+                                  "std 0.3), leaf capacity %d (%d leaves), filters on the %d "
+                                  "largest leaves, %d queries, 1-NN, target %.2f"
+                                  % (a.n, m, a.leaf_cap, L, a.filters, a.queries, a.target)},
+           "data": "synthetic"})
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -653,7 +716,7 @@ def main():
         return
     if a.config != "batched":
         {"serving": run_serving, "mixed": run_mixed, "precision": run_precision,
-         "ablation": run_ablation}[a.config](a)
+         "ablation": run_ablation, "cnn": run_cnn}[a.config](a)
         return
     import torch
     rank, world, local, dist = dist_setup(a.gpus)

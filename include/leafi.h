@@ -73,7 +73,11 @@ typedef struct {
   int32_t scan_path;            /* 0: tensor-core scan (float16 dot products on tcgen05
                                    with a proven error band and a canonical float32
                                    re-check); 1: CUDA-core scan (canonical float32 for
-                                   every pair).  Both give identical results. */
+                                   every pair); 2: tensor-core scan on float8 e4m3
+                                   operands with a power-of-two scale per series and
+                                   per query (kind::f8f6f4; its band is about 140 times
+                                   wider than float16's, so far more pairs are
+                                   re-checked; m <= 256).  All give identical results. */
   int32_t host_build;           /* 0: the tree is built level by level on the GPU (the
                                    series in id order are copied to the device once);
                                    1: sequential insertion on the host.  Both give the

@@ -1,5 +1,7 @@
 // C ABI (include/leafi.h): argument checks, host/device staging, and the
 // search driver that runs the LeaFi path (Alg. 2) on the GPU in waves.
+#include <cuda_fp8.h>
+
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -214,6 +216,38 @@ __global__ void half_copy_kernel(const float* __restrict__ X, int64_t n, int mp,
   }
 }
 
+// e4m3 copy (rows of kp bytes, zero padded) with a power-of-two scale per
+// series (max |x_i| / sx <= 448, the largest finite e4m3 value) and the
+// squared norms, one warp per series
+__global__ void fp8_copy_kernel(const float* __restrict__ X, int64_t n, int mp, int m, int kp,
+                                unsigned char* __restrict__ X8, float* __restrict__ sx,
+                                float* __restrict__ xn) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x / 32);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float ss = 0.0f, mx = 0.0f;
+  for (int i = lane; i < m; i += 32) {
+    const float v = X[row * mp + i];
+    ss = fmaf(v, v, ss);
+    mx = fmaxf(mx, fabsf(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  int e = 0;
+  if (mx > 0.0f) frexpf(mx / 448.0f, &e);
+  const float sc = mx > 0.0f ? ldexpf(1.0f, e) : 1.0f;
+  for (int i = lane; i < kp; i += 32) {
+    const float v = i < m ? X[row * mp + i] : 0.0f;
+    X8[row * kp + i] = (unsigned char)__nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
+  }
+  if (lane == 0) {
+    xn[row] = ss;
+    sx[row] = sc;
+  }
+}
+
 __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int F,
                                  int rows, int cols) {
   // in [F][rows][cols] -> out [F][cols][rows]
@@ -257,8 +291,12 @@ bool encode_2d(CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t in
   return r == CUDA_SUCCESS;
 }
 
-// 2-D TMA descriptor of the float16 copy: dims {kp, n}, boxes of 64 x 128
+// 2-D TMA descriptor of the operand copy: dims {kp, n}, 128-byte boxes of
+// 128 rows (64 float16 or 128 e4m3 columns)
 bool encode_xh_map(leafi_index* ix) {
+  if (ix->scan_path == 2)
+    return encode_2d(&ix->xh_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, ix->X8.p, (uint64_t)ix->kp,
+                     (uint64_t)ix->n, (uint64_t)ix->kp, 128, 128);
   return encode_2d(&ix->xh_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, ix->Xh.p, (uint64_t)ix->kp,
                    (uint64_t)ix->n, (uint64_t)ix->kp * 2, 64, 128);
 }
@@ -267,7 +305,7 @@ bool encode_xh_map(leafi_index* ix) {
 // The tensor-core forward (3xTF32) serves indexes on the tensor-core scan path
 // whose hidden width fits one MMA (h <= 256); the CUDA-core forward the rest.
 bool filter_tc(const leafi_index* ix) {
-  return ix->model == LEAFI_FILTER_MLP && ix->scan_path == 0 && ix->F > 0 &&
+  return ix->model == LEAFI_FILTER_MLP && ix->scan_path != 1 && ix->F > 0 &&
          filter_tc_fits(ix->m, ix->h, ix->smem_optin);
 }
 
@@ -312,31 +350,38 @@ void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_
 // One scan round: group pairs by leaf, scan, merge candidates into slots.
 // query tiles of the tensor-core scan for top-k lists of k keys (0: CUDA-core scan)
 int tc_nbuf(leafi_index* ix, int k, int* qkeys = nullptr) {
-  if (!ix->tc_ok || ix->scan_path != 0) return 0;
+  if (!ix->tc_scan()) return 0;
   auto it = ix->tc_plan.find(k);
   if (it == ix->tc_plan.end()) {
     int qk = 0;
-    const int nb = tc_scan_plan(ix->kp, k, ix->smem_optin, nullptr, &qk);
+    const int nb = tc_scan_plan(ix->op_row_bytes(), k, ix->smem_optin, nullptr, &qk);
     it = ix->tc_plan.emplace(k, std::make_pair(nb, qk)).first;
   }
   if (qkeys) *qkeys = it->second.second;
   return it->second.first;
 }
 
-// float16 rows and band constants of nq queries for the tensor-core scan
-// (null pointers when the index scans on CUDA cores)
+// float16 (or e4m3) rows and band constants of nq queries for the tensor-core
+// scan (null pointers when the index scans on CUDA cores)
 struct TcQueries {
   __half* Qh = nullptr;
+  unsigned char* Q8 = nullptr;
   float4* Qk = nullptr;
+  bool on() const { return Qh || Q8; }
 };
+void launch_query_prep(const leafi_index* ix, const float* dQ, int nq, const TcQueries& t,
+                       cudaStream_t s) {
+  if (t.Q8) launch_tc_query_prep8(dQ, nq, ix->mp, ix->kp, t.Q8, t.Qk, s);
+  else if (t.Qh) launch_tc_query_prep(dQ, nq, ix->mp, ix->kp, t.Qh, t.Qk, s);
+}
 TcQueries prep_tc_queries(leafi_index* ix, const float* dQ, int nq, int cap_rows) {
   TcQueries r;
-  if (!ix->tc_ok || ix->scan_path != 0) return r;
-  __half* Qh = ix->sc->sQh.need((size_t)std::max(nq, cap_rows) * ix->kp);
-  float4* Qk = ix->sc->sQk.need((size_t)2 * std::max(nq, cap_rows));
-  launch_tc_query_prep(dQ, nq, ix->mp, ix->kp, Qh, Qk, ix->stream);
-  r.Qh = Qh;
-  r.Qk = Qk;
+  if (!ix->tc_scan()) return r;
+  const size_t rows = (size_t)std::max(nq, cap_rows);
+  if (ix->scan_path == 2) r.Q8 = ix->sc->sQ8.need(rows * ix->kp);
+  else r.Qh = ix->sc->sQh.need(rows * ix->kp);
+  r.Qk = ix->sc->sQk.need(2 * rows);
+  launch_query_prep(ix, dQ, nq, r, ix->stream);
   return r;
 }
 
@@ -354,7 +399,7 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
   Pair* grouped = ix->sc->sGrouped.need(std::max(npairs_max, 1));
   int32_t* nitems = ix->sc->sNItems.need(1);
   int qkeys = 0;
-  const int nbuf = tq.Qh ? tc_nbuf(ix, kstride, &qkeys) : 0;
+  const int nbuf = tq.on() ? tc_nbuf(ix, kstride, &qkeys) : 0;
   const bool use_tc = nbuf > 0;
   const bool var_groups = use_tc && kstride > 1;  // groups bounded by the sum of their k
   // the tensor-core scan's rounds pick their work-item size on the device: the
@@ -395,6 +440,9 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.part_dev = part_dev;
     t.Q = dQ;
     t.Qh = tq.Qh;
+    t.Q8 = tq.Q8;
+    t.sx = ix->sx.p;
+    t.fp8 = ix->scan_path == 2 ? 1 : 0;
     t.Qk = tq.Qk;
     t.nbuf = nbuf;
     t.G = tc_group_size(kstride);
@@ -494,7 +542,7 @@ void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dL
   const TcQueries tq = prep_tc_queries(ix, dQ, nq, 0);
   // batches of queries keep the CUDA-core scan's candidate buffer bounded
   // (the tensor-core scan merges into the lists directly)
-  const bool direct = tq.Qh && tc_nbuf(ix, k) > 0;
+  const bool direct = tq.on() && tc_nbuf(ix, k) > 0;
   const size_t per_query = (size_t)nl * cap * sizeof(unsigned long long);
   int qb = (int)std::max<size_t>(1, kKnnBudget / std::max<size_t>(per_query, 1));
   qb = direct ? nq : std::min(qb, nq);
@@ -506,8 +554,9 @@ void leaf_knn_device(leafi_index* ix, const float* dQ, int nq, const int32_t* dL
     const int ns = nb * nl;
     launch_leafknn_pairs(nb, nl, dLeaves + (size_t)q0 * nl, L, pairs, np, s);
     TcQueries tb;
-    if (tq.Qh) {
-      tb.Qh = tq.Qh + (size_t)q0 * ix->kp;
+    if (tq.on()) {
+      if (tq.Qh) tb.Qh = tq.Qh + (size_t)q0 * ix->kp;
+      if (tq.Q8) tb.Q8 = tq.Q8 + (size_t)q0 * ix->kp;
       tb.Qk = tq.Qk + (size_t)2 * q0;
     }
     // slots of this batch are [q0*nl, q0*nl + ns): shift the bases
@@ -752,8 +801,9 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     v.order_tmp = L > calib_max_sort() ? S.sOrderTmp.need(leaf_order_scratch(qb, L)) : nullptr;
     if (any_filtered && filter_tc(ix)) S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
     v.tq = TcQueries();
-    if (ix->tc_ok && ix->scan_path == 0) {
-      v.tq.Qh = S.sQh.need((size_t)qb * ix->kp);
+    if (ix->tc_scan()) {
+      if (ix->scan_path == 2) v.tq.Q8 = S.sQ8.need((size_t)qb * ix->kp);
+      else v.tq.Qh = S.sQh.need((size_t)qb * ix->kp);
       v.tq.Qk = S.sQk.need((size_t)2 * qb);
       S.sItemLeaf.need(std::max((size_t)qb * std::max(W, 1) * max_parts(ix),
                                 (size_t)3 * ix->items_per_sm * sm_count(ix->device) + 1));
@@ -832,7 +882,7 @@ void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
   ix->tick(2);
   compute_bounds(ix, v.gQ, nb, v.lb2, v.route, pre_p);
   ix->tock();
-  if (v.tq.Qh) launch_tc_query_prep(v.gQ, nb, ix->mp, ix->kp, v.tq.Qh, v.tq.Qk, s);
+  launch_query_prep(ix, v.gQ, nb, v.tq, s);
   if (use_f) {
     ix->tick(4);
     filter_forward(ix, v.gQ, nb, v.P, qb);
@@ -1236,7 +1286,7 @@ void leafi_index::drop_graphs() {
 }
 
 size_t leafi::Scratch::bytes() const {
-  return sQ.bytes() + sQh.bytes() + sQk.bytes() + sQs.bytes() + sItemLeaf.bytes() +
+  return sQ.bytes() + sQh.bytes() + sQ8.bytes() + sQk.bytes() + sQs.bytes() + sItemLeaf.bytes() +
          sWork.bytes() + sP.bytes() + sIv.bytes() + sNode.bytes() + sLb.bytes() + sPaa.bytes() +
          sTarget.bytes() + sRoute.bytes() + sK.bytes() + sJpos.bytes() + sCnt.bytes() +
          sGrpOff.bytes() + sItemOff.bytes() + sNpairs.bytes() + sCandCnt.bytes() +
@@ -1339,7 +1389,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     if (m < 1 || m > 512) fail(LEAFI_EINVAL, "m must be in [1, 512]");
     if (p->leaf_capacity < 1) fail(LEAFI_EINVAL, "leaf_capacity < 1");
     if (p->wave < 1 || p->wave > calib_max_wave()) fail(LEAFI_EINVAL, "wave must be in [1, %d]", calib_max_wave());
-    if (p->scan_path < 0 || p->scan_path > 1) fail(LEAFI_EINVAL, "scan_path must be 0 or 1");
+    if (p->scan_path < 0 || p->scan_path > 2) fail(LEAFI_EINVAL, "scan_path must be 0, 1 or 2");
     if (p->host_build < 0 || p->host_build > 1) fail(LEAFI_EINVAL, "host_build must be 0 or 1");
     if (p->index_type == LEAFI_DSTREE) {
       if (p->dstree_init_segments < 1 || p->dstree_init_segments > m)
@@ -1477,6 +1527,23 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
         ix->Xh.release();
         ix->xn.release();
       }
+    } else if (p->scan_path == 2 && (m + 127) / 128 * 128 <= 256) {
+      // e4m3 operands with per-series scales: rows of m rounded up to 128 bytes
+      ix->kp = (m + 127) / 128 * 128;
+      unsigned char* X8 = ix->X8.need((size_t)n * ix->kp);
+      float* sx = ix->sx.need((size_t)n);
+      float* xn = ix->xn.need((size_t)n);
+      fp8_copy_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(X, n, ix->mp, m, ix->kp, X8, sx, xn);
+      LF_CHECK_LAUNCH();
+      LF_CUDA(cudaStreamSynchronize(s));
+      ix->tc_ok = encode_xh_map(ix.get());
+      for (int w0 = 0; w0 < t.n_leaves && !ix->pack_small; w0 += 8)
+        ix->pack_small = t.leaf_off[std::min(w0 + 8, t.n_leaves)] - t.leaf_off[w0] <= 128;
+      if (!ix->tc_ok) {
+        ix->X8.release();
+        ix->sx.release();
+        ix->xn.release();
+      }
     }
     std::vector<int32_t> lf(t.n_leaves, -1);
     ix->d_leaf_filter.upload(lf, s);
@@ -1595,10 +1662,11 @@ leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info) {
     r.n_calib = index->nc;
     r.n_kclasses = index->nk;
     for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) r.kclasses[i] = index->kclasses[i];
-    r.device_bytes = (int64_t)(index->X.bytes() + index->Xh.bytes() + index->xn.bytes() +
+    r.device_bytes = (int64_t)(index->X.bytes() + index->Xh.bytes() + index->X8.bytes() +
+                               index->sx.bytes() + index->xn.bytes() +
                                index->ids.bytes() + index->W1t.bytes() + index->cnn.bytes());
-    r.tensor_scan = (index->tc_ok && index->scan_path == 0) ? 1 : 0;
-    r.scan_row_bytes = r.tensor_scan ? index->kp * 2 : index->mp * 4;
+    r.tensor_scan = index->tc_scan() ? 1 : 0;
+    r.scan_row_bytes = r.tensor_scan ? index->op_row_bytes() : index->mp * 4;
     r.calib_confidence = index->calib_confidence;
     r.filter_model = index->model;
     r.filter_width = index->F ? index->h : 0;
@@ -1726,7 +1794,7 @@ void select_auto_core(leafi_index* index, const leafi_select_params* params,
   if (params->model != LEAFI_FILTER_MLP && !cnn) fail(LEAFI_EINVAL, "unknown filter model");
   if (cnn && !cnn_fits(m, h, ix->smem_optin))
     fail(LEAFI_EINVAL, "CNN filters of %d channels at m = %d exceed shared memory", h, m);
-  const bool tc = !cnn && ix->scan_path == 0 && filter_tc_fits(m, h, ix->smem_optin);
+  const bool tc = !cnn && ix->scan_path != 1 && filter_tc_fits(m, h, ix->smem_optin);
   DBuf<float> W1t, b1, w2, b2, P, Ws, Qs, theta;
   P.need((size_t)nq * Fp);
   double t_f = 0.0;

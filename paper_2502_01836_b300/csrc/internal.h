@@ -223,6 +223,9 @@ struct TcScanArgs {
   int part;
   const float* Q;                  // [nq][mp]
   const __half* Qh;                // [nq][kp] float16 queries (launch_tc_query_prep)
+  const unsigned char* Q8;         // [nq][kp] e4m3 queries (launch_tc_query_prep8), or null
+  const float* sx;                 // e4m3 operands: [n] power-of-two scale of every series
+  int fp8;                         // 1: the operands are e4m3 (X8, Q8), kp bytes per row
   const float4* Qk;                // [nq][2] band constants (launch_tc_query_prep)
   int nbuf;                        // query tiles in shared memory (tc_scan_plan)
   int G;                           // queries per work item of the fixed grouping (tc_group_size)
@@ -251,12 +254,14 @@ int tc_group_size(int k);
 // query tiles (2 or 1) the tensor-core scan can keep for rows of kp halves and
 // top-k lists of k keys within `smem_optin` bytes (0 if it does not fit);
 // qkeys: for k > 1 the keys of each lane quarter's lists (a group's sum of k)
-int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem, int* qkeys);
+int tc_scan_plan(int rb, int k, int smem_optin, size_t* smem, int* qkeys);  // rb: operand row bytes
 // out[p][i] = X[order[p]][i] for i < m, 0 for m <= i < mp (leaf-major rows)
 void launch_gather_rows(const float* X, int64_t n, int m, const int32_t* order, int mp, float* out,
                         cudaStream_t s);
 void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, float4* Qk,
                           cudaStream_t s);
+void launch_tc_query_prep8(const float* Q, int nq, int mp, int kp, unsigned char* Q8, float4* Qk,
+                           cudaStream_t s);
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s);
 // before a tensor-core round: pad every slot's list (entries [cnt, k)) with
@@ -389,6 +394,7 @@ constexpr int kMaxLanes = 8;  // search lanes an index (or a server) may use
 struct Scratch {
   DBuf<float> sQ;
   DBuf<__half> sQh;        // float16 queries of the tensor-core scan
+  DBuf<unsigned char> sQ8; // e4m3 queries of the tensor-core scan (scan_path 2)
   DBuf<float4> sQk;        // their band constants
   DBuf<float> sQs;         // tf32 hi/lo query planes of the tensor-core filter forward
   DBuf<int32_t> sItemLeaf; // leaf of every scan work item of a round
@@ -435,12 +441,16 @@ struct leafi_index {
 
   // resident data
   leafi::DBuf<float> X;          // [n][mp] leaf-major
-  leafi::DBuf<__half> Xh;        // [n][kp] float16 copy for the tensor-core scan
+  leafi::DBuf<__half> Xh;        // [n][kp] float16 copy for the tensor-core scan (scan_path 0)
+  leafi::DBuf<unsigned char> X8; // [n][kp] e4m3 copy (scan_path 2), with
+  leafi::DBuf<float> sx;         //   [n] power-of-two scales (x ~ sx * e4m3 row)
   leafi::DBuf<float> xn;         // [n] squared norms
-  int kp = 0;                    // float16 row length (multiple of 64)
+  int kp = 0;                    // operand row length (fp16: m rounded up to 64; e4m3: to 128)
   bool tc_ok = false;            // tensor-core scan usable for this index
   bool pack_small = false;       // some window of 8 consecutive leaves fits one 128-row chunk
-  CUtensorMap xh_map;            // 2-D TMA map of Xh: {kp columns, n rows}, box {64, 128}
+  CUtensorMap xh_map;            // 2-D TMA map of Xh (box {64, 128}) or X8 (box {128, 128})
+  bool tc_scan() const { return tc_ok && scan_path != 1; }  // leaf scans on tensor cores
+  int op_row_bytes() const { return scan_path == 2 ? kp : 2 * kp; }
   int smem_optin = 0;            // opt-in shared memory per block of the device
   leafi::DBuf<int32_t> ids;      // position -> original id
   leafi::DBuf<int64_t> leaf_off;

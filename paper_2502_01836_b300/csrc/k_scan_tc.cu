@@ -32,6 +32,13 @@
 // list per query (the quarter's two warps split the columns), re-checks run
 // at once, and the quarter lists merge at the end of the item.
 //
+// The operands may instead be float8 e4m3 with a power-of-two scale per
+// series and per query (x ~ s_x x^, q ~ s_q q^, kind::f8f6f4 MMAs of K = 32):
+// the dot product is s_q s_x <q^, x^> and the band widens to
+// c8 = 2^-3 + 2^-7 + 2^-8 (e4m3 rounding of both operands, |e| <= 2^-4 |v| in
+// the normal range) plus the subnormal and accumulation terms (see
+// tc_query_prep8_kernel); everything else, re-check included, is the same.
+//
 // Work items merge their results straight into each query's top-k list (an
 // atomic minimum for k = 1; for k > 1 a warp-wide merge under the slot's
 // lock), and every item admits against the list's current k-th key, read
@@ -39,6 +46,8 @@
 // belongs to exactly one item, so a series of the final top-k has a smaller
 // key than the k-th key of any list that does not contain it and is never
 // dropped; the final lists do not depend on the order of items.
+#include <cuda_fp8.h>
+
 #include <algorithm>
 #include <cfloat>
 
@@ -82,6 +91,7 @@ struct TcShared {
   float H[kTcG];       // k = 1: running admission bound (thrd, smallest a + band so far)
   float4 qb[kTcG];     // per query: U_lo, U_hi, alpha, |q|^2 (see the epilogue)
   float qm[kTcG];      // |q|
+  float qs[kTcG];      // e4m3 operands: the query's scale s_q (1 for fp16)
   int slot[kTcG], kq[kTcG], cnt[kTcG], qrow[kTcG], wide[kTcG];
   int cnt4[4][kTcG];   // k > 1: entries of each TMEM lane quarter's list per query
   int loff[kTcG];      // k > 1: offset of each query's list in a quarter's lists (sum of earlier k)
@@ -163,7 +173,10 @@ __device__ __forceinline__ Item decode_item(const TcScanArgs& a, int item, int p
 // in 16-byte units: +32 bytes per step inside a 128-byte swizzled row of A and
 // +16 KB per 64-column block; +256 bytes per step of the no-swizzle B), so the
 // issuing thread spends a few instructions per MMA.
-template <int KS>
+// A K step is 32 bytes of both operands for either kind: 16 fp16 or 32 e4m3
+// values (the instruction descriptor's operand formats are 0 in both cases:
+// F16 for kind::f16, E4M3 for kind::f8f6f4).
+template <int KS, bool kFp8>
 __device__ __forceinline__ void issue_chunk(uint32_t dt, uint32_t a_lo, uint32_t a_hi,
                                             uint32_t b_lo, uint32_t b_hi, uint32_t idesc) {
 #pragma unroll
@@ -171,11 +184,18 @@ __device__ __forceinline__ void issue_chunk(uint32_t dt, uint32_t a_lo, uint32_t
     const uint32_t ao = a_lo + (uint32_t)((kk >> 2) * 1024 + (kk & 3) * 2);
     const uint32_t bo = b_lo + (uint32_t)(kk * 16);
     const uint32_t acc = kk > 0 ? 1u : 0u;
-    asm volatile(
-        "{\n.reg .b64 ad, bd;\n.reg .pred p;\nmov.b64 ad, {%1, %2};\nmov.b64 bd, {%3, %4};\n"
-        "setp.ne.b32 p, %6, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n}\n" ::"r"(dt),
-        "r"(ao), "r"(a_hi), "r"(bo), "r"(b_hi), "r"(idesc), "r"(acc)
-        : "memory");
+    if (kFp8)
+      asm volatile(
+          "{\n.reg .b64 ad, bd;\n.reg .pred p;\nmov.b64 ad, {%1, %2};\nmov.b64 bd, {%3, %4};\n"
+          "setp.ne.b32 p, %6, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], ad, bd, %5, p;\n}\n" ::"r"(dt),
+          "r"(ao), "r"(a_hi), "r"(bo), "r"(b_hi), "r"(idesc), "r"(acc)
+          : "memory");
+    else
+      asm volatile(
+          "{\n.reg .b64 ad, bd;\n.reg .pred p;\nmov.b64 ad, {%1, %2};\nmov.b64 bd, {%3, %4};\n"
+          "setp.ne.b32 p, %6, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n}\n" ::"r"(dt),
+          "r"(ao), "r"(a_hi), "r"(bo), "r"(b_hi), "r"(idesc), "r"(acc)
+          : "memory");
   }
 }
 
@@ -445,10 +465,65 @@ __global__ void tc_query_prep_kernel(const float* __restrict__ Q, int nq, int mp
   }
 }
 
+// e4m3 query rows (Kp bytes, zero padded) with a power-of-two scale s_q
+// (max |q_i| / s_q <= 448, the largest finite e4m3 value; s_q < max |q_i| / 224)
+// and band constants, one warp per query: Qk[2q] = (U_lo, U_hi, alpha, |q|^2),
+// Qk[2q+1] = (|q|, 0, s_q, 0).  Rounding to e4m3 moves a value v by at most
+// 2^-4 |v| in the normal range and 2^-10 s in the subnormal one, so for the
+// scaled dot product
+//   |<q, x> - s_q s_x <q^, x^>| <= c1 |q||x| + c2 sqrt(m) (s_x |q| + s_q |x|)
+//                                  + c3 m s_q s_x
+// with c1 = 2 (1 + 2^-4) 2^-4 + 2^-8, c2 = (1 + 2^-4) 2^-10 + 2^-13 + 2^-14,
+// c3 = 3 2^-20; with s < |v| / 224 every term is a multiple of |q||x|, and the
+// float32 accumulation of K exact products adds K 2^-23 (1 + 2^-4)^2 |q||x|.
+// The band then has the fp16 form with c8 in place of c.
+__global__ void tc_query_prep8_kernel(const float* __restrict__ Q, int nq, int mp, int Kp,
+                                      unsigned char* __restrict__ Q8, float4* __restrict__ Qk) {
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  float ss = 0.0f, mx = 0.0f;
+  for (int i = lane; i < mp; i += 32) {
+    const float v = Q[(size_t)q * mp + i];
+    ss = fmaf(v, v, ss);
+    mx = fmaxf(mx, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  int e = 0;
+  if (mx > 0.0f) frexpf(mx / 448.0f, &e);
+  const float sc = mx > 0.0f ? ldexpf(1.0f, e) : 1.0f;
+  for (int piece = lane; piece < Kp / 16; piece += 32) {
+    __align__(16) unsigned char b[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = piece * 16 + u;
+      const float v = i < mp ? Q[(size_t)q * mp + i] : 0.0f;
+      b[u] = (unsigned char)__nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
+    }
+    *reinterpret_cast<uint4*>(Q8 + (size_t)q * Kp + piece * 16) = *reinterpret_cast<const uint4*>(b);
+  }
+  if (lane == 0) {
+    const float qm = sqrtf(ss);
+    const float sm = band_s(mp);
+    const float rm = sqrtf((float)mp);
+    const float c8 = 0.13671875f + 2.0f * 0.0011596680f * rm / 224.0f +
+                     2.8610229e-6f * (float)mp / 50176.0f + (float)Kp * 1.1920929e-7f * 1.1289063f +
+                     9.5367432e-7f;
+    const float alpha = 2.0f * (c8 * qm + sm);
+    const float beta = 2.0f * sm * qm + 1e-4f * ss;
+    Qk[2 * (size_t)q] = make_float4(ss - beta, ss + beta, alpha, ss);
+    Qk[2 * (size_t)q + 1] = make_float4(qm, 0.0f, sc, 0.0f);
+  }
+}
+
 // kSplit: k = 1 (one best key per query, fixed groups of 64); otherwise top-k
 // lists per lane quarter and groups sized by k.  Two instantiations, so each
 // path is compiled and scheduled on its own.
-template <bool kSplit>
+template <bool kSplit, bool kFp8>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     const __grid_constant__ CUtensorMap tmap, TcScanArgs a, const int32_t* __restrict__ n_items_dev,
     const int32_t* __restrict__ slot_k) {
@@ -465,14 +540,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   // 128-byte swizzled tiles need 1024-byte aligned bases
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int Kp = a.kp;                       // fp16 row length (multiple of 64)
-  const int tileA = kTcRows * Kp * 2;        // bytes per A stage
+  const int Kp = a.kp;                       // operand row length (fp16: multiple of 64,
+                                             // e4m3: multiple of 128)
+  const int RB = kFp8 ? Kp : 2 * Kp;         // operand bytes per row
+  const int tileA = kTcRows * RB;            // bytes per A stage
   const int G = a.G;                         // queries per work item (64, or 16 for large k)
-  const int tileB = G * Kp * 2;              // bytes per query tile
+  const int tileB = G * RB;                  // bytes per query tile
   const int nbuf = a.nbuf;                   // query tiles (1 or 2)
   unsigned char* A0 = smem;
   unsigned char* A1 = smem + tileA;
-  unsigned char* B0 = smem + 2 * tileA;      // G x Kp fp16, no swizzle
+  unsigned char* B0 = smem + 2 * tileA;      // G x Kp operands, no swizzle
   unsigned char* B1 = B0 + (nbuf - 1) * tileB;
   // k = 1: [G] best keys; k > 1: four quarters of a.qkeys keys, query j's list at S.loff[j]
   u64* lists = reinterpret_cast<u64*>(B0 + nbuf * tileB);
@@ -481,7 +558,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
   float* cb_lo = reinterpret_cast<float*>(cb_j + kCandCap);
   constexpr bool split = kSplit;             // k = 1: halves on alternate accumulators, deferred re-checks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t sbo = 16u * Kp;             // B: bytes between 8-row groups
+  const uint32_t sbo = 8u * RB;              // B: bytes between 8-row groups
   const int m4 = a.mp / 4;
   volatile int* abort = &S.abort;
 
@@ -559,8 +636,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           unsigned char* dst = st ? A1 : A0;
           const int r0 = (int)(I.p0 + (int64_t)c * kTcRows);
           dev::mbar_expect_tx(&S.full[st], (uint32_t)tileA);
-          for (int kb = 0; kb < Kp / 64; ++kb)
-            dev::tma_load_2d(dst + kb * 16384, &tmap, kb * 64, r0, &S.full[st]);
+          // one 128-byte swizzled box (64 fp16 or 128 e4m3 columns) per block
+          for (int kb = 0; kb < RB / 128; ++kb)
+            dev::tma_load_2d(dst + kb * 16384, &tmap, kb * (kFp8 ? 128 : 64), r0, &S.full[st]);
           ++g_ld;
           ++ld_cnt[st];
         }
@@ -581,7 +659,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     PROF_T0();
     uint32_t bempty_ph[2] = {0u, 0u};
     int li = 0;
-    const int pieces = Kp / 8;                 // 16-byte pieces per query row
+    const int pieces = RB / 16;                // 16-byte pieces per query row
+    const unsigned char* qops = kFp8 ? a.Q8 : reinterpret_cast<const unsigned char*>(a.Qh);
     for (;; ++li) {
       int item = -1;
       if (lane == 0) item = ring_take(S, li, abort);
@@ -608,13 +687,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       // group are zero-filled), so all of them are in flight at once
       for (int qq = 0; qq < I.N; ++qq) {
         const int row = qq < I.nqg ? I.pr[qq].q : -1;
-        const __half* src = a.Qh + (size_t)(row >= 0 ? row : 0) * Kp;
+        const unsigned char* src = qops + (size_t)(row >= 0 ? row : 0) * RB;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int piece = lane + 32 * h;
           if (piece < pieces)
             dev::cp_async16_zfill(Bt + (qq / 8) * sbo + piece * 128 + (qq % 8) * 16,
-                                  src + piece * 8, row >= 0 ? 16 : 0);
+                                  src + piece * 16, row >= 0 ? 16 : 0);
         }
       }
       dev::cp_async_commit();
@@ -665,11 +744,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           const uint32_t dt = tmem + (uint32_t)(t * kTcG);
           const uint32_t alo = (uint32_t)ad, ahi = (uint32_t)(ad >> 32);
           const uint32_t blo = (uint32_t)bd, bhi = (uint32_t)(bd >> 32);
-          switch (Kp) {
-            case 64: issue_chunk<4>(dt, alo, ahi, blo, bhi, idesc); break;
-            case 128: issue_chunk<8>(dt, alo, ahi, blo, bhi, idesc); break;
-            case 192: issue_chunk<12>(dt, alo, ahi, blo, bhi, idesc); break;
-            default: issue_chunk<16>(dt, alo, ahi, blo, bhi, idesc); break;
+          switch (RB) {
+            case 128: issue_chunk<4, kFp8>(dt, alo, ahi, blo, bhi, idesc); break;
+            case 256: issue_chunk<8, kFp8>(dt, alo, ahi, blo, bhi, idesc); break;
+            case 384: issue_chunk<12, kFp8>(dt, alo, ahi, blo, bhi, idesc); break;
+            default: issue_chunk<16, kFp8>(dt, alo, ahi, blo, bhi, idesc); break;
           }
           PROF_ADD(14);
           dev::mma_commit(&S.empty[st]);
@@ -696,8 +775,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
     // ------------------------------------------------ epilogue warps 0-7
     const float4* Q4 = reinterpret_cast<const float4*>(a.Q);
     const float4* X4 = reinterpret_cast<const float4*>(a.X);
-    const float cK = band_c(Kp);
-    const float sm = band_s(a.mp);
     const float kInf = __int_as_float(0x7f800000);
     const int half = warp >> 2;
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
@@ -737,6 +814,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           S.wide[qq] = k1.y != 0.0f ? 1 : 0;
           S.qb[qq] = k0;
           S.qm[qq] = k1.x;
+          S.qs[qq] = kFp8 ? k1.z : 1.0f;
           if (I.packed) {
             const int lf = I.pr[qq].leaf;
             S.rs[qq] = (int)(a.leaf_off[lf] - I.p0);
@@ -745,6 +823,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
           if (split) lists[qq * a.k] = th;
         } else {
           S.qb[qq] = make_float4(kInf, kInf, 0.0f, 0.0f);
+          S.qs[qq] = 1.0f;
           S.H[qq] = 0.0f;  // lo = inf > 0: never a candidate
           S.Tq[qq] = 0.0f;
           S.rs[qq] = S.re[qq] = 0;
@@ -777,6 +856,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
         const int64_t pos = I.p0 + (int64_t)c * kTcRows + r;
         const bool valid = pos < I.p1;
         const float xn = valid ? a.xn[pos] : 0.0f;
+        // e4m3 operands: the dot product of the row with column j is
+        // -2 s_x s_q acc (powers of two: the scaling is exact)
+        const float m2sx = kFp8 ? (valid ? -2.0f * a.sx[pos] : 0.0f) : -2.0f;
         // k = 1: bounds other work items of the round have published since
         // the item started (thread r refreshes query column r)
         const float ubr = (split && a.ub && r < nqg) ? __ldcg(&a.ub[S.slot[r]]) : kInf;
@@ -805,8 +887,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
               const float4 qb = S.qb[c0 + jj];
-              lov[jj] = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
-              hw[jj] = fmaxf(fmaf(-2.0f, d[jj], fmaf(qb.z, xnorm, qb.y + vhi)), 0.0f);
+              const float cf = kFp8 ? m2sx * S.qs[c0 + jj] : -2.0f;
+              lov[jj] = fmaf(cf, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
+              hw[jj] = fmaxf(fmaf(cf, d[jj], fmaf(qb.z, xnorm, qb.y + vhi)), 0.0f);
             }
             if (I.packed) {
               // a pair only meets the rows of its own leaf
@@ -922,7 +1005,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
               for (int u = 0; u < 4; ++u) {
                 const int jj = 4 * v4 + u;
                 const float4 qb = S.qb[c0 + jj];
-                const float lo = fmaf(-2.0f, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
+                const float cf = kFp8 ? m2sx * S.qs[c0 + jj] : -2.0f;
+                const float lo = fmaf(cf, d[jj], fmaf(-qb.z, xnorm, qb.x + vlo));
                 if (!(lo > tt[u])) cand |= 1u << jj;
               }
             }
@@ -1100,22 +1184,23 @@ int tc_group_size(int k) {
   return kTcG;
 }
 
-static size_t tc_dyn_smem(int kp, int k, int nbuf, int qkeys) {
+// rb: operand bytes per row (2 kp for fp16, kp for e4m3)
+static size_t tc_dyn_smem(int rb, int k, int nbuf, int qkeys) {
   // k = 1: one key per query plus the deferred re-check buffer; k > 1: four
   // lane quarters' lists of qkeys keys each
   const size_t G = (size_t)kTcG;
-  return 1024 + (size_t)2 * kTcRows * kp * 2 + (size_t)nbuf * G * kp * 2 +
+  return 1024 + (size_t)2 * kTcRows * rb + (size_t)nbuf * G * rb +
          (k == 1 ? G * 8 + (size_t)kCandCap * 12 : (size_t)4 * qkeys * 8);
 }
 
-int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem, int* qkeys) {
+int tc_scan_plan(int rb, int k, int smem_optin, size_t* smem, int* qkeys) {
   cudaFuncAttributes fa;
-  if (k == 1) LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel<true>));
-  else LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel<false>));
+  if (k == 1) LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel<true, false>));
+  else LF_CUDA(cudaFuncGetAttributes(&fa, tc_scan_kernel<false, false>));
   const size_t avail = (size_t)smem_optin > fa.sharedSizeBytes ? smem_optin - fa.sharedSizeBytes : 0;
   if (k == 1) {
     for (int nbuf = 2; nbuf >= 1; --nbuf) {
-      const size_t dyn = tc_dyn_smem(kp, k, nbuf, 0);
+      const size_t dyn = tc_dyn_smem(rb, k, nbuf, 0);
       if (dyn <= avail) {
         if (smem) *smem = dyn;
         if (qkeys) *qkeys = 0;
@@ -1130,14 +1215,14 @@ int tc_scan_plan(int kp, int k, int smem_optin, size_t* smem, int* qkeys) {
   const size_t target = (size_t)kTcG * k;
   size_t q[3] = {0, 0, 0};
   for (int nbuf = 1; nbuf <= 2; ++nbuf) {
-    const size_t base = tc_dyn_smem(kp, k, nbuf, 0);
+    const size_t base = tc_dyn_smem(rb, k, nbuf, 0);
     if (base < avail) q[nbuf] = std::min(target, (avail - base) / 32 / 8 * 8);
   }
   int nbuf = 0;
   if (q[2] >= (size_t)k && 5 * q[2] >= 4 * q[1]) nbuf = 2;
   else if (q[1] >= (size_t)k) nbuf = 1;
   if (nbuf == 0) return 0;
-  if (smem) *smem = tc_dyn_smem(kp, k, nbuf, (int)q[nbuf]);
+  if (smem) *smem = tc_dyn_smem(rb, k, nbuf, (int)q[nbuf]);
   if (qkeys) *qkeys = (int)q[nbuf];
   return nbuf;
 }
@@ -1200,33 +1285,47 @@ void launch_tc_query_prep(const float* Q, int nq, int mp, int kp, __half* Qh, fl
   LF_CHECK_LAUNCH();
 }
 
-void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
-                    const int32_t* slot_k, int grid, cudaStream_t s) {
-  const size_t smem = tc_dyn_smem(a.kp, a.k, a.nbuf, a.qkeys);
+void launch_tc_query_prep8(const float* Q, int nq, int mp, int kp, unsigned char* Q8, float4* Qk,
+                           cudaStream_t s) {
+  if (nq <= 0) return;
+  tc_query_prep8_kernel<<<(nq + 7) / 8, 256, 0, s>>>(Q, nq, mp, kp, Q8, Qk);
+  LF_CHECK_LAUNCH();
+}
+
+namespace {
+template <bool kSplit, bool kFp8>
+void launch_tc_scan_as(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
+                       const int32_t* slot_k, int grid, size_t smem, cudaStream_t s) {
   // the opt-in shared-memory size is raised only when a launch needs more than
   // any earlier one on this device (the attribute persists)
   static std::mutex mu;
-  static std::map<std::pair<int, int>, size_t> set;  // (device, instantiation) -> bytes
+  static std::map<int, size_t> set;  // device -> bytes
   int dev = 0;
   LF_CUDA(cudaGetDevice(&dev));
   {
     std::lock_guard<std::mutex> lk(mu);
-    size_t& have = set[{dev, a.k == 1 ? 1 : 0}];
+    size_t& have = set[dev];
     if (smem > have) {
-      if (a.k == 1)
-        LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      else
-        LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      LF_CUDA(cudaFuncSetAttribute(tc_scan_kernel<kSplit, kFp8>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       have = smem;
     }
   }
-  if (a.k == 1)
-    tc_scan_kernel<true><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
-  else
-    tc_scan_kernel<false><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
+  tc_scan_kernel<kSplit, kFp8><<<grid, kTcThreads, smem, s>>>(tmap, a, n_items_dev, slot_k);
   LF_CHECK_LAUNCH();
+}
+}  // namespace
+
+void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
+                    const int32_t* slot_k, int grid, cudaStream_t s) {
+  const size_t smem = tc_dyn_smem(a.fp8 ? a.kp : 2 * a.kp, a.k, a.nbuf, a.qkeys);
+  if (a.k == 1) {
+    if (a.fp8) launch_tc_scan_as<true, true>(tmap, a, n_items_dev, slot_k, grid, smem, s);
+    else launch_tc_scan_as<true, false>(tmap, a, n_items_dev, slot_k, grid, smem, s);
+  } else {
+    if (a.fp8) launch_tc_scan_as<false, true>(tmap, a, n_items_dev, slot_k, grid, smem, s);
+    else launch_tc_scan_as<false, false>(tmap, a, n_items_dev, slot_k, grid, smem, s);
+  }
   if (a.prof) {
     tc_timeline_kernel<<<1, 1, 0, s>>>(a.prof);
     LF_CHECK_LAUNCH();

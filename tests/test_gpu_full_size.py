@@ -180,7 +180,7 @@ def test_mixed_k_isax_config_reduced():
         lf.leafi_free(idx)
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_precision_config_reduced(path):
     m, n, k = 96, 300_000, 10
     X = fx.embedding_like(n, m)
@@ -189,7 +189,7 @@ def test_precision_config_reduced(path):
                                            scan_path=path))
     try:
         info = lf.leafi_get_info(idx)
-        assert bool(info.tensor_scan) == (path == 0)
+        assert bool(info.tensor_scan) == (path != 1)
         ids = np.zeros((len(Q), k), np.int64)
         d = np.zeros((len(Q), k), np.float32)
         st = lf.SearchStats()

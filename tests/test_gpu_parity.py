@@ -72,11 +72,11 @@ def test_exact_search_bit_exact(ds, k):
     assert int(o_st[:, 0].sum()) == st.leaves_scanned
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 @pytest.mark.parametrize("k", [1, 7, 100])
 def test_scan_paths_bit_exact(k, path):
-    """Tensor-core scan (float16 MMA + band + canonical re-check) and CUDA-core scan
-    both return the brute-force answer."""
+    """Tensor-core scan (float16 or e4m3 MMA + band + canonical re-check) and
+    CUDA-core scan all return the brute-force answer."""
     X = fx.random_walk(12000, 96, seed=201)
     Q = fx.test_queries(X, 70, seed=202)
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=700, wave=3, device=0, scan_path=path))
@@ -84,6 +84,28 @@ def test_scan_paths_bit_exact(k, path):
         ids, d, _ = _exact(idx, Q, k)
         bf_ids, bf_d2 = O.knn(X, Q, k)
         assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+    finally:
+        lf.leafi_free(idx)
+
+
+@pytest.mark.parametrize("m", [64, 200, 256])
+@pytest.mark.parametrize("k", [1, 10])
+def test_e4m3_scan_lengths_bit_exact(m, k):
+    """The e4m3 path over rows of 128 and 256 bytes (m = 200: zero padding in
+    the last block), with a series scaled far from the others (its scale
+    keeps it in range) and an all-zero series."""
+    X = fx.random_walk(6000, m, seed=211)
+    X[17] *= 1000.0
+    X[23] = 0.0
+    Q = fx.test_queries(X, 50, seed=212)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=500, wave=3, device=0, scan_path=2))
+    try:
+        info = lf.leafi_get_info(idx)
+        assert info.tensor_scan == 1 and info.scan_row_bytes == (128 if m <= 128 else 256)
+        ids, d, st = _exact(idx, Q, k)
+        bf_ids, bf_d2 = O.knn(X, Q, k)
+        assert np.array_equal(ids, bf_ids) and np.array_equal(d, np.sqrt(bf_d2))
+        assert 0 < st.rechecks <= st.series_scanned
     finally:
         lf.leafi_free(idx)
 
