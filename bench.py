@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--part", type=int, default=2048, help="series per leaf-scan work item")
     ap.add_argument("--items-per-sm", type=int, default=4,
                     help="scan work items per SM a round aims at (0: fixed part)")
+    ap.add_argument("--min-part", type=int, default=512,
+                    help="smallest series per work item a round may take")
     ap.add_argument("--scan-blocks", type=int, default=0,
                     help="thread blocks per tensor-core scan launch (0: one per SM)")
     a = ap.parse_args()
@@ -230,6 +232,7 @@ def workload_config(a):
             "schedule": "route-leaf order" if not getattr(a, "no_schedule", False) else "caller order",
             "lanes": getattr(a, "lanes", 8), "part": getattr(a, "part", 2048),
             "items_per_sm": getattr(a, "items_per_sm", 4),
+            "min_part": getattr(a, "min_part", 512),
             "scan_blocks": getattr(a, "scan_blocks", 0),
             "l2": "inputs larger than L2 (%.2f GB float32 series, %.2f GB float16 copy)"
                   % (a.n * M * 4 / 1e9, a.n * M * 2 / 1e9)}
@@ -731,7 +734,7 @@ def main():
     lf.leafi_set_stream(idx, stream.cuda_stream)
     lf.leafi_set_query_schedule(idx, not a.no_schedule)
     lf.leafi_set_search_lanes(idx, a.lanes)
-    lf.leafi_set_scan_part(idx, a.part, a.items_per_sm, a.scan_blocks)
+    lf.leafi_set_scan_part(idx, a.part, a.items_per_sm, a.min_part, a.scan_blocks)
     t_train = time.perf_counter()
     enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs, tune_search=int(a.tune))
     torch.cuda.synchronize()

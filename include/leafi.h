@@ -481,15 +481,15 @@ leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes);
 /* Work items of the leaf scan.  A work item is (leaf, part of at most `rows`
  * series, group of queries); rows is a multiple of 128 in [128, 8192]
  * (default 2048).  The tensor-core scan picks each round's part on the device:
- * the largest of rows, rows / 2, ... (>= 128) that gives the round at least
- * items_per_sm items per SM (default 4; 0 always uses rows), since a launch
- * lasts as long as its most loaded SM.  Smaller parts balance better, larger
- * ones cost less per item.  `blocks`: thread blocks of a tensor-core scan
- * launch (0 = one per SM); fewer blocks leave SMs to the scans of other batches
- * in flight, which then run side by side.  Results do not depend on any of
- * them. */
+ * the largest of rows, rows / 2, ... but not below min_rows (a multiple of 128,
+ * default 512) that gives the round at least items_per_sm items per SM
+ * (default 4; 0 always uses rows), since a launch lasts as long as its most
+ * loaded SM.  Smaller parts balance better, larger ones cost less per item; a
+ * round too small for every SM leaves SMs to the other batches in flight.
+ * `blocks`: thread blocks of a tensor-core scan launch (0 = one per SM).
+ * Results do not depend on any of them. */
 leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm,
-                                 int32_t blocks);
+                                 int32_t min_rows, int32_t blocks);
 
 /* Query scheduling of calls with more than one internal batch (on by
  * default): the batches are cut from the queries in order of their route

@@ -227,7 +227,7 @@ def lib():
             "leafi_set_calibration_confidence": [vp, f64],
             "leafi_set_query_schedule": [vp, i32],
             "leafi_set_search_lanes": [vp, i32],
-            "leafi_set_scan_part": [vp, i32, i32, i32],
+            "leafi_set_scan_part": [vp, i32, i32, i32, i32],
             "leafi_tune_search": [vp, C.POINTER(TuneParams), C.POINTER(TuneReport)],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
@@ -470,10 +470,12 @@ def leafi_set_search_lanes(index, lanes):
     _check(lib().leafi_set_search_lanes(index, int(lanes)))
 
 
-def leafi_set_scan_part(index, rows=2048, items_per_sm=4, blocks=0):
+def leafi_set_scan_part(index, rows=2048, items_per_sm=4, min_rows=512, blocks=0):
     """Leaf-scan work items: at most `rows` series (multiple of 128); rounds aim at
-    items_per_sm items per SM (0: always `rows`); `blocks` per scan launch (0: one per SM)."""
-    _check(lib().leafi_set_scan_part(index, int(rows), int(items_per_sm), int(blocks)))
+    items_per_sm items per SM (0: always `rows`) with parts of at least min_rows;
+    `blocks` per scan launch (0: one per SM)."""
+    _check(lib().leafi_set_scan_part(index, int(rows), int(items_per_sm), int(min_rows),
+                                     int(blocks)))
 
 
 def leafi_tune_search(index, params: TuneParams | None = None):

@@ -414,14 +414,15 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
                use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped, nitems,
                distinct_stat, s, var_groups ? nullptr : item_leaf,
                use_tc && !var_groups && ix->pack_small, var_groups ? 0 : target,
-               var_groups ? nullptr : part_dev);
+               var_groups ? nullptr : part_dev, std::min(ix->min_part, ix->part));
   int32_t *gfirst = nullptr, *gbound = nullptr;
   if (var_groups) {
     int32_t* ngr = ix->sc->sNGroups.need(L);
     gfirst = ix->sc->sGFirst.need(L + 1);
     gbound = ix->sc->sGBound.need((size_t)std::max(npairs_max, 1) + 1);
     launch_var_groups(L, ix->leaf_off.p, ix->part, goff, grouped, slot_k, kstride, qkeys, ngr, gfirst,
-                      gbound, ioff, item_leaf, nitems, s, target, part_dev);
+                      gbound, ioff, item_leaf, nitems, s, target, part_dev,
+                      std::min(ix->min_part, ix->part));
   }
   const int grid = use_tc ? (ix->scan_blocks > 0 ? ix->scan_blocks : sm_count(ix->device))
                           : sm_count(ix->device) * 2;
@@ -2802,16 +2803,19 @@ leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes) {
 }
 
 leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm,
-                                 int32_t blocks) {
+                                 int32_t min_rows, int32_t blocks) {
   return guarded([&] {
     require_device(index);
     if (rows < 128 || rows > 8192 || rows % 128) fail(LEAFI_EINVAL, "rows must be a multiple of 128 in [128, 8192]");
     if (items_per_sm < 0 || items_per_sm > 64) fail(LEAFI_EINVAL, "items_per_sm must be in [0, 64]");
+    if (min_rows < 128 || min_rows > 8192 || min_rows % 128)
+      fail(LEAFI_EINVAL, "min_rows must be a multiple of 128 in [128, 8192]");
     if (blocks < 0 || blocks > 4096) fail(LEAFI_EINVAL, "blocks must be in [0, 4096]");
     std::lock_guard<std::mutex> lk(index->mu);
     index->drop_graphs();
     index->part = rows;
     index->items_per_sm = items_per_sm;
+    index->min_part = min_rows;
     index->scan_blocks = blocks;
   });
 }

@@ -286,14 +286,15 @@ void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* 
                        const Pair* grouped, const int32_t* slot_k, int kstride, int budget,
                        int32_t* ngroups, int32_t* gfirst, int32_t* gbound, int32_t* item_off,
                        int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s,
-                       int target_items = 0, int32_t* part_out = nullptr);
+                       int target_items = 0, int32_t* part_out = nullptr, int min_part = 128);
 // stat (nullable): stat[0] += series of the distinct leaves in this round;
 // g = queries per work item of the scan kernel that follows
 void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s, int32_t* item_leaf = nullptr,
-                  bool pack_small = false, int target_items = 0, int32_t* part_out = nullptr);
+                  bool pack_small = false, int target_items = 0, int32_t* part_out = nullptr,
+                  int min_part = 128);
 
 void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
                   int32_t* topk_cnt, unsigned long long* thr, const unsigned long long* cand,
@@ -494,6 +495,7 @@ struct leafi_index {
   int part = 2048;         // series per scan work item (leafi_set_scan_part); the tensor-core
                            // scan's rounds may take part / 2, ... (>= 128) for balance
   int items_per_sm = 4;    // work items per SM a tensor-core round aims at
+  int min_part = 512;      // smallest part a tensor-core round may take
   int scan_blocks = 0;     // blocks of a tensor-core scan launch (0: one per SM)
   leafi::Schedule sched;
   int lock_tries = leafi::kDefaultLockTries;  // see leafi_debug_set_lock_tries

@@ -245,9 +245,12 @@ __device__ __forceinline__ int leaf_items(int c, const int64_t* __restrict__ lea
 }
 
 // Work-item size of a round (tensor-core scan): candidate parts part_max,
-// part_max / 2, ... (multiples of 128 rows); the largest whose item count
-// reaches `target` (a few items per SM, so that a launch's items balance)
-// is taken, else the smallest.  target 0 keeps part_max.
+// part_max / 2, ... (multiples of 128 rows, none below min_part); the largest
+// whose item count reaches `target` (a few items per SM, so that a launch's
+// items balance) is taken, else the smallest allowed.  target 0 keeps
+// part_max.  The floor keeps small rounds (a batch's route leaves) from being
+// cut into one-chunk items, whose fixed costs would dominate; such a round
+// occupies fewer SMs and the other lanes' work takes the rest.
 constexpr int kPartLevels = 5;
 
 __device__ __forceinline__ int part_level(int part_max, int c) {
@@ -256,9 +259,10 @@ __device__ __forceinline__ int part_level(int part_max, int c) {
 }
 
 // thread's item counts per level have been added to tot[]; returns the level
-__device__ __forceinline__ int pick_part_level(const int* tot, int target) {
+__device__ __forceinline__ int pick_part_level(const int* tot, int target, int part_max,
+                                                int min_part) {
   int c = 0;
-  while (c + 1 < kPartLevels && tot[c] < target) ++c;
+  while (c + 1 < kPartLevels && tot[c] < target && part_level(part_max, c + 1) >= min_part) ++c;
   return c;
 }
 
@@ -268,7 +272,7 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
                                int32_t* __restrict__ item_off, int32_t* __restrict__ n_items,
                                unsigned long long* __restrict__ stat,
                                int32_t* __restrict__ item_leaf, bool pack_small, int target,
-                               int32_t* __restrict__ part_out) {
+                               int min_part, int32_t* __restrict__ part_out) {
   __shared__ int s_a[1024], s_b[1024];
   __shared__ int tot[kPartLevels];
   const int T = blockDim.x;
@@ -302,7 +306,7 @@ __global__ void offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int 
   for (int c = 0; c < kPartLevels; ++c)
     if (sbl[c]) atomicAdd(&tot[c], sbl[c]);
   __syncthreads();
-  const int lev = pick_part_level(tot, target);
+  const int lev = pick_part_level(tot, target, part_max, min_part);
   const int part = part_level(part_max, lev);
   int sb = 0;
 #pragma unroll
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
     const int64_t* __restrict__ leaf_off, int part_max, int g, int32_t* __restrict__ grp_off,
     int32_t* __restrict__ item_off, int32_t* __restrict__ n_items, Pair* __restrict__ grouped,
     unsigned long long* __restrict__ stat, int32_t* __restrict__ item_leaf, bool pack_small,
-    int target, int32_t* __restrict__ part_out) {
+    int target, int min_part, int32_t* __restrict__ part_out) {
   __shared__ int cnt[kFuseLeaves];
   __shared__ int s_a[1024], s_b[1024];
   __shared__ int tot[kPartLevels];
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
   for (int c = 0; c < kPartLevels; ++c)
     if (sbl[c]) atomicAdd(&tot[c], sbl[c]);
   __syncthreads();
-  const int lev = pick_part_level(tot, target);
+  const int lev = pick_part_level(tot, target, part_max, min_part);
   const int part = part_level(part_max, lev);
   int sb = 0;
 #pragma unroll
@@ -484,7 +488,7 @@ __global__ void vgroup_count_kernel(int L, const int32_t* __restrict__ grp_off,
 __global__ void vgroup_offsets_kernel(int L, const int64_t* __restrict__ leaf_off, int part_max,
                                       const int32_t* __restrict__ ngroups,
                                       int32_t* __restrict__ gfirst, int32_t* __restrict__ item_off,
-                                      int32_t* __restrict__ n_items, int target,
+                                      int32_t* __restrict__ n_items, int target, int min_part,
                                       int32_t* __restrict__ part_out) {
   __shared__ int s_a[1024], s_b[1024];
   __shared__ int tot[kPartLevels];
@@ -507,7 +511,7 @@ __global__ void vgroup_offsets_kernel(int L, const int64_t* __restrict__ leaf_of
   for (int c = 0; c < kPartLevels; ++c)
     if (sbl[c]) atomicAdd(&tot[c], sbl[c]);
   __syncthreads();
-  const int lev = pick_part_level(tot, target);
+  const int lev = pick_part_level(tot, target, part_max, min_part);
   const int part = part_level(part_max, lev);
   int sb = 0;
 #pragma unroll
@@ -894,11 +898,11 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s, int32_t* item_leaf,
-                  bool pack_small, int target_items, int32_t* part_out) {
+                  bool pack_small, int target_items, int32_t* part_out, int min_part) {
   if (L <= kFuseLeaves) {
     group_fused_kernel<<<1, 1024, 0, s>>>(pairs, npairs_dev, L, leaf_off, part, g, grp_off,
                                           item_off, n_items_dev, grouped, stat, item_leaf,
-                                          pack_small, target_items, part_out);
+                                          pack_small, target_items, min_part, part_out);
     LF_CHECK_LAUNCH();
     return;
   }
@@ -908,7 +912,7 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
     LF_CHECK_LAUNCH();
   }
   offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, g, cnt, grp_off, item_off, n_items_dev,
-                                    stat, item_leaf, pack_small, target_items, part_out);
+                                    stat, item_leaf, pack_small, target_items, min_part, part_out);
   LF_CHECK_LAUNCH();
   if (npairs_max > 0) {
     scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
@@ -920,13 +924,13 @@ void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* 
                        const Pair* grouped, const int32_t* slot_k, int kstride, int budget,
                        int32_t* ngroups, int32_t* gfirst, int32_t* gbound, int32_t* item_off,
                        int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s,
-                       int target_items, int32_t* part_out) {
+                       int target_items, int32_t* part_out, int min_part) {
   if (L <= 0) return;
   vgroup_count_kernel<<<nblk(L, 256), 256, 0, s>>>(L, grp_off, grouped, slot_k, kstride, budget,
                                                    ngroups);
   LF_CHECK_LAUNCH();
   vgroup_offsets_kernel<<<1, 1024, 0, s>>>(L, leaf_off, part, ngroups, gfirst, item_off, n_items_dev,
-                                           target_items, part_out);
+                                           target_items, min_part, part_out);
   LF_CHECK_LAUNCH();
   vgroup_fill_kernel<<<nblk(L, 256), 256, 0, s>>>(L, leaf_off, part, grp_off, grouped, slot_k,
                                                   kstride, budget, gfirst, item_off, gbound,
