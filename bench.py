@@ -987,7 +987,9 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
             "build": {"leaves": info.n_leaves, "filters": info.n_filters,
-                      "wave": info.wave, "train_and_tune_s": t_train,
+                      "wave": info.wave, "wave_exact": info.wave_exact,
+                      "items_per_sm": info.items_per_sm,
+                      "train_and_tune_s": t_train,
                       "epochs_run_mean": float(np.mean(enh.epochs_run))},
         }
         print(json.dumps(line), flush=True)

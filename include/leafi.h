@@ -139,6 +139,8 @@ typedef struct {
   double calib_confidence;/* see leafi_set_calibration_confidence */
   int32_t filter_model;  /* LEAFI_FILTER_MLP or LEAFI_FILTER_CNN */
   int32_t filter_width;  /* MLP hidden width h, or CNN channels C */
+  int32_t wave_exact;    /* wave width of calls without filtered queries (`wave`: with) */
+  int32_t items_per_sm;  /* leaf-scan work items per SM a round aims at (leafi_set_scan_part) */
 } leafi_index_info;
 
 leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info);
@@ -317,8 +319,10 @@ typedef struct {
   uint64_t seed;
   double confidence;        /* calibration confidence of the search's offsets (0.95; see
                                leafi_set_calibration_confidence) */
-  int32_t tune_search;      /* 1: before the auto-tuners are fitted, leafi_tune_search picks
-                               the wave width and work-item balance (its defaults) */
+  int32_t tune_search;      /* 1: leafi_tune_search picks the wave width and work-item
+                               balance of exact searches, then, after the auto-tuners
+                               are fitted, those of LeaFi searches at target 0.99 (its
+                               defaults; the tables are refitted for the chosen width) */
   int32_t model;            /* LEAFI_FILTER_MLP (Sec. 5.1) or LEAFI_FILTER_CNN (Sec. 5.2;
                                `hidden` is then the channel count C, 0 = m) */
 } leafi_train_params;
@@ -441,25 +445,31 @@ leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, 
                           double recall_target, int64_t* ids, float* dists,
                           leafi_search_stats* stats);
 /* Search-schedule autotuner (no counterpart in the paper; the wave width W is
- * this implementation's batching parameter).  Times exact k-NN searches of
- * n_probe probe queries (dataset series drawn by the library's generator plus
+ * this implementation's batching parameter).  Times k-NN searches of n_probe
+ * probe queries (dataset series drawn by the library's generator plus
  * Gaussian noise of sigma in [noise_lo, noise_hi], z-normalised) for every
  * candidate (wave width, work items per SM), `reps` timed runs after one
- * warm-up each, and keeps the fastest on the index.  The wave width is part
- * of what the auto-tuners calibrate, so an index with fitted auto-tuners is
- * refused (LEAFI_EINVAL): tune first (leafi_train_filters does when
- * tune_search is set).  Zero-length candidate lists take the defaults: waves
- * {16, 32, 64, 128, 256, 1024, n_leaves}, items per SM {2, 4, 8}. */
+ * warm-up each, and keeps the fastest on the index.  target >= 1 (or 0) times
+ * exact searches and sets the wave width of calls without filtered queries
+ * (and of all calls while no auto-tuners are fitted).  target in (0, 1) times
+ * LeaFi searches at that recall target: the wave width is part of what the
+ * auto-tuners calibrate (Alg. 4 simulates the search), so every candidate
+ * width first refits the tables from the calibration queries the index keeps
+ * (LEAFI_EINVAL if it has none, e.g. tables set by leafi_set_autotuners);
+ * the chosen width and its tables are installed.  Zero-length candidate
+ * lists take the defaults: waves {16, 32, 64, 128, 256, 1024, n_leaves},
+ * items per SM {2, 4, 8}. */
 typedef struct {
-  int32_t n_probe;          /* probe queries (2048: eight batches) */
+  int32_t n_probe;          /* probe queries (8192: 32 batches) */
   int32_t k;                /* k of the probe searches (1) */
   double noise_lo, noise_hi;/* (0.1, 0.4) */
   uint64_t seed;
-  int32_t reps;             /* timed runs per candidate (2) */
+  int32_t reps;             /* timed runs per candidate (3) */
   int32_t n_waves;          /* candidates (<= 8; 0 = defaults) */
   int32_t waves[8];
   int32_t n_items;          /* candidates (<= 4; 0 = defaults) */
   int32_t items_per_sm[4];
+  double target;            /* 0 or >= 1: exact searches; (0, 1): LeaFi searches */
 } leafi_tune_params;
 typedef struct {
   int32_t wave, items_per_sm;  /* chosen and installed */

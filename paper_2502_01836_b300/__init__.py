@@ -92,7 +92,8 @@ class IndexInfo(C.Structure):
                 ("kclasses", C.c_int32 * 4), ("device_bytes", C.c_int64),
                 ("tensor_scan", C.c_int32), ("scan_row_bytes", C.c_int32),
                 ("calib_confidence", C.c_double), ("filter_model", C.c_int32),
-                ("filter_width", C.c_int32)]
+                ("filter_width", C.c_int32), ("wave_exact", C.c_int32),
+                ("items_per_sm", C.c_int32)]
 
 
 class TrainParams(C.Structure):
@@ -120,14 +121,14 @@ class TuneParams(C.Structure):
     _fields_ = [("n_probe", C.c_int32), ("k", C.c_int32), ("noise_lo", C.c_double),
                 ("noise_hi", C.c_double), ("seed", C.c_uint64), ("reps", C.c_int32),
                 ("n_waves", C.c_int32), ("waves", C.c_int32 * 8), ("n_items", C.c_int32),
-                ("items_per_sm", C.c_int32 * 4)]
+                ("items_per_sm", C.c_int32 * 4), ("target", C.c_double)]
 
-    def __init__(self, n_probe=2048, k=1, noise_lo=0.1, noise_hi=0.4, seed=2502018361, reps=2,
-                 waves=(), items_per_sm=()):
+    def __init__(self, n_probe=8192, k=1, noise_lo=0.1, noise_hi=0.4, seed=2502018361, reps=3,
+                 waves=(), items_per_sm=(), target=1.0):
         w = (C.c_int32 * 8)(*(list(waves) + [0] * (8 - len(waves))))
         it = (C.c_int32 * 4)(*(list(items_per_sm) + [0] * (4 - len(items_per_sm))))
         super().__init__(n_probe, k, noise_lo, noise_hi, seed, reps, len(waves), w,
-                         len(items_per_sm), it)
+                         len(items_per_sm), it, target)
 
 
 class TuneReport(C.Structure):

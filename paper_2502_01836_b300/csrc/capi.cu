@@ -766,7 +766,9 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
   stat = counters;
   const HostTree& t = ix->tree;
   L = t.n_leaves;
-  W = std::min(ix->wave, std::max(L, 1));  // wider waves take every leaf all the same
+  // wider waves take every leaf all the same; calls without filtered queries
+  // take the exact searches' own width
+  W = std::min(any_filtered ? ix->wave : ix->wave_exact, std::max(L, 1));
   // the tensor-core scan merges into the top-k lists directly; the CUDA-core
   // scan appends every work item's list to a candidate buffer
   cap = tc_nbuf(ix, kmax) > 0 ? 0 : std::max(W, 1) * max_parts(ix) * kmax;
@@ -1410,7 +1412,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
       ix->m = m;
       ix->mp = (m + 3) / 4 * 4;
       ix->n = n;
-      ix->wave = p->wave;
+      ix->wave = ix->wave_exact = p->wave;
       if (p->index_type == LEAFI_DSTREE)
         ix->tree = build_dstree(series, n, m, p->leaf_capacity, p->dstree_init_segments);
       else
@@ -1427,7 +1429,7 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
     ix->m = m;
     ix->mp = (m + 3) / 4 * 4;
     ix->n = n;
-    ix->wave = p->wave;
+    ix->wave = ix->wave_exact = p->wave;
     cudaStream_t s = ix->stream;
     float* X = nullptr;
     if (!p->host_build) {
@@ -1658,6 +1660,8 @@ leafi_status leafi_get_info(const leafi_index* index, leafi_index_info* info) {
     r.n_leaves = index->tree.n_leaves;
     r.n_nodes = index->tree.n_nodes;
     r.wave = index->wave;
+    r.wave_exact = index->wave_exact;
+    r.items_per_sm = index->items_per_sm;
     r.n_filters = index->F;
     r.filters_trained = index->trained ? 1 : 0;
     r.n_calib = index->nc;
@@ -1927,6 +1931,7 @@ void install_filters(leafi_index* index, const std::vector<int32_t>& fl, int h,
   index->trained = false;
   index->nc = 0;
   index->nk = 0;
+  index->calib_q.release();
 }
 
 }  // namespace
@@ -2295,10 +2300,23 @@ void check_kclasses(const int32_t* kclasses, int32_t nk) {
   }
 }
 
-// Alg. 4 on staged calibration queries dQ [nc][mp] for the k-classes; the
-// caller holds the index mutex with the device current
-void fit_core(leafi_index* index, const float* dQ, int64_t nc, const int32_t* kclasses,
-              int32_t nk) {
+// Alg. 4 in two steps: everything that does not depend on the wave width
+// (bounds, routes, per-leaf top keys and predictions of the calibration
+// queries, the sorted alpha table) and, per wave width, the search simulation
+// that fills the q' tables.
+struct CalibState {
+  DBuf<double> lb2;
+  DBuf<int32_t> route, dl, lk_cnt, ord, cnt_true;
+  DBuf<unsigned long long> lk_keys, work;
+  DBuf<float> P;
+  DBuf<long long> hits;
+  DBuf<unsigned char> order_tmp;
+  CalibArgs a;
+  std::vector<int32_t> kc;
+};
+
+void calib_prepare(leafi_index* index, const float* dQ, int64_t nc, const int32_t* kclasses,
+                   int32_t nk, CalibState& cs) {
   if (nc < 1 || nc > calib_max_sort()) fail(LEAFI_EINVAL, "nc must be in [1, %d]", calib_max_sort());
   check_kclasses(kclasses, nk);
   const int L = index->tree.n_leaves;
@@ -2306,58 +2324,76 @@ void fit_core(leafi_index* index, const float* dQ, int64_t nc, const int32_t* kc
   cudaStream_t s = index->stream;
   const int F = index->F;
   const int kmax = kclasses[nk - 1];
-  DBuf<double> lb2;
-  DBuf<int32_t> route;
-  compute_bounds(index, dQ, (int)nc, lb2.need((size_t)nc * L), route.need(nc));
+  compute_bounds(index, dQ, (int)nc, cs.lb2.need((size_t)nc * L), cs.route.need(nc));
   std::vector<int32_t> lv((size_t)nc * L);
   for (int64_t c = 0; c < nc; ++c)
     for (int l = 0; l < L; ++l) lv[(size_t)c * L + l] = l;
-  DBuf<int32_t> dl;
-  dl.upload(lv, s);
-  DBuf<unsigned long long> lk_keys;
-  DBuf<int32_t> lk_cnt;
-  leaf_knn_device(index, dQ, (int)nc, dl.p, L, kmax, lk_keys, lk_cnt);
-  DBuf<float> P;
+  cs.dl.upload(lv, s);
+  leaf_knn_device(index, dQ, (int)nc, cs.dl.p, L, kmax, cs.lk_keys, cs.lk_cnt);
   ensure_wsplit(index);
-  filter_forward(index, dQ, (int)nc, P.need((size_t)nc * F));
-  double* alpha = index->alpha.need((size_t)F * nc);
-  double* qprime = index->qprime.need((size_t)nk * nc);
-  DBuf<int32_t> ord, cnt_true;
-  DBuf<unsigned long long> work;
-  DBuf<long long> hits;
-  DBuf<unsigned char> order_tmp;
-  CalibArgs a;
-  a.order_scratch = L > calib_max_sort() ? order_tmp.need(leaf_order_scratch((int)nc, L)) : nullptr;
+  filter_forward(index, dQ, (int)nc, cs.P.need((size_t)nc * F));
+  CalibArgs& a = cs.a;
+  a = CalibArgs();
+  a.order_scratch =
+      L > calib_max_sort() ? cs.order_tmp.need(leaf_order_scratch((int)nc, L)) : nullptr;
   a.nc = (int)nc;
   a.L = L;
   a.F = F;
   a.W = index->wave;
-  a.lb2 = lb2.p;
-  a.route = route.p;
-  a.lk = lk_keys.p;
+  a.lb2 = cs.lb2.p;
+  a.route = cs.route.p;
+  a.lk = cs.lk_keys.p;
   a.lk_stride = kmax;
-  a.P = P.p;
+  a.P = cs.P.p;
   a.filter_leaf = index->d_filter_leaf.p;
   a.leaf_filter = index->d_leaf_filter.p;
-  a.alpha = alpha;
-  a.ord = ord.need((size_t)nc * L);
-  a.cnt_true = cnt_true.need((size_t)nc * L);
-  a.hits = hits.need(nc);
+  a.alpha = index->alpha.need((size_t)F * nc);
+  a.ord = cs.ord.need((size_t)nc * L);
+  a.cnt_true = cs.cnt_true.need((size_t)nc * L);
+  a.hits = cs.hits.need(nc);
   a.kc = 1;
   launch_calib_alpha(a, s);
+  cs.kc.assign(kclasses, kclasses + nk);
+}
+
+// q' tables for wave width W (installed on the index with the k-classes)
+void calib_simulate(leafi_index* index, CalibState& cs, int W) {
+  cudaStream_t s = index->stream;
+  CalibArgs& a = cs.a;
+  const int nk = (int)cs.kc.size();
+  const int64_t nc = a.nc;
+  index->drop_graphs();
+  double* qprime = index->qprime.need((size_t)nk * nc);
+  a.W = W;
   for (int ci = 0; ci < nk; ++ci) {
-    a.kc = kclasses[ci];
+    a.kc = cs.kc[ci];
     a.kk = (int)std::min<int64_t>(a.kc, index->n);
-    a.work = work.need(std::max((size_t)nc * nc * a.kc, (size_t)nc * L / 2 + 1));
+    a.work = cs.work.need(std::max((size_t)nc * nc * a.kc, (size_t)nc * a.L / 2 + 1));
     a.qprime = qprime + (size_t)ci * nc;
     launch_calib_sim(a, s);
   }
-  std::vector<int32_t> kc(kclasses, kclasses + nk);
-  index->d_kclasses.upload(kc, s);
+  index->d_kclasses.upload(cs.kc, s);
   LF_CUDA(cudaStreamSynchronize(s));
   index->nc = (int)nc;
   index->nk = nk;
-  for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? kclasses[i] : 0;
+  for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? cs.kc[i] : 0;
+  index->rq_cache.clear();
+}
+
+// Alg. 4 on staged calibration queries dQ [nc][mp] for the k-classes at the
+// index's wave width; the queries are kept for later refits.  The caller holds
+// the index mutex with the device current.
+void fit_core(leafi_index* index, const float* dQ, int64_t nc, const int32_t* kclasses,
+              int32_t nk) {
+  CalibState cs;
+  calib_prepare(index, dQ, nc, kclasses, nk, cs);
+  calib_simulate(index, cs, index->wave);
+  if (dQ != index->calib_q.p) {
+    float* keep = index->calib_q.need((size_t)nc * index->mp);
+    LF_CUDA(cudaMemcpyAsync(keep, dQ, sizeof(float) * nc * index->mp, cudaMemcpyDeviceToDevice,
+                            index->stream));
+    LF_CUDA(cudaStreamSynchronize(index->stream));
+  }
 }
 
 }  // namespace
@@ -2482,12 +2518,17 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// the search-schedule autotuner (leafi_tune_search); caller holds the mutex
+// the search-schedule autotuner (leafi_tune_search); caller holds the mutex.
+// Exact mode times exact searches and sets the exact searches' wave width (and
+// the index's while no tables are fitted); LeaFi mode times searches at the
+// target after refitting the tables for every candidate wave width.
 void tune_core(leafi_index* ix, const leafi_tune_params* p, leafi_tune_report* rep) {
-  if (ix->nc > 0) fail(LEAFI_EINVAL, "tune the search before fitting the auto-tuners");
+  const bool leafi_mode = p->target > 0.0 && p->target < 1.0;
   if (p->n_probe < 1 || p->k < 1 || p->k > LEAFI_MAX_K || p->reps < 1 || p->n_waves < 0 ||
-      p->n_waves > 8 || p->n_items < 0 || p->n_items > 4)
+      p->n_waves > 8 || p->n_items < 0 || p->n_items > 4 || !(p->target >= 0.0))
     fail(LEAFI_EINVAL, "bad tuning parameters");
+  if (leafi_mode && (ix->F == 0 || ix->nc == 0 || !ix->calib_q.p))
+    fail(LEAFI_EINVAL, "LeaFi-mode tuning needs auto-tuners fitted from calibration queries");
   const int L = ix->tree.n_leaves;
   std::vector<int> waves, items;
   if (p->n_waves) waves.assign(p->waves, p->waves + p->n_waves);
@@ -2524,12 +2565,27 @@ void tune_core(leafi_index* ix, const leafi_tune_params* p, leafi_tune_report* r
   oi.need((size_t)p->n_probe * p->k);
   od.need((size_t)p->n_probe * p->k);
   std::vector<int32_t> kq(p->n_probe, p->k);
-  std::vector<double> tg(p->n_probe, 1.0);
-  const int w0 = ix->wave, i0 = ix->items_per_sm;
-  auto time_it = [&](int w, int ips) {
-    if (w != ix->wave || ips != ix->items_per_sm) ix->drop_graphs();
-    ix->wave = w;
+  std::vector<double> tg(p->n_probe, leafi_mode ? p->target : 1.0);
+  // LeaFi mode: the wave-independent half of Alg. 4, from the kept queries
+  CalibState cs;
+  int fitted_w = ix->wave;
+  if (leafi_mode) {
+    const std::vector<int32_t> kc(ix->kclasses, ix->kclasses + ix->nk);
+    calib_prepare(ix, ix->calib_q.p, ix->nc, kc.data(), ix->nk, cs);
+  }
+  int& wave = leafi_mode ? ix->wave : ix->wave_exact;
+  const int w0 = wave, i0 = ix->items_per_sm;
+  auto install = [&](int w, int ips) {
+    if (w != wave || ips != ix->items_per_sm) ix->drop_graphs();
+    wave = w;
     ix->items_per_sm = ips;
+    if (leafi_mode && fitted_w != w) {
+      calib_simulate(ix, cs, w);
+      fitted_w = w;
+    }
+  };
+  auto time_it = [&](int w, int ips) {
+    install(w, ips);
     search_impl(ix, dQ, p->n_probe, kq, tg, p->k, oi.p, od.p, nullptr);  // warm-up
     double best = std::numeric_limits<double>::infinity();
     for (int r = 0; r < p->reps; ++r) {
@@ -2559,16 +2615,17 @@ void tune_core(leafi_index* ix, const leafi_tune_params* p, leafi_tune_report* r
           bi = v;
         }
       }
-    if (bw != ix->wave || bi != ix->items_per_sm) ix->drop_graphs();
-    ix->wave = bw;
-    ix->items_per_sm = bi;
+    install(bw, bi);
+    // exact mode on an index without tables sets the width of every call
+    if (!leafi_mode && ix->nc == 0) ix->wave = bw;
     r.wave = bw;
     r.items_per_sm = bi;
     r.ms_best = bms;
   } catch (...) {
     ix->drop_graphs();
-    ix->wave = w0;
     ix->items_per_sm = i0;
+    wave = w0;
+    if (leafi_mode && fitted_w != w0) calib_simulate(ix, cs, w0);
     throw;
   }
   if (rep) *rep = r;
@@ -2576,12 +2633,13 @@ void tune_core(leafi_index* ix, const leafi_tune_params* p, leafi_tune_report* r
 
 leafi_tune_params default_tune_params(uint64_t seed) {
   leafi_tune_params t{};
-  t.n_probe = 2048;
+  t.n_probe = 8192;
   t.k = 1;
   t.noise_lo = 0.1;
   t.noise_hi = 0.4;
   t.seed = seed;
-  t.reps = 2;
+  t.reps = 3;
+  t.target = 1.0;
   return t;
 }
 
@@ -2661,14 +2719,20 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     train_core(index, &sp, dQg, dQl, hperm, ep.data(), bv.data());
     rep.seconds_train = seconds_since(t0);
     t0 = std::chrono::steady_clock::now();
-    // the search schedule the auto-tuners will calibrate
+    // the exact searches' schedule
     if (p->tune_search) {
       const leafi_tune_params tp = default_tune_params(p->seed);
       tune_core(index, &tp, nullptr);
     }
     // line 10: auto-tuners on the calibration set (the global validation queries)
-    fit_core(index, dQg + (size_t)c.n_gtrain * index->mp, c.n_gval, p->kclasses, p->n_kclasses);
     index->calib_confidence = p->confidence;
+    fit_core(index, dQg + (size_t)c.n_gtrain * index->mp, c.n_gval, p->kclasses, p->n_kclasses);
+    // the LeaFi searches' schedule (the tables are refitted for each candidate)
+    if (p->tune_search) {
+      leafi_tune_params tp = default_tune_params(p->seed);
+      tp.target = 0.99;
+      tune_core(index, &tp, nullptr);
+    }
     index->rq_cache.clear();
     rep.seconds_calibrate = seconds_since(t0);
     rep.n_filters = F;
@@ -2880,6 +2944,8 @@ leafi_status leafi_set_autotuners(leafi_index* index, const double* alpha_sorted
     index->nc = (int)nc;
     index->nk = nk;
     for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? kc[i] : 0;
+    index->calib_q.release();  // these tables come without their calibration queries
+    index->rq_cache.clear();
   });
 }
 

@@ -438,6 +438,7 @@ struct leafi_index {
   cudaStream_t stream = nullptr;
   leafi::HostTree tree;
   int m = 0, mp = 0, wave = 8, scan_path = 0;
+  int wave_exact = 8;      // wave width of calls without filtered queries (tuned on its own)
   int64_t n = 0;
 
   // resident data
@@ -477,6 +478,8 @@ struct leafi_index {
   int kclasses[LEAFI_MAX_KCLASSES] = {0, 0, 0, 0};
   leafi::DBuf<double> alpha, qprime;
   leafi::DBuf<int32_t> d_kclasses;
+  leafi::DBuf<float> calib_q;    // the calibration queries [nc][mp] behind the tables (kept so
+                                 // that the tables can be refitted for another wave width)
 
   // scratch (grown on demand): lanes[0] serves every entry point; a search of
   // more than one batch spreads its batches over several lanes in turn

@@ -698,7 +698,10 @@ def test_query_schedule_keeps_every_result(ds, tuned):
 def test_search_schedule_autotuner():
     """leafi_tune_search times exact searches of probe queries for every
     (wave, items per SM) candidate and installs the fastest; exact results do
-    not depend on the choice; an index with fitted auto-tuners is refused."""
+    not depend on the choice.  With fitted tables, exact-mode tuning sets only
+    the exact searches' width, and LeaFi-mode tuning refits the tables for each
+    candidate width: the installed tables equal a fresh fit at the chosen one.
+    Tables set without their calibration queries refuse LeaFi-mode tuning."""
     X = fx.random_walk(40000, 128, seed=131)
     Q = fx.test_queries(X, 300, seed=132)
     idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=1500, wave=4, device=0))
@@ -711,16 +714,32 @@ def test_search_schedule_autotuner():
         assert rep["ms_best"] <= best[2] and rep["ms_best"] <= rep["ms_before"]
         info = lf.leafi_get_info(idx)
         # candidates wider than the index take every leaf (clamped to n_leaves)
-        assert info.wave == rep["wave"]
+        assert info.wave == info.wave_exact == rep["wave"]
         assert rep["wave"] in (2, 4, 8, min(64, info.n_leaves))
         ids, d, _ = _exact(idx, Q, 3)
         assert np.array_equal(ids, bf) and np.array_equal(d, np.sqrt(bf_d2))
         L = info.n_leaves
+        assert L > 4
         lf.leafi_set_filters(idx, lf.leafi_select_leaves(idx, 4),
                              *fx.filter_init(4, 128, 128, seed=133))
         lf.leafi_fit_autotuners(idx, Q[:50], [1])
+        w_leafi = lf.leafi_get_info(idx).wave
+        rep2 = lf.leafi_tune_search(idx, lf.TuneParams(n_probe=64, reps=1, waves=(2, 8)))
+        info = lf.leafi_get_info(idx)
+        assert info.wave_exact == rep2["wave"] and info.wave == w_leafi
+        rep3 = lf.leafi_tune_search(idx, lf.TuneParams(n_probe=128, reps=1, waves=(2, 8, 64),
+                                                       items_per_sm=(4,), target=0.9))
+        info = lf.leafi_get_info(idx)
+        assert info.wave == rep3["wave"] and len(rep3["tried"]) == 3
+        a1, q1 = np.zeros((4, 50)), np.zeros((1, 50))
+        lf.leafi_get_autotuners(idx, a1, q1)
+        lf.leafi_fit_autotuners(idx, Q[:50], [1])
+        a2, q2 = np.zeros((4, 50)), np.zeros((1, 50))
+        lf.leafi_get_autotuners(idx, a2, q2)
+        assert np.array_equal(a1, a2) and np.array_equal(q1, q2)
+        lf.leafi_set_autotuners(idx, a1, q1, [1])
         with pytest.raises(lf.LeafiError) as e:
-            lf.leafi_tune_search(idx, lf.TuneParams(n_probe=64, reps=1))
-        assert e.value.status == 1 and L > 4
+            lf.leafi_tune_search(idx, lf.TuneParams(n_probe=64, reps=1, target=0.9))
+        assert e.value.status == 1
     finally:
         lf.leafi_free(idx)
