@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-schedule", action="store_true",
                     help="batches in the callers' query order (no route-leaf scheduling)")
     ap.add_argument("--lanes", type=int, default=8, help="batches of one call in flight")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="queries per internal batch of a call (default: --launch)")
     ap.add_argument("--part", type=int, default=2048, help="series per leaf-scan work item")
     ap.add_argument("--items-per-sm", type=int, default=4,
                     help="scan work items per SM a round aims at (0: fixed part)")
@@ -734,6 +736,7 @@ def main():
     lf.leafi_set_stream(idx, stream.cuda_stream)
     lf.leafi_set_query_schedule(idx, not a.no_schedule)
     lf.leafi_set_search_lanes(idx, a.lanes)
+    lf.leafi_set_search_batch(idx, a.batch or a.launch)
     lf.leafi_set_scan_part(idx, a.part, a.items_per_sm, a.min_part, a.scan_blocks)
     t_train = time.perf_counter()
     enh = enhance(idx, a.filters, kclasses=(1,), max_epochs=a.epochs, tune_search=int(a.tune))

@@ -501,6 +501,16 @@ leafi_status leafi_set_search_lanes(leafi_index* index, int32_t lanes);
 leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items_per_sm,
                                  int32_t min_rows, int32_t blocks);
 
+/* Queries per batch of a search call, 1..4096 (default 256).  A batch is
+ * one unit of Alg. 2 on the device: one launch of each of its bound, filter
+ * and preparation kernels, then waves of leaf-scan rounds over all of its
+ * queries, so a leaf that several of its queries need is read once per wave
+ * for all of them.  Each query is searched on its own terms (its own route
+ * leaf, bound, offsets and best-so-far), so results do not depend on the
+ * batch size; larger batches read fewer bytes per query, smaller ones answer
+ * sooner. */
+leafi_status leafi_set_search_batch(leafi_index* index, int32_t queries);
+
 /* Query scheduling of calls with more than one internal batch (on by
  * default): the batches are cut from the queries in order of their route
  * leaf, so that each batch's queries need largely the same leaves and the

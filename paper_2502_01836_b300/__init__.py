@@ -31,6 +31,7 @@ __all__ = [
     "leafi_get_filter_leaves", "leafi_debug_set_lock_tries", "leafi_debug_fail_allocations",
     "leafi_set_calibration_confidence", "leafi_set_query_schedule", "leafi_set_search_lanes",
     "leafi_set_scan_part", "leafi_tune_search", "TuneParams", "TuneReport",
+    "leafi_set_search_batch",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -59,7 +60,7 @@ EXPORTED_SYMBOLS = [
     "leafi_debug_fail_allocations", "leafi_set_calibration_confidence",
     "leafi_set_query_schedule", "leafi_set_search_lanes", "leafi_set_scan_part",
     "leafi_tune_search", "leafi_cnn_params", "leafi_set_cnn_filters", "leafi_get_cnn_filters",
-    "leafi_initial_cnn_weights",
+    "leafi_initial_cnn_weights", "leafi_set_search_batch",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -229,6 +230,7 @@ def lib():
             "leafi_set_query_schedule": [vp, i32],
             "leafi_set_search_lanes": [vp, i32],
             "leafi_set_scan_part": [vp, i32, i32, i32, i32],
+            "leafi_set_search_batch": [vp, i32],
             "leafi_tune_search": [vp, C.POINTER(TuneParams), C.POINTER(TuneReport)],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
@@ -469,6 +471,11 @@ def leafi_set_query_schedule(index, on=True):
 def leafi_set_search_lanes(index, lanes):
     """Batches of one search call in flight (1..8)."""
     _check(lib().leafi_set_search_lanes(index, int(lanes)))
+
+
+def leafi_set_search_batch(index, queries=256):
+    """Queries per internal batch of a search call (results do not depend on it)."""
+    _check(lib().leafi_set_search_batch(index, int(queries)))
 
 
 def leafi_set_scan_part(index, rows=2048, items_per_sm=4, min_rows=512, blocks=0):

@@ -28,7 +28,7 @@ unsigned long long g_realloc_epoch = 0;
 
 namespace {
 thread_local std::string g_last_error;
-constexpr int kBatch = 256;       // queries per search batch
+constexpr int kBatch = 256;       // queries per search batch (default; a server's maximum)
 constexpr int kSearchLanes = 8;   // batches of one search call in flight
 constexpr int kServeLanes = 4;    // batches of a server in flight
 constexpr size_t kKnnBudget = 256ull << 20;  // bytes of candidate buffer per leaf-knn batch
@@ -727,7 +727,7 @@ struct Pipeline {
 
   // size every buffer of a full batch on each lane (before any graph capture)
   void setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k_max, bool any_filtered,
-             unsigned long long* counters);
+             unsigned long long* counters, int batch = kBatch);
   void use_lane(int li);
   void make_sa(const LaneView& v, int nb, bool use_f);
   void select(const LaneView& v);
@@ -758,7 +758,7 @@ namespace {
 }  // namespace
 
 void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k_max,
-                     bool any_filtered, unsigned long long* counters) {
+                     bool any_filtered, unsigned long long* counters, int batch) {
   ix = index;
   lanes = lane_array;
   nlanes = n_lanes;
@@ -772,7 +772,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
   // the tensor-core scan merges into the top-k lists directly; the CUDA-core
   // scan appends every work item's list to a candidate buffer
   cap = tc_nbuf(ix, kmax) > 0 ? 0 : std::max(W, 1) * max_parts(ix) * kmax;
-  qb = kBatch;
+  qb = batch;
   for (int li = 0; li < nlanes; ++li) {
     Scratch& S = lanes[li];
     if (!S.st) {
@@ -1107,7 +1107,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   if (any_filtered && (ix->nc == 0 || ix->F == 0))
     fail(LEAFI_ENOTTRAINED, "recall_target < 1 needs fitted auto-tuners");
   if (any_filtered) ensure_wsplit(ix);
-  const int qb = kBatch;
+  const int qb = ix->search_batch;
   const int nlanes = (int)std::min<int64_t>(ix->search_lanes, (nq + qb - 1) / qb);
   const cudaStream_t user = ix->stream;
   // every entry point after this one runs on lanes[0] and the caller's stream
@@ -1122,7 +1122,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   } restore{ix, user};
   unsigned long long* stat = ix->sStat.need(4);
   Pipeline pl;
-  pl.setup(ix, ix->lanes, nlanes, kmax, any_filtered, stat);
+  pl.setup(ix, ix->lanes, nlanes, kmax, any_filtered, stat, qb);
   const bool uniform =
       std::all_of(kq.begin(), kq.end(), [&](int32_t v) { return v == kq[0]; }) &&
       std::all_of(target.begin(), target.end(), [&](double v) { return v == target[0]; });
@@ -2881,6 +2881,16 @@ leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items
     index->items_per_sm = items_per_sm;
     index->min_part = min_rows;
     index->scan_blocks = blocks;
+  });
+}
+
+leafi_status leafi_set_search_batch(leafi_index* index, int32_t queries) {
+  return guarded([&] {
+    require_device(index);
+    if (queries < 1 || queries > 4096) fail(LEAFI_EINVAL, "queries must be in [1, 4096]");
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->drop_graphs();
+    index->search_batch = queries;
   });
 }
 

@@ -495,6 +495,7 @@ struct leafi_index {
 
   bool schedule = true;    // multi-batch calls cut batches in route-leaf order
   int search_lanes = 8;    // batches of one search call in flight (leafi_set_search_lanes)
+  int search_batch = 256;  // queries per batch of a search call (leafi_set_search_batch)
   int part = 2048;         // series per scan work item (leafi_set_scan_part); the tensor-core
                            // scan's rounds may take part / 2, ... (>= 128) for balance
   int items_per_sm = 4;    // work items per SM a tensor-core round aims at

@@ -743,3 +743,29 @@ def test_search_schedule_autotuner():
         assert e.value.status == 1
     finally:
         lf.leafi_free(idx)
+
+
+def test_search_batch_size_keeps_every_result(ds, tuned):
+    """Every query is searched on its own terms, so the batch size of a call
+    (and with it how many queries share a wave's leaf reads) changes no result:
+    exact and LeaFi searches of 700 queries in batches of 37, 256 and 700."""
+    X, Q, idx, t = ds
+    fl, Wt, Qc, tables = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_fit_autotuners(idx, Qc, [1, 10])
+    lf.leafi_set_calibration_confidence(idx, 0.0)
+    Q2 = fx.test_queries(X, 700, seed=141)
+    try:
+        for k, target in ((1, 1.0), (1, 0.9), (10, 0.95)):
+            res = []
+            for b in (37, 256, 700):
+                lf.leafi_set_search_batch(idx, b)
+                ids = np.zeros((700, k), np.int64)
+                d = np.zeros((700, k), np.float32)
+                lf.leafi_search(idx, Q2, k, target, ids, d)
+                res.append((ids, d))
+            for ids, d in res[1:]:
+                assert np.array_equal(ids, res[0][0]) and np.array_equal(d, res[0][1]), (k, target)
+    finally:
+        lf.leafi_set_search_batch(idx, 256)
+        lf.leafi_set_calibration_confidence(idx, 0.95)
