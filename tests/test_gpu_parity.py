@@ -57,6 +57,19 @@ def test_lower_bounds_and_routes_bit_exact(ds):
     assert np.array_equal(r, t.route(Q))
 
 
+@pytest.mark.parametrize("nq", [1, 7, 37])
+def test_bounds_ragged_query_tiles(ds, nq):
+    """Query counts that leave the last tile of the one-launch DSTree bounds
+    kernel partly empty."""
+    X, Q, idx, t = ds
+    lb = np.zeros((nq, t.L), np.float64)
+    lf.leafi_leaf_lower_bounds(idx, Q[:nq], lb)
+    assert np.array_equal(lb, t.lb2(Q[:nq]))
+    r = np.zeros(nq, np.int32)
+    lf.leafi_route(idx, Q[:nq], r)
+    assert np.array_equal(r, t.route(Q[:nq]))
+
+
 @pytest.mark.parametrize("k", [1, 10, 100])
 def test_exact_search_bit_exact(ds, k):
     X, Q, idx, t = ds
@@ -407,6 +420,10 @@ def test_more_than_4096_leaves(wave):
         t = O.Tree(X, "dstree", leaf_cap=10, init_segments=4)
         assert t.L > 4096
         assert np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
+        # bounds of a tree too large for the one-launch bounds kernel
+        lb = np.zeros((37, t.L), np.float64)
+        lf.leafi_leaf_lower_bounds(idx, Q[:37], lb)
+        assert np.array_equal(lb, t.lb2(Q[:37]))
         ids = np.zeros((300, 5), np.int64)
         d = np.zeros((300, 5), np.float32)
         st = lf.SearchStats()
