@@ -405,7 +405,8 @@ def run_serving(a):
            "config": {"workload": "DSTree over %d random walks x %d, leaf capacity %d, filters on "
                                   "the %d largest leaves, single-query requests with k ~ U{1..100} "
                                   "and target in {0.9, 0.95, 0.99, exact}" % (a.n, M, a.leaf_cap, F),
-                      "leaves": info.n_leaves, "max_batch": a.launch, "max_wait_ms": a.max_wait_ms},
+                      "leaves": info.n_leaves, "max_batch": a.launch, "max_wait_ms": a.max_wait_ms,
+                      "wave": lf.leafi_get_info(idx).wave, "tuned": bool(a.tune)},
            "rates": rows, "data": "synthetic",
            "build_s": {"data": t_data, "index": t_build, "train_and_tune": t_train},
            "device_bytes": info.device_bytes})
@@ -499,7 +500,10 @@ def run_mixed(a):
                                   "{0.9,0.95,0.99}" % (a.n, M, a.leaf_cap, a.queries),
                       "leaves": info.n_leaves, "leaf_size_min_median_max":
                           [int(sizes.min()), float(np.median(sizes)), int(sizes.max())],
-                      "filters": F, "wave": a.wave, "scan_path": a.scan_path},
+                      "filters": F, "scan_path": a.scan_path,
+                      "wave": lf.leafi_get_info(idx).wave if a.tune else a.wave,
+                      "wave_exact": lf.leafi_get_info(idx).wave_exact,
+                      "tuned": bool(a.tune)},
            "build_s": {"data": t_data, "index": t_build, "train_and_tune": t_train},
            "data": "synthetic"})
     lf.leafi_free(idx)
