@@ -684,9 +684,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(
       PROF_ADD(12);
       unsigned char* Bt = b ? B1 : B0;
       // every 16-byte piece of the tile is an asynchronous copy (rows beyond the
-      // group are zero-filled), so all of them are in flight at once
+      // group are zero-filled), so all of them are in flight at once; the
+      // group's query rows (at most 64) are read two per lane up front and
+      // broadcast, rather than one dependent load per row
+      const int r_lo = lane < I.nqg ? I.pr[lane].q : -1;
+      const int r_hi = lane + 32 < I.nqg ? I.pr[lane + 32].q : -1;
       for (int qq = 0; qq < I.N; ++qq) {
-        const int row = qq < I.nqg ? I.pr[qq].q : -1;
+        const int row = __shfl_sync(0xffffffffu, qq < 32 ? r_lo : r_hi, qq & 31);
         const unsigned char* src = qops + (size_t)(row >= 0 ? row : 0) * RB;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
