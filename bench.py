@@ -43,9 +43,10 @@ SMS = 148
 FP32_LANES = 128
 # DRAM bytes (read + write) per tensor-core leaf-scan launch on the default
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
-# eight consecutive launches of the timed region, averaged), valid only for the
-# kernel code it was taken on (SHA-1 of k_scan_tc.cu without comments and blank lines)
-SCAN_TRAFFIC = {"bytes_per_launch": 418.2e6, "kernel_sha1": "934ae00f3214b2480e6b5d7011d0e1b581bb29d0",
+# every scan launch of the timed LeaFi region at W = 64, averaged), valid only
+# for the kernel code it was taken on (SHA-1 of k_scan_tc.cu without comments
+# and blank lines)
+SCAN_TRAFFIC = {"bytes_per_launch": 161.0e6, "kernel_sha1": "d41d88c9e71982ee4be88eef50efc8552b125c31",
                 "source": "stored ncu capture (profiles/leaf_scan_tc_dram_1M.md), not measured "
                           "in this run"}
 
