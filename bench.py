@@ -339,7 +339,8 @@ def run_serving(a):
     t_train = time.perf_counter() - t0
     kmax = 100
     lf.leafi_set_profiling(idx, 2)
-    sv = lf.leafi_serve_start(idx, kmax=kmax, max_batch=a.launch, max_wait_ms=a.max_wait_ms)
+    sv = lf.leafi_serve_start(idx, kmax=kmax, max_batch=a.batch or a.launch,
+                              max_wait_ms=a.max_wait_ms)
     rows = []
     try:
         for ri, lam in enumerate(float(x) for x in a.rates.split(",")):
@@ -406,7 +407,8 @@ def run_serving(a):
            "config": {"workload": "DSTree over %d random walks x %d, leaf capacity %d, filters on "
                                   "the %d largest leaves, single-query requests with k ~ U{1..100} "
                                   "and target in {0.9, 0.95, 0.99, exact}" % (a.n, M, a.leaf_cap, F),
-                      "leaves": info.n_leaves, "max_batch": a.launch, "max_wait_ms": a.max_wait_ms,
+                      "leaves": info.n_leaves, "max_batch": a.batch or a.launch,
+                      "max_wait_ms": a.max_wait_ms,
                       "wave": lf.leafi_get_info(idx).wave, "tuned": bool(a.tune)},
            "rates": rows, "data": "synthetic",
            "build_s": {"data": t_data, "index": t_build, "train_and_tune": t_train},

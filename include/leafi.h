@@ -550,7 +550,8 @@ leafi_status leafi_search_mixed(leafi_index* index, const float* queries, int64_
 typedef struct leafi_server leafi_server;
 
 typedef struct {
-  int32_t max_batch;    /* queries per batch, 1..256 (default 256) */
+  int32_t max_batch;    /* queries per batch, 1..4096 (default 256; larger batches share
+                           each wave's leaf reads among more queries) */
   int32_t kmax;         /* largest k of any request, 1..LEAFI_MAX_K; results are [nq][kmax] */
   double max_wait_ms;   /* a partial batch waits at most this long for company (default 0.2) */
   int64_t max_bytes;    /* admission budget: host bytes of queries and results of the requests

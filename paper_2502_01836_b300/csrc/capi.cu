@@ -28,7 +28,8 @@ unsigned long long g_realloc_epoch = 0;
 
 namespace {
 thread_local std::string g_last_error;
-constexpr int kBatch = 256;       // queries per search batch (default; a server's maximum)
+constexpr int kBatch = 256;       // queries per search batch (default)
+constexpr int kMaxBatch = 4096;   // largest batch of a search call or a server
 constexpr int kSearchLanes = 8;   // batches of one search call in flight
 constexpr int kServeLanes = 4;    // batches of a server in flight
 constexpr size_t kKnnBudget = 256ull << 20;  // bytes of candidate buffer per leaf-knn batch
@@ -2887,7 +2888,7 @@ leafi_status leafi_set_scan_part(leafi_index* index, int32_t rows, int32_t items
 leafi_status leafi_set_search_batch(leafi_index* index, int32_t queries) {
   return guarded([&] {
     require_device(index);
-    if (queries < 1 || queries > 4096) fail(LEAFI_EINVAL, "queries must be in [1, 4096]");
+    if (queries < 1 || queries > kMaxBatch) fail(LEAFI_EINVAL, "queries must be in [1, %d]", kMaxBatch);
     std::lock_guard<std::mutex> lk(index->mu);
     index->drop_graphs();
     index->search_batch = queries;
@@ -3127,7 +3128,8 @@ void serve_loop(leafi_server* sv) {
         on_index(sv, [&] {
           leafi::DeviceGuard dg(ix->device);
           if (use_f) leafi::ensure_wsplit(ix);
-          sv->pl.setup(ix, sv->lanes, kServeLanes, kmax, ix->F > 0 && ix->nc > 0, sv->stat.p);
+          sv->pl.setup(ix, sv->lanes, kServeLanes, kmax, ix->F > 0 && ix->nc > 0, sv->stat.p,
+                       sv->p.max_batch);
           sv->pl.start(li, sv->hq[li], nb, sv->hk[li], sv->ht[li], false, sv->hi[li], sv->hd[li]);
         });
         next = (next + 1) % kServeLanes;
@@ -3186,7 +3188,8 @@ leafi_status leafi_serve_start(leafi_index* index, const leafi_serve_params* par
     if (!out) fail(LEAFI_EINVAL, "out is NULL");
     leafi_serve_params p{256, 1, 0.2, 0};
     if (params) p = *params;
-    if (p.max_batch < 1 || p.max_batch > kBatch) fail(LEAFI_EINVAL, "max_batch must be in [1, %d]", kBatch);
+    if (p.max_batch < 1 || p.max_batch > kMaxBatch)
+      fail(LEAFI_EINVAL, "max_batch must be in [1, %d]", kMaxBatch);
     if (p.kmax < 1 || p.kmax > LEAFI_MAX_K) fail(LEAFI_EINVAL, "kmax must be in [1, %d]", LEAFI_MAX_K);
     if (!(p.max_wait_ms >= 0.0)) fail(LEAFI_EINVAL, "max_wait_ms must be >= 0");
     if (p.max_bytes <= 0) p.max_bytes = (int64_t)1 << 30;
@@ -3198,11 +3201,12 @@ leafi_status leafi_serve_start(leafi_index* index, const leafi_serve_params* par
       sv->stat.need(4);
       LF_CUDA(cudaMemset(sv->stat.p, 0, 4 * sizeof(unsigned long long)));
       for (int li = 0; li < kServeLanes; ++li) {
-        LF_CUDA(cudaMallocHost(&sv->hq[li], sizeof(float) * kBatch * index->m));
-        LF_CUDA(cudaMallocHost(&sv->hk[li], sizeof(int32_t) * kBatch));
-        LF_CUDA(cudaMallocHost(&sv->ht[li], sizeof(double) * kBatch));
-        LF_CUDA(cudaMallocHost(&sv->hi[li], sizeof(int64_t) * kBatch * p.kmax));
-        LF_CUDA(cudaMallocHost(&sv->hd[li], sizeof(float) * kBatch * p.kmax));
+        const size_t b = (size_t)p.max_batch;
+        LF_CUDA(cudaMallocHost(&sv->hq[li], sizeof(float) * b * index->m));
+        LF_CUDA(cudaMallocHost(&sv->hk[li], sizeof(int32_t) * b));
+        LF_CUDA(cudaMallocHost(&sv->ht[li], sizeof(double) * b));
+        LF_CUDA(cudaMallocHost(&sv->hi[li], sizeof(int64_t) * b * p.kmax));
+        LF_CUDA(cudaMallocHost(&sv->hd[li], sizeof(float) * b * p.kmax));
       }
     }
     sv->worker = std::thread(serve_loop, sv.get());

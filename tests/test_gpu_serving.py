@@ -32,7 +32,8 @@ def _alone(idx, Q, k, t):
     return ids, d
 
 
-def test_results_alone_equal_results_in_the_mix(served):
+@pytest.mark.parametrize("max_batch", [256, 700])
+def test_results_alone_equal_results_in_the_mix(served, max_batch):
     X, idx = served
     rng = np.random.default_rng(82)
     reqs = []
@@ -42,7 +43,7 @@ def test_results_alone_equal_results_in_the_mix(served):
         k = rng.choice([1, 5, 10, 20], nq).astype(np.int32)
         t = rng.choice([0.9, 0.95, 0.99, 1.0], nq).astype(np.float64)
         reqs.append((Q, k, t))
-    sv = lf.leafi_serve_start(idx, kmax=KMAX, max_batch=256, max_wait_ms=0.5)
+    sv = lf.leafi_serve_start(idx, kmax=KMAX, max_batch=max_batch, max_wait_ms=0.5)
     try:
         tickets = [None] * len(reqs)
 
