@@ -974,12 +974,18 @@ def main():
             "recall_at_1": recall,
             "plain_lb": {"value": value_ex, "unit": "queries/s", "ms_per_step": ms_ex_max,
                          "series_scanned_per_query": st_ex["series_scanned"] / (a.steps * a.queries),
+                         "distinct_bytes_per_batch": st_ex["distinct_series"] * info.scan_row_bytes
+                                                     / max(st_ex["batches"], 1),
                          "p50_ms": float(np.percentile(lat_ex, 50)),
                          "p99_ms": float(np.percentile(lat_ex, 99))},
             "speedup_vs_plain_lb": value / value_ex,
             "latency_per_launch_ms": {"p50": float(np.percentile(lat_sorted, 50)),
                                       "p99": float(np.percentile(lat_sorted, 99))},
             "series_scanned_per_query": st["series_scanned"] / (a.steps * a.queries),
+            # bytes of the distinct series a batch's rounds read (a series read in two
+            # rounds counts twice), LeaFi here and plain-LB above
+            "distinct_bytes_per_batch": st["distinct_series"] * info.scan_row_bytes
+                                        / max(st["batches"], 1),
             "rechecks_per_query": st["rechecks"] / (a.steps * a.queries),
             "pruning_ratio": 1.0 - st["series_scanned"] / (a.steps * a.queries * a.n),
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),

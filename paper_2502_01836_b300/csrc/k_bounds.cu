@@ -83,6 +83,39 @@ __global__ void ds_node_kernel(DsTables T, const double* __restrict__ ivstat, in
   node_lb[t] = acc;
 }
 
+// The same node bounds with each thread taking one node for a tile of QT
+// queries: a node's synopses are read once per tile instead of once per query
+// (on large trees the synopses, not the arithmetic, are the traffic), and each
+// (query, node) sum runs over the node's segments in the same order as
+// ds_node_kernel, so the values are bit-identical.
+template <int QT>
+__global__ void ds_node_tiled_kernel(DsTables T, const double* __restrict__ ivstat, int nq,
+                                     double* __restrict__ node_lb) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q0 = blockIdx.y * QT;
+  if (v >= T.n_nodes) return;
+  const int nqt = min(QT, nq - q0);
+  double acc[QT];
+#pragma unroll
+  for (int qq = 0; qq < QT; ++qq) acc[qq] = 0.0;
+  for (int r = T.seg_off[v]; r < T.seg_off[v + 1]; ++r) {
+    const int iv = T.seg_iv[r];
+    const double mlo = T.mlo[r], mhi = T.mhi[r], slo = T.slo[r], shi = T.shi[r];
+    const double len = (double)(T.iv_e[iv] - T.iv_s[iv]);
+#pragma unroll
+    for (int qq = 0; qq < QT; ++qq) {
+      if (qq >= nqt) break;
+      const double* st = ivstat + ((size_t)(q0 + qq) * T.n_iv + iv) * 2;
+      const double gm = gap(st[0], mlo, mhi);
+      const double gs = gap(st[1], slo, shi);
+      acc[qq] = __dadd_rn(acc[qq], __dmul_rn(len, __dadd_rn(__dmul_rn(gm, gm), __dmul_rn(gs, gs))));
+    }
+  }
+#pragma unroll
+  for (int qq = 0; qq < QT; ++qq)
+    if (qq < nqt) node_lb[(size_t)(q0 + qq) * T.n_nodes + v] = acc[qq];
+}
+
 // leaf bound = max over the root-to-leaf path
 __global__ void ds_leaf_kernel(DsTables T, const double* __restrict__ node_lb, int nq,
                                double* __restrict__ leaf_lb) {
@@ -299,8 +332,14 @@ void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double*
                                                                                       ivstat);
   }
   LF_CHECK_LAUNCH();
-  ds_node_kernel<<<blocks_for((int64_t)nq * T.n_nodes, kThreads), kThreads, 0, s>>>(T, ivstat, nq,
-                                                                                    node_lb);
+  if (T.n_nodes >= 2048) {
+    // large trees: tiles of 8 queries per thread share each node's synopses
+    dim3 grid(blocks_for(T.n_nodes, kThreads), blocks_for(nq, 8));
+    ds_node_tiled_kernel<8><<<grid, kThreads, 0, s>>>(T, ivstat, nq, node_lb);
+  } else {
+    ds_node_kernel<<<blocks_for((int64_t)nq * T.n_nodes, kThreads), kThreads, 0, s>>>(T, ivstat, nq,
+                                                                                      node_lb);
+  }
   LF_CHECK_LAUNCH();
   ds_leaf_kernel<<<blocks_for((int64_t)nq * T.n_leaves, kThreads), kThreads, 0, s>>>(
       T, node_lb, nq, leaf_lb);
