@@ -84,7 +84,8 @@ def parse():
     ap.add_argument("--wave", type=int, default=None,
                     help="leaves per wave (64; 512 for the iSAX configuration's small leaves)")
     ap.add_argument("--target", type=float, default=0.99)
-    ap.add_argument("--cpu-sample", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=1024,
+                    help="queries of the oracle's timed sample (about 10 s on 16 host threads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schedule", action="store_true",
                     help="batches in the callers' query order (no route-leaf scheduling)")
@@ -284,7 +285,7 @@ def run_reference(a):
     Wt, _, _ = O.train(p, Qg, Tg, Ql, Tl, O.epoch_perms(3, 1600, seed), *W)
     alpha, qp = O.fit_autotuner(t, Wt, fl, Qg[1200:], 1, a.wave)
     j = O.offset_position(qp, a.target)
-    per = max(4, min(a.cpu_sample, 64))
+    per = max(4, min(a.cpu_sample, 64))  # per step: a whole run stays within a minute
     times = []
     for s in range(a.warmup + a.steps):
         Qs = np.ascontiguousarray(Q[(s * per) % a.queries:][:per])
