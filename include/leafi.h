@@ -56,6 +56,10 @@ enum { LEAFI_MAX_K = 128, LEAFI_MAX_KCLASSES = 4 };
 /* Filter models: the MLP of Sec. 5.1 (default) and the CNN of the model-type
  * study in Sec. 5.2 (see leafi_set_cnn_filters). */
 enum { LEAFI_FILTER_MLP = 0, LEAFI_FILTER_CNN = 1 };
+/* Query-time offsets from the auto-tuner tables (Sec. 4.4.2): the certified
+ * STEP position (default) or the paper's spline through the table (Steffen's
+ * monotone interpolation), see leafi_set_calibration_mode. */
+enum { LEAFI_CALIB_STEP = 0, LEAFI_CALIB_STEFFEN = 1 };
 
 /* ------------------------------------------------------------------ */
 /* Index building (Sec. 3 "Tree-based indexes"; Alg. 1 input I)        */
@@ -325,6 +329,8 @@ typedef struct {
                                defaults; the tables are refitted for the chosen width) */
   int32_t model;            /* LEAFI_FILTER_MLP (Sec. 5.1) or LEAFI_FILTER_CNN (Sec. 5.2;
                                `hidden` is then the channel count C, 0 = m) */
+  int32_t calib_mode;       /* LEAFI_CALIB_STEP (default) or LEAFI_CALIB_STEFFEN, installed
+                               with the tables (leafi_set_calibration_mode) */
 } leafi_train_params;
 
 typedef struct {
@@ -405,6 +411,24 @@ leafi_status leafi_fit_autotuners(leafi_index* index, const float* Qc, int64_t n
  * the calibration queries); a target no position can certify runs exactly.
  * confidence 0 uses the point estimate qprime_j >= t.  Default 0.95. */
 leafi_status leafi_set_calibration_confidence(leafi_index* index, double confidence);
+
+/* LEAFI_CALIB_STEP (default): the certified position above.  LEAFI_CALIB_STEFFEN
+ * (the paper's auto-tuner f^c: a monotone spline through each filter's
+ * calibration points): for a query of k-class c and target t in (0, 1),
+ * filter f's offset is Steffen's (1990) monotone cubic interpolation, in
+ * float64, through the points (qprime[c][j], alpha_f,(j)) ordered by
+ * increasing qprime (j from nc - 1 down to 0; of equal qprime values the one
+ * of the largest j, i.e. the smallest offset, is kept), evaluated at t and
+ * clamped to the end points outside them.  It carries no certificate (the
+ * confidence setting does not apply); a query whose k exceeds every class or
+ * whose target is >= 1 runs exactly in both modes. */
+leafi_status leafi_set_calibration_mode(leafi_index* index, int32_t mode);
+/* The offsets the search uses for one query of this k and recall target
+ * under the index's current mode and confidence: offsets [F] (float64, host).
+ * *uses_filters (nullable) receives 1, or 0 when the query runs exactly
+ * (offsets are then left unchanged). */
+leafi_status leafi_calibration_offsets(leafi_index* index, int32_t k, double recall_target,
+                                       double* offsets, int32_t* uses_filters);
 
 /* Read (alpha_sorted [F][nc] float64, qprime [nk][nc] float64) back. */
 leafi_status leafi_get_autotuners(leafi_index* index, double* alpha_sorted, double* qprime);

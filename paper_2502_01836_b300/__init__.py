@@ -31,7 +31,7 @@ __all__ = [
     "leafi_get_filter_leaves", "leafi_debug_set_lock_tries", "leafi_debug_fail_allocations",
     "leafi_set_calibration_confidence", "leafi_set_query_schedule", "leafi_set_search_lanes",
     "leafi_set_scan_part", "leafi_tune_search", "TuneParams", "TuneReport",
-    "leafi_set_search_batch",
+    "leafi_set_search_batch", "leafi_set_calibration_mode", "leafi_calibration_offsets",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -39,6 +39,7 @@ LIB_PATH = os.path.join(_HERE, "libleafi.so")
 
 DSTREE, ISAX = 0, 1
 FILTER_MLP, FILTER_CNN = 0, 1
+CALIB_STEP, CALIB_STEFFEN = 0, 1
 MAX_K = 128
 _STATUS = {0: "LEAFI_OK", 1: "LEAFI_EINVAL", 2: "LEAFI_ENOMEM", 3: "LEAFI_ECUDA",
            4: "LEAFI_ETIMEOUT", 5: "LEAFI_ENOTTRAINED", 6: "LEAFI_EINTERNAL",
@@ -60,7 +61,8 @@ EXPORTED_SYMBOLS = [
     "leafi_debug_fail_allocations", "leafi_set_calibration_confidence",
     "leafi_set_query_schedule", "leafi_set_search_lanes", "leafi_set_scan_part",
     "leafi_tune_search", "leafi_cnn_params", "leafi_set_cnn_filters", "leafi_get_cnn_filters",
-    "leafi_initial_cnn_weights", "leafi_set_search_batch",
+    "leafi_initial_cnn_weights", "leafi_set_search_batch", "leafi_set_calibration_mode",
+    "leafi_calibration_offsets",
 ]
 
 KERNEL_KINDS = ["leaf_scan", "merge", "bounds", "reserved", "filter_forward", "select"]
@@ -105,16 +107,16 @@ class TrainParams(C.Structure):
                 ("batch", C.c_int32), ("max_epochs", C.c_int32), ("patience", C.c_int32),
                 ("lr0", C.c_double), ("lr_min", C.c_double), ("n_kclasses", C.c_int32),
                 ("kclasses", C.c_int32 * 4), ("seed", C.c_uint64), ("confidence", C.c_double),
-                ("tune_search", C.c_int32), ("model", C.c_int32)]
+                ("tune_search", C.c_int32), ("model", C.c_int32), ("calib_mode", C.c_int32)]
 
     def __init__(self, n_filters=100, a=2.0, mem_cap=8 << 30, hidden=0, n_train=2000,
                  global_local_ratio=3.0, val_frac=0.2, noise_lo=0.1, noise_hi=0.4, batch=64,
                  max_epochs=1000, patience=10, lr0=0.01, lr_min=1e-5, kclasses=(1,),
-                 seed=2502018361, confidence=0.95, tune_search=1, model=0):
+                 seed=2502018361, confidence=0.95, tune_search=1, model=0, calib_mode=0):
         kc = (C.c_int32 * 4)(*(list(kclasses) + [0] * (4 - len(kclasses))))
         super().__init__(n_filters, a, mem_cap, hidden, n_train, global_local_ratio, val_frac,
                          noise_lo, noise_hi, batch, max_epochs, patience, lr0, lr_min,
-                         len(kclasses), kc, seed, confidence, tune_search, model)
+                         len(kclasses), kc, seed, confidence, tune_search, model, calib_mode)
 
 
 class TuneParams(C.Structure):
@@ -231,6 +233,8 @@ def lib():
             "leafi_set_search_lanes": [vp, i32],
             "leafi_set_scan_part": [vp, i32, i32, i32, i32],
             "leafi_set_search_batch": [vp, i32],
+            "leafi_set_calibration_mode": [vp, i32],
+            "leafi_calibration_offsets": [vp, i32, f64, vp, C.POINTER(i32)],
             "leafi_tune_search": [vp, C.POINTER(TuneParams), C.POINTER(TuneReport)],
             "leafi_fit_autotuners": [vp, vp, i64, vp, i32],
             "leafi_get_autotuners": [vp, vp, vp],
@@ -471,6 +475,20 @@ def leafi_set_query_schedule(index, on=True):
 def leafi_set_search_lanes(index, lanes):
     """Batches of one search call in flight (1..8)."""
     _check(lib().leafi_set_search_lanes(index, int(lanes)))
+
+
+def leafi_set_calibration_mode(index, mode):
+    """CALIB_STEP (certified position) or CALIB_STEFFEN (the paper's spline)."""
+    _check(lib().leafi_set_calibration_mode(index, int(mode)))
+
+
+def leafi_calibration_offsets(index, k, recall_target):
+    """The offsets [F] a query of this k and target uses, or None if it runs exactly."""
+    out = np.zeros(max(1, leafi_get_info(index).n_filters), np.float64)
+    use = C.c_int32()
+    _check(lib().leafi_calibration_offsets(index, int(k), float(recall_target), out.ctypes.data,
+                                           C.byref(use)))
+    return out if use.value else None
 
 
 def leafi_set_search_batch(index, queries=256):

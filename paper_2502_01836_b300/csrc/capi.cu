@@ -612,8 +612,103 @@ double required_quality(int64_t N, double t, double conf) {
   return (double)(N - m_star) / (double)N;
 }
 
+// Steffen (1990) monotone cubic interpolation at t through points of strictly
+// increasing x, clamped to the end values: the cubic Hermite piece of each
+// interval with slopes limited to keep monotone data monotone.
+double steffen_at(const std::vector<double>& x, const std::vector<double>& y, double t) {
+  const int n = (int)x.size();
+  if (n == 1 || t <= x[0]) return y[0];
+  if (t >= x[n - 1]) return y[n - 1];
+  auto secant = [&](int i) { return (y[i + 1] - y[i]) / (x[i + 1] - x[i]); };
+  auto sign = [](double v) { return (double)((v > 0.0) - (v < 0.0)); };
+  // slope at node i (interior: limited harmonic-style choice; ends: one-sided
+  // parabola through three points, limited)
+  auto slope = [&](int i) {
+    if (n == 2) return secant(0);
+    if (i > 0 && i < n - 1) {
+      const double h0 = x[i] - x[i - 1], h1 = x[i + 1] - x[i];
+      const double s0 = secant(i - 1), s1 = secant(i);
+      const double p = (s0 * h1 + s1 * h0) / (h0 + h1);
+      return (sign(s0) + sign(s1)) * std::min(std::min(std::fabs(s0), std::fabs(s1)),
+                                              0.5 * std::fabs(p));
+    }
+    const int a = i == 0 ? 0 : n - 2, b = i == 0 ? 1 : n - 3;
+    const double h0 = x[a + 1] - x[a], h1 = x[b + 1] - x[b];
+    const double s0 = secant(a), s1 = secant(b);
+    const double p = s0 * (1.0 + h0 / (h0 + h1)) - s1 * h0 / (h0 + h1);
+    if (p * s0 <= 0.0) return 0.0;
+    return std::fabs(p) > 2.0 * std::fabs(s0) ? 2.0 * s0 : p;
+  };
+  int i = 0;
+  while (i < n - 2 && t >= x[i + 1]) ++i;
+  const double h = x[i + 1] - x[i], s = secant(i);
+  const double d0 = slope(i), d1 = slope(i + 1);
+  const double a3 = (d0 + d1 - 2.0 * s) / (h * h);
+  const double a2 = (3.0 * s - 2.0 * d0 - d1) / h;
+  const double u = t - x[i];
+  return ((a3 * u + a2) * u + d0) * u + y[i];
+}
+
+constexpr int kSteffenCols = 64;  // (k-class, target) columns of the offset table
+
+// Steffen offsets of every filter for k-class c at target t (host tables)
+void steffen_offsets(const leafi_index* ix, int c, double t, double* out) {
+  const int nc = ix->nc;
+  const double* qp = ix->h_qprime.data() + (size_t)c * nc;
+  std::vector<int> js;  // nodes by increasing qprime, the largest j of equal values
+  for (int j = nc - 1; j >= 0; --j)
+    if (js.empty() || qp[j] > qp[js.back()]) js.push_back(j);
+  std::vector<double> x(js.size()), y(js.size());
+  for (size_t z = 0; z < js.size(); ++z) x[z] = qp[js[z]];
+  for (int f = 0; f < ix->F; ++f) {
+    const double* a = ix->h_alpha.data() + (size_t)f * nc;
+    for (size_t z = 0; z < js.size(); ++z) y[z] = a[js[z]];
+    out[f] = steffen_at(x, y, t);
+  }
+}
+
+// the offset table of STEFFEN mode: alpha in the first nc columns, one column
+// per (k-class, target) in use after them; rebuilt when the tables change.
+// Returns the column for (c, t).  The caller holds the index mutex.
+int steffen_column(leafi_index* ix, int c, double t) {
+  cudaStream_t s = ix->stream;
+  const int F = ix->F, nc = ix->nc;
+  if (ix->offs_gen != ix->tables_gen) {
+    ix->h_alpha.resize((size_t)F * nc);
+    ix->h_qprime.resize((size_t)ix->nk * nc);
+    LF_CUDA(cudaMemcpyAsync(ix->h_alpha.data(), ix->alpha.p, sizeof(double) * F * nc,
+                            cudaMemcpyDeviceToHost, s));
+    LF_CUDA(cudaMemcpyAsync(ix->h_qprime.data(), ix->qprime.p, sizeof(double) * ix->nk * nc,
+                            cudaMemcpyDeviceToHost, s));
+    LF_CUDA(cudaStreamSynchronize(s));
+    ix->steffen_cols.clear();
+    ix->offs_stride = nc + kSteffenCols;
+    double* o = ix->offs.need((size_t)F * ix->offs_stride);
+    LF_CUDA(cudaMemcpy2DAsync(o, sizeof(double) * ix->offs_stride, ix->alpha.p, sizeof(double) * nc,
+                              sizeof(double) * nc, (size_t)F, cudaMemcpyDeviceToDevice, s));
+    LF_CUDA(cudaStreamSynchronize(s));
+    ix->offs_gen = ix->tables_gen;
+  }
+  const auto key = std::make_pair(c, t);
+  auto it = ix->steffen_cols.find(key);
+  if (it != ix->steffen_cols.end()) return it->second;
+  if ((int)ix->steffen_cols.size() >= kSteffenCols) {
+    // every column in use: start over (the graphs hold no column numbers)
+    ix->steffen_cols.clear();
+  }
+  const int col = nc + (int)ix->steffen_cols.size();
+  std::vector<double> v(F);
+  steffen_offsets(ix, c, t, v.data());
+  LF_CUDA(cudaMemcpy2DAsync(ix->offs.p + col, sizeof(double) * ix->offs_stride, v.data(),
+                            sizeof(double), sizeof(double), (size_t)F, cudaMemcpyHostToDevice, s));
+  LF_CUDA(cudaStreamSynchronize(s));
+  ix->steffen_cols.emplace(key, col);
+  return col;
+}
+
 // per query: the quality its k-class table must reach for its target (2 when
-// the query runs exactly); cached per (N, target) on the index
+// the query runs exactly); cached per (N, target) on the index.  STEFFEN mode:
+// -(column + 1) of the query's offsets in the offset table.
 void required_qualities(leafi_index* ix, int nb, const int32_t* kq, const double* target,
                         bool uniform, std::vector<double>& out) {
   out.resize(uniform ? 1 : nb);
@@ -627,6 +722,10 @@ void required_qualities(leafi_index* ix, int nb, const int32_t* kq, const double
       }
     if (c < 0 || !(t < 1.0) || ix->nc == 0) {
       out[i] = 2.0;
+      continue;
+    }
+    if (ix->calib_mode == LEAFI_CALIB_STEFFEN) {
+      out[i] = -(double)(steffen_column(ix, c, t) + 1);
       continue;
     }
     const int64_t N = std::min<int64_t>(ix->kclasses[c], ix->n) * ix->nc;
@@ -852,8 +951,10 @@ void Pipeline::make_sa(const LaneView& v, int nb, bool use_f) {
   sa.thr = v.thr;
   sa.F = ix->F;
   sa.leaf_filter = ix->d_leaf_filter.p;
-  sa.alpha = ix->alpha.p;
-  sa.nc = ix->nc;
+  // STEFFEN mode: the offset table whose extra columns hold interpolated offsets
+  const bool steff = ix->calib_mode == LEAFI_CALIB_STEFFEN && ix->offs.p;
+  sa.alpha = steff ? ix->offs.p : ix->alpha.p;
+  sa.nc = steff ? ix->offs_stride : ix->nc;
   sa.leaf_off = ix->leaf_off.p;
   sa.scanned = v.scanned;
   sa.done = v.done;
@@ -1933,6 +2034,7 @@ void install_filters(leafi_index* index, const std::vector<int32_t>& fl, int h,
   index->nc = 0;
   index->nk = 0;
   index->calib_q.release();
+  index->tables_gen += 1;
 }
 
 }  // namespace
@@ -2379,6 +2481,7 @@ void calib_simulate(leafi_index* index, CalibState& cs, int W) {
   index->nk = nk;
   for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? cs.kc[i] : 0;
   index->rq_cache.clear();
+  index->tables_gen += 1;
 }
 
 // Alg. 4 on staged calibration queries dQ [nc][mp] for the k-classes at the
@@ -2669,6 +2772,8 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     const int h = p->hidden > 0 ? p->hidden : index->m;
     if (p->model != LEAFI_FILTER_MLP && p->model != LEAFI_FILTER_CNN)
       fail(LEAFI_EINVAL, "unknown filter model %d", p->model);
+    if (p->calib_mode != LEAFI_CALIB_STEP && p->calib_mode != LEAFI_CALIB_STEFFEN)
+      fail(LEAFI_EINVAL, "unknown calibration mode %d", p->calib_mode);
     if (p->model == LEAFI_FILTER_CNN && !cnn_fits(index->m, h, index->smem_optin))
       fail(LEAFI_EINVAL, "CNN filters of %d channels at m = %d exceed shared memory", h, index->m);
     std::lock_guard<std::mutex> lk(index->mu);
@@ -2727,6 +2832,7 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     }
     // line 10: auto-tuners on the calibration set (the global validation queries)
     index->calib_confidence = p->confidence;
+    index->calib_mode = p->calib_mode;
     fit_core(index, dQg + (size_t)c.n_gtrain * index->mp, c.n_gval, p->kclasses, p->n_kclasses);
     // the LeaFi searches' schedule (the tables are refitted for each candidate)
     if (p->tune_search) {
@@ -2913,6 +3019,70 @@ leafi_status leafi_set_calibration_confidence(leafi_index* index, double confide
   });
 }
 
+leafi_status leafi_set_calibration_mode(leafi_index* index, int32_t mode) {
+  return guarded([&] {
+    require_device(index);
+    if (mode != LEAFI_CALIB_STEP && mode != LEAFI_CALIB_STEFFEN)
+      fail(LEAFI_EINVAL, "unknown calibration mode %d", mode);
+    std::lock_guard<std::mutex> lk(index->mu);
+    index->drop_graphs();
+    index->calib_mode = mode;
+  });
+}
+
+leafi_status leafi_calibration_offsets(leafi_index* index, int32_t k, double recall_target,
+                                       double* offsets, int32_t* uses_filters) {
+  return guarded([&] {
+    require_device(index);
+    if (index->nc == 0 || index->F == 0) fail(LEAFI_ENOTTRAINED, "no auto-tuners fitted");
+    if (!offsets) fail(LEAFI_EINVAL, "NULL output");
+    if (k < 1 || k > LEAFI_MAX_K) fail(LEAFI_EINVAL, "k must be in [1, %d]", LEAFI_MAX_K);
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    std::vector<double> rq;
+    required_qualities(index, 1, &k, &recall_target, true, rq);
+    const int F = index->F;
+    int use = 0;
+    std::vector<double> col(F);
+    if (rq[0] < 0.0) {
+      // STEFFEN: the query's column of the offset table
+      const int c = (int)(-rq[0]) - 1;
+      LF_CUDA(cudaMemcpy2DAsync(col.data(), sizeof(double), index->offs.p + c,
+                                sizeof(double) * index->offs_stride, sizeof(double), (size_t)F,
+                                cudaMemcpyDeviceToHost, index->stream));
+      LF_CUDA(cudaStreamSynchronize(index->stream));
+      use = 1;
+    } else if (rq[0] <= 1.0) {
+      // STEP: the last position whose quality reaches rq, as the position kernel takes it
+      int c = -1;
+      for (int z = 0; z < index->nk; ++z)
+        if (index->kclasses[z] >= k) {
+          c = z;
+          break;
+        }
+      const int nc = index->nc;
+      std::vector<double> qp(nc), a((size_t)F * nc);
+      LF_CUDA(cudaMemcpyAsync(qp.data(), index->qprime.p + (size_t)c * nc, sizeof(double) * nc,
+                              cudaMemcpyDeviceToHost, index->stream));
+      LF_CUDA(cudaMemcpyAsync(a.data(), index->alpha.p, sizeof(double) * F * nc,
+                              cudaMemcpyDeviceToHost, index->stream));
+      LF_CUDA(cudaStreamSynchronize(index->stream));
+      int j = nc - 1;
+      for (int i = 0; i < nc; ++i)
+        if (!(qp[i] >= rq[0])) {
+          j = i - 1;
+          break;
+        }
+      if (j >= 0) {
+        for (int f = 0; f < F; ++f) col[f] = a[(size_t)f * nc + j];
+        use = 1;
+      }
+    }
+    if (use) std::memcpy(offsets, col.data(), sizeof(double) * F);
+    if (uses_filters) *uses_filters = use;
+  });
+}
+
 leafi_status leafi_get_autotuners(leafi_index* index, double* alpha_sorted, double* qprime) {
   return guarded([&] {
     require_device(index);
@@ -2957,6 +3127,7 @@ leafi_status leafi_set_autotuners(leafi_index* index, const double* alpha_sorted
     for (int i = 0; i < LEAFI_MAX_KCLASSES; ++i) index->kclasses[i] = i < nk ? kc[i] : 0;
     index->calib_q.release();  // these tables come without their calibration queries
     index->rq_cache.clear();
+    index->tables_gen += 1;
   });
 }
 

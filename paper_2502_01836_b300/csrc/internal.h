@@ -480,6 +480,17 @@ struct leafi_index {
   leafi::DBuf<int32_t> d_kclasses;
   leafi::DBuf<float> calib_q;    // the calibration queries [nc][mp] behind the tables (kept so
                                  // that the tables can be refitted for another wave width)
+  // query-time offsets: LEAFI_CALIB_STEP reads alpha at a certified position;
+  // LEAFI_CALIB_STEFFEN interpolates each filter's (q', alpha) points at the
+  // target.  The Steffen offsets of each (k-class, target) in use are extra
+  // columns of `offs` [F][offs_stride] (the alpha table in the first nc columns).
+  int calib_mode = LEAFI_CALIB_STEP;
+  unsigned long long tables_gen = 0;       // bumped whenever alpha / qprime change
+  unsigned long long offs_gen = ~0ull;     // tables_gen `offs` was built from
+  std::vector<double> h_alpha, h_qprime;   // host copies behind `offs`
+  std::map<std::pair<int, double>, int> steffen_cols;  // (k-class, target) -> column
+  leafi::DBuf<double> offs;
+  int offs_stride = 0;
 
   // scratch (grown on demand): lanes[0] serves every entry point; a search of
   // more than one batch spreads its batches over several lanes in turn

@@ -823,7 +823,10 @@ __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double*
       break;
     }
   int j = -1;
-  if (c >= 0 && r <= 1.0) {
+  if (r < 0.0) {
+    // interpolated offsets (STEFFEN mode): r = -(column + 1) of the offset table
+    j = (int)(-r) - 1;
+  } else if (c >= 0 && r <= 1.0) {
     const double* qp = qprime + (size_t)c * nc;
     j = nc - 1;
     for (int base = 0; base < nc; base += 32) {

@@ -786,3 +786,67 @@ def test_search_batch_size_keeps_every_result(ds, tuned):
     finally:
         lf.leafi_set_search_batch(idx, 256)
         lf.leafi_set_calibration_confidence(idx, 0.95)
+
+
+def _steffen_ref(alpha, qp_row, t):
+    """The oracle's Steffen interpolation through the reading's points: qprime
+    ascending (j from nc - 1 down), the largest j of equal qprime values."""
+    nc = qp_row.shape[0]
+    js = []
+    for j in range(nc - 1, -1, -1):
+        if not js or qp_row[j] > qp_row[js[-1]]:
+            js.append(j)
+    x = np.array([qp_row[j] for j in js])
+    return np.array([O.steffen_eval(x, np.array([a[j] for j in js]), t) for a in alpha])
+
+
+@pytest.mark.parametrize("k,target", [(1, 0.95), (1, 0.9), (10, 0.93)])
+def test_steffen_offsets_and_search_bit_exact(ds, tuned, k, target):
+    """STEFFEN mode (the paper's spline auto-tuner): the offsets equal the
+    oracle's Steffen interpolation of the same tables, and the search equals the
+    oracle's fed the GPU's predictions and those offsets (ids, distances,
+    scanned leaves and series); STEP mode's offsets are the table column at the
+    oracle's position."""
+    X, Q, idx, t = ds
+    fl, Wt, Qc, _ = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_fit_autotuners(idx, Qc, [1, 10])
+    F, nc = Wt[0].shape[0], Qc.shape[0]
+    alpha = np.zeros((F, nc))
+    qp = np.zeros((2, nc))
+    lf.leafi_get_autotuners(idx, alpha, qp)
+    c = 0 if k == 1 else 1
+    try:
+        lf.leafi_set_calibration_confidence(idx, 0.0)
+        j = O.offset_position(qp[c], target, kk=k, confidence=0.0)
+        step = lf.leafi_calibration_offsets(idx, k, target)
+        if j < 0:
+            assert step is None
+        else:
+            assert np.array_equal(step, alpha[:, j])
+        lf.leafi_set_calibration_mode(idx, lf.CALIB_STEFFEN)
+        offs = lf.leafi_calibration_offsets(idx, k, target)
+        ref = _steffen_ref(alpha, qp[c], target)
+        assert np.abs(offs - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        assert lf.leafi_calibration_offsets(idx, k, 1.0) is None
+        assert lf.leafi_calibration_offsets(idx, 11, target) is None  # no class >= 11
+        P = np.zeros((NQ, F), np.float32)
+        lf.leafi_filter_predict(idx, Q, P)
+        ids = np.zeros((NQ, k), np.int64)
+        d = np.zeros((NQ, k), np.float32)
+        st = lf.SearchStats()
+        lf.leafi_search(idx, Q, k, target, ids, d, st)
+        ext = np.concatenate([alpha, offs[:, None]], axis=1)
+        o_ids, o_d2, o_st, _ = O.leafi_search_pred(t, P.astype(np.float64), fl, ext, Q, k, nc, 4)
+        assert np.array_equal(ids, o_ids)
+        assert np.array_equal(d, np.sqrt(o_d2))
+        assert st.leaves_scanned == o_st[:, 0].sum()
+        assert st.series_scanned == o_st[:, 1].sum()
+        # exact requests are unaffected by the mode
+        e_ids, _, _ = _exact(idx, Q, k)
+        ids2 = np.zeros((NQ, k), np.int64)
+        lf.leafi_search(idx, Q, k, 1.0, ids2, np.zeros((NQ, k), np.float32))
+        assert np.array_equal(ids2, e_ids)
+    finally:
+        lf.leafi_set_calibration_mode(idx, lf.CALIB_STEP)
+        lf.leafi_set_calibration_confidence(idx, 0.95)
