@@ -454,6 +454,9 @@ typedef struct {
   double host_wait_ms;     /* host time the call spent waiting for the GPU (batch pair
                               counts, its end) */
   double host_ms;          /* host time of the whole call */
+  int64_t filter_pruned;   /* (query, leaf) pairs pruned by the leaf's filter (Alg. 2 line 6) */
+  int64_t lb_pruned;       /* (query, leaf) pairs neither searched nor filter-pruned: pruned
+                              by the summarisation bound (Alg. 2 line 4) */
 } leafi_search_stats;
 
 /* k-NN of nq queries (1 <= k <= LEAFI_MAX_K).  recall_target >= 1 runs the

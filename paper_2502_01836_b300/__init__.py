@@ -164,7 +164,7 @@ class SearchStats(C.Structure):
                 ("filter_evals", C.c_int64), ("waves", C.c_int64), ("batches", C.c_int64),
                 ("distinct_series", C.c_int64), ("rechecks", C.c_int64),
                 ("graph_batches", C.c_int64), ("host_wait_ms", C.c_double),
-                ("host_ms", C.c_double)]
+                ("host_ms", C.c_double), ("filter_pruned", C.c_int64), ("lb_pruned", C.c_int64)]
 
 
 class SelectParams(C.Structure):

@@ -1222,14 +1222,14 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       ix->capturing = nullptr;
     }
   } restore{ix, user};
-  unsigned long long* stat = ix->sStat.need(4);
+  unsigned long long* stat = ix->sStat.need(5);
   Pipeline pl;
   pl.setup(ix, ix->lanes, nlanes, kmax, any_filtered, stat, qb);
   const bool uniform =
       std::all_of(kq.begin(), kq.end(), [&](int32_t v) { return v == kq[0]; }) &&
       std::all_of(target.begin(), target.end(), [&](double v) { return v == target[0]; });
   // the lanes start after the caller's stream (inputs written there are visible)
-  LF_CUDA(cudaMemsetAsync(stat, 0, 4 * sizeof(unsigned long long), user));
+  LF_CUDA(cudaMemsetAsync(stat, 0, 5 * sizeof(unsigned long long), user));
   cudaEvent_t ev_start = nullptr;
   LF_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
   struct EvGuard {
@@ -1332,7 +1332,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     deliver(ids, out_i, (size_t)nq * kmax, user);
     deliver(dists, out_d, (size_t)nq * kmax, user);
   }
-  unsigned long long h_stat[4] = {0, 0, 0, 0};
+  unsigned long long h_stat[5] = {0, 0, 0, 0, 0};
   LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, user));
   const auto w_end = std::chrono::steady_clock::now();
   LF_CUDA(cudaStreamSynchronize(user));
@@ -1345,6 +1345,8 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   st.series_scanned = (int64_t)h_stat[1];
   st.distinct_series = (int64_t)h_stat[2];
   st.rechecks = (int64_t)h_stat[3];
+  st.filter_pruned = (int64_t)h_stat[4];
+  st.lb_pruned = nq * (int64_t)ix->tree.n_leaves - st.leaves_scanned - st.filter_pruned;
   ix->settle();
   if (stats) *stats = st;
 }
@@ -3369,8 +3371,8 @@ leafi_status leafi_serve_start(leafi_index* index, const leafi_serve_params* par
     sv->p = p;
     {
       DeviceGuard dg(index->device);
-      sv->stat.need(4);
-      LF_CUDA(cudaMemset(sv->stat.p, 0, 4 * sizeof(unsigned long long)));
+      sv->stat.need(5);
+      LF_CUDA(cudaMemset(sv->stat.p, 0, 5 * sizeof(unsigned long long)));
       for (int li = 0; li < kServeLanes; ++li) {
         const size_t b = (size_t)p.max_batch;
         LF_CUDA(cudaMallocHost(&sv->hq[li], sizeof(float) * b * index->m));
@@ -3465,7 +3467,7 @@ leafi_status leafi_serve_get_stats(leafi_server* sv, leafi_serve_stats* stats) {
       std::lock_guard<std::mutex> lk(sv->mu);
       c = sv->counters;
     }
-    unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
     on_index(sv, [&] {
       DeviceGuard dg(sv->ix->device);
       LF_CUDA(cudaMemcpy(h, sv->stat.p, sizeof(h), cudaMemcpyDeviceToHost));
@@ -3475,6 +3477,8 @@ leafi_status leafi_serve_get_stats(leafi_server* sv, leafi_serve_stats* stats) {
     st.series_scanned = (int64_t)h[1];
     st.distinct_series = (int64_t)h[2];
     st.rechecks = (int64_t)h[3];
+    st.filter_pruned = (int64_t)h[4];
+    st.lb_pruned = c.queries * (int64_t)sv->ix->tree.n_leaves - st.leaves_scanned - st.filter_pruned;
     c.graph_batches = st.graph_batches;
     c.search = st;
     c.device_bytes = 0;

@@ -317,7 +317,8 @@ struct SelectArgs {
   int32_t* done;                  // [nq]
   Pair* pairs;
   int32_t* npairs;
-  unsigned long long* stat;       // [0] leaves searched, [1] series scanned
+  unsigned long long* stat;       // [0] leaves searched, [1] series scanned, [4] leaves
+                                  // pruned by their filter (each once per query)
 };
 
 // one captured search batch (full 256-query batch, route round + one wave)

@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(kSelThreads) select_walk_kernel(SelectArgs a,
   bool finished = false;  // reached the end or a bound-pruned leaf
   while (pos0 < L && picked < a.W) {
     const int p = pos0 + (int)threadIdx.x;
-    int leaf = -1, elig = 0, stop = 0;
+    int leaf = -1, elig = 0, stop = 0, fpruned = 0;
     if (p < L) {
       leaf = od[p];
       if (__dmul_rn(lb[leaf], kDeflate) > bsf2d) {
@@ -685,7 +685,10 @@ __global__ void __launch_bounds__(kSelThreads) select_walk_kernel(SelectArgs a,
           if (f >= 0) {
             const double df =
                 __dsub_rn((double)a.P[(size_t)q * a.F + f], a.alpha[(size_t)f * a.nc + jp]);
-            if (df > bsf) elig = 0;
+            if (df > bsf) {
+              elig = 0;
+              fpruned = 1;
+            }
           }
         }
       }
@@ -718,6 +721,13 @@ __global__ void __launch_bounds__(kSelThreads) select_walk_kernel(SelectArgs a,
       if (rank == a.W - 1) s_newcur = p + 1;
     }
     __syncthreads();
+    // filter-pruned positions the cursor passes for good (Alg. 2 line 6); a
+    // position at or after the next wave's start is examined again then
+    const int cut = picked + total >= a.W ? s_newcur : first_stop;
+    {
+      const unsigned fb = __ballot_sync(0xffffffffu, fpruned && p < cut);
+      if (lane == 0 && fb && a.stat) atomicAdd(&a.stat[4], (u64)__popc(fb));
+    }
     if (picked + total >= a.W) {
       pos0 = s_newcur;
       picked = a.W;
@@ -759,7 +769,10 @@ __global__ void select_all_kernel(SelectArgs a) {
       const double bsf = (double)__fsqrt_rn(bsf2);
       const double df =
           __dsub_rn((double)a.P[(size_t)q * a.F + f], a.alpha[(size_t)f * a.nc + a.jpos[q]]);
-      if (df > bsf) return;
+      if (df > bsf) {
+        atomicAdd(&a.stat[4], 1ull);  // filter-pruned (Alg. 2 line 6)
+        return;
+      }
     }
   }
   sc[leaf] = 1;

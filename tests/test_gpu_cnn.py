@@ -165,6 +165,7 @@ def test_cnn_leafi_search_bit_exact_on_gpu_predictions(cnn_index, k, target):
     assert np.array_equal(d, np.sqrt(o_d2))
     assert st.leaves_scanned == o_st[:, 0].sum()
     assert st.series_scanned == o_st[:, 1].sum()
+    assert st.filter_pruned == o_st[:, 3].sum() and st.lb_pruned == o_st[:, 2].sum()
     assert st.filter_evals == Q.shape[0] * len(fl)
 
 

@@ -306,6 +306,7 @@ def test_leafi_search_bit_exact_on_gpu_predictions(ds, tuned, k, target):
     assert np.array_equal(d, np.sqrt(o_d2))
     assert st.leaves_scanned == o_st[:, 0].sum()
     assert st.series_scanned == o_st[:, 1].sum()
+    assert st.filter_pruned == o_st[:, 3].sum() and st.lb_pruned == o_st[:, 2].sum()
     if j >= 0:
         assert o_st[:, 3].sum() > 0     # some filter pruned a leaf: the comparison covers it
 
@@ -842,6 +843,7 @@ def test_steffen_offsets_and_search_bit_exact(ds, tuned, k, target):
         assert np.array_equal(d, np.sqrt(o_d2))
         assert st.leaves_scanned == o_st[:, 0].sum()
         assert st.series_scanned == o_st[:, 1].sum()
+        assert st.filter_pruned == o_st[:, 3].sum() and st.lb_pruned == o_st[:, 2].sum()
         # exact requests are unaffected by the mode
         e_ids, _, _ = _exact(idx, Q, k)
         ids2 = np.zeros((NQ, k), np.int64)
@@ -850,3 +852,42 @@ def test_steffen_offsets_and_search_bit_exact(ds, tuned, k, target):
     finally:
         lf.leafi_set_calibration_mode(idx, lf.CALIB_STEP)
         lf.leafi_set_calibration_confidence(idx, 0.95)
+
+
+def test_wave_of_every_leaf_bit_exact_on_gpu_predictions(ds, tuned):
+    """The one-pass select of a wave as wide as the index (W >= L), with its
+    tables refitted for that width by the LeaFi-mode tuner: the search equals
+    the oracle's at W = L, pruning counts included."""
+    X, Q, idx, t = ds
+    fl, Wt, Qc, _ = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_fit_autotuners(idx, Qc, [1, 10])
+    try:
+        rep = lf.leafi_tune_search(idx, lf.TuneParams(n_probe=256, reps=1, waves=(65536,),
+                                                      items_per_sm=(4,), target=0.9))
+        L = t.L
+        assert rep["wave"] == L and lf.leafi_get_info(idx).wave == L
+        F, nc = Wt[0].shape[0], Qc.shape[0]
+        alpha = np.zeros((F, nc))
+        qp = np.zeros((2, nc))
+        lf.leafi_get_autotuners(idx, alpha, qp)
+        Pc = np.zeros((nc, F), np.float32)
+        lf.leafi_filter_predict(idx, Qc, Pc)
+        a_ref, q_ref = O.fit_autotuner_pred(t, Pc.astype(np.float64), fl, Qc, 1, L)
+        assert np.array_equal(alpha, a_ref) and np.array_equal(qp[0], q_ref)
+        P = np.zeros((NQ, F), np.float32)
+        lf.leafi_filter_predict(idx, Q, P)
+        lf.leafi_set_calibration_confidence(idx, 0.0)
+        ids = np.zeros((NQ, 1), np.int64)
+        d = np.zeros((NQ, 1), np.float32)
+        st = lf.SearchStats()
+        lf.leafi_search(idx, Q, 1, 0.9, ids, d, st)
+        j = O.offset_position(qp[0], 0.9, kk=1, confidence=0.0)
+        o_ids, o_d2, o_st, _ = O.leafi_search_pred(t, P.astype(np.float64), fl, alpha, Q, 1, j, L)
+        assert np.array_equal(ids, o_ids) and np.array_equal(d, np.sqrt(o_d2))
+        assert st.leaves_scanned == o_st[:, 0].sum()
+        assert st.filter_pruned == o_st[:, 3].sum() and st.lb_pruned == o_st[:, 2].sum()
+    finally:
+        lf.leafi_set_calibration_confidence(idx, 0.95)
+        lf.leafi_tune_search(idx, lf.TuneParams(n_probe=64, reps=1, waves=(4,), items_per_sm=(4,),
+                                                target=0.9))
