@@ -989,6 +989,11 @@ def main():
                                         / max(st["batches"], 1),
             "rechecks_per_query": st["rechecks"] / (a.steps * a.queries),
             "pruning_ratio": 1.0 - st["series_scanned"] / (a.steps * a.queries * a.n),
+            # per query: leaves pruned by the summarisation bound and by a filter (Alg. 2)
+            "leaves_per_query": {"searched": st["leaves_scanned"] / (a.steps * a.queries),
+                                 "bound_pruned": st["lb_pruned"] / (a.steps * a.queries),
+                                 "filter_pruned": st["filter_pruned"] / (a.steps * a.queries),
+                                 "plain_searched": st_ex["leaves_scanned"] / (a.steps * a.queries)},
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
             "waves_per_launch": st["waves"] / max(st["batches"], 1),
             "host_ms_per_step": {"call": st["host_ms"] / a.steps,
