@@ -179,10 +179,14 @@ leafi_status leafi_leaf_of(const leafi_index* index, int32_t* leaf_of);
 /* Lower bounds and routing (Sec. 3; Alg. 2 line 4)                    */
 /* ------------------------------------------------------------------ */
 
-/* Squared leaf lower bounds LB^2 (float64, nq x n_leaves, row-major):
- * DSTree: max over the root-to-leaf path of sum_r l_r (gap(mu_q,r)^2 +
- * gap(sigma_q,r)^2) against each node's mean / sigma ranges; iSAX: MINDIST^2
- * of the leaf's word.  Segment statistics use float64 prefix sums. */
+/* Squared leaf lower bounds LB^2 (nq x n_leaves, row-major, float64 arrays
+ * holding float32 values): DSTree: max over the root-to-leaf path of
+ * sum_r l_r (gap(mu_q,r)^2 + gap(sigma_q,r)^2) against each node's mean /
+ * sigma ranges; iSAX: MINDIST^2 of the leaf's word.  Segment statistics and
+ * PAA values come from float64 prefix sums; the gaps, products and sums are
+ * float32, each statistic taken as the two floats around it and each range
+ * end and breakpoint rounded outward, so a gap never exceeds its float64
+ * value. */
 leafi_status leafi_leaf_lower_bounds(leafi_index* index, const float* queries, int64_t nq,
                                      double* lb2);
 /* Leaf that each query's own summary routes to (int32, nq). */
@@ -199,8 +203,9 @@ leafi_status leafi_route(leafi_index* index, const float* queries, int64_t nq, i
  * caller guarantees them.  The work is queued on the index's stream and the
  * call returns without synchronising.  Scratch is one static device array of
  * 16 MiB per GPU, held until the process exits; requests that need more
- * (roughly nq*(2m+2) + nq*(2*intervals + nodes) doubles for a DSTree) are
- * rejected with LEAFI_EINVAL naming the largest nq that fits.  The first call
+ * (roughly nq*(2m+2) + nq*(4*intervals + nodes) doubles for a DSTree,
+ * nq*(2m+2) + nq*2w for iSAX) are rejected with LEAFI_EINVAL naming the
+ * largest nq that fits.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make it before any stream capture.  Every call shares the array and keeps
  * nothing from the previous one (each scratch word read is written earlier in

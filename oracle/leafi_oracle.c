@@ -9,8 +9,8 @@
  *   Sec. 4.4.2  query-time offsets, d^F = d^f - o
  *   Alg. 2      search with the lower-bound / filter cascade
  * Readings of points the paper leaves open are stated where they are used.
- * Compiled with -O2 -ffp-contract=off (no fast-math) so every float64
- * expression is evaluated exactly as written.
+ * Compiled with -O2 -ffp-contract=off (no fast-math) so every float32 and
+ * float64 expression is evaluated exactly as written.
  */
 #include "leafi_oracle.h"
 
@@ -102,10 +102,29 @@ void or_segment_stats(const float* x, int m, int s, int e, double* mu, double* s
   free(P);
 }
 
-static double gap(double v, double lo, double hi) {
-  if (v < lo) return lo - v;
-  if (v > hi) return v - hi;
-  return 0.0;
+/* Reading of the bound arithmetic: the node bounds are evaluated in float32
+ * (FP64 stays with the sums and statistics).  A float64 value v becomes the
+ * two floats around it, f32_down(v) <= v <= f32_up(v); a synopsis range
+ * [lo, hi] becomes [f32_down(lo), f32_up(hi)].  The gap is then taken between
+ * the nearest ends, so it never exceeds the float64 gap, and the bound stays a
+ * lower bound up to the relative rounding of the float32 products and sums. */
+static float f32_down(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = nextafterf(f, -INFINITY);
+  return f;
+}
+
+static float f32_up(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = nextafterf(f, INFINITY);
+  return f;
+}
+
+static float gap_f32(double v, double lo, double hi) {
+  float vd = f32_down(v), vu = f32_up(v), a = f32_down(lo), b = f32_up(hi);
+  if (vu < a) return a - vu;
+  if (vd > b) return vd - b;
+  return 0.0f;
 }
 
 /* ------------------------------------------------------------------ */
@@ -656,34 +675,35 @@ int64_t or_tree_leaf_members(const or_tree* t, int32_t leaf, int64_t* ids, int64
 /* DSTree node bound (reading of the EAPCA bound): per segment r of the node,
  * LB^2 += l_r * (gap(mu_q) ^2 + gap(sigma_q)^2) against the node's ranges.
  * Valid because sum_r (q-x)^2 = l (mu_q-mu_x)^2 + |(q-mu_q)-(x-mu_x)|^2 and
- * |a-b| >= | |a|-|b| | with |q - mu_q| = sqrt(l) sigma_q. */
+ * |a-b| >= | |a|-|b| | with |q - mu_q| = sqrt(l) sigma_q.  Float32 gaps,
+ * products and sum (reading above). */
 static double ds_node_lb2(const node_t* nd, const double* P1, const double* P2) {
-  double acc = 0.0;
+  float acc = 0.0f;
   for (int r = 0; r < nd->nseg; ++r) {
     int s = r ? nd->seg[r - 1] : 0;
     double mu, sd;
     seg_stats(P1, P2, s, nd->seg[r], &mu, &sd);
-    double gm = gap(mu, nd->mlo[r], nd->mhi[r]);
-    double gs = gap(sd, nd->slo[r], nd->shi[r]);
-    double term = (double)(nd->seg[r] - s) * (gm * gm + gs * gs);
+    float gm = gap_f32(mu, nd->mlo[r], nd->mhi[r]);
+    float gs = gap_f32(sd, nd->slo[r], nd->shi[r]);
+    float term = (float)(nd->seg[r] - s) * (gm * gm + gs * gs);
     acc = acc + term;
   }
-  return acc;
+  return (double)acc;
 }
 
-/* iSAX MINDIST^2: sum_j l_j gap(PAA_j, [beta_lo, beta_hi])^2. */
+/* iSAX MINDIST^2: sum_j l_j gap(PAA_j, [beta_lo, beta_hi])^2, float32 as above. */
 static double isax_node_lb2(const or_tree* t, const node_t* nd, const double* a) {
-  double acc = 0.0;
+  float acc = 0.0f;
   int l = t->m / t->w;
   for (int j = 0; j < t->w; ++j) {
     int sh = t->b - nd->bits[j];
     double lo = t->beta[nd->sym[j] << sh];
     double hi = t->beta[(nd->sym[j] + 1) << sh];
-    double g = gap(a[j], lo, hi);
-    double term = (double)l * (g * g);
+    float g = gap_f32(a[j], lo, hi);
+    float term = (float)l * (g * g);
     acc = acc + term;
   }
-  return acc;
+  return (double)acc;
 }
 
 static void query_leaf_lb2(const or_tree* t, const float* q, double* P, double* a, double* out) {

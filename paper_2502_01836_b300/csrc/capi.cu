@@ -87,6 +87,18 @@ leafi_status guarded(Fn&& fn) {
   }
 }
 
+// float32 values enclosing a float64 one: the largest float at or below it and
+// the smallest at or above it (the bound kernels widen every synopsis range
+// and breakpoint outward, so their float32 gaps never exceed the float64 ones)
+float f32_below(double v) {
+  const float f = (float)v;
+  return (double)f > v ? std::nextafter(f, -std::numeric_limits<float>::infinity()) : f;
+}
+float f32_above(double v) {
+  const float f = (float)v;
+  return (double)f < v ? std::nextafter(f, std::numeric_limits<float>::infinity()) : f;
+}
+
 bool on_device(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -518,11 +530,11 @@ void compute_bounds(leafi_index* ix, const float* dQ, int nq, double* lb2, int32
   double* P = ix->sc->sP.need((size_t)nq * 2 * (ix->m + 1));
   if (!have_p) launch_prefix(dQ, nq, ix->mp, ix->m, P, s);
   if (t.type == LEAFI_DSTREE) {
-    double* iv = ix->sc->sIv.need((size_t)nq * t.iv_s.size() * 2);
+    double* iv = ix->sc->sIv.need(ds_ivstat_doubles(nq, t.iv_s.size()));
     double* nodes = ix->sc->sNode.need((size_t)nq * t.n_nodes);
     launch_ds_bounds(ix->ds(), P, nq, ix->m, iv, nodes, lb2, route, s);
   } else {
-    double* paa = ix->sc->sPaa.need((size_t)nq * t.w);
+    double* paa = ix->sc->sPaa.need(isax_paa_doubles(nq, t.w));
     launch_isax_bounds(ix->isax(), P, nq, ix->m, paa, lb2, route, s);
   }
 }
@@ -927,10 +939,10 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     S.sNItems.need(1);
     S.sP.need((size_t)qb * 2 * (ix->m + 1));
     if (t.type == LEAFI_DSTREE) {
-      S.sIv.need((size_t)qb * t.iv_s.size() * 2);
+      S.sIv.need(ds_ivstat_doubles(qb, t.iv_s.size()));
       S.sNode.need((size_t)qb * t.n_nodes);
     } else {
-      S.sPaa.need((size_t)qb * t.w);
+      S.sPaa.need(isax_paa_doubles(qb, t.w));
     }
   }
 }
@@ -1366,10 +1378,7 @@ leafi::DsTables leafi_index::ds() const {
   T.iv_e = iv_e.p;
   T.seg_off = seg_off.p;
   T.seg_iv = seg_iv.p;
-  T.mlo = mlo.p;
-  T.mhi = mhi.p;
-  T.slo = slo.p;
-  T.shi = shi.p;
+  T.syn32 = syn32.p;
   T.left = left.p;
   T.right = right.p;
   T.node_leaf = node_leaf.p;
@@ -1469,6 +1478,7 @@ leafi::IsaxTables leafi_index::isax() const {
   T.w = tree.w;
   T.bits = tree.bits;
   T.beta = beta.p;
+  T.beta32 = beta32.p;
   T.root_child = root_child.p;
   T.left = left.p;
   T.right = right.p;
@@ -1594,15 +1604,22 @@ leafi_status leafi_build(const float* series, int64_t n, int32_t m, const leafi_
       ix->iv_e.upload(t.iv_e, s);
       ix->seg_off.upload(t.node_seg_off, s);
       ix->seg_iv.upload(t.seg_iv, s);
-      ix->mlo.upload(t.seg_mlo, s);
-      ix->mhi.upload(t.seg_mhi, s);
-      ix->slo.upload(t.seg_slo, s);
-      ix->shi.upload(t.seg_shi, s);
+      std::vector<float4> syn(t.seg_mlo.size());
+      for (size_t r = 0; r < syn.size(); ++r)
+        syn[r] = make_float4(f32_below(t.seg_mlo[r]), f32_above(t.seg_mhi[r]),
+                             f32_below(t.seg_slo[r]), f32_above(t.seg_shi[r]));
+      ix->syn32.upload(syn, s);
+      LF_CUDA(cudaStreamSynchronize(s));  // `syn` is released on return
       ix->split_iv.upload(t.split_iv, s);
       ix->split_sd.upload(t.split_sd, s);
       ix->thresh.upload(t.split_thresh, s);
     } else {
       ix->beta.upload(t.beta, s);
+      std::vector<float2> b32(t.beta.size());
+      for (size_t i = 0; i < b32.size(); ++i)
+        b32[i] = make_float2(f32_below(t.beta[i]), f32_above(t.beta[i]));
+      ix->beta32.upload(b32, s);
+      LF_CUDA(cudaStreamSynchronize(s));  // `b32` is released on return
       ix->root_child.upload(t.root_child, s);
       ix->isplit.upload(t.isax_split, s);
       ix->node_bits.upload(t.node_bits, s);

@@ -100,7 +100,9 @@ struct DsTables {  // device view of a DSTree
   int n_nodes, n_leaves, n_iv, root;
   const int32_t *iv_s, *iv_e;
   const int32_t *seg_off, *seg_iv;
-  const double *mlo, *mhi, *slo, *shi;
+  // per node segment row: the float32 enclosure of its synopsis ranges,
+  // {mu_lo rounded down, mu_hi rounded up, sigma_lo down, sigma_hi up}
+  const float4* syn32;
   const int32_t *left, *right, *node_leaf, *split_iv, *split_sd;
   const double* thresh;
   const int32_t *path_off, *path;
@@ -108,7 +110,8 @@ struct DsTables {  // device view of a DSTree
 
 struct IsaxTables {  // device view of an iSAX tree
   int n_nodes, n_leaves, w, bits;
-  const double* beta;  // 2^bits + 1
+  const double* beta;    // 2^bits + 1
+  const float2* beta32;  // 2^bits + 1: each breakpoint rounded {down, up} to float32
   const int32_t *root_child, *left, *right, *node_leaf, *isplit, *node_bits;
   const int32_t *lo_sym, *hi_sym;  // leaf x w
 };
@@ -122,6 +125,12 @@ struct Pair {
 // ----------------------------------------------------------------- kernels
 // (declared here, defined in the k_*.cu files)
 void launch_prefix(const float* Q, int nq, int mp, int m, double* P, cudaStream_t s);
+// Scratch of the bound kernels, in doubles: DSTree interval statistics are
+// [nq][n_iv] float64 {mu, sigma} followed by [nq][n_iv] float32 enclosures
+// {mu down, mu up, sigma down, sigma up}; iSAX PAA values are [nq][w] float64
+// followed by [nq][w] float32 {down, up}.
+inline size_t ds_ivstat_doubles(size_t nq, size_t n_iv) { return nq * n_iv * 4; }
+inline size_t isax_paa_doubles(size_t nq, size_t w) { return nq * w * 2; }
 void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double* ivstat,
                       double* node_lb, double* leaf_lb, int32_t* route, cudaStream_t s);
 void launch_isax_bounds(const IsaxTables& T, const double* P, int nq, int m, double* paa,
@@ -460,9 +469,11 @@ struct leafi_index {
   // DSTree tables
   leafi::DBuf<int32_t> iv_s, iv_e, seg_off, seg_iv, left, right, node_leaf, split_iv, split_sd,
       path_off, path;
-  leafi::DBuf<double> mlo, mhi, slo, shi, thresh;
+  leafi::DBuf<float4> syn32;
+  leafi::DBuf<double> thresh;
   // iSAX tables
   leafi::DBuf<double> beta;
+  leafi::DBuf<float2> beta32;
   leafi::DBuf<int32_t> root_child, isplit, node_bits, lo_sym, hi_sym;
 
   // filters

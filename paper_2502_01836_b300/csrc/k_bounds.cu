@@ -1,9 +1,13 @@
 // Query preparation and summarisation lower bounds (Sec. 3, Alg. 2 line 4).
 //
-// Every float64 operation is written with an explicit round-to-nearest
-// intrinsic so nothing is contracted or reassociated: query statistics,
-// DSTree EAPCA bounds, iSAX MINDIST and the routing decisions equal the host
-// build's arithmetic bit for bit.
+// Query statistics (prefix sums, segment means and sigmas, PAA values) are
+// float64 and route queries exactly as the host build routed the series.  The
+// bounds themselves are float32: each statistic is carried as the pair of
+// floats enclosing it (conversions rounded down and up), each synopsis range
+// and breakpoint is widened outward the same way, so every float32 gap is at
+// most the float64 one and the bound stays a lower bound up to the relative
+// rounding of the final products and sums.  Every operation is written with an
+// explicit round-to-nearest intrinsic so nothing is contracted or reassociated.
 #include <cfloat>
 
 #include "internal.h"
@@ -46,13 +50,38 @@ __device__ __forceinline__ void interval_stat(const double* p1, const double* p2
   sd = __dsqrt_rn(var);
 }
 
-__device__ __forceinline__ double gap(double v, double lo, double hi) {
-  if (v < lo) return __dsub_rn(lo, v);
-  if (v > hi) return __dsub_rn(v, hi);
-  return 0.0;
+// gap of a value enclosed by [vd, vu] to a range [lo, hi] already widened
+// outward: zero when they may overlap, else one float32 subtraction between
+// the nearest ends, which is never above the gap of the value itself
+__device__ __forceinline__ float gap32(float vd, float vu, float lo, float hi) {
+  if (vu < lo) return __fsub_rn(lo, vu);
+  if (vd > hi) return __fsub_rn(vd, hi);
+  return 0.0f;
+}
+
+__device__ __forceinline__ float4 enclose(double mu, double sd) {
+  return make_float4(__double2float_rd(mu), __double2float_ru(mu), __double2float_rd(sd),
+                     __double2float_ru(sd));
+}
+
+// the float32 enclosures follow the float64 statistics of all nq queries
+__device__ __forceinline__ float4* ivstat_enclosures(double* ivstat, int nq, int n_iv) {
+  return reinterpret_cast<float4*>(ivstat + (size_t)nq * n_iv * 2);
+}
+__device__ __forceinline__ const float4* ivstat_enclosures(const double* ivstat, int nq,
+                                                           int n_iv) {
+  return reinterpret_cast<const float4*>(ivstat + (size_t)nq * n_iv * 2);
+}
+
+// one segment's term l (gap_mu^2 + gap_sigma^2) in float32, in this order
+__device__ __forceinline__ float seg_term(float4 st, float4 syn, float len) {
+  const float gm = gap32(st.x, st.y, syn.x, syn.y);
+  const float gs = gap32(st.z, st.w, syn.z, syn.w);
+  return __fmul_rn(len, __fadd_rn(__fmul_rn(gm, gm), __fmul_rn(gs, gs)));
 }
 
 // query statistics of every distinct segment interval: ivstat [nq][n_iv][2]
+// float64, then their enclosures [nq][n_iv] float4
 __global__ void ds_interval_kernel(DsTables T, const double* __restrict__ P, int nq, int m,
                                    double* __restrict__ ivstat) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,6 +92,7 @@ __global__ void ds_interval_kernel(DsTables T, const double* __restrict__ P, int
   interval_stat(p1, p1 + m + 1, T.iv_s[iv], T.iv_e[iv], mu, sd);
   ivstat[2 * t] = mu;
   ivstat[2 * t + 1] = sd;
+  ivstat_enclosures(ivstat, nq, T.n_iv)[t] = enclose(mu, sd);
 }
 
 // node bound: sum over the node's segments of l_r (gap_mu^2 + gap_sigma^2)
@@ -71,16 +101,14 @@ __global__ void ds_node_kernel(DsTables T, const double* __restrict__ ivstat, in
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nq * T.n_nodes) return;
   const int q = (int)(t / T.n_nodes), v = (int)(t % T.n_nodes);
-  const double* st = ivstat + (size_t)q * T.n_iv * 2;
-  double acc = 0.0;
+  const float4* st = ivstat_enclosures(ivstat, nq, T.n_iv) + (size_t)q * T.n_iv;
+  float acc = 0.0f;
   for (int r = T.seg_off[v]; r < T.seg_off[v + 1]; ++r) {
     const int iv = T.seg_iv[r];
-    const double gm = gap(st[2 * iv], T.mlo[r], T.mhi[r]);
-    const double gs = gap(st[2 * iv + 1], T.slo[r], T.shi[r]);
-    const double len = (double)(T.iv_e[iv] - T.iv_s[iv]);
-    acc = __dadd_rn(acc, __dmul_rn(len, __dadd_rn(__dmul_rn(gm, gm), __dmul_rn(gs, gs))));
+    const float len = (float)(T.iv_e[iv] - T.iv_s[iv]);
+    acc = __fadd_rn(acc, seg_term(st[iv], T.syn32[r], len));
   }
-  node_lb[t] = acc;
+  node_lb[t] = (double)acc;
 }
 
 // The same node bounds with each thread taking one node for a tile of QT
@@ -95,25 +123,23 @@ __global__ void ds_node_tiled_kernel(DsTables T, const double* __restrict__ ivst
   const int q0 = blockIdx.y * QT;
   if (v >= T.n_nodes) return;
   const int nqt = min(QT, nq - q0);
-  double acc[QT];
+  const float4* st = ivstat_enclosures(ivstat, nq, T.n_iv);
+  float acc[QT];
 #pragma unroll
-  for (int qq = 0; qq < QT; ++qq) acc[qq] = 0.0;
+  for (int qq = 0; qq < QT; ++qq) acc[qq] = 0.0f;
   for (int r = T.seg_off[v]; r < T.seg_off[v + 1]; ++r) {
     const int iv = T.seg_iv[r];
-    const double mlo = T.mlo[r], mhi = T.mhi[r], slo = T.slo[r], shi = T.shi[r];
-    const double len = (double)(T.iv_e[iv] - T.iv_s[iv]);
+    const float4 syn = T.syn32[r];
+    const float len = (float)(T.iv_e[iv] - T.iv_s[iv]);
 #pragma unroll
     for (int qq = 0; qq < QT; ++qq) {
       if (qq >= nqt) break;
-      const double* st = ivstat + ((size_t)(q0 + qq) * T.n_iv + iv) * 2;
-      const double gm = gap(st[0], mlo, mhi);
-      const double gs = gap(st[1], slo, shi);
-      acc[qq] = __dadd_rn(acc[qq], __dmul_rn(len, __dadd_rn(__dmul_rn(gm, gm), __dmul_rn(gs, gs))));
+      acc[qq] = __fadd_rn(acc[qq], seg_term(st[(size_t)(q0 + qq) * T.n_iv + iv], syn, len));
     }
   }
 #pragma unroll
   for (int qq = 0; qq < QT; ++qq)
-    if (qq < nqt) node_lb[(size_t)(q0 + qq) * T.n_nodes + v] = acc[qq];
+    if (qq < nqt) node_lb[(size_t)(q0 + qq) * T.n_nodes + v] = (double)acc[qq];
 }
 
 // leaf bound = max over the root-to-leaf path
@@ -154,11 +180,13 @@ __global__ void ds_interval_route_kernel(DsTables T, const double* __restrict__ 
   const int q = blockIdx.x;
   const double* p1 = P + (size_t)q * 2 * (m + 1);
   double* out = ivstat + (size_t)q * T.n_iv * 2;
+  float4* enc = ivstat_enclosures(ivstat, nq, T.n_iv) + (size_t)q * T.n_iv;
   for (int iv = threadIdx.x; iv < T.n_iv; iv += blockDim.x) {
     double mu, sd;
     interval_stat(p1, p1 + m + 1, T.iv_s[iv], T.iv_e[iv], mu, sd);
     out[2 * iv] = mu;
     out[2 * iv + 1] = sd;
+    enc[iv] = enclose(mu, sd);
     st_s[2 * iv] = mu;
     st_s[2 * iv + 1] = sd;
   }
@@ -174,6 +202,7 @@ __global__ void ds_interval_route_kernel(DsTables T, const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------- iSAX
+// PAA values [nq][w] float64, then their enclosures [nq][w] float2 {down, up}
 __global__ void isax_paa_kernel(IsaxTables T, const double* __restrict__ P, int nq, int m,
                                 double* __restrict__ paa) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -181,7 +210,10 @@ __global__ void isax_paa_kernel(IsaxTables T, const double* __restrict__ P, int 
   const int q = t / T.w, j = t % T.w;
   const int l = m / T.w;
   const double* p1 = P + (size_t)q * 2 * (m + 1);
-  paa[t] = __ddiv_rn(__dsub_rn(p1[(j + 1) * l], p1[j * l]), (double)l);
+  const double a = __ddiv_rn(__dsub_rn(p1[(j + 1) * l], p1[j * l]), (double)l);
+  paa[t] = a;
+  reinterpret_cast<float2*>(paa + (size_t)nq * T.w)[t] =
+      make_float2(__double2float_rd(a), __double2float_ru(a));
 }
 
 // MINDIST^2 of each leaf's word: sum_j l (gap(PAA_j, [beta_lo, beta_hi]))^2
@@ -190,16 +222,17 @@ __global__ void isax_leaf_kernel(IsaxTables T, const double* __restrict__ paa, i
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nq * T.n_leaves) return;
   const int q = (int)(t / T.n_leaves), lf = (int)(t % T.n_leaves);
-  const double len = (double)(m / T.w);
-  const double* a = paa + (size_t)q * T.w;
+  const float len = (float)(m / T.w);
+  const float2* a = reinterpret_cast<const float2*>(paa + (size_t)nq * T.w) + (size_t)q * T.w;
   const int32_t* lo = T.lo_sym + (size_t)lf * T.w;
   const int32_t* hi = T.hi_sym + (size_t)lf * T.w;
-  double acc = 0.0;
+  float acc = 0.0f;
   for (int j = 0; j < T.w; ++j) {
-    const double g = gap(a[j], T.beta[lo[j]], T.beta[hi[j]]);
-    acc = __dadd_rn(acc, __dmul_rn(len, __dmul_rn(g, g)));
+    const float2 v = a[j];
+    const float g = gap32(v.x, v.y, T.beta32[lo[j]].x, T.beta32[hi[j]].y);
+    acc = __fadd_rn(acc, __fmul_rn(len, __fmul_rn(g, g)));
   }
-  leaf_lb[t] = acc;
+  leaf_lb[t] = (double)acc;
 }
 
 __device__ int sax_symbol(const double* beta, int C, double v) {

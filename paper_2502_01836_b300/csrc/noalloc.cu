@@ -100,10 +100,10 @@ extern "C" leafi_status leafi_leaf_lower_bounds_noalloc(leafi_index* index, cons
     size_t need = bP;
     size_t bA = 0, bB = 0;
     if (t.type == LEAFI_DSTREE) {
-      bA = align256(sizeof(double) * (size_t)nq * t.iv_s.size() * 2);
+      bA = align256(sizeof(double) * ds_ivstat_doubles(nq, t.iv_s.size()));
       bB = align256(sizeof(double) * (size_t)nq * t.n_nodes);
     } else {
-      bA = align256(sizeof(double) * (size_t)nq * t.w);
+      bA = align256(sizeof(double) * isax_paa_doubles(nq, t.w));
     }
     need += bA + bB;
     if (need > kNoAllocScratchBytes)

@@ -148,6 +148,115 @@ def test_dstree_structure_and_lb_invariant(rw):
     assert (own[np.arange(50), lo[:50]] == 0.0).all()
 
 
+U32 = 2.0 ** -24  # unit roundoff of float32
+
+
+def _stats64(X, cuts):
+    """Segment means and sigmas of float32 rows from float64 running sums."""
+    X = X.astype(np.float64)
+    P1 = np.concatenate([np.zeros((len(X), 1)), np.cumsum(X, axis=1)], axis=1)
+    P2 = np.concatenate([np.zeros((len(X), 1)), np.cumsum(X * X, axis=1)], axis=1)
+    mu, sd = [], []
+    for s, e in zip(cuts[:-1], cuts[1:]):
+        u = (P1[:, e] - P1[:, s]) / (e - s)
+        v = (P2[:, e] - P2[:, s]) / (e - s) - u * u
+        mu.append(u)
+        sd.append(np.sqrt(np.maximum(v, 0.0)))
+    return np.stack(mu, 1), np.stack(sd, 1)
+
+
+def _gap_and_slack(v, lo, hi):
+    """float64 gap of v to [lo, hi] and how far the float32 enclosures of v,
+    lo and hi can pull the float32 gap below it (one float32 ulp each)."""
+    g = np.where(v < lo, lo - v, np.where(v > hi, v - hi, 0.0))
+    mag = np.maximum(np.abs(v), np.maximum(np.where(np.isfinite(lo), np.abs(lo), 0.0),
+                                           np.where(np.isfinite(hi), np.abs(hi), 0.0)))
+    return g, 2.0 ** -22 * mag + 1e-44
+
+
+def _within_enclosure_error(lb32, terms, n_terms):
+    """The float32 bound lies between the float64 bound computed on the
+    narrowed gaps and the float64 bound itself, each widened by the relative
+    rounding of n_terms float32 products and sums."""
+    lo_terms, hi_terms = terms
+    grow = (1 + U32) ** (n_terms + 5)
+    assert (lb32 <= hi_terms.sum(1) * grow).all(), np.max(lb32 / np.maximum(hi_terms.sum(1), 1e-300))
+    assert (lb32 >= lo_terms.sum(1) / grow).all()
+
+
+def test_dstree_float32_bound_within_enclosure_error():
+    """The DSTree bound is evaluated in float32 on outward-rounded synopses and
+    query statistics: against the float64 bound of the same one-leaf tree it
+    is never larger beyond product/sum rounding, and never smaller than the
+    gaps narrowed by one ulp of each end.  The queries sit just outside the
+    ranges (gaps of 1e-5 in the mean, 1e-5 relative in sigma), where rounding
+    the query statistic or a range end the wrong way would exceed the upper
+    side by orders of magnitude; random queries and the series themselves
+    (bound 0) are included."""
+    m = 64
+    X = fx.random_walk(500, m, seed=41)
+    t = O.Tree(X, "dstree", leaf_cap=1000, init_segments=4)
+    assert t.L == 1
+    cuts = [0, 16, 32, 48, 64]
+    mu, sd = _stats64(X, cuts)
+    mlo, mhi, slo, shi = mu.min(0), mu.max(0), sd.min(0), sd.max(0)
+    near = []
+    for r in range(4):
+        s, e = cuts[r], cuts[r + 1]
+        hi_row = X[np.argmax(mu[:, r])].copy()
+        hi_row[s:e] += np.float32(1e-5)
+        lo_row = X[np.argmin(mu[:, r])].copy()
+        lo_row[s:e] -= np.float32(1e-5)
+        wide = X[np.argmax(sd[:, r])].copy()
+        c = wide[s:e].astype(np.float64).mean()
+        wide[s:e] = (c + (wide[s:e] - c) * (1 + 1e-5)).astype(np.float32)
+        near += [hi_row, lo_row, wide]
+    Q = np.concatenate([np.array(near, np.float32), fx.test_queries(X, 40, seed=42), X[:20]])
+    qmu, qsd = _stats64(Q, cuts)
+    gm, em = _gap_and_slack(qmu, mlo, mhi)
+    gs, es = _gap_and_slack(qsd, slo, shi)
+    ln = np.diff(cuts).astype(np.float64)
+    hi_terms = ln * (gm * gm + gs * gs)
+    lo_terms = ln * (np.maximum(gm - em, 0) ** 2 + np.maximum(gs - es, 0) ** 2)
+    lb32 = t.lb2(Q)[:, 0]
+    assert (gm[:12] > 0).any() and (hi_terms[:12].sum(1) < 1e-6).any()
+    _within_enclosure_error(lb32, (lo_terms, hi_terms), 4)
+    assert (lb32[-20:] == 0.0).all()
+    assert (lb32 == lb32.astype(np.float32)).all()  # a float32 value
+
+
+def test_isax_float32_bound_within_enclosure_error():
+    """iSAX MINDIST in float32 against the float64 one, on a tree whose leaf
+    words end at the breakpoint 0.6745 (not a float32): two series with PAA
+    (0.3, 0.3) and (1.0, 0.3) share a root child of capacity 1, which splits
+    segment 0 at that breakpoint.  Queries put PAA_0 1e-4 on either side of it,
+    where rounding the breakpoint inward would raise the bound far above the
+    float64 one."""
+    beta = O.isax_breakpoints(2)[2]  # 0.67449...
+    X = np.array([[0.3, 0.3, 0.3, 0.3], [1.0, 1.0, 0.3, 0.3]], np.float32)
+    t = O.Tree(X, "isax", leaf_cap=1, isax_w=2, isax_bits=2)
+    assert t.L == 2
+    la, lb_ = t.leaf_of()
+    # leaf of series 0: segment 0 in [0, beta), segment 1 in [0, inf);
+    # leaf of series 1: segment 0 in [beta, inf), segment 1 in [0, inf)
+    ranges = {la: ((0.0, beta), (0.0, np.inf)), lb_: ((beta, np.inf), (0.0, np.inf))}
+    vals = [beta + 1e-4, beta - 1e-4, beta + 3e-7, beta - 3e-7, 2.0, -0.5, 0.1]
+    Q = np.array([[v, v, w, w] for v in vals for w in (0.25, -0.01)], np.float32)
+    paa = Q.astype(np.float64).reshape(len(Q), 2, 2).mean(2)
+    lb32 = t.lb2(Q)
+    for leaf, rg in ranges.items():
+        lo = np.array([r[0] for r in rg])
+        hi = np.array([r[1] for r in rg])
+        g, e = _gap_and_slack(paa, lo, hi)
+        hi_terms = 2.0 * g * g
+        lo_terms = 2.0 * np.maximum(g - e, 0) ** 2
+        _within_enclosure_error(lb32[:, leaf], (lo_terms, hi_terms), 2)
+    # 1e-4 from the breakpoint with segment 1 inside its range: one leaf's
+    # bound is 0, the other's positive and about 2e-8
+    near = lb32[[0, 2]]
+    assert (near.min(1) == 0).all() and (near.max(1) > 1e-8).all() and (near.max(1) < 3e-8).all()
+
+
 # ---------------------------------------------------------------- iSAX
 
 def test_isax_breakpoints_are_normal_quantiles():
