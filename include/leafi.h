@@ -176,7 +176,7 @@ leafi_status leafi_leaf_sizes(const leafi_index* index, int64_t* sizes);
 leafi_status leafi_leaf_of(const leafi_index* index, int32_t* leaf_of);
 
 /* ------------------------------------------------------------------ */
-/* Lower bounds and routing (Sec. 3; Alg. 2 line 4)                    */
+/* Lower bounds and routing (Sec. 3; Alg. 2's bound test)             */
 /* ------------------------------------------------------------------ */
 
 /* Squared leaf lower bounds LB^2 (nq x n_leaves, row-major, float64 arrays
@@ -300,7 +300,7 @@ leafi_status leafi_leaf_knn(leafi_index* index, const float* queries, int64_t nq
 leafi_status leafi_train_targets(leafi_index* index, const float* Qg, int64_t ng,
                                  const float* Ql, int64_t nl, float* Tg, float* Tl);
 
-/* LeaFi-enhanced index building, Alg. 1 end to end (lines 1-10): select the
+/* LeaFi-enhanced index building, Alg. 1 end to end: select the
  * filtered leaves (Alg. 3), generate the global and local training queries,
  * compute their targets d^L, train every filter by SGD and fit the auto-tuners
  * on the calibration set.  Every random draw (which series a query comes from,
@@ -378,8 +378,8 @@ typedef struct {
   double lr0, lr_min;       /* 0.01 and 1e-5 in the paper */
 } leafi_sgd_params;
 
-/* Alg. 1 lines 3-9 on queries the caller supplies (inspection export for
- * parity checks): computes the targets of Qg [n_gtrain+n_gval][m] and
+/* Alg. 1's target collection and training on queries the caller supplies
+ * (inspection export for parity checks): computes the targets of Qg [n_gtrain+n_gval][m] and
  * Ql [F][n_ltrain+n_lval][m] on the device, then trains every installed
  * filter (either model) by SGD on the MSE loss from its current weights, one shuffle
  * perms [max_epochs][n_gtrain+n_ltrain] per epoch; keeps the weights of the
@@ -459,9 +459,9 @@ typedef struct {
   double host_wait_ms;     /* host time the call spent waiting for the GPU (batch pair
                               counts, its end) */
   double host_ms;          /* host time of the whole call */
-  int64_t filter_pruned;   /* (query, leaf) pairs pruned by the leaf's filter (Alg. 2 line 6) */
+  int64_t filter_pruned;   /* (query, leaf) pairs pruned by the leaf's filter (Alg. 2) */
   int64_t lb_pruned;       /* (query, leaf) pairs neither searched nor filter-pruned: pruned
-                              by the summarisation bound (Alg. 2 line 4) */
+                              by the summarisation bound (Alg. 2) */
 } leafi_search_stats;
 
 /* k-NN of nq queries (1 <= k <= LEAFI_MAX_K).  recall_target >= 1 runs the

@@ -839,8 +839,8 @@ void or_train_targets(const or_tree* t, const int32_t* filter_leaf, int F, const
 }
 
 /* ------------------------------------------------------------------ */
-/* Alg. 1 random draws: GenerateGlobalQueries / GenerateLocalQueries    */
-/* (lines 2 and 6), initial weights and per-epoch shuffles.            */
+/* Alg. 1 random draws: GenerateGlobalQueries / GenerateLocalQueries,   */
+/* initial weights and per-epoch shuffles.                             */
 /*                                                                     */
 /* Counter-based generator: Philox4x32-10 as published by Salmon,      */
 /* Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2,   */
@@ -934,12 +934,12 @@ void or_training_queries(const or_tree* t, const int32_t* filter_leaf, int F, in
                          float* Qg, float* Ql, int64_t* gpick, int64_t* lpick) {
   const int m = t->m;
   double* tmp = (double*)malloc(sizeof(double) * (m + 1));
-  /* line 2: global queries from uniformly drawn dataset series (original ids) */
+  /* GenerateGlobalQueries: uniformly drawn dataset series (original ids) */
   floyd(seed, OR_TAG_GPICK, 0, (uint64_t)t->n, n_global, gpick);
   for (int64_t i = 0; i < n_global; ++i)
     noisy_query(t->X + gpick[i] * m, m, seed, (uint32_t)i, 0, noise_lo, noise_hi, tmp,
                 Qg + i * m);
-  /* line 6: local queries from the members of each filtered leaf (ascending ids) */
+  /* GenerateLocalQueries: members of each filtered leaf (ascending ids) */
   for (int f = 0; f < F; ++f) {
     const node_t* nd = &t->nodes[t->leaf_node[filter_leaf[f]]];
     const uint64_t sz = (uint64_t)nd->nids;
@@ -1393,9 +1393,9 @@ void or_cnn_train(const or_train_params* p, int F, int C, int m, const float* Qg
 /* first, then the remaining leaves are visited in ascending (LB^2,    */
 /* leaf id).  A wave takes the next `wave` leaves that survive the     */
 /* cascade against the best-so-far of the wave's start; wave = 1 is    */
-/* the sequential loop of Alg. 2.  LB test (line 4): LB^2 (1 - 1e-4) >  */
+/* the sequential loop of Alg. 2.  Bound test: LB^2 (1 - 1e-4) >       */
 /* bsf^2, the factor absorbing float32 rounding of the distance.       */
-/* Filter test (line 6): d^F > sqrtf(bsf^2) in float64.                 */
+/* Filter test: d^F > sqrtf(bsf^2) in float64.                         */
 /* ------------------------------------------------------------------ */
 
 typedef struct {

@@ -130,7 +130,7 @@ int32_t or_select_leaves_alg3(const int64_t* sizes, int32_t L, double th, double
 /* Philox4x32-10 (Salmon et al., SC 2011): out = bijection(ctr) under key. */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
-/* Alg. 1 lines 2 and 6: n_global queries from distinct dataset series (gpick,
+/* Alg. 1's query generation: n_global queries from distinct dataset series (gpick,
  * original ids) and n_local queries per filtered leaf from its members (lpick
  * [F][n_local], original ids), each + Gaussian noise of sigma ~ U[lo, hi] and
  * re-z-normalised.  Qg [n_global][m], Ql [F][n_local][m]. */

@@ -224,7 +224,7 @@ def philox4x32_10(ctr, key):
 
 
 def training_queries(tree: Tree, filter_leaf, n_global, n_local, noise_lo, noise_hi, seed):
-    """Alg. 1 lines 2 and 6 -> (Qg [ng, m], Ql [F, nl, m], gpick [ng], lpick [F, nl])."""
+    """Alg. 1 GenerateGlobalQueries / GenerateLocalQueries -> (Qg [ng, m], Ql [F, nl, m], gpick [ng], lpick [F, nl])."""
     fl = np.ascontiguousarray(filter_leaf, np.int32)
     F = fl.shape[0]
     Qg = np.zeros((n_global, tree.m), np.float32)

@@ -609,7 +609,7 @@ def leafi_epoch_permutations(epochs, n, seed):
 
 def leafi_train_filters_on(index, params: SgdParams, Qg, Ql, perms, epochs_run=None,
                            best_val=None):
-    """Alg. 1 lines 3-9 on caller-supplied queries and shuffles (parity checks)."""
+    """Alg. 1 target collection and training on caller-supplied queries and shuffles (parity checks)."""
     _check(lib().leafi_train_filters_on(index, C.byref(params), _ptr(Qg, np.float32, "Qg"),
                                         _ptr(Ql, np.float32, "Ql"), _ptr(perms, np.int32, "perms"),
                                         _ptr(epochs_run, np.int32, "epochs_run", True),

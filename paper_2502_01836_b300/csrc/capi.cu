@@ -2311,7 +2311,7 @@ void finish_training(leafi_index* index, int F, const int32_t* d_ep, const doubl
   index->nk = 0;
 }
 
-// Alg. 1 lines 3-9 on staged queries: targets of Qg [ng][mp] and Ql
+// Alg. 1 target collection and training on staged queries: targets of Qg [ng][mp] and Ql
 // [F][nl][mp] on the device, then SGD of every filter from its installed
 // weights with one shuffle per epoch (hperm [max_epochs][n_gtrain + n_ltrain]).
 // The caller holds the index mutex with the device current.
@@ -2588,7 +2588,7 @@ Alg1Counts alg1_counts(const leafi_train_params* p) {
   return c;
 }
 
-// Alg. 1 lines 2 and 6 for the leaves fl: rows [ng + F*nl][mp] of out, the
+// Alg. 1 GenerateGlobalQueries / GenerateLocalQueries for the leaves fl: rows [ng + F*nl][mp] of out, the
 // global queries first, then filter by filter; picks (original ids) to gpick
 // [ng] and lpick [F][nl] when given.  Caller holds the mutex, device current.
 void generate_training_queries(leafi_index* ix, const leafi_train_params* p, const Alg1Counts& c,
@@ -2800,7 +2800,7 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     cudaStream_t s = index->stream;
     leafi_train_report rep{};
     auto t0 = std::chrono::steady_clock::now();
-    // line 1: SelectLeafNodes
+    // SelectLeafNodes
     std::vector<int32_t> fl;
     if (p->n_filters > 0) {
       std::vector<int32_t> idx(L);
@@ -2829,14 +2829,14 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
     else
       launch_gen_weights(F, h, index->m, p->seed, index->W1t.p, index->b1.p, index->w2.p,
                          index->b2.p, s);
-    // lines 2 and 6: GenerateGlobalQueries / GenerateLocalQueries
+    // GenerateGlobalQueries / GenerateLocalQueries
     DBuf<float> Q;
     generate_training_queries(index, p, c, fl, Q, nullptr, nullptr);
     std::vector<int32_t> hperm((size_t)p->max_epochs * (c.n_gtrain + c.n_ltrain));
     gen_epoch_perms(p->max_epochs, c.n_gtrain + c.n_ltrain, p->seed, hperm.data());
     rep.seconds_generate = seconds_since(t0);
     t0 = std::chrono::steady_clock::now();
-    // lines 3-9: targets and training
+    // targets and training
     const float* dQg = Q.p;
     const float* dQl = Q.p + (size_t)c.ng * index->mp;
     std::vector<int32_t> ep(F);
@@ -2849,7 +2849,7 @@ leafi_status leafi_train_filters(leafi_index* index, const leafi_train_params* p
       const leafi_tune_params tp = default_tune_params(p->seed);
       tune_core(index, &tp, nullptr);
     }
-    // line 10: auto-tuners on the calibration set (the global validation queries)
+    // auto-tuners on the calibration set (the global validation queries)
     index->calib_confidence = p->confidence;
     index->calib_mode = p->calib_mode;
     fit_core(index, dQg + (size_t)c.n_gtrain * index->mp, c.n_gval, p->kclasses, p->n_kclasses);

@@ -348,7 +348,7 @@ struct KernelClock {
   double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
-// wave selection (Alg. 2 lines 3-7) walking a precomputed visiting order
+// wave selection (Alg. 2's leaf loop) walking a precomputed visiting order
 // (`ord` [nq][L] ascending (LB^2, leaf id), cursor = next position per query)
 void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s);
 // the same picks for a wave at least as wide as the index (a.W >= a.L): no order needed

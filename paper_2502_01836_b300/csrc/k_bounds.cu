@@ -1,4 +1,4 @@
-// Query preparation and summarisation lower bounds (Sec. 3, Alg. 2 line 4).
+// Query preparation and summarisation lower bounds (Sec. 3; Alg. 2's bound test).
 //
 // Query statistics (prefix sums, segment means and sigmas, PAA values) are
 // float64 and route queries exactly as the host build routed the series.  The

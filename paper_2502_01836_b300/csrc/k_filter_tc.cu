@@ -1,4 +1,4 @@
-// Learned-filter forward on the tensor cores (Sec. 4, Sec. 5.1; Alg. 2 line 5):
+// Learned-filter forward on the tensor cores (Sec. 4, Sec. 5.1; Alg. 2's filter inference):
 //   out[q][f] = b2_f + sum_j w2_fj relu(b1_fj + sum_i W1_fji q_i)
 // for a whole query batch against every filter.
 //

@@ -1,5 +1,5 @@
 // Alg. 1's random draws inside the library: the training queries of
-// GenerateGlobalQueries / GenerateLocalQueries (Alg. 1 lines 2 and 6), the
+// GenerateGlobalQueries / GenerateLocalQueries (Alg. 1), the
 // filters' initial weights and the per-epoch SGD shuffles, plus float64
 // z-normalisation of caller data.
 //

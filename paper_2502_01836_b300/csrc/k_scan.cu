@@ -641,8 +641,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(
 // ---------------------------------------------------------------- select
 // One block per query: the next W leaves of the wave, i.e. the W smallest
 // (LB^2, leaf) keys beyond the query's cursor among leaves that are neither
-// searched, nor pruned by the bound (Alg. 2 line 4), nor by the filter
-// (Alg. 2 line 6) against the best-so-far of the wave's start.
+// searched, nor pruned by the bound test of Alg. 2, nor by its filter
+// test, against the best-so-far of the wave's start.
 constexpr int kSelThreads = 128;
 
 // Walk of the precomputed visiting order from the query's cursor: the next W
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(kSelThreads) select_walk_kernel(SelectArgs a,
       if (rank == a.W - 1) s_newcur = p + 1;
     }
     __syncthreads();
-    // filter-pruned positions the cursor passes for good (Alg. 2 line 6); a
+    // filter-pruned positions the cursor passes for good (Alg. 2's filter test); a
     // position at or after the next wave's start is examined again then
     const int cut = picked + total >= a.W ? s_newcur : first_stop;
     {
@@ -770,7 +770,7 @@ __global__ void select_all_kernel(SelectArgs a) {
       const double df =
           __dsub_rn((double)a.P[(size_t)q * a.F + f], a.alpha[(size_t)f * a.nc + a.jpos[q]]);
       if (df > bsf) {
-        atomicAdd(&a.stat[4], 1ull);  // filter-pruned (Alg. 2 line 6)
+        atomicAdd(&a.stat[4], 1ull);  // filter-pruned (Alg. 2's filter test)
         return;
       }
     }

@@ -424,7 +424,7 @@ def gen_tree():
 def test_training_queries_picks(gen_tree):
     """Global picks are distinct dataset ids; local picks are members of their
     leaf, distinct when the leaf is large enough, drawn with replacement
-    otherwise (Alg. 1 lines 2 and 6)."""
+    otherwise (Alg. 1's query generation)."""
     X, t = gen_tree
     sizes = t.leaf_sizes()
     small = int(np.argmin(sizes))
