@@ -238,6 +238,8 @@ def workload_config(a):
             "items_per_sm": getattr(a, "items_per_sm", 4),
             "min_part": getattr(a, "min_part", 512),
             "scan_blocks": getattr(a, "scan_blocks", 0),
+            "scan_path": {0: "float16 tensor cores", 1: "CUDA cores",
+                          2: "e4m3 tensor cores"}.get(getattr(a, "scan_path", 0)),
             "l2": "inputs larger than L2 (%.2f GB float32 series, %.2f GB float16 copy)"
                   % (a.n * M * 4 / 1e9, a.n * M * 2 / 1e9)}
 
@@ -739,7 +741,8 @@ def main():
     from paper_2502_01836_b300.workflow import enhance
 
     X = fx.random_walk(a.n, M)
-    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=local))
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=local,
+                                           scan_path=a.scan_path))
     stream = torch.cuda.current_stream(dev)
     lf.leafi_set_stream(idx, stream.cuda_stream)
     lf.leafi_set_query_schedule(idx, not a.no_schedule)
