@@ -693,7 +693,8 @@ def run_cnn(a):
             lf.leafi_search(idx, Qd, 1, target, ids, dd, st)
         torch.cuda.synchronize()
         sec = (time.perf_counter() - t0) / reps
-        return a.queries / sec, ids[:, 0].cpu().numpy().copy(), st.series_scanned / a.queries / reps
+        # the statistics describe the last call
+        return a.queries / sec, ids[:, 0].cpu().numpy().copy(), st.series_scanned / a.queries
 
     bp = lf.BuildParams(leaf_capacity=a.leaf_cap, wave=a.wave, device=0)
     idx = lf.leafi_build(X, bp)
@@ -997,6 +998,9 @@ def main():
                                  "bound_pruned": st["lb_pruned"] / (a.steps * a.queries),
                                  "filter_pruned": st["filter_pruned"] / (a.steps * a.queries),
                                  "plain_searched": st_ex["leaves_scanned"] / (a.steps * a.queries)},
+            # filter predictions made per query (query tiles whose pairs no wave
+            # select can read are skipped once the route leaves set a best-so-far)
+            "filter_evals_per_query": st["filter_evals"] / (a.steps * a.queries),
             "plain_pruning_ratio": 1.0 - st_ex["series_scanned"] / (a.steps * a.queries * a.n),
             "waves_per_launch": st["waves"] / max(st["batches"], 1),
             "host_ms_per_step": {"call": st["host_ms"] / a.steps,

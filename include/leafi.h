@@ -449,7 +449,11 @@ leafi_status leafi_set_autotuners(leafi_index* index, const double* alpha_sorted
 typedef struct {
   int64_t leaves_scanned;  /* (query, leaf) pairs searched */
   int64_t series_scanned;  /* (query, series) distances computed */
-  int64_t filter_evals;    /* (query, filter) predictions */
+  int64_t filter_evals;    /* (query, filter) predictions made: after the route
+                              leaves' round the tensor-core forward skips the
+                              128-query tiles in which no (query, filter) pair
+                              can reach a filter test (leaf searched or bound-
+                              pruned for every query of the tile) */
   int64_t waves;           /* scan rounds launched, summed over batches (a full batch
                               always launches its first two, the second maybe empty) */
   int64_t batches;         /* internal query batches (256 queries each) */

@@ -335,8 +335,11 @@ void ensure_wsplit(leafi_index* ix) {
 }
 
 // P[q][f] for nq queries (device rows of mp floats); `cap_rows` sizes the
-// scratch for later calls of up to that many queries
-void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_rows = 0) {
+// scratch for later calls of up to that many queries.  need / evals (the
+// tensor-core forward only): skip the (filter, query tile) blocks whose flag
+// is 0 and count the predictions made.
+void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_rows = 0,
+                    const int32_t* need = nullptr, unsigned long long* evals = nullptr) {
   if (nq <= 0 || ix->F <= 0) return;
   if (ix->model == LEAFI_FILTER_CNN) {
     launch_cnn_forward(dQ, nq, ix->mp, ix->m, ix->F, ix->h, ix->cnn.p, P, ix->stream);
@@ -357,7 +360,7 @@ void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_
                  (uint64_t)Kq * 4, 32, 128))
     fail(LEAFI_ECUDA, "cannot encode the query tensor map");
   launch_filter_tc(qmap, ix->wmap, dQ, nq, ix->mp, ix->m, ix->F, ix->h, Qs, ix->b1.p, ix->w2.p,
-                   ix->b2.p, P, ix->sErr.p, ix->stream);
+                   ix->b2.p, P, ix->sErr.p, ix->stream, need, evals);
 }
 
 // One scan round: group pairs by leaf, scan, merge candidates into slots.
@@ -827,6 +830,7 @@ struct Pipeline {
   int nlanes = 1;
   int kmax = 1, W = 1, L = 0, cap = 0, qb = kBatch;
   unsigned long long* stat = nullptr;   // device counters of the pipeline's batches
+                                        // (kPipelineStats)
   bool pre_p = false;                   // scheduled batches: prefix sums gathered, not computed
   leafi_search_stats st{};
   LaneView lv[kMaxLanes];
@@ -914,7 +918,10 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     v.ord = S.sOrd.need((size_t)qb * L);
     v.cursor = S.sCursor.need(qb);
     v.order_tmp = L > calib_max_sort() ? S.sOrderTmp.need(leaf_order_scratch(qb, L)) : nullptr;
-    if (any_filtered && filter_tc(ix)) S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
+    if (any_filtered && filter_tc(ix)) {
+      S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
+      S.sNeed.need((size_t)((qb + kFilterTile - 1) / kFilterTile) * ix->F);
+    }
     v.tq = TcQueries();
     if (ix->tc_scan()) {
       if (ix->scan_path == 2) v.tq.Q8 = S.sQ8.need((size_t)qb * ix->kp);
@@ -1000,12 +1007,8 @@ void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
   compute_bounds(ix, v.gQ, nb, v.lb2, v.route, pre_p);
   ix->tock();
   launch_query_prep(ix, v.gQ, nb, v.tq, s);
-  if (use_f) {
-    ix->tick(4);
-    filter_forward(ix, v.gQ, nb, v.P, qb);
-    ix->tock();
+  if (use_f)
     launch_jpos(nb, v.dK, v.dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, v.jpos, s);
-  }
   LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
   if (W < L) launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);  // a wave of W >= L needs no order
   LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
@@ -1015,6 +1018,20 @@ void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
   launch_route_pairs(nb, v.route, L, v.scanned, ix->leaf_off.p, v.pairs, v.np, stat, s);
   run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr, v.cand,
             v.cand_cnt, cap, stat + 2, stat + 3);
+  // the filters run once the route leaves have set a best-so-far: only the
+  // (filter, query tile) blocks whose predictions a wave select can read
+  if (use_f) {
+    ix->tick(4);
+    int32_t* need = lanes[cur_lane].sNeed.p;  // sized by setup for filtered calls
+    if (filter_tc(ix) && need) {
+      launch_filter_need(nb, ix->F, L, ix->d_filter_leaf.p, v.lb2, v.thr, v.scanned, v.jpos, need,
+                         s);
+      filter_forward(ix, v.gQ, nb, v.P, qb, need, stat + 5);
+    } else {
+      filter_forward(ix, v.gQ, nb, v.P, qb);
+    }
+    ix->tock();
+  }
   select(v);
 }
 
@@ -1151,7 +1168,8 @@ void Pipeline::launch_batch(int li, int nb, const int32_t* kq, const double* tar
   f.nb = nb;
   f.use_f = false;
   for (int i = 0; i < (uniform ? 1 : nb); ++i) f.use_f = f.use_f || target[i] < 1.0;
-  if (f.use_f) st.filter_evals += (int64_t)nb * ix->F;
+  // the tensor-core forward of a pipeline counts its own predictions (stat[5])
+  if (f.use_f && !(filter_tc(ix) && lanes[li].sNeed.p)) st.filter_evals += (int64_t)nb * ix->F;
   f.g = graph_for(v, nb, f.use_f);
   if (f.g) {
     LF_CUDA(cudaGraphLaunch(f.g->exec, s));
@@ -1234,14 +1252,14 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       ix->capturing = nullptr;
     }
   } restore{ix, user};
-  unsigned long long* stat = ix->sStat.need(5);
+  unsigned long long* stat = ix->sStat.need(kPipelineStats);
   Pipeline pl;
   pl.setup(ix, ix->lanes, nlanes, kmax, any_filtered, stat, qb);
   const bool uniform =
       std::all_of(kq.begin(), kq.end(), [&](int32_t v) { return v == kq[0]; }) &&
       std::all_of(target.begin(), target.end(), [&](double v) { return v == target[0]; });
   // the lanes start after the caller's stream (inputs written there are visible)
-  LF_CUDA(cudaMemsetAsync(stat, 0, 5 * sizeof(unsigned long long), user));
+  LF_CUDA(cudaMemsetAsync(stat, 0, kPipelineStats * sizeof(unsigned long long), user));
   cudaEvent_t ev_start = nullptr;
   LF_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
   struct EvGuard {
@@ -1344,7 +1362,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
     deliver(ids, out_i, (size_t)nq * kmax, user);
     deliver(dists, out_d, (size_t)nq * kmax, user);
   }
-  unsigned long long h_stat[5] = {0, 0, 0, 0, 0};
+  unsigned long long h_stat[kPipelineStats] = {};
   LF_CUDA(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, user));
   const auto w_end = std::chrono::steady_clock::now();
   LF_CUDA(cudaStreamSynchronize(user));
@@ -1358,6 +1376,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   st.distinct_series = (int64_t)h_stat[2];
   st.rechecks = (int64_t)h_stat[3];
   st.filter_pruned = (int64_t)h_stat[4];
+  st.filter_evals += (int64_t)h_stat[5];
   st.lb_pruned = nq * (int64_t)ix->tree.n_leaves - st.leaves_scanned - st.filter_pruned;
   ix->settle();
   if (stats) *stats = st;
@@ -3388,8 +3407,8 @@ leafi_status leafi_serve_start(leafi_index* index, const leafi_serve_params* par
     sv->p = p;
     {
       DeviceGuard dg(index->device);
-      sv->stat.need(5);
-      LF_CUDA(cudaMemset(sv->stat.p, 0, 5 * sizeof(unsigned long long)));
+      sv->stat.need(kPipelineStats);
+      LF_CUDA(cudaMemset(sv->stat.p, 0, kPipelineStats * sizeof(unsigned long long)));
       for (int li = 0; li < kServeLanes; ++li) {
         const size_t b = (size_t)p.max_batch;
         LF_CUDA(cudaMallocHost(&sv->hq[li], sizeof(float) * b * index->m));
@@ -3484,7 +3503,7 @@ leafi_status leafi_serve_get_stats(leafi_server* sv, leafi_serve_stats* stats) {
       std::lock_guard<std::mutex> lk(sv->mu);
       c = sv->counters;
     }
-    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    unsigned long long h[kPipelineStats] = {};
     on_index(sv, [&] {
       DeviceGuard dg(sv->ix->device);
       LF_CUDA(cudaMemcpy(h, sv->stat.p, sizeof(h), cudaMemcpyDeviceToHost));
@@ -3495,6 +3514,7 @@ leafi_status leafi_serve_get_stats(leafi_server* sv, leafi_serve_stats* stats) {
     st.distinct_series = (int64_t)h[2];
     st.rechecks = (int64_t)h[3];
     st.filter_pruned = (int64_t)h[4];
+    st.filter_evals += (int64_t)h[5];
     st.lb_pruned = c.queries * (int64_t)sv->ix->tree.n_leaves - st.leaves_scanned - st.filter_pruned;
     c.graph_batches = st.graph_batches;
     c.search = st;

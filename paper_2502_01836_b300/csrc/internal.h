@@ -142,9 +142,18 @@ void launch_route_keys(const leafi_index* ix, const double* P, int nq, int32_t* 
                        cudaStream_t s);
 bool filter_tc_fits(int m, int h, int smem_optin);
 void launch_wsplit(const float* W1t, int F, int m, int h, float* Ws, cudaStream_t s);
+// device counters of a search pipeline: [0] leaves searched, [1] series
+// scanned, [2] distinct series, [3] canonical re-checks, [4] filter-pruned
+// (query, leaf) pairs, [5] filter predictions made by the tensor-core forward
+constexpr int kPipelineStats = 6;
+// queries per CTA of the tensor-core filter forward (the tiles of `need`)
+constexpr int kFilterTile = 128;
+// need (nullable): [ceil(nq / kFilterTile)][F], a (filter, query tile) CTA
+// whose flag is 0 computes nothing; evals (nullable) += the predictions made
 void launch_filter_tc(const CUtensorMap& qmap, const CUtensorMap& wmap, const float* Q, int nq,
                       int mp, int m, int F, int h, float* Qs, const float* b1, const float* w2,
-                      const float* b2, float* out, int32_t* err, cudaStream_t s);
+                      const float* b2, float* out, int32_t* err, cudaStream_t s,
+                      const int32_t* need = nullptr, unsigned long long* evals = nullptr);
 void launch_filter_forward(const float* Q, int nq, int mp, int m, int F, int h, const float* W1t,
                            const float* b1, const float* w2, const float* b2, float* out,
                            cudaStream_t s);
@@ -353,6 +362,12 @@ struct KernelClock {
 void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s);
 // the same picks for a wave at least as wide as the index (a.W >= a.L): no order needed
 void launch_select_all(const SelectArgs& a, cudaStream_t s);
+// need[tile][f] = 1 when some query of the kFilterTile-query tile may have its
+// filter f read by a later wave select: it uses filters, f's leaf is not
+// searched and passes the bound test against the current best-so-far
+void launch_filter_need(int nq, int F, int L, const int32_t* filter_leaf, const double* lb2,
+                        const unsigned long long* thr, const unsigned char* scanned,
+                        const int32_t* jpos, int32_t* need, cudaStream_t s);
 void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
                         const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
                         unsigned long long* stat, cudaStream_t s);
@@ -421,6 +436,7 @@ struct Scratch {
   DBuf<int32_t> sPart;            // the round's work-item rows (chosen by the grouping kernels)
   DBuf<int32_t> sNGroups, sGFirst, sGBound;  // k > 1: query groups sized by k (launch_var_groups)
   DBuf<float> sPred, sOutD;
+  DBuf<int32_t> sNeed;            // [query tiles][F] filter predictions a batch needs
   DBuf<int64_t> sOutI;
   // search lane
   cudaStream_t st = nullptr;       // created on first use (non-blocking)

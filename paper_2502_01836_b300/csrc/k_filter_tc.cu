@@ -22,7 +22,8 @@ namespace {
 
 using dev::u64;
 
-constexpr int kFRows = 128;          // queries per CTA (MMA M)
+constexpr int kFRows = kFilterTile;  // queries per CTA (MMA M)
+static_assert(kFRows == 128, "one MMA of M = 128 per query tile");
 constexpr int kFThreads = 128;
 constexpr int kSlice = 32;           // K columns per stage (128 bytes of float32)
 constexpr int kAPlane = kFRows * kSlice * 4;   // 16 KB
@@ -90,13 +91,16 @@ __global__ void __launch_bounds__(kFThreads, 2) filter_tc_kernel(
     const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap wmap, int nq,
     int nqp, int F, int h, int hp, int Kq, const float* __restrict__ b1,
     const float* __restrict__ w2, const float* __restrict__ b2, float* __restrict__ out,
-    int32_t* __restrict__ err) {
+    int32_t* __restrict__ err, const int32_t* __restrict__ need, unsigned long long* evals) {
   extern __shared__ __align__(1024) unsigned char fsm_raw[];
   __shared__ FShared S;
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(fsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int f = blockIdx.x, tile = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // predictions nobody will read are not made (the whole block leaves)
+  if (need && !need[(size_t)tile * F + f]) return;
+  if (evals && tid == 0) atomicAdd(evals, (unsigned long long)min(kFRows, nq - tile * kFRows));
   const int nK = Kq / kSlice;
   if (tid == 0) {
     for (int i = 0; i < kFStages; ++i) {
@@ -204,7 +208,8 @@ void launch_wsplit(const float* W1t, int F, int m, int h, float* Ws, cudaStream_
 
 void launch_filter_tc(const CUtensorMap& qmap, const CUtensorMap& wmap, const float* Q, int nq,
                       int mp, int m, int F, int h, float* Qs, const float* b1, const float* w2,
-                      const float* b2, float* out, int32_t* err, cudaStream_t s) {
+                      const float* b2, float* out, int32_t* err, cudaStream_t s,
+                      const int32_t* need, unsigned long long* evals) {
   if (nq <= 0 || F <= 0) return;
   const int hp = (h + 15) / 16 * 16, Kq = (m + kSlice - 1) / kSlice * kSlice;
   const int nqp = (nq + kFRows - 1) / kFRows * kFRows;
@@ -216,7 +221,7 @@ void launch_filter_tc(const CUtensorMap& qmap, const CUtensorMap& wmap, const fl
                                (int)smem));
   dim3 grid(F, nqp / kFRows);
   filter_tc_kernel<<<grid, kFThreads, smem, s>>>(qmap, wmap, nq, nqp, F, h, hp, Kq, b1, w2, b2,
-                                                 out, err);
+                                                 out, err, need, evals);
   LF_CHECK_LAUNCH();
 }
 

@@ -2,7 +2,8 @@
 
 Bars: exact-mode ids bit-exact with ties on the lowest id, distances bit-exact
 (both sides use the canonical float32 distance); lower bounds and routes
-bit-exact (both sides evaluate the same float64 operations); filter
+bit-exact (both sides evaluate the same float64 statistics and the same
+float32 bound operations on the same outward-rounded enclosures); filter
 predictions within 1e-5 of the float64 forward, scaled by |b2| + sum_j
 |w2_j| relu(z_j); Alg. 4 tables and LeaFi-mode results bit-exact (scanned
 leaves and series included) when the oracle takes the GPU's own predictions;
@@ -68,6 +69,62 @@ def test_bounds_ragged_query_tiles(ds, nq):
     r = np.zeros(nq, np.int32)
     lf.leafi_route(idx, Q[:nq], r)
     assert np.array_equal(r, t.route(Q[:nq]))
+
+
+def _segment_means_sds(X, cuts):
+    X = X.astype(np.float64)
+    mu = np.stack([X[:, s:e].mean(1) for s, e in zip(cuts[:-1], cuts[1:])], 1)
+    sd = np.stack([X[:, s:e].std(1) for s, e in zip(cuts[:-1], cuts[1:])], 1)
+    return mu, sd
+
+
+def test_bounds_at_range_edges_bit_exact():
+    """Float32 bounds where the enclosures decide: queries 1e-5 outside a
+    one-leaf DSTree's mean ranges (and 1e-5 relative outside its sigma
+    ranges), so each gap is a few float32 ulps of the statistic; and an iSAX
+    tree whose leaf words end at the non-float32 breakpoint 0.6745 with PAA
+    values 1e-4 and 3e-7 from it.  Bit-exact with the oracle."""
+    X = fx.random_walk(500, 64, seed=121)
+    idx = lf.leafi_build(X, lf.BuildParams(leaf_capacity=1000, device=0))
+    try:
+        t = O.Tree(X, "dstree", leaf_cap=1000, init_segments=4)
+        assert t.L == 1
+        cuts = [0, 16, 32, 48, 64]
+        mu, sd = _segment_means_sds(X, cuts)
+        rows = []
+        for r in range(4):
+            s, e = cuts[r], cuts[r + 1]
+            for src, d in ((np.argmax(mu[:, r]), 1e-5), (np.argmin(mu[:, r]), -1e-5)):
+                q = X[src].copy()
+                q[s:e] += np.float32(d)
+                rows.append(q)
+            q = X[np.argmax(sd[:, r])].copy()
+            c = q[s:e].astype(np.float64).mean()
+            q[s:e] = (c + (q[s:e] - c) * (1 + 1e-5)).astype(np.float32)
+            rows.append(q)
+        Q = np.concatenate([np.array(rows, np.float32), X[:20]])
+        lb = np.zeros((Q.shape[0], 1), np.float64)
+        lf.leafi_leaf_lower_bounds(idx, Q, lb)
+        ref = t.lb2(Q)
+        assert np.array_equal(lb, ref)
+        assert (ref[:12, 0] > 0).any() and (ref[12:, 0] == 0).all()
+    finally:
+        lf.leafi_free(idx)
+    beta = O.isax_breakpoints(2)[2]
+    X = np.array([[0.3, 0.3, 0.3, 0.3], [1.0, 1.0, 0.3, 0.3]], np.float32)
+    # two series: the host build (the device build is tested on larger trees)
+    idx = lf.leafi_build(X, lf.BuildParams(index_type=lf.ISAX, leaf_capacity=1, isax_segments=2,
+                                           isax_card_bits=2, device=0, host_build=1))
+    try:
+        t = O.Tree(X, "isax", leaf_cap=1, isax_w=2, isax_bits=2)
+        assert t.L == 2 and np.array_equal(lf.leafi_leaf_of(idx), t.leaf_of())
+        vals = [beta + 1e-4, beta - 1e-4, beta + 3e-7, beta - 3e-7, 2.0, -0.5]
+        Q = np.array([[v, v, w, w] for v in vals for w in (0.25, -0.01)], np.float32)
+        lb = np.zeros((Q.shape[0], 2), np.float64)
+        lf.leafi_leaf_lower_bounds(idx, Q, lb)
+        assert np.array_equal(lb, t.lb2(Q))
+    finally:
+        lf.leafi_free(idx)
 
 
 @pytest.mark.parametrize("k", [1, 10, 100])
@@ -335,7 +392,10 @@ def test_leafi_search_matches_oracle(ds, tuned, k, target):
     assert same.mean() >= 0.95
     assert np.array_equal(d[same], np.sqrt(o_d2[same]))
     if j >= 0:
-        assert st.filter_evals == NQ * len(fl)
+        # the forward skips query tiles whose predictions no wave select reads
+        # (every filter-pruned pair was read); NQ queries make one tile
+        assert st.filter_pruned <= st.filter_evals <= NQ * len(fl)
+        assert st.filter_evals % NQ == 0
 
 
 def test_search_mixed_matches_oracle(ds, tuned):
