@@ -335,11 +335,12 @@ void ensure_wsplit(leafi_index* ix) {
 }
 
 // P[q][f] for nq queries (device rows of mp floats); `cap_rows` sizes the
-// scratch for later calls of up to that many queries.  need / evals (the
-// tensor-core forward only): skip the (filter, query tile) blocks whose flag
-// is 0 and count the predictions made.
+// scratch for later calls of up to that many queries.  rows_of / cnt / evals
+// (the tensor-core forward only): predict filter f only for the queries
+// rows_of[f][0 .. cnt[f]) and count the predictions made.
 void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_rows = 0,
-                    const int32_t* need = nullptr, unsigned long long* evals = nullptr) {
+                    const int32_t* rows_of = nullptr, const int32_t* cnt = nullptr,
+                    unsigned long long* evals = nullptr) {
   if (nq <= 0 || ix->F <= 0) return;
   if (ix->model == LEAFI_FILTER_CNN) {
     launch_cnn_forward(dQ, nq, ix->mp, ix->m, ix->F, ix->h, ix->cnn.p, P, ix->stream);
@@ -352,15 +353,10 @@ void filter_forward(leafi_index* ix, const float* dQ, int nq, float* P, int cap_
   }
   if (ix->ws_dirty) fail(LEAFI_EINTERNAL, "filter weight planes are stale");
   const int Kq = (ix->m + 31) / 32 * 32;
-  const int nqp = (nq + 127) / 128 * 128;
   const int capp = (std::max(nq, cap_rows) + 127) / 128 * 128;
   float* Qs = ix->sc->sQs.need((size_t)2 * capp * Kq);
-  CUtensorMap qmap;
-  if (!encode_2d(&qmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Qs, (uint64_t)Kq, (uint64_t)2 * nqp,
-                 (uint64_t)Kq * 4, 32, 128))
-    fail(LEAFI_ECUDA, "cannot encode the query tensor map");
-  launch_filter_tc(qmap, ix->wmap, dQ, nq, ix->mp, ix->m, ix->F, ix->h, Qs, ix->b1.p, ix->w2.p,
-                   ix->b2.p, P, ix->sErr.p, ix->stream, need, evals);
+  launch_filter_tc(ix->wmap, dQ, nq, ix->mp, ix->m, ix->F, ix->h, Qs, ix->b1.p, ix->w2.p,
+                   ix->b2.p, P, ix->sErr.p, ix->stream, rows_of, cnt, evals);
 }
 
 // One scan round: group pairs by leaf, scan, merge candidates into slots.
@@ -920,7 +916,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     v.order_tmp = L > calib_max_sort() ? S.sOrderTmp.need(leaf_order_scratch(qb, L)) : nullptr;
     if (any_filtered && filter_tc(ix)) {
       S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
-      S.sNeed.need((size_t)((qb + kFilterTile - 1) / kFilterTile) * ix->F);
+      S.sNeed.need((size_t)(qb + 1) * ix->F);
     }
     v.tq = TcQueries();
     if (ix->tc_scan()) {
@@ -1024,9 +1020,10 @@ void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
     ix->tick(4);
     int32_t* need = lanes[cur_lane].sNeed.p;  // sized by setup for filtered calls
     if (filter_tc(ix) && need) {
+      int32_t* cnt = need + (size_t)nb * ix->F;
       launch_filter_need(nb, ix->F, L, ix->d_filter_leaf.p, v.lb2, v.thr, v.scanned, v.jpos, need,
-                         s);
-      filter_forward(ix, v.gQ, nb, v.P, qb, need, stat + 5);
+                         cnt, s);
+      filter_forward(ix, v.gQ, nb, v.P, qb, need, cnt, stat + 5);
     } else {
       filter_forward(ix, v.gQ, nb, v.P, qb);
     }
@@ -1956,16 +1953,14 @@ void select_auto_core(leafi_index* index, const leafi_select_params* params,
     t_f = timed([&] { launch_cnn_forward(dQ, nq, mp, m, Fp, h, theta.p, P.p, s); }, 3);
   } else if (tc) {
     launch_wsplit(W1t.p, Fp, m, h, Ws.need((size_t)2 * Fp * hp * Kq), s);
-    CUtensorMap wm, qm;
+    CUtensorMap wm;
     const int nqp = (nq + 127) / 128 * 128;
     Qs.need((size_t)2 * nqp * Kq);
     if (!encode_2d(&wm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws.p, (uint64_t)Kq,
-                   (uint64_t)2 * Fp * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp) ||
-        !encode_2d(&qm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Qs.p, (uint64_t)Kq, (uint64_t)2 * nqp,
-                   (uint64_t)Kq * 4, 32, 128))
-      fail(LEAFI_ECUDA, "cannot encode the probe tensor maps");
+                   (uint64_t)2 * Fp * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp))
+      fail(LEAFI_ECUDA, "cannot encode the probe tensor map");
     t_f = timed([&] {
-      launch_filter_tc(qm, wm, dQ, nq, mp, m, Fp, h, Qs.p, b1.p, w2.p, b2.p, P.p, ix->sErr.p, s);
+      launch_filter_tc(wm, dQ, nq, mp, m, Fp, h, Qs.p, b1.p, w2.p, b2.p, P.p, ix->sErr.p, s);
     }, 10);
   } else {
     t_f = timed([&] {

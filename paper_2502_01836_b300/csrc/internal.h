@@ -146,14 +146,16 @@ void launch_wsplit(const float* W1t, int F, int m, int h, float* Ws, cudaStream_
 // scanned, [2] distinct series, [3] canonical re-checks, [4] filter-pruned
 // (query, leaf) pairs, [5] filter predictions made by the tensor-core forward
 constexpr int kPipelineStats = 6;
-// queries per CTA of the tensor-core filter forward (the tiles of `need`)
+// queries per CTA of the tensor-core filter forward
 constexpr int kFilterTile = 128;
-// need (nullable): [ceil(nq / kFilterTile)][F], a (filter, query tile) CTA
-// whose flag is 0 computes nothing; evals (nullable) += the predictions made
-void launch_filter_tc(const CUtensorMap& qmap, const CUtensorMap& wmap, const float* Q, int nq,
-                      int mp, int m, int F, int h, float* Qs, const float* b1, const float* w2,
-                      const float* b2, float* out, int32_t* err, cudaStream_t s,
-                      const int32_t* need = nullptr, unsigned long long* evals = nullptr);
+// Qs: scratch for the query planes, 2 x ceil(nq / 128) * 128 rows of m
+// rounded up to 32.  rows_of / cnt (nullable, together): predict filter f only
+// for the queries rows_of[f][0 .. cnt[f]) (a row stride of nq); otherwise for
+// every query.  evals (nullable) += the predictions made.
+void launch_filter_tc(const CUtensorMap& wmap, const float* Q, int nq, int mp, int m, int F,
+                      int h, float* Qs, const float* b1, const float* w2, const float* b2,
+                      float* out, int32_t* err, cudaStream_t s, const int32_t* rows_of = nullptr,
+                      const int32_t* cnt = nullptr, unsigned long long* evals = nullptr);
 void launch_filter_forward(const float* Q, int nq, int mp, int m, int F, int h, const float* W1t,
                            const float* b1, const float* w2, const float* b2, float* out,
                            cudaStream_t s);
@@ -362,12 +364,13 @@ struct KernelClock {
 void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor, cudaStream_t s);
 // the same picks for a wave at least as wide as the index (a.W >= a.L): no order needed
 void launch_select_all(const SelectArgs& a, cudaStream_t s);
-// need[tile][f] = 1 when some query of the kFilterTile-query tile may have its
-// filter f read by a later wave select: it uses filters, f's leaf is not
-// searched and passes the bound test against the current best-so-far
+// rows_of[f][0 .. cnt[f]) = the queries (any order) whose prediction of
+// filter f a later wave select may read: the query uses filters, f's leaf is
+// not searched and passes the bound test against the current best-so-far
+// (rows_of: F rows of stride nq; cnt: F counters, zeroed here)
 void launch_filter_need(int nq, int F, int L, const int32_t* filter_leaf, const double* lb2,
                         const unsigned long long* thr, const unsigned char* scanned,
-                        const int32_t* jpos, int32_t* need, cudaStream_t s);
+                        const int32_t* jpos, int32_t* rows_of, int32_t* cnt, cudaStream_t s);
 void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
                         const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
                         unsigned long long* stat, cudaStream_t s);
@@ -436,7 +439,8 @@ struct Scratch {
   DBuf<int32_t> sPart;            // the round's work-item rows (chosen by the grouping kernels)
   DBuf<int32_t> sNGroups, sGFirst, sGBound;  // k > 1: query groups sized by k (launch_var_groups)
   DBuf<float> sPred, sOutD;
-  DBuf<int32_t> sNeed;            // [query tiles][F] filter predictions a batch needs
+  DBuf<int32_t> sNeed;            // [F][batch] queries of each filter's predictions a batch needs,
+                                  // then [F] their counts
   DBuf<int64_t> sOutI;
   // search lane
   cudaStream_t st = nullptr;       // created on first use (non-blocking)

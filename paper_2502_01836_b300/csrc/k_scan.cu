@@ -786,11 +786,13 @@ __global__ void select_all_kernel(SelectArgs a) {
 // when the leaf is not searched and passes the bound test against the wave's
 // best-so-far; the best-so-far never rises, so after the route leaves' round a
 // pair failing the same test (or of a query without filters, or of a searched
-// leaf) is never read.  One thread per (query, filter).
+// leaf) is never read.  One thread per (query, filter); each filter's list of
+// queries comes out in any order (a prediction does not depend on its row).
 __global__ void filter_need_kernel(int nq, int F, int L, const int32_t* __restrict__ filter_leaf,
                                    const double* __restrict__ lb2, const u64* __restrict__ thr,
                                    const unsigned char* __restrict__ scanned,
-                                   const int32_t* __restrict__ jpos, int32_t* __restrict__ need) {
+                                   const int32_t* __restrict__ jpos, int32_t* __restrict__ rows_of,
+                                   int32_t* __restrict__ cnt) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nq * F) return;
   const int q = (int)(t / F), f = (int)(t % F);
@@ -800,7 +802,7 @@ __global__ void filter_need_kernel(int nq, int F, int L, const int32_t* __restri
   const u64 th = thr[q];
   const float bsf2 = (th == kNoKey) ? __int_as_float(0x7f800000) : key_d2(th);
   if (__dmul_rn(lb2[(size_t)q * L + leaf], kDeflate) > (double)bsf2) return;
-  need[(size_t)(q / kFilterTile) * F + f] = 1;
+  rows_of[(size_t)f * nq + atomicAdd(&cnt[f], 1)] = q;
 }
 
 __global__ void done_all_kernel(int nq, int32_t* __restrict__ done) {
@@ -996,13 +998,12 @@ void launch_select_all(const SelectArgs& a, cudaStream_t s) {
 
 void launch_filter_need(int nq, int F, int L, const int32_t* filter_leaf, const double* lb2,
                         const unsigned long long* thr, const unsigned char* scanned,
-                        const int32_t* jpos, int32_t* need, cudaStream_t s) {
+                        const int32_t* jpos, int32_t* rows_of, int32_t* cnt, cudaStream_t s) {
   if (nq <= 0 || F <= 0) return;
-  const int tiles = (nq + kFilterTile - 1) / kFilterTile;
-  LF_CUDA(cudaMemsetAsync(need, 0, sizeof(int32_t) * (size_t)tiles * F, s));
+  LF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)F, s));
   const int64_t tot = (int64_t)nq * F;
   filter_need_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nq, F, L, filter_leaf, lb2, thr,
-                                                                   scanned, jpos, need);
+                                                                   scanned, jpos, rows_of, cnt);
   LF_CHECK_LAUNCH();
 }
 

@@ -366,6 +366,7 @@ def test_leafi_search_bit_exact_on_gpu_predictions(ds, tuned, k, target):
     assert st.filter_pruned == o_st[:, 3].sum() and st.lb_pruned == o_st[:, 2].sum()
     if j >= 0:
         assert o_st[:, 3].sum() > 0     # some filter pruned a leaf: the comparison covers it
+        assert st.filter_evals == _needed_predictions(t, Q, fl, k)
 
 
 @pytest.mark.parametrize("k,target", [(1, 0.99), (1, 0.9), (10, 0.95)])
@@ -392,10 +393,20 @@ def test_leafi_search_matches_oracle(ds, tuned, k, target):
     assert same.mean() >= 0.95
     assert np.array_equal(d[same], np.sqrt(o_d2[same]))
     if j >= 0:
-        # the forward skips query tiles whose predictions no wave select reads
-        # (every filter-pruned pair was read); NQ queries make one tile
-        assert st.filter_pruned <= st.filter_evals <= NQ * len(fl)
-        assert st.filter_evals % NQ == 0
+        assert st.filter_evals == _needed_predictions(t, Q, fl, k)
+
+
+def _needed_predictions(t, Q, fl, k):
+    """(query, filter) pairs whose prediction a wave select may read once the
+    route leaves are searched: the filter's leaf is not the route leaf and its
+    bound passes the pruning test against the route leaf's k-th distance (the
+    forward makes exactly these predictions)."""
+    route = t.route(Q)
+    d2, _ = t.leaf_topk(Q, route[:, None].astype(np.int32), k)
+    bsf2 = d2[:, 0, k - 1].astype(np.float64)
+    lb = t.lb2(Q)[:, np.asarray(fl)]
+    need = (lb * (1.0 - 1e-4) <= bsf2[:, None]) & (np.asarray(fl)[None, :] != route[:, None])
+    return int(need.sum())
 
 
 def test_search_mixed_matches_oracle(ds, tuned):
