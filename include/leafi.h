@@ -450,10 +450,11 @@ typedef struct {
   int64_t leaves_scanned;  /* (query, leaf) pairs searched */
   int64_t series_scanned;  /* (query, series) distances computed */
   int64_t filter_evals;    /* (query, filter) predictions made: after the route
-                              leaves' round the tensor-core forward skips the
-                              128-query tiles in which no (query, filter) pair
-                              can reach a filter test (leaf searched or bound-
-                              pruned for every query of the tile) */
+                              leaves' round the tensor-core forward predicts
+                              only the pairs that can reach a filter test
+                              (leaf not searched, bound test passed against
+                              the current best-so-far); the CUDA-core and CNN
+                              forwards predict every pair */
   int64_t waves;           /* scan rounds launched, summed over batches (a full batch
                               always launches its first two, the second maybe empty) */
   int64_t batches;         /* internal query batches (256 queries each) */
