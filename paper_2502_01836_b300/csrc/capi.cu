@@ -328,8 +328,9 @@ void ensure_wsplit(leafi_index* ix) {
   const int hp = (ix->h + 15) / 16 * 16, Kq = (ix->m + 31) / 32 * 32;
   float* Ws = ix->Ws.need((size_t)2 * ix->F * hp * Kq);
   launch_wsplit(ix->W1t.p, ix->F, ix->m, ix->h, Ws, ix->stream);
-  if (!encode_2d(&ix->wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws, (uint64_t)Kq,
-                 (uint64_t)2 * ix->F * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp))
+  // slice-major planes: rows of 32 floats, one box = one slice of one plane
+  if (!encode_2d(&ix->wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws, 32,
+                 (uint64_t)2 * ix->F * (Kq / 32) * hp, 128, 32, (uint32_t)hp))
     fail(LEAFI_ECUDA, "cannot encode the filter weight tensor map");
   ix->ws_dirty = false;
 }
@@ -915,7 +916,7 @@ void Pipeline::setup(leafi_index* index, Scratch* lane_array, int n_lanes, int k
     v.cursor = S.sCursor.need(qb);
     v.order_tmp = L > calib_max_sort() ? S.sOrderTmp.need(leaf_order_scratch(qb, L)) : nullptr;
     if (any_filtered && filter_tc(ix)) {
-      S.sQs.need((size_t)2 * qb * ((ix->m + 31) / 32 * 32));
+      S.sQs.need((size_t)2 * ((qb + 127) / 128 * 128) * ((ix->m + 31) / 32 * 32));
       S.sNeed.need((size_t)(qb + 1) * ix->F);
     }
     v.tq = TcQueries();
@@ -1956,8 +1957,8 @@ void select_auto_core(leafi_index* index, const leafi_select_params* params,
     CUtensorMap wm;
     const int nqp = (nq + 127) / 128 * 128;
     Qs.need((size_t)2 * nqp * Kq);
-    if (!encode_2d(&wm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws.p, (uint64_t)Kq,
-                   (uint64_t)2 * Fp * hp, (uint64_t)Kq * 4, 32, (uint32_t)hp))
+    if (!encode_2d(&wm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ws.p, 32,
+                   (uint64_t)2 * Fp * (Kq / 32) * hp, 128, 32, (uint32_t)hp))
       fail(LEAFI_ECUDA, "cannot encode the probe tensor map");
     t_f = timed([&] {
       launch_filter_tc(wm, dQ, nq, mp, m, Fp, h, Qs.p, b1.p, w2.p, b2.p, P.p, ix->sErr.p, s);

@@ -56,7 +56,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t 
       : "memory");
 }
 
-// query planes: Qs[r][i] = hi(q_ri), Qs[nqp + r][i] = lo(q_ri); zero padding
+// query planes, slice-major (a query's 32-column slice is 128 contiguous
+// bytes): Qs[p][i / 32][r][i % 32] = hi (p = 0) or lo (p = 1) of q_ri; zero padding
 __global__ void qsplit_kernel(const float* __restrict__ Q, int nq, int mp, int m, int Kq, int nqp,
                               float* __restrict__ Qs) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,11 +65,14 @@ __global__ void qsplit_kernel(const float* __restrict__ Q, int nq, int mp, int m
   const int r = (int)(t / Kq), i = (int)(t % Kq);
   const float v = (r < nq && i < m) ? Q[(size_t)r * mp + i] : 0.0f;
   const float hi = tf32_rna(v);
-  Qs[t] = hi;
-  Qs[(size_t)nqp * Kq + t] = tf32_rna(v - hi);
+  const size_t o = ((size_t)(i / kSlice) * nqp + r) * kSlice + i % kSlice;
+  Qs[o] = hi;
+  Qs[(size_t)nqp * Kq + o] = tf32_rna(v - hi);
 }
 
-// weight planes from W1t [F][m][h]: Ws[(2f + p) hp + j][i], p = 0 hi, 1 lo
+// weight planes from W1t [F][m][h], slice-major so that each TMA box (one
+// 32-column slice of one plane, hp rows) is 16-32 KB of contiguous memory:
+// Ws[(2f + p)][i / 32][j][i % 32], p = 0 hi, 1 lo
 __global__ void wsplit_kernel(const float* __restrict__ W1t, int F, int m, int h, int hp, int Kq,
                               float* __restrict__ Ws) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,8 +81,9 @@ __global__ void wsplit_kernel(const float* __restrict__ W1t, int F, int m, int h
   const int j = (int)((t / Kq) % hp), i = (int)(t % Kq);
   const float w = (j < h && i < m) ? W1t[((size_t)f * m + i) * h + j] : 0.0f;
   const float hi = tf32_rna(w);
-  Ws[((size_t)(2 * f) * hp + j) * Kq + i] = hi;
-  Ws[((size_t)(2 * f + 1) * hp + j) * Kq + i] = tf32_rna(w - hi);
+  const int nK = Kq / kSlice, kc = i / kSlice, ii = i % kSlice;
+  Ws[(((size_t)(2 * f) * nK + kc) * hp + j) * kSlice + ii] = hi;
+  Ws[(((size_t)(2 * f + 1) * nK + kc) * hp + j) * kSlice + ii] = tf32_rna(w - hi);
 }
 
 struct FShared {
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kFThreads, 1) filter_tc_kernel(
     const int src_bytes = q >= 0 ? 16 : 0;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-      const float* src = Qs + ((size_t)p * nqp + (q >= 0 ? q : 0)) * Kq + kc * kSlice;
+      const float* src = Qs + (size_t)p * nqp * Kq + ((size_t)kc * nqp + (q >= 0 ? q : 0)) * kSlice;
       unsigned char* dst = st + p * kAPlane + tid * 128;
 #pragma unroll
       for (int c = 0; c < 8; ++c)
@@ -152,8 +157,8 @@ __global__ void __launch_bounds__(kFThreads, 1) filter_tc_kernel(
     const int sx = kc % kFStages;
     unsigned char* st = sm + sx * kStage;
     dev::mbar_expect_tx(&S.full[sx], bbytes);
-    dev::tma_load_2d(st + 2 * kAPlane, &wmap, kc * kSlice, (2 * f) * hp, &S.full[sx]);
-    dev::tma_load_2d(st + 2 * kAPlane + kBPlane, &wmap, kc * kSlice, (2 * f + 1) * hp,
+    dev::tma_load_2d(st + 2 * kAPlane, &wmap, 0, ((2 * f) * nK + kc) * hp, &S.full[sx]);
+    dev::tma_load_2d(st + 2 * kAPlane + kBPlane, &wmap, 0, ((2 * f + 1) * nK + kc) * hp,
                      &S.full[sx]);
     ++b_issued[sx];
   };
