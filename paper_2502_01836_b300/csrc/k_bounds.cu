@@ -95,27 +95,11 @@ __global__ void ds_interval_kernel(DsTables T, const double* __restrict__ P, int
   ivstat_enclosures(ivstat, nq, T.n_iv)[t] = enclose(mu, sd);
 }
 
-// node bound: sum over the node's segments of l_r (gap_mu^2 + gap_sigma^2)
-__global__ void ds_node_kernel(DsTables T, const double* __restrict__ ivstat, int nq,
-                               double* __restrict__ node_lb) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nq * T.n_nodes) return;
-  const int q = (int)(t / T.n_nodes), v = (int)(t % T.n_nodes);
-  const float4* st = ivstat_enclosures(ivstat, nq, T.n_iv) + (size_t)q * T.n_iv;
-  float acc = 0.0f;
-  for (int r = T.seg_off[v]; r < T.seg_off[v + 1]; ++r) {
-    const int iv = T.seg_iv[r];
-    const float len = (float)(T.iv_e[iv] - T.iv_s[iv]);
-    acc = __fadd_rn(acc, seg_term(st[iv], T.syn32[r], len));
-  }
-  node_lb[t] = (double)acc;
-}
-
-// The same node bounds with each thread taking one node for a tile of QT
-// queries: a node's synopses are read once per tile instead of once per query
-// (on large trees the synopses, not the arithmetic, are the traffic), and each
-// (query, node) sum runs over the node's segments in the same order as
-// ds_node_kernel, so the values are bit-identical.
+// Node bound: sum over the node's segments of l_r (gap_mu^2 + gap_sigma^2).
+// Large trees: each thread takes one node for a tile of QT queries, so a
+// node's synopses are read once per tile instead of once per query (there the
+// synopses, not the arithmetic, are the traffic); every (query, node) sum runs
+// over the node's segments in order, as in ds_node_leaf_kernel.
 template <int QT>
 __global__ void ds_node_tiled_kernel(DsTables T, const double* __restrict__ ivstat, int nq,
                                      double* __restrict__ node_lb) {
@@ -140,6 +124,33 @@ __global__ void ds_node_tiled_kernel(DsTables T, const double* __restrict__ ivst
 #pragma unroll
   for (int qq = 0; qq < QT; ++qq)
     if (qq < nqt) node_lb[(size_t)(q0 + qq) * T.n_nodes + v] = (double)acc[qq];
+}
+
+// Node and leaf bounds of one query per block (trees of fewer than 2048
+// nodes): the node bounds, each the float32 sum over the node's segments in
+// order, stay in shared memory, and each leaf takes the maximum over
+// its root-to-leaf path from there, so no node bound goes through global
+// memory and one launch replaces two.
+__global__ void ds_node_leaf_kernel(DsTables T, const double* __restrict__ ivstat, int nq,
+                                    double* __restrict__ leaf_lb) {
+  extern __shared__ float s_node[];  // [n_nodes]
+  const int q = blockIdx.x;
+  const float4* st = ivstat_enclosures(ivstat, nq, T.n_iv) + (size_t)q * T.n_iv;
+  for (int v = threadIdx.x; v < T.n_nodes; v += blockDim.x) {
+    float acc = 0.0f;
+    for (int r = T.seg_off[v]; r < T.seg_off[v + 1]; ++r) {
+      const int iv = T.seg_iv[r];
+      const float len = (float)(T.iv_e[iv] - T.iv_s[iv]);
+      acc = __fadd_rn(acc, seg_term(st[iv], T.syn32[r], len));
+    }
+    s_node[v] = acc;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < T.n_leaves; l += blockDim.x) {
+    float best = 0.0f;
+    for (int i = T.path_off[l]; i < T.path_off[l + 1]; ++i) best = fmaxf(best, s_node[T.path[i]]);
+    leaf_lb[(size_t)q * T.n_leaves + l] = (double)best;
+  }
 }
 
 // leaf bound = max over the root-to-leaf path
@@ -369,13 +380,12 @@ void launch_ds_bounds(const DsTables& T, const double* P, int nq, int m, double*
     // large trees: tiles of 8 queries per thread share each node's synopses
     dim3 grid(blocks_for(T.n_nodes, kThreads), blocks_for(nq, 8));
     ds_node_tiled_kernel<8><<<grid, kThreads, 0, s>>>(T, ivstat, nq, node_lb);
+    LF_CHECK_LAUNCH();
+    ds_leaf_kernel<<<blocks_for((int64_t)nq * T.n_leaves, kThreads), kThreads, 0, s>>>(
+        T, node_lb, nq, leaf_lb);
   } else {
-    ds_node_kernel<<<blocks_for((int64_t)nq * T.n_nodes, kThreads), kThreads, 0, s>>>(T, ivstat, nq,
-                                                                                      node_lb);
+    ds_node_leaf_kernel<<<nq, 256, sizeof(float) * T.n_nodes, s>>>(T, ivstat, nq, leaf_lb);
   }
-  LF_CHECK_LAUNCH();
-  ds_leaf_kernel<<<blocks_for((int64_t)nq * T.n_leaves, kThreads), kThreads, 0, s>>>(
-      T, node_lb, nq, leaf_lb);
   LF_CHECK_LAUNCH();
   if (route && !fused) {
     ds_route_kernel<<<blocks_for(nq, 64), 64, 0, s>>>(T, ivstat, nq, route);
