@@ -1487,7 +1487,8 @@ static int wave_search(int L, const double* lb2, const int* ord, int route,
 void or_leafi_search_pred(const or_tree* t, const double* P, const int32_t* filter_leaf, int F,
                           const double* alpha_sorted, int64_t nc, const float* Q, int64_t nq,
                           const int32_t* k, const int32_t* jpos, int kmax, int wave,
-                          int64_t* ids, float* d2, int64_t* stats, double* min_margin) {
+                          int64_t* ids, float* d2, int64_t* stats, double* min_margin,
+                          unsigned char* scanned) {
   const int L = t->nleaves, m = t->m;
   double* lb2 = (double*)malloc(sizeof(double) * (size_t)nq * L);
   int32_t* route = (int32_t*)malloc(sizeof(int32_t) * nq);
@@ -1531,6 +1532,7 @@ void or_leafi_search_pred(const or_tree* t, const double* P, const int32_t* filt
         stats[i * 4 + 3] = fp;
       }
       if (min_margin) min_margin[i] = mm;
+      if (scanned) memcpy(scanned + (size_t)i * L, sc, (size_t)L);
     }
     free(df);
     free(sc);
@@ -1550,7 +1552,7 @@ void or_leafi_search(const or_tree* t, const float* W1, const float* b1, const f
   double* P = (double*)malloc(sizeof(double) * (size_t)(nq > 0 ? nq : 1) * (F > 0 ? F : 1));
   if (F > 0) or_mlp_forward(W1, b1, w2, b2, F, h, t->m, Q, nq, P);
   or_leafi_search_pred(t, P, filter_leaf, F, alpha_sorted, nc, Q, nq, k, jpos, kmax, wave, ids,
-                       d2, stats, min_margin);
+                       d2, stats, min_margin, NULL);
   free(P);
 }
 

@@ -110,7 +110,8 @@ void or_leafi_search_pred(const or_tree* t, const double* P, const int32_t* filt
                           const double* alpha_sorted, int64_t nc,
                           const float* Q, int64_t nq, const int32_t* k, const int32_t* jpos,
                           int kmax, int wave, int64_t* ids, float* d2, int64_t* stats,
-                          double* min_margin);
+                          double* min_margin, unsigned char* scanned /* nullable: [nq][L], 1 =
+                          the leaf was searched (Alg. 2) */);
 
 /* Auto-tuner learning (Alg. 4) for one k: calibration queries Qc (nc).
  * Outputs alpha_sorted [F][nc] (descending) and qprime [nc] (running-min

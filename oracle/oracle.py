@@ -103,7 +103,7 @@ def lib():
                                       i64p, f32p, i64p, f64p]
         L.or_leafi_search_pred.argtypes = [vp, f64p, i32p, C.c_int, f64p, C.c_int64, f32p,
                                            C.c_int64, i32p, i32p, C.c_int, C.c_int, i64p, f32p,
-                                           i64p, f64p]
+                                           i64p, f64p, vp]
         L.or_fit_autotuner_pred.argtypes = [vp, f64p, i32p, C.c_int, f32p, C.c_int64, C.c_int,
                                             C.c_int, f64p, f64p]
         L.or_cnn_params.argtypes = [C.c_int]
@@ -431,8 +431,12 @@ def fit_autotuner_pred(tree: Tree, Pc, filter_leaf, Qc, k, wave):
     return alpha, qp
 
 
-def leafi_search_pred(tree: Tree, P, filter_leaf, alpha_sorted, Q, k, jpos, wave, kmax=None):
-    """leafi_search on given predictions P [nq, F] (any filter model)."""
+def leafi_search_pred(tree: Tree, P, filter_leaf, alpha_sorted, Q, k, jpos, wave, kmax=None,
+                      return_scanned=False):
+    """leafi_search on given predictions P [nq, F] (any filter model).
+
+    With return_scanned, a fifth result: uint8 [nq, n_leaves], 1 where Alg. 2
+    searched the leaf for the query."""
     Q = _f32(Q)
     nq = Q.shape[0]
     P = np.ascontiguousarray(P, np.float64)
@@ -445,6 +449,10 @@ def leafi_search_pred(tree: Tree, P, filter_leaf, alpha_sorted, Q, k, jpos, wave
     d2 = np.empty((nq, kmax), np.float32)
     st = np.empty((nq, 4), np.int64)
     mm = np.empty(nq, np.float64)
+    sc = np.zeros((nq, tree.L), np.uint8) if return_scanned else None
     lib().or_leafi_search_pred(tree._h, P, np.ascontiguousarray(filter_leaf, np.int32), F, alpha,
-                               alpha.shape[1], Q, nq, k, jpos, kmax, wave, ids, d2, st, mm)
+                               alpha.shape[1], Q, nq, k, jpos, kmax, wave, ids, d2, st, mm,
+                               sc.ctypes.data if return_scanned else None)
+    if return_scanned:
+        return ids, d2, st, mm, sc
     return ids, d2, st, mm

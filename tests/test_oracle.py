@@ -500,8 +500,9 @@ def test_steffen_properties():
 
 # ---------------------------------------------------------------- search
 
-def _alg2_sequential(lb_row, route, lists, df_row, k):
-    """Literal Alg. 2 loop: route leaf first, then ascending (LB, id)."""
+def _alg2_sequential(lb_row, route, lists, df_row, k, searched=None):
+    """Literal Alg. 2 loop: route leaf first, then ascending (LB, id).
+    `searched` (a set, optional) receives the leaves the loop searches."""
     L = lb_row.shape[0]
     order = [route] + sorted((l for l in range(L) if l != route), key=lambda l: (lb_row[l], l))
     res = []
@@ -512,6 +513,8 @@ def _alg2_sequential(lb_row, route, lists, df_row, k):
         if df_row is not None and not np.isnan(df_row[leaf]) and \
                 df_row[leaf] > float(np.sqrt(np.float32(bsf))):
             continue
+        if searched is not None:
+            searched.add(leaf)
         d2, ids = lists[leaf]
         res = sorted(res + [(float(a), int(b)) for a, b in zip(d2, ids) if b >= 0])[:k]
         bsf = np.float32(res[k - 1][0]) if len(res) == k else np.float32(np.inf)
@@ -534,6 +537,42 @@ def test_exact_search_equals_brute_force_for_any_wave(small_index):
             ids, d2, st, _ = O.leafi_search(t, None, None, None, Q, k, -1, wave)
             assert np.array_equal(ids, bf_ids) and np.array_equal(d2, bf_d2)
             assert (st[:, 0] <= t.L).all()
+
+
+def test_searched_leaves_of_wave_one_are_the_sequential_algorithms(small_index):
+    """The per-query searched-leaf flags of the oracle's search (Alg. 2) at
+    W = 1 are exactly the leaves a literal transcription of the loop searches,
+    with filters and without; they agree with the search's own counters."""
+    X, t, Q = small_index
+    rng = np.random.default_rng(8)
+    F = min(6, t.L)
+    W = fx.filter_init(F, 32, 32, seed=9)
+    fl = np.arange(F, dtype=np.int32)
+    alpha = np.sort(rng.uniform(0, 3, (F, 7)), axis=1)[:, ::-1].copy()
+    P = O.mlp_forward(*W, Q)
+    lb = t.lb2(Q)
+    route = t.route(Q)
+    sizes = t.leaf_sizes()
+    leaves = np.tile(np.arange(t.L, dtype=np.int32), (Q.shape[0], 1))
+    for k in (1, 4):
+        d2l, idl = t.leaf_topk(Q, leaves, k)
+        for j in (-1, 0, 3, 6):
+            _, _, st, _, sc = O.leafi_search_pred(t, P, fl, alpha, Q, k, j, 1, return_scanned=True)
+            assert sc.dtype == np.uint8 and set(np.unique(sc).tolist()) <= {0, 1}
+            assert np.array_equal(sc.sum(axis=1), st[:, 0])
+            assert np.array_equal(sc.astype(np.int64) @ sizes, st[:, 1])
+            pruned_some = False
+            for i in range(Q.shape[0]):
+                df = None
+                if j >= 0:
+                    df = np.full(t.L, np.nan)
+                    df[fl] = P[i] - alpha[:, j]
+                lists = [(d2l[i, l], idl[i, l]) for l in range(t.L)]
+                searched = set()
+                _alg2_sequential(lb[i], route[i], lists, df, k, searched)
+                assert set(np.flatnonzero(sc[i]).tolist()) == searched, (k, j, i)
+                pruned_some |= len(searched) < t.L
+            assert pruned_some
 
 
 def test_wave_one_is_the_sequential_algorithm(small_index):
