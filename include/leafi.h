@@ -481,6 +481,15 @@ typedef struct {
 leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, int32_t k,
                           double recall_target, int64_t* ids, float* dists,
                           leafi_search_stats* stats);
+/* Inspection export of Alg. 2: the same search as leafi_search, which also
+ * writes scanned [nq][n_leaves] uint8 (host or device, caller-owned): 1 where
+ * the leaf was searched for the query (its route leaf and every leaf a wave
+ * took), 0 where the lower bound or the filter pruned it or the search ended
+ * first.  Allocates nq * n_leaves bytes of device scratch for the call;
+ * LEAFI_EINVAL on a NULL output, the errors of leafi_search otherwise. */
+leafi_status leafi_search_scanned(leafi_index* index, const float* queries, int64_t nq,
+                                  int32_t k, double recall_target, int64_t* ids, float* dists,
+                                  uint8_t* scanned);
 /* Search-schedule autotuner (no counterpart in the paper; the wave width W is
  * this implementation's batching parameter).  Times k-NN searches of n_probe
  * probe queries (dataset series drawn by the library's generator plus

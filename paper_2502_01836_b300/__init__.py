@@ -20,7 +20,8 @@ __all__ = [
     "leafi_leaf_of", "leafi_leaf_lower_bounds", "leafi_route", "leafi_select_leaves",
     "leafi_set_filters", "leafi_get_filters", "leafi_filter_predict", "leafi_leaf_knn",
     "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
-    "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
+    "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_search_scanned",
+    "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
     "KERNEL_KINDS", "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases", "SCAN_PHASES",
     "DSTREE", "ISAX", "MAX_K", "EXPORTED_SYMBOLS", "EAGAIN", "ServeParams", "ServeStats",
@@ -51,7 +52,8 @@ EXPORTED_SYMBOLS = [
     "leafi_leaf_sizes", "leafi_leaf_of", "leafi_leaf_lower_bounds", "leafi_route",
     "leafi_select_leaves", "leafi_set_filters", "leafi_get_filters", "leafi_filter_predict",
     "leafi_leaf_knn", "leafi_train_targets", "leafi_train_filters", "leafi_fit_autotuners",
-    "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_exact_search",
+    "leafi_get_autotuners", "leafi_set_autotuners", "leafi_search", "leafi_search_scanned",
+    "leafi_exact_search",
     "leafi_search_mixed", "leafi_launch_count", "leafi_set_profiling", "leafi_get_kernel_times",
     "leafi_leaf_lower_bounds_noalloc", "leafi_get_scan_phases",
     "leafi_serve_start", "leafi_serve_submit", "leafi_serve_poll", "leafi_serve_get_stats",
@@ -241,6 +243,7 @@ def lib():
             "leafi_set_autotuners": [vp, vp, vp, i64, vp, i32],
             "leafi_search": [vp, vp, i64, i32, f64, vp, vp, C.POINTER(SearchStats)],
             "leafi_exact_search": [vp, vp, i64, i32, vp, vp, C.POINTER(SearchStats)],
+            "leafi_search_scanned": [vp, vp, i64, i32, f64, vp, vp, vp],
             "leafi_search_mixed": [vp, vp, i64, vp, vp, i32, vp, vp, C.POINTER(SearchStats)],
             "leafi_set_profiling": [vp, i32],
             "leafi_get_kernel_times": [vp, vp, vp],
@@ -273,7 +276,8 @@ def _check(st):
         raise LeafiError(st, lib().leafi_last_error().decode())
 
 
-_NP = {np.float32: "float32", np.float64: "float64", np.int32: "int32", np.int64: "int64"}
+_NP = {np.float32: "float32", np.float64: "float64", np.int32: "int32", np.int64: "int64",
+       np.uint8: "uint8"}
 
 
 def _ptr(a, dtype, name="array", writable=False):
@@ -290,7 +294,7 @@ def _ptr(a, dtype, name="array", writable=False):
     if mod.startswith("torch"):
         import torch
         tmap = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
-                np.int64: torch.int64}
+                np.int64: torch.int64, np.uint8: torch.uint8}
         if a.dtype != tmap[dtype] or not a.is_contiguous():
             raise TypeError("%s must be a contiguous torch.%s tensor" % (name, _NP[dtype]))
         return a.data_ptr()
@@ -651,6 +655,17 @@ def leafi_search(index, queries, k, recall_target, ids, dists, stats: SearchStat
                               _ptr(dists, np.float32, "dists", True),
                               C.byref(stats) if stats is not None else None))
     return ids, dists
+
+
+def leafi_search_scanned(index, queries, k, recall_target, ids, dists, scanned):
+    """leafi_search that also writes scanned [nq, n_leaves] uint8: 1 where the
+    search searched the leaf for the query (an inspection export)."""
+    _check(lib().leafi_search_scanned(index, _ptr(queries, np.float32, "queries"),
+                                      queries.shape[0], k, float(recall_target),
+                                      _ptr(ids, np.int64, "ids", True),
+                                      _ptr(dists, np.float32, "dists", True),
+                                      _ptr(scanned, np.uint8, "scanned", True)))
+    return ids, dists, scanned
 
 
 def leafi_exact_search(index, queries, k, ids, dists, stats: SearchStats | None = None):

@@ -809,7 +809,20 @@ struct InFlight {
   float* dists = nullptr;
   const int32_t* rows = nullptr;  // scheduled batch: output row of each query (device);
                                   // ids / dists are then the call's device arrays
+  int64_t row0 = 0;               // otherwise: the call's row of the batch's first query
 };
+
+// inspection: a finished batch's searched-leaf flags [nb][L] to the call's rows
+// (rows[i], or row0 + i) of out [nq][L]
+__global__ void scanned_out_kernel(int nb, int L, const unsigned char* __restrict__ scanned,
+                                   const int32_t* __restrict__ rows, int64_t row0,
+                                   unsigned char* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nb * L) return;
+  const int i = (int)(t / L), l = (int)(t % L);
+  const int64_t row = rows ? (int64_t)rows[i] : row0 + i;
+  out[row * L + l] = scanned[t];
+}
 
 }  // namespace
 
@@ -829,6 +842,7 @@ struct Pipeline {
   unsigned long long* stat = nullptr;   // device counters of the pipeline's batches
                                         // (kPipelineStats)
   bool pre_p = false;                   // scheduled batches: prefix sums gathered, not computed
+  unsigned char* scanned_out = nullptr; // inspection (device, nullable): [nq][L] searched flags
   leafi_search_stats st{};
   LaneView lv[kMaxLanes];
   InFlight fl[kMaxLanes];
@@ -1204,6 +1218,12 @@ bool Pipeline::step(int li) {
   }
   st.waves += f.waves;
   st.batches += 1;
+  if (scanned_out && f.nb > 0) {
+    const int64_t tot = (int64_t)f.nb * L;
+    scanned_out_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(f.nb, L, v.scanned, f.rows,
+                                                                      f.row0, scanned_out);
+    LF_CHECK_LAUNCH();
+  }
   if (f.rows) {
     launch_write_results(f.nb, kmax, v.dK, v.topk, kmax, v.topk_cnt, f.ids, f.dists, s, f.rows);
   } else {
@@ -1231,7 +1251,7 @@ namespace {
 // the search entry points: one call, batches of kBatch through the index's pipeline
 void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::vector<int32_t>& kq,
                  const std::vector<double>& target, int kmax, int64_t* ids, float* dists,
-                 leafi_search_stats* stats) {
+                 leafi_search_stats* stats, unsigned char* scanned_dev = nullptr) {
   const auto t_call = std::chrono::steady_clock::now();
   const bool any_filtered = std::any_of(target.begin(), target.end(), [](double v) { return v < 1.0; });
   if (any_filtered && (ix->nc == 0 || ix->F == 0))
@@ -1253,6 +1273,7 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
   unsigned long long* stat = ix->sStat.need(kPipelineStats);
   Pipeline pl;
   pl.setup(ix, ix->lanes, nlanes, kmax, any_filtered, stat, qb);
+  pl.scanned_out = scanned_dev;
   const bool uniform =
       std::all_of(kq.begin(), kq.end(), [&](int32_t v) { return v == kq[0]; }) &&
       std::all_of(target.begin(), target.end(), [&](double v) { return v == target[0]; });
@@ -1322,10 +1343,12 @@ void search_impl(leafi_index* ix, const float* queries, int64_t nq, const std::v
       pl.start_rows(li, dQall, ix->sched.P.p, dperm + b0, nb,
                     (uniform ? kq.data() : kq_s.data() + b0),
                     (uniform ? target.data() : tg_s.data() + b0), uniform, out_i, out_d);
-    else
+    else {
       pl.start(li, queries + (size_t)b0 * ix->m, nb, kq.data() + (uniform ? 0 : b0),
                target.data() + (uniform ? 0 : b0), uniform, ids + (size_t)b0 * kmax,
                dists + (size_t)b0 * kmax);
+      pl.fl[li].row0 = b0;
+    }
   };
   for (int li = 0; li < nlanes && next_b0 < nq; ++li) start_next(li);
   for (;;) {
@@ -3179,6 +3202,28 @@ leafi_status leafi_search(leafi_index* index, const float* queries, int64_t nq, 
     std::vector<int32_t> kq(nq, k);
     std::vector<double> tg(nq, recall_target);
     search_impl(index, queries, nq, kq, tg, k, ids, dists, stats);
+  });
+}
+
+leafi_status leafi_search_scanned(leafi_index* index, const float* queries, int64_t nq,
+                                  int32_t k, double recall_target, int64_t* ids, float* dists,
+                                  uint8_t* scanned) {
+  return guarded([&] {
+    require_device(index);
+    check_queries(index, queries, nq);
+    if (k < 1 || k > LEAFI_MAX_K) fail(LEAFI_EINVAL, "k must be in [1, %d]", LEAFI_MAX_K);
+    if (!(recall_target > 0.0)) fail(LEAFI_EINVAL, "recall_target must be > 0");
+    if (nq > 0 && (!ids || !dists || !scanned)) fail(LEAFI_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(index->mu);
+    DeviceGuard dg(index->device);
+    const size_t bytes = (size_t)nq * index->tree.n_leaves;
+    DBuf<unsigned char> sc;
+    unsigned char* dsc = sc.need(std::max<size_t>(bytes, 1));
+    std::vector<int32_t> kq(nq, k);
+    std::vector<double> tg(nq, recall_target);
+    search_impl(index, queries, nq, kq, tg, k, ids, dists, nullptr, dsc);
+    deliver(scanned, dsc, bytes, index->stream);
+    LF_CUDA(cudaStreamSynchronize(index->stream));
   });
 }
 

@@ -335,6 +335,48 @@ def test_autotuner_bit_exact_on_gpu_predictions(ds, tuned):
         assert np.array_equal(qp[i], q_ref), k
 
 
+@pytest.mark.parametrize("k,target,batch,sched", [(1, 0.99, 256, True), (1, 0.9, 16, True),
+                                                  (10, 0.95, 16, False), (3, 1.0, 16, True)])
+def test_searched_leaves_equal_oracle(ds, tuned, k, target, batch, sched):
+    """Per query, the set of leaves the GPU search searched (Alg. 2: the route
+    leaf and every leaf a wave took) equals the oracle's, fed the GPU's
+    predictions and tables; with 16-query batches the call runs as several
+    batches (cut in route-leaf order, or in order) whose flags go back to the
+    callers' rows."""
+    X, Q, idx, t = ds
+    fl, Wt, Qc, _ = tuned
+    lf.leafi_set_filters(idx, fl, *Wt)
+    lf.leafi_fit_autotuners(idx, Qc, [1, 10])
+    F, nc = Wt[0].shape[0], Qc.shape[0]
+    alpha = np.zeros((F, nc))
+    qp = np.zeros((2, nc))
+    lf.leafi_get_autotuners(idx, alpha, qp)
+    P = np.zeros((NQ, F), np.float32)
+    lf.leafi_filter_predict(idx, Q, P)
+    lf.leafi_set_calibration_confidence(idx, 0.0)
+    lf.leafi_set_search_batch(idx, batch)
+    lf.leafi_set_query_schedule(idx, sched)
+    try:
+        ids = np.zeros((NQ, k), np.int64)
+        d = np.zeros((NQ, k), np.float32)
+        sc = np.full((NQ, t.L), 7, np.uint8)
+        lf.leafi_search_scanned(idx, Q, k, target, ids, d, sc)
+    finally:
+        lf.leafi_set_calibration_confidence(idx, 0.95)
+        lf.leafi_set_search_batch(idx, 256)
+        lf.leafi_set_query_schedule(idx, True)
+    j = -1 if target >= 1.0 else O.offset_position(qp[0 if k == 1 else 1], target, kk=k,
+                                                    confidence=0.0)
+    o_ids, o_d2, o_st, _, o_sc = O.leafi_search_pred(t, P.astype(np.float64), fl, alpha, Q, k,
+                                                     j, 4, return_scanned=True)
+    assert np.array_equal(ids, o_ids) and np.array_equal(d, np.sqrt(o_d2))
+    assert np.array_equal(sc, o_sc)
+    assert (sc[np.arange(NQ), t.route(Q)] == 1).all()
+    assert 0 < sc.sum() < NQ * t.L          # some leaves searched, some pruned
+    if j >= 0:
+        assert o_st[:, 3].sum() > 0         # some filter pruned a leaf
+
+
 @pytest.mark.parametrize("k,target", [(1, 0.99), (1, 0.9), (10, 0.95)])
 def test_leafi_search_bit_exact_on_gpu_predictions(ds, tuned, k, target):
     """Alg. 2 with filters on the GPU equals the oracle's fed the GPU's
