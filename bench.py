@@ -84,8 +84,8 @@ def parse():
     ap.add_argument("--wave", type=int, default=None,
                     help="leaves per wave (64; 512 for the iSAX configuration's small leaves)")
     ap.add_argument("--target", type=float, default=0.99)
-    ap.add_argument("--cpu-sample", type=int, default=1024,
-                    help="queries of the oracle's timed sample (about 10 s on 16 host threads)")
+    ap.add_argument("--cpu-sample", type=int, default=3072,
+                    help="queries of the oracle's timed sample (about 12 s on 16 host threads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schedule", action="store_true",
                     help="batches in the callers' query order (no route-leaf scheduling)")
