@@ -185,16 +185,6 @@ __global__ void sqrt_kernel(const float* __restrict__ in, float* __restrict__ ou
   if (i < n) out[i] = __fsqrt_rn(in[i]);
 }
 
-__global__ void search_init_kernel(int nq, int32_t* topk_cnt, unsigned long long* thr,
-                                   int32_t* cand_cnt, int32_t* done) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nq) return;
-  topk_cnt[q] = 0;
-  thr[q] = kNoKey;
-  cand_cnt[q] = 0;
-  done[q] = 0;
-}
-
 __global__ void slots_init_kernel(int nslots, int32_t* topk_cnt, unsigned long long* thr,
                                   int32_t* cand_cnt) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1018,15 +1008,11 @@ void Pipeline::enqueue_head(const LaneView& v, int nb, bool use_f) {
   compute_bounds(ix, v.gQ, nb, v.lb2, v.route, pre_p);
   ix->tock();
   launch_query_prep(ix, v.gQ, nb, v.tq, s);
-  if (use_f)
-    launch_jpos(nb, v.dK, v.dT, ix->nk, ix->d_kclasses.p, ix->qprime.p, ix->nc, v.jpos, s);
-  LF_CUDA(cudaMemsetAsync(v.scanned, 0, (size_t)nb * L, s));
   if (W < L) launch_leaf_order(nb, L, v.lb2, v.ord, s, v.order_tmp);  // a wave of W >= L needs no order
-  LF_CUDA(cudaMemsetAsync(v.cursor, 0, sizeof(int32_t) * nb, s));
-  search_init_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, v.topk_cnt, v.thr, v.cand_cnt, v.done);
-  LF_CHECK_LAUNCH();
-  // wave 0: every query searches its route leaf
-  launch_route_pairs(nb, v.route, L, v.scanned, ix->leaf_off.p, v.pairs, v.np, stat, s);
+  // per-query state and wave 0: every query searches its route leaf
+  launch_batch_init(nb, L, v.route, v.scanned, ix->leaf_off.p, v.pairs, v.np, stat, v.cursor,
+                    v.topk_cnt, v.thr, v.cand_cnt, v.done, v.dK, v.dT, ix->nk, ix->d_kclasses.p,
+                    ix->qprime.p, ix->nc, use_f ? v.jpos : nullptr, s);
   run_round(ix, v.gQ, v.tq, v.pairs, v.np, nb, nb, kmax, v.dK, v.topk, v.topk_cnt, v.thr, v.cand,
             v.cand_cnt, cap, stat + 2, stat + 3);
   // the filters run once the route leaves have set a best-so-far: only the

@@ -371,14 +371,19 @@ void launch_select_all(const SelectArgs& a, cudaStream_t s);
 void launch_filter_need(int nq, int F, int L, const int32_t* filter_leaf, const double* lb2,
                         const unsigned long long* thr, const unsigned char* scanned,
                         const int32_t* jpos, int32_t* rows_of, int32_t* cnt, cudaStream_t s);
-void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
-                        const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
-                        unsigned long long* stat, cudaStream_t s);
 void launch_leafknn_pairs(int nq, int nl, const int32_t* leaves, int L, Pair* pairs,
                           int32_t* npairs, cudaStream_t s);
 void launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_t s);
-void launch_jpos(int nq, const int32_t* k, const double* target, int nk, const int32_t* kclasses,
-                 const double* qprime, int nc, int32_t* jpos, cudaStream_t s);
+// a batch's per-query state before its first wave in one launch: searched flags
+// (route leaf only), route pairs (npairs = nq, stat[0..1] counted), cursor,
+// list counts, thresholds, candidate counts, done flags and, with jpos non-null,
+// the sorted offset positions
+void launch_batch_init(int nq, int L, const int32_t* route, unsigned char* scanned,
+                       const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
+                       unsigned long long* stat, int32_t* cursor, int32_t* topk_cnt,
+                       unsigned long long* thr, int32_t* cand_cnt, int32_t* done,
+                       const int32_t* k, const double* target, int nk, const int32_t* kclasses,
+                       const double* qprime, int nc, int32_t* jpos, cudaStream_t s);
 void launch_write_results(int nq, int kmax, const int32_t* kq, const unsigned long long* topk,
                           int kstride, const int32_t* topk_cnt, int64_t* ids, float* dists,
                           cudaStream_t s,

@@ -810,20 +810,6 @@ __global__ void done_all_kernel(int nq, int32_t* __restrict__ done) {
   if (q < nq) done[q] = 1;
 }
 
-__global__ void route_pairs_kernel(int nq, const int32_t* __restrict__ route, int L,
-                                   unsigned char* __restrict__ scanned,
-                                   const int64_t* __restrict__ leaf_off, Pair* __restrict__ pairs,
-                                   int32_t* __restrict__ npairs, u64* __restrict__ stat) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q == 0) *npairs = nq;
-  if (q >= nq) return;
-  const int leaf = route[q];
-  scanned[(size_t)q * L + leaf] = 1;
-  pairs[q] = Pair{q, q, leaf, 0};
-  atomicAdd(&stat[0], 1ull);
-  atomicAdd(&stat[1], (u64)(leaf_off[leaf + 1] - leaf_off[leaf]));
-}
-
 __global__ void leafknn_pairs_kernel(int nq, int nl, const int32_t* __restrict__ leaves, int L,
                                      Pair* __restrict__ pairs, int32_t* __restrict__ npairs) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -840,21 +826,17 @@ __global__ void fill_u64_kernel(u64* p, u64 v, size_t n) {
 
 // sorted position per query (Sec. 4.4.2 with the STEP reading): the query's
 // k picks the smallest calibrated class >= k; the position is the largest j
-// whose calibrated quality qprime[class][j] still reaches rq[q], the quality
+// whose calibrated quality qprime[class][j] still reaches rq, the quality
 // that certifies the query's recall target (computed on the host from the
 // binomial tail of the calibration misses); rq > 1 leaves no position (exact).
-__global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double* __restrict__ rq,
-                            int nk, const int32_t* __restrict__ kclasses,
-                            const double* __restrict__ qprime, int nc, int32_t* __restrict__ jpos) {
-  // one warp per query; the table is read 32 entries at a time and the
-  // position is the entry before the first one below the target
-  const int q = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (q >= nq) return;
-  const double r = rq[q];
+// Computed by a whole warp (every lane gets the result): the table is read 32
+// entries at a time and the position is the entry before the first one below
+// the target.
+__device__ __forceinline__ int jpos_of(int kq, double r, int nk, const int32_t* __restrict__ kclasses,
+                                       const double* __restrict__ qprime, int nc, int lane) {
   int c = -1;
   for (int i = 0; i < nk; ++i)
-    if (kclasses[i] >= k[q]) {
+    if (kclasses[i] >= kq) {
       c = i;
       break;
     }
@@ -874,7 +856,45 @@ __global__ void jpos_kernel(int nq, const int32_t* __restrict__ k, const double*
       }
     }
   }
-  if (lane == 0) jpos[q] = j;
+  return j;
+}
+
+// A batch's per-query state before its first wave, one warp per query: the
+// searched flags cleared and the route leaf marked, the route leaf's pair
+// (wave 0 of Alg. 2), the wave cursor, list counts, thresholds and done flags,
+// and (jpos non-null) the sorted offset position.
+__global__ void batch_init_kernel(int nq, int L, const int32_t* __restrict__ route,
+                                  unsigned char* __restrict__ scanned,
+                                  const int64_t* __restrict__ leaf_off, Pair* __restrict__ pairs,
+                                  int32_t* __restrict__ npairs, u64* __restrict__ stat,
+                                  int32_t* __restrict__ cursor, int32_t* __restrict__ topk_cnt,
+                                  u64* __restrict__ thr, int32_t* __restrict__ cand_cnt,
+                                  int32_t* __restrict__ done, const int32_t* __restrict__ k,
+                                  const double* __restrict__ rq, int nk,
+                                  const int32_t* __restrict__ kclasses,
+                                  const double* __restrict__ qprime, int nc,
+                                  int32_t* __restrict__ jpos) {
+  const int q = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q == 0 && lane == 0) *npairs = nq;
+  if (q >= nq) return;
+  const int leaf = route[q];
+  unsigned char* sc = scanned + (size_t)q * L;
+  for (int l = lane; l < L; l += 32) sc[l] = l == leaf ? 1 : 0;
+  if (jpos) {
+    const int j = jpos_of(k[q], rq[q], nk, kclasses, qprime, nc, lane);
+    if (lane == 0) jpos[q] = j;
+  }
+  if (lane == 0) {
+    pairs[q] = Pair{q, q, leaf, 0};
+    atomicAdd(&stat[0], 1ull);
+    atomicAdd(&stat[1], (u64)(leaf_off[leaf + 1] - leaf_off[leaf]));
+    cursor[q] = 0;
+    topk_cnt[q] = 0;
+    thr[q] = kNoKey;
+    cand_cnt[q] = 0;
+    done[q] = 0;
+  }
 }
 
 // results of batch query q go to row rows[q] of ids / dists (row q without rows)
@@ -1013,14 +1033,6 @@ void launch_select_walk(const SelectArgs& a, const int32_t* ord, int32_t* cursor
   LF_CHECK_LAUNCH();
 }
 
-void launch_route_pairs(int nq, const int32_t* route, int L, unsigned char* scanned,
-                        const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
-                        unsigned long long* stat, cudaStream_t s) {
-  route_pairs_kernel<<<nblk(nq > 0 ? nq : 1, 128), 128, 0, s>>>(nq, route, L, scanned, leaf_off,
-                                                                 pairs, npairs, stat);
-  LF_CHECK_LAUNCH();
-}
-
 void launch_leafknn_pairs(int nq, int nl, const int32_t* leaves, int L, Pair* pairs,
                           int32_t* npairs, cudaStream_t s) {
   LF_CUDA(cudaMemsetAsync(npairs, 0, sizeof(int32_t), s));
@@ -1035,10 +1047,15 @@ void launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cuda
   LF_CHECK_LAUNCH();
 }
 
-void launch_jpos(int nq, const int32_t* k, const double* target, int nk, const int32_t* kclasses,
-                 const double* qprime, int nc, int32_t* jpos, cudaStream_t s) {
-  if (nq <= 0) return;
-  jpos_kernel<<<nblk((int64_t)nq * 32, 256), 256, 0, s>>>(nq, k, target, nk, kclasses, qprime, nc, jpos);
+void launch_batch_init(int nq, int L, const int32_t* route, unsigned char* scanned,
+                       const int64_t* leaf_off, Pair* pairs, int32_t* npairs,
+                       unsigned long long* stat, int32_t* cursor, int32_t* topk_cnt,
+                       unsigned long long* thr, int32_t* cand_cnt, int32_t* done,
+                       const int32_t* k, const double* target, int nk, const int32_t* kclasses,
+                       const double* qprime, int nc, int32_t* jpos, cudaStream_t s) {
+  batch_init_kernel<<<nblk((int64_t)(nq > 0 ? nq : 1) * 32, 256), 256, 0, s>>>(
+      nq, L, route, scanned, leaf_off, pairs, npairs, stat, cursor, topk_cnt, thr, cand_cnt, done,
+      k, target, nk, kclasses, qprime, nc, jpos);
   LF_CHECK_LAUNCH();
 }
 
