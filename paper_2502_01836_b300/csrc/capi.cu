@@ -457,13 +457,12 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.gfirst = gfirst;
     t.gbound = gbound;
     t.qkeys = qkeys;
-    t.work = ix->sc->sWork.need(1);
-    LF_CUDA(cudaMemsetAsync(t.work, 0, sizeof(int32_t), s));
+    t.work = ix->sc->sWork.need(1);  // zeroed by the round's prep kernel
     t.topk = topk;
     t.glock = ix->sc->sGlock.need(nslots);
     t.ub = kstride == 1 ? ix->sc->sUb.need(nslots) : nullptr;
     t.lock_tries = ix->lock_tries;
-    launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, t.ub, s);
+    launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, t.ub, t.work, s);
     t.err = ix->sErr.p;
     t.stat = recheck_stat;
     t.prof = ix->profiling >= 2 ? ix->scan_prof.p : nullptr;

@@ -285,10 +285,12 @@ void launch_tc_query_prep8(const float* Q, int nq, int mp, int kp, unsigned char
 void launch_tc_scan(const CUtensorMap& tmap, const TcScanArgs& a, const int32_t* n_items_dev,
                     const int32_t* slot_k, int grid, cudaStream_t s);
 // before a tensor-core round: pad every slot's list (entries [cnt, k)) with
-// kNoKey and release the slot locks; after it: count the list entries and
-// set each slot's threshold (its k-th key, kNoKey while fewer than k)
+// kNoKey, release the slot locks, reset the shared upper bounds and zero the
+// work-item counter; after it: count the list entries and set each slot's
+// threshold (its k-th key, kNoKey while fewer than k)
 void launch_tc_round_prep(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
-                          const int32_t* topk_cnt, int32_t* glock, float* ub, cudaStream_t s);
+                          const int32_t* topk_cnt, int32_t* glock, float* ub, int32_t* work,
+                          cudaStream_t s);
 void launch_tc_round_finish(int nslots, int kstride, const int32_t* slot_k,
                             const unsigned long long* topk, int32_t* topk_cnt,
                             unsigned long long* thr, cudaStream_t s);

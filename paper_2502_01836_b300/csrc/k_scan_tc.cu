@@ -1234,8 +1234,10 @@ int tc_scan_plan(int rb, int k, int smem_optin, size_t* smem, int* qkeys) {
 namespace {
 __global__ void round_prep_kernel(int nslots, int kstride, const int32_t* __restrict__ slot_k,
                                   u64* __restrict__ topk, const int32_t* __restrict__ topk_cnt,
-                                  int32_t* __restrict__ glock, float* __restrict__ ub) {
+                                  int32_t* __restrict__ glock, float* __restrict__ ub,
+                                  int32_t* __restrict__ work) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *work = 0;
   if (t >= (int64_t)nslots * kstride) return;
   const int slot = (int)(t / kstride), z = (int)(t % kstride);
   if (z >= topk_cnt[slot]) topk[t] = kNoKey;
@@ -1265,11 +1267,11 @@ __global__ void round_finish_kernel(int nslots, int kstride, const int32_t* __re
 }  // namespace
 
 void launch_tc_round_prep(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
-                          const int32_t* topk_cnt, int32_t* glock, float* ub, cudaStream_t s) {
-  const int64_t tot = (int64_t)nslots * kstride;
-  if (tot == 0) return;
+                          const int32_t* topk_cnt, int32_t* glock, float* ub, int32_t* work,
+                          cudaStream_t s) {
+  const int64_t tot = std::max<int64_t>((int64_t)nslots * kstride, 1);
   round_prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nslots, kstride, slot_k, topk,
-                                                                   topk_cnt, glock, ub);
+                                                                   topk_cnt, glock, ub, work);
   LF_CHECK_LAUNCH();
 }
 
