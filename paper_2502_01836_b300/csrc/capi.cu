@@ -413,11 +413,24 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
       use_tc ? ix->sc->sItemLeaf.need(std::max((size_t)std::max(npairs_max, 1) * max_parts(ix),
                                                (size_t)3 * target + 1))
              : nullptr;
-  launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, ix->part,
-               use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped, nitems,
-               distinct_stat, s, var_groups ? nullptr : item_leaf,
-               use_tc && !var_groups && ix->pack_small, var_groups ? 0 : target,
-               var_groups ? nullptr : part_dev, std::min(ix->min_part, ix->part));
+  // the tensor-core round's prep rides on the one-block grouping kernel when small
+  RoundPrep rp;
+  if (use_tc) {
+    rp.topk = topk;
+    rp.topk_cnt = topk_cnt;
+    rp.glock = ix->sc->sGlock.need(nslots);
+    rp.ub = kstride == 1 ? ix->sc->sUb.need(nslots) : nullptr;
+    rp.work = ix->sc->sWork.need(1);
+    rp.nslots = nslots;
+    rp.kstride = kstride;
+  }
+  const bool prepped =
+      launch_group(pairs, dNpairs, npairs_max, L, ix->leaf_off.p, ix->part,
+                   use_tc ? tc_group_size(kstride) : scan_group_size(), cnt, goff, ioff, grouped,
+                   nitems, distinct_stat, s, var_groups ? nullptr : item_leaf,
+                   use_tc && !var_groups && ix->pack_small, var_groups ? 0 : target,
+                   var_groups ? nullptr : part_dev, std::min(ix->min_part, ix->part),
+                   use_tc ? &rp : nullptr);
   int32_t *gfirst = nullptr, *gbound = nullptr;
   if (var_groups) {
     int32_t* ngr = ix->sc->sNGroups.need(L);
@@ -457,12 +470,12 @@ void run_round(leafi_index* ix, const float* dQ, const TcQueries& tq, const Pair
     t.gfirst = gfirst;
     t.gbound = gbound;
     t.qkeys = qkeys;
-    t.work = ix->sc->sWork.need(1);  // zeroed by the round's prep kernel
+    t.work = rp.work;  // zeroed by the round's prep
     t.topk = topk;
-    t.glock = ix->sc->sGlock.need(nslots);
-    t.ub = kstride == 1 ? ix->sc->sUb.need(nslots) : nullptr;
+    t.glock = rp.glock;
+    t.ub = rp.ub;
     t.lock_tries = ix->lock_tries;
-    launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, t.ub, t.work, s);
+    if (!prepped) launch_tc_round_prep(nslots, kstride, slot_k, topk, topk_cnt, t.glock, t.ub, t.work, s);
     t.err = ix->sErr.p;
     t.stat = recheck_stat;
     t.prof = ix->profiling >= 2 ? ix->scan_prof.p : nullptr;

@@ -309,14 +309,25 @@ void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* 
                        int32_t* ngroups, int32_t* gfirst, int32_t* gbound, int32_t* item_off,
                        int32_t* item_leaf, int32_t* n_items_dev, cudaStream_t s,
                        int target_items = 0, int32_t* part_out = nullptr, int min_part = 128);
+// The tensor-core round's prep (launch_tc_round_prep's work), which the
+// one-block grouping kernel takes on when it is small
+struct RoundPrep {
+  unsigned long long* topk = nullptr;  // null: nothing to prepare
+  const int32_t* topk_cnt = nullptr;
+  int32_t* glock = nullptr;
+  float* ub = nullptr;
+  int32_t* work = nullptr;
+  int nslots = 0, kstride = 0;
+};
 // stat (nullable): stat[0] += series of the distinct leaves in this round;
-// g = queries per work item of the scan kernel that follows
-void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
+// g = queries per work item of the scan kernel that follows; rp (nullable):
+// returns true when the grouping launch also did the round's prep
+bool launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s, int32_t* item_leaf = nullptr,
                   bool pack_small = false, int target_items = 0, int32_t* part_out = nullptr,
-                  int min_part = 128);
+                  int min_part = 128, const RoundPrep* rp = nullptr);
 
 void launch_merge(int nslots, int kstride, const int32_t* slot_k, unsigned long long* topk,
                   int32_t* topk_cnt, unsigned long long* thr, const unsigned long long* cand,

@@ -363,8 +363,22 @@ __global__ void __launch_bounds__(1024) group_fused_kernel(
     const int64_t* __restrict__ leaf_off, int part_max, int g, int32_t* __restrict__ grp_off,
     int32_t* __restrict__ item_off, int32_t* __restrict__ n_items, Pair* __restrict__ grouped,
     unsigned long long* __restrict__ stat, int32_t* __restrict__ item_leaf, bool pack_small,
-    int target, int min_part, int32_t* __restrict__ part_out) {
+    int target, int min_part, int32_t* __restrict__ part_out, RoundPrep rp) {
   __shared__ int cnt[kFuseLeaves];
+  if (rp.topk) {
+    // the following scan round's prep: lists padded past their counts, locks
+    // released, shared upper bounds reset, work counter zeroed
+    const int64_t tot = (int64_t)rp.nslots * rp.kstride;
+    for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int slot = (int)(t / rp.kstride), z = (int)(t % rp.kstride);
+      if (z >= rp.topk_cnt[slot]) rp.topk[t] = kNoKey;
+      if (z == 0) {
+        rp.glock[slot] = 0;
+        if (rp.ub) rp.ub[slot] = __int_as_float(0x7f800000);
+      }
+    }
+    if (threadIdx.x == 0) *rp.work = 0;
+  }
   __shared__ int s_a[1024], s_b[1024];
   __shared__ int tot[kPartLevels];
   const int T = blockDim.x;
@@ -953,17 +967,22 @@ void launch_scan(const ScanArgs& a, const int32_t* n_items_dev, const int32_t* s
   LF_CHECK_LAUNCH();
 }
 
-void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
+bool launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, int L,
                   const int64_t* leaf_off, int part, int g, int32_t* cnt, int32_t* grp_off,
                   int32_t* item_off, Pair* grouped, int32_t* n_items_dev,
                   unsigned long long* stat, cudaStream_t s, int32_t* item_leaf,
-                  bool pack_small, int target_items, int32_t* part_out, int min_part) {
+                  bool pack_small, int target_items, int32_t* part_out, int min_part,
+                  const RoundPrep* rp) {
   if (L <= kFuseLeaves) {
+    // the one-block kernel also preps the round while that is at most 16
+    // entries per thread
+    const bool fuse = rp && rp->topk && (int64_t)rp->nslots * rp->kstride <= 16 * 1024;
     group_fused_kernel<<<1, 1024, 0, s>>>(pairs, npairs_dev, L, leaf_off, part, g, grp_off,
                                           item_off, n_items_dev, grouped, stat, item_leaf,
-                                          pack_small, target_items, min_part, part_out);
+                                          pack_small, target_items, min_part, part_out,
+                                          fuse ? *rp : RoundPrep());
     LF_CHECK_LAUNCH();
-    return;
+    return fuse;
   }
   LF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * L, s));
   if (npairs_max > 0) {
@@ -977,6 +996,7 @@ void launch_group(const Pair* pairs, const int32_t* npairs_dev, int npairs_max, 
     scatter_kernel<<<nblk(npairs_max, 256), 256, 0, s>>>(pairs, npairs_dev, grp_off, cnt, grouped);
     LF_CHECK_LAUNCH();
   }
+  return false;
 }
 
 void launch_var_groups(int L, const int64_t* leaf_off, int part, const int32_t* grp_off,
